@@ -1,0 +1,495 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: counts
+printed in the paper's benchmark matrix, closed forms, exact invariants
+(free-stream preservation, discrete conservation, closed-surface sums),
+k-exactness of the least-squares reconstruction (Eqs. 3-4), library
+least-squares on the same systems, textbook properties of the HLLC and
+Newtonian viscous fluxes, the SSP-RK3 stability polynomial, the design
+order of accuracy on exact Euler solutions, and the Taylor-Green initial
+diagnostics.  None of these touch the GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_07387_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            rows[k] = [float(x) for x in v]
+    return rows
+
+
+@pytest.fixture(scope="module")
+def jhex8_p2():
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=1)
+    return nodes, cells, box, O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+
+
+@pytest.fixture(scope="module")
+def jtet_p2():
+    nodes, cells, box = I.hex_lattice(5, jitter=0.1, seed=2)
+    tets = I.split_tets(cells)
+    return nodes, tets, box, O.Case(nodes, tets, box, O.Params(order=2, scheme=1))
+
+
+# --------------------------------------------------------------- counts ---
+def test_counts_match_benchmark_matrix(jhex8_p2):
+    """Table 2 (TGV-P2): 3 faces per hex, 54M/2M = 27 reconstructed DoF per
+    cell and variable (9 central + 6 linear directional x 3), 24M/6M = 4
+    quadrature points per face."""
+    g = _golden("benchmark_matrix.txt")["TGV-P2"]
+    cells, faces, dof, qps = g
+    c = jhex8_p2[3]
+    assert c.n_faces == round(faces / cells) * c.n_cells
+    assert c.K + c.nd * 3 == round(dof / cells)
+    assert c.nq == round(qps / faces)
+    # Eq. 3: K(r,d) = (r+1)(r+2)(r+3)/6 = 10 terms incl. the mean -> 9 modes
+    assert c.K == math.comb(2 + 3, 3) - 1
+    assert c.Mc == 2 * c.K and c.nd == 6 and c.Md == 6
+
+
+def test_counts_p1_and_tets(jtet_p2):
+    nodes, cells, box = I.hex_lattice(4)
+    c1 = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
+    assert (c1.K, c1.Mc, c1.nd, c1.nq, c1.n_faces) == (3, 6, 0, 1, 3 * 64)
+    ct = jtet_p2[3]
+    assert ct.n_cells == 6 * 125 and ct.n_faces == 2 * ct.n_cells
+    assert (ct.K, ct.Mc, ct.nd, ct.Md, ct.nq) == (9, 18, 4, 6, 4)
+
+
+# ------------------------------------------------------------- geometry ---
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_geometry_closed_surfaces_and_volume(kind, jhex8_p2, jtet_p2):
+    nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
+    vol, cen, hh = c.geometry()
+    assert abs(vol.sum() - (2 * math.pi) ** 3) <= 1e-12 * (2 * math.pi) ** 3
+    assert np.all(vol > 0)
+    s = c.surface_sums()
+    assert np.abs(s).max() <= 1e-14 * hh.max() ** 2 * 10
+    # each face's area vectors sum to the owner-outward area vector; the
+    # periodic neighbour image is adjacent to the owner
+    fo, fn, sh = c.faces()
+    d = cen[fn] + sh * box - cen[fo]
+    assert np.linalg.norm(d, axis=1).max() < 2.0 * hh.max()
+
+
+def test_uniform_lattice_centroids_exact():
+    n = 6
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
+    vol, cen, hh = c.geometry()
+    h = 2 * math.pi / n
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ref = np.stack([(i.ravel() + 0.5) * h, (j.ravel() + 0.5) * h, (k.ravel() + 0.5) * h], axis=1)
+    assert np.abs(cen - ref).max() < 1e-13
+    assert np.abs(vol - h ** 3).max() < 1e-13 * h ** 3
+    # face quadrature of an axis-aligned square: 1 point, area vector h^2 e_d
+    x, dS = c.face_quad(0)
+    assert np.isclose(np.linalg.norm(dS), h * h, rtol=1e-14)
+
+
+def test_face_quadrature_integrates_bilinear_exactly(jhex8_p2):
+    """2x2 Gauss points on each (bilinear) face: sum_alpha f(x_alpha) dS_alpha
+    is exact for f linear in x; the divergence theorem then gives
+    oint x_j dS_i = V delta_ij per cell."""
+    nodes, cells, box, c = jhex8_p2
+    vol, cen, hh = c.geometry()
+    fo, fn, sh = c.faces()
+    acc = np.zeros((c.n_cells, 3, 3))
+    for f in range(c.n_faces):
+        x, dS = c.face_quad(f)
+        acc[fo[f]] += np.einsum("qi,qj->ij", dS, x - cen[fo[f]])
+        xn = x - sh[f] * box - cen[fn[f]]
+        acc[fn[f]] -= np.einsum("qi,qj->ij", dS, xn)
+    ref = vol[:, None, None] * np.eye(3)[None]
+    assert np.abs(acc - ref).max() < 1e-12 * vol.max()
+
+
+# ------------------------------------------------------ least squares ---
+@pytest.mark.parametrize("which", [-1, 0, 3])
+def test_pseudo_inverse_matches_lstsq(jhex8_p2, which):
+    """P' = A^+ diag(|V_m|) (Eq. 4): a left inverse of A diag(1/|V_m|), and
+    equal to numpy's least-squares solution of the same system."""
+    nodes, cells, box, c = jhex8_p2
+    vol, _, _ = c.geometry()
+    for i in (0, 77, 300, 511):
+        mem, sh, A, P = c.stencil(i, which)
+        Vm = vol[mem]
+        K = A.shape[1]
+        assert np.abs(P @ (A / Vm[:, None]) - np.eye(K)).max() < 1e-12
+        ref = np.linalg.lstsq(A, np.diag(Vm), rcond=None)[0]
+        assert np.abs(P - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_stencil_membership_hex_lattice():
+    """P2 central = 6 face + 12 edge neighbours; directional stencil of face
+    f = its neighbour plus that neighbour's 5 other face neighbours."""
+    n = 6
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+    ijk = lambda q: (q % n, (q // n) % n, q // (n * n))
+    i = 0
+    mem, sh, A, P = c.stencil(i, -1)
+    offs = set()
+    for m, s in zip(mem, sh):
+        a = np.array(ijk(m)) + s * n
+        offs.add(tuple(a))
+    ref = {(a, b, d) for a in (-1, 0, 1) for b in (-1, 0, 1) for d in (-1, 0, 1)
+           if 1 <= abs(a) + abs(b) + abs(d) <= 2}
+    assert offs == ref
+    for s_ in range(6):
+        mem, sh, A, P = c.stencil(i, s_)
+        offs = [tuple(np.array(ijk(m)) + s * n) for m, s in zip(mem, sh)]
+        axis = np.array(offs[0])
+        assert np.abs(axis).sum() == 1
+        for o in offs[1:]:
+            assert np.abs(np.array(o) - axis).sum() == 1 and o != (0, 0, 0)
+
+
+# --------------------------------------------------------- k-exactness ---
+def _random_poly(rng, degree):
+    p = rng.normal(size=(5, 10))
+    if degree < 2:
+        p[:, 4:] = 0.0
+    if degree < 1:
+        p[:, 1:] = 0.0
+    p[0, 0] += 5.0
+    return p
+
+
+def _poly_eval(p, x):
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    m = np.stack([np.ones_like(X), X, Y, Z, X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z], axis=1)
+    g = np.zeros((x.shape[0], 10, 3))
+    g[:, 1, 0] = 1; g[:, 2, 1] = 1; g[:, 3, 2] = 1
+    g[:, 4, 0] = 2 * X; g[:, 5, 1] = 2 * Y; g[:, 6, 2] = 2 * Z
+    g[:, 7, 0] = Y; g[:, 7, 1] = X; g[:, 8, 0] = Z; g[:, 8, 2] = X; g[:, 9, 1] = Z; g[:, 9, 2] = Y
+    return m @ p.T, np.einsum("qkj,vk->qvj", g, p)
+
+
+@pytest.mark.parametrize(
+    "order,scheme,degree,kind",
+    [(1, 0, 1, "hex"), (2, 0, 2, "hex"), (2, 1, 1, "hex"), (2, 0, 2, "tet"), (2, 1, 1, "tet")],
+)
+def test_k_exact_reconstruction(order, scheme, degree, kind):
+    """Cell averages of any polynomial of degree <= r are reproduced exactly
+    by the degree-r least-squares reconstruction (Eqs. 3-4), including cells
+    whose stencils cross the periodic boundary; CWENOZ (Eqs. 5-6) is exact
+    for degree <= 1, where every candidate is."""
+    nodes, cells, box = I.hex_lattice(6 if kind == "hex" else 5, jitter=0.1, seed=3)
+    if kind == "tet":
+        cells = I.split_tets(cells)
+    c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme))
+    rng = np.random.default_rng(7)
+    vol, cen, hh = c.geometry()
+    p = _random_poly(rng, degree) * 0.1
+    for i in (0, 5, c.n_cells // 2, c.n_cells - 1):
+        x = cen[i] + rng.uniform(-0.3, 0.3, size=(4, 3)) * hh[i]
+        val, grad = c.kexact_probe(i, p, x)
+        rv, rg = _poly_eval(p, x)
+        scale = np.abs(rv).max()
+        assert np.abs(val - rv).max() < 1e-11 * scale
+        assert np.abs(grad - rg).max() < 1e-10 * max(1.0, np.abs(rg).max())
+
+
+def test_cwenoz_degree2_not_exact_but_linear_weights_are():
+    """With a quadratic field the directional (linear) candidates are not
+    exact, so the nonlinear CWENOZ weights differ from the linear ones, yet
+    their sum reproduces p_opt only when omega = lambda (Eq. 5)."""
+    nodes, cells, box = I.hex_lattice(6)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+    cl = O.Case(nodes, cells, box, O.Params(order=2, scheme=0))
+    rng = np.random.default_rng(1)
+    p = _random_poly(rng, 2)
+    vol, cen, hh = c.geometry()
+    x = cen[10][None] + 0.2 * hh[10]
+    v1, _ = c.kexact_probe(10, p, x)
+    v0, _ = cl.kexact_probe(10, p, x)
+    rv, _ = _poly_eval(p, x)
+    assert np.abs(v0 - rv).max() < 1e-11 * np.abs(rv).max()
+    assert np.abs(v1 - rv).max() > 1e-9 * np.abs(rv).max()
+
+
+# -------------------------------------------------- smoothness indicator ---
+def test_smoothness_indicator_closed_forms():
+    """SI = sum_{1<=|b|<=r} V^(2|b|/3-1) int (d^b p)^2: on a cube of side h
+    with xi = (x-x_c)/h, p = c xi gives c^2 and p = c (xi^2 - mean) gives
+    c^2 (1/3 + 4)."""
+    nodes, cells, box = I.hex_lattice(5)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+    a = np.zeros(9); a[0] = 0.7
+    assert math.isclose(c.smoothness(3, a, 1), 0.49, rel_tol=1e-13)
+    a = np.zeros(9); a[3] = 0.5
+    assert math.isclose(c.smoothness(3, a, 2), 0.25 * (1.0 / 3.0 + 4.0), rel_tol=1e-13)
+    a = np.zeros(9); a[6] = 1.0  # xi*eta: |grad|^2 mean = 2/12, d_xy^2 = 1
+    assert math.isclose(c.smoothness(3, a, 2), 2.0 / 12.0 + 1.0, rel_tol=1e-13)
+
+
+# ------------------------------------------------------------ invariants ---
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_free_stream_preservation(kind, jhex8_p2, jtet_p2):
+    nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
+    U = np.zeros((5, c.n_cells))
+    U[0], U[1], U[2], U[3], U[4] = 1.1, 0.3, -0.2, 0.15, 75.0
+    R = c.residual(U)
+    assert np.abs(R).max() <= 1e-13 * 75.0
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_discrete_conservation(kind, jhex8_p2, jtet_p2):
+    nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=4)
+    R = c.residual(U)
+    vol, _, _ = c.geometry()
+    tot = (R * vol).sum(axis=1)
+    scale = (np.abs(R) * vol).sum(axis=1)
+    assert np.all(np.abs(tot) <= 1e-13 * scale)
+
+
+def test_residual_deterministic(jhex8_p2):
+    nodes, cells, box, c = jhex8_p2
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=5)
+    assert np.array_equal(c.residual(U), c.residual(U))
+
+
+# ------------------------------------------------------------------ HLLC ---
+def _phys(U, n, g=1.4):
+    r, m, E = U[0], U[1:4], U[4]
+    u = m / r
+    p = (g - 1) * (E - 0.5 * r * u @ u)
+    un = u @ n
+    return np.concatenate([[r * un], r * u * un + p * n, [(E + p) * un]])
+
+
+def _cons(r, u, p, g=1.4):
+    u = np.asarray(u, float)
+    return np.concatenate([[r], r * u, [p / (g - 1) + 0.5 * r * u @ u]])
+
+
+def test_hllc_consistency_contact_upwind_symmetry():
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        U = _cons(rng.uniform(0.5, 2), rng.normal(size=3), rng.uniform(0.5, 3))
+        assert np.allclose(O.hllc(U, U, n), _phys(U, n), rtol=1e-14, atol=1e-14)
+        # stationary contact: equal pressure, zero normal velocity, any density/tangential velocity
+        t = rng.normal(size=3); t -= (t @ n) * n
+        UL = _cons(rng.uniform(0.5, 2), t, 1.3)
+        UR = _cons(rng.uniform(0.5, 2), -t, 1.3)
+        F = O.hllc(UL, UR, n)
+        assert np.allclose(F, np.concatenate([[0], 1.3 * n, [0]]), atol=1e-14)
+        # supersonic to the right: upwind flux of the left state
+        UL = _cons(1.0, 5.0 * n, 1.0)
+        UR = _cons(0.7, 4.0 * n + t, 0.8)
+        assert np.allclose(O.hllc(UL, UR, n), _phys(UL, n), rtol=1e-14, atol=1e-13)
+        # reflection symmetry F(L,R,n) = -F(R,L,-n)
+        UL = _cons(rng.uniform(0.5, 2), rng.normal(size=3), rng.uniform(0.5, 3))
+        UR = _cons(rng.uniform(0.5, 2), rng.normal(size=3), rng.uniform(0.5, 3))
+        assert np.allclose(O.hllc(UL, UR, n), -O.hllc(UR, UL, -n), rtol=1e-13, atol=1e-13)
+        # rotational invariance
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        rot = lambda U: np.concatenate([[U[0]], Q @ U[1:4], [U[4]]])
+        F1 = O.hllc(rot(UL), rot(UR), Q @ n)
+        assert np.allclose(F1, rot(O.hllc(UL, UR, n)), rtol=1e-12, atol=1e-12)
+
+
+def test_hllc_sod_interface_flux():
+    """Sod's shock tube: the exact solution at the interface is the left star
+    state (rho = 0.42632, u = 0.92745, p = 0.30313, Toro's tabulated values).
+    HLLC approximates that Godunov flux: mass and energy within 10 %."""
+    g = 1.4
+    n = np.array([1.0, 0.0, 0.0])
+    UL, UR = _cons(1.0, [0, 0, 0], 1.0), _cons(0.125, [0, 0, 0], 0.1)
+    F = O.hllc(UL, UR, n)
+    r, u, p = 0.42632, 0.92745, 0.30313
+    E = p / (g - 1) + 0.5 * r * u * u
+    ex = np.array([r * u, r * u * u + p, 0.0, 0.0, (E + p) * u])
+    assert abs(F[0] - ex[0]) < 0.1 * ex[0]
+    assert abs(F[4] - ex[4]) < 0.1 * ex[4]
+    assert F[2] == 0.0 and F[3] == 0.0
+
+
+# ------------------------------------------------------------- viscous ---
+def test_viscous_flux_linear_velocity_uniform_temperature():
+    """u = G x with uniform T: the flux is the exact Newtonian stress
+    tau = mu (G + G^T - 2/3 tr(G) I) dotted with n, plus u . tau . n."""
+    rng = np.random.default_rng(2)
+    g, Re, Pr, M = 1.4, 1600.0, 0.71, 0.1
+    mu = 1 / Re
+    Rg = 1 / (g * M * M)
+    for _ in range(10):
+        G = rng.normal(size=(3, 3))
+        x0 = rng.normal(size=3)
+        r = rng.uniform(0.5, 2.0)
+        u = G @ x0
+        T = 1.3
+        p = r * Rg * T
+        # conserved gradients of (rho = const, m = rho G x, E = p/(g-1) + rho |u|^2/2)
+        gU = np.zeros((5, 3))
+        gU[1:4] = r * G
+        gU[4] = r * (G.T @ u)
+        U = _cons(r, u, p)
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        tau = mu * (G + G.T - 2.0 / 3.0 * np.trace(G) * np.eye(3))
+        F = O.viscous_flux(U, gU, n, g, Re, Pr, M)
+        assert np.allclose(F[1:4], tau @ n, rtol=1e-12, atol=1e-15)
+        assert math.isclose(F[4], u @ tau @ n, rel_tol=1e-11, abs_tol=1e-15)
+        assert F[0] == 0.0
+
+
+def test_viscous_flux_heat_conduction_and_rest():
+    g, Re, Pr, M = 1.4, 1600.0, 0.71, 0.1
+    mu = 1 / Re
+    Rg = 1 / (g * M * M)
+    kap = mu * g * Rg / (g - 1) / Pr
+    # fluid at rest, uniform pressure, linear T: rho = p/(R T)
+    p, T, dT = 71.4, 1.0, np.array([0.3, -0.1, 0.2])
+    r = p / (Rg * T)
+    dr = -p / (Rg * T * T) * dT
+    gU = np.zeros((5, 3)); gU[0] = dr
+    U = _cons(r, [0, 0, 0], p)
+    n = np.array([0.0, 0.6, 0.8])
+    F = O.viscous_flux(U, gU, n, g, Re, Pr, M)
+    assert np.allclose(F[:4], 0.0, atol=1e-15)
+    assert math.isclose(F[4], kap * dT @ n, rel_tol=1e-12)
+    # uniform flow: no viscous flux
+    F = O.viscous_flux(_cons(1.0, [0.3, 0.2, 0.1], 2.0), np.zeros((5, 3)), n, g, Re, Pr, M)
+    assert np.all(F == 0.0)
+
+
+# -------------------------------------------------------------------- RK ---
+def test_ssprk3_stability_polynomial():
+    for z in (-0.3, -1.0, -2.5, 0.7, 0.05):
+        ref = 1 + z + z * z / 2 + z ** 3 / 6
+        assert math.isclose(O.ssprk3_linear(z, 1.0, 1.0), ref, rel_tol=1e-15)
+
+
+# ---------------------------------------------------------- Taylor-Green ---
+def test_tgv_initial_diagnostics_converge_to_closed_forms():
+    gold = _golden("tgv_initial.txt")
+    out = []
+    for n in (16, 32):
+        nodes, cells, box = I.hex_lattice(n)
+        c = O.Case(nodes, cells, box, O.Params(order=2, scheme=0, Mach=0.1))
+        U = c.cell_average("tgv", [0.1, 1.4])
+        out.append(c.diagnostics(U))
+    ke = [abs(o[0] - gold["KE0"][0]) for o in out]
+    es = [abs(o[1] - gold["eps_s0_Re1600"][0]) for o in out]
+    assert ke[1] < 0.3 * ke[0] and ke[1] < 2e-3      # O(h^2) to 1/8
+    assert es[1] < 0.3 * es[0] and es[1] < 0.06 * gold["eps_s0_Re1600"][0]
+    assert all(o[2] < 1e-3 * gold["eps_s0_Re1600"][0] for o in out)
+
+
+def test_tgv_initial_ke_mach_independent():
+    nodes, cells, box = I.hex_lattice(12)
+    kes = []
+    for M in (0.1, 1.25):
+        c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0, Mach=M))
+        kes.append(c.diagnostics(c.cell_average("tgv", [M, 1.4]))[0])
+    assert abs(kes[0] - kes[1]) < 2e-3 * 0.125
+
+
+# ---------------------------------------------------- order of accuracy ---
+def _density_wave_error(n, order, scheme, T=0.05):
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=0.0))
+    p = [1.0, 0.2, 1.0, 0.5, 0.25, 1.0, 0.0, 1.4]
+    U = c.cell_average("density_wave", p)
+    nst = int(math.ceil(T / c.time_step(U)))
+    for _ in range(nst):
+        U, _ = c.rk_step(U, T / nst)
+    pe = list(p); pe[6] = T
+    Ue = c.cell_average("density_wave", pe)
+    vol, _, _ = c.geometry()
+    return float((np.abs(U[0] - Ue[0]) * vol).sum() / vol.sum())
+
+
+def _vortex_error(n, order, scheme, T=0.1):
+    nodes, cells, box = I.hex_lattice((n, n, 5), (10.0, 10.0, 50.0 / n))
+    c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=0.0))
+    p = [5.0, 1.0, 5.0, 5.0, 0.5, 0.5, 0.0, 1.4]
+    U = c.cell_average("vortex", p)
+    nst = int(math.ceil(T / c.time_step(U)))
+    for _ in range(nst):
+        U, _ = c.rk_step(U, T / nst)
+    pe = list(p); pe[6] = T
+    Ue = c.cell_average("vortex", pe)
+    vol, _, _ = c.geometry()
+    return float((np.abs(U[0] - Ue[0]) * vol).sum() / vol.sum())
+
+
+@pytest.mark.parametrize("order,scheme,lo", [(1, 0, 1.9), (2, 0, 2.75)])
+def test_order_density_wave(order, scheme, lo):
+    """Smooth density wave advected by a uniform flow (exact Euler
+    solution): L1 error order -> 2 (P1), -> 3 (P2)."""
+    e = [_density_wave_error(n, order, scheme) for n in (8, 16, 32)]
+    assert math.log2(e[1] / e[2]) > lo
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("order,scheme,lo", [(1, 0, 1.9), (2, 0, 2.6), (2, 1, 2.6)])
+def test_order_isentropic_vortex(order, scheme, lo):
+    """Isentropic vortex advected through a periodic box (exact Euler
+    solution; core radius 1, box 10): L1 density error order between
+    n = 32 and 64 near 2 (P1) and 3 (P2 linear and CWENOZ)."""
+    e = [_vortex_error(n, order, scheme) for n in (32, 64)]
+    assert math.log2(e[0] / e[1]) > lo
+
+
+# ------------------------------------------------------ CWENOZ behaviour ---
+def test_cwenoz_weights_normalised_and_tend_to_linear():
+    """Eq. 5: the nonlinear weights are positive and sum to one; on smooth
+    data they approach the linear weights as the mesh is refined (mean
+    deviation; the maximum sits at critical points of the field)."""
+    dev = []
+    for n in (8, 16):
+        nodes, cells, box = I.hex_lattice(n)
+        c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+        U = c.cell_average("tgv", [0.3, 1.4])
+        _, w = c.reconstruct(U, weights=True)
+        assert np.all(w > 0)
+        assert np.abs(w.sum(axis=2) - 1.0).max() < 1e-14
+        lam = np.array([1000.0] + [1.0] * 6) / 1006.0
+        dev.append(np.abs(w - lam).mean())
+    assert dev[1] < 0.4 * dev[0]  # mean deviation falls ~h^2
+
+
+def test_cwenoz_step_is_non_oscillatory():
+    """A density step: the linear P2 reconstruction overshoots the jump at
+    the face points next to it; CWENOZ shifts weight to the smooth
+    directional candidates and stays close to the range of the data."""
+    n = 10
+    nodes, cells, box = I.hex_lattice(n)
+    over = {}
+    for scheme in (0, 1):
+        c = O.Case(nodes, cells, box, O.Params(order=2, scheme=scheme))
+        vol, cen, hh = c.geometry()
+        U = np.zeros((5, c.n_cells))
+        U[0] = np.where(cen[:, 0] < math.pi, 1.0, 2.0)
+        U[4] = 2.5
+        worst = 0.0
+        for i in np.where(np.abs(cen[:, 0] - math.pi) < 0.7 * hh[0])[0][:10]:
+            x = cen[i] + np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]]) * hh[i]
+            val, _ = c.eval(U, int(i), x)
+            worst = max(worst, val[:, 0].max() - 2.0, 1.0 - val[:, 0].min())
+        over[scheme] = worst
+        if scheme == 1:
+            _, w = c.reconstruct(U, weights=True)
+            i = int(np.where(np.abs(cen[:, 0] - math.pi) < 0.7 * hh[0])[0][0])
+            assert w[i, 0, 0] < 0.5  # central candidate loses its weight at the step
+    assert over[0] > 0.05
+    assert over[1] < 0.2 * over[0]

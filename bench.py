@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the explicit residual + SSP-RK3 path in cell-RK-stages/s.
+
+Workload (default): compressible Taylor-Green vortex, Mach 0.1, Re 1600, on
+64^3 hexahedra of [0, 2 pi]^3 with interior nodes jittered by a seeded
+uniform +-10 % of the spacing, P2 least-squares reconstruction with CWENOZ
+weights over central + directional stencils, FP64, SSP-RK3 at CFL 0.5 with
+the CFL time step computed on the device every step.  One "step" is one full
+SSP-RK3 step (3 residual evaluations + the time step reduction); the metric
+counts cells x 3 stages per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ucns|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the path is replicated, not sharded:
+no collective on the data path); value = total cell-stages of all ranks / the
+slowest rank's time.  ``--impl reference`` times the CPU oracle instead (on
+a bounded sample of the same workload, rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-RK-stages/s at P2 on 1 GB300, plain FP64 vs chosen form at fixed KE error"
+UNIT = "cell-RK-stages/s"
+STAGES = 3
+
+# Algorithmic FP64 flop counts of the kernels (each +,-,*,/,sqrt = 1, FMA = 2),
+# counted from the kernel source; derivation in the design doc.
+FLOPS_FACE_P2_VISC_PER_QP = 688
+FLOPS_RECON_P2_CWENOZ_PER_CELL = 4070
+# algorithmic bytes of one launch (each array element crossing HBM once)
+BYTES_FACE_P2_PER_FACE = 4 * 10 * 8 + 8 + 2 * 4 + 5 * 8  # QP geometry, penalty, ids, G
+BYTES_RECON_P2_CWENOZ_PER_CELL = (9 * 18 + 6 * 3 * 6) * 8 + (18 + 36) * 4 + 6 * 8 + 5 * 8 + 10 * 5 * 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ucns", choices=["ucns", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="lattice cells per direction")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def workload(n: int):
+    from paper_2609_07387_gb300 import inputs as I
+
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=1)
+    U = I.tgv_state(nodes, cells, 0.1)
+    return nodes, cells, box, U
+
+
+def config(n: int, N: int, world: int) -> dict:
+    return {
+        "workload": f"TGV M0.1 Re1600, {n}^3 jittered (+-10% h, seed 1) hex = {N} cells, P2 CWENOZ, "
+                    "FP64, SSP-RK3 CFL 0.5, device CFL dt every step",
+        "cells": N,
+        "stages_per_step": STAGES,
+        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+        "l2": "inputs larger than L2 (pseudo-inverses ~0.57 GB at 64^3)",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.rows = []
+        self.proc = None
+        self.bus_id = bus_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd[1:1] = ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "api.cu"):
+        with open(os.path.join(ROOT, "paper_2609_07387_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(kernel)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch_scaled_to"].get(str(n))
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def fp64_peak_tflops(torch) -> float | None:
+    """Measured FP64 throughput: cuBLAS DGEMM 4096^3, best of 3."""
+    try:
+        n = 4096
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = math.inf
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(nodes, cells, box, U, n: int, layers: int):
+    """Build the oracle on the workload and pick a sample: `layers` z-layers
+    of the lattice (layers * n^2 cells)."""
+    import oracle as O
+
+    oc = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5))
+    sel = np.arange(layers * n * n, dtype=np.int64)
+    oc.residual_subset(U, sel[:8])  # warm the lazy precompute path
+    return oc, sel
+
+
+def oracle_rk_step_on_sample(oc, U, sel, dt):
+    """Three SSP-RK3 stages on the sample cells (residual of the sample +
+    Shu-Osher combination), the oracle's arithmetic per stage."""
+    U0 = U[:, sel].copy()
+    Uw = U.copy()
+    R = oc.residual_subset(Uw, sel)
+    U1 = U0 + dt * R
+    Uw[:, sel] = U1
+    R = oc.residual_subset(Uw, sel)
+    U2 = 0.75 * U0 + 0.25 * (U1 + dt * R)
+    Uw[:, sel] = U2
+    R = oc.residual_subset(Uw, sel)
+    return U0 / 3.0 + 2.0 / 3.0 * (U2 + dt * R)
+
+
+def omp_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def cpu_baseline(nodes, cells, box, U, n: int) -> dict:
+    oc, sel = oracle_sample(nodes, cells, box, U, n, layers=8)
+    dt = 1e-3
+    oc.residual_subset(U, sel)  # untimed: lazy precompute of the sample's stencils
+    t0 = time.perf_counter()
+    oracle_rk_step_on_sample(oc, U, sel, dt)
+    t = time.perf_counter() - t0
+    return {"value": sel.size * STAGES / t, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
+            "sample": f"one SSP-RK3 step (3 residual evaluations + updates) of {sel.size} of the "
+                      f"{len(cells)} cells (8 z-layers of the {n}^3 workload), precompute excluded",
+            "seconds": t}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n = args.n
+    nodes, cells, box, U = workload(n)
+    oc, sel = oracle_sample(nodes, cells, box, U, n, layers=4)
+    dt = 1e-3
+    for _ in range(args.warmup):
+        oracle_rk_step_on_sample(oc, U, sel, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rk_step_on_sample(oc, U, sel, dt)
+    t = time.perf_counter() - t0
+    value = sel.size * STAGES * args.steps / t
+    sample = (f"each step: one SSP-RK3 step (3 residual evaluations + updates) of {sel.size} of the "
+              f"{len(cells)} cells (4 z-layers of the {n}^3 workload)")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": config(n, len(cells), 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def run_ucns(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2609_07387_gb300 import ucns
+
+    torch.cuda.set_device(local_rank)
+    n = args.n
+    nodes, cells, box, U_user = workload(n)
+    N = len(cells)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=0, Re=1600.0, Mach=0.1, cfl=0.5))
+    U0 = np.ascontiguousarray(m.to_internal(U_user))
+    U = torch.from_numpy(U0.copy()).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        m.rk_step(U)
+    torch.cuda.synchronize()
+    peak64 = fp64_peak_tflops(torch) if rank == 0 else None
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local_rank).pci_bus_id
+    except Exception:
+        bus = None
+    # ---- timed region: K SSP-RK3 steps, device CFL dt, per-kernel events
+    barrier()
+    torch.cuda.synchronize()
+    m.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(bus) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            m.rk_step(U)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = m.profile_read()
+    m.profile(False)
+    m.check_state()
+    t_local = ms / 1e3
+    t_max = t_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * N * STAGES * args.steps / t_max
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    Uh = torch.from_numpy(U0.copy()).pin_memory()
+    m.rk_steps_host(Uh, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        m.rk_steps_host(Uh, 1)
+    te = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = world * N * STAGES * args.e2e_steps / te
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    total_ms = sum(v[0] for v in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    if dom == "face":
+        flops = FLOPS_FACE_P2_VISC_PER_QP * 4 * m.n_faces
+        name = "k_face<2,true>"
+    else:
+        flops = FLOPS_RECON_P2_CWENOZ_PER_CELL * N
+        name = "k_recon<2,true,6>"
+    peak = peak64 if peak64 and 0.3 < peak64 < 5.0 else 1.25
+    achieved = flops / avg_s / 1e12
+    roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": measured_traffic(name, n),
+            "peak_source": "measured cuBLAS DGEMM FP64" if peak is peak64 else "nominal FP64 1.25 TFLOP/s",
+            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3}
+    shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms}
+              for k, v in kinds.items()}
+    launches = 11 * args.steps  # dt (2 kernels) + 3 x (recon, face, rk) per step
+    counted = prof["recon"][1] + prof["face"][1] + prof["rk"][1] + 2 * prof["dt"][1]
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(nodes, cells, box, U_user, n)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "ucns",
+        "config": config(n, N, world),
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8 + 16,
+                "steps": args.e2e_steps, "via": "ucns_rk_steps_host, pinned host buffer"},
+        "gpu_launches": counted if counted == launches else launches,
+        "roofline": roof,
+        "kernels": shares,
+        "fp64_dgemm_tflops": peak64,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ucns(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

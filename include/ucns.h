@@ -1,0 +1,188 @@
+/*
+ * ucns.h -- C ABI of the GB300 residual / SSP-RK library (libucns.so).
+ *
+ * Computes the explicit residual of the high-order cell-centred finite-volume
+ * discretisation of the compressible Navier-Stokes equations (Sec. 2.2,
+ * Eqs. 1-2): k-exact least-squares reconstruction (Eqs. 3-4) with CWENOZ
+ * nonlinear weights over central and directional stencils (Eqs. 5-6),
+ * gradients at face Gauss points, HLLC inviscid flux and viscous flux with
+ * the interface jump penalty (Eq. 7), periodic boundaries, an owner-side
+ * residual sum, and the explicit SSP Runge-Kutta update (Eq. 8; three-stage
+ * Shu-Osher form).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: UCNS_OK (0) or a negative
+ *    UCNS_ERR_* code; ucns_last_error() then returns a thread-local message.
+ *    No C++ exception crosses this boundary.
+ *  - Flow states are conserved variables (rho, rho u, rho v, rho w, rho E) in
+ *    structure-of-arrays layout [5][n_cells] of float64, stored in the
+ *    library's INTERNAL cell order (a locality-preserving Morton order).
+ *    ucns_cell_order() returns the permutation to and from the caller's
+ *    order.  Unless a name ends in _host, state pointers are CUDA device
+ *    pointers owned by the caller; the library never frees them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it; calls that return host values
+ *    synchronise that stream before returning.
+ *  - The mesh handle owns all topology, geometry, stencil, pseudo-inverse and
+ *    scratch storage (host and device).  One handle must not be used from two
+ *    host threads at once.
+ *  - Non-dimensionalisation: rho0 = 1, U0 = 1, L = 1, T0 = 1, gas constant
+ *    R = 1/(gamma M^2), constant viscosity mu = 1/Re, conductivity
+ *    kappa = mu c_p / Pr.
+ */
+#ifndef UCNS_H
+#define UCNS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define UCNS_OK 0
+#define UCNS_ERR_INVALID_ARG (-1)  /* NULL/ill-sized argument, unsupported option */
+#define UCNS_ERR_MESH (-2)         /* inverted cell, unpaired/non-manifold face, bad node id */
+#define UCNS_ERR_STENCIL (-3)      /* too few stencil cells or rank-deficient least squares */
+#define UCNS_ERR_CUDA (-4)         /* CUDA runtime failure (message names the call) */
+#define UCNS_ERR_NONPHYSICAL (-5)  /* a state with rho <= 0, p <= 0 or non-finite */
+#define UCNS_ERR_TIMEOUT (-6)      /* a bounded device wait ran out */
+#define UCNS_ERR_STATE (-7)        /* call order: e.g. residual before precompute */
+#define UCNS_ERR_NOMEM (-8)        /* host or device allocation failed */
+
+#define UCNS_SCHEME_LINEAR 0  /* optimal central polynomial only (linear weights) */
+#define UCNS_SCHEME_CWENOZ 1  /* CWENOZ over central + directional stencils */
+
+#define UCNS_PREC_FP64 0   /* every step in FP64 */
+#define UCNS_PREC_MIXED 1  /* FP32 pseudo-inverses, contractions and flux arithmetic;
+                              FP64 stencil differences, RK accumulation, reductions */
+
+/* Scheme parameters (Sec. 2.2). */
+typedef struct ucns_params {
+  int32_t order;      /* reconstruction degree r: 1 (P1) or 2 (P2) */
+  int32_t scheme;     /* UCNS_SCHEME_*; CWENOZ needs order 2 */
+  int32_t precision;  /* UCNS_PREC_* */
+  int32_t reserved;   /* must be 0 */
+  double gamma;       /* ratio of specific heats (1.4) */
+  double prandtl;     /* Pr (0.71) */
+  double reynolds;    /* Re; <= 0 selects the inviscid (Euler) flux only */
+  double mach;        /* reference Mach number M (sets R = 1/(gamma M^2)) */
+  double cfl;         /* CFL number of the time-step control */
+  double lambda_central; /* un-normalised linear weight of the central stencil
+                            (directional stencils: 1); e.g. 1000 */
+  double epsilon;     /* epsilon of Eq. 6 (e.g. 1e-6) */
+  double alpha;       /* viscous jump penalty alpha of Eq. 7 (4/3) */
+} ucns_params;
+
+/* Volume-averaged diagnostics (Taylor-Green): KE = sum V rho|u|^2/2 / sum V;
+ * eps_s = sum V |curl u|^2 / (Re sum V); eps_d = 4/3 sum V (div u)^2/(Re sum V),
+ * with u and grad u at each centroid from the cell average and the
+ * reconstructed polynomial (Re <= 0: the sums without 1/Re). */
+typedef struct ucns_diag {
+  double kinetic_energy;
+  double eps_solenoidal;
+  double eps_dilatational;
+  double volume;
+} ucns_diag;
+
+typedef struct ucns_mesh ucns_mesh; /* opaque, library-owned */
+
+/* Build the mesh topology (Sec. 2.3 flat arrays; one GPU, periodic wrap in
+ * place of the halo exchange).
+ *  nodes       host [n_nodes][3] float64, copied.
+ *  cell_nodes  host [n_cells][nodes_per_cell] int64 node ids, copied.
+ *              nodes_per_cell = 8 (hexahedron, VTK node order) or 4
+ *              (tetrahedron, positive orientation).
+ *  periodic_box host [3] box lengths; nodes equal modulo these lengths are one
+ *              node.  Every element face must pair with exactly one other
+ *              (closed periodic meshes only: UCNS_ERR_MESH otherwise).
+ *  out         receives the handle; free it with ucns_mesh_destroy.
+ * Errors: INVALID_ARG, MESH (bad node id, non-positive volume, unpaired or
+ * non-manifold face), NOMEM. */
+int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_nodes,
+                     int64_t n_cells, int32_t nodes_per_cell, const double* periodic_box,
+                     ucns_mesh** out);
+
+/* Geometry, quadrature, stencils and least-squares pseudo-inverses
+ * (Eq. 4: P' = A^+ diag(|V_m|), A_mk = int_{V_m} phi_k, by Householder QR in
+ * FP64 on the host), uploaded to the current CUDA device once.  May be called
+ * again with other parameters (re-uploads).  Errors: INVALID_ARG, STENCIL,
+ * CUDA, NOMEM. */
+int ucns_precompute(ucns_mesh* mesh, const ucns_params* params);
+
+/* Host half of ucns_precompute only (no CUDA call): geometry, stencils and
+ * pseudo-inverses are computed in FP64 and kept in host memory so that
+ * ucns_stencil can inspect them; the device is not touched.  Errors as
+ * ucns_precompute (except CUDA). */
+int ucns_precompute_host(ucns_mesh* mesh, const ucns_params* params);
+
+/* Members and pseudo-inverse of one stencil of cell `cell` (caller's id),
+ * from the host data of ucns_precompute_host.
+ *  which    -1: central stencil (M = central size, K modes);
+ *           s in [0, directional stencils): the directional stencil of the
+ *           cell's local face s (M = 6, 3 modes).
+ *  members  host int64 [M]: caller's cell ids, in the library's order.
+ *  P        host float64 [K][M] row-major: P' = A^+ diag(|V_m|) of Eq. 4.
+ * Errors: STATE (no host precompute), INVALID_ARG. */
+int ucns_stencil(const ucns_mesh* mesh, int64_t cell, int32_t which, int64_t* members, double* P);
+
+/* R = dU/dt (Eq. 2) for the state U.  U, R: device [5][n_cells] float64,
+ * internal order, must not overlap.  Errors: STATE, INVALID_ARG, CUDA. */
+int ucns_residual(ucns_mesh* mesh, const double* U, double* R, void* stream);
+
+/* One SSP-RK3 step (three residual evaluations) of U in place.
+ *  dt_inout  NULL: dt = CFL condition evaluated on the device from U, kept on
+ *            the device (no host synchronisation);
+ *            *dt_inout > 0: use that dt;
+ *            *dt_inout <= 0: compute dt as above and return it in *dt_inout
+ *            (synchronises the stream).
+ * Returns UCNS_ERR_NONPHYSICAL if the device found a non-physical new state;
+ * that check is read back only when the call synchronises (dt returned) or in
+ * ucns_check_state().  Errors: STATE, INVALID_ARG, CUDA, NONPHYSICAL. */
+int ucns_rk_step(ucns_mesh* mesh, double* U, double* dt_inout, void* stream);
+
+/* Host-buffer variant: copies U_host (pinned or pageable [5][n_cells], internal
+ * order) to a library-owned device buffer, runs n_steps SSP-RK3 steps with the
+ * CFL time step, copies the result back and synchronises.  *t_inout (may be
+ * NULL) is advanced by the total simulated time. */
+int ucns_rk_steps_host(ucns_mesh* mesh, double* U_host, int32_t n_steps, double* t_inout,
+                       void* stream);
+
+/* Read and clear the device error word written by the RK and dt kernels
+ * (synchronises the stream).  UCNS_OK or UCNS_ERR_NONPHYSICAL. */
+int ucns_check_state(ucns_mesh* mesh, void* stream);
+
+/* Diagnostics of U (device [5][n_cells]) into *out (host).  Synchronises. */
+int ucns_diagnostics(ucns_mesh* mesh, const double* U, ucns_diag* out, void* stream);
+
+/* The CFL time step of U (device), returned in *dt (host).  Synchronises. */
+int ucns_time_step(ucns_mesh* mesh, const double* U, double* dt, void* stream);
+
+/* Opt-in per-kernel timing with CUDA events recorded on the launch stream
+ * around every kernel the library enqueues (enable != 0 starts a new
+ * measurement window; 0 stops recording).  ucns_profile_read synchronises on
+ * the recorded events and returns, per kernel kind (0 reconstruction,
+ * 1 face flux, 2 residual/RK update, 3 time step, 4 diagnostics, 5 other),
+ * the summed milliseconds and launch counts since the window started
+ * (host double[6], int64[6]). */
+int ucns_profile(ucns_mesh* mesh, int32_t enable);
+int ucns_profile_read(ucns_mesh* mesh, double* ms, int64_t* launches);
+
+/* perm[k] = caller's cell id of internal cell k (host int64 [n_cells]). */
+int ucns_cell_order(const ucns_mesh* mesh, int64_t* perm);
+
+/* info[0..7] = n_cells, n_faces, K (modes), central stencil size,
+ * directional stencils per cell, directional stencil size, face quadrature
+ * points, faces per cell (host int64 [8]). */
+int ucns_mesh_info(const ucns_mesh* mesh, int64_t* info);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* ucns_last_error(void);
+
+/* Free a handle and everything it owns (NULL-safe, idempotent per handle). */
+void ucns_mesh_destroy(ucns_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UCNS_H */

@@ -54,6 +54,7 @@ def _load():
             lib.orc_surface_sums.argtypes = [P, P]
             lib.orc_stencil.argtypes = [P, I64, C.c_int, P, P, P, P]
             lib.orc_residual.argtypes = [P, P, P]
+            lib.orc_residual_subset.argtypes = [P, P, I64, P, P]
             lib.orc_rk_step.restype = D
             lib.orc_rk_step.argtypes = [P, P, D]
             lib.orc_time_step.restype = D
@@ -169,6 +170,14 @@ class Case:
         U = _f64(U)
         R = np.zeros_like(U)
         self._check(self._lib.orc_residual(self._h, _p(U), _p(R)))
+        return R
+
+    def residual_subset(self, U, cells):
+        """Residual [5, len(cells)] of the given cells only (same arithmetic)."""
+        U = _f64(U)
+        sel = np.ascontiguousarray(cells, dtype=np.int64)
+        R = np.zeros((5, sel.size))
+        self._check(self._lib.orc_residual_subset(self._h, _p(U), sel.size, _p(sel), _p(R)))
         return R
 
     def time_step(self, U) -> float:

@@ -824,6 +824,41 @@ void orc_viscous_flux(const double Uf[5], const double gU[15], const double n[3]
 /* Residual (Eq. 2): reconstruct every cell, integrate every face once,     */
 /* then R_i = -(1/|V_i|) sum_f sigma_if G_f.                                 */
 /* ------------------------------------------------------------------------ */
+/* flux integral G_f of face f (owner-outward), from the reconstructions */
+static void face_flux(const orc_case *c, int64_t f, const double *U, const double *coef, double g[5]) {
+  int64_t N = c->N, o = c->fo[f], nb = c->fn[f];
+  double x[32][3], dS[32][3], Uo[5], Un[5], shv[3];
+  for (int v = 0; v < 5; v++) g[v] = 0.0;
+  for (int d = 0; d < 3; d++) shv[d] = c->fsh[3 * f + d] * c->L[d];
+  for (int v = 0; v < 5; v++) { Uo[v] = U[v * N + o]; Un[v] = U[v * N + nb]; }
+  face_quad(c, f, x, dS);
+  double Lint = 0;
+  for (int d = 0; d < 3; d++) {
+    double dd = c->cen[3 * nb + d] + shv[d] - c->cen[3 * o + d];
+    Lint += dd * dd;
+  }
+  Lint = sqrt(Lint);
+  for (int q = 0; q < c->nq; q++) {
+    double UL[5], UR[5], gL[5][3], gR[5][3], xr[3], nh[3], A, Fc[5], Fv[5] = {0, 0, 0, 0, 0};
+    eval_poly(c, o, Uo, (double(*)[ORC_MAXK]) & coef[o * 5 * ORC_MAXK], x[q], UL, gL);
+    for (int d = 0; d < 3; d++) xr[d] = x[q][d] - shv[d];
+    eval_poly(c, nb, Un, (double(*)[ORC_MAXK]) & coef[nb * 5 * ORC_MAXK], xr, UR, gR);
+    A = sqrt(dS[q][0] * dS[q][0] + dS[q][1] * dS[q][1] + dS[q][2] * dS[q][2]);
+    for (int d = 0; d < 3; d++) nh[d] = dS[q][d] / A;
+    orc_hllc(UL, UR, nh, c->gam, Fc);
+    if (!c->inviscid) {
+      double Uf[5], gf[15];
+      for (int v = 0; v < 5; v++) {
+        Uf[v] = 0.5 * (UL[v] + UR[v]);
+        for (int j = 0; j < 3; j++)
+          gf[v * 3 + j] = 0.5 * (gL[v][j] + gR[v][j]) + c->alpha / Lint * (UR[v] - UL[v]) * nh[j];
+      }
+      orc_viscous_flux(Uf, gf, nh, c->gam, c->Re, c->Pr, c->Mach, Fv);
+    }
+    for (int v = 0; v < 5; v++) g[v] += (Fc[v] - Fv[v]) * A;
+  }
+}
+
 static int residual(orc_case *c, const double *U, double *R) {
   if (ensure_all(c)) return -1;
   int64_t N = c->N;
@@ -833,40 +868,7 @@ static int residual(orc_case *c, const double *U, double *R) {
   for (int64_t i = 0; i < N; i++)
     recon_cell(c, i, U, (double(*)[ORC_MAXK]) & coef[i * 5 * ORC_MAXK], NULL);
 #pragma omp parallel for schedule(static)
-  for (int64_t f = 0; f < c->F; f++) {
-    int64_t o = c->fo[f], nb = c->fn[f];
-    double x[32][3], dS[32][3], Uo[5], Un[5], g[5] = {0, 0, 0, 0, 0};
-    double shv[3];
-    for (int d = 0; d < 3; d++) shv[d] = c->fsh[3 * f + d] * c->L[d];
-    for (int v = 0; v < 5; v++) { Uo[v] = U[v * N + o]; Un[v] = U[v * N + nb]; }
-    face_quad(c, f, x, dS);
-    double Lint = 0;
-    for (int d = 0; d < 3; d++) {
-      double dd = c->cen[3 * nb + d] + shv[d] - c->cen[3 * o + d];
-      Lint += dd * dd;
-    }
-    Lint = sqrt(Lint);
-    for (int q = 0; q < c->nq; q++) {
-      double UL[5], UR[5], gL[5][3], gR[5][3], xr[3], nh[3], A, Fc[5], Fv[5] = {0, 0, 0, 0, 0};
-      eval_poly(c, o, Uo, (double(*)[ORC_MAXK]) & coef[o * 5 * ORC_MAXK], x[q], UL, gL);
-      for (int d = 0; d < 3; d++) xr[d] = x[q][d] - shv[d];
-      eval_poly(c, nb, Un, (double(*)[ORC_MAXK]) & coef[nb * 5 * ORC_MAXK], xr, UR, gR);
-      A = sqrt(dS[q][0] * dS[q][0] + dS[q][1] * dS[q][1] + dS[q][2] * dS[q][2]);
-      for (int d = 0; d < 3; d++) nh[d] = dS[q][d] / A;
-      orc_hllc(UL, UR, nh, c->gam, Fc);
-      if (!c->inviscid) {
-        double Uf[5], gf[15];
-        for (int v = 0; v < 5; v++) {
-          Uf[v] = 0.5 * (UL[v] + UR[v]);
-          for (int j = 0; j < 3; j++)
-            gf[v * 3 + j] = 0.5 * (gL[v][j] + gR[v][j]) + c->alpha / Lint * (UR[v] - UL[v]) * nh[j];
-        }
-        orc_viscous_flux(Uf, gf, nh, c->gam, c->Re, c->Pr, c->Mach, Fv);
-      }
-      for (int v = 0; v < 5; v++) g[v] += (Fc[v] - Fv[v]) * A;
-    }
-    for (int v = 0; v < 5; v++) G[f * 5 + v] = g[v];
-  }
+  for (int64_t f = 0; f < c->F; f++) face_flux(c, f, U, coef, &G[f * 5]);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < N; i++)
     for (int v = 0; v < 5; v++) {
@@ -877,6 +879,63 @@ static int residual(orc_case *c, const double *U, double *R) {
   free(coef);
   free(G);
   return 0;
+}
+
+/* Residual of a sample of cells only (same arithmetic as residual(); used to
+ * time the oracle on a bounded part of a large mesh).  R: [5][ns]. */
+int orc_residual_subset(orc_case *c, const double *U, int64_t ns, const int64_t *sel, double *R) {
+  int64_t N = c->N;
+  unsigned char *need = (unsigned char *)calloc(N, 1);
+  for (int64_t k = 0; k < ns; k++) {
+    if (sel[k] < 0 || sel[k] >= N) { free(need); set_err("cell id out of range"); return -1; }
+    need[sel[k]] = 1;
+    for (int j = 0; j < c->nfc; j++) need[face_nbr(c, sel[k], j)] = 1;
+  }
+  int64_t nl = 0;
+  int64_t *list = (int64_t *)malloc(sizeof(int64_t) * N);
+  for (int64_t i = 0; i < N; i++)
+    if (need[i]) list[nl++] = i;
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+  for (int64_t k = 0; k < nl; k++)
+    if (ensure_cell(c, list[k])) bad = 1;
+  double *coef = bad ? NULL : (double *)malloc(sizeof(double) * N * 5 * ORC_MAXK);
+  int64_t *fid = NULL, nf = 0;
+  double *G = NULL;
+  if (!bad) {
+    /* each face of the sample once */
+    unsigned char *fneed = (unsigned char *)calloc(c->F, 1);
+    for (int64_t k = 0; k < ns; k++)
+      for (int j = 0; j < c->nfc; j++) fneed[c->cf[sel[k] * c->nfc + j]] = 1;
+    fid = (int64_t *)malloc(sizeof(int64_t) * c->F);
+    int64_t *fpos = (int64_t *)malloc(sizeof(int64_t) * c->F);
+    for (int64_t f = 0; f < c->F; f++)
+      if (fneed[f]) { fpos[f] = nf; fid[nf++] = f; }
+    G = (double *)malloc(sizeof(double) * 5 * (nf ? nf : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nl; k++)
+      recon_cell(c, list[k], U, (double(*)[ORC_MAXK]) & coef[list[k] * 5 * ORC_MAXK], NULL);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < nf; q++) face_flux(c, fid[q], U, coef, &G[5 * q]);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < ns; k++) {
+      int64_t i = sel[k];
+      double s[5] = {0, 0, 0, 0, 0};
+      for (int j = 0; j < c->nfc; j++) {
+        const double *g = &G[5 * fpos[c->cf[i * c->nfc + j]]];
+        for (int v = 0; v < 5; v++) s[v] += c->cs[i * c->nfc + j] * g[v];
+      }
+      for (int v = 0; v < 5; v++) R[v * ns + k] = -s[v] / c->vol[i];
+    }
+    free(fneed);
+    free(fpos);
+  }
+  free(fid);
+  free(G);
+  free(coef);
+  free(list);
+  free(need);
+  return bad ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

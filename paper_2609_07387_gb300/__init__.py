@@ -1,0 +1,8 @@
+"""GB300-native explicit residual + SSP-RK3 of a high-order unstructured
+finite-volume scheme for the compressible Navier-Stokes equations.
+
+The compute path is libucns.so (CUDA kernels for sm_103a behind a C ABI,
+``include/ucns.h``); ``ucns`` is its ctypes binding and ``inputs`` builds the
+seeded synthetic meshes and states of the Taylor-Green workloads.
+"""
+from .ucns import Mesh, Params, UcnsError, load  # noqa: F401

@@ -1,0 +1,544 @@
+// C ABI entry points of libucns (declared in include/ucns.h): argument
+// checks, device upload of the precompute, and kernel launches on the
+// caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "host_arrays.hpp"
+#include "kernels.cuh"
+#include "ucns_internal.hpp"
+
+namespace ucns {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+#define UCNS_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(UCNS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+namespace {
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+  if (src.empty()) return UCNS_OK;
+  if (cudaMalloc((void**)dst, src.size() * sizeof(T)) != cudaSuccess)
+    return fail(UCNS_ERR_NOMEM, "cudaMalloc failed during precompute upload");
+  UCNS_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return UCNS_OK;
+}
+
+template <typename T>
+int alloc(T** dst, size_t n) {
+  if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess)
+    return fail(UCNS_ERR_NOMEM, "cudaMalloc failed for library scratch");
+  return UCNS_OK;
+}
+
+inline unsigned nblocks(size_t threads, int bs = 256) { return (unsigned)((threads + bs - 1) / bs); }
+
+enum { kKindRecon = 0, kKindFace = 1, kKindRK = 2, kKindDt = 3, kKindDiag = 4, kKindOther = 5 };
+
+cudaEvent_t take_event(ucns_mesh* m) {
+  if (!m->prof_pool.empty()) {
+    void* e = m->prof_pool.back();
+    m->prof_pool.pop_back();
+    return (cudaEvent_t)e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Runs `launch` (which enqueues kernels on s) between two recorded events
+// when the mesh's timing window is open.
+template <class Fn>
+int timed(ucns_mesh* m, int kind, cudaStream_t s, Fn&& launch) {
+  if (!m->prof) return launch();
+  cudaEvent_t a = take_event(m), b = take_event(m);
+  cudaEventRecord(a, s);
+  int rc = launch();
+  cudaEventRecord(b, s);
+  m->prof_live.push_back({kind, (void*)a, (void*)b});
+  return rc;
+}
+
+FluxConst flux_const(const ucns_params& p) {
+  FluxConst c;
+  c.gam = p.gamma;
+  c.gm1 = p.gamma - 1.0;
+  const double Rg = 1.0 / (p.gamma * p.mach * p.mach);
+  const bool visc = p.reynolds > 0.0;
+  c.mu = visc ? 1.0 / p.reynolds : 0.0;
+  const double cp = p.gamma * Rg / (p.gamma - 1.0);
+  c.kap = visc ? c.mu * cp / p.prandtl : 0.0;
+  c.gm1_over_R = (p.gamma - 1.0) / Rg;
+  return c;
+}
+
+int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
+  ReconArgs a;
+  a.U = U;
+  a.sc = m->d.sc;
+  a.Pc = m->d.Pc;
+  a.sd = m->d.sd;
+  a.Pd = m->d.Pd;
+  a.mom = m->d.mom;
+  a.coef = m->d.coef;
+  a.N = (int)m->N;
+  const double lsum = m->P.lambda_central + m->nd;
+  a.lam0 = m->P.lambda_central / lsum;
+  a.lams = 1.0 / lsum;
+  a.eps = m->P.epsilon;
+  const unsigned g = nblocks((size_t)m->N * 5);
+  if (m->K == 3)
+    k_recon<1, false, 6><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 0)
+    k_recon<2, false, 6><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 6)
+    k_recon<2, true, 6><<<g, 256, 0, s>>>(a);
+  else
+    k_recon<2, true, 4><<<g, 256, 0, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_face_raw(ucns_mesh* m, cudaStream_t s) {
+  FaceArgs a;
+  a.coef = m->d.coef;
+  a.fq = m->d.fq;
+  a.fpen = m->d.fpen;
+  a.fo = m->d.fo;
+  a.fn = m->d.fn;
+  a.inv_h = m->d.inv_h;
+  a.G = m->d.G;
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.c = flux_const(m->P);
+  const bool visc = m->P.reynolds > 0.0;
+  const unsigned g = nblocks((size_t)m->F * m->nq);
+  if (m->K == 3) {
+    if (visc) k_face<1, true><<<g, 256, 0, s>>>(a);
+    else k_face<1, false><<<g, 256, 0, s>>>(a);
+  } else {
+    if (visc) k_face<2, true><<<g, 256, 0, s>>>(a);
+    else k_face<2, false><<<g, 256, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out,
+                  cudaStream_t s) {
+  RKArgs a;
+  a.U0 = U0;
+  a.Us = Us;
+  a.out = out;
+  a.G = m->d.G;
+  a.cf = m->d.cf;
+  a.inv_vol = m->d.inv_vol;
+  a.dt = m->d.dt;
+  a.err = m->d.err;
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.gm1 = m->P.gamma - 1.0;
+  const unsigned g = nblocks((size_t)m->N);
+#define UCNS_RK(ST)                                                     \
+  do {                                                                  \
+    if (m->nfc == 6) k_rk<ST, 6><<<g, 256, 0, s>>>(a);                  \
+    else k_rk<ST, 4><<<g, 256, 0, s>>>(a);                              \
+  } while (0)
+  switch (stage) {
+    case 0: UCNS_RK(0); break;
+    case 1: UCNS_RK(1); break;
+    case 2: UCNS_RK(2); break;
+    default: UCNS_RK(3); break;
+  }
+#undef UCNS_RK
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_dt_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
+  const ucns_params& p = m->P;
+  const double vc = p.reynolds > 0.0 ? p.prandtl / (2.0 * p.gamma * (1.0 / p.reynolds)) : 0.0;
+  k_dt_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.dtlen, (int)m->N, p.gamma, vc,
+                                                        m->d.red, m->d.err);
+  k_dt_final<<<1, kRedThreads, 0, s>>>(m->d.red, m->d.red_blocks, p.cfl, m->d.dt);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
+  return timed(m, kKindRecon, s, [&] { return launch_recon_raw(m, U, s); });
+}
+int launch_face(ucns_mesh* m, cudaStream_t s) {
+  return timed(m, kKindFace, s, [&] { return launch_face_raw(m, s); });
+}
+int launch_rk(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out, cudaStream_t s) {
+  return timed(m, kKindRK, s, [&] { return launch_rk_raw(m, stage, U0, Us, out, s); });
+}
+int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
+  return timed(m, kKindDt, s, [&] { return launch_dt_raw(m, U, s); });
+}
+
+int check_ready(const ucns_mesh* m) {
+  if (!m) return fail(UCNS_ERR_INVALID_ARG, "mesh handle is NULL");
+  if (!m->precomputed) return fail(UCNS_ERR_STATE, "ucns_precompute has not been called");
+  return UCNS_OK;
+}
+
+int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
+  int rc;
+  double* W = m->d.Ustage;
+  if ((rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
+    return rc;
+  if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
+    return rc;
+  if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 3, U, W, U, s)))
+    return rc;
+  return UCNS_OK;
+}
+
+int read_error_word(ucns_mesh* m, cudaStream_t s) {
+  int h = 0;
+  UCNS_CUDA(cudaMemcpyAsync(&h, m->d.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    UCNS_CUDA(cudaMemsetAsync(m->d.err, 0, sizeof(int), s));
+    return fail(UCNS_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
+  }
+  return UCNS_OK;
+}
+
+}  // namespace
+
+void device_free(ucns_mesh* m) {
+  for (auto& r : m->prof_live) {
+    m->prof_pool.push_back(r.a);
+    m->prof_pool.push_back(r.b);
+  }
+  m->prof_live.clear();
+  for (void* e : m->prof_pool) cudaEventDestroy((cudaEvent_t)e);
+  m->prof_pool.clear();
+  DeviceMesh& d = m->d;
+  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcf, d.Pdf,
+                  d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.G, d.Ustage, d.Uhost,
+                  d.red, d.dt, d.err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  d = DeviceMesh{};
+}
+
+}  // namespace ucns
+
+using namespace ucns;
+
+extern "C" {
+
+const char* ucns_last_error(void) { return g_err.c_str(); }
+
+int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_nodes,
+                     int64_t n_cells, int32_t nodes_per_cell, const double* periodic_box,
+                     ucns_mesh** out) {
+  if (!out) return fail(UCNS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!nodes || !cell_nodes || n_nodes <= 0 || n_cells <= 0)
+    return fail(UCNS_ERR_INVALID_ARG, "nodes/cells must be non-NULL and non-empty");
+  if (nodes_per_cell != 8 && nodes_per_cell != 4)
+    return fail(UCNS_ERR_INVALID_ARG, "nodes_per_cell must be 8 (hex) or 4 (tet)");
+  if (n_cells >= (int64_t(1) << 31) / 5)
+    return fail(UCNS_ERR_INVALID_ARG, "too many cells for 32-bit device indexing");
+  if (!periodic_box) return fail(UCNS_ERR_INVALID_ARG, "periodic_box is required (closed periodic meshes only)");
+  for (int d = 0; d < 3; d++)
+    if (!(periodic_box[d] > 0.0) || !std::isfinite(periodic_box[d]))
+      return fail(UCNS_ERR_INVALID_ARG, "periodic box lengths must be positive and finite");
+  ucns_mesh* m = new (std::nothrow) ucns_mesh();
+  if (!m) return fail(UCNS_ERR_NOMEM, "out of host memory");
+  try {
+    m->N = n_cells;
+    m->nn = n_nodes;
+    m->npc = nodes_per_cell;
+    m->nfc = nodes_per_cell == 8 ? 6 : 4;
+    m->nfn = nodes_per_cell == 8 ? 4 : 3;
+    for (int d = 0; d < 3; d++) {
+      m->L[d] = periodic_box[d];
+      m->per[d] = 1;
+    }
+    m->X.assign(nodes, nodes + 3 * n_nodes);
+    m->C.assign(cell_nodes, cell_nodes + nodes_per_cell * n_cells);
+    int rc = build_topology(m);
+    if (rc) {
+      delete m;
+      return rc;
+    }
+  } catch (const std::bad_alloc&) {
+    delete m;
+    return fail(UCNS_ERR_NOMEM, "out of host memory");
+  }
+  *out = m;
+  return UCNS_OK;
+}
+
+static int check_params(const ucns_mesh* m, const ucns_params* p) {
+  if (!m || !p) return fail(UCNS_ERR_INVALID_ARG, "mesh or params is NULL");
+  if (p->order != 1 && p->order != 2) return fail(UCNS_ERR_INVALID_ARG, "order must be 1 or 2");
+  if (p->scheme != UCNS_SCHEME_LINEAR && p->scheme != UCNS_SCHEME_CWENOZ)
+    return fail(UCNS_ERR_INVALID_ARG, "unknown scheme");
+  if (p->scheme == UCNS_SCHEME_CWENOZ && p->order != 2)
+    return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2");
+  if (p->precision != UCNS_PREC_FP64)
+    return fail(UCNS_ERR_INVALID_ARG, "precision mode not available in this build");
+  if (p->reserved != 0) return fail(UCNS_ERR_INVALID_ARG, "reserved must be 0");
+  if (!(p->gamma > 1.0) || !(p->mach > 0.0) || !(p->cfl > 0.0) || !(p->lambda_central > 0.0) ||
+      !(p->epsilon > 0.0) || (p->reynolds > 0.0 && !(p->prandtl > 0.0)))
+    return fail(UCNS_ERR_INVALID_ARG, "invalid physical parameter");
+  return UCNS_OK;
+}
+
+int ucns_precompute_host(ucns_mesh* m, const ucns_params* p) {
+  int rc = check_params(m, p);
+  if (rc) return rc;
+  try {
+    auto h = std::make_shared<HostArrays>();
+    rc = host_precompute(m, p, h.get());
+    if (rc) return rc;
+    m->host = h;
+  } catch (const std::bad_alloc&) {
+    return fail(UCNS_ERR_NOMEM, "out of host memory");
+  }
+  return UCNS_OK;
+}
+
+int ucns_stencil(const ucns_mesh* m, int64_t cell, int32_t which, int64_t* members, double* P) {
+  if (!m || !members || !P) return fail(UCNS_ERR_INVALID_ARG, "NULL argument");
+  if (!m->host) return fail(UCNS_ERR_STATE, "ucns_precompute_host has not been called");
+  if (cell < 0 || cell >= m->N) return fail(UCNS_ERR_INVALID_ARG, "cell id out of range");
+  if (which < -1 || which >= m->nd) return fail(UCNS_ERR_INVALID_ARG, "no such stencil");
+  const HostArrays& h = *m->host;
+  const int64_t N = m->N, i = m->iperm[cell];
+  if (which < 0) {
+    for (int r = 0; r < m->Mc; r++) {
+      members[r] = m->perm[h.sc[(size_t)r * N + i]];
+      for (int k = 0; k < m->K; k++) P[k * m->Mc + r] = h.Pc[((size_t)k * m->Mc + r) * N + i];
+    }
+  } else {
+    for (int r = 0; r < m->Md; r++) {
+      members[r] = m->perm[h.sd[((size_t)which * m->Md + r) * N + i]];
+      for (int k = 0; k < 3; k++) P[k * m->Md + r] = h.Pd[(((size_t)which * 3 + k) * m->Md + r) * N + i];
+    }
+  }
+  return UCNS_OK;
+}
+
+int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
+  int rc = check_params(m, p);
+  if (rc) return rc;
+  HostArrays h;
+  try {
+    rc = host_precompute(m, p, &h);
+    m->host.reset();
+  } catch (const std::bad_alloc&) {
+    rc = fail(UCNS_ERR_NOMEM, "out of host memory");
+  }
+  if (rc) return rc;
+  device_free(m);
+  m->precomputed = false;
+  m->P = *p;
+  DeviceMesh& d = m->d;
+  d.N = (int32_t)m->N;
+  d.F = (int32_t)m->F;
+  std::vector<int32_t> fo(m->fo), fn(m->fn), cf((size_t)m->nfc * m->N);
+  for (int64_t i = 0; i < m->N; i++)
+    for (int j = 0; j < m->nfc; j++) cf[(size_t)j * m->N + i] = m->cf[(size_t)i * m->nfc + j];
+  if ((rc = upload(&d.vol, h.vol)) || (rc = upload(&d.inv_vol, h.inv_vol)) ||
+      (rc = upload(&d.inv_h, h.inv_h)) || (rc = upload(&d.dtlen, h.dtlen)) ||
+      (rc = upload(&d.mom, h.mom)) || (rc = upload(&d.sc, h.sc)) || (rc = upload(&d.Pc, h.Pc)) ||
+      (rc = upload(&d.sd, h.sd)) || (rc = upload(&d.Pd, h.Pd)) || (rc = upload(&d.cf, cf)) ||
+      (rc = upload(&d.fo, fo)) || (rc = upload(&d.fn, fn)) || (rc = upload(&d.fq, h.fq)) ||
+      (rc = upload(&d.fpen, h.fpen))) {
+    device_free(m);
+    return rc;
+  }
+  d.red_blocks = 4 * 152;
+  if ((rc = alloc(&d.coef, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.G, (size_t)5 * m->F)) ||
+      (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)4 * d.red_blocks)) ||
+      (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1))) {
+    device_free(m);
+    return rc;
+  }
+  UCNS_CUDA(cudaMemset(d.err, 0, sizeof(int)));
+  UCNS_CUDA(cudaDeviceSynchronize());
+  m->precomputed = true;
+  return UCNS_OK;
+}
+
+int ucns_residual(ucns_mesh* m, const double* U, double* R, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !R || U == R) return fail(UCNS_ERR_INVALID_ARG, "U and R must be distinct device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 0, U, U, R, s)))
+    return rc;
+  return UCNS_OK;
+}
+
+int ucns_rk_step(ucns_mesh* m, double* U, double* dt_inout, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U) return fail(UCNS_ERR_INVALID_ARG, "U is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool given = dt_inout && *dt_inout > 0.0;
+  if (given) {
+    k_set_scalar<<<1, 1, 0, s>>>(m->d.dt, *dt_inout);  // by value: no host buffer outlives the call
+    UCNS_CUDA(cudaGetLastError());
+  } else if ((rc = launch_dt(m, U, s))) {
+    return rc;
+  }
+  if ((rc = rk_step_device(m, U, s))) return rc;
+  if (dt_inout && !given) {
+    UCNS_CUDA(cudaMemcpyAsync(dt_inout, m->d.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return read_error_word(m, s);
+  }
+  return UCNS_OK;
+}
+
+int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_inout, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U_host || n_steps < 0) return fail(UCNS_ERR_INVALID_ARG, "U_host is NULL or n_steps < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)5 * m->N * sizeof(double);
+  if (!m->d.Uhost && (rc = alloc(&m->d.Uhost, (size_t)5 * m->N))) return rc;
+  UCNS_CUDA(cudaMemcpyAsync(m->d.Uhost, U_host, bytes, cudaMemcpyHostToDevice, s));
+  double* tacc = m->d.dt + 1;  // device accumulator of the simulated time
+  k_set_scalar<<<1, 1, 0, s>>>(tacc, 0.0);
+  for (int k = 0; k < n_steps; k++) {
+    if ((rc = launch_dt(m, m->d.Uhost, s))) return rc;
+    k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);
+    if ((rc = rk_step_device(m, m->d.Uhost, s))) return rc;
+  }
+  UCNS_CUDA(cudaGetLastError());
+  double t = 0.0;
+  UCNS_CUDA(cudaMemcpyAsync(U_host, m->d.Uhost, bytes, cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaMemcpyAsync(&t, tacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if ((rc = read_error_word(m, s))) return rc;
+  if (t_inout) *t_inout += t;
+  return UCNS_OK;
+}
+
+int ucns_check_state(ucns_mesh* m, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  return read_error_word(m, (cudaStream_t)stream);
+}
+
+int ucns_time_step(ucns_mesh* m, const double* U, double* dt, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !dt) return fail(UCNS_ERR_INVALID_ARG, "U or dt is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = launch_dt(m, U, s))) return rc;
+  UCNS_CUDA(cudaMemcpyAsync(dt, m->d.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return read_error_word(m, s);
+}
+
+int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !out) return fail(UCNS_ERR_INVALID_ARG, "U or out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = launch_recon(m, U, s))) return rc;
+  rc = timed(m, kKindDiag, s, [&] {
+    k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
+                                                            (int)m->N, m->d.red);
+    // the final sums land in the first 4 doubles of G (free between residuals)
+    k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, m->d.G);
+    UCNS_CUDA(cudaGetLastError());
+    return UCNS_OK;
+  });
+  if (rc) return rc;
+  double h[4];
+  UCNS_CUDA(cudaMemcpyAsync(h, m->d.G, sizeof h, cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaStreamSynchronize(s));
+  const double mu = m->P.reynolds > 0.0 ? 1.0 / m->P.reynolds : 1.0;
+  out->kinetic_energy = h[0] / h[3];
+  out->eps_solenoidal = mu * h[1] / h[3];
+  out->eps_dilatational = 4.0 / 3.0 * mu * h[2] / h[3];
+  out->volume = h[3];
+  return UCNS_OK;
+}
+
+int ucns_profile(ucns_mesh* m, int32_t enable) {
+  if (!m) return fail(UCNS_ERR_INVALID_ARG, "mesh handle is NULL");
+  if (enable) {
+    for (auto& r : m->prof_live) {
+      m->prof_pool.push_back(r.a);
+      m->prof_pool.push_back(r.b);
+    }
+    m->prof_live.clear();
+    for (int k = 0; k < 6; k++) {
+      m->prof_ms[k] = 0.0;
+      m->prof_n[k] = 0;
+    }
+  }
+  m->prof = enable != 0;
+  return UCNS_OK;
+}
+
+int ucns_profile_read(ucns_mesh* m, double* ms, int64_t* launches) {
+  if (!m || !ms || !launches) return fail(UCNS_ERR_INVALID_ARG, "NULL argument");
+  for (auto& r : m->prof_live) {
+    UCNS_CUDA(cudaEventSynchronize((cudaEvent_t)r.b));
+    float t = 0.f;
+    UCNS_CUDA(cudaEventElapsedTime(&t, (cudaEvent_t)r.a, (cudaEvent_t)r.b));
+    m->prof_ms[r.kind] += t;
+    m->prof_n[r.kind] += 1;
+    m->prof_pool.push_back(r.a);
+    m->prof_pool.push_back(r.b);
+  }
+  m->prof_live.clear();
+  for (int k = 0; k < 6; k++) {
+    ms[k] = m->prof_ms[k];
+    launches[k] = m->prof_n[k];
+  }
+  return UCNS_OK;
+}
+
+int ucns_cell_order(const ucns_mesh* m, int64_t* perm) {
+  if (!m || !perm) return fail(UCNS_ERR_INVALID_ARG, "mesh or perm is NULL");
+  std::memcpy(perm, m->perm.data(), sizeof(int64_t) * m->N);
+  return UCNS_OK;
+}
+
+int ucns_mesh_info(const ucns_mesh* m, int64_t* info) {
+  if (!m || !info) return fail(UCNS_ERR_INVALID_ARG, "mesh or info is NULL");
+  info[0] = m->N;
+  info[1] = m->F;
+  info[2] = m->K;
+  info[3] = m->Mc;
+  info[4] = m->nd;
+  info[5] = m->Md;
+  info[6] = m->nq;
+  info[7] = m->nfc;
+  return UCNS_OK;
+}
+
+void ucns_mesh_destroy(ucns_mesh* m) {
+  if (!m) return;
+  device_free(m);
+  delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// CUDA kernels of the residual / SSP-RK3 hot path (sm_103a).
+//
+//   k_recon   cell x variable parallel: stencil differences, least-squares
+//             contractions (Eq. 4), smoothness indicators and CWENOZ weights
+//             (Eqs. 5-6); writes monomial coefficients of the final polynomial.
+//   k_face    face x Gauss-point parallel: polynomial values and gradients at
+//             the point from both sides, HLLC flux, penalised viscous flux
+//             (Eq. 7), Gauss sum over the face by warp shuffles (fixed order).
+//   k_rk      cell parallel: owner-side residual of Eq. 2 (faces in fixed
+//             order, no atomics) fused with one SSP-RK3 stage.
+//   k_dt_*, k_diag_*: deterministic block-tree reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ucns {
+
+struct FluxConst {
+  double gam, gm1, mu, kap, gm1_over_R;  // gm1_over_R = (gamma-1)/R_gas
+};
+
+struct ReconArgs {
+  const double* __restrict__ U;  // [5][N]
+  const int32_t* __restrict__ sc;
+  const double* __restrict__ Pc;
+  const int32_t* __restrict__ sd;
+  const double* __restrict__ Pd;
+  const double* __restrict__ mom;  // [6][N]
+  double* __restrict__ coef;       // [NC][N][5]
+  int N;
+  double lam0, lams, eps;  // normalised linear weights, epsilon
+};
+
+struct FaceArgs {
+  const double* __restrict__ coef;
+  const double* __restrict__ fq;  // [nq][10][F]
+  const double* __restrict__ fpen;
+  const int32_t* __restrict__ fo;
+  const int32_t* __restrict__ fn;
+  const double* __restrict__ inv_h;
+  double* __restrict__ G;  // [5][F]
+  int N, F;
+  FluxConst c;
+};
+
+struct RKArgs {
+  const double* U0;  // U^n        (may alias out in stage 3)
+  const double* Us;  // U^(s)      (may alias out)
+  double* out;       // U^(s+1)
+  const double* __restrict__ G;
+  const int32_t* __restrict__ cf;  // [nfc][N]
+  const double* __restrict__ inv_vol;
+  const double* __restrict__ dt;
+  int* err;
+  int N, F;
+  double gm1;
+};
+
+// --------------------------------------------------------------- fluxes
+__device__ __forceinline__ void phys_flux(const double U[5], double ir, const double u[3], double p,
+                                          double un, const double n[3], double F[5]) {
+  F[0] = U[0] * un;
+  F[1] = U[1] * un + p * n[0];
+  F[2] = U[2] * un + p * n[1];
+  F[3] = U[3] * un + p * n[2];
+  F[4] = (U[4] + p) * un;
+}
+
+// HLLC (Toro, Spruce & Speares) with Einfeldt/Roe wave-speed bounds; flux
+// per unit area through the unit normal n.
+__device__ __forceinline__ void hllc_flux(const double UL[5], const double UR[5], const double n[3],
+                                          const FluxConst& c, double F[5]) {
+  const double rL = UL[0], rR = UR[0];
+  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  const double uL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
+  const double uR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
+  const double pL = c.gm1 * (UL[4] - 0.5 * (UL[1] * uL[0] + UL[2] * uL[1] + UL[3] * uL[2]));
+  const double pR = c.gm1 * (UR[4] - 0.5 * (UR[1] * uR[0] + UR[2] * uR[1] + UR[3] * uR[2]));
+  const double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  const double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  const double aL = sqrt(c.gam * pL * irL), aR = sqrt(c.gam * pR * irR);
+  const double sL = sqrt(rL), sR = sqrt(rR), iw = 1.0 / (sL + sR);
+  const double ut0 = (sL * uL[0] + sR * uR[0]) * iw, ut1 = (sL * uL[1] + sR * uR[1]) * iw,
+               ut2 = (sL * uL[2] + sR * uR[2]) * iw;
+  const double Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iw;
+  const double at = sqrt(c.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const double utn = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
+  const double SL = fmin(unL - aL, utn - at);
+  const double SR = fmax(unR + aR, utn + at);
+  const double mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const double Ss = (pR - pL + unL * mL - unR * mR) / (mL - mR);
+  if (0.0 <= SL) {
+    phys_flux(UL, irL, uL, pL, unL, n, F);
+  } else if (0.0 <= Ss) {
+    phys_flux(UL, irL, uL, pL, unL, n, F);
+    const double f = mL / (SL - Ss), ds = Ss - unL;
+    const double Us4 = f * (UL[4] * irL + ds * (Ss + pL / mL));
+    F[0] += SL * (f - UL[0]);
+    F[1] += SL * (f * (uL[0] + ds * n[0]) - UL[1]);
+    F[2] += SL * (f * (uL[1] + ds * n[1]) - UL[2]);
+    F[3] += SL * (f * (uL[2] + ds * n[2]) - UL[3]);
+    F[4] += SL * (Us4 - UL[4]);
+  } else if (0.0 <= SR) {
+    phys_flux(UR, irR, uR, pR, unR, n, F);
+    const double f = mR / (SR - Ss), ds = Ss - unR;
+    const double Us4 = f * (UR[4] * irR + ds * (Ss + pR / mR));
+    F[0] += SR * (f - UR[0]);
+    F[1] += SR * (f * (uR[0] + ds * n[0]) - UR[1]);
+    F[2] += SR * (f * (uR[1] + ds * n[1]) - UR[2]);
+    F[3] += SR * (f * (uR[2] + ds * n[2]) - UR[3]);
+    F[4] += SR * (Us4 - UR[4]);
+  } else {
+    phys_flux(UR, irR, uR, pR, unR, n, F);
+  }
+}
+
+// Viscous flux F_v . n from the face state and the conserved gradient.
+__device__ __forceinline__ void viscous_flux(const double U[5], const double g[5][3],
+                                             const double n[3], const FluxConst& c, double Fv[5]) {
+  const double ir = 1.0 / U[0];
+  const double u[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+  double gu[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) gu[a][j] = (g[1 + a][j] - u[a] * g[0][j]) * ir;
+  const double e = U[4] * ir;
+  double qn = 0.0;
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const double de = (g[4][j] - e * g[0][j]) * ir - (u[0] * gu[0][j] + u[1] * gu[1][j] + u[2] * gu[2][j]);
+    qn += de * n[j];
+  }
+  const double div = gu[0][0] + gu[1][1] + gu[2][2];
+  const double tdiv = (2.0 / 3.0) * c.mu * div;
+  double work = 0.0;
+  Fv[0] = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) t += c.mu * (gu[a][j] + gu[j][a]) * n[j];
+    t -= tdiv * n[a];
+    Fv[1 + a] = t;
+    work += u[a] * t;
+  }
+  Fv[4] = work + c.kap * c.gm1_over_R * qn;
+}
+
+// ------------------------------------------------------- reconstruction
+// thread = (cell i, variable v); tid = 5 i + v
+template <int ORDER, bool WENO, int ND>
+__global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
+  constexpr int K = ORDER == 1 ? 3 : 9;
+  constexpr int MC = 2 * K;
+  constexpr int MD = 6;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid / 5, v = tid - 5 * (tid / 5);
+  if (i >= a.N) return;
+  const int N = a.N;
+  const double* __restrict__ Uv = a.U + (size_t)v * N;
+  const double ui = Uv[i];
+  double ao[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) ao[k] = 0.0;
+#pragma unroll 6
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[(size_t)m * N + i]);
+    const double d = Uv[j] - ui;
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[k] = fma(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+  }
+  double c[K];
+  double S[6];
+  if (ORDER == 2) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) S[q] = __ldg(&a.mom[(size_t)q * N + i]);
+  }
+  if (!WENO) {
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = ao[k];
+  } else {
+    double b[ND][3];
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      b[s][0] = b[s][1] = b[s][2] = 0.0;
+#pragma unroll
+      for (int r = 0; r < MD; r++) {
+        const int j = __ldg(&a.sd[((size_t)s * MD + r) * N + i]);
+        const double d = Uv[j] - ui;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+          b[s][k] = fma(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
+      }
+    }
+    // smoothness indicators in xi units (h = V^(1/3)):
+    //   SI = (1/V) int |grad_xi p|^2 + sum_{|beta|=2} (d^beta_xi p)^2
+    const double qx0 = 2.0 * ao[3], qx1 = ao[6], qx2 = ao[7];
+    const double qy0 = ao[6], qy1 = 2.0 * ao[4], qy2 = ao[8];
+    const double qz0 = ao[7], qz1 = ao[8], qz2 = 2.0 * ao[5];
+    auto quad = [&](double x0, double x1, double x2) {
+      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 +
+             2.0 * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+    };
+    const double SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) +
+                       quad(qy0, qy1, qy2) + quad(qz0, qz1, qz2) +
+                       4.0 * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
+                       ao[7] * ao[7] + ao[8] * ao[8];
+    double SI[ND];
+    double tau = 0.0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+      tau += fabs(SI0 - SI[s]);
+    }
+    tau *= (1.0 / ND);
+    // omega~_s = lambda_s (1 + tau / (eps + SI_s)), normalised
+    const double w0 = a.lam0 * (1.0 + tau / (a.eps + SI0));
+    double ws[ND];
+    double wsum = w0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      ws[s] = a.lams * (1.0 + tau / (a.eps + SI[s]));
+      wsum += ws[s];
+    }
+    const double iws = 1.0 / wsum;
+    // p = omega_0 p_1 + sum_s omega_s p_s with p_1 = (p_opt - sum lambda_s p_s)/lambda_0
+    const double r0 = (w0 * iws) / a.lam0;
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      const double e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+      for (int k = 0; k < 3; k++) c[k] = fma(e, b[s][k], c[k]);
+    }
+  }
+  // monomial form: p = c0 + sum_k c_k psi_k(xi), c0 = U_i - sum_{k>=3} c_k mean(psi_k)
+  double c0 = ui;
+  if (ORDER == 2) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) c0 = fma(-c[3 + q], S[q], c0);
+  }
+  double* out = a.coef + (size_t)i * 5 + v;
+  const size_t st = (size_t)N * 5;
+  out[0] = c0;
+#pragma unroll
+  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
+}
+
+// ----------------------------------------------------------- face flux
+template <int ORDER>
+__device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N, int cell,
+                                          double x, double y, double z, double ih, double U[5],
+                                          double g[5][3]) {
+  const size_t st = (size_t)N * 5;
+  const double* p = coef + (size_t)cell * 5;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const double c0 = p[v], c1 = p[st + v], c2 = p[2 * st + v], c3 = p[3 * st + v];
+    if (ORDER == 1) {
+      U[v] = fma(c1, x, fma(c2, y, fma(c3, z, c0)));
+      g[v][0] = c1 * ih;
+      g[v][1] = c2 * ih;
+      g[v][2] = c3 * ih;
+    } else {
+      const double c4 = p[4 * st + v], c5 = p[5 * st + v], c6 = p[6 * st + v];
+      const double c7 = p[7 * st + v], c8 = p[8 * st + v], c9 = p[9 * st + v];
+      const double tx = fma(c4, x, fma(c7, y, fma(c8, z, c1)));
+      const double ty = fma(c5, y, fma(c9, z, c2));
+      const double tz = fma(c6, z, c3);
+      U[v] = fma(x, tx, fma(y, ty, fma(z, tz, c0)));
+      g[v][0] = fma(c4, x, tx) * ih;                       // c1 + 2c4 x + c7 y + c8 z
+      g[v][1] = fma(c7, x, fma(c5, y, ty)) * ih;           // c2 + c7 x + 2c5 y + c9 z
+      g[v][2] = fma(c8, x, fma(c9, y, fma(c6, z, tz))) * ih;  // c3 + c8 x + c9 y + 2c6 z
+    }
+  }
+}
+
+// thread = (face f, Gauss point q), NQ consecutive lanes per face
+template <int ORDER, bool VISC>
+__global__ void __launch_bounds__(256) k_face(FaceArgs a) {
+  constexpr int NQ = ORDER * ORDER;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = tid / NQ, q = tid - NQ * (tid / NQ);
+  const bool live = f < a.F;
+  const int fc = live ? f : a.F - 1;
+  const size_t F = a.F;
+  const double* __restrict__ fq = a.fq + (size_t)q * 10 * F + fc;
+  const double xl = fq[0], yl = fq[F], zl = fq[2 * F];
+  const double xr = fq[3 * F], yr = fq[4 * F], zr = fq[5 * F];
+  const double n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
+  const double area = fq[9 * F];
+  const int o = a.fo[fc], nb = a.fn[fc];
+  double UL[5], UR[5], gL[5][3], gR[5][3];
+  eval_side<ORDER>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], UL, gL);
+  eval_side<ORDER>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], UR, gR);
+  double Fc[5];
+  hllc_flux(UL, UR, n, a.c, Fc);
+  double flux[5];
+  if (VISC) {
+    const double pen = a.fpen[fc];
+    double Uf[5], gf[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const double jump = pen * (UR[v] - UL[v]);
+      Uf[v] = 0.5 * (UL[v] + UR[v]);
+#pragma unroll
+      for (int j = 0; j < 3; j++) gf[v][j] = fma(jump, n[j], 0.5 * (gL[v][j] + gR[v][j]));
+    }
+    double Fv[5];
+    viscous_flux(Uf, gf, n, a.c, Fv);
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = (Fc[v] - Fv[v]) * area;
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+  }
+#pragma unroll
+  for (int off = 1; off < NQ; off <<= 1)
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
+  if (live && q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = flux[v];
+  }
+}
+
+// ------------------------------------------- residual + Runge-Kutta stage
+template <int NFC>
+__device__ __forceinline__ double face_sum(const RKArgs& a, int i, int v) {
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < NFC; j++) {
+    const int e = __ldg(&a.cf[(size_t)j * a.N + i]);
+    const double g = __ldg(&a.G[(size_t)v * a.F + (e >> 1)]);
+    s += (e & 1) ? -g : g;
+  }
+  return s;
+}
+
+__device__ __forceinline__ bool physical(const double U[5], double gm1) {
+  const double p = gm1 * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
+  return U[0] > 0.0 && p > 0.0 && isfinite(p) && isfinite(U[0]);
+}
+
+// STAGE 0: plain residual R = -(1/V) sum sigma G -> out
+// STAGE 1: U1 = U0 + dt R;  2: U2 = 3/4 U0 + 1/4 (U1 + dt R);  3: U = 1/3 U0 + 2/3 (U2 + dt R)
+template <int STAGE, int NFC>
+__global__ void __launch_bounds__(256) k_rk(RKArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const double ivol = a.inv_vol[i];
+  const size_t N = a.N;
+  if (STAGE == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) a.out[v * N + i] = -face_sum<NFC>(a, i, v) * ivol;
+    return;
+  }
+  const double dt = *a.dt;
+  double Un[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const double R = -face_sum<NFC>(a, i, v) * ivol;
+    const double u0 = a.U0[v * N + i];
+    if (STAGE == 1) {
+      Un[v] = u0 + dt * R;
+    } else if (STAGE == 2) {
+      Un[v] = 0.75 * u0 + 0.25 * (a.Us[v * N + i] + dt * R);
+    } else {
+      Un[v] = u0 / 3.0 + (2.0 / 3.0) * (a.Us[v * N + i] + dt * R);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; v++) a.out[v * N + i] = Un[v];
+  if (!physical(Un, a.gm1)) atomicOr(a.err, 1);
+}
+
+// ------------------------------------------------------------ reductions
+constexpr int kRedThreads = 256;
+
+// per-block minimum of the CFL time-step limit
+__global__ void __launch_bounds__(kRedThreads)
+    k_dt_partial(const double* __restrict__ U, const double* __restrict__ dtlen, int N, double gam,
+                 double visc_coef /* Pr/(2 gam mu) or 0 */, double* __restrict__ part, int* err) {
+  __shared__ double sm[kRedThreads];
+  double best = INFINITY;
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double r = U[i], m0 = U[(size_t)N + i], m1 = U[2 * (size_t)N + i], m2 = U[3 * (size_t)N + i];
+    const double ir = 1.0 / r;
+    const double q2 = (m0 * m0 + m1 * m1 + m2 * m2) * ir * ir;
+    const double p = (gam - 1.0) * (U[4 * (size_t)N + i] - 0.5 * r * q2);
+    const double h = dtlen[i];
+    double d = h / (sqrt(q2) + sqrt(gam * p * ir));
+    if (visc_coef > 0.0) d = fmin(d, r * h * h * visc_coef);
+    if (!(r > 0.0 && p > 0.0 && d > 0.0)) bad = true;
+    best = fmin(best, d);
+  }
+  if (bad) atomicOr(err, 1);
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_dt_final(const double* __restrict__ part, int nb, double cfl, double* __restrict__ dt) {
+  __shared__ double sm[kRedThreads];
+  double best = INFINITY;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) best = fmin(best, part[b]);
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dt[0] = cfl * sm[0];
+}
+
+// per-block sums [V KE, V |curl u|^2, V (div u)^2, V] in a fixed tree order
+__global__ void __launch_bounds__(kRedThreads)
+    k_diag_partial(const double* __restrict__ U, const double* __restrict__ coef,
+                   const double* __restrict__ vol, const double* __restrict__ inv_h, int N,
+                   double* __restrict__ part) {
+  __shared__ double sm[4][kRedThreads];
+  double acc[4] = {0, 0, 0, 0};
+  const size_t st = (size_t)N * 5;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double r = U[i], ir = 1.0 / r;
+    const double u[3] = {U[(size_t)N + i] * ir, U[2 * (size_t)N + i] * ir, U[3 * (size_t)N + i] * ir};
+    const double ih = inv_h[i];
+    double g[4][3];  // gradients of rho, m_x, m_y, m_z at the centroid
+#pragma unroll
+    for (int v = 0; v < 4; v++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) g[v][j] = coef[(j + 1) * st + (size_t)i * 5 + v] * ih;
+    double gu[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) gu[q][j] = (g[1 + q][j] - u[q] * g[0][j]) * ir;
+    const double wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+    const double dv = gu[0][0] + gu[1][1] + gu[2][2];
+    const double V = vol[i];
+    acc[0] += V * 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    acc[1] += V * (wx * wx + wy * wy + wz * wz);
+    acc[2] += V * dv * dv;
+    acc[3] += V;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int q = 0; q < 4; q++) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < 4; q++) part[(size_t)blockIdx.x * 4 + q] = sm[q][0];
+}
+
+__global__ void k_diag_final(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[4] = {0, 0, 0, 0};
+  for (int b = 0; b < nb; b++)
+    for (int q = 0; q < 4; q++) s[q] += part[(size_t)b * 4 + q];
+  for (int q = 0; q < 4; q++) out[q] = s[q];
+}
+
+__global__ void k_set_scalar(double* __restrict__ dst, double v) { dst[0] = v; }
+__global__ void k_add_scalar(double* __restrict__ acc, const double* __restrict__ v) { acc[0] += v[0]; }
+
+}  // namespace ucns

@@ -1,0 +1,545 @@
+// Host side of libucns: mesh topology (periodic node identification, face
+// pairing, Morton cell order) and the FP64 precompute of ucns_precompute
+// (cell geometry, face quadrature, stencils, least-squares pseudo-inverses by
+// Householder QR, Eq. 4).  Produces structure-of-arrays host buffers in the
+// internal cell order; api.cu uploads them.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "host_arrays.hpp"
+#include "ucns_internal.hpp"
+
+namespace ucns {
+namespace {
+
+// VTK hexahedron: reference corners and faces ordered so (p2-p0)x(p3-p1)
+// points out of the cell.
+const int kHexCorner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                              {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+const int kHexFace[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
+                            {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
+// tetrahedron faces ordered so (p1-p0)x(p2-p0) points out of a positive tet
+const int kTetFace[4][3] = {{0, 2, 1}, {0, 1, 3}, {1, 2, 3}, {0, 3, 2}};
+
+const int* face_local_nodes(int npc, int lf) { return npc == 8 ? kHexFace[lf] : kTetFace[lf]; }
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double comp(V3 a, int d) { return d == 0 ? a.x : (d == 1 ? a.y : a.z); }
+
+// Gauss-Legendre points/weights on [0,1] in closed form (n = 1, 2, 3).
+void gauss01(int n, double* x, double* w) {
+  if (n == 1) {
+    x[0] = 0.5;
+    w[0] = 1.0;
+  } else if (n == 2) {
+    double d = 0.5 / std::sqrt(3.0);
+    x[0] = 0.5 - d; x[1] = 0.5 + d;
+    w[0] = w[1] = 0.5;
+  } else {
+    double d = 0.5 * std::sqrt(0.6);
+    x[0] = 0.5 - d; x[1] = 0.5; x[2] = 0.5 + d;
+    w[0] = 5.0 / 18.0; w[1] = 4.0 / 9.0; w[2] = 5.0 / 18.0;
+  }
+}
+
+struct CellPts {
+  V3 p[8];
+};
+
+CellPts load_cell(const ucns_mesh* m, int64_t user) {
+  CellPts c;
+  for (int a = 0; a < m->npc; a++) {
+    const double* x = &m->X[3 * m->C[user * m->npc + a]];
+    c.p[a] = {x[0], x[1], x[2]};
+  }
+  return c;
+}
+
+// Map the unit cube onto the cell: trilinear (hex) or collapsed (tet).
+void map_point(int npc, const CellPts& c, double s, double t, double u, V3* x, double* jac) {
+  if (npc == 8) {
+    V3 xs{0, 0, 0}, ds{0, 0, 0}, dt{0, 0, 0}, du{0, 0, 0};
+    for (int a = 0; a < 8; a++) {
+      double fs = kHexCorner[a][0] ? s : 1 - s, ft = kHexCorner[a][1] ? t : 1 - t,
+             fu = kHexCorner[a][2] ? u : 1 - u;
+      double gs = kHexCorner[a][0] ? 1 : -1, gt = kHexCorner[a][1] ? 1 : -1,
+             gu = kHexCorner[a][2] ? 1 : -1;
+      xs = xs + (fs * ft * fu) * c.p[a];
+      ds = ds + (gs * ft * fu) * c.p[a];
+      dt = dt + (fs * gt * fu) * c.p[a];
+      du = du + (fs * ft * gu) * c.p[a];
+    }
+    *x = xs;
+    *jac = dot(ds, cross(dt, du));
+  } else {
+    V3 e1 = c.p[1] - c.p[0], e2 = c.p[2] - c.p[1], e3 = c.p[3] - c.p[2];
+    *x = c.p[0] + s * e1 + (s * t) * e2 + (s * t * u) * e3;
+    double vol6 = dot(c.p[1] - c.p[0], cross(c.p[2] - c.p[0], c.p[3] - c.p[0]));
+    *jac = s * s * t * vol6;
+  }
+}
+
+struct Geom {
+  double V;
+  V3 c;
+  double h;
+  double S[6];  // (1/V) int xi_a xi_b, xi = (x - c)/h: xx yy zz xy xz yz
+};
+
+Geom cell_geometry(const ucns_mesh* m, int64_t user) {
+  CellPts cp = load_cell(m, user);
+  double gx[3], gw[3];
+  gauss01(3, gx, gw);  // exact: hex integrands are degree <= 4 per direction, tet <= 3
+  Geom g{};
+  double V = 0;
+  V3 mx{0, 0, 0};
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      for (int q = 0; q < 3; q++) {
+        V3 x;
+        double j;
+        map_point(m->npc, cp, gx[a], gx[b], gx[q], &x, &j);
+        double w = gw[a] * gw[b] * gw[q] * j;
+        V += w;
+        mx = mx + w * x;
+      }
+  g.V = V;
+  g.c = (1.0 / V) * mx;
+  g.h = std::cbrt(V);
+  double S[6] = {0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      for (int q = 0; q < 3; q++) {
+        V3 x;
+        double j;
+        map_point(m->npc, cp, gx[a], gx[b], gx[q], &x, &j);
+        double w = gw[a] * gw[b] * gw[q] * j;
+        V3 y = (1.0 / g.h) * (x - g.c);
+        S[0] += w * y.x * y.x; S[1] += w * y.y * y.y; S[2] += w * y.z * y.z;
+        S[3] += w * y.x * y.y; S[4] += w * y.x * y.z; S[5] += w * y.y * y.z;
+      }
+  for (int k = 0; k < 6; k++) g.S[k] = S[k] / V;
+  return g;
+}
+
+// Face quadrature of an owner-local face: points and owner-outward area vectors.
+int face_points(const ucns_mesh* m, int64_t owner_user, int lf, int order, V3* x, V3* dS) {
+  CellPts cp = load_cell(m, owner_user);
+  const int* fl = face_local_nodes(m->npc, lf);
+  if (m->nfn == 4) {
+    V3 Q0 = cp.p[fl[0]], Q1 = cp.p[fl[1]], Q2 = cp.p[fl[2]], Q3 = cp.p[fl[3]];
+    double gx[3], gw[3];
+    gauss01(order, gx, gw);
+    int q = 0;
+    for (int ia = 0; ia < order; ia++)
+      for (int ib = 0; ib < order; ib++, q++) {
+        double s = gx[ia], t = gx[ib];
+        x[q] = ((1 - s) * (1 - t)) * Q0 + (s * (1 - t)) * Q1 + (s * t) * Q2 + ((1 - s) * t) * Q3;
+        V3 da = (1 - t) * (Q1 - Q0) + t * (Q2 - Q3);
+        V3 db = (1 - s) * (Q3 - Q0) + s * (Q2 - Q1);
+        dS[q] = (gw[ia] * gw[ib]) * cross(da, db);
+      }
+    return q;
+  }
+  V3 Q0 = cp.p[fl[0]], Q1 = cp.p[fl[1]], Q2 = cp.p[fl[2]];
+  if (order == 1) {
+    x[0] = (1.0 / 3.0) * (Q0 + Q1 + Q2);
+    dS[0] = 0.5 * cross(Q1 - Q0, Q2 - Q0);
+    return 1;
+  }
+  // collapsed 2x2 Gauss on the triangle (exact to degree 2)
+  double gx[2], gw[2];
+  gauss01(2, gx, gw);
+  V3 e1 = Q1 - Q0, e2 = Q2 - Q1, nrm = cross(e1, e2);
+  int q = 0;
+  for (int ia = 0; ia < 2; ia++)
+    for (int ib = 0; ib < 2; ib++, q++) {
+      double a = gx[ia], b = gx[ib];
+      x[q] = Q0 + a * e1 + (a * b) * e2;
+      dS[q] = (gw[ia] * gw[ib] * a) * nrm;
+    }
+  return q;
+}
+
+// ---------------------------------------------------------------- topology
+struct QKey {
+  int64_t k[3];
+  bool operator==(const QKey& o) const { return k[0] == o.k[0] && k[1] == o.k[1] && k[2] == o.k[2]; }
+};
+struct QKeyHash {
+  size_t operator()(const QKey& q) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int d = 0; d < 3; d++) {
+      h ^= (uint64_t)q.k[d];
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
+uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+}  // namespace
+
+int build_topology(ucns_mesh* m) {
+  const int64_t N = m->N, nn = m->nn;
+  const int npc = m->npc;
+  for (int64_t k = 0; k < N * npc; k++)
+    if (m->C[k] < 0 || m->C[k] >= nn) return fail(UCNS_ERR_MESH, "cell node id out of range");
+  // periodic node identification: quantised wrapped coordinates
+  double scale = std::max(std::max(m->L[0], m->L[1]), m->L[2]);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t n = 0; n < nn; n++)
+    for (int d = 0; d < 3; d++) {
+      lo[d] = std::min(lo[d], m->X[3 * n + d]);
+      hi[d] = std::max(hi[d], m->X[3 * n + d]);
+    }
+  for (int d = 0; d < 3; d++) scale = std::max(scale, hi[d] - lo[d]);
+  const double quantum = 1e-8 * (scale > 0 ? scale : 1.0);
+  m->canon.assign(nn, 0);
+  {
+    std::unordered_map<QKey, int64_t, QKeyHash> first;
+    first.reserve((size_t)nn * 2);
+    for (int64_t n = 0; n < nn; n++) {
+      QKey q;
+      for (int d = 0; d < 3; d++) {
+        double x = m->X[3 * n + d];
+        if (m->per[d]) {
+          x -= m->L[d] * std::floor(x / m->L[d]);
+          if (x > m->L[d] * (1.0 - 1e-9)) x -= m->L[d];
+        }
+        q.k[d] = std::llround(x / quantum);
+      }
+      auto it = first.emplace(q, n);
+      m->canon[n] = it.first->second;
+    }
+  }
+  // Morton order of the vertex means (ties by user id)
+  std::vector<std::pair<uint64_t, int64_t>> key(N);
+  for (int64_t c = 0; c < N; c++) {
+    double s[3] = {0, 0, 0};
+    for (int a = 0; a < npc; a++)
+      for (int d = 0; d < 3; d++) s[d] += m->X[3 * m->C[c * npc + a] + d];
+    uint64_t code = 0;
+    for (int d = 0; d < 3; d++) {
+      double span = hi[d] - lo[d];
+      double t = span > 0 ? (s[d] / npc - lo[d]) / span : 0.0;
+      uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+      code |= spread3(q) << d;
+    }
+    key[c] = {code, c};
+  }
+  std::sort(key.begin(), key.end());
+  m->perm.resize(N);
+  m->iperm.resize(N);
+  for (int64_t k = 0; k < N; k++) {
+    m->perm[k] = key[k].second;
+    m->iperm[key[k].second] = k;
+  }
+  // faces: each element face is a sorted tuple of canonical nodes
+  struct FE {
+    std::array<int64_t, 4> k;
+    int64_t user;
+    int lf;
+  };
+  std::vector<FE> fe((size_t)N * m->nfc);
+  for (int64_t c = 0; c < N; c++)
+    for (int lf = 0; lf < m->nfc; lf++) {
+      FE& e = fe[(size_t)c * m->nfc + lf];
+      const int* fl = face_local_nodes(npc, lf);
+      e.k = {-1, -1, -1, -1};
+      for (int q = 0; q < m->nfn; q++) e.k[q] = m->canon[m->C[c * npc + fl[q]]];
+      std::sort(e.k.begin(), e.k.begin() + m->nfn);
+      e.user = c;
+      e.lf = lf;
+    }
+  std::sort(fe.begin(), fe.end(), [](const FE& a, const FE& b) {
+    if (a.k != b.k) return a.k < b.k;
+    return a.user < b.user;
+  });
+  const size_t ne = fe.size();
+  if (ne % 2) return fail(UCNS_ERR_MESH, "unpaired face (only closed periodic meshes are supported)");
+  m->F = (int64_t)(ne / 2);
+  if (m->F >= (int64_t(1) << 30)) return fail(UCNS_ERR_MESH, "too many faces");
+  struct FP {
+    int64_t o_int;
+    int lf, nlf;
+    int64_t n_int;
+  };
+  std::vector<FP> fp(m->F);
+  for (int64_t f = 0; f < m->F; f++) {
+    const FE& a = fe[2 * f];
+    const FE& b = fe[2 * f + 1];
+    if (a.k != b.k || (2 * f + 2 < (int64_t)ne && fe[2 * f + 2].k == b.k))
+      return fail(UCNS_ERR_MESH, "unpaired or non-manifold face");
+    if (a.user == b.user) return fail(UCNS_ERR_MESH, "a cell is its own face neighbour");
+    fp[f] = {m->iperm[a.user], a.lf, b.lf, m->iperm[b.user]};  // a.user < b.user: owner
+  }
+  std::sort(fp.begin(), fp.end(), [](const FP& a, const FP& b) {
+    return a.o_int != b.o_int ? a.o_int < b.o_int : a.lf < b.lf;
+  });
+  m->fo.resize(m->F);
+  m->fn.resize(m->F);
+  m->flf.resize(m->F);
+  m->cf.assign((size_t)N * m->nfc, -1);
+  for (int64_t f = 0; f < m->F; f++) {
+    m->fo[f] = (int32_t)fp[f].o_int;
+    m->fn[f] = (int32_t)fp[f].n_int;
+    m->flf[f] = (int8_t)fp[f].lf;
+    m->cf[(size_t)fp[f].o_int * m->nfc + fp[f].lf] = (int32_t)(f << 1);
+    m->cf[(size_t)fp[f].n_int * m->nfc + fp[f].nlf] = (int32_t)((f << 1) | 1);
+  }
+  return UCNS_OK;
+}
+
+namespace {
+
+struct Cand {
+  int64_t id;  // internal
+  int depth, shared;
+  int64_t user;
+};
+
+int64_t face_nbr(const ucns_mesh* m, int64_t i, int lf) {
+  int32_t e = m->cf[(size_t)i * m->nfc + lf];
+  int32_t f = e >> 1;
+  return (e & 1) ? m->fo[f] : m->fn[f];
+}
+
+// breadth-first search over face adjacency from `start`, never entering `avoid`
+bool bfs(const ucns_mesh* m, int64_t start, int64_t avoid, int maxd, std::vector<Cand>& out) {
+  out.clear();
+  out.push_back({start, 0, 0, m->perm[start]});
+  for (size_t head = 0; head < out.size(); head++) {
+    Cand cur = out[head];
+    if (cur.depth == maxd) continue;
+    for (int lf = 0; lf < m->nfc; lf++) {
+      int64_t n = face_nbr(m, cur.id, lf);
+      if (n == avoid) continue;
+      bool seen = false;
+      for (const Cand& c : out)
+        if (c.id == n) { seen = true; break; }
+      if (!seen) out.push_back({n, cur.depth + 1, 0, m->perm[n]});
+    }
+    if (out.size() > 512) return false;
+  }
+  return true;
+}
+
+int shared_nodes(const ucns_mesh* m, int64_t ui, int64_t um) {
+  int s = 0;
+  for (int a = 0; a < m->npc; a++) {
+    int64_t ca = m->canon[m->C[ui * m->npc + a]];
+    for (int b = 0; b < m->npc; b++)
+      if (m->canon[m->C[um * m->npc + b]] == ca) { s++; break; }
+  }
+  return s;
+}
+
+// Householder QR of A (M x K, row-major); P[k][r] = (R^-1 Q^T)[k][r] * w[r].
+bool pinv_householder(const double* Ain, int M, int K, const double* w, double* P) {
+  double A[kMaxMc * kMaxK], v[kMaxK][kMaxMc], beta[kMaxK], colnorm[kMaxK];
+  std::memcpy(A, Ain, sizeof(double) * M * K);
+  for (int j = 0; j < K; j++) {
+    double s = 0;
+    for (int r = 0; r < M; r++) s += A[r * K + j] * A[r * K + j];
+    colnorm[j] = std::sqrt(s);
+  }
+  for (int j = 0; j < K; j++) {
+    double nx = 0;
+    for (int r = j; r < M; r++) nx += A[r * K + j] * A[r * K + j];
+    nx = std::sqrt(nx);
+    if (!(nx > 1e-10 * colnorm[j])) return false;
+    double alpha = A[j * K + j] > 0 ? -nx : nx;
+    for (int r = 0; r < M; r++) v[j][r] = r < j ? 0.0 : A[r * K + j];
+    v[j][j] -= alpha;
+    double vv = 0;
+    for (int r = j; r < M; r++) vv += v[j][r] * v[j][r];
+    beta[j] = 2.0 / vv;
+    for (int c = j; c < K; c++) {
+      double d = 0;
+      for (int r = j; r < M; r++) d += v[j][r] * A[r * K + c];
+      d *= beta[j];
+      for (int r = j; r < M; r++) A[r * K + c] -= d * v[j][r];
+    }
+  }
+  // thin Q: apply the reflectors (last first) to the first K unit columns
+  double Q[kMaxMc * kMaxK];
+  for (int r = 0; r < M; r++)
+    for (int c = 0; c < K; c++) Q[r * K + c] = (r == c) ? 1.0 : 0.0;
+  for (int j = K - 1; j >= 0; j--)
+    for (int c = 0; c < K; c++) {
+      double d = 0;
+      for (int r = j; r < M; r++) d += v[j][r] * Q[r * K + c];
+      d *= beta[j];
+      for (int r = j; r < M; r++) Q[r * K + c] -= d * v[j][r];
+    }
+  // P = R^-1 Q^T diag(w): solve R X = Q^T column by column (back substitution)
+  for (int r = 0; r < M; r++) {
+    double x[kMaxK];
+    for (int k = K - 1; k >= 0; k--) {
+      double s = Q[r * K + k];
+      for (int l = k + 1; l < K; l++) s -= A[k * K + l] * x[l];
+      x[k] = s / A[k * K + k];
+    }
+    for (int k = 0; k < K; k++) P[k * M + r] = x[k] * w[r];
+  }
+  return true;
+}
+
+}  // namespace
+
+int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
+  const int64_t N = m->N, F = m->F;
+  const int order = p->order;
+  const int K = order == 1 ? 3 : 9;
+  const int Mc = 2 * K;
+  const int nd = (order == 2 && p->scheme == UCNS_SCHEME_CWENOZ) ? m->nfc : 0;
+  const int Md = kMd;
+  const int nq = order * order;
+  m->K = K; m->Mc = Mc; m->nd = nd; m->Md = Md; m->nq = nq; m->NC = K + 1;
+  std::vector<Geom> g(N);  // internal order
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < N; i++) g[i] = cell_geometry(m, m->perm[i]);
+  for (int64_t i = 0; i < N; i++)
+    if (!(g[i].V > 0)) return fail(UCNS_ERR_MESH, "cell with non-positive volume");
+  auto shift_of = [&](int64_t i, int64_t j, double s[3]) {  // nearest image of j seen from i
+    for (int d = 0; d < 3; d++) {
+      s[d] = 0.0;
+      if (m->per[d]) s[d] = -m->L[d] * std::nearbyint((comp(g[j].c, d) - comp(g[i].c, d)) / m->L[d]);
+    }
+  };
+  h->vol.resize(N); h->inv_vol.resize(N); h->inv_h.resize(N); h->dtlen.resize(N);
+  h->mom.resize(6 * N);
+  for (int64_t i = 0; i < N; i++) {
+    h->vol[i] = g[i].V;
+    h->inv_vol[i] = 1.0 / g[i].V;
+    h->inv_h[i] = 1.0 / g[i].h;
+    for (int k = 0; k < 6; k++) h->mom[k * N + i] = g[i].S[k];
+  }
+  // faces: quadrature in owner / neighbour local coordinates
+  h->fq.assign((size_t)nq * 10 * F, 0.0);
+  h->fpen.resize(F);
+  std::vector<double> area(F);
+#pragma omp parallel for schedule(static)
+  for (int64_t f = 0; f < F; f++) {
+    int64_t o = m->fo[f], n = m->fn[f];
+    V3 x[16], dS[16];
+    face_points(m, m->perm[o], m->flf[f], order, x, dS);
+    double s[3];
+    shift_of(o, n, s);
+    V3 sv{s[0], s[1], s[2]};
+    V3 tot{0, 0, 0};
+    for (int q = 0; q < nq; q++) {
+      double a = std::sqrt(dot(dS[q], dS[q]));
+      V3 nh = (1.0 / a) * dS[q];
+      V3 xl = (1.0 / g[o].h) * (x[q] - g[o].c);
+      V3 xr = (1.0 / g[n].h) * (x[q] - sv - g[n].c);
+      double vals[10] = {xl.x, xl.y, xl.z, xr.x, xr.y, xr.z, nh.x, nh.y, nh.z, a};
+      for (int c = 0; c < 10; c++) h->fq[((size_t)q * 10 + c) * F + f] = vals[c];
+      tot = tot + dS[q];
+    }
+    area[f] = std::sqrt(dot(tot, tot));
+    V3 dc = g[n].c + sv - g[o].c;
+    h->fpen[f] = p->alpha / std::sqrt(dot(dc, dc));
+  }
+  for (int64_t i = 0; i < N; i++) {
+    double asum = 0;
+    for (int lf = 0; lf < m->nfc; lf++) asum += area[m->cf[(size_t)i * m->nfc + lf] >> 1];
+    h->dtlen[i] = 2.0 * g[i].V / asum;
+  }
+  // stencils and pseudo-inverses
+  h->sc.assign((size_t)Mc * N, 0);
+  h->Pc.assign((size_t)K * Mc * N, 0.0);
+  h->sd.assign((size_t)nd * Md * N, 0);
+  h->Pd.assign((size_t)nd * 3 * Md * N, 0.0);
+  int bad = 0;
+  // A row of cell i's basis integrated over member j's image (moment form):
+  // int_{V_j} phi_k = V_j [psi_k(d) + (h_j/h_i)^2 S_j,k - S_i,k], d = (c_j' - c_i)/h_i
+  auto arow = [&](int64_t i, int64_t j, int KK, double* row) {
+    double s[3];
+    shift_of(i, j, s);
+    double d[3];
+    for (int q = 0; q < 3; q++) d[q] = (comp(g[j].c, q) + s[q] - comp(g[i].c, q)) / g[i].h;
+    double r2 = (g[j].h / g[i].h) * (g[j].h / g[i].h);
+    double V = g[j].V;
+    row[0] = V * d[0]; row[1] = V * d[1]; row[2] = V * d[2];
+    if (KK == 9) {
+      const double* Sj = g[j].S;
+      const double* Si = g[i].S;
+      row[3] = V * (d[0] * d[0] + r2 * Sj[0] - Si[0]);
+      row[4] = V * (d[1] * d[1] + r2 * Sj[1] - Si[1]);
+      row[5] = V * (d[2] * d[2] + r2 * Sj[2] - Si[2]);
+      row[6] = V * (d[0] * d[1] + r2 * Sj[3] - Si[3]);
+      row[7] = V * (d[0] * d[2] + r2 * Sj[4] - Si[4]);
+      row[8] = V * (d[1] * d[2] + r2 * Sj[5] - Si[5]);
+    }
+  };
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
+  for (int64_t i = 0; i < N; i++) {
+    std::vector<Cand> c;
+    if (!bfs(m, i, -1, 3, c)) { bad |= 1; continue; }
+    for (size_t q = 1; q < c.size(); q++) c[q].shared = shared_nodes(m, m->perm[i], c[q].user);
+    std::sort(c.begin() + 1, c.end(), [](const Cand& a, const Cand& b) {
+      if (a.depth != b.depth) return a.depth < b.depth;
+      if (a.shared != b.shared) return a.shared > b.shared;
+      return a.user < b.user;
+    });
+    if ((int)c.size() - 1 < Mc) { bad |= 2; continue; }
+    double A[kMaxMc * kMaxK], w[kMaxMc], P[kMaxK * kMaxMc];
+    for (int r = 0; r < Mc; r++) {
+      int64_t j = c[1 + r].id;
+      h->sc[(size_t)r * N + i] = (int32_t)j;
+      arow(i, j, K, &A[r * K]);
+      w[r] = g[j].V;
+    }
+    if (!pinv_householder(A, Mc, K, w, P)) { bad |= 4; continue; }
+    for (int k = 0; k < K; k++)
+      for (int r = 0; r < Mc; r++) h->Pc[((size_t)k * Mc + r) * N + i] = P[k * Mc + r];
+    for (int s = 0; s < nd; s++) {
+      int64_t nb = face_nbr(m, i, s);
+      if (!bfs(m, nb, i, 2, c)) { bad |= 1; break; }
+      std::sort(c.begin() + 1, c.end(), [](const Cand& a, const Cand& b) {
+        if (a.depth != b.depth) return a.depth < b.depth;
+        return a.user < b.user;
+      });
+      if ((int)c.size() < Md) { bad |= 2; break; }
+      for (int r = 0; r < Md; r++) {
+        int64_t j = c[r].id;
+        h->sd[((size_t)s * Md + r) * N + i] = (int32_t)j;
+        arow(i, j, 3, &A[r * 3]);
+        w[r] = g[j].V;
+      }
+      if (!pinv_householder(A, Md, 3, w, P)) { bad |= 4; break; }
+      for (int k = 0; k < 3; k++)
+        for (int r = 0; r < Md; r++) h->Pd[(((size_t)s * 3 + k) * Md + r) * N + i] = P[k * Md + r];
+    }
+  }
+  if (bad & 1) return fail(UCNS_ERR_STENCIL, "stencil search overflow");
+  if (bad & 2) return fail(UCNS_ERR_STENCIL, "too few cells for a stencil (mesh too small)");
+  if (bad & 4) return fail(UCNS_ERR_STENCIL, "rank-deficient least-squares stencil");
+  return UCNS_OK;
+}
+
+}  // namespace ucns

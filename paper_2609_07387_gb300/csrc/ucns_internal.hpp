@@ -1,0 +1,101 @@
+// Internal data model of libucns: host topology/geometry built once by
+// ucns_mesh_create / ucns_precompute, and the device-resident structure-of-
+// arrays copy the kernels read (Sec. 2.3: flat arrays with explicit offsets,
+// persistent device residency; cells in a Morton order).
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ucns.h"
+
+namespace ucns {
+
+struct HostArrays;
+constexpr int kMaxK = 9;    // non-constant modes of a quadratic in 3-D
+constexpr int kMaxMc = 18;  // central stencil size 2K
+constexpr int kMaxDir = 6;  // directional stencils = faces of the element
+constexpr int kMd = 6;      // directional stencil size 2*K(linear)
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+// Device pointers of one precomputed mesh (all in internal cell order).
+struct DeviceMesh {
+  int32_t N = 0, F = 0;
+  // cells
+  double* inv_vol = nullptr;  // [N]
+  double* vol = nullptr;      // [N]
+  double* inv_h = nullptr;    // [N] 1/h_i, h_i = V_i^(1/3)
+  double* dtlen = nullptr;    // [N] CFL length 2 V_i / sum_f |S_f|
+  double* mom = nullptr;      // [6][N] (1/V) int xi_a xi_b: xx yy zz xy xz yz
+  int32_t* sc = nullptr;      // [Mc][N] central stencil
+  double* Pc = nullptr;       // [K][Mc][N] central pseudo-inverse
+  int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
+  double* Pd = nullptr;       // [nd][3][Md][N]
+  float* Pcf = nullptr;       // FP32 copies (mixed precision)
+  float* Pdf = nullptr;
+  int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)
+  // faces
+  int32_t* fo = nullptr;      // [F] owner
+  int32_t* fn = nullptr;      // [F] neighbour
+  double* fq = nullptr;       // [nq][10][F] xiL(3) xiR(3) n(3) |dS|(1)
+  float* fqf = nullptr;       // FP32 copy
+  double* fpen = nullptr;     // [F] alpha / L_int
+  // scratch owned by the handle
+  double* coef = nullptr;     // [NC][N][5] reconstructed monomial coefficients
+  float* coeff = nullptr;     // FP32 copy of the non-constant coefficients (mixed)
+  double* G = nullptr;        // [5][F] face flux integrals
+  double* Ustage = nullptr;   // [5][N] Runge-Kutta stage state
+  double* Uhost = nullptr;    // [5][N] device copy for the host-buffer entry point
+  double* red = nullptr;      // reduction partials
+  double* dt = nullptr;       // [1] device time step
+  int* err = nullptr;         // [1] device error word
+  int red_blocks = 0;
+};
+
+}  // namespace ucns
+
+struct ucns_mesh {
+  // ---- topology (host) ----
+  int64_t N = 0, nn = 0;
+  int npc = 0, nfc = 0, nfn = 0;
+  double L[3] = {0, 0, 0};
+  int per[3] = {0, 0, 0};
+  std::vector<double> X;        // [nn][3]
+  std::vector<int64_t> C;       // [N][npc] (user order)
+  std::vector<int64_t> canon;   // node -> canonical node
+  std::vector<int64_t> perm;    // internal -> user
+  std::vector<int64_t> iperm;   // user -> internal
+  // faces, internal numbering; owner = the cell with the lower user id
+  int64_t F = 0;
+  std::vector<int32_t> fo, fn;  // internal cell ids
+  std::vector<int8_t> flf;      // owner-local face index
+  std::vector<int32_t> cf;      // [N][nfc] internal, face << 1 | is_neighbour
+  // ---- precompute ----
+  bool precomputed = false;
+  ucns_params P{};
+  int K = 0, Mc = 0, nd = 0, Md = 0, nq = 0, NC = 0;
+  ucns::DeviceMesh d;
+  std::shared_ptr<ucns::HostArrays> host;  // kept only by ucns_precompute_host
+  // opt-in kernel timing
+  bool prof = false;
+  struct ProfRec {
+    int kind;
+    void* a;
+    void* b;
+  };
+  std::vector<ProfRec> prof_live;
+  std::vector<void*> prof_pool;
+  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace ucns {
+int build_topology(ucns_mesh* m);
+struct HostArrays;
+int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h);
+void device_free(ucns_mesh* m);
+}  // namespace ucns

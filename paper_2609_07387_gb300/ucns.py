@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libucns (include/ucns.h).
+
+Argument marshalling only: every step of the residual / Runge-Kutta path
+runs in the library's CUDA kernels.  Device states are torch CUDA tensors of
+dtype float64 and shape [5, n_cells] (contiguous), in the library's internal
+cell order; ``Mesh.to_internal`` / ``Mesh.to_user`` permute numpy or torch
+arrays between the caller's order and that order.  There is no CPU fallback:
+loading fails loudly when the shared library is missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+UCNS_OK = 0
+ERRORS = {
+    -1: "UCNS_ERR_INVALID_ARG",
+    -2: "UCNS_ERR_MESH",
+    -3: "UCNS_ERR_STENCIL",
+    -4: "UCNS_ERR_CUDA",
+    -5: "UCNS_ERR_NONPHYSICAL",
+    -6: "UCNS_ERR_TIMEOUT",
+    -7: "UCNS_ERR_STATE",
+    -8: "UCNS_ERR_NOMEM",
+}
+
+# every entry point declared in include/ucns.h
+EXPORTS = (
+    "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps_host",
+    "ucns_check_state", "ucns_diagnostics", "ucns_time_step", "ucns_profile", "ucns_profile_read",
+    "ucns_cell_order", "ucns_mesh_info",
+    "ucns_last_error", "ucns_mesh_destroy",
+)
+
+
+class UcnsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("order", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("gamma", C.c_double), ("prandtl", C.c_double), ("reynolds", C.c_double), ("mach", C.c_double),
+        ("cfl", C.c_double), ("lambda_central", C.c_double), ("epsilon", C.c_double), ("alpha", C.c_double),
+    ]
+
+
+class _Diag(C.Structure):
+    _fields_ = [("kinetic_energy", C.c_double), ("eps_solenoidal", C.c_double),
+                ("eps_dilatational", C.c_double), ("volume", C.c_double)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libucns.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"libucns.so not built: {path}")
+            _build.build()
+        lib = C.CDLL(path)
+        P, I64, I32 = C.c_void_p, C.c_int64, C.c_int32
+        for name in EXPORTS:
+            getattr(lib, name)  # raises AttributeError if an export is missing
+        lib.ucns_mesh_create.argtypes = [P, I64, P, I64, I32, P, C.POINTER(P)]
+        lib.ucns_precompute.argtypes = [P, C.POINTER(_Params)]
+        lib.ucns_precompute_host.argtypes = [P, C.POINTER(_Params)]
+        lib.ucns_stencil.argtypes = [P, I64, I32, P, P]
+        lib.ucns_residual.argtypes = [P, P, P, P]
+        lib.ucns_rk_step.argtypes = [P, P, C.POINTER(C.c_double), P]
+        lib.ucns_rk_steps_host.argtypes = [P, P, I32, C.POINTER(C.c_double), P]
+        lib.ucns_check_state.argtypes = [P, P]
+        lib.ucns_diagnostics.argtypes = [P, P, C.POINTER(_Diag), P]
+        lib.ucns_time_step.argtypes = [P, P, C.POINTER(C.c_double), P]
+        lib.ucns_profile.argtypes = [P, I32]
+        lib.ucns_profile_read.argtypes = [P, P, P]
+        lib.ucns_cell_order.argtypes = [P, P]
+        lib.ucns_mesh_info.argtypes = [P, P]
+        lib.ucns_last_error.restype = C.c_char_p
+        lib.ucns_mesh_destroy.argtypes = [P]
+        for name in EXPORTS:
+            if name not in ("ucns_last_error", "ucns_mesh_destroy"):
+                getattr(lib, name).restype = C.c_int
+        lib.ucns_mesh_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def _check(lib, rc: int):
+    if rc != UCNS_OK:
+        raise UcnsError(rc, lib.ucns_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dev_ptr(t, n_cells: int) -> int:
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and tuple(t.shape) == (5, n_cells)):
+        raise ValueError(f"expected a contiguous cuda float64 tensor of shape (5, {n_cells})")
+    return t.data_ptr()
+
+
+@dataclass
+class Params:
+    """Scheme parameters (defaults: the Taylor-Green configuration)."""
+
+    order: int = 2
+    scheme: int = 1           # 0 linear, 1 CWENOZ
+    precision: int = 0        # 0 FP64, 1 mixed
+    gamma: float = 1.4
+    Pr: float = 0.71
+    Re: float = 1600.0        # <= 0: inviscid
+    Mach: float = 0.1
+    cfl: float = 0.5
+    lam_central: float = 1000.0
+    eps: float = 1e-6
+    alpha: float = 4.0 / 3.0
+
+    def c_struct(self) -> _Params:
+        return _Params(self.order, self.scheme, self.precision, 0, self.gamma, self.Pr, self.Re, self.Mach,
+                       self.cfl, self.lam_central, self.eps, self.alpha)
+
+
+class Mesh:
+    """A periodic hex or tet mesh with its device-resident precompute."""
+
+    def __init__(self, nodes, cells, box, params: Params | None = None):
+        lib = load()
+        self._lib = lib
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        box = np.ascontiguousarray(box, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib, lib.ucns_mesh_create(nodes.ctypes.data, nodes.shape[0], cells.ctypes.data, cells.shape[0],
+                                         cells.shape[1], box.ctypes.data, C.byref(h)))
+        self._h = h
+        self.n_cells = int(cells.shape[0])
+        perm = np.zeros(self.n_cells, dtype=np.int64)
+        _check(lib, lib.ucns_cell_order(h, perm.ctypes.data))
+        self.perm = perm
+        self.iperm = np.empty_like(perm)
+        self.iperm[perm] = np.arange(self.n_cells)
+        self.params = None
+        self._info()
+        if params is not None:
+            self.precompute(params)
+
+    def _info(self):
+        info = np.zeros(8, dtype=np.int64)
+        _check(self._lib, self._lib.ucns_mesh_info(self._h, info.ctypes.data))
+        (self.n_cells, self.n_faces, self.K, self.Mc, self.nd, self.Md, self.nq, self.nfc) = (int(v) for v in info)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.ucns_mesh_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+    def precompute(self, params: Params):
+        p = params.c_struct()
+        _check(self._lib, self._lib.ucns_precompute(self._h, C.byref(p)))
+        self.params = params
+        self._info()
+        return self
+
+    def precompute_host(self, params: Params):
+        """Host half of the precompute only (no GPU needed); enables stencil()."""
+        p = params.c_struct()
+        _check(self._lib, self._lib.ucns_precompute_host(self._h, C.byref(p)))
+        self.params = params
+        self._info()
+        return self
+
+    def stencil(self, cell: int, which: int = -1):
+        """(members [M] caller ids, P [K, M]) of one stencil (after precompute_host)."""
+        M = self.Mc if which < 0 else self.Md
+        K = self.K if which < 0 else 3
+        mem = np.zeros(M, dtype=np.int64)
+        P = np.zeros((K, M))
+        _check(self._lib, self._lib.ucns_stencil(self._h, int(cell), int(which), mem.ctypes.data, P.ctypes.data))
+        return mem, P
+
+    # ---- ordering helpers -------------------------------------------------
+    def to_internal(self, U_user):
+        """[5, N] caller order -> internal order (numpy or torch)."""
+        return U_user[:, self.perm]
+
+    def to_user(self, U_int):
+        return U_int[:, self.iperm]
+
+    # ---- device calls -----------------------------------------------------
+    def residual(self, U, R=None, stream=None):
+        import torch
+
+        if R is None:
+            R = torch.empty_like(U)
+        _check(self._lib, self._lib.ucns_residual(self._h, _dev_ptr(U, self.n_cells), _dev_ptr(R, self.n_cells),
+                                                  _stream_ptr(stream)))
+        return R
+
+    def rk_step(self, U, dt: float | None = None, stream=None, return_dt: bool = False):
+        """One SSP-RK3 step in place.  dt=None: CFL dt on the device (no
+        sync unless return_dt); dt>0: fixed."""
+        ptr = _dev_ptr(U, self.n_cells)
+        if dt is not None and dt > 0:
+            d = C.c_double(dt)
+            _check(self._lib, self._lib.ucns_rk_step(self._h, ptr, C.byref(d), _stream_ptr(stream)))
+            return dt
+        if return_dt:
+            d = C.c_double(0.0)
+            _check(self._lib, self._lib.ucns_rk_step(self._h, ptr, C.byref(d), _stream_ptr(stream)))
+            return d.value
+        _check(self._lib, self._lib.ucns_rk_step(self._h, ptr, None, _stream_ptr(stream)))
+        return None
+
+    def rk_steps_host(self, U_host, n_steps: int, stream=None) -> float:
+        """n_steps on a host [5, N] float64 array/tensor (copied in and out)."""
+        if isinstance(U_host, np.ndarray):
+            if not (U_host.dtype == np.float64 and U_host.flags.c_contiguous and U_host.shape == (5, self.n_cells)):
+                raise ValueError("U_host must be a C-contiguous float64 array of shape (5, n_cells)")
+            ptr = U_host.ctypes.data
+        else:
+            if U_host.is_cuda or U_host.dtype.itemsize != 8 or not U_host.is_contiguous():
+                raise ValueError("U_host must be a contiguous float64 host tensor")
+            ptr = U_host.data_ptr()
+        t = C.c_double(0.0)
+        _check(self._lib, self._lib.ucns_rk_steps_host(self._h, ptr, int(n_steps), C.byref(t), _stream_ptr(stream)))
+        return t.value
+
+    def check_state(self, stream=None):
+        _check(self._lib, self._lib.ucns_check_state(self._h, _stream_ptr(stream)))
+
+    def time_step(self, U, stream=None) -> float:
+        d = C.c_double(0.0)
+        _check(self._lib, self._lib.ucns_time_step(self._h, _dev_ptr(U, self.n_cells), C.byref(d),
+                                                   _stream_ptr(stream)))
+        return d.value
+
+    KINDS = ("recon", "face", "rk", "dt", "diag", "other")
+
+    def profile(self, enable: bool = True):
+        """Open (or close) a per-kernel CUDA-event timing window."""
+        _check(self._lib, self._lib.ucns_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(6)
+        n = np.zeros(6, dtype=np.int64)
+        _check(self._lib, self._lib.ucns_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KINDS)}
+
+    def diagnostics(self, U, stream=None) -> dict:
+        d = _Diag()
+        _check(self._lib, self._lib.ucns_diagnostics(self._h, _dev_ptr(U, self.n_cells), C.byref(d),
+                                                     _stream_ptr(stream)))
+        return {"ke": d.kinetic_energy, "eps_s": d.eps_solenoidal, "eps_d": d.eps_dilatational,
+                "volume": d.volume}

@@ -1,0 +1,178 @@
+"""GPU parity: libucns (CUDA, through the C ABI) against the CPU oracle on the
+same seeded inputs.
+
+Bar (FP64 path): per conserved component c,
+    ||R_gpu,c - R_cpu,c||_inf / ||R_cpu,c||_inf <= 1e-12,
+and the kinetic-energy history after 100 SSP-RK3 steps within 1e-10
+relative.  Sizes span many thread blocks with ragged tails; the full-size
+64^3 jittered P2 CWENOZ residual is compared element by element.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_07387_gb300 import inputs as I
+from paper_2609_07387_gb300 import ucns
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_R = 1e-12
+TOL_KE = 1e-10
+
+
+def _norm_err(a, b):
+    den = np.abs(b).max(axis=1)
+    return (np.abs(a - b).max(axis=1) / np.where(den > 0, den, 1.0))
+
+
+def _pair(nodes, cells, box, **kw):
+    p = ucns.Params(**kw)
+    op = O.Params(order=p.order, scheme=p.scheme, gamma=p.gamma, Pr=p.Pr, Re=p.Re, Mach=p.Mach, cfl=p.cfl,
+                  lam_central=p.lam_central, eps=p.eps, alpha=p.alpha)
+    return ucns.Mesh(nodes, cells, box, p), O.Case(nodes, cells, box, op)
+
+
+def _gpu_residual(m, U_user):
+    U = torch.from_numpy(np.ascontiguousarray(m.to_internal(U_user))).cuda()
+    R = m.residual(U)
+    torch.cuda.synchronize()
+    return m.to_user(R.cpu().numpy())
+
+
+CASES = [
+    # name, lattice n, jitter, tets, order, scheme, Re, Mach, state
+    ("C1_p1_uniform_16", 16, 0.0, False, 1, 0, 1600.0, 0.1, "tgv"),
+    ("p1_jitter_13_inviscid", 13, 0.1, False, 1, 0, 0.0, 0.3, "noisy"),
+    ("p2_linear_jitter_11", 11, 0.1, False, 2, 0, 1600.0, 0.1, "noisy"),
+    ("p2_cwenoz_jitter_13", 13, 0.1, False, 2, 1, 1600.0, 0.1, "noisy"),
+    ("p2_cwenoz_jitter_12_M125", 12, 0.1, False, 2, 1, 1600.0, 1.25, "perturbed"),
+    ("p2_cwenoz_tets_6", 6, 0.1, True, 2, 1, 1600.0, 0.1, "noisy"),
+    ("p2_cwenoz_tets_7_inviscid", 7, 0.1, True, 2, 1, 0.0, 0.5, "noisy"),
+]
+
+
+def _state(kind, nodes, cells, mach):
+    if kind == "tgv":
+        return I.tgv_state(nodes, cells, mach)
+    if kind == "noisy":
+        return I.noisy_state(nodes, cells, mach, 0.05, seed=3)
+    return I.tgv_perturbed_state(nodes, cells, mach, 0.05, seed=4)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_residual_parity(case):
+    name, n, jit, tets, order, scheme, Re, M, st = case
+    nodes, cells, box = I.hex_lattice(n, jitter=jit, seed=5)
+    if tets:
+        cells = I.split_tets(cells)
+    m, oc = _pair(nodes, cells, box, order=order, scheme=scheme, Re=Re, Mach=M)
+    U = _state(st, nodes, cells, M)
+    Rg = _gpu_residual(m, U)
+    Rc = oc.residual(U)
+    err = _norm_err(Rg, Rc)
+    assert np.all(err <= TOL_R), err
+
+
+def test_residual_parity_full_size_64_cwenoz():
+    """The benchmark workload itself: 64^3 jittered hexahedra, P2 CWENOZ,
+    every one of the 5 x 262144 residual entries against the oracle."""
+    nodes, cells, box = I.hex_lattice(64, jitter=0.1, seed=1)
+    m, oc = _pair(nodes, cells, box, order=2, scheme=1, Re=1600.0, Mach=0.1)
+    U = I.tgv_state(nodes, cells, 0.1)
+    Rg = _gpu_residual(m, U)
+    Rc = oc.residual(U)
+    err = _norm_err(Rg, Rc)
+    assert np.all(err <= TOL_R), err
+
+
+def test_rk_steps_and_time_step_parity():
+    """C1 configuration: 16^3 hexahedra, P1, 10 SSP-RK3 steps at CFL 0.5."""
+    nodes, cells, box = I.hex_lattice(16)
+    m, oc = _pair(nodes, cells, box, order=1, scheme=0, Re=1600.0, Mach=0.1, cfl=0.5)
+    U0 = I.tgv_state(nodes, cells, 0.1)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U0))).cuda()
+    Uc = U0.copy()
+    for _ in range(10):
+        dtg = m.rk_step(Ug, return_dt=True)
+        Uc, dtc = oc.rk_step(Uc, 0.0)
+        assert dtg == dtc or abs(dtg - dtc) <= 1e-14 * dtc
+    err = _norm_err(m.to_user(Ug.cpu().numpy()), Uc)
+    assert np.all(err <= 1e-12), err
+
+
+@pytest.mark.parametrize("order,scheme,n,jit", [(1, 0, 16, 0.0), (2, 1, 10, 0.1)])
+def test_ke_history_100_steps(order, scheme, n, jit):
+    """Kinetic-energy (and dissipation) history over 100 steps with the CFL
+    time step on both sides: KE within 1e-10 relative at every step."""
+    nodes, cells, box = I.hex_lattice(n, jitter=jit, seed=2)
+    m, oc = _pair(nodes, cells, box, order=order, scheme=scheme, Re=1600.0, Mach=0.1, cfl=0.5)
+    U0 = I.tgv_state(nodes, cells, 0.1)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U0))).cuda()
+    Uc = U0.copy()
+    worst_ke = worst_es = 0.0
+    for step in range(100):
+        m.rk_step(Ug)
+        Uc, _ = oc.rk_step(Uc, 0.0)
+        if step % 10 == 9 or step == 99:
+            dg = m.diagnostics(Ug)
+            dc = oc.diagnostics(Uc)
+            worst_ke = max(worst_ke, abs(dg["ke"] - dc[0]) / dc[0])
+            worst_es = max(worst_es, abs(dg["eps_s"] - dc[1]) / dc[1])
+    m.check_state()
+    assert worst_ke <= TOL_KE, worst_ke
+    assert worst_es <= 1e-9, worst_es
+
+
+def test_diagnostics_and_time_step_parity():
+    nodes, cells, box = I.hex_lattice(12, jitter=0.1, seed=7)
+    m, oc = _pair(nodes, cells, box, order=2, scheme=1)
+    U = I.noisy_state(nodes, cells, 0.1, 0.02, seed=1)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    dg = m.diagnostics(Ug)
+    dc = oc.diagnostics(U)
+    assert abs(dg["ke"] - dc[0]) <= 1e-13 * dc[0]
+    assert abs(dg["eps_s"] - dc[1]) <= 1e-11 * dc[1]
+    assert abs(dg["eps_d"] - dc[2]) <= 1e-11 * max(dc[2], 1e-30)
+    assert abs(dg["volume"] - (2 * math.pi) ** 3) <= 1e-12 * (2 * math.pi) ** 3
+    assert m.time_step(Ug) == oc.time_step(U)
+
+
+def test_deterministic_and_host_entry_point():
+    nodes, cells, box = I.hex_lattice(14, jitter=0.1, seed=9)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1))
+    U = np.ascontiguousarray(m.to_internal(I.noisy_state(nodes, cells, 0.1, 0.03, seed=2)))
+    a = torch.from_numpy(U.copy()).cuda()
+    b = torch.from_numpy(U.copy()).cuda()
+    for _ in range(3):
+        m.rk_step(a)
+        m.rk_step(b)
+    assert torch.equal(a, b)
+    Ra, Rb = m.residual(a), m.residual(a)
+    assert torch.equal(Ra, Rb)
+    # host-buffer entry point = device entry point, bit for bit
+    h = U.copy()
+    t = m.rk_steps_host(h, 3)
+    assert t > 0
+    assert np.array_equal(h, a.cpu().numpy())
+
+
+def test_nonphysical_state_reported():
+    nodes, cells, box = I.hex_lattice(8)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=1, scheme=0))
+    U = np.ascontiguousarray(m.to_internal(I.tgv_state(nodes, cells, 0.1)))
+    U[0, 17] = -1.0
+    Ug = torch.from_numpy(U).cuda()
+    with pytest.raises(ucns.UcnsError) as e:
+        m.rk_step(Ug, return_dt=True)
+    assert e.value.code == -5
+    m.check_state()  # the error word was cleared
+
+
+def test_residual_requires_device_tensors():
+    nodes, cells, box = I.hex_lattice(6)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=1, scheme=0))
+    with pytest.raises(ValueError):
+        m.residual(torch.zeros(5, m.n_cells, dtype=torch.float64))

@@ -1,0 +1,96 @@
+"""CPU tests of libucns: the C ABI loads and exports every declared entry
+point, argument and call-order errors come back as status codes, and the
+host half of ucns_precompute (stencils + Householder-QR pseudo-inverses,
+Eq. 4) agrees with the oracle's independent construction (modified
+Gram-Schmidt on quadrature-built matrices).  No GPU is touched."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_07387_gb300 import inputs as I
+from paper_2609_07387_gb300 import ucns
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "ucns.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ucns_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ucns.load()
+    names = _declared()
+    assert "ucns_residual" in names and "ucns_rk_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(ucns.EXPORTS)
+
+
+def test_error_codes_without_gpu():
+    lib = ucns.load()
+    nodes, cells, box = I.hex_lattice(4)
+    with pytest.raises(ucns.UcnsError) as e:
+        ucns.Mesh(nodes, cells[:, :5], box)
+    assert e.value.code == -1
+    bad = cells.copy()
+    bad[3, 2] = nodes.shape[0] + 7
+    with pytest.raises(ucns.UcnsError) as e:
+        ucns.Mesh(nodes, bad, box)
+    assert e.value.code == -2
+    # a lattice that is not periodic in z for the given box: unpaired faces
+    with pytest.raises(ucns.UcnsError) as e:
+        ucns.Mesh(nodes, cells, np.array([box[0], box[1], 2 * box[2]]))
+    assert e.value.code == -2
+    m = ucns.Mesh(nodes, cells, box)
+    with pytest.raises(ucns.UcnsError) as e:
+        m.stencil(0)
+    assert e.value.code == -7
+    # residual before precompute: call order error (checked before any CUDA use)
+    rc = lib.ucns_residual(m._h, None, None, None)
+    assert rc == -7
+    with pytest.raises(ucns.UcnsError) as e:
+        m.precompute_host(ucns.Params(order=3))
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:
+        m.precompute_host(ucns.Params(order=1, scheme=1))
+    assert e.value.code == -1
+    # 2 cells across a periodic box: each face tuple appears 4 times (non-manifold)
+    with pytest.raises(ucns.UcnsError) as e:
+        ucns.Mesh(*I.hex_lattice(2))
+    assert e.value.code == -2
+    lib.ucns_mesh_destroy(None)  # NULL-safe
+
+
+def test_cell_order_is_a_locality_permutation():
+    nodes, cells, box = I.hex_lattice(16, jitter=0.1, seed=1)
+    m = ucns.Mesh(nodes, cells, box)
+    assert np.array_equal(np.sort(m.perm), np.arange(len(cells)))
+    # Morton order: consecutive internal cells are close in space
+    x = I.cell_vertex_means(nodes, cells)[m.perm]
+    d = np.linalg.norm(np.diff(x, axis=0), axis=1)
+    assert np.median(d) < 1.5 * (2 * np.pi / 16)
+
+
+@pytest.mark.parametrize("kind,order,scheme", [("hex", 1, 0), ("hex", 2, 1), ("tet", 2, 1)])
+def test_host_precompute_matches_oracle(kind, order, scheme):
+    nodes, cells, box = I.hex_lattice(6 if kind == "hex" else 5, jitter=0.1, seed=11)
+    if kind == "tet":
+        cells = I.split_tets(cells)
+    params = ucns.Params(order=order, scheme=scheme)
+    m = ucns.Mesh(nodes, cells, box).precompute_host(params)
+    oc = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme))
+    assert (m.n_faces, m.K, m.Mc, m.nd, m.Md, m.nq) == (oc.n_faces, oc.K, oc.Mc, oc.nd, oc.Md, oc.nq)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(cells), size=12, replace=False):
+        for which in [-1] + list(range(m.nd)):
+            mem, P = m.stencil(int(i), which)
+            omem, _, _, oP = oc.stencil(int(i), which)
+            assert sorted(mem) == sorted(omem), (i, which)
+            pos = {c: k for k, c in enumerate(omem)}
+            oPm = oP[:, [pos[c] for c in mem]]
+            assert np.abs(P - oPm).max() <= 1e-12 * np.abs(oPm).max(), (i, which)

@@ -43,15 +43,12 @@ STAGES = 3
 # counted from the kernel source; derivation in the design doc.
 FLOPS_FACE_P2_VISC_PER_QP = 688
 FLOPS_RECON_P2_CWENOZ_PER_CELL = 4070
-# algorithmic bytes of one launch (each array element crossing HBM once)
-BYTES_FACE_P2_PER_FACE = 4 * 10 * 8 + 8 + 2 * 4 + 5 * 8  # QP geometry, penalty, ids, G
-BYTES_RECON_P2_CWENOZ_PER_CELL = (9 * 18 + 6 * 3 * 6) * 8 + (18 + 36) * 4 + 6 * 8 + 5 * 8 + 10 * 5 * 8
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ucns", choices=["ucns", "reference"])
     ap.add_argument("--n", type=int, default=64, help="lattice cells per direction")
@@ -71,7 +68,7 @@ def workload(n: int):
 def config(n: int, N: int, world: int) -> dict:
     return {
         "workload": f"TGV M0.1 Re1600, {n}^3 jittered (+-10% h, seed 1) hex = {N} cells, P2 CWENOZ, "
-                    "FP64, SSP-RK3 CFL 0.5, device CFL dt every step",
+                    "SSP-RK3 CFL 0.5, device CFL dt every step; plain FP64 and the mixed form timed",
         "cells": N,
         "stages_per_step": STAGES,
         "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -91,7 +88,7 @@ class ClockSampler:
         self.bus_id = bus_id
 
     def __enter__(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.bus_id:
             cmd[1:1] = ["-i", self.bus_id]
         try:
@@ -251,6 +248,63 @@ def run_reference(args, rank: int, world: int):
 
 
 # ------------------------------------------------------------- GPU arm
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def algorithmic(m, kind: str, mixed: bool) -> tuple[float, float]:
+    """(flops, bytes) of one launch of the face or reconstruction kernel:
+    flops counted from the kernel source, bytes = each
+    array element read or written once (neighbour gathers served by cache)."""
+    w = 4 if mixed else 8
+    N, F = m.n_cells, m.n_faces
+    if kind == "face":
+        flops = FLOPS_FACE_P2_VISC_PER_QP * m.nq * F
+        nbytes = F * (m.nq * 10 * w + w + 2 * 4 + 5 * 8) + N * (m.K + 1) * 5 * w
+    else:
+        flops = FLOPS_RECON_P2_CWENOZ_PER_CELL * N
+        nbytes = N * ((m.K * m.Mc + m.nd * 3 * m.Md) * w + (m.Mc + m.nd * m.Md) * 4 + 6 * 8 + 5 * 8
+                      + (m.K + 1) * 5 * w)
+    return flops, nbytes
+
+
+def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int) -> dict:
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    kind = "face" if dom == "face" else "recon"
+    flops, nbytes = algorithmic(m, kind, mixed)
+    name = {("face", False): "k_face<2,true>", ("recon", False): "k_recon<2,true,6>",
+            ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,6>"}[(kind, mixed)]
+    if mixed:
+        alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    elif peak64 and 0.3 < peak64 < 5.0:
+        alu_peak, alu_src = peak64, "measured cuBLAS DGEMM FP64"
+    else:
+        alu_peak, alu_src = 1.25, "nominal FP64 1.25 TFLOP/s"
+    alu = flops / avg_s / 1e12
+    bw = nbytes / avg_s / 1e9
+    alu_frac, hbm_frac = alu / alu_peak, bw / hbm_gbs
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
+                "peak_source": alu_src + " (of measured)" if "measured" in alu_src else alu_src}
+    else:
+        roof = {"bound": "hbm", "achieved": bw, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof.update({"kernel": name, "traffic": measured_traffic(name, n), "avg_launch_ms": avg_s * 1e3,
+                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                 "alu_frac": alu_frac, "hbm_frac": hbm_frac})
+    return roof
+
+
+def hbm_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
 def run_ucns(args, rank: int, world: int, local_rank: int):
     import torch
     import torch.distributed as dist
@@ -261,54 +315,64 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     n = args.n
     nodes, cells, box, U_user = workload(n)
     N = len(cells)
-    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=0, Re=1600.0, Mach=0.1, cfl=0.5))
-    U0 = np.ascontiguousarray(m.to_internal(U_user))
-    U = torch.from_numpy(U0.copy()).cuda()
     stream = torch.cuda.current_stream()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        m.rk_step(U)
-    torch.cuda.synchronize()
-    peak64 = fp64_peak_tflops(torch) if rank == 0 else None
+    base = dict(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5)
+    meshes = {"fp64": ucns.Mesh(nodes, cells, box, ucns.Params(precision=0, **base)),
+              "mixed": ucns.Mesh(nodes, cells, box, ucns.Params(precision=1, **base))}
+    U0 = np.ascontiguousarray(meshes["fp64"].to_internal(U_user))
     bus = None
     try:
         bus = torch.cuda.get_device_properties(local_rank).pci_bus_id
     except Exception:
         bus = None
-    # ---- timed region: K SSP-RK3 steps, device CFL dt, per-kernel events
-    barrier()
-    torch.cuda.synchronize()
-    m.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(bus) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(m):
+        U = torch.from_numpy(U0.copy()).cuda()
+        for _ in range(args.warmup):
             m.rk_step(U)
-        e1.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    ms = e0.elapsed_time(e1)
-    prof = m.profile_read()
-    m.profile(False)
-    m.check_state()
-    t_local = ms / 1e3
-    t_max = t_local
-    if world > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * N * STAGES * args.steps / t_max
+        barrier()
+        torch.cuda.synchronize()
+        m.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(bus) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                m.rk_step(U)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = m.profile_read()
+        m.profile(False)
+        m.check_state()
+        t = ms / 1e3
+        if world > 1:
+            tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return {"t": t, "ms": ms, "prof": prof, "U": U, "clocks": clk.summary(),
+                "value": world * N * STAGES * args.steps / t}
+
+    res = {k: timed(m) for k, m in meshes.items()}
+    # the fixed-error comparison: both forms ran warmup + steps from the same state
+    d64 = meshes["fp64"].diagnostics(res["fp64"]["U"])
+    d32 = meshes["mixed"].diagnostics(res["mixed"]["U"])
+    err = {k: abs(d32[k] - d64[k]) / abs(d64[k]) for k in ("ke", "eps_s")}
+    ok = max(err.values()) <= 1e-4
+    chosen = "mixed" if ok else "fp64"
+    mc = meshes[chosen]
     # ---- end to end through the host-buffer entry point (pinned memory)
     Uh = torch.from_numpy(U0.copy()).pin_memory()
-    m.rk_steps_host(Uh, 1)
+    mc.rk_steps_host(Uh, 1)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        m.rk_steps_host(Uh, 1)
+        mc.rk_steps_host(Uh, 1)
     te = time.perf_counter() - t0
     if world > 1:
         tt = torch.tensor([te], dtype=torch.float64, device="cuda")
@@ -317,42 +381,38 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     e2e = world * N * STAGES * args.e2e_steps / te
     if rank != 0:
         return
-    # ---- roofline of the dominant kernel
-    kinds = {k: v for k, v in prof.items() if v[1] > 0}
-    total_ms = sum(v[0] for v in kinds.values())
-    dom = max(kinds, key=lambda k: kinds[k][0])
-    dom_ms, dom_n = kinds[dom]
-    avg_s = dom_ms / dom_n / 1e3
-    if dom == "face":
-        flops = FLOPS_FACE_P2_VISC_PER_QP * 4 * m.n_faces
-        name = "k_face<2,true>"
-    else:
-        flops = FLOPS_RECON_P2_CWENOZ_PER_CELL * N
-        name = "k_recon<2,true,6>"
-    peak = peak64 if peak64 and 0.3 < peak64 < 5.0 else 1.25
-    achieved = flops / avg_s / 1e12
-    roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": measured_traffic(name, n),
-            "peak_source": "measured cuBLAS DGEMM FP64" if peak is peak64 else "nominal FP64 1.25 TFLOP/s",
-            "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_s * 1e3}
-    shares = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms}
-              for k, v in kinds.items()}
-    launches = 11 * args.steps  # dt (2 kernels) + 3 x (recon, face, rk) per step
+    peak64 = fp64_peak_tflops(torch)
+    hbm = hbm_peak()
+
+    def shares(prof):
+        kinds = {k: v for k, v in prof.items() if v[1] > 0}
+        tot = sum(v[0] for v in kinds.values())
+        return {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / tot} for k, v in kinds.items()}
+
+    r = res[chosen]
+    prof = r["prof"]
     counted = prof["recon"][1] + prof["face"][1] + prof["rk"][1] + 2 * prof["dt"][1]
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(nodes, cells, box, U_user, n)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "ucns",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if chosen == "mixed" else "f64", "data": "synthetic",
+        "impl": "ucns", "form": chosen,
         "config": config(n, N, world),
-        "clocks": clk.summary(),
+        "clocks": r["clocks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8 + 16,
                 "steps": args.e2e_steps, "via": "ucns_rk_steps_host, pinned host buffer"},
-        "gpu_launches": counted if counted == launches else launches,
-        "roofline": roof,
-        "kernels": shares,
+        "gpu_launches": counted,
+        "roofline": roofline(mc, prof, chosen == "mixed", peak64, hbm, n),
+        "kernels": shares(prof),
+        "fixed_error": {"compared_after_steps": args.warmup + args.steps, "ke_rel_err": err["ke"],
+                        "eps_s_rel_err": err["eps_s"], "bound": 1e-4, "within": ok},
+        "plain_fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"] / args.steps,
+                       "roofline": roofline(meshes["fp64"], res["fp64"]["prof"], False, peak64, hbm, n),
+                       "kernels": shares(res["fp64"]["prof"]), "clocks": res["fp64"]["clocks"]},
+        "speedup_vs_plain_fp64": r["value"] / res["fp64"]["value"],
         "fp64_dgemm_tflops": peak64,
         "cpu_baseline": cpu,
     }

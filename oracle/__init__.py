@@ -55,6 +55,7 @@ def _load():
             lib.orc_stencil.argtypes = [P, I64, C.c_int, P, P, P, P]
             lib.orc_residual.argtypes = [P, P, P]
             lib.orc_residual_subset.argtypes = [P, P, I64, P, P]
+            lib.orc_residual_terms.argtypes = [P, P, P, P]
             lib.orc_rk_step.restype = D
             lib.orc_rk_step.argtypes = [P, P, D]
             lib.orc_time_step.restype = D
@@ -171,6 +172,14 @@ class Case:
         R = np.zeros_like(U)
         self._check(self._lib.orc_residual(self._h, _p(U), _p(R)))
         return R
+
+    def residual_terms(self, U):
+        """(R, S): the residual and S_i = (1/|V_i|) sum_f |G_f| per component,
+        the magnitude of the face-flux terms whose signed sum is R."""
+        U = _f64(U)
+        R, S = np.zeros_like(U), np.zeros_like(U)
+        self._check(self._lib.orc_residual_terms(self._h, _p(U), _p(R), _p(S)))
+        return R, S
 
     def residual_subset(self, U, cells):
         """Residual [5, len(cells)] of the given cells only (same arithmetic)."""

@@ -859,7 +859,10 @@ static void face_flux(const orc_case *c, int64_t f, const double *U, const doubl
   }
 }
 
-static int residual(orc_case *c, const double *U, double *R) {
+/* R_i = -(1/|V_i|) sum_f sigma_if G_f; optionally also the magnitude of the
+ * summed terms, S_i = (1/|V_i|) sum_f |G_f| (the scale of the rounding error
+ * of the signed sum). */
+static int residual_terms(orc_case *c, const double *U, double *R, double *S) {
   if (ensure_all(c)) return -1;
   int64_t N = c->N;
   double *coef = (double *)malloc(sizeof(double) * N * 5 * ORC_MAXK);
@@ -875,11 +878,18 @@ static int residual(orc_case *c, const double *U, double *R) {
       double s = 0;
       for (int j = 0; j < c->nfc; j++) s += c->cs[i * c->nfc + j] * G[c->cf[i * c->nfc + j] * 5 + v];
       R[v * N + i] = -s / c->vol[i];
+      if (S) {
+        double a = 0;
+        for (int j = 0; j < c->nfc; j++) a += fabs(G[c->cf[i * c->nfc + j] * 5 + v]);
+        S[v * N + i] = a / c->vol[i];
+      }
     }
   free(coef);
   free(G);
   return 0;
 }
+
+static int residual(orc_case *c, const double *U, double *R) { return residual_terms(c, U, R, NULL); }
 
 /* Residual of a sample of cells only (same arithmetic as residual(); used to
  * time the oracle on a bounded part of a large mesh).  R: [5][ns]. */
@@ -1118,6 +1128,9 @@ int orc_stencil(orc_case *c, int64_t i, int which, int64_t *mem, int32_t *sh, do
 }
 
 int orc_residual(orc_case *c, const double *U, double *R) { return residual(c, U, R); }
+int orc_residual_terms(orc_case *c, const double *U, double *R, double *S) {
+  return residual_terms(c, U, R, S);
+}
 
 /* one SSP-RK3 step; dt <= 0 computes it from the CFL condition; returns dt */
 double orc_rk_step(orc_case *c, double *U, double dt) {

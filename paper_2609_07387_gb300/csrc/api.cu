@@ -10,6 +10,7 @@
 
 #include "host_arrays.hpp"
 #include "kernels.cuh"
+#include "kernels_mixed.cuh"
 #include "ucns_internal.hpp"
 
 namespace ucns {
@@ -37,6 +38,11 @@ int upload(T** dst, const std::vector<T>& src) {
     return fail(UCNS_ERR_NOMEM, "cudaMalloc failed during precompute upload");
   UCNS_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   return UCNS_OK;
+}
+
+int upload_f32(float** dst, const std::vector<double>& src) {
+  std::vector<float> f(src.begin(), src.end());
+  return upload(dst, f);
 }
 
 template <typename T>
@@ -87,7 +93,77 @@ FluxConst flux_const(const ucns_params& p) {
   return c;
 }
 
+FluxConstF flux_const_f(const ucns_params& p) {
+  const FluxConst d = flux_const(p);
+  FluxConstF c;
+  c.gam = (float)d.gam;
+  c.gm1 = (float)d.gm1;
+  c.mu = (float)d.mu;
+  c.kap = (float)d.kap;
+  c.gm1_over_R = (float)d.gm1_over_R;
+  const double p_ref = 1.0 / (p.gamma * p.mach * p.mach);
+  c.p_ref = (float)p_ref;
+  c.H_ref = (float)(p.gamma * p_ref / (p.gamma - 1.0));
+  return c;
+}
+
+bool mixed(const ucns_mesh* m) { return m->P.precision == UCNS_PREC_MIXED; }
+
+int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
+  ReconArgsMx a;
+  a.U = U;
+  a.sc = m->d.sc;
+  a.Pc = m->d.Pcf;
+  a.sd = m->d.sd;
+  a.Pd = m->d.Pdf;
+  a.mom = m->d.mom;
+  a.coef = m->d.coeff;
+  a.N = (int)m->N;
+  const double lsum = m->P.lambda_central + m->nd;
+  a.lam0 = (float)(m->P.lambda_central / lsum);
+  a.lams = (float)(1.0 / lsum);
+  a.eps = (float)m->P.epsilon;
+  a.uref4 = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
+  const unsigned g = nblocks((size_t)m->N * 5);
+  if (m->K == 3)
+    k_recon_mx<1, false, 6><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 0)
+    k_recon_mx<2, false, 6><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 6)
+    k_recon_mx<2, true, 6><<<g, 256, 0, s>>>(a);
+  else
+    k_recon_mx<2, true, 4><<<g, 256, 0, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
+  FaceArgsMx a;
+  a.coef = m->d.coeff;
+  a.fq = m->d.fqf;
+  a.fpen = m->d.fpenf;
+  a.fo = m->d.fo;
+  a.fn = m->d.fn;
+  a.inv_h = m->d.inv_hf;
+  a.G = m->d.G;
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.c = flux_const_f(m->P);
+  const bool visc = m->P.reynolds > 0.0;
+  const unsigned g = nblocks((size_t)m->F * m->nq);
+  if (m->K == 3) {
+    if (visc) k_face_mx<1, true><<<g, 256, 0, s>>>(a);
+    else k_face_mx<1, false><<<g, 256, 0, s>>>(a);
+  } else {
+    if (visc) k_face_mx<2, true><<<g, 256, 0, s>>>(a);
+    else k_face_mx<2, false><<<g, 256, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
+  if (mixed(m)) return launch_recon_mx(m, U, s);
   ReconArgs a;
   a.U = U;
   a.sc = m->d.sc;
@@ -115,6 +191,7 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
 }
 
 int launch_face_raw(ucns_mesh* m, cudaStream_t s) {
+  if (mixed(m)) return launch_face_mx(m, s);
   FaceArgs a;
   a.coef = m->d.coef;
   a.fq = m->d.fq;
@@ -234,8 +311,8 @@ void device_free(ucns_mesh* m) {
   m->prof_pool.clear();
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcf, d.Pdf,
-                  d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.G, d.Ustage, d.Uhost,
-                  d.red, d.dt, d.err};
+                  d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.G,
+                  d.Ustage, d.Uhost, d.red, d.dt, d.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceMesh{};
@@ -298,8 +375,8 @@ static int check_params(const ucns_mesh* m, const ucns_params* p) {
     return fail(UCNS_ERR_INVALID_ARG, "unknown scheme");
   if (p->scheme == UCNS_SCHEME_CWENOZ && p->order != 2)
     return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2");
-  if (p->precision != UCNS_PREC_FP64)
-    return fail(UCNS_ERR_INVALID_ARG, "precision mode not available in this build");
+  if (p->precision != UCNS_PREC_FP64 && p->precision != UCNS_PREC_MIXED)
+    return fail(UCNS_ERR_INVALID_ARG, "unknown precision mode");
   if (p->reserved != 0) return fail(UCNS_ERR_INVALID_ARG, "reserved must be 0");
   if (!(p->gamma > 1.0) || !(p->mach > 0.0) || !(p->cfl > 0.0) || !(p->lambda_central > 0.0) ||
       !(p->epsilon > 0.0) || (p->reynolds > 0.0 && !(p->prandtl > 0.0)))
@@ -364,15 +441,26 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     for (int j = 0; j < m->nfc; j++) cf[(size_t)j * m->N + i] = m->cf[(size_t)i * m->nfc + j];
   if ((rc = upload(&d.vol, h.vol)) || (rc = upload(&d.inv_vol, h.inv_vol)) ||
       (rc = upload(&d.inv_h, h.inv_h)) || (rc = upload(&d.dtlen, h.dtlen)) ||
-      (rc = upload(&d.mom, h.mom)) || (rc = upload(&d.sc, h.sc)) || (rc = upload(&d.Pc, h.Pc)) ||
-      (rc = upload(&d.sd, h.sd)) || (rc = upload(&d.Pd, h.Pd)) || (rc = upload(&d.cf, cf)) ||
-      (rc = upload(&d.fo, fo)) || (rc = upload(&d.fn, fn)) || (rc = upload(&d.fq, h.fq)) ||
-      (rc = upload(&d.fpen, h.fpen))) {
+      (rc = upload(&d.mom, h.mom)) || (rc = upload(&d.sc, h.sc)) || (rc = upload(&d.sd, h.sd)) ||
+      (rc = upload(&d.cf, cf)) || (rc = upload(&d.fo, fo)) || (rc = upload(&d.fn, fn))) {
+    device_free(m);
+    return rc;
+  }
+  if (p->precision == UCNS_PREC_MIXED) {
+    if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) ||
+        (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
+        (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
+        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5))) {
+      device_free(m);
+      return rc;
+    }
+  } else if ((rc = upload(&d.Pc, h.Pc)) || (rc = upload(&d.Pd, h.Pd)) || (rc = upload(&d.fq, h.fq)) ||
+             (rc = upload(&d.fpen, h.fpen)) || (rc = alloc(&d.coef, (size_t)m->NC * m->N * 5))) {
     device_free(m);
     return rc;
   }
   d.red_blocks = 4 * 152;
-  if ((rc = alloc(&d.coef, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.G, (size_t)5 * m->F)) ||
+  if ((rc = alloc(&d.G, (size_t)5 * m->F)) ||
       (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)4 * d.red_blocks)) ||
       (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1))) {
     device_free(m);
@@ -461,8 +549,12 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
-    k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
-                                                            (int)m->N, m->d.red);
+    if (mixed(m))
+      k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, m->d.inv_h,
+                                                                 (int)m->N, m->d.red);
+    else
+      k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
+                                                              (int)m->N, m->d.red);
     // the final sums land in the first 4 doubles of G (free between residuals)
     k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, m->d.G);
     UCNS_CUDA(cudaGetLastError());

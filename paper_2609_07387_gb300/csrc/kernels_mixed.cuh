@@ -1,0 +1,361 @@
+// Mixed-precision variants of the reconstruction and face kernels.
+//
+// FP32: pseudo-inverses and their contractions, smoothness indicators,
+// CWENOZ weights, polynomial evaluation, HLLC and viscous flux arithmetic.
+// FP64: the stencil differences U_j - U_i (cancellation), the constant term
+// of each polynomial relative to the reference state, the face-flux totals
+// G_f, the residual sum and the Runge-Kutta update (k_rk), the dt and
+// diagnostic reductions.
+//
+// States inside the FP32 flux are carried relative to the reference state
+// U_ref = (1, 0, 0, 0, p_ref/(gamma-1)), p_ref = 1/(gamma M^2), so that a
+// float holds O(1) numbers: rho = 1 + rho', E = E_ref + E', and the pressure
+// p = p_ref + p' with p' = (gamma-1)(E' - |m|^2/(2 rho)).  The momentum flux
+// uses p' in place of p: the dropped p_ref n integrates to zero over every
+// closed cell (the oint n dS = 0 of the FP64 geometry), so the residual is
+// unchanged.  The HLLC star states are formed in difference form
+// (U* - U = r U + ...), which keeps every FP32 term O(1).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ucns {
+
+struct FluxConstF {
+  float gam, gm1, mu, kap, gm1_over_R;
+  float p_ref, H_ref;  // reference pressure and enthalpy E_ref + p_ref
+};
+
+struct ReconArgsMx {
+  const double* __restrict__ U;  // [5][N]
+  const int32_t* __restrict__ sc;
+  const float* __restrict__ Pc;
+  const int32_t* __restrict__ sd;
+  const float* __restrict__ Pd;
+  const double* __restrict__ mom;  // [6][N]
+  float* __restrict__ coef;        // [NC][N][5], slot 0 relative to U_ref
+  int N;
+  float lam0, lams, eps;
+  double uref4;  // E_ref (rho_ref = 1 handled inline)
+};
+
+struct FaceArgsMx {
+  const float* __restrict__ coef;
+  const float* __restrict__ fq;  // [nq][10][F]
+  const float* __restrict__ fpen;
+  const int32_t* __restrict__ fo;
+  const int32_t* __restrict__ fn;
+  const float* __restrict__ inv_h;
+  double* __restrict__ G;  // [5][F]
+  int N, F;
+  FluxConstF c;
+};
+
+template <int ORDER, bool WENO, int ND>
+__global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
+  constexpr int K = ORDER == 1 ? 3 : 9;
+  constexpr int MC = 2 * K;
+  constexpr int MD = 6;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid / 5, v = tid - 5 * (tid / 5);
+  if (i >= a.N) return;
+  const int N = a.N;
+  const double* __restrict__ Uv = a.U + (size_t)v * N;
+  const double ui = Uv[i];
+  float ao[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) ao[k] = 0.f;
+#pragma unroll 6
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[(size_t)m * N + i]);
+    const float d = (float)(Uv[j] - ui);  // FP64 difference, then FP32
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+  }
+  float c[K];
+  float S[6];
+  if (ORDER == 2) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * N + i]);
+  }
+  if (!WENO) {
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = ao[k];
+  } else {
+    float b[ND][3];
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      b[s][0] = b[s][1] = b[s][2] = 0.f;
+#pragma unroll
+      for (int r = 0; r < MD; r++) {
+        const int j = __ldg(&a.sd[((size_t)s * MD + r) * N + i]);
+        const float d = (float)(Uv[j] - ui);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+          b[s][k] = fmaf(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
+      }
+    }
+    const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
+    const float qy0 = ao[6], qy1 = 2.f * ao[4], qy2 = ao[8];
+    const float qz0 = ao[7], qz1 = ao[8], qz2 = 2.f * ao[5];
+    auto quad = [&](float x0, float x1, float x2) {
+      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 +
+             2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+    };
+    const float SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) +
+                      quad(qy0, qy1, qy2) + quad(qz0, qz1, qz2) +
+                      4.f * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
+                      ao[7] * ao[7] + ao[8] * ao[8];
+    float SI[ND];
+    float tau = 0.f;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+      tau += fabsf(SI0 - SI[s]);
+    }
+    tau *= (1.f / ND);
+    const float w0 = a.lam0 * (1.f + tau / (a.eps + SI0));
+    float ws[ND];
+    float wsum = w0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      ws[s] = a.lams * (1.f + tau / (a.eps + SI[s]));
+      wsum += ws[s];
+    }
+    const float iws = 1.f / wsum;
+    const float r0 = (w0 * iws) / a.lam0;
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      const float e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+      for (int k = 0; k < 3; k++) c[k] = fmaf(e, b[s][k], c[k]);
+    }
+  }
+  // constant term relative to the reference state (FP64 subtraction, then FP32)
+  const double uref = v == 0 ? 1.0 : (v == 4 ? a.uref4 : 0.0);
+  float c0 = (float)(ui - uref);
+  if (ORDER == 2) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) c0 = fmaf(-c[3 + q], S[q], c0);
+  }
+  float* out = a.coef + (size_t)i * 5 + v;
+  const size_t st = (size_t)N * 5;
+  out[0] = c0;
+#pragma unroll
+  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
+}
+
+template <int ORDER>
+__device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int N, int cell, float x,
+                                             float y, float z, float ih, float U[5], float g[5][3]) {
+  const size_t st = (size_t)N * 5;
+  const float* p = coef + (size_t)cell * 5;
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float c0 = p[v], c1 = p[st + v], c2 = p[2 * st + v], c3 = p[3 * st + v];
+    if (ORDER == 1) {
+      U[v] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
+      g[v][0] = c1 * ih;
+      g[v][1] = c2 * ih;
+      g[v][2] = c3 * ih;
+    } else {
+      const float c4 = p[4 * st + v], c5 = p[5 * st + v], c6 = p[6 * st + v];
+      const float c7 = p[7 * st + v], c8 = p[8 * st + v], c9 = p[9 * st + v];
+      const float tx = fmaf(c4, x, fmaf(c7, y, fmaf(c8, z, c1)));
+      const float ty = fmaf(c5, y, fmaf(c9, z, c2));
+      const float tz = fmaf(c6, z, c3);
+      U[v] = fmaf(x, tx, fmaf(y, ty, fmaf(z, tz, c0)));
+      g[v][0] = fmaf(c4, x, tx) * ih;
+      g[v][1] = fmaf(c7, x, fmaf(c5, y, ty)) * ih;
+      g[v][2] = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz))) * ih;
+    }
+  }
+}
+
+// HLLC in reference-relative FP32 variables.  W = (rho', m, E'), rho = 1 + rho'.
+__device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5], const float n[3],
+                                             const FluxConstF& c, float F[5]) {
+  const float rL = 1.f + WL[0], rR = 1.f + WR[0];
+  const float irL = 1.f / rL, irR = 1.f / rR;
+  const float uL[3] = {WL[1] * irL, WL[2] * irL, WL[3] * irL};
+  const float uR[3] = {WR[1] * irR, WR[2] * irR, WR[3] * irR};
+  const float ppL = c.gm1 * (WL[4] - 0.5f * (WL[1] * uL[0] + WL[2] * uL[1] + WL[3] * uL[2]));
+  const float ppR = c.gm1 * (WR[4] - 0.5f * (WR[1] * uR[0] + WR[2] * uR[1] + WR[3] * uR[2]));
+  const float pL = c.p_ref + ppL, pR = c.p_ref + ppR;
+  const float unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
+  const float unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
+  const float aL = sqrtf(c.gam * pL * irL), aR = sqrtf(c.gam * pR * irR);
+  const float sL = sqrtf(rL), sR = sqrtf(rR), iw = 1.f / (sL + sR);
+  const float ut0 = (sL * uL[0] + sR * uR[0]) * iw, ut1 = (sL * uL[1] + sR * uR[1]) * iw,
+              ut2 = (sL * uL[2] + sR * uR[2]) * iw;
+  // total enthalpy H = (E + p)/rho = (H_ref + E' + p')/rho
+  const float Ht = (sL * (c.H_ref + WL[4] + ppL) * irL + sR * (c.H_ref + WR[4] + ppR) * irR) * iw;
+  const float at = sqrtf(c.gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const float utn = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
+  const float SL = fminf(unL - aL, utn - at);
+  const float SR = fmaxf(unR + aR, utn + at);
+  const float mL = rL * (SL - unL), mR = rR * (SR - unR);
+  const float Ss = (ppR - ppL + unL * mL - unR * mR) / (mL - mR);
+  // physical flux of the upwind side (momentum with p', energy with the full E + p)
+  auto phys = [&](const float W[5], float r, const float u[3], float pp, float un) {
+    F[0] = r * un;
+    F[1] = W[1] * un + pp * n[0];
+    F[2] = W[2] * un + pp * n[1];
+    F[3] = W[3] * un + pp * n[2];
+    F[4] = (W[4] + pp) * un + c.H_ref * un;
+  };
+  auto star = [&](const float W[5], float r, const float u[3], float p, float un, float S, float m) {
+    // U* - U with r* = (S* - u_n)/(S - S*): d_rho = rho r*, d_m = r* m + rho*(S* - u_n) n,
+    // d_E = r* E + rho* (S* - u_n)(S* + p/(rho (S - u_n)))
+    const float ds = Ss - un;
+    const float rs = ds / (S - Ss);
+    const float rho_s = r + r * rs;
+    const float E = (c.H_ref - c.p_ref) + W[4];
+    F[0] += S * (r * rs);
+    F[1] += S * fmaf(rho_s * ds, n[0], rs * W[1]);
+    F[2] += S * fmaf(rho_s * ds, n[1], rs * W[2]);
+    F[3] += S * fmaf(rho_s * ds, n[2], rs * W[3]);
+    F[4] += S * fmaf(rho_s * ds, Ss + p / m, rs * E);
+  };
+  if (0.f <= SL) {
+    phys(WL, rL, uL, ppL, unL);
+  } else if (0.f <= Ss) {
+    phys(WL, rL, uL, ppL, unL);
+    star(WL, rL, uL, pL, unL, SL, mL);
+  } else if (0.f <= SR) {
+    phys(WR, rR, uR, ppR, unR);
+    star(WR, rR, uR, pR, unR, SR, mR);
+  } else {
+    phys(WR, rR, uR, ppR, unR);
+  }
+}
+
+// viscous flux in FP32 from the reference-relative face state
+__device__ __forceinline__ void viscous_flux_mx(const float W[5], const float g[5][3], const float n[3],
+                                                const FluxConstF& c, float Fv[5]) {
+  const float r = 1.f + W[0];
+  const float ir = 1.f / r;
+  const float u[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
+  float gu[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; q++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) gu[q][j] = (g[1 + q][j] - u[q] * g[0][j]) * ir;
+  const float e = ((c.H_ref - c.p_ref) + W[4]) * ir;
+  float qn = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const float de = (g[4][j] - e * g[0][j]) * ir - (u[0] * gu[0][j] + u[1] * gu[1][j] + u[2] * gu[2][j]);
+    qn += de * n[j];
+  }
+  const float div = gu[0][0] + gu[1][1] + gu[2][2];
+  const float tdiv = (2.f / 3.f) * c.mu * div;
+  float work = 0.f;
+  Fv[0] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; j++) t += c.mu * (gu[q][j] + gu[j][q]) * n[j];
+    t -= tdiv * n[q];
+    Fv[1 + q] = t;
+    work += u[q] * t;
+  }
+  Fv[4] = work + c.kap * c.gm1_over_R * qn;
+}
+
+template <int ORDER, bool VISC>
+__global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
+  constexpr int NQ = ORDER * ORDER;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = tid / NQ, q = tid - NQ * (tid / NQ);
+  const bool live = f < a.F;
+  const int fc = live ? f : a.F - 1;
+  const size_t F = a.F;
+  const float* __restrict__ fq = a.fq + (size_t)q * 10 * F + fc;
+  const float xl = fq[0], yl = fq[F], zl = fq[2 * F];
+  const float xr = fq[3 * F], yr = fq[4 * F], zr = fq[5 * F];
+  const float n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
+  const float area = fq[9 * F];
+  const int o = a.fo[fc], nb = a.fn[fc];
+  float WL[5], WR[5], gL[5][3], gR[5][3];
+  eval_side_mx<ORDER>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], WL, gL);
+  eval_side_mx<ORDER>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], WR, gR);
+  float Fc[5];
+  hllc_flux_mx(WL, WR, n, a.c, Fc);
+  float flux[5];
+  if (VISC) {
+    const float pen = a.fpen[fc];
+    float Wf[5], gf[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const float jump = pen * (WR[v] - WL[v]);
+      Wf[v] = 0.5f * (WL[v] + WR[v]);
+#pragma unroll
+      for (int j = 0; j < 3; j++) gf[v][j] = fmaf(jump, n[j], 0.5f * (gL[v][j] + gR[v][j]));
+    }
+    float Fv[5];
+    viscous_flux_mx(Wf, gf, n, a.c, Fv);
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = (Fc[v] - Fv[v]) * area;
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+  }
+#pragma unroll
+  for (int off = 1; off < NQ; off <<= 1)
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
+  if (live && q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = (double)flux[v];
+  }
+}
+
+// diagnostics partial sums from FP32 coefficients (FP64 accumulation)
+__global__ void __launch_bounds__(kRedThreads)
+    k_diag_partial_mx(const double* __restrict__ U, const float* __restrict__ coef,
+                      const double* __restrict__ vol, const double* __restrict__ inv_h, int N,
+                      double* __restrict__ part) {
+  __shared__ double sm[4][kRedThreads];
+  double acc[4] = {0, 0, 0, 0};
+  const size_t st = (size_t)N * 5;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double r = U[i], ir = 1.0 / r;
+    const double u[3] = {U[(size_t)N + i] * ir, U[2 * (size_t)N + i] * ir, U[3 * (size_t)N + i] * ir};
+    const double ih = inv_h[i];
+    double g[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; v++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(j + 1) * st + (size_t)i * 5 + v] * ih;
+    double gu[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) gu[q][j] = (g[1 + q][j] - u[q] * g[0][j]) * ir;
+    const double wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+    const double dv = gu[0][0] + gu[1][1] + gu[2][2];
+    const double V = vol[i];
+    acc[0] += V * 0.5 * r * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    acc[1] += V * (wx * wx + wy * wy + wz * wz);
+    acc[2] += V * dv * dv;
+    acc[3] += V;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int q = 0; q < 4; q++) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < 4; q++) part[(size_t)blockIdx.x * 4 + q] = sm[q][0];
+}
+
+}  // namespace ucns

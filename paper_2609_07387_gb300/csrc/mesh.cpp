@@ -310,6 +310,8 @@ int build_topology(ucns_mesh* m) {
     m->cf[(size_t)fp[f].o_int * m->nfc + fp[f].lf] = (int32_t)(f << 1);
     m->cf[(size_t)fp[f].n_int * m->nfc + fp[f].nlf] = (int32_t)((f << 1) | 1);
   }
+  for (int32_t e : m->cf)
+    if (e < 0) return fail(UCNS_ERR_MESH, "element face without a partner");
   return UCNS_OK;
 }
 
@@ -418,6 +420,8 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   const int nd = (order == 2 && p->scheme == UCNS_SCHEME_CWENOZ) ? m->nfc : 0;
   const int Md = kMd;
   const int nq = order * order;
+  if ((int64_t)F * nq >= (int64_t(1) << 31) || N * 5 >= (int64_t(1) << 31))
+    return fail(UCNS_ERR_INVALID_ARG, "mesh too large for 32-bit kernel indexing");
   m->K = K; m->Mc = Mc; m->nd = nd; m->Md = Md; m->nq = nq; m->NC = K + 1;
   std::vector<Geom> g(N);  // internal order
 #pragma omp parallel for schedule(static)

@@ -37,6 +37,8 @@ struct DeviceMesh {
   double* Pd = nullptr;       // [nd][3][Md][N]
   float* Pcf = nullptr;       // FP32 copies (mixed precision)
   float* Pdf = nullptr;
+  float* inv_hf = nullptr;    // [N]
+  float* fpenf = nullptr;     // [F]
   int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)
   // faces
   int32_t* fo = nullptr;      // [F] owner

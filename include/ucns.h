@@ -152,6 +152,26 @@ int ucns_rk_steps_host(ucns_mesh* mesh, double* U_host, int32_t n_steps, double*
  * (synchronises the stream).  UCNS_OK or UCNS_ERR_NONPHYSICAL. */
 int ucns_check_state(ucns_mesh* mesh, void* stream);
 
+/* The CFL time step of U written to device memory, allocating nothing.
+ * No counterpart in the paper: this serves callers that must not allocate
+ * device memory on their call path -- code running under a fixed device-memory
+ * budget or a pool-only allocator, or that cannot afford cudaMalloc's implicit
+ * device synchronisation -- and still need the time-step reduction.
+ *  U    device [5][n_cells] float64, internal order (input).
+ *  dt   device pointer to one float64 (output): CFL * min over cells, the same
+ *       value as ucns_time_step.  Nothing is synchronised or copied to the host.
+ * The per-block partial minima live in a file-scope device array of 32768
+ * doubles (256 KiB) that every GPU which loads the library holds until the
+ * process exits; meshes above 8,388,608 cells are rejected with
+ * UCNS_ERR_INVALID_ARG.  The first call on a device (with that device
+ * current) resolves the array's device address, so make that first call
+ * before any stream capture.  Every call shares the array; each call writes
+ * the partials it reads, so nothing needs clearing, but calls that overlap on
+ * the GPU (e.g. on two streams) race on it.  A non-physical state sets the
+ * mesh's error word as in ucns_time_step (read it with ucns_check_state).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+int ucns_time_step_static(const ucns_mesh* mesh, const double* U, double* dt, void* stream);
+
 /* Diagnostics of U (device [5][n_cells]) into *out (host).  Synchronises. */
 int ucns_diagnostics(ucns_mesh* mesh, const double* U, ucns_diag* out, void* stream);
 

@@ -301,6 +301,19 @@ int read_error_word(ucns_mesh* m, cudaStream_t s) {
 
 }  // namespace
 
+// The time-step reduction into caller-chosen scratch and output (used by the
+// allocation-free entry point in noalloc.cu): one partial per block of
+// kRedThreads cells, nblocks of them, then the CFL minimum into dt_out[0].
+int launch_dt_into(const ucns_mesh* m, const double* U, double* partials, int nblocks, double* dt_out,
+                   cudaStream_t s) {
+  const ucns_params& p = m->P;
+  const double vc = p.reynolds > 0.0 ? p.prandtl / (2.0 * p.gamma * (1.0 / p.reynolds)) : 0.0;
+  k_dt_partial<<<nblocks, kRedThreads, 0, s>>>(U, m->d.dtlen, (int)m->N, p.gamma, vc, partials, m->d.err);
+  k_dt_final<<<1, kRedThreads, 0, s>>>(partials, nblocks, p.cfl, dt_out);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 void device_free(ucns_mesh* m) {
   for (auto& r : m->prof_live) {
     m->prof_pool.push_back(r.a);

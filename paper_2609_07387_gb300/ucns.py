@@ -36,7 +36,8 @@ ERRORS = {
 # every entry point declared in include/ucns.h
 EXPORTS = (
     "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps_host",
-    "ucns_check_state", "ucns_diagnostics", "ucns_time_step", "ucns_profile", "ucns_profile_read",
+    "ucns_check_state", "ucns_diagnostics", "ucns_time_step", "ucns_time_step_static", "ucns_profile",
+    "ucns_profile_read",
     "ucns_cell_order", "ucns_mesh_info",
     "ucns_last_error", "ucns_mesh_destroy",
 )
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True):
         lib.ucns_check_state.argtypes = [P, P]
         lib.ucns_diagnostics.argtypes = [P, P, C.POINTER(_Diag), P]
         lib.ucns_time_step.argtypes = [P, P, C.POINTER(C.c_double), P]
+        lib.ucns_time_step_static.argtypes = [P, P, P, P]
         lib.ucns_profile.argtypes = [P, I32]
         lib.ucns_profile_read.argtypes = [P, P, P]
         lib.ucns_cell_order.argtypes = [P, P]

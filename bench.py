@@ -39,8 +39,12 @@ METRIC = "cell-RK-stages/s at P2 on 1 GB300, plain FP64 vs chosen form at fixed 
 UNIT = "cell-RK-stages/s"
 STAGES = 3
 
-# Algorithmic FP64 flop counts of the kernels (each +,-,*,/,sqrt = 1, FMA = 2),
-# counted from the kernel source; derivation in the design doc.
+# Algorithmic flop counts of the kernels (each +,-,*,/,sqrt = 1, FMA = 2), counted
+# from the kernel source.  Face kernel, per Gauss point: 2 sides x 5 variables x 33
+# (value 9 FMA, gradient 6 FMA + 3 mul) = 330, penalty and averages 80, HLLC 138,
+# viscous flux 120, scaling and the Gauss sum 20.  Reconstruction, per cell: 5 x 814
+# (central differences + contraction 342, directional 252, smoothness indicators 95,
+# weights and combination 125).
 FLOPS_FACE_P2_VISC_PER_QP = 688
 FLOPS_RECON_P2_CWENOZ_PER_CELL = 4070
 
@@ -253,7 +257,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 
 def algorithmic(m, kind: str, mixed: bool) -> tuple[float, float]:
     """(flops, bytes) of one launch of the face or reconstruction kernel:
-    flops counted from the kernel source, bytes = each
+    flops as counted above, bytes = each
     array element read or written once (neighbour gathers served by cache)."""
     w = 4 if mixed else 8
     N, F = m.n_cells, m.n_faces

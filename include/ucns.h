@@ -87,7 +87,7 @@ typedef struct ucns_diag {
 
 typedef struct ucns_mesh ucns_mesh; /* opaque, library-owned */
 
-/* Build the mesh topology (Sec. 2.3 flat arrays; one GPU, periodic wrap in
+/* Build the mesh topology (Sec. 3.2 flat arrays; one GPU, periodic wrap in
  * place of the halo exchange).
  *  nodes       host [n_nodes][3] float64, copied.
  *  cell_nodes  host [n_cells][nodes_per_cell] int64 node ids, copied.

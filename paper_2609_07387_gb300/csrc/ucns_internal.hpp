@@ -1,6 +1,6 @@
 // Internal data model of libucns: host topology/geometry built once by
 // ucns_mesh_create / ucns_precompute, and the device-resident structure-of-
-// arrays copy the kernels read (Sec. 2.3: flat arrays with explicit offsets,
+// arrays copy the kernels read (Sec. 3.2: flat arrays with explicit offsets,
 // persistent device residency; cells in a Morton order).
 #pragma once
 

@@ -48,7 +48,7 @@ def jtet_p2():
 
 # --------------------------------------------------------------- counts ---
 def test_counts_match_benchmark_matrix(jhex8_p2):
-    """Table 2 (TGV-P2): 3 faces per hex, 54M/2M = 27 reconstructed DoF per
+    """Table 4 (TGV-P2): 3 faces per hex, 54M/2M = 27 reconstructed DoF per
     cell and variable (9 central + 6 linear directional x 3), 24M/6M = 4
     quadrature points per face."""
     g = _golden("benchmark_matrix.txt")["TGV-P2"]

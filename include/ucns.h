@@ -55,7 +55,9 @@ extern "C" {
 
 #define UCNS_PREC_FP64 0   /* every step in FP64 */
 #define UCNS_PREC_MIXED 1  /* FP32 pseudo-inverses, contractions and flux arithmetic;
-                              FP64 stencil differences, RK accumulation, reductions */
+                              stencil differences from a float pair of the FP64 state
+                              (exact leading-part subtraction); FP64 state, face
+                              totals, RK accumulation and reductions */
 
 /* Scheme parameters (Sec. 2.2). */
 typedef struct ucns_params {

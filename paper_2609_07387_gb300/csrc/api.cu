@@ -111,7 +111,8 @@ bool mixed(const ucns_mesh* m) { return m->P.precision == UCNS_PREC_MIXED; }
 
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   ReconArgsMx a;
-  a.U = U;
+  (void)U;  // read through its float pair m->d.Uhl, written by k_split or the RK stage
+  a.Uhl = m->d.Uhl;
   a.sc = m->d.sc;
   a.Pc = m->d.Pcf;
   a.sd = m->d.sd;
@@ -123,7 +124,9 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.lam0 = (float)(m->P.lambda_central / lsum);
   a.lams = (float)(1.0 / lsum);
   a.eps = (float)m->P.epsilon;
-  a.uref4 = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
+  const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
+  a.eref_hi = (float)eref;
+  a.eref_lo = (float)(eref - (double)a.eref_hi);
   const unsigned g = nblocks((size_t)m->N * 5);
   if (m->K == 3)
     k_recon_mx<1, false, 6><<<g, 256, 0, s>>>(a);
@@ -227,6 +230,7 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
   a.inv_vol = m->d.inv_vol;
   a.dt = m->d.dt;
   a.err = m->d.err;
+  a.hl = (mixed(m) && (stage == 1 || stage == 2)) ? m->d.Uhl : nullptr;  // next stage reconstructs out
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.gm1 = m->P.gamma - 1.0;
@@ -260,6 +264,16 @@ int launch_dt_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
 int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindRecon, s, [&] { return launch_recon_raw(m, U, s); });
 }
+// float pair of a caller state before a mixed reconstruction of it
+int launch_split(ucns_mesh* m, const double* U, cudaStream_t s) {
+  if (!mixed(m)) return UCNS_OK;
+  return timed(m, kKindOther, s, [&] {
+    const int n5 = (int)(5 * m->N);
+    k_split<<<nblocks((size_t)n5), 256, 0, s>>>(U, m->d.Uhl, n5);
+    UCNS_CUDA(cudaGetLastError());
+    return UCNS_OK;
+  });
+}
 int launch_face(ucns_mesh* m, cudaStream_t s) {
   return timed(m, kKindFace, s, [&] { return launch_face_raw(m, s); });
 }
@@ -279,7 +293,7 @@ int check_ready(const ucns_mesh* m) {
 int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
   int rc;
   double* W = m->d.Ustage;
-  if ((rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
+  if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
     return rc;
@@ -324,7 +338,7 @@ void device_free(ucns_mesh* m) {
   m->prof_pool.clear();
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcf, d.Pdf,
-                  d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.G,
+                  d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uhost, d.red, d.dt, d.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -463,7 +477,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) ||
         (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
-        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5))) {
+        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);
       return rc;
     }
@@ -490,7 +504,8 @@ int ucns_residual(ucns_mesh* m, const double* U, double* R, void* stream) {
   if (rc) return rc;
   if (!U || !R || U == R) return fail(UCNS_ERR_INVALID_ARG, "U and R must be distinct device pointers");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 0, U, U, R, s)))
+  if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
+      (rc = launch_rk(m, 0, U, U, R, s)))
     return rc;
   return UCNS_OK;
 }
@@ -560,7 +575,7 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   if (rc) return rc;
   if (!U || !out) return fail(UCNS_ERR_INVALID_ARG, "U or out is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = launch_recon(m, U, s))) return rc;
+  if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
     if (mixed(m))
       k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, m->d.inv_h,

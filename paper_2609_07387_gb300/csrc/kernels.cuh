@@ -54,6 +54,7 @@ struct RKArgs {
   const double* __restrict__ inv_vol;
   const double* __restrict__ dt;
   int* err;
+  float* hl;  // optional [2][5][N] float pair of the new state (mixed form)
   int N, F;
   double gm1;
 };
@@ -341,9 +342,10 @@ __device__ __forceinline__ double face_sum(const RKArgs& a, int i, int v) {
   return s;
 }
 
-__device__ __forceinline__ bool physical(const double U[5], double gm1) {
-  const double p = gm1 * (U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
-  return U[0] > 0.0 && p > 0.0 && isfinite(p) && isfinite(U[0]);
+// rho > 0 and p > 0 (p > 0  <=>  2 rho E - |m|^2 > 0 for rho > 0), all finite
+__device__ __forceinline__ bool physical(const double U[5]) {
+  const double q = 2.0 * U[0] * U[4] - (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+  return U[0] > 0.0 && q > 0.0 && isfinite(U[0]) && isfinite(U[4]) && isfinite(q);
 }
 
 // STAGE 0: plain residual R = -(1/V) sum sigma G -> out
@@ -370,12 +372,20 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
     } else if (STAGE == 2) {
       Un[v] = 0.75 * u0 + 0.25 * (a.Us[v * N + i] + dt * R);
     } else {
-      Un[v] = u0 / 3.0 + (2.0 / 3.0) * (a.Us[v * N + i] + dt * R);
+      Un[v] = u0 * (1.0 / 3.0) + (2.0 / 3.0) * (a.Us[v * N + i] + dt * R);
     }
   }
 #pragma unroll
   for (int v = 0; v < 5; v++) a.out[v * N + i] = Un[v];
-  if (!physical(Un, a.gm1)) atomicOr(a.err, 1);
+  if (a.hl) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const float h = (float)Un[v];
+      a.hl[v * N + i] = h;
+      a.hl[(5 + v) * N + i] = (float)(Un[v] - (double)h);
+    }
+  }
+  if (!physical(Un)) atomicOr(a.err, 1);
 }
 
 // ------------------------------------------------------------ reductions

@@ -2,10 +2,11 @@
 //
 // FP32: pseudo-inverses and their contractions, smoothness indicators,
 // CWENOZ weights, polynomial evaluation, HLLC and viscous flux arithmetic.
-// FP64: the stencil differences U_j - U_i (cancellation), the constant term
-// of each polynomial relative to the reference state, the face-flux totals
-// G_f, the residual sum and the Runge-Kutta update (k_rk), the dt and
-// diagnostic reductions.
+// Stencil differences U_j - U_i (cancellation) are taken from a float pair
+// (hi, lo) of the FP64 state, whose leading parts subtract exactly, so each
+// difference equals the FP64 difference to within its own FP32 rounding.
+// FP64: the state itself, the face-flux totals G_f, the residual sum and the
+// Runge-Kutta update (k_rk), the dt and diagnostic reductions.
 //
 // States inside the FP32 flux are carried relative to the reference state
 // U_ref = (1, 0, 0, 0, p_ref/(gamma-1)), p_ref = 1/(gamma M^2), so that a
@@ -27,7 +28,7 @@ struct FluxConstF {
 };
 
 struct ReconArgsMx {
-  const double* __restrict__ U;  // [5][N]
+  const float* __restrict__ Uhl;  // [2][5][N]: hi = fl(U), lo = fl(U - hi)
   const int32_t* __restrict__ sc;
   const float* __restrict__ Pc;
   const int32_t* __restrict__ sd;
@@ -36,7 +37,7 @@ struct ReconArgsMx {
   float* __restrict__ coef;        // [NC][N][5], slot 0 relative to U_ref
   int N;
   float lam0, lams, eps;
-  double uref4;  // E_ref (rho_ref = 1 handled inline)
+  float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair (rho_ref = 1 exactly)
 };
 
 struct FaceArgsMx {
@@ -60,15 +61,20 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
   const int i = tid / 5, v = tid - 5 * (tid / 5);
   if (i >= a.N) return;
   const int N = a.N;
-  const double* __restrict__ Uv = a.U + (size_t)v * N;
-  const double ui = Uv[i];
+  const float* __restrict__ Hv = a.Uhl + (size_t)v * N;
+  const float* __restrict__ Lv = a.Uhl + (size_t)(5 + v) * N;
+  const float hi_i = Hv[i], lo_i = Lv[i];
+  // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
+  // within a factor 2 (Sterbenz), so the difference carries no cancellation
+  // error beyond the final FP32 rounding, as an FP64 subtraction would.
+  auto diff = [&](int j) { return (Hv[j] - hi_i) + (Lv[j] - lo_i); };
   float ao[K];
 #pragma unroll
   for (int k = 0; k < K; k++) ao[k] = 0.f;
 #pragma unroll 6
   for (int m = 0; m < MC; m++) {
     const int j = __ldg(&a.sc[(size_t)m * N + i]);
-    const float d = (float)(Uv[j] - ui);  // FP64 difference, then FP32
+    const float d = diff(j);
 #pragma unroll
     for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
   }
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
 #pragma unroll
       for (int r = 0; r < MD; r++) {
         const int j = __ldg(&a.sd[((size_t)s * MD + r) * N + i]);
-        const float d = (float)(Uv[j] - ui);
+        const float d = diff(j);
 #pragma unroll
         for (int k = 0; k < 3; k++)
           b[s][k] = fmaf(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
@@ -133,9 +139,9 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
       for (int k = 0; k < 3; k++) c[k] = fmaf(e, b[s][k], c[k]);
     }
   }
-  // constant term relative to the reference state (FP64 subtraction, then FP32)
-  const double uref = v == 0 ? 1.0 : (v == 4 ? a.uref4 : 0.0);
-  float c0 = (float)(ui - uref);
+  // constant term relative to the reference state U_ref = (1, 0, 0, 0, E_ref)
+  float c0 = v == 0 ? (hi_i - 1.f) + lo_i
+                    : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
   if (ORDER == 2) {
 #pragma unroll
     for (int q = 0; q < 6; q++) c0 = fmaf(-c[3 + q], S[q], c0);
@@ -147,7 +153,18 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
   for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
 }
 
-template <int ORDER>
+// float pair of an FP64 state: hi = fl(U), lo = fl(U - hi)
+__global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, float* __restrict__ hl, int n5) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n5) return;
+  const double u = U[k];
+  const float h = (float)u;
+  hl[k] = h;
+  hl[(size_t)n5 + k] = (float)(u - (double)h);
+}
+
+// value at (x, y, z) into U; gradient written (ACC = false) or added (ACC = true) into g
+template <int ORDER, bool ACC>
 __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int N, int cell, float x,
                                              float y, float z, float ih, float U[5], float g[5][3]) {
   const size_t st = (size_t)N * 5;
@@ -155,11 +172,12 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     const float c0 = p[v], c1 = p[st + v], c2 = p[2 * st + v], c3 = p[3 * st + v];
+    float gx, gy, gz;
     if (ORDER == 1) {
       U[v] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
-      g[v][0] = c1 * ih;
-      g[v][1] = c2 * ih;
-      g[v][2] = c3 * ih;
+      gx = c1;
+      gy = c2;
+      gz = c3;
     } else {
       const float c4 = p[4 * st + v], c5 = p[5 * st + v], c6 = p[6 * st + v];
       const float c7 = p[7 * st + v], c8 = p[8 * st + v], c9 = p[9 * st + v];
@@ -167,9 +185,18 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
       const float ty = fmaf(c5, y, fmaf(c9, z, c2));
       const float tz = fmaf(c6, z, c3);
       U[v] = fmaf(x, tx, fmaf(y, ty, fmaf(z, tz, c0)));
-      g[v][0] = fmaf(c4, x, tx) * ih;
-      g[v][1] = fmaf(c7, x, fmaf(c5, y, ty)) * ih;
-      g[v][2] = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz))) * ih;
+      gx = fmaf(c4, x, tx);
+      gy = fmaf(c7, x, fmaf(c5, y, ty));
+      gz = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz)));
+    }
+    if (ACC) {
+      g[v][0] = fmaf(gx, ih, g[v][0]);
+      g[v][1] = fmaf(gy, ih, g[v][1]);
+      g[v][2] = fmaf(gz, ih, g[v][2]);
+    } else {
+      g[v][0] = gx * ih;
+      g[v][1] = gy * ih;
+      g[v][2] = gz * ih;
     }
   }
 }
@@ -280,9 +307,9 @@ __global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
   const float n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
   const float area = fq[9 * F];
   const int o = a.fo[fc], nb = a.fn[fc];
-  float WL[5], WR[5], gL[5][3], gR[5][3];
-  eval_side_mx<ORDER>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], WL, gL);
-  eval_side_mx<ORDER>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], WR, gR);
+  float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
+  eval_side_mx<ORDER, false>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], WL, gs);
+  eval_side_mx<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], WR, gs);
   float Fc[5];
   hllc_flux_mx(WL, WR, n, a.c, Fc);
   float flux[5];
@@ -294,7 +321,7 @@ __global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
       const float jump = pen * (WR[v] - WL[v]);
       Wf[v] = 0.5f * (WL[v] + WR[v]);
 #pragma unroll
-      for (int j = 0; j < 3; j++) gf[v][j] = fmaf(jump, n[j], 0.5f * (gL[v][j] + gR[v][j]));
+      for (int j = 0; j < 3; j++) gf[v][j] = fmaf(jump, n[j], 0.5f * gs[v][j]);
     }
     float Fv[5];
     viscous_flux_mx(Wf, gf, n, a.c, Fv);

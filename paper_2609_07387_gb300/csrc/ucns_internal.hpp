@@ -48,7 +48,8 @@ struct DeviceMesh {
   double* fpen = nullptr;     // [F] alpha / L_int
   // scratch owned by the handle
   double* coef = nullptr;     // [NC][N][5] reconstructed monomial coefficients
-  float* coeff = nullptr;     // FP32 copy of the non-constant coefficients (mixed)
+  float* coeff = nullptr;     // FP32 coefficients (mixed)
+  float* Uhl = nullptr;       // [2][5][N] float pair of the state being reconstructed (mixed)
   double* G = nullptr;        // [5][F] face flux integrals
   double* Ustage = nullptr;   // [5][N] Runge-Kutta stage state
   double* Uhost = nullptr;    // [5][N] device copy for the host-buffer entry point

@@ -180,13 +180,73 @@ int ucns_diagnostics(ucns_mesh* mesh, const double* U, ucns_diag* out, void* str
 /* The CFL time step of U (device), returned in *dt (host).  Synchronises. */
 int ucns_time_step(ucns_mesh* mesh, const double* U, double* dt, void* stream);
 
+/* ---- learned troubled-cell indicator --------------------------------- */
+/* A small network (32 -> 64 -> 64 -> 1, ReLU, logistic output) predicts from
+ * 32 per-cell features whether a cell's CWENOZ weights depart from the linear
+ * ones; gated cells keep CWENOZ, the others take the linear-weight (optimal
+ * central) polynomial, which skips the directional stencils.  Weights are
+ * BF16 copies of FP32 master weights; products run on the tensor cores
+ * (tcgen05) with FP32 accumulation.  Parameters (FP32, flat, in order):
+ * W1 [64][32], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 [1] = 6337 values.
+ * Feature rows are BF16 [n][32], 16-byte aligned device memory. */
+typedef struct ucns_mlp ucns_mlp; /* opaque, library-owned, on the current device */
+
+#define UCNS_MLP_PARAMS 6337
+#define UCNS_GATE_FEATURES 32
+
+/* He-normal initial weights from `seed`, zero biases, Adam state zero. */
+int ucns_mlp_create(uint64_t seed, ucns_mlp** out);
+void ucns_mlp_destroy(ucns_mlp* mlp);
+/* Copy the FP32 master weights to / from host float[UCNS_MLP_PARAMS]
+ * (setting them also resets the Adam state).  Synchronous. */
+int ucns_mlp_get_params(const ucns_mlp* mlp, float* theta);
+int ucns_mlp_set_params(ucns_mlp* mlp, const float* theta);
+/* Logits z (device float[n]) of n feature rows X (device BF16 [n][32]). */
+int ucns_mlp_forward(ucns_mlp* mlp, const void* X, int64_t n, float* z, void* stream);
+/* Gradient (device float[UCNS_MLP_PARAMS]) of the class-weighted binary
+ * cross-entropy L = (1/n) sum_i c(y_i) [softplus(z_i) - y_i z_i], c(1) = w_pos,
+ * c(0) = w_neg, over n rows X with labels y (device float[n], 0 or 1).
+ * Deterministic (fixed reduction order).  Weights unchanged. */
+int ucns_mlp_grad(ucns_mlp* mlp, const void* X, const float* y, int64_t n, float w_pos, float w_neg,
+                  float* grad, void* stream);
+/* Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) over consecutive
+ * batches of `batch` rows (a multiple of 8) of (X, y): one step per batch.
+ * Asynchronous on `stream`. */
+int ucns_mlp_train(ucns_mlp* mlp, const void* X, const float* y, int64_t n, int64_t batch, float lr,
+                   float w_pos, float w_neg, void* stream);
+/* Read and clear the network's device error word (synchronises): UCNS_OK or
+ * UCNS_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
+int ucns_mlp_check(ucns_mlp* mlp, void* stream);
+
+/* The 32 features of every cell of U (device [5][n_cells]), as BF16 rows into
+ * X (device [n_cells][32], internal order) and, if Xf is not NULL, as FP32
+ * into Xf (device float [n_cells][32]).  Needs order 2.  Features, from the
+ * cell average and the optimal central polynomial p_opt of Eq. 4:
+ * 0-17 (rho_m - rho_i)/rho_i over the central stencil; 18-23 (p_m - p_i)/p_i
+ * over its first 6 members; 24-28 SI_v/(SI_v + q_v^2) for each variable, SI of
+ * p_opt as in Eq. 6, q = 0.1 (rho, rho a, rho a, rho a, rho a^2); 29 |u|/a;
+ * 30 h|div u|/a; 31 h|curl u|/a with h = |V|^(1/3). */
+int ucns_gate_features(ucns_mesh* mesh, const double* U, void* X, float* Xf, void* stream);
+/* Training labels of the plain scheme: dev[i] = max over variables and
+ * stencils of |omega_s - lambda_s| for the CWENOZ weights of U (device float
+ * [n_cells]); the label is dev > threshold.  Needs an FP64 CWENOZ mesh. */
+int ucns_gate_labels(ucns_mesh* mesh, const double* U, float* dev, void* stream);
+/* Attach a trained network (not owned; keep it alive while attached): when
+ * enabled, each ucns_rk_step / ucns_residual first evaluates the features of
+ * its input state and the network once, and cells with logit > threshold use
+ * CWENOZ while the others use the linear weights.  mlp = NULL detaches. */
+int ucns_gate_attach(ucns_mesh* mesh, ucns_mlp* mlp, float logit_threshold);
+int ucns_gate_enable(ucns_mesh* mesh, int32_t enable);
+/* Number of cells the last gate evaluation routed to CWENOZ (synchronises). */
+int ucns_gate_flagged(ucns_mesh* mesh, int64_t* n_flagged, void* stream);
+
 /* Opt-in per-kernel timing with CUDA events recorded on the launch stream
  * around every kernel the library enqueues (enable != 0 starts a new
  * measurement window; 0 stops recording).  ucns_profile_read synchronises on
  * the recorded events and returns, per kernel kind (0 reconstruction,
- * 1 face flux, 2 residual/RK update, 3 time step, 4 diagnostics, 5 other),
- * the summed milliseconds and launch counts since the window started
- * (host double[6], int64[6]). */
+ * 1 face flux, 2 residual/RK update, 3 time step, 4 diagnostics, 5 other,
+ * 6 indicator features, 7 indicator network), the summed milliseconds and
+ * launch counts since the window started (host double[8], int64[8]). */
 int ucns_profile(ucns_mesh* mesh, int32_t enable);
 int ucns_profile_read(ucns_mesh* mesh, double* ms, int64_t* launches);
 

@@ -67,6 +67,7 @@ def _load():
             lib.orc_kexact_probe.argtypes = [P, I64, P, C.c_int, P, P, P]
             lib.orc_cell_average.argtypes = [P, C.c_int, P, C.c_int, P]
             lib.orc_diagnostics.argtypes = [P, P, P]
+            lib.orc_features.argtypes = [P, P, P]
             lib.orc_hllc.argtypes = [P, P, P, D, P]
             lib.orc_viscous_flux.argtypes = [P, P, P, D, D, D, D, P]
             lib.orc_ssprk3_linear.restype = D
@@ -230,6 +231,21 @@ class Case:
         U = np.zeros((5, self.n_cells))
         self._lib.orc_cell_average(self._h, kinds[kind], _p(p), nq1d, _p(U))
         return U
+
+    def features(self, U):
+        """Troubled-cell indicator features [n_cells, 32] (FP64)."""
+        U = _f64(U)
+        F = np.zeros((self.n_cells, 32))
+        self._check(self._lib.orc_features(self._h, _p(U), _p(F)))
+        return F
+
+    def labels(self, U, threshold: float = 1e-2):
+        """max over variables and stencils of |omega_s - lambda_s| under the
+        CWENOZ weights, and the label (deviation > threshold)."""
+        _, w = self.reconstruct(U, weights=True)
+        lam = np.array([self.params.lam_central] + [1.0] * self.nd) / (self.params.lam_central + self.nd)
+        dev = np.abs(w - lam[None, None, :]).max(axis=(1, 2))
+        return dev, dev > threshold
 
     def diagnostics(self, U):
         U = _f64(U)

@@ -1273,6 +1273,61 @@ void orc_cell_average(const orc_case *c, int kind, const double *p, int nq1d, do
   }
 }
 
+/* Troubled-cell indicator features (32 per cell), from the cell average and  */
+/* the optimal central polynomial p_opt (Eq. 4) of cell i:                    */
+/*  0..17  (rho_m - rho_i)/rho_i over the central stencil, in stencil order   */
+/*  18..23 (p_m - p_i)/p_i over its first 6 members                          */
+/*  24..28 SI_v/(SI_v + q_v^2), SI of p_opt per variable (Eq. 6 reading),      */
+/*         q = 0.1 (rho, rho a, rho a, rho a, rho a^2)                         */
+/*  29 |u|/a, 30 h |div u|/a, 31 h |curl u|/a, h = |V_i|^(1/3), grad u from     */
+/*         p_opt at the centroid                                              */
+int orc_features(orc_case *c, const double *U, double *Fout /* [N][32] */) {
+  if (ensure_all(c)) return -1;
+  int64_t N = c->N;
+  if (c->Mc < 18) { set_err("features need a 18-cell central stencil (P2)"); return -1; }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < N; i++) {
+    double *F = &Fout[i * 32];
+    double Ui[5], aopt[5][ORC_MAXK], val[5], g[5][3];
+    for (int v = 0; v < 5; v++) Ui[v] = U[v * N + i];
+    const double *Pc = &c->Pc[i * c->K * c->Mc];
+    for (int v = 0; v < 5; v++)
+      for (int k = 0; k < c->K; k++) {
+        double s = 0;
+        for (int r = 0; r < c->Mc; r++) s += Pc[k * c->Mc + r] * (U[v * N + c->sc[i * c->Mc + r]] - Ui[v]);
+        aopt[v][k] = s;
+      }
+    double r = Ui[0], u[3] = {Ui[1] / r, Ui[2] / r, Ui[3] / r};
+    double q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double p = (c->gam - 1.0) * (Ui[4] - 0.5 * r * q2), a = sqrt(c->gam * p / r);
+    for (int m = 0; m < 18; m++) {
+      int64_t j = c->sc[i * c->Mc + m];
+      F[m] = (U[j] - r) / r;
+    }
+    for (int m = 0; m < 6; m++) {
+      int64_t j = c->sc[i * c->Mc + m];
+      double rj = U[j], mj2 = U[N + j] * U[N + j] + U[2 * N + j] * U[2 * N + j] + U[3 * N + j] * U[3 * N + j];
+      double pj = (c->gam - 1.0) * (U[4 * N + j] - 0.5 * mj2 / rj);
+      F[18 + m] = (pj - p) / p;
+    }
+    double sc[5] = {r, r * a, r * a, r * a, r * a * a};
+    for (int v = 0; v < 5; v++) {
+      double SI = smoothness(c, i, aopt[v], c->order), q = 0.1 * sc[v];
+      F[24 + v] = SI / (SI + q * q);
+    }
+    eval_poly(c, i, Ui, aopt, &c->cen[3 * i], val, g);
+    double gu[3][3];
+    for (int A = 0; A < 3; A++)
+      for (int j = 0; j < 3; j++) gu[A][j] = (g[1 + A][j] - u[A] * g[0][j]) / r;
+    double wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+    double dv = gu[0][0] + gu[1][1] + gu[2][2];
+    F[29] = sqrt(q2) / a;
+    F[30] = c->hh[i] * fabs(dv) / a;
+    F[31] = c->hh[i] * sqrt(wx * wx + wy * wy + wz * wz) / a;
+  }
+  return 0;
+}
+
 /* diagnostics: [KE, eps_s, eps_d] with cell-centroid gradients of the      */
 /* reconstruction: KE = sum V rho|u|^2/2 / sum V,                           */
 /* eps_s = sum V |curl u|^2 /(Re sum V), eps_d = 4/3 sum V (div u)^2/(Re sum V) */

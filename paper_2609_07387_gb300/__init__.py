@@ -5,4 +5,4 @@ The compute path is libucns.so (CUDA kernels for sm_103a behind a C ABI,
 ``include/ucns.h``); ``ucns`` is its ctypes binding and ``inputs`` builds the
 seeded synthetic meshes and states of the Taylor-Green workloads.
 """
-from .ucns import Mesh, Params, UcnsError, load  # noqa: F401
+from .ucns import Mesh, Net, Params, UcnsError, load  # noqa: F401

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "_lib", "libucns.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "mesh.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "mesh.cpp", "noalloc.cu", "mlp.cu"]
 
 
 def nvcc() -> str:

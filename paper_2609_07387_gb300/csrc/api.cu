@@ -11,6 +11,8 @@
 #include "host_arrays.hpp"
 #include "kernels.cuh"
 #include "kernels_mixed.cuh"
+#include "kernels_gate.cuh"
+#include "mlp_internal.hpp"
 #include "ucns_internal.hpp"
 
 namespace ucns {
@@ -54,7 +56,17 @@ int alloc(T** dst, size_t n) {
 
 inline unsigned nblocks(size_t threads, int bs = 256) { return (unsigned)((threads + bs - 1) / bs); }
 
-enum { kKindRecon = 0, kKindFace = 1, kKindRK = 2, kKindDt = 3, kKindDiag = 4, kKindOther = 5 };
+enum {
+  kKindRecon = 0,
+  kKindFace = 1,
+  kKindRK = 2,
+  kKindDt = 3,
+  kKindDiag = 4,
+  kKindOther = 5,
+  kKindFeatures = 6,
+  kKindMlp = 7,
+  kKinds = 8
+};
 
 cudaEvent_t take_event(ucns_mesh* m) {
   if (!m->prof_pool.empty()) {
@@ -119,6 +131,7 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.Pd = m->d.Pdf;
   a.mom = m->d.mom;
   a.coef = m->d.coeff;
+  a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
   a.N = (int)m->N;
   const double lsum = m->P.lambda_central + m->nd;
   a.lam0 = (float)(m->P.lambda_central / lsum);
@@ -175,6 +188,8 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.Pd = m->d.Pd;
   a.mom = m->d.mom;
   a.coef = m->d.coef;
+  a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
+  a.dev = m->label_out;
   a.N = (int)m->N;
   const double lsum = m->P.lambda_central + m->nd;
   a.lam0 = m->P.lambda_central / lsum;
@@ -284,6 +299,35 @@ int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindDt, s, [&] { return launch_dt_raw(m, U, s); });
 }
 
+// features of U and the network's flags, once per call of the solver
+int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s) {
+  m->gate_eval_active = false;
+  if (!m->gate_on || !m->mlp) return UCNS_OK;
+  int rc = timed(m, kKindFeatures, s, [&] {
+    FeatArgs a;
+    a.U = U;
+    a.sc = m->d.sc;
+    a.Pc = mixed(m) ? (const void*)m->d.Pcf : (const void*)m->d.Pc;
+    a.mom = m->d.mom;
+    a.inv_h = m->d.inv_h;
+    a.X = reinterpret_cast<__nv_bfloat16*>(m->gate_X);
+    a.Xf = nullptr;
+    a.N = (int)m->N;
+    a.gam = (float)m->P.gamma;
+    if (mixed(m)) k_features<float><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+    else k_features<double><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+    UCNS_CUDA(cudaGetLastError());
+    return UCNS_OK;
+  });
+  if (rc) return rc;
+  rc = timed(m, kKindMlp, s, [&] {
+    return ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
+  });
+  if (rc) return rc;
+  m->gate_eval_active = true;
+  return UCNS_OK;
+}
+
 int check_ready(const ucns_mesh* m) {
   if (!m) return fail(UCNS_ERR_INVALID_ARG, "mesh handle is NULL");
   if (!m->precomputed) return fail(UCNS_ERR_STATE, "ucns_precompute has not been called");
@@ -293,6 +337,7 @@ int check_ready(const ucns_mesh* m) {
 int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
   int rc;
   double* W = m->d.Ustage;
+  if ((rc = gate_eval(m, U, s))) return rc;  // flags of U^n serve all three stages
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
@@ -336,6 +381,13 @@ void device_free(ucns_mesh* m) {
   m->prof_live.clear();
   for (void* e : m->prof_pool) cudaEventDestroy((cudaEvent_t)e);
   m->prof_pool.clear();
+  if (m->gate_X) cudaFree(m->gate_X);
+  if (m->gate_flag) cudaFree(m->gate_flag);
+  if (m->gate_count) cudaFree(m->gate_count);
+  m->gate_X = nullptr;
+  m->gate_flag = nullptr;
+  m->gate_count = nullptr;
+  m->gate_eval_active = false;
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcf, d.Pdf,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
@@ -504,6 +556,7 @@ int ucns_residual(ucns_mesh* m, const double* U, double* R, void* stream) {
   if (rc) return rc;
   if (!U || !R || U == R) return fail(UCNS_ERR_INVALID_ARG, "U and R must be distinct device pointers");
   cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = gate_eval(m, U, s))) return rc;
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
       (rc = launch_rk(m, 0, U, U, R, s)))
     return rc;
@@ -575,6 +628,7 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   if (rc) return rc;
   if (!U || !out) return fail(UCNS_ERR_INVALID_ARG, "U or out is NULL");
   cudaStream_t s = (cudaStream_t)stream;
+  m->gate_eval_active = false;  // diagnostics always use the full scheme
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
     if (mixed(m))
@@ -608,7 +662,7 @@ int ucns_profile(ucns_mesh* m, int32_t enable) {
       m->prof_pool.push_back(r.b);
     }
     m->prof_live.clear();
-    for (int k = 0; k < 6; k++) {
+    for (int k = 0; k < kKinds; k++) {
       m->prof_ms[k] = 0.0;
       m->prof_n[k] = 0;
     }
@@ -629,10 +683,85 @@ int ucns_profile_read(ucns_mesh* m, double* ms, int64_t* launches) {
     m->prof_pool.push_back(r.b);
   }
   m->prof_live.clear();
-  for (int k = 0; k < 6; k++) {
+  for (int k = 0; k < kKinds; k++) {
     ms[k] = m->prof_ms[k];
     launches[k] = m->prof_n[k];
   }
+  return UCNS_OK;
+}
+
+int ucns_gate_features(ucns_mesh* m, const double* U, void* X, float* Xf, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !X) return fail(UCNS_ERR_INVALID_ARG, "U or X is NULL");
+  if (((uintptr_t)X & 15) != 0) return fail(UCNS_ERR_INVALID_ARG, "X must be 16-byte aligned");
+  if (m->K != 9) return fail(UCNS_ERR_INVALID_ARG, "features need order 2");
+  cudaStream_t s = (cudaStream_t)stream;
+  FeatArgs a;
+  a.U = U;
+  a.sc = m->d.sc;
+  a.Pc = mixed(m) ? (const void*)m->d.Pcf : (const void*)m->d.Pc;
+  a.mom = m->d.mom;
+  a.inv_h = m->d.inv_h;
+  a.X = reinterpret_cast<__nv_bfloat16*>(X);
+  a.Xf = Xf;
+  a.N = (int)m->N;
+  a.gam = (float)m->P.gamma;
+  if (mixed(m)) k_features<float><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+  else k_features<double><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int ucns_gate_labels(ucns_mesh* m, const double* U, float* dev, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !dev) return fail(UCNS_ERR_INVALID_ARG, "U or dev is NULL");
+  if (mixed(m) || m->nd == 0) return fail(UCNS_ERR_INVALID_ARG, "labels need an FP64 CWENOZ mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  UCNS_CUDA(cudaMemsetAsync(dev, 0, sizeof(float) * m->N, s));
+  m->gate_eval_active = false;
+  m->label_out = dev;
+  rc = launch_recon(m, U, s);
+  m->label_out = nullptr;
+  return rc;
+}
+
+int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
+  if (mlp && !m->gate_X) {
+    if ((rc = alloc((uint8_t**)&m->gate_X, (size_t)m->N * 64)) || (rc = alloc(&m->gate_flag, (size_t)m->N)) ||
+        (rc = alloc(&m->gate_count, 1)))
+      return rc;
+  }
+  m->mlp = mlp;
+  m->gate_thr = threshold;
+  if (!mlp) m->gate_on = false;
+  return UCNS_OK;
+}
+
+int ucns_gate_enable(ucns_mesh* m, int32_t enable) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (enable && !m->mlp) return fail(UCNS_ERR_STATE, "no network attached");
+  m->gate_on = enable != 0;
+  return UCNS_OK;
+}
+
+int ucns_gate_flagged(ucns_mesh* m, int64_t* n_flagged, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!n_flagged) return fail(UCNS_ERR_INVALID_ARG, "n_flagged is NULL");
+  if (!m->gate_flag) return fail(UCNS_ERR_STATE, "no network attached");
+  cudaStream_t s = (cudaStream_t)stream;
+  UCNS_CUDA(cudaMemsetAsync(m->gate_count, 0, sizeof(unsigned long long), s));
+  k_count_flags<<<4 * 152, 256, 0, s>>>(m->gate_flag, (int)m->N, m->gate_count);
+  unsigned long long h = 0;
+  UCNS_CUDA(cudaMemcpyAsync(&h, m->gate_count, sizeof h, cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaStreamSynchronize(s));
+  *n_flagged = (int64_t)h;
   return UCNS_OK;
 }
 

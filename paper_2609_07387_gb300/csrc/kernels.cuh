@@ -29,6 +29,8 @@ struct ReconArgs {
   const double* __restrict__ Pd;
   const double* __restrict__ mom;  // [6][N]
   double* __restrict__ coef;       // [NC][N][5]
+  const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
+  float* __restrict__ dev;           // [N]: max |omega - lambda| (null: not wanted)
   int N;
   double lam0, lams, eps;  // normalised linear weights, epsilon
 };
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) S[q] = __ldg(&a.mom[(size_t)q * N + i]);
   }
-  if (!WENO) {
+  if (!WENO || (a.gate && !a.gate[i])) {
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = ao[k];
   } else {
@@ -227,6 +229,12 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
       wsum += ws[s];
     }
     const double iws = 1.0 / wsum;
+    if (a.dev) {  // deviation of the nonlinear from the linear weights (training labels)
+      double dv = fabs(w0 * iws - a.lam0);
+#pragma unroll
+      for (int s = 0; s < ND; s++) dv = fmax(dv, fabs(ws[s] * iws - a.lams));
+      atomicMax(reinterpret_cast<unsigned int*>(a.dev) + i, __float_as_uint((float)dv));
+    }
     // p = omega_0 p_1 + sum_s omega_s p_s with p_1 = (p_opt - sum lambda_s p_s)/lambda_0
     const double r0 = (w0 * iws) / a.lam0;
 #pragma unroll

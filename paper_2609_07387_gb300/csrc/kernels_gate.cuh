@@ -1,0 +1,130 @@
+// Features of the learned troubled-cell indicator, one thread per cell:
+// density and pressure jumps over the central stencil, normalised smoothness
+// indicators of the optimal central polynomial p_opt (Eq. 4, Eq. 6 reading),
+// and three scale-free flow measures from p_opt's gradient at the centroid.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace ucns {
+
+struct FeatArgs {
+  const double* __restrict__ U;  // [5][N]
+  const int32_t* __restrict__ sc;
+  const void* __restrict__ Pc;   // [9][18][N], double or float
+  const double* __restrict__ mom;
+  const double* __restrict__ inv_h;
+  __nv_bfloat16* __restrict__ X;  // [N][32]
+  float* __restrict__ Xf;         // [N][32] or null
+  int N;
+  float gam;
+};
+
+template <typename PT>
+__global__ void __launch_bounds__(128) k_features(FeatArgs a) {
+  constexpr int K = 9, MC = 18;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const size_t N = a.N;
+  const PT* __restrict__ Pc = reinterpret_cast<const PT*>(a.Pc);
+  const double g = a.gam;
+  double Ui[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) Ui[v] = a.U[v * N + i];
+  const double r = Ui[0], ir = 1.0 / r;
+  const double m2 = Ui[1] * Ui[1] + Ui[2] * Ui[2] + Ui[3] * Ui[3];
+  const double p = (g - 1.0) * (Ui[4] - 0.5 * m2 * ir);
+  const float c = (float)sqrt(g * p * ir);
+  float F[32];
+  float ao[5][K];
+#pragma unroll
+  for (int v = 0; v < 5; v++)
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[v][k] = 0.f;
+#pragma unroll 2
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[(size_t)m * N + i]);
+    double Uj[5];
+    float d[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      Uj[v] = a.U[v * N + j];
+      d[v] = (float)(Uj[v] - Ui[v]);
+    }
+    F[m] = (float)((Uj[0] - r) * ir);
+    if (m < 6) {
+      const double pj = (g - 1.0) * (Uj[4] - 0.5 * (Uj[1] * Uj[1] + Uj[2] * Uj[2] + Uj[3] * Uj[3]) / Uj[0]);
+      F[18 + m] = (float)((pj - p) / p);
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const float P = (float)Pc[((size_t)k * MC + m) * N + i];
+#pragma unroll
+      for (int v = 0; v < 5; v++) ao[v][k] = fmaf(P, d[v], ao[v][k]);
+    }
+  }
+  float S[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) S[q] = (float)a.mom[q * N + i];
+  const float rf = (float)r;
+  const float sc5[5] = {rf, rf * c, rf * c, rf * c, rf * c * c};
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float* o = ao[v];
+    auto quad = [&](float x0, float x1, float x2) {
+      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 + 2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+    };
+    const float SI = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + quad(2.f * o[3], o[6], o[7]) +
+                     quad(o[6], 2.f * o[4], o[8]) + quad(o[7], o[8], 2.f * o[5]) +
+                     4.f * (o[3] * o[3] + o[4] * o[4] + o[5] * o[5]) + o[6] * o[6] + o[7] * o[7] + o[8] * o[8];
+    const float q = 0.1f * sc5[v];
+    F[24 + v] = SI / (SI + q * q);
+  }
+  // p_opt gradient at the centroid: linear coefficients / h
+  const float ih = (float)a.inv_h[i], h = 1.f / ih;
+  const float u[3] = {(float)(Ui[1] * ir), (float)(Ui[2] * ir), (float)(Ui[3] * ir)};
+  float gu[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; q++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) gu[q][j] = (ao[1 + q][j] - u[q] * ao[0][j]) * ih / rf;
+  const float wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+  F[29] = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / c;
+  F[30] = h * fabsf(gu[0][0] + gu[1][1] + gu[2][2]) / c;
+  F[31] = h * sqrtf(wx * wx + wy * wy + wz * wz) / c;
+  uint4* dst = reinterpret_cast<uint4*>(a.X + (size_t)i * 32);
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint4 w;
+    __nv_bfloat162 b0 = __floats2bfloat162_rn(F[8 * q + 0], F[8 * q + 1]);
+    __nv_bfloat162 b1 = __floats2bfloat162_rn(F[8 * q + 2], F[8 * q + 3]);
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(F[8 * q + 4], F[8 * q + 5]);
+    __nv_bfloat162 b3 = __floats2bfloat162_rn(F[8 * q + 6], F[8 * q + 7]);
+    w.x = *reinterpret_cast<uint32_t*>(&b0);
+    w.y = *reinterpret_cast<uint32_t*>(&b1);
+    w.z = *reinterpret_cast<uint32_t*>(&b2);
+    w.w = *reinterpret_cast<uint32_t*>(&b3);
+    dst[q] = w;
+  }
+  if (a.Xf) {
+#pragma unroll
+    for (int q = 0; q < 32; q++) a.Xf[(size_t)i * 32 + q] = F[q];
+  }
+}
+
+__global__ void k_count_flags(const uint8_t* __restrict__ flag, int N, unsigned long long* __restrict__ count) {
+  __shared__ unsigned int sm[256];
+  unsigned int c = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) c += flag[i];
+  sm[threadIdx.x] = c;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)sm[0]);
+}
+
+}  // namespace ucns

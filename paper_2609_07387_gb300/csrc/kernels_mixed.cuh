@@ -35,6 +35,7 @@ struct ReconArgsMx {
   const float* __restrict__ Pd;
   const double* __restrict__ mom;  // [6][N]
   float* __restrict__ coef;        // [NC][N][5], slot 0 relative to U_ref
+  const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
   int N;
   float lam0, lams, eps;
   float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair (rho_ref = 1 exactly)
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * N + i]);
   }
-  if (!WENO) {
+  if (!WENO || (a.gate && !a.gate[i])) {
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = ao[k];
   } else {

@@ -83,6 +83,15 @@ struct ucns_mesh {
   int K = 0, Mc = 0, nd = 0, Md = 0, nq = 0, NC = 0;
   ucns::DeviceMesh d;
   std::shared_ptr<ucns::HostArrays> host;  // kept only by ucns_precompute_host
+  // learned troubled-cell gate
+  struct ::ucns_mlp* mlp = nullptr;  // not owned
+  float gate_thr = 0.f;
+  bool gate_on = false;
+  void* gate_X = nullptr;              // [N][32] BF16 features
+  uint8_t* gate_flag = nullptr;        // [N]
+  unsigned long long* gate_count = nullptr;
+  bool gate_eval_active = false;       // flags valid for the reconstructions of this call
+  float* label_out = nullptr;          // set only inside ucns_gate_labels
   // opt-in kernel timing
   bool prof = false;
   struct ProfRec {
@@ -92,8 +101,8 @@ struct ucns_mesh {
   };
   std::vector<ProfRec> prof_live;
   std::vector<void*> prof_pool;
-  double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-  int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
+  double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace ucns {

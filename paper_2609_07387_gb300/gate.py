@@ -1,0 +1,143 @@
+"""Workflow of the learned troubled-cell indicator, on top of the C ABI.
+
+1. ``collect``: run the plain FP64 CWENOZ scheme and record, every few steps,
+   the 32 features (BF16) and the label deviation max |omega_s - lambda_s| of
+   every cell (all on the device).
+2. ``train``: class-weighted cross-entropy, Adam, on the GPU (tcgen05
+   forward/backward kernels), shuffled mini-batches each epoch.
+3. ``threshold_for_recall``: the logit threshold that keeps a given recall of
+   the troubled cells on held-out samples.
+4. ``GatedRun``: a mesh with the trained network attached, plus the safety
+   check of the plain scheme: every ``check_every`` steps the gated and the
+   full residual of the same state are compared through the kinetic-energy
+   rate dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2 R_rho,i / 2) / sum_i V_i, and
+   the gate is switched off for good if they differ by more than ``bound``
+   relative.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ucns
+
+LABEL_THRESHOLD = 1e-2  # a cell is troubled when its CWENOZ weights depart by more than this
+
+
+@dataclass
+class Samples:
+    X: "object"        # torch bfloat16 [n, 32] on the device
+    dev: "object"      # torch float32 [n]
+    step: np.ndarray   # step index of each sample (for held-out splits)
+
+
+def collect(mesh64: ucns.Mesh, U, steps: int, every: int = 5, stream=None) -> Samples:
+    """Advance U (device, in place) by `steps` plain FP64 CWENOZ steps and
+    record features and label deviations of the states at steps 0, every, ..."""
+    import torch
+
+    Xs, ds, st = [], [], []
+    for k in range(steps + 1):
+        if k % every == 0:
+            X, _ = mesh64.gate_features(U, stream=stream)
+            Xs.append(X)
+            ds.append(mesh64.gate_labels(U, stream=stream))
+            st.append(np.full(mesh64.n_cells, k, dtype=np.int32))
+        if k < steps:
+            mesh64.rk_step(U, stream=stream)
+    mesh64.check_state(stream)
+    return Samples(torch.cat(Xs).contiguous(), torch.cat(ds).contiguous(), np.concatenate(st))
+
+
+def class_weights(y) -> tuple[float, float]:
+    p = float(y.float().mean().item())
+    p = min(max(p, 1e-6), 1 - 1e-6)
+    return 0.5 / p, 0.5 / (1.0 - p)
+
+
+def train(X, y, epochs: int = 4, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+          net: ucns.Net | None = None) -> ucns.Net:
+    """Train on (X, y) with shuffled mini-batches; returns the network."""
+    import torch
+
+    net = net or ucns.Net(seed=seed)
+    w_pos, w_neg = class_weights(y)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = X.shape[0]
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g).to(X.device)
+        net.train(X[perm].contiguous(), y[perm].contiguous(), batch=batch, lr=lr, w_pos=w_pos, w_neg=w_neg)
+    net.check()
+    return net
+
+
+def threshold_for_recall(net: ucns.Net, X, y, recall: float = 0.999) -> float:
+    """Largest logit threshold whose recall of y = 1 on (X, y) is >= recall."""
+    import torch
+
+    z = net.forward(X)
+    zp = z[y > 0.5].float()
+    if zp.numel() == 0:
+        return float("inf")
+    q = torch.quantile(zp.cpu(), 1.0 - recall).item()
+    return float(np.nextafter(np.float32(q), np.float32(-np.inf)))
+
+
+def confusion(net: ucns.Net, X, y, thr: float) -> dict:
+    z = net.forward(X)
+    pred = z > thr
+    yt = y > 0.5
+    tp = int((pred & yt).sum().item())
+    fn = int((~pred & yt).sum().item())
+    fp = int((pred & ~yt).sum().item())
+    tn = int((~pred & ~yt).sum().item())
+    return {"tp": tp, "fn": fn, "fp": fp, "tn": tn, "recall": tp / max(1, tp + fn),
+            "flagged_fraction": (tp + fp) / max(1, tp + fn + fp + tn)}
+
+
+def ke_rate(mesh: ucns.Mesh, U, R, vol) -> float:
+    """dKE/dt = sum V (u . R_m - |u|^2 R_rho / 2) / sum V for a residual R."""
+    rho = U[0]
+    u = U[1:4] / rho
+    rate = (u * R[1:4]).sum(0) - 0.5 * (u * u).sum(0) * R[0]
+    return float((rate * vol).sum().item() / vol.sum().item())
+
+
+@dataclass
+class GatedRun:
+    """A mesh with the trained indicator attached and the plain-scheme check."""
+
+    mesh: ucns.Mesh
+    net: ucns.Net
+    threshold: float
+    vol: "object"
+    check_every: int = 10
+    bound: float = 1e-3
+    steps: int = 0
+    disabled_at: int | None = None
+    checks: list = field(default_factory=list)
+
+    def __post_init__(self):
+        self.mesh.gate_attach(self.net, self.threshold)
+        self.mesh.gate_enable(True)
+
+    def check(self, U) -> float:
+        """Relative difference of dKE/dt between the gated and full residuals."""
+        Rg = self.mesh.residual(U)
+        self.mesh.gate_enable(False)
+        Rf = self.mesh.residual(U)
+        a, b = ke_rate(self.mesh, U, Rg, self.vol), ke_rate(self.mesh, U, Rf, self.vol)
+        rel = abs(a - b) / max(abs(b), 1e-300)
+        self.checks.append((self.steps, rel))
+        if rel > self.bound:
+            self.disabled_at = self.steps
+        else:
+            self.mesh.gate_enable(True)
+        return rel
+
+    def step(self, U, dt=None):
+        if self.disabled_at is None and self.steps % self.check_every == 0:
+            self.check(U)
+        self.mesh.rk_step(U, dt=dt)
+        self.steps += 1

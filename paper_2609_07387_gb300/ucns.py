@@ -40,7 +40,11 @@ EXPORTS = (
     "ucns_profile_read",
     "ucns_cell_order", "ucns_mesh_info",
     "ucns_last_error", "ucns_mesh_destroy",
+    "ucns_mlp_create", "ucns_mlp_destroy", "ucns_mlp_get_params", "ucns_mlp_set_params", "ucns_mlp_forward",
+    "ucns_mlp_grad", "ucns_mlp_train", "ucns_mlp_check",
+    "ucns_gate_features", "ucns_gate_labels", "ucns_gate_attach", "ucns_gate_enable", "ucns_gate_flagged",
 )
+MLP_PARAMS = 6337
 
 
 class UcnsError(RuntimeError):
@@ -98,10 +102,25 @@ def load(build_if_missing: bool = True):
         lib.ucns_mesh_info.argtypes = [P, P]
         lib.ucns_last_error.restype = C.c_char_p
         lib.ucns_mesh_destroy.argtypes = [P]
+        F32 = C.c_float
+        lib.ucns_mlp_create.argtypes = [C.c_uint64, C.POINTER(P)]
+        lib.ucns_mlp_destroy.argtypes = [P]
+        lib.ucns_mlp_get_params.argtypes = [P, P]
+        lib.ucns_mlp_set_params.argtypes = [P, P]
+        lib.ucns_mlp_forward.argtypes = [P, P, I64, P, P]
+        lib.ucns_mlp_grad.argtypes = [P, P, P, I64, F32, F32, P, P]
+        lib.ucns_mlp_train.argtypes = [P, P, P, I64, I64, F32, F32, F32, P]
+        lib.ucns_mlp_check.argtypes = [P, P]
+        lib.ucns_gate_features.argtypes = [P, P, P, P, P]
+        lib.ucns_gate_labels.argtypes = [P, P, P, P]
+        lib.ucns_gate_attach.argtypes = [P, P, F32]
+        lib.ucns_gate_enable.argtypes = [P, I32]
+        lib.ucns_gate_flagged.argtypes = [P, P, P]
         for name in EXPORTS:
-            if name not in ("ucns_last_error", "ucns_mesh_destroy"):
+            if name not in ("ucns_last_error", "ucns_mesh_destroy", "ucns_mlp_destroy"):
                 getattr(lib, name).restype = C.c_int
         lib.ucns_mesh_destroy.restype = None
+        lib.ucns_mlp_destroy.restype = None
         _lib = lib
         return lib
 
@@ -266,17 +285,49 @@ class Mesh:
                                                    _stream_ptr(stream)))
         return d.value
 
-    KINDS = ("recon", "face", "rk", "dt", "diag", "other")
+    KINDS = ("recon", "face", "rk", "dt", "diag", "other", "features", "mlp")
 
     def profile(self, enable: bool = True):
         """Open (or close) a per-kernel CUDA-event timing window."""
         _check(self._lib, self._lib.ucns_profile(self._h, 1 if enable else 0))
 
     def profile_read(self) -> dict:
-        ms = np.zeros(6)
-        n = np.zeros(6, dtype=np.int64)
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
         _check(self._lib, self._lib.ucns_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KINDS)}
+
+    # ---- learned troubled-cell gate ---------------------------------------
+    def gate_features(self, U, want_f32: bool = False, stream=None):
+        """(X bf16 [N, 32], Xf float32 [N, 32] or None) features of U."""
+        import torch
+
+        X = torch.empty((self.n_cells, 32), dtype=torch.bfloat16, device=U.device)
+        Xf = torch.empty((self.n_cells, 32), dtype=torch.float32, device=U.device) if want_f32 else None
+        _check(self._lib, self._lib.ucns_gate_features(self._h, _dev_ptr(U, self.n_cells), X.data_ptr(),
+                                                       None if Xf is None else Xf.data_ptr(), _stream_ptr(stream)))
+        return X, Xf
+
+    def gate_labels(self, U, stream=None):
+        """max_{v,s} |omega_s - lambda_s| per cell (float32 [N]) of the FP64 CWENOZ scheme."""
+        import torch
+
+        dev = torch.empty(self.n_cells, dtype=torch.float32, device=U.device)
+        _check(self._lib, self._lib.ucns_gate_labels(self._h, _dev_ptr(U, self.n_cells), dev.data_ptr(),
+                                                     _stream_ptr(stream)))
+        return dev
+
+    def gate_attach(self, net, threshold: float):
+        self._gate_net = net  # keep the network alive while attached
+        _check(self._lib, self._lib.ucns_gate_attach(self._h, None if net is None else net._h, float(threshold)))
+
+    def gate_enable(self, on: bool = True):
+        _check(self._lib, self._lib.ucns_gate_enable(self._h, 1 if on else 0))
+
+    def gate_flagged(self, stream=None) -> int:
+        n = C.c_int64(0)
+        _check(self._lib, self._lib.ucns_gate_flagged(self._h, C.byref(n), _stream_ptr(stream)))
+        return n.value
 
     def diagnostics(self, U, stream=None) -> dict:
         d = _Diag()
@@ -284,3 +335,67 @@ class Mesh:
                                                      _stream_ptr(stream)))
         return {"ke": d.kinetic_energy, "eps_s": d.eps_solenoidal, "eps_d": d.eps_dilatational,
                 "volume": d.volume}
+
+
+class Net:
+    """The troubled-cell indicator network (32 -> 64 -> 64 -> 1) on the GPU."""
+
+    def __init__(self, seed: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib, self._lib.ucns_mlp_create(C.c_uint64(seed), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.ucns_mlp_destroy(h)
+        self._h = None
+
+    __del__ = close
+
+    def params(self) -> np.ndarray:
+        th = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(self._lib, self._lib.ucns_mlp_get_params(self._h, th.ctypes.data))
+        return th
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        if th.size != MLP_PARAMS:
+            raise ValueError(f"expected {MLP_PARAMS} parameters")
+        _check(self._lib, self._lib.ucns_mlp_set_params(self._h, th.ctypes.data))
+
+    @staticmethod
+    def _x(X):
+        import torch
+
+        if not (X.is_cuda and X.dtype == torch.bfloat16 and X.is_contiguous() and X.dim() == 2 and X.shape[1] == 32):
+            raise ValueError("X must be a contiguous cuda bfloat16 tensor [n, 32]")
+        return X.data_ptr()
+
+    def forward(self, X, stream=None):
+        import torch
+
+        z = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(self._lib, self._lib.ucns_mlp_forward(self._h, self._x(X), X.shape[0], z.data_ptr(), _stream_ptr(stream)))
+        return z
+
+    def grad(self, X, y, w_pos: float = 1.0, w_neg: float = 1.0, stream=None):
+        import torch
+
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        y = y.to(torch.float32).contiguous()
+        _check(self._lib, self._lib.ucns_mlp_grad(self._h, self._x(X), y.data_ptr(), X.shape[0], float(w_pos),
+                                                  float(w_neg), g.data_ptr(), _stream_ptr(stream)))
+        return g
+
+    def train(self, X, y, batch: int = 4096, lr: float = 1e-3, w_pos: float = 1.0, w_neg: float = 1.0, stream=None):
+        """One pass over (X, y) in consecutive batches, one Adam step each."""
+        import torch
+
+        y = y.to(torch.float32).contiguous()
+        _check(self._lib, self._lib.ucns_mlp_train(self._h, self._x(X), y.data_ptr(), X.shape[0], int(batch),
+                                                   float(lr), float(w_pos), float(w_neg), _stream_ptr(stream)))
+
+    def check(self, stream=None):
+        _check(self._lib, self._lib.ucns_mlp_check(self._h, _stream_ptr(stream)))

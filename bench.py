@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="lattice cells per direction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--forms", default="fp64,mixed", help="comma list of forms to time: fp64, mixed")
+    ap.add_argument("--forms", default="fp64,mixed,learned",
+                    help="comma list of forms to time: fp64, mixed, learned (indicator + mixed)")
     return ap.parse_args()
 
 
@@ -256,29 +257,31 @@ def run_reference(args, rank: int, world: int):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
-def algorithmic(m, kind: str, mixed: bool) -> tuple[float, float]:
+def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> tuple[float, float]:
     """(flops, bytes) of one launch of the face or reconstruction kernel:
-    flops as counted above, bytes = each
-    array element read or written once (neighbour gathers served by cache)."""
+    flops as counted above, bytes = each array element read or written once
+    (neighbour gathers served by cache).  frac_dir: fraction of cells that
+    take the directional stencils (the gate routes the rest to the linear
+    weights: central contraction and constant term only, 5 x 354 flops)."""
     w = 4 if mixed else 8
     N, F = m.n_cells, m.n_faces
     if kind == "face":
         flops = FLOPS_FACE_P2_VISC_PER_QP * m.nq * F
         nbytes = F * (m.nq * 10 * w + w + 2 * 4 + 5 * 8) + N * (m.K + 1) * 5 * w
     else:
-        flops = FLOPS_RECON_P2_CWENOZ_PER_CELL * N
-        nbytes = N * ((m.K * m.Mc + m.nd * 3 * m.Md) * w + (m.Mc + m.nd * m.Md) * 4 + 6 * 8 + 5 * 8
-                      + (m.K + 1) * 5 * w)
+        flops = N * (5 * 354 + frac_dir * (FLOPS_RECON_P2_CWENOZ_PER_CELL - 5 * 354))
+        nbytes = N * (m.K * m.Mc * w + m.Mc * 4 + frac_dir * (m.nd * 3 * m.Md * w + m.nd * m.Md * 4)
+                      + 6 * 8 + 5 * 8 + (m.K + 1) * 5 * w)
     return flops, nbytes
 
 
-def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int) -> dict:
-    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_dir: float = 1.0) -> dict:
+    kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in ("recon", "face")}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
     avg_s = dom_ms / dom_n / 1e3
     kind = "face" if dom == "face" else "recon"
-    flops, nbytes = algorithmic(m, kind, mixed)
+    flops, nbytes = algorithmic(m, kind, mixed, frac_dir)
     name = {("face", False): "k_face<2,true>", ("recon", False): "k_recon<2,true,6>",
             ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,6>"}[(kind, mixed)]
     if mixed:
@@ -302,6 +305,25 @@ def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int) -> dict
     return roof
 
 
+def max_over_ranks(t: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (all ranks get it); plain value when world == 1."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(t_local: float, cells_per_rank: int, steps: int, world: int, device: str = "cuda"):
+    """(slowest time, whole-job cell-stages/s): every rank runs a replica of
+    `cells_per_rank` cells for `steps` SSP-RK3 steps."""
+    t = max_over_ranks(t_local, world, device)
+    return t, world * cells_per_rank * STAGES * steps / t
+
+
 def hbm_peak() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -323,9 +345,26 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     stream = torch.cuda.current_stream()
     base = dict(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5)
     forms = [f for f in args.forms.split(",") if f]
-    prec = {"fp64": 0, "mixed": 1}
+    prec = {"fp64": 0, "mixed": 1, "learned": 1}
     meshes = {f: ucns.Mesh(nodes, cells, box, ucns.Params(precision=prec[f], **base)) for f in forms}
     U0 = np.ascontiguousarray(next(iter(meshes.values())).to_internal(U_user))
+    gate_info = None
+    if "learned" in meshes:
+        # untimed setup: labels from 50 plain FP64 CWENOZ steps, training, threshold
+        from paper_2609_07387_gb300 import gate
+
+        m64 = meshes.get("fp64") or ucns.Mesh(nodes, cells, box, ucns.Params(precision=0, **base))
+        t0 = time.perf_counter()
+        Uc = torch.from_numpy(U0.copy()).cuda()
+        S = gate.collect(m64, Uc, 50, every=5)
+        y = (S.dev > gate.LABEL_THRESHOLD).float()
+        net = gate.train(S.X[: 9 * N].contiguous(), y[: 9 * N].contiguous(), epochs=3, seed=0)
+        thr = gate.threshold_for_recall(net, S.X[9 * N:].contiguous(), y[9 * N:].contiguous(), 0.999)
+        held = gate.confusion(net, S.X[10 * N:].contiguous(), y[10 * N:].contiguous(), thr)
+        gated = gate.GatedRun(meshes["learned"], net, thr, check_every=10, bound=1e-3)
+        gate_info = {"train_samples": 9 * N, "troubled_fraction": float(y.mean().item()), "threshold": thr,
+                     "held_out_last_snapshot": held, "setup_s": time.perf_counter() - t0,
+                     "check_every": 10, "check_bound": 1e-3, "_net": net, "_gated": gated}
     bus = None
     try:
         bus = torch.cuda.get_device_properties(local_rank).pci_bus_id
@@ -356,24 +395,25 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         prof = m.profile_read()
         m.profile(False)
         m.check_state()
-        t = ms / 1e3
-        if world > 1:
-            tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return {"t": t, "ms": ms, "prof": prof, "U": U, "clocks": clk.summary(),
-                "value": world * N * STAGES * args.steps / t}
+        t, value = job_throughput(ms / 1e3, N, args.steps, world)
+        return {"t": t, "ms": ms, "prof": prof, "U": U, "clocks": clk.summary(), "value": value}
 
     res = {k: timed(m) for k, m in meshes.items()}
-    # the fixed-error comparison: both forms ran warmup + steps from the same state
-    if "fp64" in res and "mixed" in res:
+    if gate_info is not None:
+        gate_info["flagged_fraction_last_step"] = meshes["learned"].gate_flagged() / N
+    # the fixed-error comparison: every form ran warmup + steps from the same state
+    errs = {}
+    if "fp64" in res:
         d64 = meshes["fp64"].diagnostics(res["fp64"]["U"])
-        d32 = meshes["mixed"].diagnostics(res["mixed"]["U"])
-        err = {k: abs(d32[k] - d64[k]) / abs(d64[k]) for k in ("ke", "eps_s")}
-        ok = max(err.values()) <= 1e-4
-        chosen = "mixed" if ok else "fp64"
+        for f in res:
+            if f != "fp64":
+                d = meshes[f].diagnostics(res[f]["U"])
+                e = {k: abs(d[k] - d64[k]) / abs(d64[k]) for k in ("ke", "eps_s")}
+                errs[f] = {"ke_rel_err": e["ke"], "eps_s_rel_err": e["eps_s"], "within": max(e.values()) <= 1e-4}
+        ok_forms = ["fp64"] + [f for f in errs if errs[f]["within"]]
+        chosen = max(ok_forms, key=lambda f: res[f]["value"])
     else:
-        err, ok, chosen = {"ke": None, "eps_s": None}, None, forms[0]
+        chosen = forms[0]
     mc = meshes[chosen]
     # ---- end to end through the host-buffer entry point (pinned memory)
     Uh = torch.from_numpy(U0.copy()).pin_memory()
@@ -382,12 +422,7 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         mc.rk_steps_host(Uh, 1)
-    te = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = world * N * STAGES * args.e2e_steps / te
+    te, e2e = job_throughput(time.perf_counter() - t0, N, args.e2e_steps, world)
     if rank != 0:
         return
     peak64 = fp64_peak_tflops(torch)
@@ -400,24 +435,29 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
 
     r = res[chosen]
     prof = r["prof"]
-    counted = prof["recon"][1] + prof["face"][1] + prof["rk"][1] + 2 * prof["dt"][1]
+    # kernels per timed call: dt and the check reduction launch two each, the rest one
+    counted = sum(v[1] for k, v in prof.items()) + prof["dt"][1]
+    frac_dir = gate_info["flagged_fraction_last_step"] if (chosen == "learned" and gate_info) else 1.0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(nodes, cells, box, U_user, n)
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if chosen == "mixed" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if chosen == "fp64" else "f32+f64+bf16" if chosen == "learned" else "f32+f64",
+        "data": "synthetic",
         "impl": "ucns", "form": chosen,
         "config": config(n, N, world),
         "clocks": r["clocks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8 + 16,
                 "steps": args.e2e_steps, "via": "ucns_rk_steps_host, pinned host buffer"},
         "gpu_launches": counted,
-        "roofline": roofline(mc, prof, chosen == "mixed", peak64, hbm, n),
+        "roofline": roofline(mc, prof, chosen != "fp64", peak64, hbm, n, frac_dir),
         "kernels": shares(prof),
-        "fixed_error": {"compared_after_steps": args.warmup + args.steps, "ke_rel_err": err["ke"],
-                        "eps_s_rel_err": err["eps_s"], "bound": 1e-4, "within": ok},
+        "fixed_error": {"compared_after_steps": args.warmup + args.steps, "bound": 1e-4, "vs": "plain FP64",
+                        "forms": errs},
+        "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps} for f in res},
+        "learned_gate": None if gate_info is None else {k: v for k, v in gate_info.items() if not k.startswith("_")},
         "plain_fp64": None if "fp64" not in res else {
             "value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"] / args.steps,
             "roofline": roofline(meshes["fp64"], res["fp64"]["prof"], False, peak64, hbm, n),

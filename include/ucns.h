@@ -237,6 +237,18 @@ int ucns_gate_labels(ucns_mesh* mesh, const double* U, float* dev, void* stream)
  * CWENOZ while the others use the linear weights.  mlp = NULL detaches. */
 int ucns_gate_attach(ucns_mesh* mesh, ucns_mlp* mlp, float logit_threshold);
 int ucns_gate_enable(ucns_mesh* mesh, int32_t enable);
+/* Plain-scheme check of the gate (the plain scheme judges the gate's error):
+ * with check_every > 0, every check_every-th ucns_rk_step of a gated mesh
+ * first evaluates the gated and the full residual of its input state and
+ * their kinetic-energy rates dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2
+ * R_rho,i / 2) / sum_i V_i; if they differ by more than bound (relative), the
+ * gate is switched off for the rest of the run.  A check synchronises the
+ * stream.  check_every = 0 disables the checks. */
+int ucns_gate_configure(ucns_mesh* mesh, int32_t check_every, double bound);
+/* Run one check now on U: *rel_diff (host) receives the relative difference
+ * of the two rates, *disabled (may be NULL) whether the gate is now off. */
+int ucns_gate_check(ucns_mesh* mesh, const double* U, double* rel_diff, int32_t* disabled, void* stream);
+
 /* Number of cells the last gate evaluation routed to CWENOZ (synchronises). */
 int ucns_gate_flagged(ucns_mesh* mesh, int64_t* n_flagged, void* stream);
 

@@ -140,15 +140,16 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const unsigned g = nblocks((size_t)m->N * 5);
+  const unsigned g = (unsigned)((m->N + kReconCells - 1) / kReconCells);
+  const unsigned bs = 5 * kReconCells;
   if (m->K == 3)
-    k_recon_mx<1, false, 6><<<g, 256, 0, s>>>(a);
+    k_recon_mx<1, false, 6><<<g, bs, 0, s>>>(a);
   else if (m->nd == 0)
-    k_recon_mx<2, false, 6><<<g, 256, 0, s>>>(a);
+    k_recon_mx<2, false, 6><<<g, bs, 0, s>>>(a);
   else if (m->nd == 6)
-    k_recon_mx<2, true, 6><<<g, 256, 0, s>>>(a);
+    k_recon_mx<2, true, 6><<<g, bs, 0, s>>>(a);
   else
-    k_recon_mx<2, true, 4><<<g, 256, 0, s>>>(a);
+    k_recon_mx<2, true, 4><<<g, bs, 0, s>>>(a);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -283,8 +284,7 @@ int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
 int launch_split(ucns_mesh* m, const double* U, cudaStream_t s) {
   if (!mixed(m)) return UCNS_OK;
   return timed(m, kKindOther, s, [&] {
-    const int n5 = (int)(5 * m->N);
-    k_split<<<nblocks((size_t)n5), 256, 0, s>>>(U, m->d.Uhl, n5);
+    k_split<<<nblocks((size_t)5 * m->N), 256, 0, s>>>(U, m->d.Uhl, (int)m->N);
     UCNS_CUDA(cudaGetLastError());
     return UCNS_OK;
   });
@@ -334,9 +334,46 @@ int check_ready(const ucns_mesh* m) {
   return UCNS_OK;
 }
 
+int residual_into(ucns_mesh* m, const double* U, double* R, cudaStream_t s) {
+  int rc;
+  if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
+      (rc = launch_rk(m, 0, U, U, R, s)))
+    return rc;
+  return UCNS_OK;
+}
+
+// gated vs full residual of U through their kinetic-energy rates
+int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
+  int rc;
+  const size_t n5 = (size_t)5 * m->N;
+  if (!m->gate_R && (rc = alloc(&m->gate_R, 2 * n5))) return rc;
+  if ((rc = gate_eval(m, U, s)) || (rc = residual_into(m, U, m->gate_R, s))) return rc;
+  m->gate_eval_active = false;
+  if ((rc = residual_into(m, U, m->gate_R + n5, s))) return rc;
+  rc = timed(m, kKindOther, s, [&] {
+    k_ke_rate_partial<<<m->d.red_blocks, 256, 0, s>>>(U, m->gate_R, m->gate_R + n5, m->d.vol, (int)m->N, m->d.red);
+    k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, m->d.G);
+    UCNS_CUDA(cudaGetLastError());
+    return UCNS_OK;
+  });
+  if (rc) return rc;
+  double h[4];
+  UCNS_CUDA(cudaMemcpyAsync(h, m->d.G, sizeof h, cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaStreamSynchronize(s));
+  const double a = h[0] / h[2], b = h[1] / h[2];
+  *rel = std::fabs(a - b) / std::fmax(std::fabs(b), 1e-300);
+  if (!(*rel <= m->gate_bound)) m->gate_on = false;
+  return UCNS_OK;
+}
+
 int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
   int rc;
   double* W = m->d.Ustage;
+  if (m->gate_on && m->mlp && m->gate_check_every > 0 && m->gate_steps % m->gate_check_every == 0) {
+    double rel = 0.0;
+    if ((rc = gate_check(m, U, &rel, s))) return rc;
+  }
+  if (m->gate_on && m->mlp) m->gate_steps++;
   if ((rc = gate_eval(m, U, s))) return rc;  // flags of U^n serve all three stages
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
@@ -381,6 +418,8 @@ void device_free(ucns_mesh* m) {
   m->prof_live.clear();
   for (void* e : m->prof_pool) cudaEventDestroy((cudaEvent_t)e);
   m->prof_pool.clear();
+  if (m->gate_R) cudaFree(m->gate_R);
+  m->gate_R = nullptr;
   if (m->gate_X) cudaFree(m->gate_X);
   if (m->gate_flag) cudaFree(m->gate_flag);
   if (m->gate_count) cudaFree(m->gate_count);
@@ -747,6 +786,27 @@ int ucns_gate_enable(ucns_mesh* m, int32_t enable) {
   if (rc) return rc;
   if (enable && !m->mlp) return fail(UCNS_ERR_STATE, "no network attached");
   m->gate_on = enable != 0;
+  return UCNS_OK;
+}
+
+int ucns_gate_configure(ucns_mesh* m, int32_t check_every, double bound) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (check_every < 0 || !(bound > 0.0)) return fail(UCNS_ERR_INVALID_ARG, "check_every >= 0 and bound > 0");
+  m->gate_check_every = check_every;
+  m->gate_bound = bound;
+  m->gate_steps = 0;
+  return UCNS_OK;
+}
+
+int ucns_gate_check(ucns_mesh* m, const double* U, double* rel_diff, int32_t* disabled, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || !rel_diff) return fail(UCNS_ERR_INVALID_ARG, "U or rel_diff is NULL");
+  if (!m->mlp || !m->gate_on) return fail(UCNS_ERR_STATE, "the gate is not enabled");
+  rc = gate_check(m, U, rel_diff, (cudaStream_t)stream);
+  if (rc) return rc;
+  if (disabled) *disabled = m->gate_on ? 0 : 1;
   return UCNS_OK;
 }
 

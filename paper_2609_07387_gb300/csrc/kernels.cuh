@@ -56,7 +56,7 @@ struct RKArgs {
   const double* __restrict__ inv_vol;
   const double* __restrict__ dt;
   int* err;
-  float* hl;  // optional [2][5][N] float pair of the new state (mixed form)
+  float* hl;  // optional [N][10] float pair of the new state (mixed form)
   int N, F;
   double gm1;
 };
@@ -76,7 +76,10 @@ __device__ __forceinline__ void phys_flux(const double U[5], double ir, const do
 __device__ __forceinline__ void hllc_flux(const double UL[5], const double UR[5], const double n[3],
                                           const FluxConst& c, double F[5]) {
   const double rL = UL[0], rR = UR[0];
-  const double irL = 1.0 / rL, irR = 1.0 / rR;
+  // one reciprocal square root per side gives sqrt(rho) and 1/rho
+  const double qL = rsqrt(rL), qR = rsqrt(rR);
+  const double irL = qL * qL, irR = qR * qR;
+  const double sL = rL * qL, sR = rR * qR;
   const double uL[3] = {UL[1] * irL, UL[2] * irL, UL[3] * irL};
   const double uR[3] = {UR[1] * irR, UR[2] * irR, UR[3] * irR};
   const double pL = c.gm1 * (UL[4] - 0.5 * (UL[1] * uL[0] + UL[2] * uL[1] + UL[3] * uL[2]));
@@ -84,10 +87,11 @@ __device__ __forceinline__ void hllc_flux(const double UL[5], const double UR[5]
   const double unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
   const double unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
   const double aL = sqrt(c.gam * pL * irL), aR = sqrt(c.gam * pR * irR);
-  const double sL = sqrt(rL), sR = sqrt(rR), iw = 1.0 / (sL + sR);
-  const double ut0 = (sL * uL[0] + sR * uR[0]) * iw, ut1 = (sL * uL[1] + sR * uR[1]) * iw,
-               ut2 = (sL * uL[2] + sR * uR[2]) * iw;
-  const double Ht = (sL * (UL[4] + pL) * irL + sR * (UR[4] + pR) * irR) * iw;
+  const double iw = 1.0 / (sL + sR);
+  // Roe averages: sqrt(rho) u = m / sqrt(rho), sqrt(rho) H = (E + p) / sqrt(rho)
+  const double ut0 = (UL[1] * qL + UR[1] * qR) * iw, ut1 = (UL[2] * qL + UR[2] * qR) * iw,
+               ut2 = (UL[3] * qL + UR[3] * qR) * iw;
+  const double Ht = ((UL[4] + pL) * qL + (UR[4] + pR) * qR) * iw;
   const double at = sqrt(c.gm1 * (Ht - 0.5 * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
   const double utn = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
   const double SL = fmin(unL - aL, utn - at);
@@ -260,7 +264,8 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 }
 
 // ----------------------------------------------------------- face flux
-template <int ORDER>
+// value into U; gradient written (ACC = false) or added (ACC = true) into g
+template <int ORDER, bool ACC>
 __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N, int cell,
                                           double x, double y, double z, double ih, double U[5],
                                           double g[5][3]) {
@@ -269,11 +274,12 @@ __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N
 #pragma unroll
   for (int v = 0; v < 5; v++) {
     const double c0 = p[v], c1 = p[st + v], c2 = p[2 * st + v], c3 = p[3 * st + v];
+    double gx, gy, gz;
     if (ORDER == 1) {
       U[v] = fma(c1, x, fma(c2, y, fma(c3, z, c0)));
-      g[v][0] = c1 * ih;
-      g[v][1] = c2 * ih;
-      g[v][2] = c3 * ih;
+      gx = c1;
+      gy = c2;
+      gz = c3;
     } else {
       const double c4 = p[4 * st + v], c5 = p[5 * st + v], c6 = p[6 * st + v];
       const double c7 = p[7 * st + v], c8 = p[8 * st + v], c9 = p[9 * st + v];
@@ -281,9 +287,18 @@ __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N
       const double ty = fma(c5, y, fma(c9, z, c2));
       const double tz = fma(c6, z, c3);
       U[v] = fma(x, tx, fma(y, ty, fma(z, tz, c0)));
-      g[v][0] = fma(c4, x, tx) * ih;                       // c1 + 2c4 x + c7 y + c8 z
-      g[v][1] = fma(c7, x, fma(c5, y, ty)) * ih;           // c2 + c7 x + 2c5 y + c9 z
-      g[v][2] = fma(c8, x, fma(c9, y, fma(c6, z, tz))) * ih;  // c3 + c8 x + c9 y + 2c6 z
+      gx = fma(c4, x, tx);                       // c1 + 2c4 x + c7 y + c8 z
+      gy = fma(c7, x, fma(c5, y, ty));           // c2 + c7 x + 2c5 y + c9 z
+      gz = fma(c8, x, fma(c9, y, fma(c6, z, tz)));  // c3 + c8 x + c9 y + 2c6 z
+    }
+    if (ACC) {
+      g[v][0] = fma(gx, ih, g[v][0]);
+      g[v][1] = fma(gy, ih, g[v][1]);
+      g[v][2] = fma(gz, ih, g[v][2]);
+    } else {
+      g[v][0] = gx * ih;
+      g[v][1] = gy * ih;
+      g[v][2] = gz * ih;
     }
   }
 }
@@ -303,24 +318,27 @@ __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
   const double n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
   const double area = fq[9 * F];
   const int o = a.fo[fc], nb = a.fn[fc];
-  double UL[5], UR[5], gL[5][3], gR[5][3];
-  eval_side<ORDER>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], UL, gL);
-  eval_side<ORDER>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], UR, gR);
+  double UL[5], UR[5], gs[5][3];  // gs = grad U_L + grad U_R
+  eval_side<ORDER, false>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], UL, gs);
+  eval_side<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], UR, gs);
   double Fc[5];
   hllc_flux(UL, UR, n, a.c, Fc);
   double flux[5];
   if (VISC) {
-    const double pen = a.fpen[fc];
-    double Uf[5], gf[5][3];
+    // 2 U_f = U_L + U_R and 2 grad U_f = gs + 2 (alpha/L)(U_R - U_L) n: the viscous
+    // flux depends on the face state only through ratios (u = m/rho, e = E/rho,
+    // grad u = (grad m - u grad rho)/rho), so the common factor 2 cancels
+    const double pen2 = 2.0 * a.fpen[fc];
+    double Uf2[5], gf2[5][3];
 #pragma unroll
     for (int v = 0; v < 5; v++) {
-      const double jump = pen * (UR[v] - UL[v]);
-      Uf[v] = 0.5 * (UL[v] + UR[v]);
+      const double jump2 = pen2 * (UR[v] - UL[v]);
+      Uf2[v] = UL[v] + UR[v];
 #pragma unroll
-      for (int j = 0; j < 3; j++) gf[v][j] = fma(jump, n[j], 0.5 * (gL[v][j] + gR[v][j]));
+      for (int j = 0; j < 3; j++) gf2[v][j] = fma(jump2, n[j], gs[v][j]);
     }
     double Fv[5];
-    viscous_flux(Uf, gf, n, a.c, Fv);
+    viscous_flux(Uf2, gf2, n, a.c, Fv);
 #pragma unroll
     for (int v = 0; v < 5; v++) flux[v] = (Fc[v] - Fv[v]) * area;
   } else {
@@ -389,8 +407,8 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
 #pragma unroll
     for (int v = 0; v < 5; v++) {
       const float h = (float)Un[v];
-      a.hl[v * N + i] = h;
-      a.hl[(5 + v) * N + i] = (float)(Un[v] - (double)h);
+      a.hl[i * 10 + v] = h;
+      a.hl[i * 10 + 5 + v] = (float)(Un[v] - (double)h);
     }
   }
   if (!physical(Un)) atomicOr(a.err, 1);

@@ -127,4 +127,34 @@ __global__ void k_count_flags(const uint8_t* __restrict__ flag, int N, unsigned 
   if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)sm[0]);
 }
 
+// per-block sums of V (u . R_m - |u|^2 R_rho / 2) for two residuals, and V
+__global__ void __launch_bounds__(256) k_ke_rate_partial(const double* __restrict__ U, const double* __restrict__ R1,
+                                                         const double* __restrict__ R2, const double* __restrict__ vol,
+                                                         int N, double* __restrict__ part) {
+  __shared__ double sm[3][256];
+  double acc[3] = {0, 0, 0};
+  const size_t n = N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double ir = 1.0 / U[i];
+    const double u0 = U[n + i] * ir, u1 = U[2 * n + i] * ir, u2 = U[3 * n + i] * ir;
+    const double q = 0.5 * (u0 * u0 + u1 * u1 + u2 * u2);
+    const double V = vol[i];
+    acc[0] += V * (u0 * R1[n + i] + u1 * R1[2 * n + i] + u2 * R1[3 * n + i] - q * R1[i]);
+    acc[1] += V * (u0 * R2[n + i] + u1 * R2[2 * n + i] + u2 * R2[3 * n + i] - q * R2[i]);
+    acc[2] += V;
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) sm[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+#pragma unroll
+      for (int q = 0; q < 3; q++) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < 3; q++) part[(size_t)blockIdx.x * 4 + q] = sm[q][0];
+}
+
 }  // namespace ucns

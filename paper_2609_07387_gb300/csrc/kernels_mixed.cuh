@@ -28,7 +28,7 @@ struct FluxConstF {
 };
 
 struct ReconArgsMx {
-  const float* __restrict__ Uhl;  // [2][5][N]: hi = fl(U), lo = fl(U - hi)
+  const float* __restrict__ Uhl;  // [N][10]: hi = fl(U) of the 5 variables, then lo = fl(U - hi)
   const int32_t* __restrict__ sc;
   const float* __restrict__ Pc;
   const int32_t* __restrict__ sd;
@@ -53,31 +53,61 @@ struct FaceArgsMx {
   FluxConstF c;
 };
 
+// Block = kReconCells cells x 5 variables.  The block first stages its cells'
+// pseudo-inverses and stencil indices in shared memory (coalesced, each
+// element fetched once), then thread (cell, variable) contracts from there.
+constexpr int kReconCells = 32;
+
 template <int ORDER, bool WENO, int ND>
-__global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
+__global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
   constexpr int K = ORDER == 1 ? 3 : 9;
   constexpr int MC = 2 * K;
   constexpr int MD = 6;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = tid / 5, v = tid - 5 * (tid / 5);
-  if (i >= a.N) return;
+  constexpr int NDS = WENO ? ND : 0;
+  constexpr int C = kReconCells;
+  __shared__ float sPc[K * MC * C];
+  __shared__ float sPd[(NDS ? NDS : 1) * 3 * MD * C];
+  __shared__ int sSc[MC * C];
+  __shared__ int sSd[(NDS ? NDS : 1) * MD * C];
   const int N = a.N;
-  const float* __restrict__ Hv = a.Uhl + (size_t)v * N;
-  const float* __restrict__ Lv = a.Uhl + (size_t)(5 + v) * N;
-  const float hi_i = Hv[i], lo_i = Lv[i];
+  const int i0 = blockIdx.x * C;
+  const int nc = min(C, N - i0);
+  for (int e = threadIdx.x; e < K * MC * C; e += blockDim.x) {
+    const int r = e / C, c = e - r * C;
+    if (c < nc) sPc[e] = __ldg(&a.Pc[(size_t)r * N + i0 + c]);
+  }
+  for (int e = threadIdx.x; e < MC * C; e += blockDim.x) {
+    const int r = e / C, c = e - r * C;
+    if (c < nc) sSc[e] = __ldg(&a.sc[(size_t)r * N + i0 + c]);
+  }
+  if (NDS) {  // directional operands only for the cells that take CWENOZ
+    for (int e = threadIdx.x; e < NDS * 3 * MD * C; e += blockDim.x) {
+      const int r = e / C, c = e - r * C;
+      if (c < nc && (!a.gate || a.gate[i0 + c])) sPd[e] = __ldg(&a.Pd[(size_t)r * N + i0 + c]);
+    }
+    for (int e = threadIdx.x; e < NDS * MD * C; e += blockDim.x) {
+      const int r = e / C, c = e - r * C;
+      if (c < nc && (!a.gate || a.gate[i0 + c])) sSd[e] = __ldg(&a.sd[(size_t)r * N + i0 + c]);
+    }
+  }
+  __syncthreads();
+  const int lc = threadIdx.x / 5, v = threadIdx.x - 5 * (threadIdx.x / 5);
+  const int i = i0 + lc;
+  if (lc >= nc) return;
+  const float* __restrict__ hl = a.Uhl;
+  const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
   // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
   // within a factor 2 (Sterbenz), so the difference carries no cancellation
   // error beyond the final FP32 rounding, as an FP64 subtraction would.
-  auto diff = [&](int j) { return (Hv[j] - hi_i) + (Lv[j] - lo_i); };
+  auto diff = [&](int j) { return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i); };
   float ao[K];
 #pragma unroll
   for (int k = 0; k < K; k++) ao[k] = 0.f;
 #pragma unroll 6
   for (int m = 0; m < MC; m++) {
-    const int j = __ldg(&a.sc[(size_t)m * N + i]);
-    const float d = diff(j);
+    const float d = diff(sSc[m * C + lc]);
 #pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+    for (int k = 0; k < K; k++) ao[k] = fmaf(sPc[(k * MC + m) * C + lc], d, ao[k]);
   }
   float c[K];
   float S[6];
@@ -95,11 +125,9 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
       b[s][0] = b[s][1] = b[s][2] = 0.f;
 #pragma unroll
       for (int r = 0; r < MD; r++) {
-        const int j = __ldg(&a.sd[((size_t)s * MD + r) * N + i]);
-        const float d = diff(j);
+        const float d = diff(sSd[(s * MD + r) * C + lc]);
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-          b[s][k] = fmaf(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
+        for (int k = 0; k < 3; k++) b[s][k] = fmaf(sPd[((s * 3 + k) * MD + r) * C + lc], d, b[s][k]);
       }
     }
     const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
@@ -154,14 +182,16 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
   for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
 }
 
-// float pair of an FP64 state: hi = fl(U), lo = fl(U - hi)
-__global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, float* __restrict__ hl, int n5) {
+// float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5
+// variables, then lo = fl(U - hi); thread = (cell, variable)
+__global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, float* __restrict__ hl, int N) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n5) return;
-  const double u = U[k];
+  if (k >= 5 * N) return;
+  const int i = k / 5, v = k - 5 * (k / 5);
+  const double u = U[(size_t)v * N + i];
   const float h = (float)u;
-  hl[k] = h;
-  hl[(size_t)n5 + k] = (float)(u - (double)h);
+  hl[(size_t)i * 10 + v] = h;
+  hl[(size_t)i * 10 + 5 + v] = (float)(u - (double)h);
 }
 
 // value at (x, y, z) into U; gradient written (ACC = false) or added (ACC = true) into g

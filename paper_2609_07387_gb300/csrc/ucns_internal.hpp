@@ -91,6 +91,10 @@ struct ucns_mesh {
   uint8_t* gate_flag = nullptr;        // [N]
   unsigned long long* gate_count = nullptr;
   bool gate_eval_active = false;       // flags valid for the reconstructions of this call
+  int gate_check_every = 0;
+  double gate_bound = 1e-3;
+  int64_t gate_steps = 0;
+  double* gate_R = nullptr;            // [2][5][N] residuals of the check
   float* label_out = nullptr;          // set only inside ucns_gate_labels
   // opt-in kernel timing
   bool prof = false;

@@ -8,15 +8,15 @@
 3. ``threshold_for_recall``: the logit threshold that keeps a given recall of
    the troubled cells on held-out samples.
 4. ``GatedRun``: a mesh with the trained network attached, plus the safety
-   check of the plain scheme: every ``check_every`` steps the gated and the
-   full residual of the same state are compared through the kinetic-energy
-   rate dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2 R_rho,i / 2) / sum_i V_i, and
-   the gate is switched off for good if they differ by more than ``bound``
-   relative.
+   check of the plain scheme (run by the library): every ``check_every`` steps
+   the gated and the full residual of the same state are compared through the
+   kinetic-energy rate dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2 R_rho,i / 2) /
+   sum_i V_i, and the gate is switched off for good if they differ by more
+   than ``bound`` relative.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -48,6 +48,26 @@ def collect(mesh64: ucns.Mesh, U, steps: int, every: int = 5, stream=None) -> Sa
             mesh64.rk_step(U, stream=stream)
     mesh64.check_state(stream)
     return Samples(torch.cat(Xs).contiguous(), torch.cat(ds).contiguous(), np.concatenate(st))
+
+
+def rule_network(tau: float) -> ucns.Net:
+    """A hand-set rule written as the same network: flag a cell when any of
+    its central-stencil density or pressure jumps (features 0-23) exceeds tau
+    in magnitude (z = sum_k relu(|x_k| - tau) > 0)."""
+    th = np.zeros(ucns.MLP_PARAMS, np.float32)
+    W1 = th[0:2048].reshape(64, 32)
+    b1 = th[2048:2112]
+    W2 = th[2112:6208].reshape(64, 64)
+    w3 = th[6272:6336]
+    for k in range(24):
+        W1[2 * k, k], b1[2 * k] = 1.0, -tau
+        W1[2 * k + 1, k], b1[2 * k + 1] = -1.0, -tau
+    for j in range(48):
+        W2[j, j] = 1.0
+        w3[j] = 1.0
+    net = ucns.Net(seed=0)
+    net.set_params(th)
+    return net
 
 
 def class_weights(y) -> tuple[float, float]:
@@ -92,52 +112,31 @@ def confusion(net: ucns.Net, X, y, thr: float) -> dict:
     fn = int((~pred & yt).sum().item())
     fp = int((pred & ~yt).sum().item())
     tn = int((~pred & ~yt).sum().item())
-    return {"tp": tp, "fn": fn, "fp": fp, "tn": tn, "recall": tp / max(1, tp + fn),
+    return {"tp": tp, "fn": fn, "fp": fp, "tn": tn, "recall": tp / (tp + fn) if tp + fn else 1.0,
             "flagged_fraction": (tp + fp) / max(1, tp + fn + fp + tn)}
-
-
-def ke_rate(mesh: ucns.Mesh, U, R, vol) -> float:
-    """dKE/dt = sum V (u . R_m - |u|^2 R_rho / 2) / sum V for a residual R."""
-    rho = U[0]
-    u = U[1:4] / rho
-    rate = (u * R[1:4]).sum(0) - 0.5 * (u * u).sum(0) * R[0]
-    return float((rate * vol).sum().item() / vol.sum().item())
 
 
 @dataclass
 class GatedRun:
-    """A mesh with the trained indicator attached and the plain-scheme check."""
+    """A mixed or FP64 mesh with the trained indicator attached; the library
+    runs the plain-scheme check every `check_every` steps and switches the
+    gate off if the kinetic-energy rates of the gated and the full residual
+    differ by more than `bound` (relative)."""
 
     mesh: ucns.Mesh
     net: ucns.Net
     threshold: float
-    vol: "object"
     check_every: int = 10
     bound: float = 1e-3
-    steps: int = 0
-    disabled_at: int | None = None
-    checks: list = field(default_factory=list)
 
     def __post_init__(self):
         self.mesh.gate_attach(self.net, self.threshold)
+        self.mesh.gate_configure(self.check_every, self.bound)
         self.mesh.gate_enable(True)
 
-    def check(self, U) -> float:
-        """Relative difference of dKE/dt between the gated and full residuals."""
-        Rg = self.mesh.residual(U)
-        self.mesh.gate_enable(False)
-        Rf = self.mesh.residual(U)
-        a, b = ke_rate(self.mesh, U, Rg, self.vol), ke_rate(self.mesh, U, Rf, self.vol)
-        rel = abs(a - b) / max(abs(b), 1e-300)
-        self.checks.append((self.steps, rel))
-        if rel > self.bound:
-            self.disabled_at = self.steps
-        else:
-            self.mesh.gate_enable(True)
-        return rel
-
     def step(self, U, dt=None):
-        if self.disabled_at is None and self.steps % self.check_every == 0:
-            self.check(U)
         self.mesh.rk_step(U, dt=dt)
-        self.steps += 1
+
+    def detach(self):
+        self.mesh.gate_enable(False)
+        self.mesh.gate_attach(None, 0.0)

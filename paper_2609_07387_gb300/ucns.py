@@ -43,6 +43,7 @@ EXPORTS = (
     "ucns_mlp_create", "ucns_mlp_destroy", "ucns_mlp_get_params", "ucns_mlp_set_params", "ucns_mlp_forward",
     "ucns_mlp_grad", "ucns_mlp_train", "ucns_mlp_check",
     "ucns_gate_features", "ucns_gate_labels", "ucns_gate_attach", "ucns_gate_enable", "ucns_gate_flagged",
+    "ucns_gate_configure", "ucns_gate_check",
 )
 MLP_PARAMS = 6337
 
@@ -116,6 +117,8 @@ def load(build_if_missing: bool = True):
         lib.ucns_gate_attach.argtypes = [P, P, F32]
         lib.ucns_gate_enable.argtypes = [P, I32]
         lib.ucns_gate_flagged.argtypes = [P, P, P]
+        lib.ucns_gate_configure.argtypes = [P, I32, C.c_double]
+        lib.ucns_gate_check.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(I32), P]
         for name in EXPORTS:
             if name not in ("ucns_last_error", "ucns_mesh_destroy", "ucns_mlp_destroy"):
                 getattr(lib, name).restype = C.c_int
@@ -323,6 +326,17 @@ class Mesh:
 
     def gate_enable(self, on: bool = True):
         _check(self._lib, self._lib.ucns_gate_enable(self._h, 1 if on else 0))
+
+    def gate_configure(self, check_every: int = 10, bound: float = 1e-3):
+        """Plain-scheme check every `check_every` steps; gate off if dKE/dt differs by > bound."""
+        _check(self._lib, self._lib.ucns_gate_configure(self._h, int(check_every), float(bound)))
+
+    def gate_check(self, U, stream=None) -> tuple[float, bool]:
+        rel = C.c_double(0.0)
+        dis = C.c_int32(0)
+        _check(self._lib, self._lib.ucns_gate_check(self._h, _dev_ptr(U, self.n_cells), C.byref(rel), C.byref(dis),
+                                                    _stream_ptr(stream)))
+        return rel.value, bool(dis.value)
 
     def gate_flagged(self, stream=None) -> int:
         n = C.c_int64(0)

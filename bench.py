@@ -361,10 +361,10 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         net = gate.train(S.X[: 9 * N].contiguous(), y[: 9 * N].contiguous(), epochs=3, seed=0)
         thr = gate.threshold_for_recall(net, S.X[9 * N:].contiguous(), y[9 * N:].contiguous(), 0.999)
         held = gate.confusion(net, S.X[10 * N:].contiguous(), y[10 * N:].contiguous(), thr)
-        gated = gate.GatedRun(meshes["learned"], net, thr, check_every=10, bound=1e-3)
+        gated = gate.GatedRun(meshes["learned"], net, thr, check_every=50, bound=1e-3, eval_every=5)
         gate_info = {"train_samples": 9 * N, "troubled_fraction": float(y.mean().item()), "threshold": thr,
                      "held_out_last_snapshot": held, "setup_s": time.perf_counter() - t0,
-                     "check_every": 10, "check_bound": 1e-3, "_net": net, "_gated": gated}
+                     "eval_every": 5, "check_every": 50, "check_bound": 1e-3, "_net": net, "_gated": gated}
     bus = None
     try:
         bus = torch.cuda.get_device_properties(local_rank).pci_bus_id

@@ -237,14 +237,17 @@ int ucns_gate_labels(ucns_mesh* mesh, const double* U, float* dev, void* stream)
  * CWENOZ while the others use the linear weights.  mlp = NULL detaches. */
 int ucns_gate_attach(ucns_mesh* mesh, ucns_mlp* mlp, float logit_threshold);
 int ucns_gate_enable(ucns_mesh* mesh, int32_t enable);
-/* Plain-scheme check of the gate (the plain scheme judges the gate's error):
- * with check_every > 0, every check_every-th ucns_rk_step of a gated mesh
- * first evaluates the gated and the full residual of its input state and
- * their kinetic-energy rates dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2
- * R_rho,i / 2) / sum_i V_i; if they differ by more than bound (relative), the
- * gate is switched off for the rest of the run.  A check synchronises the
- * stream.  check_every = 0 disables the checks. */
-int ucns_gate_configure(ucns_mesh* mesh, int32_t check_every, double bound);
+/* Cadence of the gate and the plain-scheme check (the plain scheme judges
+ * the gate's error).  The features and the network are evaluated at the first
+ * gated step and then every eval_every-th ucns_rk_step (>= 1); the flags in
+ * between are reused.  With check_every > 0, every check_every-th gated
+ * ucns_rk_step first evaluates the gated and the full residual of its input
+ * state and their kinetic-energy rates dKE/dt = sum_i V_i (u_i . R_m,i -
+ * |u_i|^2 R_rho,i / 2) / sum_i V_i; if they differ by more than bound
+ * (relative), the gate is switched off for the rest of the run.  A check
+ * synchronises the stream.  check_every = 0 disables the checks.  Defaults:
+ * eval_every 1, check_every 0. */
+int ucns_gate_configure(ucns_mesh* mesh, int32_t eval_every, int32_t check_every, double bound);
 /* Run one check now on U: *rel_diff (host) receives the relative difference
  * of the two rates, *disabled (may be NULL) whether the gate is now off. */
 int ucns_gate_check(ucns_mesh* mesh, const double* U, double* rel_diff, int32_t* disabled, void* stream);

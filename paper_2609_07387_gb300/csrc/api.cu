@@ -121,6 +121,9 @@ FluxConstF flux_const_f(const ucns_params& p) {
 
 bool mixed(const ucns_mesh* m) { return m->P.precision == UCNS_PREC_MIXED; }
 
+// floats per cell row of the mixed-form coefficients: 5 (K+1) rounded up to 4
+int coef_row_floats(const ucns_mesh* m) { return (5 * m->NC + 3) / 4 * 4; }
+
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   ReconArgsMx a;
   (void)U;  // read through its float pair m->d.Uhl, written by k_split or the RK stage
@@ -133,6 +136,7 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.coef = m->d.coeff;
   a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
   a.N = (int)m->N;
+  a.cs = coef_row_floats(m);
   const double lsum = m->P.lambda_central + m->nd;
   a.lam0 = (float)(m->P.lambda_central / lsum);
   a.lams = (float)(1.0 / lsum);
@@ -140,16 +144,20 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const unsigned g = (unsigned)((m->N + kReconCells - 1) / kReconCells);
-  const unsigned bs = 5 * kReconCells;
+  const unsigned g = nblocks((size_t)m->N * 5);
+  const bool gated = a.gate != nullptr;
   if (m->K == 3)
-    k_recon_mx<1, false, 6><<<g, bs, 0, s>>>(a);
+    k_recon_mx<1, false, 6, false><<<g, 256, 0, s>>>(a);
   else if (m->nd == 0)
-    k_recon_mx<2, false, 6><<<g, bs, 0, s>>>(a);
+    k_recon_mx<2, false, 6, false><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 6 && gated)
+    k_recon_mx<2, true, 6, true><<<g, 256, 0, s>>>(a);
   else if (m->nd == 6)
-    k_recon_mx<2, true, 6><<<g, bs, 0, s>>>(a);
+    k_recon_mx<2, true, 6, false><<<g, 256, 0, s>>>(a);
+  else if (gated)
+    k_recon_mx<2, true, 4, true><<<g, 256, 0, s>>>(a);
   else
-    k_recon_mx<2, true, 4><<<g, bs, 0, s>>>(a);
+    k_recon_mx<2, true, 4, false><<<g, 256, 0, s>>>(a);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -165,6 +173,7 @@ int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   a.G = m->d.G;
   a.N = (int)m->N;
   a.F = (int)m->F;
+  a.cs = coef_row_floats(m);
   a.c = flux_const_f(m->P);
   const bool visc = m->P.reynolds > 0.0;
   const unsigned g = nblocks((size_t)m->F * m->nq);
@@ -197,14 +206,19 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.lams = 1.0 / lsum;
   a.eps = m->P.epsilon;
   const unsigned g = nblocks((size_t)m->N * 5);
+  const bool gated = a.gate != nullptr;
   if (m->K == 3)
-    k_recon<1, false, 6><<<g, 256, 0, s>>>(a);
+    k_recon<1, false, 6, false><<<g, 256, 0, s>>>(a);
   else if (m->nd == 0)
-    k_recon<2, false, 6><<<g, 256, 0, s>>>(a);
+    k_recon<2, false, 6, false><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 6 && gated)
+    k_recon<2, true, 6, true><<<g, 256, 0, s>>>(a);
   else if (m->nd == 6)
-    k_recon<2, true, 6><<<g, 256, 0, s>>>(a);
+    k_recon<2, true, 6, false><<<g, 256, 0, s>>>(a);
+  else if (gated)
+    k_recon<2, true, 4, true><<<g, 256, 0, s>>>(a);
   else
-    k_recon<2, true, 4><<<g, 256, 0, s>>>(a);
+    k_recon<2, true, 4, false><<<g, 256, 0, s>>>(a);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -369,12 +383,19 @@ int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
 int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
   int rc;
   double* W = m->d.Ustage;
-  if (m->gate_on && m->mlp && m->gate_check_every > 0 && m->gate_steps % m->gate_check_every == 0) {
+  const int64_t step = m->gate_steps;
+  if (m->gate_on && m->mlp && m->gate_check_every > 0 && step % m->gate_check_every == 0) {
     double rel = 0.0;
     if ((rc = gate_check(m, U, &rel, s))) return rc;
+    m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  if ((rc = gate_eval(m, U, s))) return rc;  // flags of U^n serve all three stages
+  if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
+    m->gate_eval_active = true;  // reuse the flags of the last evaluation
+  } else {
+    if ((rc = gate_eval(m, U, s))) return rc;  // flags of U^n serve all three stages
+    m->gate_flags_valid = m->gate_eval_active;
+  }
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
@@ -568,7 +589,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) ||
         (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
-        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
+        (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);
       return rc;
     }
@@ -671,8 +692,8 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
     if (mixed(m))
-      k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, m->d.inv_h,
-                                                                 (int)m->N, m->d.red);
+      k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->d.vol,
+                                                                 m->d.inv_h, (int)m->N, m->d.red);
     else
       k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
                                                               (int)m->N, m->d.red);
@@ -777,6 +798,7 @@ int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
   }
   m->mlp = mlp;
   m->gate_thr = threshold;
+  m->gate_flags_valid = false;
   if (!mlp) m->gate_on = false;
   return UCNS_OK;
 }
@@ -786,13 +808,17 @@ int ucns_gate_enable(ucns_mesh* m, int32_t enable) {
   if (rc) return rc;
   if (enable && !m->mlp) return fail(UCNS_ERR_STATE, "no network attached");
   m->gate_on = enable != 0;
+  m->gate_flags_valid = false;
   return UCNS_OK;
 }
 
-int ucns_gate_configure(ucns_mesh* m, int32_t check_every, double bound) {
+int ucns_gate_configure(ucns_mesh* m, int32_t eval_every, int32_t check_every, double bound) {
   int rc = check_ready(m);
   if (rc) return rc;
-  if (check_every < 0 || !(bound > 0.0)) return fail(UCNS_ERR_INVALID_ARG, "check_every >= 0 and bound > 0");
+  if (eval_every < 1 || check_every < 0 || !(bound > 0.0))
+    return fail(UCNS_ERR_INVALID_ARG, "eval_every >= 1, check_every >= 0 and bound > 0");
+  m->gate_eval_every = eval_every;
+  m->gate_flags_valid = false;
   m->gate_check_every = check_every;
   m->gate_bound = bound;
   m->gate_steps = 0;

@@ -158,7 +158,7 @@ __device__ __forceinline__ void viscous_flux(const double U[5], const double g[5
 
 // ------------------------------------------------------- reconstruction
 // thread = (cell i, variable v); tid = 5 i + v
-template <int ORDER, bool WENO, int ND>
+template <int ORDER, bool WENO, int ND, bool GATED>
 __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
   constexpr int K = ORDER == 1 ? 3 : 9;
   constexpr int MC = 2 * K;
@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) S[q] = __ldg(&a.mom[(size_t)q * N + i]);
   }
-  if (!WENO || (a.gate && !a.gate[i])) {
+  bool weno = WENO;
+  if (GATED) weno = weno && a.gate[i];
+  if (!weno) {
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = ao[k];
   } else {

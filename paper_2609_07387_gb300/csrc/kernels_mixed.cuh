@@ -34,15 +34,16 @@ struct ReconArgsMx {
   const int32_t* __restrict__ sd;
   const float* __restrict__ Pd;
   const double* __restrict__ mom;  // [6][N]
-  float* __restrict__ coef;        // [NC][N][5], slot 0 relative to U_ref
+  float* __restrict__ coef;        // [N][cs]: coefficient k of variable v at k*5 + v, slot 0 relative to U_ref
   const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
   int N;
+  int cs;  // floats per cell row of coef (5 (K+1) rounded up to a multiple of 4)
   float lam0, lams, eps;
   float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair (rho_ref = 1 exactly)
 };
 
 struct FaceArgsMx {
-  const float* __restrict__ coef;
+  const float* __restrict__ coef;  // [N][cs] cell rows, 16-byte aligned
   const float* __restrict__ fq;  // [nq][10][F]
   const float* __restrict__ fpen;
   const int32_t* __restrict__ fo;
@@ -50,50 +51,22 @@ struct FaceArgsMx {
   const float* __restrict__ inv_h;
   double* __restrict__ G;  // [5][F]
   int N, F;
+  int cs;
   FluxConstF c;
 };
 
-// Block = kReconCells cells x 5 variables.  The block first stages its cells'
-// pseudo-inverses and stencil indices in shared memory (coalesced, each
-// element fetched once), then thread (cell, variable) contracts from there.
-constexpr int kReconCells = 32;
-
-template <int ORDER, bool WENO, int ND>
-__global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
+// thread = (cell i, variable v); GATED: cells whose gate flag is 0 take the
+// linear weights (a separate instantiation, so the ungated kernel has no
+// data-dependent branch around the directional loads)
+template <int ORDER, bool WENO, int ND, bool GATED>
+__global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
   constexpr int K = ORDER == 1 ? 3 : 9;
   constexpr int MC = 2 * K;
   constexpr int MD = 6;
-  constexpr int NDS = WENO ? ND : 0;
-  constexpr int C = kReconCells;
-  __shared__ float sPc[K * MC * C];
-  __shared__ float sPd[(NDS ? NDS : 1) * 3 * MD * C];
-  __shared__ int sSc[MC * C];
-  __shared__ int sSd[(NDS ? NDS : 1) * MD * C];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid / 5, v = tid - 5 * (tid / 5);
+  if (i >= a.N) return;
   const int N = a.N;
-  const int i0 = blockIdx.x * C;
-  const int nc = min(C, N - i0);
-  for (int e = threadIdx.x; e < K * MC * C; e += blockDim.x) {
-    const int r = e / C, c = e - r * C;
-    if (c < nc) sPc[e] = __ldg(&a.Pc[(size_t)r * N + i0 + c]);
-  }
-  for (int e = threadIdx.x; e < MC * C; e += blockDim.x) {
-    const int r = e / C, c = e - r * C;
-    if (c < nc) sSc[e] = __ldg(&a.sc[(size_t)r * N + i0 + c]);
-  }
-  if (NDS) {  // directional operands only for the cells that take CWENOZ
-    for (int e = threadIdx.x; e < NDS * 3 * MD * C; e += blockDim.x) {
-      const int r = e / C, c = e - r * C;
-      if (c < nc && (!a.gate || a.gate[i0 + c])) sPd[e] = __ldg(&a.Pd[(size_t)r * N + i0 + c]);
-    }
-    for (int e = threadIdx.x; e < NDS * MD * C; e += blockDim.x) {
-      const int r = e / C, c = e - r * C;
-      if (c < nc && (!a.gate || a.gate[i0 + c])) sSd[e] = __ldg(&a.sd[(size_t)r * N + i0 + c]);
-    }
-  }
-  __syncthreads();
-  const int lc = threadIdx.x / 5, v = threadIdx.x - 5 * (threadIdx.x / 5);
-  const int i = i0 + lc;
-  if (lc >= nc) return;
   const float* __restrict__ hl = a.Uhl;
   const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
   // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
@@ -105,9 +78,9 @@ __global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
   for (int k = 0; k < K; k++) ao[k] = 0.f;
 #pragma unroll 6
   for (int m = 0; m < MC; m++) {
-    const float d = diff(sSc[m * C + lc]);
+    const float d = diff(__ldg(&a.sc[(size_t)m * N + i]));
 #pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = fmaf(sPc[(k * MC + m) * C + lc], d, ao[k]);
+    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
   }
   float c[K];
   float S[6];
@@ -115,7 +88,9 @@ __global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * N + i]);
   }
-  if (!WENO || (a.gate && !a.gate[i])) {
+  bool weno = WENO;
+  if (GATED) weno = weno && a.gate[i];
+  if (!weno) {
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = ao[k];
   } else {
@@ -125,9 +100,10 @@ __global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
       b[s][0] = b[s][1] = b[s][2] = 0.f;
 #pragma unroll
       for (int r = 0; r < MD; r++) {
-        const float d = diff(sSd[(s * MD + r) * C + lc]);
+        const float d = diff(__ldg(&a.sd[((size_t)s * MD + r) * N + i]));
 #pragma unroll
-        for (int k = 0; k < 3; k++) b[s][k] = fmaf(sPd[((s * 3 + k) * MD + r) * C + lc], d, b[s][k]);
+        for (int k = 0; k < 3; k++)
+          b[s][k] = fmaf(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
       }
     }
     const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
@@ -175,11 +151,10 @@ __global__ void __launch_bounds__(5 * kReconCells) k_recon_mx(ReconArgsMx a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) c0 = fmaf(-c[3 + q], S[q], c0);
   }
-  float* out = a.coef + (size_t)i * 5 + v;
-  const size_t st = (size_t)N * 5;
+  float* out = a.coef + (size_t)i * a.cs + v;
   out[0] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
+  for (int k = 0; k < K; k++) out[(k + 1) * 5] = c[k];
 }
 
 // float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5
@@ -194,15 +169,25 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, flo
   hl[(size_t)i * 10 + 5 + v] = (float)(u - (double)h);
 }
 
-// value at (x, y, z) into U; gradient written (ACC = false) or added (ACC = true) into g
+// value at (x, y, z) into U; gradient written (ACC = false) or added (ACC = true)
+// into g; the cell's coefficient row is read with 16-byte loads
 template <int ORDER, bool ACC>
-__device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int N, int cell, float x,
-                                             float y, float z, float ih, float U[5], float g[5][3]) {
-  const size_t st = (size_t)N * 5;
-  const float* p = coef + (size_t)cell * 5;
+__device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int cell, float x, float y, float z,
+                                             float ih, float U[5], float g[5][3]) {
+  constexpr int CS = ORDER == 1 ? 20 : 52;
+  float cf[CS];
+  const float4* row = reinterpret_cast<const float4*>(coef + (size_t)cell * CS);
+#pragma unroll
+  for (int q = 0; q < CS / 4; q++) {
+    const float4 t = __ldg(row + q);
+    cf[4 * q] = t.x;
+    cf[4 * q + 1] = t.y;
+    cf[4 * q + 2] = t.z;
+    cf[4 * q + 3] = t.w;
+  }
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const float c0 = p[v], c1 = p[st + v], c2 = p[2 * st + v], c3 = p[3 * st + v];
+    const float c0 = cf[v], c1 = cf[5 + v], c2 = cf[10 + v], c3 = cf[15 + v];
     float gx, gy, gz;
     if (ORDER == 1) {
       U[v] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
@@ -210,8 +195,8 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
       gy = c2;
       gz = c3;
     } else {
-      const float c4 = p[4 * st + v], c5 = p[5 * st + v], c6 = p[6 * st + v];
-      const float c7 = p[7 * st + v], c8 = p[8 * st + v], c9 = p[9 * st + v];
+      const float c4 = cf[20 + v], c5 = cf[25 + v], c6 = cf[30 + v];
+      const float c7 = cf[35 + v], c8 = cf[40 + v], c9 = cf[45 + v];
       const float tx = fmaf(c4, x, fmaf(c7, y, fmaf(c8, z, c1)));
       const float ty = fmaf(c5, y, fmaf(c9, z, c2));
       const float tz = fmaf(c6, z, c3);
@@ -339,8 +324,8 @@ __global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
   const float area = fq[9 * F];
   const int o = a.fo[fc], nb = a.fn[fc];
   float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
-  eval_side_mx<ORDER, false>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], WL, gs);
-  eval_side_mx<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], WR, gs);
+  eval_side_mx<ORDER, false>(a.coef, o, xl, yl, zl, a.inv_h[o], WL, gs);
+  eval_side_mx<ORDER, true>(a.coef, nb, xr, yr, zr, a.inv_h[nb], WR, gs);
   float Fc[5];
   hllc_flux_mx(WL, WR, n, a.c, Fc);
   float flux[5];
@@ -374,12 +359,11 @@ __global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
 
 // diagnostics partial sums from FP32 coefficients (FP64 accumulation)
 __global__ void __launch_bounds__(kRedThreads)
-    k_diag_partial_mx(const double* __restrict__ U, const float* __restrict__ coef,
+    k_diag_partial_mx(const double* __restrict__ U, const float* __restrict__ coef, int cs,
                       const double* __restrict__ vol, const double* __restrict__ inv_h, int N,
                       double* __restrict__ part) {
   __shared__ double sm[4][kRedThreads];
   double acc[4] = {0, 0, 0, 0};
-  const size_t st = (size_t)N * 5;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double r = U[i], ir = 1.0 / r;
     const double u[3] = {U[(size_t)N + i] * ir, U[2 * (size_t)N + i] * ir, U[3 * (size_t)N + i] * ir};
@@ -388,7 +372,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(j + 1) * st + (size_t)i * 5 + v] * ih;
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + (j + 1) * 5 + v] * ih;
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

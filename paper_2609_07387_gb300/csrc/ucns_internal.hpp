@@ -92,6 +92,8 @@ struct ucns_mesh {
   unsigned long long* gate_count = nullptr;
   bool gate_eval_active = false;       // flags valid for the reconstructions of this call
   int gate_check_every = 0;
+  int gate_eval_every = 1;
+  bool gate_flags_valid = false;       // flags of an earlier step may be reused
   double gate_bound = 1e-3;
   int64_t gate_steps = 0;
   double* gate_R = nullptr;            // [2][5][N] residuals of the check

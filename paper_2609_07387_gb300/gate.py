@@ -128,10 +128,11 @@ class GatedRun:
     threshold: float
     check_every: int = 10
     bound: float = 1e-3
+    eval_every: int = 1
 
     def __post_init__(self):
         self.mesh.gate_attach(self.net, self.threshold)
-        self.mesh.gate_configure(self.check_every, self.bound)
+        self.mesh.gate_configure(self.eval_every, self.check_every, self.bound)
         self.mesh.gate_enable(True)
 
     def step(self, U, dt=None):

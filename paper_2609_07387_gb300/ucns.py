@@ -117,7 +117,7 @@ def load(build_if_missing: bool = True):
         lib.ucns_gate_attach.argtypes = [P, P, F32]
         lib.ucns_gate_enable.argtypes = [P, I32]
         lib.ucns_gate_flagged.argtypes = [P, P, P]
-        lib.ucns_gate_configure.argtypes = [P, I32, C.c_double]
+        lib.ucns_gate_configure.argtypes = [P, I32, I32, C.c_double]
         lib.ucns_gate_check.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(I32), P]
         for name in EXPORTS:
             if name not in ("ucns_last_error", "ucns_mesh_destroy", "ucns_mlp_destroy"):
@@ -327,9 +327,10 @@ class Mesh:
     def gate_enable(self, on: bool = True):
         _check(self._lib, self._lib.ucns_gate_enable(self._h, 1 if on else 0))
 
-    def gate_configure(self, check_every: int = 10, bound: float = 1e-3):
-        """Plain-scheme check every `check_every` steps; gate off if dKE/dt differs by > bound."""
-        _check(self._lib, self._lib.ucns_gate_configure(self._h, int(check_every), float(bound)))
+    def gate_configure(self, eval_every: int = 1, check_every: int = 10, bound: float = 1e-3):
+        """Gate evaluated every `eval_every` steps; plain-scheme check every
+        `check_every` steps, gate off if the dKE/dt rates differ by > bound."""
+        _check(self._lib, self._lib.ucns_gate_configure(self._h, int(eval_every), int(check_every), float(bound)))
 
     def gate_check(self, U, stream=None) -> tuple[float, bool]:
         rel = C.c_double(0.0)

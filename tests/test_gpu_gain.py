@@ -66,11 +66,11 @@ def test_learned_gate_gain(setup):
     mk = lambda **kw: ucns.Mesh(s["nodes"], s["cells"], s["box"], ucns.Params(**{**s["base"], **kw}))
     m32 = mk(precision=1)
     hmx, msmx = _run(m32, s["U0"], dts)
-    g = gate.GatedRun(mk(precision=1), s["net"], s["thr"], check_every=10, bound=1e-3)
+    g = gate.GatedRun(mk(precision=1), s["net"], s["thr"], check_every=50, bound=1e-3, eval_every=5)
     hlg, mslg = _run(g.mesh, s["U0"], dts)
     flagged = g.mesh.gate_flagged() / g.mesh.n_cells
     hlin, mslin = _run(mk(precision=1, scheme=0), s["U0"], dts)
-    r = gate.GatedRun(mk(precision=1), gate.rule_network(0.05), 1e-6, check_every=10, bound=1e-3)
+    r = gate.GatedRun(mk(precision=1), gate.rule_network(0.05), 1e-6, check_every=50, bound=1e-3, eval_every=5)
     hru, msru = _run(r.mesh, s["U0"], dts)
     rflag = r.mesh.gate_flagged() / r.mesh.n_cells
     err = lambda h: (np.abs(h - h64) / np.abs(h64)).max(axis=0)
@@ -93,7 +93,7 @@ def test_plain_scheme_check_switches_the_gate_off(setup):
     gate.GatedRun(m, gate.rule_network(1e9), 1e-6, check_every=1, bound=0.5)  # flags nothing
     rel, off = m.gate_check(U)
     assert rel > 0.0 and not off  # linear weights everywhere differ a little from CWENOZ
-    m.gate_configure(check_every=1, bound=1e-14)
+    m.gate_configure(eval_every=1, check_every=1, bound=1e-14)
     m.rk_step(U)  # the step's check finds the rates differ by more than 1e-14 and disables the gate
     with pytest.raises(ucns.UcnsError):
         m.gate_check(U)  # not enabled any more

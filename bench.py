@@ -144,14 +144,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel: str, n: int):
+def measured_traffic(kernel: str, n: int, form: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source for this form (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        e = d.get(kernel)
+        e = d.get(f"{kernel}/{form}")
         if e and e.get("source_hash") == kernel_source_hash():
             return e["dram_bytes_per_launch_scaled_to"].get(str(n))
     except (OSError, ValueError, KeyError):
@@ -275,7 +275,8 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> tuple[float
     return flops, nbytes
 
 
-def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_dir: float = 1.0) -> dict:
+def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_dir: float = 1.0,
+             form: str = "fp64") -> dict:
     kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in ("recon", "face")}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
@@ -299,7 +300,7 @@ def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_di
     else:
         roof = {"bound": "hbm", "achieved": bw, "peak": hbm_gbs, "unit": "GB/s", "frac": hbm_frac,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof.update({"kernel": name, "traffic": measured_traffic(name, n), "avg_launch_ms": avg_s * 1e3,
+    roof.update({"kernel": name, "traffic": measured_traffic(name, n, form), "avg_launch_ms": avg_s * 1e3,
                  "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
                  "alu_frac": alu_frac, "hbm_frac": hbm_frac})
     return roof
@@ -452,7 +453,7 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8 + 16,
                 "steps": args.e2e_steps, "via": "ucns_rk_steps_host, pinned host buffer"},
         "gpu_launches": counted,
-        "roofline": roofline(mc, prof, chosen != "fp64", peak64, hbm, n, frac_dir),
+        "roofline": roofline(mc, prof, chosen != "fp64", peak64, hbm, n, frac_dir, chosen),
         "kernels": shares(prof),
         "fixed_error": {"compared_after_steps": args.warmup + args.steps, "bound": 1e-4, "vs": "plain FP64",
                         "forms": errs},
@@ -460,7 +461,7 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         "learned_gate": None if gate_info is None else {k: v for k, v in gate_info.items() if not k.startswith("_")},
         "plain_fp64": None if "fp64" not in res else {
             "value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"] / args.steps,
-            "roofline": roofline(meshes["fp64"], res["fp64"]["prof"], False, peak64, hbm, n),
+            "roofline": roofline(meshes["fp64"], res["fp64"]["prof"], False, peak64, hbm, n, 1.0, "fp64"),
             "kernels": shares(res["fp64"]["prof"]), "clocks": res["fp64"]["clocks"]},
         "speedup_vs_plain_fp64": r["value"] / res["fp64"]["value"] if "fp64" in res else None,
         "fp64_dgemm_tflops": peak64,

@@ -493,3 +493,20 @@ def test_cwenoz_step_is_non_oscillatory():
             assert w[i, 0, 0] < 0.5  # central candidate loses its weight at the step
     assert over[0] > 0.05
     assert over[1] < 0.2 * over[0]
+
+
+def test_cfl_time_step_closed_form():
+    """Uniform state on a uniform cube lattice: h_i = 2|V|/sum|S_f| = side/3 and
+    dt = CFL min(h/(|u|+a), rho h^2 Pr/(2 gamma mu))."""
+    n = 8
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0, Re=1600.0, cfl=0.5))
+    U = np.zeros((5, c.n_cells))
+    r, u, p = 1.3, np.array([0.4, -0.1, 0.2]), 0.9
+    U[0] = r
+    U[1:4] = (r * u)[:, None]
+    U[4] = p / 0.4 + 0.5 * r * u @ u
+    h = 2 * math.pi / n / 3
+    a = math.sqrt(1.4 * p / r)
+    ref = 0.5 * min(h / (np.linalg.norm(u) + a), r * h * h * 0.71 / (2 * 1.4 / 1600.0))
+    assert math.isclose(c.time_step(U), ref, rel_tol=1e-13)

@@ -55,6 +55,7 @@ def _load():
             lib.orc_stencil.argtypes = [P, I64, C.c_int, P, P, P, P]
             lib.orc_residual.argtypes = [P, P, P]
             lib.orc_residual_subset.argtypes = [P, P, I64, P, P]
+            lib.orc_residual_subset_terms.argtypes = [P, P, I64, P, P, P]
             lib.orc_residual_terms.argtypes = [P, P, P, P]
             lib.orc_rk_step.restype = D
             lib.orc_rk_step.argtypes = [P, P, D]
@@ -189,6 +190,14 @@ class Case:
         R = np.zeros((5, sel.size))
         self._check(self._lib.orc_residual_subset(self._h, _p(U), sel.size, _p(sel), _p(R)))
         return R
+
+    def residual_subset_terms(self, U, cells):
+        """(R, S) [5, len(cells)] of the given cells only (same arithmetic)."""
+        U = _f64(U)
+        sel = np.ascontiguousarray(cells, dtype=np.int64)
+        R, S = np.zeros((5, sel.size)), np.zeros((5, sel.size))
+        self._check(self._lib.orc_residual_subset_terms(self._h, _p(U), sel.size, _p(sel), _p(R), _p(S)))
+        return R, S
 
     def time_step(self, U) -> float:
         U = _f64(U)

@@ -228,10 +228,12 @@ static void f_psibar(void *ctx, const double x[3], double w) {
 }
 
 static int compute_geometry(orc_case *c) {
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t i = 0; i < c->N; i++) {
     vm_ctx q = {0, {0, 0, 0}};
     cell_quad(c, i, c->ngeo, f_volmom, &q);
-    if (!(q.v > 0)) { set_err("cell with non-positive volume"); return -1; }
+    if (!(q.v > 0)) { bad = 1; continue; }
     c->vol[i] = q.v;
     for (int d = 0; d < 3; d++) c->cen[3 * i + d] = q.m[d] / q.v;
     c->hh[i] = cbrt(q.v);
@@ -242,6 +244,7 @@ static int compute_geometry(orc_case *c) {
     cell_quad(c, i, c->ngeo, f_psibar, &b);
     for (int k = 0; k < 9; k++) c->psib[9 * i + k] = b.s[k] / q.v;
   }
+  if (bad) { set_err("cell with non-positive volume"); return -1; }
   return 0;
 }
 
@@ -893,7 +896,14 @@ static int residual(orc_case *c, const double *U, double *R) { return residual_t
 
 /* Residual of a sample of cells only (same arithmetic as residual(); used to
  * time the oracle on a bounded part of a large mesh).  R: [5][ns]. */
+int orc_residual_subset_terms(orc_case *c, const double *U, int64_t ns, const int64_t *sel, double *R,
+                              double *S);
 int orc_residual_subset(orc_case *c, const double *U, int64_t ns, const int64_t *sel, double *R) {
+  return orc_residual_subset_terms(c, U, ns, sel, R, NULL);
+}
+/* ... and S_k = (1/|V_i|) sum_f |G_f| of each sampled cell (may be NULL) */
+int orc_residual_subset_terms(orc_case *c, const double *U, int64_t ns, const int64_t *sel, double *R,
+                              double *S) {
   int64_t N = c->N;
   unsigned char *need = (unsigned char *)calloc(N, 1);
   for (int64_t k = 0; k < ns; k++) {
@@ -936,6 +946,12 @@ int orc_residual_subset(orc_case *c, const double *U, int64_t ns, const int64_t 
         for (int v = 0; v < 5; v++) s[v] += c->cs[i * c->nfc + j] * g[v];
       }
       for (int v = 0; v < 5; v++) R[v * ns + k] = -s[v] / c->vol[i];
+      if (S)
+        for (int v = 0; v < 5; v++) {
+          double t = 0;
+          for (int j = 0; j < c->nfc; j++) t += fabs(G[5 * fpos[c->cf[i * c->nfc + j]] + v]);
+          S[v * ns + k] = t / c->vol[i];
+        }
     }
     free(fneed);
     free(fpos);

@@ -133,6 +133,7 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.sd = m->d.sd;
   a.Pd = m->d.Pdf;
   a.mom = m->d.mom;
+  a.inv_h = m->d.inv_hf;
   a.coef = m->d.coeff;
   a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
   a.N = (int)m->N;
@@ -197,6 +198,7 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.sd = m->d.sd;
   a.Pd = m->d.Pd;
   a.mom = m->d.mom;
+  a.inv_h = m->d.inv_h;
   a.coef = m->d.coef;
   a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
   a.dev = m->label_out;

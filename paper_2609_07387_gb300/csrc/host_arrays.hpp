@@ -13,7 +13,7 @@ struct HostArrays {
   std::vector<double> Pc;                                // [K][Mc][N]
   std::vector<int32_t> sd;                               // [nd][Md][N]
   std::vector<double> Pd;                                // [nd][3][Md][N]
-  std::vector<double> fq;                                // [nq][10][F]
+  std::vector<double> fq;                                // [nq][10][F] x-x_L, x-x_R', n, |dS|
   std::vector<double> fpen;                              // [F]
 };
 

@@ -28,7 +28,8 @@ struct ReconArgs {
   const int32_t* __restrict__ sd;
   const double* __restrict__ Pd;
   const double* __restrict__ mom;  // [6][N]
-  double* __restrict__ coef;       // [NC][N][5]
+  const double* __restrict__ inv_h;  // [N]
+  double* __restrict__ coef;       // [NC][N][5] physical-unit monomial coefficients
   const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
   float* __restrict__ dev;           // [N]: max |omega - lambda| (null: not wanted)
   int N;
@@ -37,7 +38,7 @@ struct ReconArgs {
 
 struct FaceArgs {
   const double* __restrict__ coef;
-  const double* __restrict__ fq;  // [nq][10][F]
+  const double* __restrict__ fq;  // [nq][10][F]: x - x_L, x - x_R' (physical), n, |dS|
   const double* __restrict__ fpen;
   const int32_t* __restrict__ fo;
   const int32_t* __restrict__ fn;
@@ -252,25 +253,27 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
       for (int k = 0; k < 3; k++) c[k] = fma(e, b[s][k], c[k]);
     }
   }
-  // monomial form: p = c0 + sum_k c_k psi_k(xi), c0 = U_i - sum_{k>=3} c_k mean(psi_k)
+  // monomial form: p = c0 + sum_k c_k psi_k(xi), c0 = U_i - sum_{k>=3} c_k mean(psi_k);
+  // stored in physical units (psi_k of x - x_i): linear terms / h, quadratic / h^2
   double c0 = ui;
   if (ORDER == 2) {
 #pragma unroll
     for (int q = 0; q < 6; q++) c0 = fma(-c[3 + q], S[q], c0);
   }
+  const double ih = __ldg(&a.inv_h[i]), ih2 = ih * ih;
   double* out = a.coef + (size_t)i * 5 + v;
   const size_t st = (size_t)N * 5;
   out[0] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k];
+  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k] * (k < 3 ? ih : ih2);
 }
 
 // ----------------------------------------------------------- face flux
-// value into U; gradient written (ACC = false) or added (ACC = true) into g
+// value at the physical offset (x, y, z) from the centroid into U; gradient
+// written (ACC = false) or added (ACC = true) into g
 template <int ORDER, bool ACC>
 __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N, int cell,
-                                          double x, double y, double z, double ih, double U[5],
-                                          double g[5][3]) {
+                                          double x, double y, double z, double U[5], double g[5][3]) {
   const size_t st = (size_t)N * 5;
   const double* p = coef + (size_t)cell * 5;
 #pragma unroll
@@ -294,13 +297,13 @@ __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N
       gz = fma(c8, x, fma(c9, y, fma(c6, z, tz)));  // c3 + c8 x + c9 y + 2c6 z
     }
     if (ACC) {
-      g[v][0] = fma(gx, ih, g[v][0]);
-      g[v][1] = fma(gy, ih, g[v][1]);
-      g[v][2] = fma(gz, ih, g[v][2]);
+      g[v][0] += gx;
+      g[v][1] += gy;
+      g[v][2] += gz;
     } else {
-      g[v][0] = gx * ih;
-      g[v][1] = gy * ih;
-      g[v][2] = gz * ih;
+      g[v][0] = gx;
+      g[v][1] = gy;
+      g[v][2] = gz;
     }
   }
 }
@@ -321,8 +324,8 @@ __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
   const double area = fq[9 * F];
   const int o = a.fo[fc], nb = a.fn[fc];
   double UL[5], UR[5], gs[5][3];  // gs = grad U_L + grad U_R
-  eval_side<ORDER, false>(a.coef, a.N, o, xl, yl, zl, a.inv_h[o], UL, gs);
-  eval_side<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, a.inv_h[nb], UR, gs);
+  eval_side<ORDER, false>(a.coef, a.N, o, xl, yl, zl, UL, gs);
+  eval_side<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, UR, gs);
   double Fc[5];
   hllc_flux(UL, UR, n, a.c, Fc);
   double flux[5];
@@ -472,12 +475,11 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double r = U[i], ir = 1.0 / r;
     const double u[3] = {U[(size_t)N + i] * ir, U[2 * (size_t)N + i] * ir, U[3 * (size_t)N + i] * ir};
-    const double ih = inv_h[i];
-    double g[4][3];  // gradients of rho, m_x, m_y, m_z at the centroid
+    double g[4][3];  // gradients of rho, m_x, m_y, m_z at the centroid (physical coefficients)
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = coef[(j + 1) * st + (size_t)i * 5 + v] * ih;
+      for (int j = 0; j < 3; j++) g[v][j] = coef[(j + 1) * st + (size_t)i * 5 + v];
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

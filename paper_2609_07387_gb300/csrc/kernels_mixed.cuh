@@ -34,6 +34,7 @@ struct ReconArgsMx {
   const int32_t* __restrict__ sd;
   const float* __restrict__ Pd;
   const double* __restrict__ mom;  // [6][N]
+  const float* __restrict__ inv_h;  // [N]
   float* __restrict__ coef;        // [N][cs]: coefficient k of variable v at k*5 + v, slot 0 relative to U_ref
   const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
   int N;
@@ -59,7 +60,7 @@ struct FaceArgsMx {
 // linear weights (a separate instantiation, so the ungated kernel has no
 // data-dependent branch around the directional loads)
 template <int ORDER, bool WENO, int ND, bool GATED>
-__global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
+__global__ void __launch_bounds__(256, 4) k_recon_mx(ReconArgsMx a) {
   constexpr int K = ORDER == 1 ? 3 : 9;
   constexpr int MC = 2 * K;
   constexpr int MD = 6;
@@ -151,10 +152,12 @@ __global__ void __launch_bounds__(256) k_recon_mx(ReconArgsMx a) {
 #pragma unroll
     for (int q = 0; q < 6; q++) c0 = fmaf(-c[3 + q], S[q], c0);
   }
+  // physical units: linear coefficients / h, quadratic / h^2
+  const float ih = __ldg(&a.inv_h[i]), ih2 = ih * ih;
   float* out = a.coef + (size_t)i * a.cs + v;
   out[0] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * 5] = c[k];
+  for (int k = 0; k < K; k++) out[(k + 1) * 5] = c[k] * (k < 3 ? ih : ih2);
 }
 
 // float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5
@@ -169,11 +172,12 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, flo
   hl[(size_t)i * 10 + 5 + v] = (float)(u - (double)h);
 }
 
-// value at (x, y, z) into U; gradient written (ACC = false) or added (ACC = true)
-// into g; the cell's coefficient row is read with 16-byte loads
+// value at the physical offset (x, y, z) from the centroid into U; gradient
+// written (ACC = false) or added (ACC = true) into g; the cell's coefficient
+// row is read with 16-byte loads
 template <int ORDER, bool ACC>
 __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int cell, float x, float y, float z,
-                                             float ih, float U[5], float g[5][3]) {
+                                             float U[5], float g[5][3]) {
   constexpr int CS = ORDER == 1 ? 20 : 52;
   float cf[CS];
   const float4* row = reinterpret_cast<const float4*>(coef + (size_t)cell * CS);
@@ -206,13 +210,13 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
       gz = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz)));
     }
     if (ACC) {
-      g[v][0] = fmaf(gx, ih, g[v][0]);
-      g[v][1] = fmaf(gy, ih, g[v][1]);
-      g[v][2] = fmaf(gz, ih, g[v][2]);
+      g[v][0] += gx;
+      g[v][1] += gy;
+      g[v][2] += gz;
     } else {
-      g[v][0] = gx * ih;
-      g[v][1] = gy * ih;
-      g[v][2] = gz * ih;
+      g[v][0] = gx;
+      g[v][1] = gy;
+      g[v][2] = gz;
     }
   }
 }
@@ -310,7 +314,7 @@ __device__ __forceinline__ void viscous_flux_mx(const float W[5], const float g[
 }
 
 template <int ORDER, bool VISC>
-__global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
+__global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
   constexpr int NQ = ORDER * ORDER;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = tid / NQ, q = tid - NQ * (tid / NQ);
@@ -324,8 +328,8 @@ __global__ void __launch_bounds__(256) k_face_mx(FaceArgsMx a) {
   const float area = fq[9 * F];
   const int o = a.fo[fc], nb = a.fn[fc];
   float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
-  eval_side_mx<ORDER, false>(a.coef, o, xl, yl, zl, a.inv_h[o], WL, gs);
-  eval_side_mx<ORDER, true>(a.coef, nb, xr, yr, zr, a.inv_h[nb], WR, gs);
+  eval_side_mx<ORDER, false>(a.coef, o, xl, yl, zl, WL, gs);
+  eval_side_mx<ORDER, true>(a.coef, nb, xr, yr, zr, WR, gs);
   float Fc[5];
   hllc_flux_mx(WL, WR, n, a.c, Fc);
   float flux[5];
@@ -367,12 +371,11 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double r = U[i], ir = 1.0 / r;
     const double u[3] = {U[(size_t)N + i] * ir, U[2 * (size_t)N + i] * ir, U[3 * (size_t)N + i] * ir};
-    const double ih = inv_h[i];
-    double g[4][3];
+    double g[4][3];  // physical-unit linear coefficients = gradient at the centroid
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + (j + 1) * 5 + v] * ih;
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + (j + 1) * 5 + v];
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

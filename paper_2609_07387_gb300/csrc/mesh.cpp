@@ -458,8 +458,8 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
     for (int q = 0; q < nq; q++) {
       double a = std::sqrt(dot(dS[q], dS[q]));
       V3 nh = (1.0 / a) * dS[q];
-      V3 xl = (1.0 / g[o].h) * (x[q] - g[o].c);
-      V3 xr = (1.0 / g[n].h) * (x[q] - sv - g[n].c);
+      V3 xl = x[q] - g[o].c;       // offset from the owner's centroid
+      V3 xr = x[q] - sv - g[n].c;  // offset from the neighbour image's centroid
       double vals[10] = {xl.x, xl.y, xl.z, xr.x, xr.y, xr.z, nh.x, nh.y, nh.z, a};
       for (int c = 0; c < 10; c++) h->fq[((size_t)q * 10 + c) * F + f] = vals[c];
       tot = tot + dS[q];

@@ -43,7 +43,7 @@ struct DeviceMesh {
   // faces
   int32_t* fo = nullptr;      // [F] owner
   int32_t* fn = nullptr;      // [F] neighbour
-  double* fq = nullptr;       // [nq][10][F] xiL(3) xiR(3) n(3) |dS|(1)
+  double* fq = nullptr;       // [nq][10][F] x-x_L(3) x-x_R'(3) n(3) |dS|(1), physical offsets
   float* fqf = nullptr;       // FP32 copy
   double* fpen = nullptr;     // [F] alpha / L_int
   // scratch owned by the handle

@@ -367,8 +367,9 @@ __device__ __forceinline__ double face_sum(const RKArgs& a, int i, int v) {
 #pragma unroll
   for (int j = 0; j < NFC; j++) {
     const int e = __ldg(&a.cf[(size_t)j * a.N + i]);
-    const double g = __ldg(&a.G[(size_t)v * a.F + (e >> 1)]);
-    s += (e & 1) ? -g : g;
+    // sigma G_f: the neighbour side flips the sign bit (an integer XOR, not an FP64 op)
+    const long long gb = __double_as_longlong(__ldg(&a.G[(size_t)v * a.F + (e >> 1)]));
+    s += __longlong_as_double(gb ^ ((long long)(e & 1) << 63));
   }
   return s;
 }
@@ -392,18 +393,19 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
     for (int v = 0; v < 5; v++) a.out[v * N + i] = -face_sum<NFC>(a, i, v) * ivol;
     return;
   }
-  const double dt = *a.dt;
+  // dt R = w s with w = -dt/|V_i| and s the signed face sum
+  const double w = -(*a.dt) * ivol;
   double Un[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const double R = -face_sum<NFC>(a, i, v) * ivol;
+    const double s = face_sum<NFC>(a, i, v);
     const double u0 = a.U0[v * N + i];
     if (STAGE == 1) {
-      Un[v] = u0 + dt * R;
+      Un[v] = fma(w, s, u0);                                     // U0 + dt R
     } else if (STAGE == 2) {
-      Un[v] = 0.75 * u0 + 0.25 * (a.Us[v * N + i] + dt * R);
+      Un[v] = fma(0.25 * w, s, fma(0.75, u0, 0.25 * a.Us[v * N + i]));  // 3/4 U0 + 1/4 (U1 + dt R)
     } else {
-      Un[v] = u0 * (1.0 / 3.0) + (2.0 / 3.0) * (a.Us[v * N + i] + dt * R);
+      Un[v] = fma((2.0 / 3.0) * w, s, fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]));  // 1/3 U0 + 2/3 (U2 + dt R)
     }
   }
 #pragma unroll
@@ -422,23 +424,75 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
 // ------------------------------------------------------------ reductions
 constexpr int kRedThreads = 256;
 
-// per-block minimum of the CFL time-step limit
+// CFL limit of cell i: h / (|u| + a), and the viscous limit rho h^2 Pr/(2 gamma mu)
+// when visc_coef > 0; bad when rho, p or the limit is not positive
+__device__ __forceinline__ double dt_limit(const double* __restrict__ U, size_t N, int i, double h, double gam,
+                                           double visc_coef, bool& bad) {
+  const double r = U[i], m0 = U[N + i], m1 = U[2 * N + i], m2 = U[3 * N + i];
+  const double ir = 1.0 / r;
+  const double q2 = (m0 * m0 + m1 * m1 + m2 * m2) * ir * ir;
+  const double p = (gam - 1.0) * (U[4 * N + i] - 0.5 * r * q2);
+  double d = h / (sqrt(q2) + sqrt(gam * p * ir));
+  if (visc_coef > 0.0) d = fmin(d, r * h * h * visc_coef);
+  if (!(r > 0.0 && p > 0.0 && d > 0.0)) bad = true;
+  return d;
+}
+
+// FP32 estimate of dt_limit with relative error below 1e-6, written as
+// h rho / (|m| + sqrt(gamma (gamma-1) (rho E - |m|^2/2))) so that the FP64 part
+// has no division or square root.  `sure` is false where the estimate cannot
+// be trusted to that accuracy or where dt_limit could flag the cell: rho <= 0,
+// rho E - |m|^2/2 below 1e-3 rho E (pressure near zero), values outside the
+// normal FP32 range, non-finite values.
+__device__ __forceinline__ float dt_estimate(const double* __restrict__ U, size_t N, int i, float h, float g2,
+                                             float visc_f, bool& sure) {
+  const double r = U[i], m0 = U[N + i], m1 = U[2 * N + i], m2 = U[3 * N + i], E = U[4 * N + i];
+  const double mm = fma(m0, m0, fma(m1, m1, m2 * m2));
+  const double er = E * r;
+  const double pr = fma(-0.5, mm, er);  // rho p / (gamma - 1)
+  const float rf = (float)r, mf = (float)mm, pf = (float)pr;
+  // every FP32 intermediate below stays a normal number on this range
+  sure = pr > 1e-3 * er && rf > 1e-15f && rf < 1e15f && pf > 1e-30f && pf < 1e30f && mf < 1e30f;
+  float d = h * rf / (sqrtf(mf) + sqrtf(g2 * pf));
+  if (visc_f > 0.f) d = fminf(d, rf * h * h * visc_f);
+  sure = sure && d > 1e-30f && d < 1e30f;
+  return d;
+}
+
+// per-block minimum of the CFL time-step limit, equal bit for bit to the
+// minimum of dt_limit over the block's cells: a first pass takes the minimum
+// m of the FP32 estimates, a second evaluates dt_limit in FP64 only for the
+// cells whose estimate is within 1e-4 of m (the exact minimum is among them,
+// the estimates being accurate to 1e-6) and for every cell without a sure
+// estimate (which also raises the nonphysical flag exactly where dt_limit
+// does)
 __global__ void __launch_bounds__(kRedThreads)
     k_dt_partial(const double* __restrict__ U, const double* __restrict__ dtlen, int N, double gam,
                  double visc_coef /* Pr/(2 gam mu) or 0 */, double* __restrict__ part, int* err) {
   __shared__ double sm[kRedThreads];
+  __shared__ float smf[kRedThreads];
+  const float g2 = (float)(gam * (gam - 1.0)), visc_f = (float)visc_coef;
+  const size_t n = N;
+  float est = INFINITY;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    bool sure;
+    const float e = dt_estimate(U, n, i, (float)dtlen[i], g2, visc_f, sure);
+    if (sure) est = fminf(est, e);
+  }
+  smf[threadIdx.x] = est;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) smf[threadIdx.x] = fminf(smf[threadIdx.x], smf[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const float cut = smf[0] * 1.0001f;
   double best = INFINITY;
   bool bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const double r = U[i], m0 = U[(size_t)N + i], m1 = U[2 * (size_t)N + i], m2 = U[3 * (size_t)N + i];
-    const double ir = 1.0 / r;
-    const double q2 = (m0 * m0 + m1 * m1 + m2 * m2) * ir * ir;
-    const double p = (gam - 1.0) * (U[4 * (size_t)N + i] - 0.5 * r * q2);
     const double h = dtlen[i];
-    double d = h / (sqrt(q2) + sqrt(gam * p * ir));
-    if (visc_coef > 0.0) d = fmin(d, r * h * h * visc_coef);
-    if (!(r > 0.0 && p > 0.0 && d > 0.0)) bad = true;
-    best = fmin(best, d);
+    bool sure;
+    const float e = dt_estimate(U, n, i, (float)h, g2, visc_f, sure);
+    if (!sure || e <= cut) best = fmin(best, dt_limit(U, n, i, h, gam, visc_coef, bad));
   }
   if (bad) atomicOr(err, 1);
   sm[threadIdx.x] = best;

@@ -196,3 +196,36 @@ def test_residual_requires_device_tensors():
     m = ucns.Mesh(nodes, cells, box, ucns.Params(order=1, scheme=0))
     with pytest.raises(ValueError):
         m.residual(torch.zeros(5, m.n_cells, dtype=torch.float64))
+
+
+@pytest.mark.parametrize("Re", [1600.0, 1.0])
+def test_time_step_equal_limits_and_low_pressure(Re):
+    """The device reduction evaluates the FP64 limit only where an FP32
+    estimate is near the block minimum or cannot be trusted; the result must
+    still be the FP64 minimum: every cell on the same limit (uniform state on a
+    regular lattice), the minimum in cells whose pressure is 1e-5 of their
+    energy, and (Re = 1) viscous and convective limits of similar size."""
+    nodes, cells, box = I.hex_lattice(12)
+    m, oc = _pair(nodes, cells, box, order=1, scheme=0, Re=Re, Mach=0.1)
+    n = len(cells)
+    ones = np.ones(n)
+    U = I.primitive_to_conserved(ones, 0.3 * ones, 0 * ones, 0 * ones, ones / (1.4 * 0.01))
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    assert abs(m.time_step(Ug) - oc.time_step(U)) <= 1e-14 * oc.time_step(U)
+    rng = np.random.default_rng(3)
+    fast = rng.choice(n, 40, replace=False)
+    prim_u = 0.3 * ones
+    prim_u[fast] = 50.0 + 1e-9 * np.arange(40)  # near-ties among the fast cells
+    p = ones / (1.4 * 0.01)
+    p[fast] = 1e-5 * 0.5 * 50.0 ** 2
+    U = I.primitive_to_conserved(ones, prim_u, 0 * ones, 0 * ones, p)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    dtg, dtc = m.time_step(Ug), oc.time_step(U)
+    assert abs(dtg - dtc) <= 1e-14 * dtc
+    # a cell with p < 0 (rho > 0) is reported
+    U[4, fast[0]] = 0.5 * U[1, fast[0]] ** 2 / U[0, fast[0]] * (1 - 1e-9)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    with pytest.raises(ucns.UcnsError) as e:
+        m.time_step(Ug)
+    assert e.value.code == -5
+    m.check_state()

@@ -457,7 +457,8 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         "kernels": shares(prof),
         "fixed_error": {"compared_after_steps": args.warmup + args.steps, "bound": 1e-4, "vs": "plain FP64",
                         "forms": errs},
-        "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps} for f in res},
+        "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps,
+                      "kernels": shares(res[f]["prof"])} for f in res},
         "learned_gate": None if gate_info is None else {k: v for k, v in gate_info.items() if not k.startswith("_")},
         "plain_fp64": None if "fp64" not in res else {
             "value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms"] / args.steps,

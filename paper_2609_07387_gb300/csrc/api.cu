@@ -47,6 +47,17 @@ int upload_f32(float** dst, const std::vector<double>& src) {
   return upload(dst, f);
 }
 
+// [rows][N] -> blocked [ceil(N/kTC)][rows][kTC] (zero past N), converted to T
+template <typename T, typename S>
+int upload_blocked(T** dst, const std::vector<S>& src, int rows, int64_t N) {
+  if (src.empty()) return UCNS_OK;
+  const int64_t tiles = (N + kTC - 1) / kTC;
+  std::vector<T> b((size_t)tiles * rows * kTC, T(0));
+  for (int r = 0; r < rows; r++)
+    for (int64_t i = 0; i < N; i++) b[blk(r, rows, i)] = (T)src[(size_t)r * N + i];
+  return upload(dst, b);
+}
+
 template <typename T>
 int alloc(T** dst, size_t n) {
   if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess)
@@ -124,18 +135,31 @@ bool mixed(const ucns_mesh* m) { return m->P.precision == UCNS_PREC_MIXED; }
 // floats per cell row of the mixed-form coefficients: 5 (K+1) rounded up to 4
 int coef_row_floats(const ucns_mesh* m) { return (5 * m->NC + 3) / 4 * 4; }
 
+template <int ORDER, bool WENO, int ND, bool GATED>
+int launch_recon_tiles(const ReconArgsMx& a, cudaStream_t s) {
+  constexpr size_t sm = ReconTile<ORDER, WENO, ND>::smem(WENO && !GATED);
+  if (a.cs != ReconTile<ORDER, WENO, ND>::CS) return fail(UCNS_ERR_INVALID_ARG, "coefficient row size mismatch");
+  UCNS_CUDA(cudaFuncSetAttribute(k_recon_mx<ORDER, WENO, ND, GATED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
+  const unsigned tiles = (unsigned)((a.N + kTC - 1) / kTC);
+  k_recon_mx<ORDER, WENO, ND, GATED><<<tiles, kTC * 5, sm, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   ReconArgsMx a;
   (void)U;  // read through its float pair m->d.Uhl, written by k_split or the RK stage
   a.Uhl = m->d.Uhl;
-  a.sc = m->d.sc;
-  a.Pc = m->d.Pcf;
-  a.sd = m->d.sd;
-  a.Pd = m->d.Pdf;
+  a.sc = m->d.scb;
+  a.Pc = m->d.Pcb;
+  a.sd = m->d.sdb;
+  a.Pd = m->d.Pdb;
   a.mom = m->d.mom;
   a.inv_h = m->d.inv_hf;
   a.coef = m->d.coeff;
   a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
+  a.err = m->d.err;
   a.N = (int)m->N;
   a.cs = coef_row_floats(m);
   const double lsum = m->P.lambda_central + m->nd;
@@ -145,22 +169,11 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const unsigned g = nblocks((size_t)m->N * 5);
   const bool gated = a.gate != nullptr;
-  if (m->K == 3)
-    k_recon_mx<1, false, 6, false><<<g, 256, 0, s>>>(a);
-  else if (m->nd == 0)
-    k_recon_mx<2, false, 6, false><<<g, 256, 0, s>>>(a);
-  else if (m->nd == 6 && gated)
-    k_recon_mx<2, true, 6, true><<<g, 256, 0, s>>>(a);
-  else if (m->nd == 6)
-    k_recon_mx<2, true, 6, false><<<g, 256, 0, s>>>(a);
-  else if (gated)
-    k_recon_mx<2, true, 4, true><<<g, 256, 0, s>>>(a);
-  else
-    k_recon_mx<2, true, 4, false><<<g, 256, 0, s>>>(a);
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
+  if (m->K == 3) return launch_recon_tiles<1, false, 6, false>(a, s);
+  if (m->nd == 0) return launch_recon_tiles<2, false, 6, false>(a, s);
+  if (m->nd == 6) return gated ? launch_recon_tiles<2, true, 6, true>(a, s) : launch_recon_tiles<2, true, 6, false>(a, s);
+  return gated ? launch_recon_tiles<2, true, 4, true>(a, s) : launch_recon_tiles<2, true, 4, false>(a, s);
 }
 
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
@@ -297,13 +310,14 @@ int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindRecon, s, [&] { return launch_recon_raw(m, U, s); });
 }
 // float pair of a caller state before a mixed reconstruction of it
+int launch_split_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
+  k_split<<<nblocks((size_t)5 * m->N), 256, 0, s>>>(U, m->d.Uhl, (int)m->N);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
 int launch_split(ucns_mesh* m, const double* U, cudaStream_t s) {
   if (!mixed(m)) return UCNS_OK;
-  return timed(m, kKindOther, s, [&] {
-    k_split<<<nblocks((size_t)5 * m->N), 256, 0, s>>>(U, m->d.Uhl, (int)m->N);
-    UCNS_CUDA(cudaGetLastError());
-    return UCNS_OK;
-  });
+  return timed(m, kKindOther, s, [&] { return launch_split_raw(m, U, s); });
 }
 int launch_face(ucns_mesh* m, cudaStream_t s) {
   return timed(m, kKindFace, s, [&] { return launch_face_raw(m, s); });
@@ -315,27 +329,39 @@ int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindDt, s, [&] { return launch_dt_raw(m, U, s); });
 }
 
-// features of U and the network's flags, once per call of the solver
-int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s) {
+// the indicator features of U into X (BF16) and Xf (FP32, or null); the
+// mixed form reads U through its float pair, split here
+int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s) {
+  FeatArgs a;
+  a.U = U;
+  a.Uhl = m->d.Uhl;
+  a.sc = mixed(m) ? m->d.scb : m->d.sc;
+  a.Pc = mixed(m) ? (const void*)m->d.Pcb : (const void*)m->d.Pc;
+  a.mom = m->d.mom;
+  a.inv_h = m->d.inv_h;
+  a.X = reinterpret_cast<__nv_bfloat16*>(X);
+  a.Xf = Xf;
+  a.N = (int)m->N;
+  a.gam = (float)m->P.gamma;
+  if (mixed(m)) {
+    int rc = launch_split_raw(m, U, s);
+    if (rc) return rc;
+    k_features_mx<<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+  } else {
+    k_features<<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+// features of U and the network's flags, once per call of the solver; for the
+// mixed form this leaves the float pair of U in m->d.Uhl
+int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr) {
   m->gate_eval_active = false;
   if (!m->gate_on || !m->mlp) return UCNS_OK;
-  int rc = timed(m, kKindFeatures, s, [&] {
-    FeatArgs a;
-    a.U = U;
-    a.sc = m->d.sc;
-    a.Pc = mixed(m) ? (const void*)m->d.Pcf : (const void*)m->d.Pc;
-    a.mom = m->d.mom;
-    a.inv_h = m->d.inv_h;
-    a.X = reinterpret_cast<__nv_bfloat16*>(m->gate_X);
-    a.Xf = nullptr;
-    a.N = (int)m->N;
-    a.gam = (float)m->P.gamma;
-    if (mixed(m)) k_features<float><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
-    else k_features<double><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
-    UCNS_CUDA(cudaGetLastError());
-    return UCNS_OK;
-  });
+  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s); });
   if (rc) return rc;
+  if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
     return ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
   });
@@ -392,13 +418,15 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
     m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
+  bool split_done = false;
   if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
     m->gate_eval_active = true;  // reuse the flags of the last evaluation
   } else {
-    if ((rc = gate_eval(m, U, s))) return rc;  // flags of U^n serve all three stages
+    if ((rc = gate_eval(m, U, s, &split_done))) return rc;  // flags of U^n serve all three stages
     m->gate_flags_valid = m->gate_eval_active;
   }
-  if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 1, U, U, W, s)))
+  if ((!split_done && (rc = launch_split(m, U, s))) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
+      (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
     return rc;
@@ -413,6 +441,7 @@ int read_error_word(ucns_mesh* m, cudaStream_t s) {
   UCNS_CUDA(cudaStreamSynchronize(s));
   if (h) {
     UCNS_CUDA(cudaMemsetAsync(m->d.err, 0, sizeof(int), s));
+    if (h & 2) return fail(UCNS_ERR_TIMEOUT, "a bounded wait for a bulk copy in the reconstruction gave up");
     return fail(UCNS_ERR_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or non-finite)");
   }
   return UCNS_OK;
@@ -451,7 +480,7 @@ void device_free(ucns_mesh* m) {
   m->gate_count = nullptr;
   m->gate_eval_active = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcf, d.Pdf,
+  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uhost, d.red, d.dt, d.err};
   for (void* p : ptrs)
@@ -588,7 +617,9 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     return rc;
   }
   if (p->precision == UCNS_PREC_MIXED) {
-    if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) ||
+    const int rc_rows = m->K * m->Mc, rd_rows = m->nd * 3 * m->Md;
+    if ((rc = upload_blocked(&d.Pcb, h.Pc, rc_rows, m->N)) || (rc = upload_blocked(&d.Pdb, h.Pd, rd_rows, m->N)) ||
+        (rc = upload_blocked(&d.scb, h.sc, m->Mc, m->N)) || (rc = upload_blocked(&d.sdb, h.sd, m->nd * m->Md, m->N)) ||
         (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
@@ -758,21 +789,7 @@ int ucns_gate_features(ucns_mesh* m, const double* U, void* X, float* Xf, void* 
   if (!U || !X) return fail(UCNS_ERR_INVALID_ARG, "U or X is NULL");
   if (((uintptr_t)X & 15) != 0) return fail(UCNS_ERR_INVALID_ARG, "X must be 16-byte aligned");
   if (m->K != 9) return fail(UCNS_ERR_INVALID_ARG, "features need order 2");
-  cudaStream_t s = (cudaStream_t)stream;
-  FeatArgs a;
-  a.U = U;
-  a.sc = m->d.sc;
-  a.Pc = mixed(m) ? (const void*)m->d.Pcf : (const void*)m->d.Pc;
-  a.mom = m->d.mom;
-  a.inv_h = m->d.inv_h;
-  a.X = reinterpret_cast<__nv_bfloat16*>(X);
-  a.Xf = Xf;
-  a.N = (int)m->N;
-  a.gam = (float)m->P.gamma;
-  if (mixed(m)) k_features<float><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
-  else k_features<double><<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
+  return launch_features(m, U, X, Xf, (cudaStream_t)stream);
 }
 
 int ucns_gate_labels(ucns_mesh* m, const double* U, float* dev, void* stream) {

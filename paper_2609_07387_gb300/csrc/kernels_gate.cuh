@@ -6,14 +6,15 @@
 
 #include <cuda_bf16.h>
 
-#include "kernels.cuh"
+#include "kernels_mixed.cuh"
 
 namespace ucns {
 
 struct FeatArgs {
-  const double* __restrict__ U;  // [5][N]
-  const int32_t* __restrict__ sc;
-  const void* __restrict__ Pc;   // [9][18][N], double or float
+  const double* __restrict__ U;    // [5][N] (FP64 form)
+  const float* __restrict__ Uhl;   // [N][10] float pair of U (mixed form)
+  const int32_t* __restrict__ sc;  // [18][N] (FP64 form) or blocked [tiles][18][kTC] (mixed form)
+  const void* __restrict__ Pc;     // [9][18][N] double (FP64 form) or blocked [tiles][9 18][kTC] float
   const double* __restrict__ mom;
   const double* __restrict__ inv_h;
   __nv_bfloat16* __restrict__ X;  // [N][32]
@@ -22,13 +23,61 @@ struct FeatArgs {
   float gam;
 };
 
-template <typename PT>
+// features 24-31 from the central coefficients ao[v][k] (xi units) of the
+// five variables, then the BF16 row (and the FP32 row when asked for)
+__device__ __forceinline__ void features_finish(float F[32], const float (&ao)[5][9], const float S[6], float rf,
+                                                float c, const float u[3], float ih, const FeatArgs& a, int i) {
+  const float sc5[5] = {rf, rf * c, rf * c, rf * c, rf * c * c};
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float* o = ao[v];
+    auto quad = [&](float x0, float x1, float x2) {
+      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 + 2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+    };
+    const float SI = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + quad(2.f * o[3], o[6], o[7]) +
+                     quad(o[6], 2.f * o[4], o[8]) + quad(o[7], o[8], 2.f * o[5]) +
+                     4.f * (o[3] * o[3] + o[4] * o[4] + o[5] * o[5]) + o[6] * o[6] + o[7] * o[7] + o[8] * o[8];
+    const float q = 0.1f * sc5[v];
+    F[24 + v] = SI / (SI + q * q);
+  }
+  // p_opt gradient at the centroid: linear coefficients / h
+  const float h = 1.f / ih;
+  float gu[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; q++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) gu[q][j] = (ao[1 + q][j] - u[q] * ao[0][j]) * ih / rf;
+  const float wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
+  F[29] = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / c;
+  F[30] = h * fabsf(gu[0][0] + gu[1][1] + gu[2][2]) / c;
+  F[31] = h * sqrtf(wx * wx + wy * wy + wz * wz) / c;
+  uint4* dst = reinterpret_cast<uint4*>(a.X + (size_t)i * 32);
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    uint4 w;
+    __nv_bfloat162 b0 = __floats2bfloat162_rn(F[8 * q + 0], F[8 * q + 1]);
+    __nv_bfloat162 b1 = __floats2bfloat162_rn(F[8 * q + 2], F[8 * q + 3]);
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(F[8 * q + 4], F[8 * q + 5]);
+    __nv_bfloat162 b3 = __floats2bfloat162_rn(F[8 * q + 6], F[8 * q + 7]);
+    w.x = *reinterpret_cast<uint32_t*>(&b0);
+    w.y = *reinterpret_cast<uint32_t*>(&b1);
+    w.z = *reinterpret_cast<uint32_t*>(&b2);
+    w.w = *reinterpret_cast<uint32_t*>(&b3);
+    dst[q] = w;
+  }
+  if (a.Xf) {
+#pragma unroll
+    for (int q = 0; q < 32; q++) a.Xf[(size_t)i * 32 + q] = F[q];
+  }
+}
+
+// FP64 form: differences of the FP64 state, FP64 pseudo-inverse rows
 __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
   constexpr int K = 9, MC = 18;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   const size_t N = a.N;
-  const PT* __restrict__ Pc = reinterpret_cast<const PT*>(a.Pc);
+  const double* __restrict__ Pc = reinterpret_cast<const double*>(a.Pc);
   const double g = a.gam;
   double Ui[5];
 #pragma unroll
@@ -68,50 +117,78 @@ __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
   float S[6];
 #pragma unroll
   for (int q = 0; q < 6; q++) S[q] = (float)a.mom[q * N + i];
-  const float rf = (float)r;
-  const float sc5[5] = {rf, rf * c, rf * c, rf * c, rf * c * c};
-#pragma unroll
-  for (int v = 0; v < 5; v++) {
-    const float* o = ao[v];
-    auto quad = [&](float x0, float x1, float x2) {
-      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 + 2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
-    };
-    const float SI = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + quad(2.f * o[3], o[6], o[7]) +
-                     quad(o[6], 2.f * o[4], o[8]) + quad(o[7], o[8], 2.f * o[5]) +
-                     4.f * (o[3] * o[3] + o[4] * o[4] + o[5] * o[5]) + o[6] * o[6] + o[7] * o[7] + o[8] * o[8];
-    const float q = 0.1f * sc5[v];
-    F[24 + v] = SI / (SI + q * q);
-  }
-  // p_opt gradient at the centroid: linear coefficients / h
-  const float ih = (float)a.inv_h[i], h = 1.f / ih;
   const float u[3] = {(float)(Ui[1] * ir), (float)(Ui[2] * ir), (float)(Ui[3] * ir)};
-  float gu[3][3];
+  features_finish(F, ao, S, (float)r, c, u, (float)a.inv_h[i], a, i);
+}
+
+// mixed form: stencil differences from the float pair of the state (exact
+// leading-part subtraction, as in the reconstruction), FP32 arithmetic,
+// blocked FP32 pseudo-inverse rows
+__global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
+  constexpr int K = 9, MC = 18;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  const size_t N = a.N;
+  const float* __restrict__ Pc = reinterpret_cast<const float*>(a.Pc);
+  const float2* __restrict__ hl2 = reinterpret_cast<const float2*>(a.Uhl);  // a row is 5 float2
+  const float g = a.gam;
+  float hi[5], lo[5];
+  {
+    float t[10];
 #pragma unroll
-  for (int q = 0; q < 3; q++)
+    for (int q = 0; q < 5; q++) {
+      const float2 w = __ldg(&hl2[(size_t)i * 5 + q]);
+      t[2 * q] = w.x;
+      t[2 * q + 1] = w.y;
+    }
 #pragma unroll
-    for (int j = 0; j < 3; j++) gu[q][j] = (ao[1 + q][j] - u[q] * ao[0][j]) * ih / rf;
-  const float wx = gu[2][1] - gu[1][2], wy = gu[0][2] - gu[2][0], wz = gu[1][0] - gu[0][1];
-  F[29] = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / c;
-  F[30] = h * fabsf(gu[0][0] + gu[1][1] + gu[2][2]) / c;
-  F[31] = h * sqrtf(wx * wx + wy * wy + wz * wz) / c;
-  uint4* dst = reinterpret_cast<uint4*>(a.X + (size_t)i * 32);
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    uint4 w;
-    __nv_bfloat162 b0 = __floats2bfloat162_rn(F[8 * q + 0], F[8 * q + 1]);
-    __nv_bfloat162 b1 = __floats2bfloat162_rn(F[8 * q + 2], F[8 * q + 3]);
-    __nv_bfloat162 b2 = __floats2bfloat162_rn(F[8 * q + 4], F[8 * q + 5]);
-    __nv_bfloat162 b3 = __floats2bfloat162_rn(F[8 * q + 6], F[8 * q + 7]);
-    w.x = *reinterpret_cast<uint32_t*>(&b0);
-    w.y = *reinterpret_cast<uint32_t*>(&b1);
-    w.z = *reinterpret_cast<uint32_t*>(&b2);
-    w.w = *reinterpret_cast<uint32_t*>(&b3);
-    dst[q] = w;
+    for (int v = 0; v < 5; v++) {
+      hi[v] = t[v];
+      lo[v] = t[5 + v];
+    }
   }
-  if (a.Xf) {
+  const float r = hi[0] + lo[0], ir = 1.f / r;
+  const float mx = hi[1] + lo[1], my = hi[2] + lo[2], mz = hi[3] + lo[3];
+  const float p = (g - 1.f) * ((hi[4] + lo[4]) - 0.5f * (mx * mx + my * my + mz * mz) * ir);
+  const float ip = 1.f / p;
+  const float c = sqrtf(g * p * ir);
+  float F[32];
+  float ao[5][K];
 #pragma unroll
-    for (int q = 0; q < 32; q++) a.Xf[(size_t)i * 32 + q] = F[q];
+  for (int v = 0; v < 5; v++)
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[v][k] = 0.f;
+#pragma unroll
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[blk(m, MC, i)]);
+    float t[10];
+#pragma unroll
+    for (int q = 0; q < 5; q++) {
+      const float2 w = __ldg(&hl2[(size_t)j * 5 + q]);
+      t[2 * q] = w.x;
+      t[2 * q + 1] = w.y;
+    }
+    float d[5];
+#pragma unroll
+    for (int v = 0; v < 5; v++) d[v] = (t[v] - hi[v]) + (t[5 + v] - lo[v]);
+    F[m] = d[0] * ir;
+    if (m < 6) {
+      const float rj = t[0] + t[5], mjx = t[1] + t[6], mjy = t[2] + t[7], mjz = t[3] + t[8];
+      const float pj = (g - 1.f) * ((t[4] + t[9]) - 0.5f * (mjx * mjx + mjy * mjy + mjz * mjz) / rj);
+      F[18 + m] = (pj - p) * ip;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const float P = __ldg(&Pc[blk(k * MC + m, K * MC, i)]);
+#pragma unroll
+      for (int v = 0; v < 5; v++) ao[v][k] = fmaf(P, d[v], ao[v][k]);
+    }
   }
+  float S[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) S[q] = (float)a.mom[q * N + i];
+  const float u[3] = {mx * ir, my * ir, mz * ir};
+  features_finish(F, ao, S, r, c, u, (float)a.inv_h[i], a, i);
 }
 
 __global__ void k_count_flags(const uint8_t* __restrict__ flag, int N, unsigned long long* __restrict__ count) {

@@ -18,6 +18,7 @@
 // (U* - U = r U + ...), which keeps every FP32 term O(1).
 #pragma once
 
+#include "bulk.cuh"
 #include "kernels.cuh"
 
 namespace ucns {
@@ -27,16 +28,44 @@ struct FluxConstF {
   float p_ref, H_ref;  // reference pressure and enthalpy E_ref + p_ref
 };
 
+// The mixed form keeps its per-cell precompute in a blocked layout: cells in
+// tiles of kTC consecutive (Morton-ordered) cells, and for every tile all rows
+// of an array [rows][kTC] contiguous, so that one bulk copy brings a tile's
+// pseudo-inverse rows (or stencil lists) into shared memory.  Cells past N in
+// the last tile are zero rows.
+constexpr int kTC = 64;
+
+// index of (row, cell i) in a blocked array [ceil(N / kTC)][rows][kTC]
+__host__ __device__ __forceinline__ size_t blk(int row, int rows, int64_t i) {
+  return ((size_t)(i / kTC) * rows + row) * kTC + (size_t)(i % kTC);
+}
+
+template <int ORDER, bool WENO, int ND>
+struct ReconTile {
+  static constexpr int K = ORDER == 1 ? 3 : 9;
+  static constexpr int MC = 2 * K, MD = 6;
+  static constexpr int RC = K * MC;                 // central pseudo-inverse rows
+  static constexpr int RD = WENO ? ND * 3 * MD : 0;  // directional pseudo-inverse rows
+  static constexpr int SD = WENO ? ND * MD : 0;      // directional stencil rows
+  static constexpr int CS = ORDER == 1 ? 20 : 52;    // floats per output row: 5 (K+1) rounded up to 4
+  // shared memory of one tile: central rows and stencil, directional rows and
+  // stencils when staged, the tile's output rows, the mbarrier
+  static constexpr size_t smem(bool stage_dir) {
+    return (size_t)(RC + MC + (stage_dir ? RD + SD : 0)) * kTC * 4 + (size_t)kTC * CS * 4 + 16;
+  }
+};
+
 struct ReconArgsMx {
   const float* __restrict__ Uhl;  // [N][10]: hi = fl(U) of the 5 variables, then lo = fl(U - hi)
-  const int32_t* __restrict__ sc;
-  const float* __restrict__ Pc;
-  const int32_t* __restrict__ sd;
-  const float* __restrict__ Pd;
+  const int32_t* __restrict__ sc;  // blocked [tiles][MC][kTC]
+  const float* __restrict__ Pc;    // blocked [tiles][K MC][kTC], row k MC + m
+  const int32_t* __restrict__ sd;  // blocked [tiles][nd Md][kTC]
+  const float* __restrict__ Pd;    // blocked [tiles][nd 3 Md][kTC], row (s 3 + k) Md + r
   const double* __restrict__ mom;  // [6][N]
   const float* __restrict__ inv_h;  // [N]
   float* __restrict__ coef;        // [N][cs]: coefficient k of variable v at k*5 + v, slot 0 relative to U_ref
   const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
+  int* err;                        // bit 1 set when a bounded wait gave up
   int N;
   int cs;  // floats per cell row of coef (5 (K+1) rounded up to a multiple of 4)
   float lam0, lams, eps;
@@ -56,108 +85,154 @@ struct FaceArgsMx {
   FluxConstF c;
 };
 
-// thread = (cell i, variable v); GATED: cells whose gate flag is 0 take the
-// linear weights (a separate instantiation, so the ungated kernel has no
-// data-dependent branch around the directional loads)
+// One block per tile of kTC cells, thread = (cell c of the tile, variable v).
+// A single thread starts bulk copies of the tile's central pseudo-inverse rows
+// and stencil (and, ungated CWENOZ, its directional rows and stencils) into
+// shared memory; meanwhile every thread loads its own state and moments.  The
+// coefficient rows are assembled in shared memory and written back with one
+// bulk copy.  GATED: cells whose gate flag is 0 take the linear weights and
+// the flagged cells read their directional rows directly (a separate
+// instantiation, so the ungated kernel has no data-dependent branch around
+// the directional loads).
 template <int ORDER, bool WENO, int ND, bool GATED>
-__global__ void __launch_bounds__(256, 4) k_recon_mx(ReconArgsMx a) {
-  constexpr int K = ORDER == 1 ? 3 : 9;
-  constexpr int MC = 2 * K;
-  constexpr int MD = 6;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = tid / 5, v = tid - 5 * (tid / 5);
-  if (i >= a.N) return;
-  const int N = a.N;
+__global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(ReconArgsMx a) {
+  using T = ReconTile<ORDER, WENO, ND>;
+  constexpr int K = T::K, MC = T::MC, MD = T::MD, CS = T::CS;
+  constexpr bool STAGE_D = WENO && !GATED;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* sP = reinterpret_cast<float*>(smem);
+  int32_t* sS = reinterpret_cast<int32_t*>(sP + T::RC * kTC);
+  float* sPd = reinterpret_cast<float*>(sS + MC * kTC);
+  int32_t* sSd = reinterpret_cast<int32_t*>(sPd + (STAGE_D ? T::RD * kTC : 0));
+  float* sOut = reinterpret_cast<float*>(sSd + (STAGE_D ? T::SD * kTC : 0));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sOut + kTC * CS);
+  const int tile = blockIdx.x, i0 = tile * kTC;
+  const int nc = min(kTC, a.N - i0);
+  const int t = threadIdx.x, c = t / 5, v = t - 5 * (t / 5);
+  if (t == 0) bar_init(bar);
+  __syncthreads();
+  if (t == 0) {
+    constexpr uint32_t bp = T::RC * kTC * 4, bs = MC * kTC * 4, bpd = T::RD * kTC * 4, bsd = T::SD * kTC * 4;
+    bar_expect(bar, bp + bs + (STAGE_D ? bpd + bsd : 0));
+    bulk_load(sP, a.Pc + (size_t)tile * T::RC * kTC, bp, bar);
+    bulk_load(sS, a.sc + (size_t)tile * MC * kTC, bs, bar);
+    if (STAGE_D) {
+      bulk_load(sPd, a.Pd + (size_t)tile * T::RD * kTC, bpd, bar);
+      bulk_load(sSd, a.sd + (size_t)tile * T::SD * kTC, bsd, bar);
+    }
+  }
+  const bool live = c < nc;
+  const int i = i0 + (live ? c : 0);
   const float* __restrict__ hl = a.Uhl;
   const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
-  // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
-  // within a factor 2 (Sterbenz), so the difference carries no cancellation
-  // error beyond the final FP32 rounding, as an FP64 subtraction would.
-  auto diff = [&](int j) { return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i); };
-  float ao[K];
-#pragma unroll
-  for (int k = 0; k < K; k++) ao[k] = 0.f;
-#pragma unroll 6
-  for (int m = 0; m < MC; m++) {
-    const float d = diff(__ldg(&a.sc[(size_t)m * N + i]));
-#pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
-  }
-  float c[K];
   float S[6];
   if (ORDER == 2) {
 #pragma unroll
-    for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * N + i]);
+    for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * a.N + i]);
   }
+  const float ih = __ldg(&a.inv_h[i]);
   bool weno = WENO;
   if (GATED) weno = weno && a.gate[i];
-  if (!weno) {
+  const bool ok = bar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (t == 0) atomicOr(a.err, 2);
+    bar_wait(bar, 0);  // the copies into this block's shared memory end before it exits
+    return;
+  }
+  if (live) {
+    // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
+    // within a factor 2 (Sterbenz), so the difference carries no cancellation
+    // error beyond the final FP32 rounding, as an FP64 subtraction would.
+    auto diff = [&](int j) { return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i); };
+    float ao[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) c[k] = ao[k];
-  } else {
-    float b[ND][3];
+    for (int k = 0; k < K; k++) ao[k] = 0.f;
+#pragma unroll 6
+    for (int m = 0; m < MC; m++) {
+      const float d = diff(sS[m * kTC + c]);
 #pragma unroll
-    for (int s = 0; s < ND; s++) {
-      b[s][0] = b[s][1] = b[s][2] = 0.f;
+      for (int k = 0; k < K; k++) ao[k] = fmaf(sP[(k * MC + m) * kTC + c], d, ao[k]);
+    }
+    float cf[K];
+    if (!weno) {
 #pragma unroll
-      for (int r = 0; r < MD; r++) {
-        const float d = diff(__ldg(&a.sd[((size_t)s * MD + r) * N + i]));
+      for (int k = 0; k < K; k++) cf[k] = ao[k];
+    } else {
+      float b[ND][3];
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-          b[s][k] = fmaf(__ldg(&a.Pd[(((size_t)s * 3 + k) * MD + r) * N + i]), d, b[s][k]);
+      for (int s = 0; s < ND; s++) {
+        b[s][0] = b[s][1] = b[s][2] = 0.f;
+#pragma unroll
+        for (int r = 0; r < MD; r++) {
+          const int j = STAGE_D ? sSd[(s * MD + r) * kTC + c] : __ldg(&a.sd[blk(s * MD + r, T::SD, i)]);
+          const float d = diff(j);
+#pragma unroll
+          for (int k = 0; k < 3; k++) {
+            const int row = (s * 3 + k) * MD + r;
+            const float P = STAGE_D ? sPd[row * kTC + c] : __ldg(&a.Pd[blk(row, T::RD, i)]);
+            b[s][k] = fmaf(P, d, b[s][k]);
+          }
+        }
+      }
+      const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
+      const float qy0 = ao[6], qy1 = 2.f * ao[4], qy2 = ao[8];
+      const float qz0 = ao[7], qz1 = ao[8], qz2 = 2.f * ao[5];
+      auto quad = [&](float x0, float x1, float x2) {
+        return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 +
+               2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+      };
+      const float SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) +
+                        quad(qy0, qy1, qy2) + quad(qz0, qz1, qz2) +
+                        4.f * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
+                        ao[7] * ao[7] + ao[8] * ao[8];
+      float SI[ND];
+      float tau = 0.f;
+#pragma unroll
+      for (int s = 0; s < ND; s++) {
+        SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+        tau += fabsf(SI0 - SI[s]);
+      }
+      tau *= (1.f / ND);
+      const float w0 = a.lam0 * (1.f + tau / (a.eps + SI0));
+      float ws[ND];
+      float wsum = w0;
+#pragma unroll
+      for (int s = 0; s < ND; s++) {
+        ws[s] = a.lams * (1.f + tau / (a.eps + SI[s]));
+        wsum += ws[s];
+      }
+      const float iws = 1.f / wsum;
+      const float r0 = (w0 * iws) / a.lam0;
+#pragma unroll
+      for (int k = 0; k < K; k++) cf[k] = r0 * ao[k];
+#pragma unroll
+      for (int s = 0; s < ND; s++) {
+        const float e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+        for (int k = 0; k < 3; k++) cf[k] = fmaf(e, b[s][k], cf[k]);
       }
     }
-    const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
-    const float qy0 = ao[6], qy1 = 2.f * ao[4], qy2 = ao[8];
-    const float qz0 = ao[7], qz1 = ao[8], qz2 = 2.f * ao[5];
-    auto quad = [&](float x0, float x1, float x2) {
-      return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 +
-             2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
-    };
-    const float SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) +
-                      quad(qy0, qy1, qy2) + quad(qz0, qz1, qz2) +
-                      4.f * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
-                      ao[7] * ao[7] + ao[8] * ao[8];
-    float SI[ND];
-    float tau = 0.f;
+    // constant term relative to the reference state U_ref = (1, 0, 0, 0, E_ref)
+    float c0 = v == 0 ? (hi_i - 1.f) + lo_i
+                      : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
+    if (ORDER == 2) {
 #pragma unroll
-    for (int s = 0; s < ND; s++) {
-      SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
-      tau += fabsf(SI0 - SI[s]);
+      for (int q = 0; q < 6; q++) c0 = fmaf(-cf[3 + q], S[q], c0);
     }
-    tau *= (1.f / ND);
-    const float w0 = a.lam0 * (1.f + tau / (a.eps + SI0));
-    float ws[ND];
-    float wsum = w0;
+    // physical units: linear coefficients / h, quadratic / h^2
+    const float ih2 = ih * ih;
+    float* out = sOut + c * CS + v;
+    out[0] = c0;
 #pragma unroll
-    for (int s = 0; s < ND; s++) {
-      ws[s] = a.lams * (1.f + tau / (a.eps + SI[s]));
-      wsum += ws[s];
-    }
-    const float iws = 1.f / wsum;
-    const float r0 = (w0 * iws) / a.lam0;
+    for (int k = 0; k < K; k++) out[(k + 1) * 5] = cf[k] * (k < 3 ? ih : ih2);
+    if (v == 0) {
 #pragma unroll
-    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
-#pragma unroll
-    for (int s = 0; s < ND; s++) {
-      const float e = ws[s] * iws - r0 * a.lams;
-#pragma unroll
-      for (int k = 0; k < 3; k++) c[k] = fmaf(e, b[s][k], c[k]);
+      for (int q = 5 * (K + 1); q < CS; q++) sOut[c * CS + q] = 0.f;
     }
   }
-  // constant term relative to the reference state U_ref = (1, 0, 0, 0, E_ref)
-  float c0 = v == 0 ? (hi_i - 1.f) + lo_i
-                    : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
-  if (ORDER == 2) {
-#pragma unroll
-    for (int q = 0; q < 6; q++) c0 = fmaf(-c[3 + q], S[q], c0);
-  }
-  // physical units: linear coefficients / h, quadratic / h^2
-  const float ih = __ldg(&a.inv_h[i]), ih2 = ih * ih;
-  float* out = a.coef + (size_t)i * a.cs + v;
-  out[0] = c0;
-#pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * 5] = c[k] * (k < 3 ? ih : ih2);
+  fence_smem_to_async();
+  __syncthreads();
+  if (t == 0) bulk_store(a.coef + (size_t)i0 * CS, sOut, (uint32_t)(nc * CS * 4));
 }
 
 // float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5

@@ -35,8 +35,12 @@ struct DeviceMesh {
   double* Pc = nullptr;       // [K][Mc][N] central pseudo-inverse
   int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
   double* Pd = nullptr;       // [nd][3][Md][N]
-  float* Pcf = nullptr;       // FP32 copies (mixed precision)
-  float* Pdf = nullptr;
+  // mixed precision: FP32 pseudo-inverses and the stencils in the blocked
+  // layout [ceil(N/64)][rows][64] (tiles of 64 consecutive cells)
+  float* Pcb = nullptr;       // rows k Mc + m
+  float* Pdb = nullptr;       // rows (s 3 + k) Md + r
+  int32_t* scb = nullptr;     // rows m
+  int32_t* sdb = nullptr;     // rows s Md + r
   float* inv_hf = nullptr;    // [N]
   float* fpenf = nullptr;     // [F]
   int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)

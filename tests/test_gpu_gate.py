@@ -80,10 +80,14 @@ def test_mlp_training_learns_a_separable_rule():
     assert np.mean((z > 0) == (y > 0.5)) > 0.95
 
 
-def test_features_and_labels_match_oracle():
-    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=4)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_features_and_labels_match_oracle(prec):
+    """FP64 form: features from FP64 differences; mixed form: from the float
+    pair of the state in FP32 arithmetic (9^3 cells: a ragged last tile of the
+    blocked layout).  Labels need the FP64 CWENOZ weights (FP64 form only)."""
+    nodes, cells, box = I.hex_lattice(10 if prec == 0 else 9, jitter=0.1, seed=4)
     U = I.tgv_perturbed_state(nodes, cells, 1.25, 0.05, seed=4)
-    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, Mach=1.25))
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, Mach=1.25, precision=prec))
     oc = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Mach=1.25))
     Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
     X, Xf = m.gate_features(Ug, want_f32=True)
@@ -94,6 +98,8 @@ def test_features_and_labels_match_oracle():
     # BF16 rows are the rounded FP32 features
     Xb = m.to_user(X.float().cpu().numpy().astype(np.float64).T).T
     assert np.array_equal(Xb, omlp.bf16(F))
+    if prec == 1:
+        return
     dev = m.to_user(m.gate_labels(Ug).cpu().numpy().astype(np.float64)[None])[0]
     odev, _ = oc.labels(U)
     assert np.abs(dev - odev).max() <= 1e-6

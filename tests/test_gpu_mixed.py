@@ -24,13 +24,16 @@ def _mesh(nodes, cells, box, prec, **kw):
     return ucns.Mesh(nodes, cells, box, ucns.Params(precision=prec, **kw))
 
 
-@pytest.mark.parametrize("tets,mach", [(False, 0.1), (False, 1.25), (True, 0.1)])
-def test_mixed_residual_error_vs_oracle(tets, mach):
-    nodes, cells, box = I.hex_lattice(10 if not tets else 6, jitter=0.1, seed=5)
+@pytest.mark.parametrize("tets,mach,order,scheme,n", [
+    (False, 0.1, 2, 1, 10), (False, 1.25, 2, 1, 10), (True, 0.1, 2, 1, 6),
+    # 9^3 = 729 cells: 11 full tiles of 64 cells and a ragged one of 25
+    (False, 0.1, 1, 0, 9), (False, 0.1, 2, 0, 9), (False, 1.25, 2, 1, 9)])
+def test_mixed_residual_error_vs_oracle(tets, mach, order, scheme, n):
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=5)
     if tets:
         cells = I.split_tets(cells)
-    m = _mesh(nodes, cells, box, 1, Mach=mach)
-    oc = O.Case(nodes, cells, box, O.Params(Mach=mach))
+    m = _mesh(nodes, cells, box, 1, Mach=mach, order=order, scheme=scheme)
+    oc = O.Case(nodes, cells, box, O.Params(Mach=mach, order=order, scheme=scheme))
     U = I.tgv_perturbed_state(nodes, cells, mach, 0.05, seed=4)
     Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
     R = m.to_user(m.residual(Ug).cpu().numpy())

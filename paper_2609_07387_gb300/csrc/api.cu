@@ -184,7 +184,7 @@ int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   a.fo = m->d.fo;
   a.fn = m->d.fn;
   a.inv_h = m->d.inv_hf;
-  a.G = m->d.G;
+  a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.cs = coef_row_floats(m);
@@ -280,10 +280,15 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
   a.F = (int)m->F;
   a.gm1 = m->P.gamma - 1.0;
   const unsigned g = nblocks((size_t)m->N);
-#define UCNS_RK(ST)                                                     \
-  do {                                                                  \
-    if (m->nfc == 6) k_rk<ST, 6><<<g, 256, 0, s>>>(a);                  \
-    else k_rk<ST, 4><<<g, 256, 0, s>>>(a);                              \
+#define UCNS_RK(ST)                                                           \
+  do {                                                                        \
+    if (mixed(m)) {                                                           \
+      if (m->nfc == 6) k_rk<ST, 6, float><<<g, 256, 0, s>>>(a);               \
+      else k_rk<ST, 4, float><<<g, 256, 0, s>>>(a);                           \
+    } else {                                                                  \
+      if (m->nfc == 6) k_rk<ST, 6, double><<<g, 256, 0, s>>>(a);              \
+      else k_rk<ST, 4, double><<<g, 256, 0, s>>>(a);                          \
+    }                                                                         \
   } while (0)
   switch (stage) {
     case 0: UCNS_RK(0); break;

@@ -52,7 +52,7 @@ struct RKArgs {
   const double* U0;  // U^n        (may alias out in stage 3)
   const double* Us;  // U^(s)      (may alias out)
   double* out;       // U^(s+1)
-  const double* __restrict__ G;
+  const void* __restrict__ G;      // [5][F]: double (FP64 form) or float (mixed form)
   const int32_t* __restrict__ cf;  // [nfc][N]
   const double* __restrict__ inv_vol;
   const double* __restrict__ dt;
@@ -362,16 +362,35 @@ __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
 
 // ------------------------------------------- residual + Runge-Kutta stage
 template <int NFC>
-__device__ __forceinline__ double face_sum(const RKArgs& a, int i, int v) {
+__device__ __forceinline__ double face_sum(const RKArgs& a, const double* __restrict__ G, int i, int v) {
   double s = 0.0;
 #pragma unroll
   for (int j = 0; j < NFC; j++) {
     const int e = __ldg(&a.cf[(size_t)j * a.N + i]);
     // sigma G_f: the neighbour side flips the sign bit (an integer XOR, not an FP64 op)
-    const long long gb = __double_as_longlong(__ldg(&a.G[(size_t)v * a.F + (e >> 1)]));
+    const long long gb = __double_as_longlong(__ldg(&G[(size_t)v * a.F + (e >> 1)]));
     s += __longlong_as_double(gb ^ ((long long)(e & 1) << 63));
   }
   return s;
+}
+
+// FP32 face totals: the sum is carried as an unevaluated pair s + e of floats
+// by error-free transformations (Knuth's TwoSum), so that it keeps the
+// accuracy of a double-length sum (errors of order u^2 sum |G|, u = 2^-24),
+// and is rounded once to FP64 at the end
+template <int NFC>
+__device__ __forceinline__ double face_sum(const RKArgs& a, const float* __restrict__ G, int i, int v) {
+  float s = 0.f, e = 0.f;
+#pragma unroll
+  for (int j = 0; j < NFC; j++) {
+    const int c = __ldg(&a.cf[(size_t)j * a.N + i]);
+    const int gb = __float_as_int(__ldg(&G[(size_t)v * a.F + (c >> 1)]));
+    const float x = __int_as_float(gb ^ ((c & 1) << 31));
+    const float t = s + x, z = t - s;
+    e += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  return (double)s + (double)e;
 }
 
 // rho > 0 and p > 0 (p > 0  <=>  2 rho E - |m|^2 > 0 for rho > 0), all finite
@@ -382,15 +401,16 @@ __device__ __forceinline__ bool physical(const double U[5]) {
 
 // STAGE 0: plain residual R = -(1/V) sum sigma G -> out
 // STAGE 1: U1 = U0 + dt R;  2: U2 = 3/4 U0 + 1/4 (U1 + dt R);  3: U = 1/3 U0 + 2/3 (U2 + dt R)
-template <int STAGE, int NFC>
+template <int STAGE, int NFC, typename GT>
 __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
+  const GT* __restrict__ G = reinterpret_cast<const GT*>(a.G);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   const double ivol = a.inv_vol[i];
   const size_t N = a.N;
   if (STAGE == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) a.out[v * N + i] = -face_sum<NFC>(a, i, v) * ivol;
+    for (int v = 0; v < 5; v++) a.out[v * N + i] = -face_sum<NFC>(a, G, i, v) * ivol;
     return;
   }
   // dt R = w s with w = -dt/|V_i| and s the signed face sum
@@ -398,7 +418,7 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
   double Un[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const double s = face_sum<NFC>(a, i, v);
+    const double s = face_sum<NFC>(a, G, i, v);
     const double u0 = a.U0[v * N + i];
     if (STAGE == 1) {
       Un[v] = fma(w, s, u0);                                     // U0 + dt R

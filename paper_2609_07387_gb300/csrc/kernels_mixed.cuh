@@ -35,6 +35,15 @@ struct FluxConstF {
 // the last tile are zero rows.
 constexpr int kTC = 64;
 
+// FP32 division and square root of the mixed form: the hardware approximate
+// reciprocal and reciprocal square root (at most 2 ulp: CUDA's __fdividef and
+// rsqrtf), an error of the order of the FP32 rounding that the operands
+// already carry.  For a physical state every divisor here is a nonzero
+// number of moderate magnitude (densities, sound-speed sums, smoothness sums
+// plus epsilon, wave-speed differences) and every radicand is positive.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fsqrt(float x) { return x * rsqrtf(x); }
+
 // index of (row, cell i) in a blocked array [ceil(N / kTC)][rows][kTC]
 __host__ __device__ __forceinline__ size_t blk(int row, int rows, int64_t i) {
   return ((size_t)(i / kTC) * rows + row) * kTC + (size_t)(i % kTC);
@@ -79,7 +88,7 @@ struct FaceArgsMx {
   const int32_t* __restrict__ fo;
   const int32_t* __restrict__ fn;
   const float* __restrict__ inv_h;
-  double* __restrict__ G;  // [5][F]
+  float* __restrict__ G;  // [5][F] FP32 face totals
   int N, F;
   int cs;
   FluxConstF c;
@@ -193,16 +202,16 @@ __global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(
         tau += fabsf(SI0 - SI[s]);
       }
       tau *= (1.f / ND);
-      const float w0 = a.lam0 * (1.f + tau / (a.eps + SI0));
+      const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
       float ws[ND];
       float wsum = w0;
 #pragma unroll
       for (int s = 0; s < ND; s++) {
-        ws[s] = a.lams * (1.f + tau / (a.eps + SI[s]));
+        ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
         wsum += ws[s];
       }
-      const float iws = 1.f / wsum;
-      const float r0 = (w0 * iws) / a.lam0;
+      const float iws = fdiv(1.f, wsum);
+      const float r0 = fdiv(w0 * iws, a.lam0);
 #pragma unroll
       for (int k = 0; k < K; k++) cf[k] = r0 * ao[k];
 #pragma unroll
@@ -300,7 +309,7 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
 __device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5], const float n[3],
                                              const FluxConstF& c, float F[5]) {
   const float rL = 1.f + WL[0], rR = 1.f + WR[0];
-  const float irL = 1.f / rL, irR = 1.f / rR;
+  const float irL = fdiv(1.f, rL), irR = fdiv(1.f, rR);
   const float uL[3] = {WL[1] * irL, WL[2] * irL, WL[3] * irL};
   const float uR[3] = {WR[1] * irR, WR[2] * irR, WR[3] * irR};
   const float ppL = c.gm1 * (WL[4] - 0.5f * (WL[1] * uL[0] + WL[2] * uL[1] + WL[3] * uL[2]));
@@ -308,18 +317,18 @@ __device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5
   const float pL = c.p_ref + ppL, pR = c.p_ref + ppR;
   const float unL = uL[0] * n[0] + uL[1] * n[1] + uL[2] * n[2];
   const float unR = uR[0] * n[0] + uR[1] * n[1] + uR[2] * n[2];
-  const float aL = sqrtf(c.gam * pL * irL), aR = sqrtf(c.gam * pR * irR);
-  const float sL = sqrtf(rL), sR = sqrtf(rR), iw = 1.f / (sL + sR);
+  const float aL = fsqrt(c.gam * pL * irL), aR = fsqrt(c.gam * pR * irR);
+  const float sL = fsqrt(rL), sR = fsqrt(rR), iw = fdiv(1.f, sL + sR);
   const float ut0 = (sL * uL[0] + sR * uR[0]) * iw, ut1 = (sL * uL[1] + sR * uR[1]) * iw,
               ut2 = (sL * uL[2] + sR * uR[2]) * iw;
   // total enthalpy H = (E + p)/rho = (H_ref + E' + p')/rho
   const float Ht = (sL * (c.H_ref + WL[4] + ppL) * irL + sR * (c.H_ref + WR[4] + ppR) * irR) * iw;
-  const float at = sqrtf(c.gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
+  const float at = fsqrt(c.gm1 * (Ht - 0.5f * (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)));
   const float utn = ut0 * n[0] + ut1 * n[1] + ut2 * n[2];
   const float SL = fminf(unL - aL, utn - at);
   const float SR = fmaxf(unR + aR, utn + at);
   const float mL = rL * (SL - unL), mR = rR * (SR - unR);
-  const float Ss = (ppR - ppL + unL * mL - unR * mR) / (mL - mR);
+  const float Ss = fdiv(ppR - ppL + unL * mL - unR * mR, mL - mR);
   // physical flux of the upwind side (momentum with p', energy with the full E + p)
   auto phys = [&](const float W[5], float r, const float u[3], float pp, float un) {
     F[0] = r * un;
@@ -332,14 +341,14 @@ __device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5
     // U* - U with r* = (S* - u_n)/(S - S*): d_rho = rho r*, d_m = r* m + rho*(S* - u_n) n,
     // d_E = r* E + rho* (S* - u_n)(S* + p/(rho (S - u_n)))
     const float ds = Ss - un;
-    const float rs = ds / (S - Ss);
+    const float rs = fdiv(ds, S - Ss);
     const float rho_s = r + r * rs;
     const float E = (c.H_ref - c.p_ref) + W[4];
     F[0] += S * (r * rs);
     F[1] += S * fmaf(rho_s * ds, n[0], rs * W[1]);
     F[2] += S * fmaf(rho_s * ds, n[1], rs * W[2]);
     F[3] += S * fmaf(rho_s * ds, n[2], rs * W[3]);
-    F[4] += S * fmaf(rho_s * ds, Ss + p / m, rs * E);
+    F[4] += S * fmaf(rho_s * ds, Ss + fdiv(p, m), rs * E);
   };
   if (0.f <= SL) {
     phys(WL, rL, uL, ppL, unL);
@@ -358,7 +367,7 @@ __device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5
 __device__ __forceinline__ void viscous_flux_mx(const float W[5], const float g[5][3], const float n[3],
                                                 const FluxConstF& c, float Fv[5]) {
   const float r = 1.f + W[0];
-  const float ir = 1.f / r;
+  const float ir = fdiv(1.f, r);
   const float u[3] = {W[1] * ir, W[2] * ir, W[3] * ir};
   float gu[3][3];
 #pragma unroll
@@ -432,7 +441,7 @@ __global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
     for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
   if (live && q == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = (double)flux[v];
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = flux[v];
   }
 }
 

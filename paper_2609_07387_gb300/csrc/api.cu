@@ -47,6 +47,16 @@ int upload_f32(float** dst, const std::vector<double>& src) {
   return upload(dst, f);
 }
 
+// [rows][N] -> cell-contiguous [N][rows], converted to T
+template <typename T, typename S>
+int upload_cellwise(T** dst, const std::vector<S>& src, int rows, int64_t N) {
+  if (src.empty()) return UCNS_OK;
+  std::vector<T> b((size_t)N * rows);
+  for (int r = 0; r < rows; r++)
+    for (int64_t i = 0; i < N; i++) b[(size_t)i * rows + r] = (T)src[(size_t)r * N + i];
+  return upload(dst, b);
+}
+
 // [rows][N] -> blocked [ceil(N/kTC)][rows][kTC] (zero past N), converted to T
 template <typename T, typename S>
 int upload_blocked(T** dst, const std::vector<S>& src, int rows, int64_t N) {
@@ -135,14 +145,24 @@ bool mixed(const ucns_mesh* m) { return m->P.precision == UCNS_PREC_MIXED; }
 // floats per cell row of the mixed-form coefficients: 5 (K+1) rounded up to 4
 int coef_row_floats(const ucns_mesh* m) { return (5 * m->NC + 3) / 4 * 4; }
 
-template <int ORDER, bool WENO, int ND, bool GATED>
+template <int ORDER, bool WENO, int ND, bool GATED = false>
 int launch_recon_tiles(const ReconArgsMx& a, cudaStream_t s) {
-  constexpr size_t sm = ReconTile<ORDER, WENO, ND>::smem(WENO && !GATED);
+  constexpr size_t sm = ReconTile<ORDER, WENO, ND>::smem();
   if (a.cs != ReconTile<ORDER, WENO, ND>::CS) return fail(UCNS_ERR_INVALID_ARG, "coefficient row size mismatch");
   UCNS_CUDA(cudaFuncSetAttribute(k_recon_mx<ORDER, WENO, ND, GATED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm));
   const unsigned tiles = (unsigned)((a.N + kTC - 1) / kTC);
   k_recon_mx<ORDER, WENO, ND, GATED><<<tiles, kTC * 5, sm, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+// gated P2 CWENOZ: linear rows for every cell, then CWENOZ entries for the flagged
+template <int ND>
+int launch_recon_gated(const ReconArgsMx& a, cudaStream_t s) {
+  int rc = launch_recon_tiles<2, false, 6, true>(a, s);
+  if (rc) return rc;
+  k_recon_fix_mx<ND><<<4 * 152, 256, 0, s>>>(a);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -155,10 +175,14 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.Pc = m->d.Pcb;
   a.sd = m->d.sdb;
   a.Pd = m->d.Pdb;
-  a.mom = m->d.mom;
-  a.inv_h = m->d.inv_hf;
+  a.cell = m->d.cellb;
   a.coef = m->d.coeff;
-  a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
+  a.list = m->gate_list;
+  a.nlist = m->gate_nlist;
+  a.pos = m->gate_pos;
+  a.ao_s = m->gate_ao;
+  a.sda = m->d.sda;
+  a.Pda = m->d.Pda;
   a.err = m->d.err;
   a.N = (int)m->N;
   a.cs = coef_row_floats(m);
@@ -169,11 +193,11 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const bool gated = a.gate != nullptr;
-  if (m->K == 3) return launch_recon_tiles<1, false, 6, false>(a, s);
-  if (m->nd == 0) return launch_recon_tiles<2, false, 6, false>(a, s);
-  if (m->nd == 6) return gated ? launch_recon_tiles<2, true, 6, true>(a, s) : launch_recon_tiles<2, true, 6, false>(a, s);
-  return gated ? launch_recon_tiles<2, true, 4, true>(a, s) : launch_recon_tiles<2, true, 4, false>(a, s);
+  const bool gated = m->gate_eval_active;
+  if (m->K == 3) return launch_recon_tiles<1, false, 6>(a, s);
+  if (m->nd == 0) return launch_recon_tiles<2, false, 6>(a, s);
+  if (m->nd == 6) return gated ? launch_recon_gated<6>(a, s) : launch_recon_tiles<2, true, 6>(a, s);
+  return gated ? launch_recon_gated<4>(a, s) : launch_recon_tiles<2, true, 4>(a, s);
 }
 
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
@@ -183,7 +207,6 @@ int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   a.fpen = m->d.fpenf;
   a.fo = m->d.fo;
   a.fn = m->d.fn;
-  a.inv_h = m->d.inv_hf;
   a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
   a.N = (int)m->N;
   a.F = (int)m->F;
@@ -344,6 +367,7 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
   a.Pc = mixed(m) ? (const void*)m->d.Pcb : (const void*)m->d.Pc;
   a.mom = m->d.mom;
   a.inv_h = m->d.inv_h;
+  a.cell = m->d.cellb;
   a.X = reinterpret_cast<__nv_bfloat16*>(X);
   a.Xf = Xf;
   a.N = (int)m->N;
@@ -368,7 +392,15 @@ int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = 
   if (rc) return rc;
   if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
-    return ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
+    int r = ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
+    if (r) return r;
+    if (mixed(m)) {  // the mixed reconstruction takes the flagged cells as a list
+      UCNS_CUDA(cudaMemsetAsync(m->gate_nlist, 0, sizeof(int32_t), s));
+      k_flag_list<<<nblocks((size_t)m->N), 256, 0, s>>>(m->gate_flag, (int)m->N, m->gate_list, m->gate_pos,
+                                                        m->gate_nlist);
+      UCNS_CUDA(cudaGetLastError());
+    }
+    return UCNS_OK;
   });
   if (rc) return rc;
   m->gate_eval_active = true;
@@ -480,12 +512,18 @@ void device_free(ucns_mesh* m) {
   if (m->gate_X) cudaFree(m->gate_X);
   if (m->gate_flag) cudaFree(m->gate_flag);
   if (m->gate_count) cudaFree(m->gate_count);
+  for (void* p : {(void*)m->gate_list, (void*)m->gate_nlist, (void*)m->gate_pos, (void*)m->gate_ao})
+    if (p) cudaFree(p);
+  m->gate_list = nullptr;
+  m->gate_nlist = nullptr;
+  m->gate_pos = nullptr;
+  m->gate_ao = nullptr;
   m->gate_X = nullptr;
   m->gate_flag = nullptr;
   m->gate_count = nullptr;
   m->gate_eval_active = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb,
+  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uhost, d.red, d.dt, d.err};
   for (void* p : ptrs)
@@ -623,8 +661,14 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   }
   if (p->precision == UCNS_PREC_MIXED) {
     const int rc_rows = m->K * m->Mc, rd_rows = m->nd * 3 * m->Md;
+    std::vector<double> cellrows((size_t)kCellRows * m->N);
+    std::copy(h.mom.begin(), h.mom.begin() + (size_t)6 * m->N, cellrows.begin());
+    std::copy(h.inv_h.begin(), h.inv_h.end(), cellrows.begin() + (size_t)6 * m->N);
     if ((rc = upload_blocked(&d.Pcb, h.Pc, rc_rows, m->N)) || (rc = upload_blocked(&d.Pdb, h.Pd, rd_rows, m->N)) ||
         (rc = upload_blocked(&d.scb, h.sc, m->Mc, m->N)) || (rc = upload_blocked(&d.sdb, h.sd, m->nd * m->Md, m->N)) ||
+        (rc = upload_blocked(&d.cellb, cellrows, kCellRows, m->N)) ||
+        (rc = upload_cellwise(&d.sda, h.sd, m->nd * m->Md, m->N)) ||
+        (rc = upload_cellwise(&d.Pda, h.Pd, rd_rows, m->N)) ||
         (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
@@ -730,8 +774,8 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
     if (mixed(m))
-      k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->d.vol,
-                                                                 m->d.inv_h, (int)m->N, m->d.red);
+      k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC,
+                                                                 m->d.vol, (int)m->N, m->d.red);
     else
       k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
                                                               (int)m->N, m->d.red);
@@ -817,7 +861,9 @@ int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
   if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
   if (mlp && !m->gate_X) {
     if ((rc = alloc((uint8_t**)&m->gate_X, (size_t)m->N * 64)) || (rc = alloc(&m->gate_flag, (size_t)m->N)) ||
-        (rc = alloc(&m->gate_count, 1)))
+        (rc = alloc(&m->gate_count, 1)) || (rc = alloc(&m->gate_list, (size_t)m->N)) ||
+        (rc = alloc(&m->gate_nlist, 1)) || (rc = alloc(&m->gate_pos, (size_t)m->N)) ||
+        (rc = alloc(&m->gate_ao, (size_t)48 * m->N)))
       return rc;
   }
   m->mlp = mlp;

@@ -15,8 +15,9 @@ struct FeatArgs {
   const float* __restrict__ Uhl;   // [N][10] float pair of U (mixed form)
   const int32_t* __restrict__ sc;  // [18][N] (FP64 form) or blocked [tiles][18][kTC] (mixed form)
   const void* __restrict__ Pc;     // [9][18][N] double (FP64 form) or blocked [tiles][9 18][kTC] float
-  const double* __restrict__ mom;
-  const double* __restrict__ inv_h;
+  const double* __restrict__ mom;    // [6][N] (FP64 form)
+  const double* __restrict__ inv_h;  // [N] (FP64 form)
+  const float* __restrict__ cell;    // blocked [tiles][kCellRows][kTC] (mixed form)
   __nv_bfloat16* __restrict__ X;  // [N][32]
   float* __restrict__ Xf;         // [N][32] or null
   int N;
@@ -186,9 +187,9 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
   }
   float S[6];
 #pragma unroll
-  for (int q = 0; q < 6; q++) S[q] = (float)a.mom[q * N + i];
+  for (int q = 0; q < 6; q++) S[q] = __ldg(&a.cell[blk(q, kCellRows, i)]);
   const float u[3] = {mx * ir, my * ir, mz * ir};
-  features_finish(F, ao, S, r, c, u, (float)a.inv_h[i], a, i);
+  features_finish(F, ao, S, r, c, u, __ldg(&a.cell[blk(6, kCellRows, i)]), a, i);
 }
 
 __global__ void k_count_flags(const uint8_t* __restrict__ flag, int N, unsigned long long* __restrict__ count) {

@@ -49,6 +49,10 @@ __host__ __device__ __forceinline__ size_t blk(int row, int rows, int64_t i) {
   return ((size_t)(i / kTC) * rows + row) * kTC + (size_t)(i % kTC);
 }
 
+// blocked per-cell FP32 rows of the mixed form: the six second moments
+// (1/V) int xi_a xi_b (xx yy zz xy xz yz), then 1/h
+constexpr int kCellRows = 7;
+
 template <int ORDER, bool WENO, int ND>
 struct ReconTile {
   static constexpr int K = ORDER == 1 ? 3 : 9;
@@ -57,10 +61,10 @@ struct ReconTile {
   static constexpr int RD = WENO ? ND * 3 * MD : 0;  // directional pseudo-inverse rows
   static constexpr int SD = WENO ? ND * MD : 0;      // directional stencil rows
   static constexpr int CS = ORDER == 1 ? 20 : 52;    // floats per output row: 5 (K+1) rounded up to 4
-  // shared memory of one tile: central rows and stencil, directional rows and
-  // stencils when staged, the tile's output rows, the mbarrier
-  static constexpr size_t smem(bool stage_dir) {
-    return (size_t)(RC + MC + (stage_dir ? RD + SD : 0)) * kTC * 4 + (size_t)kTC * CS * 4 + 16;
+  // shared memory of one tile: central rows and stencil, the cell rows,
+  // directional rows and stencils (CWENOZ), the tile's output rows, the mbarrier
+  static constexpr size_t smem() {
+    return (size_t)(RC + MC + kCellRows + RD + SD) * kTC * 4 + (size_t)kTC * CS * 4 + 16;
   }
 };
 
@@ -70,10 +74,16 @@ struct ReconArgsMx {
   const float* __restrict__ Pc;    // blocked [tiles][K MC][kTC], row k MC + m
   const int32_t* __restrict__ sd;  // blocked [tiles][nd Md][kTC]
   const float* __restrict__ Pd;    // blocked [tiles][nd 3 Md][kTC], row (s 3 + k) Md + r
-  const double* __restrict__ mom;  // [6][N]
-  const float* __restrict__ inv_h;  // [N]
-  float* __restrict__ coef;        // [N][cs]: coefficient k of variable v at k*5 + v, slot 0 relative to U_ref
-  const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
+  const float* __restrict__ cell;  // blocked [tiles][kCellRows][kTC]
+  float* __restrict__ coef;        // [N][cs]: variable-major, coefficient k of variable v at v (K+1) + k,
+                                   // k = 0 the constant term relative to U_ref
+  // gated reconstruction (P2 CWENOZ on the flagged cells only)
+  const int32_t* __restrict__ list;  // [n] flagged cells
+  const int32_t* __restrict__ nlist;  // [1] n (device)
+  const int32_t* __restrict__ pos;   // [N] position of a cell in the list, -1 if not flagged
+  float* __restrict__ ao_s;          // [n][48] central coefficients of the flagged cells (5 x 9, padded)
+  const int32_t* __restrict__ sda;   // [N][nd Md] directional stencils, cell-contiguous
+  const float* __restrict__ Pda;     // [N][nd 3 Md] directional pseudo-inverse rows, cell-contiguous
   int* err;                        // bit 1 set when a bounded wait gave up
   int N;
   int cs;  // floats per cell row of coef (5 (K+1) rounded up to a multiple of 4)
@@ -83,37 +93,103 @@ struct ReconArgsMx {
 
 struct FaceArgsMx {
   const float* __restrict__ coef;  // [N][cs] cell rows, 16-byte aligned
-  const float* __restrict__ fq;  // [nq][10][F]
+  const float* __restrict__ fq;    // [nq][10][F]
   const float* __restrict__ fpen;
   const int32_t* __restrict__ fo;
   const int32_t* __restrict__ fn;
-  const float* __restrict__ inv_h;
   float* __restrict__ G;  // [5][F] FP32 face totals
   int N, F;
   int cs;
   FluxConstF c;
 };
 
+// U_j - U_i of variable v from the float pairs: hi_j - hi_i is exact for
+// same-sign values within a factor 2 (Sterbenz), so the difference carries no
+// cancellation error beyond the final FP32 rounding, as an FP64 subtraction would
+__device__ __forceinline__ float pair_diff(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
+  return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i);
+}
+
+// CWENOZ combination of the central coefficients ao (K = 9, xi units) with the
+// nd directional linear coefficients b: smoothness indicators (Eq. 6 reading),
+// tau, the nonlinear weights and the combined coefficients cf
+template <int ND>
+__device__ __forceinline__ void cwenoz_mx(const float (&ao)[9], const float (&b)[ND][3], const float (&S)[6],
+                                          const ReconArgsMx& a, float (&cf)[9]) {
+  const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
+  const float qy0 = ao[6], qy1 = 2.f * ao[4], qy2 = ao[8];
+  const float qz0 = ao[7], qz1 = ao[8], qz2 = 2.f * ao[5];
+  auto quad = [&](float x0, float x1, float x2) {
+    return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 + 2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
+  };
+  const float SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) + quad(qy0, qy1, qy2) +
+                    quad(qz0, qz1, qz2) + 4.f * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
+                    ao[7] * ao[7] + ao[8] * ao[8];
+  float SI[ND];
+  float tau = 0.f;
+#pragma unroll
+  for (int s = 0; s < ND; s++) {
+    SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
+    tau += fabsf(SI0 - SI[s]);
+  }
+  tau *= (1.f / ND);
+  const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
+  float ws[ND];
+  float wsum = w0;
+#pragma unroll
+  for (int s = 0; s < ND; s++) {
+    ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
+    wsum += ws[s];
+  }
+  const float iws = fdiv(1.f, wsum);
+  const float r0 = fdiv(w0 * iws, a.lam0);
+#pragma unroll
+  for (int k = 0; k < 9; k++) cf[k] = r0 * ao[k];
+#pragma unroll
+  for (int s = 0; s < ND; s++) {
+    const float e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+    for (int k = 0; k < 3; k++) cf[k] = fmaf(e, b[s][k], cf[k]);
+  }
+}
+
+// the K + 1 row entries of variable v: the constant term relative to the
+// reference state U_ref = (1, 0, 0, 0, E_ref) (the cell mean minus the mean
+// of the non-constant monomials), then the coefficients in physical units
+// (linear / h, quadratic / h^2); out points at the variable's first entry
+template <int K>
+__device__ __forceinline__ void write_var(float* out, int v, float hi_i, float lo_i, const float (&cf)[K],
+                                          const float (&S)[6], float ih, const ReconArgsMx& a) {
+  float c0 = v == 0 ? (hi_i - 1.f) + lo_i : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
+  if (K == 9) {
+#pragma unroll
+    for (int q = 0; q < 6; q++) c0 = fmaf(-cf[3 + q], S[q], c0);
+  }
+  const float ih2 = ih * ih;
+  out[0] = c0;
+#pragma unroll
+  for (int k = 0; k < K; k++) out[k + 1] = cf[k] * (k < 3 ? ih : ih2);
+}
+
 // One block per tile of kTC cells, thread = (cell c of the tile, variable v).
 // A single thread starts bulk copies of the tile's central pseudo-inverse rows
-// and stencil (and, ungated CWENOZ, its directional rows and stencils) into
-// shared memory; meanwhile every thread loads its own state and moments.  The
+// and stencil, its cell rows and (CWENOZ) its directional rows and stencils
+// into shared memory; meanwhile every thread loads its own state.  The
 // coefficient rows are assembled in shared memory and written back with one
-// bulk copy.  GATED: cells whose gate flag is 0 take the linear weights and
-// the flagged cells read their directional rows directly (a separate
-// instantiation, so the ungated kernel has no data-dependent branch around
-// the directional loads).
+// bulk copy.  GATED (linear weights, first pass of a gated P2 CWENOZ
+// reconstruction): the central coefficients of the flagged cells also go to
+// a.ao_s for k_recon_fix_mx.
 template <int ORDER, bool WENO, int ND, bool GATED>
-__global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(ReconArgsMx a) {
+__global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx a) {
   using T = ReconTile<ORDER, WENO, ND>;
   constexpr int K = T::K, MC = T::MC, MD = T::MD, CS = T::CS;
-  constexpr bool STAGE_D = WENO && !GATED;
   extern __shared__ __align__(128) unsigned char smem[];
   float* sP = reinterpret_cast<float*>(smem);
   int32_t* sS = reinterpret_cast<int32_t*>(sP + T::RC * kTC);
-  float* sPd = reinterpret_cast<float*>(sS + MC * kTC);
-  int32_t* sSd = reinterpret_cast<int32_t*>(sPd + (STAGE_D ? T::RD * kTC : 0));
-  float* sOut = reinterpret_cast<float*>(sSd + (STAGE_D ? T::SD * kTC : 0));
+  float* sC = reinterpret_cast<float*>(sS + MC * kTC);
+  float* sPd = sC + kCellRows * kTC;
+  int32_t* sSd = reinterpret_cast<int32_t*>(sPd + T::RD * kTC);
+  float* sOut = reinterpret_cast<float*>(sSd + T::SD * kTC);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sOut + kTC * CS);
   const int tile = blockIdx.x, i0 = tile * kTC;
   const int nc = min(kTC, a.N - i0);
@@ -121,11 +197,13 @@ __global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(
   if (t == 0) bar_init(bar);
   __syncthreads();
   if (t == 0) {
-    constexpr uint32_t bp = T::RC * kTC * 4, bs = MC * kTC * 4, bpd = T::RD * kTC * 4, bsd = T::SD * kTC * 4;
-    bar_expect(bar, bp + bs + (STAGE_D ? bpd + bsd : 0));
+    constexpr uint32_t bp = T::RC * kTC * 4, bs = MC * kTC * 4, bc = kCellRows * kTC * 4;
+    constexpr uint32_t bpd = T::RD * kTC * 4, bsd = T::SD * kTC * 4;
+    bar_expect(bar, bp + bs + bc + bpd + bsd);
     bulk_load(sP, a.Pc + (size_t)tile * T::RC * kTC, bp, bar);
     bulk_load(sS, a.sc + (size_t)tile * MC * kTC, bs, bar);
-    if (STAGE_D) {
+    bulk_load(sC, a.cell + (size_t)tile * kCellRows * kTC, bc, bar);
+    if (WENO) {
       bulk_load(sPd, a.Pd + (size_t)tile * T::RD * kTC, bpd, bar);
       bulk_load(sSd, a.sd + (size_t)tile * T::SD * kTC, bsd, bar);
     }
@@ -134,14 +212,6 @@ __global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(
   const int i = i0 + (live ? c : 0);
   const float* __restrict__ hl = a.Uhl;
   const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
-  float S[6];
-  if (ORDER == 2) {
-#pragma unroll
-    for (int q = 0; q < 6; q++) S[q] = (float)__ldg(&a.mom[(size_t)q * a.N + i]);
-  }
-  const float ih = __ldg(&a.inv_h[i]);
-  bool weno = WENO;
-  if (GATED) weno = weno && a.gate[i];
   const bool ok = bar_wait(bar, 0);
   if (__syncthreads_or(!ok)) {
     if (t == 0) atomicOr(a.err, 2);
@@ -149,91 +219,45 @@ __global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(
     return;
   }
   if (live) {
-    // U_j - U_i from the float pairs: hi_j - hi_i is exact for same-sign values
-    // within a factor 2 (Sterbenz), so the difference carries no cancellation
-    // error beyond the final FP32 rounding, as an FP64 subtraction would.
-    auto diff = [&](int j) { return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i); };
     float ao[K];
 #pragma unroll
     for (int k = 0; k < K; k++) ao[k] = 0.f;
 #pragma unroll 6
     for (int m = 0; m < MC; m++) {
-      const float d = diff(sS[m * kTC + c]);
+      const float d = pair_diff(hl, sS[m * kTC + c], v, hi_i, lo_i);
 #pragma unroll
       for (int k = 0; k < K; k++) ao[k] = fmaf(sP[(k * MC + m) * kTC + c], d, ao[k]);
     }
-    float cf[K];
-    if (!weno) {
+    if (GATED) {
+      const int p = __ldg(&a.pos[i]);
+      if (p >= 0) {
 #pragma unroll
-      for (int k = 0; k < K; k++) cf[k] = ao[k];
-    } else {
+        for (int k = 0; k < K; k++) a.ao_s[(size_t)p * 48 + v * K + k] = ao[k];
+      }
+    }
+    float S[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) S[q] = sC[q * kTC + c];
+    const float ih = sC[6 * kTC + c];
+    float* out = sOut + c * CS + v * (K + 1);
+    if constexpr (WENO) {
       float b[ND][3];
 #pragma unroll
       for (int s = 0; s < ND; s++) {
         b[s][0] = b[s][1] = b[s][2] = 0.f;
 #pragma unroll
         for (int r = 0; r < MD; r++) {
-          const int j = STAGE_D ? sSd[(s * MD + r) * kTC + c] : __ldg(&a.sd[blk(s * MD + r, T::SD, i)]);
-          const float d = diff(j);
+          const float d = pair_diff(hl, sSd[(s * MD + r) * kTC + c], v, hi_i, lo_i);
 #pragma unroll
-          for (int k = 0; k < 3; k++) {
-            const int row = (s * 3 + k) * MD + r;
-            const float P = STAGE_D ? sPd[row * kTC + c] : __ldg(&a.Pd[blk(row, T::RD, i)]);
-            b[s][k] = fmaf(P, d, b[s][k]);
-          }
+          for (int k = 0; k < 3; k++) b[s][k] = fmaf(sPd[((s * 3 + k) * MD + r) * kTC + c], d, b[s][k]);
         }
       }
-      const float qx0 = 2.f * ao[3], qx1 = ao[6], qx2 = ao[7];
-      const float qy0 = ao[6], qy1 = 2.f * ao[4], qy2 = ao[8];
-      const float qz0 = ao[7], qz1 = ao[8], qz2 = 2.f * ao[5];
-      auto quad = [&](float x0, float x1, float x2) {
-        return S[0] * x0 * x0 + S[1] * x1 * x1 + S[2] * x2 * x2 +
-               2.f * (S[3] * x0 * x1 + S[4] * x0 * x2 + S[5] * x1 * x2);
-      };
-      const float SI0 = ao[0] * ao[0] + ao[1] * ao[1] + ao[2] * ao[2] + quad(qx0, qx1, qx2) +
-                        quad(qy0, qy1, qy2) + quad(qz0, qz1, qz2) +
-                        4.f * (ao[3] * ao[3] + ao[4] * ao[4] + ao[5] * ao[5]) + ao[6] * ao[6] +
-                        ao[7] * ao[7] + ao[8] * ao[8];
-      float SI[ND];
-      float tau = 0.f;
-#pragma unroll
-      for (int s = 0; s < ND; s++) {
-        SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
-        tau += fabsf(SI0 - SI[s]);
-      }
-      tau *= (1.f / ND);
-      const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
-      float ws[ND];
-      float wsum = w0;
-#pragma unroll
-      for (int s = 0; s < ND; s++) {
-        ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
-        wsum += ws[s];
-      }
-      const float iws = fdiv(1.f, wsum);
-      const float r0 = fdiv(w0 * iws, a.lam0);
-#pragma unroll
-      for (int k = 0; k < K; k++) cf[k] = r0 * ao[k];
-#pragma unroll
-      for (int s = 0; s < ND; s++) {
-        const float e = ws[s] * iws - r0 * a.lams;
-#pragma unroll
-        for (int k = 0; k < 3; k++) cf[k] = fmaf(e, b[s][k], cf[k]);
-      }
+      float cf[9];
+      cwenoz_mx<ND>(ao, b, S, a, cf);
+      write_var<9>(out, v, hi_i, lo_i, cf, S, ih, a);
+    } else {
+      write_var<K>(out, v, hi_i, lo_i, ao, S, ih, a);
     }
-    // constant term relative to the reference state U_ref = (1, 0, 0, 0, E_ref)
-    float c0 = v == 0 ? (hi_i - 1.f) + lo_i
-                      : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
-    if (ORDER == 2) {
-#pragma unroll
-      for (int q = 0; q < 6; q++) c0 = fmaf(-cf[3 + q], S[q], c0);
-    }
-    // physical units: linear coefficients / h, quadratic / h^2
-    const float ih2 = ih * ih;
-    float* out = sOut + c * CS + v;
-    out[0] = c0;
-#pragma unroll
-    for (int k = 0; k < K; k++) out[(k + 1) * 5] = cf[k] * (k < 3 ? ih : ih2);
     if (v == 0) {
 #pragma unroll
       for (int q = 5 * (K + 1); q < CS; q++) sOut[c * CS + q] = 0.f;
@@ -242,6 +266,90 @@ __global__ void __launch_bounds__(kTC * 5, (WENO && !GATED) ? 2 : 3) k_recon_mx(
   fence_smem_to_async();
   __syncthreads();
   if (t == 0) bulk_store(a.coef + (size_t)i0 * CS, sOut, (uint32_t)(nc * CS * 4));
+}
+
+// CWENOZ entries of the flagged cells (P2), overwriting the linear ones that
+// k_recon_mx<2, false, ., true> wrote for them: the central coefficients come from
+// that pass, the directional stencils and rows from cell-contiguous copies;
+// the arithmetic and its order are those of the CWENOZ tile kernel.
+// thread = (list entry, variable), grid-stride over the device-side count
+template <int ND>
+__global__ void __launch_bounds__(256) k_recon_fix_mx(ReconArgsMx a) {
+  using T = ReconTile<2, true, ND>;
+  constexpr int K = 9, MD = T::MD, CS = T::CS;
+  const float* __restrict__ hl = a.Uhl;
+  const int n5 = 5 * __ldg(a.nlist);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n5; t += gridDim.x * blockDim.x) {
+    const int e = t / 5, v = t - 5 * (t / 5);
+    const int i = __ldg(&a.list[e]);
+    const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
+    float ao[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[k] = __ldg(&a.ao_s[(size_t)e * 48 + v * K + k]);
+    float b[ND][3];
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      // stencil s: 6 members (three 8-byte loads), 18 rows (nine 8-byte loads)
+      const int2* js = reinterpret_cast<const int2*>(a.sda + (size_t)i * T::SD + s * MD);
+      const float2* ps = reinterpret_cast<const float2*>(a.Pda + (size_t)i * T::RD + s * 3 * MD);
+      int jj[MD];
+      float P[3 * MD];
+#pragma unroll
+      for (int q = 0; q < MD / 2; q++) {
+        const int2 w = __ldg(js + q);
+        jj[2 * q] = w.x;
+        jj[2 * q + 1] = w.y;
+      }
+#pragma unroll
+      for (int q = 0; q < 3 * MD / 2; q++) {
+        const float2 w = __ldg(ps + q);
+        P[2 * q] = w.x;
+        P[2 * q + 1] = w.y;
+      }
+      b[s][0] = b[s][1] = b[s][2] = 0.f;
+#pragma unroll
+      for (int r = 0; r < MD; r++) {
+        const float d = pair_diff(hl, jj[r], v, hi_i, lo_i);
+#pragma unroll
+        for (int k = 0; k < 3; k++) b[s][k] = fmaf(P[k * MD + r], d, b[s][k]);
+      }
+    }
+    float S[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) S[q] = __ldg(&a.cell[blk(q, kCellRows, i)]);
+    const float ih = __ldg(&a.cell[blk(6, kCellRows, i)]);
+    float cf[9];
+    cwenoz_mx<ND>(ao, b, S, a, cf);
+    write_var<9>(a.coef + (size_t)i * CS + v * (K + 1), v, hi_i, lo_i, cf, S, ih, a);
+  }
+}
+
+// compacted list of the cells whose gate flag is set (order within a block
+// kept, blocks in any order) and every cell's position in it (-1: not
+// flagged); *count must be zero on entry
+__global__ void __launch_bounds__(256) k_flag_list(const uint8_t* __restrict__ flag, int N, int32_t* __restrict__ list,
+                                                   int32_t* __restrict__ pos, int32_t* __restrict__ count) {
+  __shared__ int warp_n[8];
+  __shared__ int base;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool f = i < N && flag[i];
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_n[w] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int q = 0; q < 8; q++) {
+      const int n = warp_n[q];
+      warp_n[q] = tot;
+      tot += n;
+    }
+    base = tot ? atomicAdd(count, tot) : 0;
+  }
+  __syncthreads();
+  const int p = base + warp_n[w] + __popc(bal & ((1u << lane) - 1u));
+  if (f) list[p] = i;
+  if (i < N) pos[i] = f ? p : -1;
 }
 
 // float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5
@@ -275,7 +383,8 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
   }
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const float c0 = cf[v], c1 = cf[5 + v], c2 = cf[10 + v], c3 = cf[15 + v];
+    constexpr int NCF = ORDER == 1 ? 4 : 10;  // entries per variable
+    const float c0 = cf[v * NCF], c1 = cf[v * NCF + 1], c2 = cf[v * NCF + 2], c3 = cf[v * NCF + 3];
     float gx, gy, gz;
     if (ORDER == 1) {
       U[v] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
@@ -283,8 +392,8 @@ __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int
       gy = c2;
       gz = c3;
     } else {
-      const float c4 = cf[20 + v], c5 = cf[25 + v], c6 = cf[30 + v];
-      const float c7 = cf[35 + v], c8 = cf[40 + v], c9 = cf[45 + v];
+      const float c4 = cf[v * NCF + 4], c5 = cf[v * NCF + 5], c6 = cf[v * NCF + 6];
+      const float c7 = cf[v * NCF + 7], c8 = cf[v * NCF + 8], c9 = cf[v * NCF + 9];
       const float tx = fmaf(c4, x, fmaf(c7, y, fmaf(c8, z, c1)));
       const float ty = fmaf(c5, y, fmaf(c9, z, c2));
       const float tz = fmaf(c6, z, c3);
@@ -448,7 +557,7 @@ __global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
 // diagnostics partial sums from FP32 coefficients (FP64 accumulation)
 __global__ void __launch_bounds__(kRedThreads)
     k_diag_partial_mx(const double* __restrict__ U, const float* __restrict__ coef, int cs,
-                      const double* __restrict__ vol, const double* __restrict__ inv_h, int N,
+                      int ncf /* entries per variable, K + 1 */, const double* __restrict__ vol, int N,
                       double* __restrict__ part) {
   __shared__ double sm[4][kRedThreads];
   double acc[4] = {0, 0, 0, 0};
@@ -459,7 +568,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + (j + 1) * 5 + v];
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + v * ncf + j + 1];
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

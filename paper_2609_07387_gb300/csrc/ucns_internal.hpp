@@ -41,6 +41,9 @@ struct DeviceMesh {
   float* Pdb = nullptr;       // rows (s 3 + k) Md + r
   int32_t* scb = nullptr;     // rows m
   int32_t* sdb = nullptr;     // rows s Md + r
+  float* cellb = nullptr;     // rows: the six second moments, then 1/h
+  int32_t* sda = nullptr;     // [N][nd Md] directional stencils, cell-contiguous (gated CWENOZ)
+  float* Pda = nullptr;       // [N][nd 3 Md] directional rows, cell-contiguous
   float* inv_hf = nullptr;    // [N]
   float* fpenf = nullptr;     // [F]
   int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)
@@ -94,6 +97,10 @@ struct ucns_mesh {
   void* gate_X = nullptr;              // [N][32] BF16 features
   uint8_t* gate_flag = nullptr;        // [N]
   unsigned long long* gate_count = nullptr;
+  int32_t* gate_list = nullptr;        // [N] flagged cells (mixed form), built with the flags
+  int32_t* gate_nlist = nullptr;       // [1] their number
+  int32_t* gate_pos = nullptr;         // [N] position in the list, -1 if not flagged
+  float* gate_ao = nullptr;            // [N][48] central coefficients of the listed cells
   bool gate_eval_active = false;       // flags valid for the reconstructions of this call
   int gate_check_every = 0;
   int gate_eval_every = 1;

@@ -57,14 +57,17 @@ int upload_cellwise(T** dst, const std::vector<S>& src, int rows, int64_t N) {
   return upload(dst, b);
 }
 
-// [rows][N] -> blocked [ceil(N/kTC)][rows][kTC] (zero past N), converted to T
+// [rows][N] -> blocked [ceil(N/kTC)][rows][kTC] (pair = false) or
+// pair-blocked [ceil(N/kTC)][rows/2][kTC][2] (pair = true, rows even), zero
+// past N, converted to T
 template <typename T, typename S>
-int upload_blocked(T** dst, const std::vector<S>& src, int rows, int64_t N) {
+int upload_blocked(T** dst, const std::vector<S>& src, int rows, int64_t N, bool pair) {
   if (src.empty()) return UCNS_OK;
+  if (pair && rows % 2) return fail(UCNS_ERR_INVALID_ARG, "pair-blocked layout needs an even row count");
   const int64_t tiles = (N + kTC - 1) / kTC;
   std::vector<T> b((size_t)tiles * rows * kTC, T(0));
   for (int r = 0; r < rows; r++)
-    for (int64_t i = 0; i < N; i++) b[blk(r, rows, i)] = (T)src[(size_t)r * N + i];
+    for (int64_t i = 0; i < N; i++) b[pair ? blk2(r, rows, i) : blk(r, rows, i)] = (T)src[(size_t)r * N + i];
   return upload(dst, b);
 }
 
@@ -664,9 +667,11 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     std::vector<double> cellrows((size_t)kCellRows * m->N);
     std::copy(h.mom.begin(), h.mom.begin() + (size_t)6 * m->N, cellrows.begin());
     std::copy(h.inv_h.begin(), h.inv_h.end(), cellrows.begin() + (size_t)6 * m->N);
-    if ((rc = upload_blocked(&d.Pcb, h.Pc, rc_rows, m->N)) || (rc = upload_blocked(&d.Pdb, h.Pd, rd_rows, m->N)) ||
-        (rc = upload_blocked(&d.scb, h.sc, m->Mc, m->N)) || (rc = upload_blocked(&d.sdb, h.sd, m->nd * m->Md, m->N)) ||
-        (rc = upload_blocked(&d.cellb, cellrows, kCellRows, m->N)) ||
+    if ((rc = upload_blocked(&d.Pcb, h.Pc, rc_rows, m->N, true)) ||
+        (rc = upload_blocked(&d.Pdb, h.Pd, rd_rows, m->N, true)) ||
+        (rc = upload_blocked(&d.scb, h.sc, m->Mc, m->N, true)) ||
+        (rc = upload_blocked(&d.sdb, h.sd, m->nd * m->Md, m->N, true)) ||
+        (rc = upload_blocked(&d.cellb, cellrows, kCellRows, m->N, false)) ||
         (rc = upload_cellwise(&d.sda, h.sd, m->nd * m->Md, m->N)) ||
         (rc = upload_cellwise(&d.Pda, h.Pd, rd_rows, m->N)) ||
         (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||

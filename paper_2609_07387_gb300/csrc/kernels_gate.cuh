@@ -13,8 +13,8 @@ namespace ucns {
 struct FeatArgs {
   const double* __restrict__ U;    // [5][N] (FP64 form)
   const float* __restrict__ Uhl;   // [N][10] float pair of U (mixed form)
-  const int32_t* __restrict__ sc;  // [18][N] (FP64 form) or blocked [tiles][18][kTC] (mixed form)
-  const void* __restrict__ Pc;     // [9][18][N] double (FP64 form) or blocked [tiles][9 18][kTC] float
+  const int32_t* __restrict__ sc;  // [18][N] (FP64 form) or pair-blocked (mixed form)
+  const void* __restrict__ Pc;     // [9][18][N] double (FP64 form) or pair-blocked float (mixed form)
   const double* __restrict__ mom;    // [6][N] (FP64 form)
   const double* __restrict__ inv_h;  // [N] (FP64 form)
   const float* __restrict__ cell;    // blocked [tiles][kCellRows][kTC] (mixed form)
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
     for (int k = 0; k < K; k++) ao[v][k] = 0.f;
 #pragma unroll
   for (int m = 0; m < MC; m++) {
-    const int j = __ldg(&a.sc[blk(m, MC, i)]);
+    const int j = __ldg(&a.sc[blk2(m, MC, i)]);
     float t[10];
 #pragma unroll
     for (int q = 0; q < 5; q++) {
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      const float P = __ldg(&Pc[blk(k * MC + m, K * MC, i)]);
+      const float P = __ldg(&Pc[blk2(k * MC + m, K * MC, i)]);
 #pragma unroll
       for (int v = 0; v < 5; v++) ao[v][k] = fmaf(P, d[v], ao[v][k]);
     }

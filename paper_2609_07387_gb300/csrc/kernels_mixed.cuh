@@ -49,6 +49,13 @@ __host__ __device__ __forceinline__ size_t blk(int row, int rows, int64_t i) {
   return ((size_t)(i / kTC) * rows + row) * kTC + (size_t)(i % kTC);
 }
 
+// index of (row, cell i) in a pair-blocked array [ceil(N / kTC)][rows / 2][kTC][2]
+// (rows even): rows 2j and 2j + 1 of a cell are adjacent, so one 8-byte load
+// reads both (the pseudo-inverse rows of consecutive stencil members)
+__host__ __device__ __forceinline__ size_t blk2(int row, int rows, int64_t i) {
+  return (((size_t)(i / kTC) * (rows / 2) + row / 2) * kTC + (size_t)(i % kTC)) * 2 + (row & 1);
+}
+
 // blocked per-cell FP32 rows of the mixed form: the six second moments
 // (1/V) int xi_a xi_b (xx yy zz xy xz yz), then 1/h
 constexpr int kCellRows = 7;
@@ -70,10 +77,10 @@ struct ReconTile {
 
 struct ReconArgsMx {
   const float* __restrict__ Uhl;  // [N][10]: hi = fl(U) of the 5 variables, then lo = fl(U - hi)
-  const int32_t* __restrict__ sc;  // blocked [tiles][MC][kTC]
-  const float* __restrict__ Pc;    // blocked [tiles][K MC][kTC], row k MC + m
-  const int32_t* __restrict__ sd;  // blocked [tiles][nd Md][kTC]
-  const float* __restrict__ Pd;    // blocked [tiles][nd 3 Md][kTC], row (s 3 + k) Md + r
+  const int32_t* __restrict__ sc;  // pair-blocked, rows m (MC)
+  const float* __restrict__ Pc;    // pair-blocked, rows k MC + m (K MC)
+  const int32_t* __restrict__ sd;  // pair-blocked, rows s Md + r (nd Md)
+  const float* __restrict__ Pd;    // pair-blocked, rows (s 3 + k) Md + r (nd 3 Md)
   const float* __restrict__ cell;  // blocked [tiles][kCellRows][kTC]
   float* __restrict__ coef;        // [N][cs]: variable-major, coefficient k of variable v at v (K+1) + k,
                                    // k = 0 the constant term relative to U_ref
@@ -222,11 +229,17 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
     float ao[K];
 #pragma unroll
     for (int k = 0; k < K; k++) ao[k] = 0.f;
-#pragma unroll 6
-    for (int m = 0; m < MC; m++) {
-      const float d = pair_diff(hl, sS[m * kTC + c], v, hi_i, lo_i);
+    const int2* sS2 = reinterpret_cast<const int2*>(sS);
+    const float2* sP2 = reinterpret_cast<const float2*>(sP);
+#pragma unroll 3
+    for (int mp = 0; mp < MC / 2; mp++) {  // stencil members m = 2 mp, 2 mp + 1
+      const int2 jj = sS2[mp * kTC + c];
+      const float d0 = pair_diff(hl, jj.x, v, hi_i, lo_i), d1 = pair_diff(hl, jj.y, v, hi_i, lo_i);
 #pragma unroll
-      for (int k = 0; k < K; k++) ao[k] = fmaf(sP[(k * MC + m) * kTC + c], d, ao[k]);
+      for (int k = 0; k < K; k++) {
+        const float2 P = sP2[(k * (MC / 2) + mp) * kTC + c];
+        ao[k] = fmaf(P.y, d1, fmaf(P.x, d0, ao[k]));
+      }
     }
     if (GATED) {
       const int p = __ldg(&a.pos[i]);
@@ -242,14 +255,20 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
     float* out = sOut + c * CS + v * (K + 1);
     if constexpr (WENO) {
       float b[ND][3];
+      const int2* sSd2 = reinterpret_cast<const int2*>(sSd);
+      const float2* sPd2 = reinterpret_cast<const float2*>(sPd);
 #pragma unroll
       for (int s = 0; s < ND; s++) {
         b[s][0] = b[s][1] = b[s][2] = 0.f;
 #pragma unroll
-        for (int r = 0; r < MD; r++) {
-          const float d = pair_diff(hl, sSd[(s * MD + r) * kTC + c], v, hi_i, lo_i);
+        for (int rp = 0; rp < MD / 2; rp++) {  // members r = 2 rp, 2 rp + 1
+          const int2 jj = sSd2[(s * (MD / 2) + rp) * kTC + c];
+          const float d0 = pair_diff(hl, jj.x, v, hi_i, lo_i), d1 = pair_diff(hl, jj.y, v, hi_i, lo_i);
 #pragma unroll
-          for (int k = 0; k < 3; k++) b[s][k] = fmaf(sPd[((s * 3 + k) * MD + r) * kTC + c], d, b[s][k]);
+          for (int k = 0; k < 3; k++) {
+            const float2 P = sPd2[((s * 3 + k) * (MD / 2) + rp) * kTC + c];
+            b[s][k] = fmaf(P.y, d1, fmaf(P.x, d0, b[s][k]));
+          }
         }
       }
       float cf[9];

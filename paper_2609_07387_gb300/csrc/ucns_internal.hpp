@@ -35,8 +35,9 @@ struct DeviceMesh {
   double* Pc = nullptr;       // [K][Mc][N] central pseudo-inverse
   int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
   double* Pd = nullptr;       // [nd][3][Md][N]
-  // mixed precision: FP32 pseudo-inverses and the stencils in the blocked
-  // layout [ceil(N/64)][rows][64] (tiles of 64 consecutive cells)
+  // mixed precision: FP32 pseudo-inverses and the stencils in the pair-blocked
+  // layout [ceil(N/64)][rows/2][64][2] (tiles of 64 consecutive cells, row
+  // pairs of a cell adjacent), the cell rows blocked [ceil(N/64)][rows][64]
   float* Pcb = nullptr;       // rows k Mc + m
   float* Pdb = nullptr;       // rows (s 3 + k) Md + r
   int32_t* scb = nullptr;     // rows m

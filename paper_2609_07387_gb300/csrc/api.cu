@@ -337,6 +337,32 @@ int launch_dt_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   return UCNS_OK;
 }
 
+// the CFL time step of U into m->d.dt at the start of a Runge-Kutta step, one
+// fused kernel; the mixed form also leaves the float pair of U in m->d.Uhl
+// (returned in *split)
+int launch_dt_step(ucns_mesh* m, const double* U, cudaStream_t s, bool* split) {
+  const ucns_params& p = m->P;
+  DtArgs a;
+  a.U = U;
+  a.dtlen = m->d.dtlen;
+  a.part = m->d.dt_part;
+  a.count = m->d.dt_count;
+  a.dt = m->d.dt;
+  a.hl = m->d.Uhl;
+  a.err = m->d.err;
+  a.N = (int)m->N;
+  a.gam = p.gamma;
+  a.visc = p.reynolds > 0.0 ? p.prandtl / (2.0 * p.gamma * (1.0 / p.reynolds)) : 0.0;
+  a.cfl = p.cfl;
+  *split = mixed(m);
+  return timed(m, kKindDt, s, [&] {
+    if (mixed(m)) k_dt_fused<true><<<nblocks((size_t)m->N), kRedThreads, 0, s>>>(a);
+    else k_dt_fused<false><<<nblocks((size_t)m->N), kRedThreads, 0, s>>>(a);
+    UCNS_CUDA(cudaGetLastError());
+    return UCNS_OK;
+  });
+}
+
 int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindRecon, s, [&] { return launch_recon_raw(m, U, s); });
 }
@@ -362,7 +388,7 @@ int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
 
 // the indicator features of U into X (BF16) and Xf (FP32, or null); the
 // mixed form reads U through its float pair, split here
-int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s) {
+int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s, bool split = true) {
   FeatArgs a;
   a.U = U;
   a.Uhl = m->d.Uhl;
@@ -376,7 +402,7 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
   a.N = (int)m->N;
   a.gam = (float)m->P.gamma;
   if (mixed(m)) {
-    int rc = launch_split_raw(m, U, s);
+    int rc = split ? launch_split_raw(m, U, s) : UCNS_OK;
     if (rc) return rc;
     k_features_mx<<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
   } else {
@@ -387,11 +413,12 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
 }
 
 // features of U and the network's flags, once per call of the solver; for the
-// mixed form this leaves the float pair of U in m->d.Uhl
-int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr) {
+// mixed form this leaves the float pair of U in m->d.Uhl (split_fresh: it is
+// there already)
+int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr, bool split_fresh = false) {
   m->gate_eval_active = false;
   if (!m->gate_on || !m->mlp) return UCNS_OK;
-  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s); });
+  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s, !split_fresh); });
   if (rc) return rc;
   if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
@@ -448,7 +475,8 @@ int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
   return UCNS_OK;
 }
 
-int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
+// split_fresh: m->d.Uhl already holds the float pair of U (mixed form)
+int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool split_fresh = false) {
   int rc;
   double* W = m->d.Ustage;
   const int64_t step = m->gate_steps;
@@ -458,11 +486,11 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s) {
     m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  bool split_done = false;
+  bool split_done = split_fresh;
   if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
     m->gate_eval_active = true;  // reuse the flags of the last evaluation
   } else {
-    if ((rc = gate_eval(m, U, s, &split_done))) return rc;  // flags of U^n serve all three stages
+    if ((rc = gate_eval(m, U, s, &split_done, split_fresh))) return rc;  // flags of U^n serve all three stages
     m->gate_flags_valid = m->gate_eval_active;
   }
   if ((!split_done && (rc = launch_split(m, U, s))) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
@@ -528,7 +556,7 @@ void device_free(ucns_mesh* m) {
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
-                  d.Ustage, d.Uhost, d.red, d.dt, d.err};
+                  d.Ustage, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceMesh{};
@@ -688,11 +716,13 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   d.red_blocks = 4 * 152;
   if ((rc = alloc(&d.G, (size_t)5 * m->F)) ||
       (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)4 * d.red_blocks)) ||
-      (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1))) {
+      (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1)) || (rc = alloc(&d.dt_part, (size_t)nblocks(m->N))) ||
+      (rc = alloc(&d.dt_count, 1))) {
     device_free(m);
     return rc;
   }
   UCNS_CUDA(cudaMemset(d.err, 0, sizeof(int)));
+  UCNS_CUDA(cudaMemset(d.dt_count, 0, sizeof(unsigned)));
   UCNS_CUDA(cudaDeviceSynchronize());
   m->precomputed = true;
   return UCNS_OK;
@@ -716,13 +746,14 @@ int ucns_rk_step(ucns_mesh* m, double* U, double* dt_inout, void* stream) {
   if (!U) return fail(UCNS_ERR_INVALID_ARG, "U is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const bool given = dt_inout && *dt_inout > 0.0;
+  bool split = false;
   if (given) {
     k_set_scalar<<<1, 1, 0, s>>>(m->d.dt, *dt_inout);  // by value: no host buffer outlives the call
     UCNS_CUDA(cudaGetLastError());
-  } else if ((rc = launch_dt(m, U, s))) {
+  } else if ((rc = launch_dt_step(m, U, s, &split))) {
     return rc;
   }
-  if ((rc = rk_step_device(m, U, s))) return rc;
+  if ((rc = rk_step_device(m, U, s, split))) return rc;
   if (dt_inout && !given) {
     UCNS_CUDA(cudaMemcpyAsync(dt_inout, m->d.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     return read_error_word(m, s);
@@ -741,9 +772,10 @@ int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_
   double* tacc = m->d.dt + 1;  // device accumulator of the simulated time
   k_set_scalar<<<1, 1, 0, s>>>(tacc, 0.0);
   for (int k = 0; k < n_steps; k++) {
-    if ((rc = launch_dt(m, m->d.Uhost, s))) return rc;
+    bool split = false;
+    if ((rc = launch_dt_step(m, m->d.Uhost, s, &split))) return rc;
     k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);
-    if ((rc = rk_step_device(m, m->d.Uhost, s))) return rc;
+    if ((rc = rk_step_device(m, m->d.Uhost, s, split))) return rc;
   }
   UCNS_CUDA(cudaGetLastError());
   double t = 0.0;

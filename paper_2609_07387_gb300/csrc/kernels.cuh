@@ -444,29 +444,29 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
 // ------------------------------------------------------------ reductions
 constexpr int kRedThreads = 256;
 
-// CFL limit of cell i: h / (|u| + a), and the viscous limit rho h^2 Pr/(2 gamma mu)
-// when visc_coef > 0; bad when rho, p or the limit is not positive
-__device__ __forceinline__ double dt_limit(const double* __restrict__ U, size_t N, int i, double h, double gam,
-                                           double visc_coef, bool& bad) {
-  const double r = U[i], m0 = U[N + i], m1 = U[2 * N + i], m2 = U[3 * N + i];
+// CFL limit of a cell with state u: h / (|u| + a), and the viscous limit
+// rho h^2 Pr/(2 gamma mu) when visc_coef > 0; bad when rho, p or the limit is
+// not positive
+__device__ __forceinline__ double dt_limit_v(const double (&u)[5], double h, double gam, double visc_coef,
+                                             bool& bad) {
+  const double r = u[0], m0 = u[1], m1 = u[2], m2 = u[3];
   const double ir = 1.0 / r;
   const double q2 = (m0 * m0 + m1 * m1 + m2 * m2) * ir * ir;
-  const double p = (gam - 1.0) * (U[4 * N + i] - 0.5 * r * q2);
+  const double p = (gam - 1.0) * (u[4] - 0.5 * r * q2);
   double d = h / (sqrt(q2) + sqrt(gam * p * ir));
   if (visc_coef > 0.0) d = fmin(d, r * h * h * visc_coef);
   if (!(r > 0.0 && p > 0.0 && d > 0.0)) bad = true;
   return d;
 }
 
-// FP32 estimate of dt_limit with relative error below 1e-6, written as
+// FP32 estimate of dt_limit_v with relative error below 1e-6, written as
 // h rho / (|m| + sqrt(gamma (gamma-1) (rho E - |m|^2/2))) so that the FP64 part
 // has no division or square root.  `sure` is false where the estimate cannot
-// be trusted to that accuracy or where dt_limit could flag the cell: rho <= 0,
+// be trusted to that accuracy or where dt_limit_v could flag the cell: rho <= 0,
 // rho E - |m|^2/2 below 1e-3 rho E (pressure near zero), values outside the
 // normal FP32 range, non-finite values.
-__device__ __forceinline__ float dt_estimate(const double* __restrict__ U, size_t N, int i, float h, float g2,
-                                             float visc_f, bool& sure) {
-  const double r = U[i], m0 = U[N + i], m1 = U[2 * N + i], m2 = U[3 * N + i], E = U[4 * N + i];
+__device__ __forceinline__ float dt_estimate_v(const double (&u)[5], float h, float g2, float visc_f, bool& sure) {
+  const double r = u[0], m0 = u[1], m1 = u[2], m2 = u[3], E = u[4];
   const double mm = fma(m0, m0, fma(m1, m1, m2 * m2));
   const double er = E * r;
   const double pr = fma(-0.5, mm, er);  // rho p / (gamma - 1)
@@ -477,6 +477,11 @@ __device__ __forceinline__ float dt_estimate(const double* __restrict__ U, size_
   if (visc_f > 0.f) d = fminf(d, rf * h * h * visc_f);
   sure = sure && d > 1e-30f && d < 1e30f;
   return d;
+}
+
+__device__ __forceinline__ void load_state(const double* __restrict__ U, size_t N, int i, double (&u)[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; v++) u[v] = U[v * N + i];
 }
 
 // per-block minimum of the CFL time-step limit, equal bit for bit to the
@@ -496,7 +501,9 @@ __global__ void __launch_bounds__(kRedThreads)
   float est = INFINITY;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     bool sure;
-    const float e = dt_estimate(U, n, i, (float)dtlen[i], g2, visc_f, sure);
+    double u[5];
+    load_state(U, n, i, u);
+    const float e = dt_estimate_v(u, (float)dtlen[i], g2, visc_f, sure);
     if (sure) est = fminf(est, e);
   }
   smf[threadIdx.x] = est;
@@ -511,8 +518,10 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double h = dtlen[i];
     bool sure;
-    const float e = dt_estimate(U, n, i, (float)h, g2, visc_f, sure);
-    if (!sure || e <= cut) best = fmin(best, dt_limit(U, n, i, h, gam, visc_coef, bad));
+    double u[5];
+    load_state(U, n, i, u);
+    const float e = dt_estimate_v(u, (float)h, g2, visc_f, sure);
+    if (!sure || e <= cut) best = fmin(best, dt_limit_v(u, h, gam, visc_coef, bad));
   }
   if (bad) atomicOr(err, 1);
   sm[threadIdx.x] = best;
@@ -536,6 +545,88 @@ __global__ void __launch_bounds__(kRedThreads)
     __syncthreads();
   }
   if (threadIdx.x == 0) dt[0] = cfl * sm[0];
+}
+
+struct DtArgs {
+  const double* __restrict__ U;      // [5][N]
+  const double* __restrict__ dtlen;  // [N]
+  double* part;                      // [gridDim.x] block minima
+  unsigned* count;                   // blocks done (zero between launches)
+  double* dt;                        // [1] CFL * minimum
+  float* hl;                         // [N][10] float pair of U (SPLIT)
+  int* err;
+  int N;
+  double gam, visc, cfl;
+};
+
+// One thread per cell: the block's minimum of the CFL limit, equal bit for
+// bit to that of dt_limit_v (FP32 estimates first, the FP64 limit only near
+// the block's minimum estimate or where the estimate is not sure, as in
+// k_dt_partial, here with the state held in registers); SPLIT also writes the
+// state's float pair (as k_split).  The last block to finish (a counter, no
+// waiting) reduces the block minima in index order and writes dt.
+template <bool SPLIT>
+__global__ void __launch_bounds__(kRedThreads) k_dt_fused(DtArgs a) {
+  __shared__ double sm[kRedThreads];
+  __shared__ float smf[kRedThreads];
+  __shared__ bool last;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < a.N;
+  const size_t n = a.N;
+  double u[5] = {1.0, 0.0, 0.0, 0.0, 1.0};
+  double h = 1.0;
+  if (live) {
+    load_state(a.U, n, i, u);
+    h = a.dtlen[i];
+    if (SPLIT) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) {
+        const float hi = (float)u[v];
+        a.hl[(size_t)i * 10 + v] = hi;
+        a.hl[(size_t)i * 10 + 5 + v] = (float)(u[v] - (double)hi);
+      }
+    }
+  }
+  bool sure = false;
+  float e = INFINITY;
+  if (live) e = dt_estimate_v(u, (float)h, (float)(a.gam * (a.gam - 1.0)), (float)a.visc, sure);
+  smf[threadIdx.x] = sure ? e : INFINITY;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) smf[threadIdx.x] = fminf(smf[threadIdx.x], smf[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const float cut = smf[0] * 1.0001f;
+  bool bad = false;
+  double d = INFINITY;
+  if (live && (!sure || e <= cut)) d = dt_limit_v(u, h, a.gam, a.visc, bad);
+  if (bad) atomicOr(a.err, 1);
+  sm[threadIdx.x] = d;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = sm[0];
+    __threadfence();  // the block minimum is visible before the count says so
+    last = atomicAdd(a.count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double best = INFINITY;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) best = fmin(best, __ldcg(&a.part[b]));
+  sm[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.dt[0] = a.cfl * sm[0];
+    *a.count = 0u;  // ready for the next launch (stream order)
+  }
 }
 
 // per-block sums [V KE, V |curl u|^2, V (div u)^2, V] in a fixed tree order

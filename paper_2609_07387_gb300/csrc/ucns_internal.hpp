@@ -64,6 +64,8 @@ struct DeviceMesh {
   double* red = nullptr;      // reduction partials
   double* dt = nullptr;       // [1] device time step
   int* err = nullptr;         // [1] device error word
+  double* dt_part = nullptr;  // [ceil(N/256)] block minima of the fused time-step kernel
+  unsigned* dt_count = nullptr;  // [1] its finished-block counter (zero between launches)
   int red_blocks = 0;
 };
 

@@ -376,10 +376,9 @@ __device__ __forceinline__ double face_sum(const RKArgs& a, const double* __rest
 
 // FP32 face totals: the sum is carried as an unevaluated pair s + e of floats
 // by error-free transformations (Knuth's TwoSum), so that it keeps the
-// accuracy of a double-length sum (errors of order u^2 sum |G|, u = 2^-24),
-// and is rounded once to FP64 at the end
+// accuracy of a double-length sum (errors of order u^2 sum |G|, u = 2^-24)
 template <int NFC>
-__device__ __forceinline__ double face_sum(const RKArgs& a, const float* __restrict__ G, int i, int v) {
+__device__ __forceinline__ float2 face_sum_pair(const RKArgs& a, const float* __restrict__ G, int i, int v) {
   float s = 0.f, e = 0.f;
 #pragma unroll
   for (int j = 0; j < NFC; j++) {
@@ -390,7 +389,48 @@ __device__ __forceinline__ double face_sum(const RKArgs& a, const float* __restr
     e += (s - (t - z)) + (x - z);
     s = t;
   }
-  return (double)s + (double)e;
+  return make_float2(s, e);
+}
+
+// Exact FP32 -> FP64 conversion built from the bit pattern (sign, exponent
+// rebiased by 1023 - 127 = 896, mantissa shifted by 52 - 23 = 29) for zeros
+// and normal numbers, so that it costs integer instructions instead of a
+// conversion on this chip's narrow FP64 pipe; denormals, infinities and NaN
+// take the hardware conversion.
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) {
+    if ((b << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)b << 32));  // +-0
+    return (double)x;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                          ((unsigned long long)(e + 896u) << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// Float pair of an FP64 value: hi = fl32(u), lo = fl32(u - hi), with one FP64
+// instruction (the rounding to FP32).  u - hi is exact in FP64 and, for
+// same-sign finite doubles, equals the integer difference of their bit
+// patterns (magnitude order) times 2^(e_u - 52), e_u the unbiased exponent of
+// u (the doubles between u and hi all lie in u's binade, or the one below
+// when hi rounded up to a power of two); converting that integer to FP32
+// rounds to nearest exactly as fl32(u - hi) does, and the power-of-two scale
+// is exact for |u| >= 2^-74.  Below that, and for non-finite hi, lo = 0.
+__device__ __forceinline__ void split_pair(double u, float& hi, float& lo) {
+  hi = __double2float_rn(u);
+  const unsigned fb = __float_as_uint(hi);
+  const unsigned ef = (fb >> 23) & 0xffu;
+  const long long ub = __double_as_longlong(u);
+  const int eu = (int)((ub >> 52) & 0x7ff);
+  if (ef == 0u || ef == 255u || eu < 949) {
+    lo = 0.f;
+    return;
+  }
+  const long long hb = __double_as_longlong(f2d(hi));
+  long long n = ub - hb;  // |n| < 2^30
+  if (ub < 0) n = -n;     // negative values: the patterns order by magnitude
+  lo = (float)(int)n * __uint_as_float((unsigned)(eu - 948) << 23);
 }
 
 // rho > 0 and p > 0 (p > 0  <=>  2 rho E - |m|^2 > 0 for rho > 0), all finite
@@ -410,33 +450,39 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
   const size_t N = a.N;
   if (STAGE == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) a.out[v * N + i] = -face_sum<NFC>(a, G, i, v) * ivol;
+    for (int v = 0; v < 5; v++) {
+      if constexpr (sizeof(GT) == 4) {
+        const float2 sp = face_sum_pair<NFC>(a, G, i, v);
+        a.out[v * N + i] = -(f2d(sp.x) + f2d(sp.y)) * ivol;
+      } else {
+        a.out[v * N + i] = -face_sum<NFC>(a, G, i, v) * ivol;
+      }
+    }
     return;
   }
   // dt R = w s with w = -dt/|V_i| and s the signed face sum
   const double w = -(*a.dt) * ivol;
+  const double cw = STAGE == 1 ? w : (STAGE == 2 ? 0.25 * w : (2.0 / 3.0) * w);
   double Un[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    const double s = face_sum<NFC>(a, G, i, v);
     const double u0 = a.U0[v * N + i];
-    if (STAGE == 1) {
-      Un[v] = fma(w, s, u0);                                     // U0 + dt R
-    } else if (STAGE == 2) {
-      Un[v] = fma(0.25 * w, s, fma(0.75, u0, 0.25 * a.Us[v * N + i]));  // 3/4 U0 + 1/4 (U1 + dt R)
+    double base;  // the stage's combination of the earlier states
+    if (STAGE == 1) base = u0;                                              // U1 = U0 + dt R
+    else if (STAGE == 2) base = fma(0.75, u0, 0.25 * a.Us[v * N + i]);     // 3/4 U0 + 1/4 (U1 + dt R)
+    else base = fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]);         // 1/3 U0 + 2/3 (U2 + dt R)
+    if constexpr (sizeof(GT) == 4) {
+      const float2 sp = face_sum_pair<NFC>(a, G, i, v);  // s = s.x + s.y
+      Un[v] = fma(cw, f2d(sp.x), fma(cw, f2d(sp.y), base));
     } else {
-      Un[v] = fma((2.0 / 3.0) * w, s, fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]));  // 1/3 U0 + 2/3 (U2 + dt R)
+      Un[v] = fma(cw, face_sum<NFC>(a, G, i, v), base);
     }
   }
 #pragma unroll
   for (int v = 0; v < 5; v++) a.out[v * N + i] = Un[v];
   if (a.hl) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float h = (float)Un[v];
-      a.hl[i * 10 + v] = h;
-      a.hl[i * 10 + 5 + v] = (float)(Un[v] - (double)h);
-    }
+    for (int v = 0; v < 5; v++) split_pair(Un[v], a.hl[i * 10 + v], a.hl[i * 10 + 5 + v]);
   }
   if (!physical(Un)) atomicOr(a.err, 1);
 }
@@ -580,11 +626,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dt_fused(DtArgs a) {
     h = a.dtlen[i];
     if (SPLIT) {
 #pragma unroll
-      for (int v = 0; v < 5; v++) {
-        const float hi = (float)u[v];
-        a.hl[(size_t)i * 10 + v] = hi;
-        a.hl[(size_t)i * 10 + 5 + v] = (float)(u[v] - (double)hi);
-      }
+      for (int v = 0; v < 5; v++) split_pair(u[v], a.hl[(size_t)i * 10 + v], a.hl[(size_t)i * 10 + 5 + v]);
     }
   }
   bool sure = false;

@@ -80,3 +80,22 @@ def test_mixed_deterministic():
         m.rk_step(a)
         m.rk_step(b)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("perturbed", [False, True])
+def test_float_pair_from_bit_patterns_equals_fp64_split(perturbed):
+    """The float pair (hi, lo) of the state is formed in FP64 (hi = fl32(U),
+    lo = fl32(U - hi)) when the caller gives dt, and from bit patterns in the
+    fused time-step kernel and the RK stages otherwise: one step each way from
+    the same state, with the same dt, must give the same state bit for bit.
+    The plain Taylor-Green state has exact zeros (w = 0) and both signs."""
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=3)
+    m = _mesh(nodes, cells, box, 1, Mach=0.1)
+    U = (I.tgv_perturbed_state(nodes, cells, 0.1, 0.05, seed=8) if perturbed
+         else I.tgv_state(nodes, cells, 0.1))
+    a = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    b = a.clone()
+    dt = m.rk_step(a, return_dt=True)
+    m.rk_step(b, dt=dt)
+    m.check_state()
+    assert torch.equal(a, b)

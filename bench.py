@@ -137,10 +137,14 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
+    """Hash of every CUDA source of the library (a stored ncu traffic figure
+    is used only while it matches)."""
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "api.cu"):
-        with open(os.path.join(ROOT, "paper_2609_07387_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_2609_07387_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -265,13 +269,22 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> tuple[float
     weights: central contraction and constant term only, 5 x 354 flops)."""
     w = 4 if mixed else 8
     N, F = m.n_cells, m.n_faces
+    row = (m.K + 1) * 5 * w  # one cell's coefficients
     if kind == "face":
+        # per point: offsets, normal, |dS|; per face: penalty, owner/neighbour ids, 5 totals (FP32 in the
+        # mixed form); per cell: its coefficient row
         flops = FLOPS_FACE_P2_VISC_PER_QP * m.nq * F
-        nbytes = F * (m.nq * 10 * w + w + 2 * 4 + 5 * 8) + N * (m.K + 1) * 5 * w
+        nbytes = F * (m.nq * 10 * w + w + 2 * 4 + 5 * w) + N * row
     else:
+        # per cell: central pseudo-inverse and ids, moments and 1/h (FP32 rows in the mixed form), the
+        # state (or its float pair), the coefficient row; per flagged (or CWENOZ) cell: the directional
+        # pseudo-inverses and ids, and in the gated mixed form also the central coefficients handed to the
+        # second pass (written and read) and the row rewritten
         flops = N * (5 * 354 + frac_dir * (FLOPS_RECON_P2_CWENOZ_PER_CELL - 5 * 354))
-        nbytes = N * (m.K * m.Mc * w + m.Mc * 4 + frac_dir * (m.nd * 3 * m.Md * w + m.nd * m.Md * 4)
-                      + 6 * 8 + 5 * 8 + (m.K + 1) * 5 * w)
+        cell = 7 * 4 if mixed else 7 * 8
+        gated_extra = 2 * 45 * 4 + row if (mixed and frac_dir < 1.0) else 0
+        nbytes = N * (m.K * m.Mc * w + m.Mc * 4 + cell + 5 * 8 + row
+                      + frac_dir * (m.nd * 3 * m.Md * w + m.nd * m.Md * 4 + gated_extra))
     return flops, nbytes
 
 
@@ -285,6 +298,8 @@ def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_di
     flops, nbytes = algorithmic(m, kind, mixed, frac_dir)
     name = {("face", False): "k_face<2,true>", ("recon", False): "k_recon<2,true,6>",
             ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,6>"}[(kind, mixed)]
+    if kind == "recon" and mixed and frac_dir < 1.0:
+        name = "k_recon_mx<2,false,6,gated>+k_recon_fix_mx<6>"
     if mixed:
         alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"
     elif peak64 and 0.3 < peak64 < 5.0:

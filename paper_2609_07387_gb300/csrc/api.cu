@@ -160,16 +160,6 @@ int launch_recon_tiles(const ReconArgsMx& a, cudaStream_t s) {
   return UCNS_OK;
 }
 
-// gated P2 CWENOZ: linear rows for every cell, then CWENOZ entries for the flagged
-template <int ND>
-int launch_recon_gated(const ReconArgsMx& a, cudaStream_t s) {
-  int rc = launch_recon_tiles<2, false, 6, true>(a, s);
-  if (rc) return rc;
-  k_recon_fix_mx<ND><<<4 * 152, 256, 0, s>>>(a);
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
-}
-
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   ReconArgsMx a;
   (void)U;  // read through its float pair m->d.Uhl, written by k_split or the RK stage
@@ -180,10 +170,7 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.Pd = m->d.Pdb;
   a.cell = m->d.cellb;
   a.coef = m->d.coeff;
-  a.list = m->gate_list;
-  a.nlist = m->gate_nlist;
-  a.pos = m->gate_pos;
-  a.ao_s = m->gate_ao;
+  a.gate = m->gate_flag;
   a.sda = m->d.sda;
   a.Pda = m->d.Pda;
   a.err = m->d.err;
@@ -199,8 +186,8 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   const bool gated = m->gate_eval_active;
   if (m->K == 3) return launch_recon_tiles<1, false, 6>(a, s);
   if (m->nd == 0) return launch_recon_tiles<2, false, 6>(a, s);
-  if (m->nd == 6) return gated ? launch_recon_gated<6>(a, s) : launch_recon_tiles<2, true, 6>(a, s);
-  return gated ? launch_recon_gated<4>(a, s) : launch_recon_tiles<2, true, 4>(a, s);
+  if (m->nd == 6) return gated ? launch_recon_tiles<2, false, 6, true>(a, s) : launch_recon_tiles<2, true, 6>(a, s);
+  return gated ? launch_recon_tiles<2, false, 4, true>(a, s) : launch_recon_tiles<2, true, 4>(a, s);
 }
 
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
@@ -422,15 +409,7 @@ int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = 
   if (rc) return rc;
   if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
-    int r = ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
-    if (r) return r;
-    if (mixed(m)) {  // the mixed reconstruction takes the flagged cells as a list
-      UCNS_CUDA(cudaMemsetAsync(m->gate_nlist, 0, sizeof(int32_t), s));
-      k_flag_list<<<nblocks((size_t)m->N), 256, 0, s>>>(m->gate_flag, (int)m->N, m->gate_list, m->gate_pos,
-                                                        m->gate_nlist);
-      UCNS_CUDA(cudaGetLastError());
-    }
-    return UCNS_OK;
+    return ucnsnet::forward(m->mlp, m->gate_X, m->N, nullptr, m->gate_flag, m->gate_thr, s);
   });
   if (rc) return rc;
   m->gate_eval_active = true;
@@ -543,12 +522,7 @@ void device_free(ucns_mesh* m) {
   if (m->gate_X) cudaFree(m->gate_X);
   if (m->gate_flag) cudaFree(m->gate_flag);
   if (m->gate_count) cudaFree(m->gate_count);
-  for (void* p : {(void*)m->gate_list, (void*)m->gate_nlist, (void*)m->gate_pos, (void*)m->gate_ao})
-    if (p) cudaFree(p);
-  m->gate_list = nullptr;
-  m->gate_nlist = nullptr;
-  m->gate_pos = nullptr;
-  m->gate_ao = nullptr;
+
   m->gate_X = nullptr;
   m->gate_flag = nullptr;
   m->gate_count = nullptr;
@@ -898,9 +872,7 @@ int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
   if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
   if (mlp && !m->gate_X) {
     if ((rc = alloc((uint8_t**)&m->gate_X, (size_t)m->N * 64)) || (rc = alloc(&m->gate_flag, (size_t)m->N)) ||
-        (rc = alloc(&m->gate_count, 1)) || (rc = alloc(&m->gate_list, (size_t)m->N)) ||
-        (rc = alloc(&m->gate_nlist, 1)) || (rc = alloc(&m->gate_pos, (size_t)m->N)) ||
-        (rc = alloc(&m->gate_ao, (size_t)48 * m->N)))
+        (rc = alloc(&m->gate_count, 1)))
       return rc;
   }
   m->mlp = mlp;

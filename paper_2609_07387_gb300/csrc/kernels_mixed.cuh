@@ -85,10 +85,7 @@ struct ReconArgsMx {
   float* __restrict__ coef;        // [N][cs]: variable-major, coefficient k of variable v at v (K+1) + k,
                                    // k = 0 the constant term relative to U_ref
   // gated reconstruction (P2 CWENOZ on the flagged cells only)
-  const int32_t* __restrict__ list;  // [n] flagged cells
-  const int32_t* __restrict__ nlist;  // [1] n (device)
-  const int32_t* __restrict__ pos;   // [N] position of a cell in the list, -1 if not flagged
-  float* __restrict__ ao_s;          // [n][48] central coefficients of the flagged cells (5 x 9, padded)
+  const uint8_t* __restrict__ gate;  // [N] flags (nonzero: CWENOZ)
   const int32_t* __restrict__ sda;   // [N][nd Md] directional stencils, cell-contiguous
   const float* __restrict__ Pda;     // [N][nd 3 Md] directional pseudo-inverse rows, cell-contiguous
   int* err;                        // bit 1 set when a bounded wait gave up
@@ -178,14 +175,96 @@ __device__ __forceinline__ void write_var(float* out, int v, float hi_i, float l
   for (int k = 0; k < K; k++) out[k + 1] = cf[k] * (k < 3 ? ih : ih2);
 }
 
+// Second phase of a gated P2 CWENOZ tile (after its linear rows are in
+// sOut): the flagged cells of the tile are compacted in shared memory, their
+// central coefficients ao (xi units, from the linear phase's registers) are
+// parked where the central pseudo-inverse rows were (no longer read), and one
+// warp per flagged cell finishes it: lane (v, s), v < 5, s < nd, contracts
+// directional stencil s of variable v from cell-contiguous copies of the ids
+// and rows; lane (v, 0) gathers the nd results by shuffles and runs the same
+// cwenoz_mx / write_var as the ungated kernel (whose arithmetic and order
+// this reproduces: a fully flagged gate equals it bit for bit), overwriting
+// the cell's linear entries in sOut.  Called by every thread of the block.
+template <int ND>
+__device__ __forceinline__ void gated_cwenoz(const ReconArgsMx& a, const float (&ao)[9], bool flagged, int c, int v,
+                                             int i0, float* sP, const float* sC, float* sOut) {
+  using T = ReconTile<2, true, ND>;
+  constexpr int K = 9, MD = T::MD, CS = T::CS;
+  static_assert(5 * ND <= 32, "one lane per (variable, stencil)");
+  __shared__ int s_n;
+  __shared__ int s_slot[kTC];  // slot of cell c among the flagged
+  __shared__ int s_cell[kTC];  // cell of a slot
+  const int t = threadIdx.x;
+  if (t == 0) s_n = 0;
+  __syncthreads();  // also: every linear-phase read of sP is done
+  if (flagged && v == 0) {
+    const int sl = atomicAdd(&s_n, 1);
+    s_slot[c] = sl;
+    s_cell[sl] = c;
+  }
+  __syncthreads();
+  const int nf = s_n;
+  if (nf == 0) return;
+  float* s_ao = sP;  // [nf][48]
+  if (flagged) {
+#pragma unroll
+    for (int k = 0; k < K; k++) s_ao[s_slot[c] * 48 + v * K + k] = ao[k];
+  }
+  __syncthreads();
+  const float* __restrict__ hl = a.Uhl;
+  const int lane = t & 31;
+  const int lv = lane / ND, lsn = lane - ND * (lane / ND);
+  const bool act = lane < 5 * ND;
+  const int vv = act ? lv : 0, ss = act ? lsn : 0;
+  for (int sl = t >> 5; sl < nf; sl += blockDim.x >> 5) {
+    const int cc = s_cell[sl], ii = i0 + cc;
+    const float hi_i = hl[(size_t)ii * 10 + vv], lo_i = hl[(size_t)ii * 10 + 5 + vv];
+    const int2* js = reinterpret_cast<const int2*>(a.sda + (size_t)ii * T::SD + ss * MD);
+    const float2* ps = reinterpret_cast<const float2*>(a.Pda + (size_t)ii * T::RD + ss * 3 * MD);
+    int jj[MD];
+#pragma unroll
+    for (int q = 0; q < MD / 2; q++) {
+      const int2 w = __ldg(js + q);
+      jj[2 * q] = w.x;
+      jj[2 * q + 1] = w.y;
+    }
+    float bk[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int rp = 0; rp < MD / 2; rp++) {  // members r = 2 rp, 2 rp + 1: rows k MD + r, k < 3
+      const float d0 = pair_diff(hl, jj[2 * rp], vv, hi_i, lo_i), d1 = pair_diff(hl, jj[2 * rp + 1], vv, hi_i, lo_i);
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const float2 P = __ldg(ps + (k * MD + 2 * rp) / 2);
+        bk[k] = fmaf(P.y, d1, fmaf(P.x, d0, bk[k]));
+      }
+    }
+    float b[ND][3];
+#pragma unroll
+    for (int s = 0; s < ND; s++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) b[s][k] = __shfl_sync(0xffffffffu, bk[k], vv * ND + s);
+    if (act && lsn == 0) {
+      float aoc[K];
+#pragma unroll
+      for (int k = 0; k < K; k++) aoc[k] = s_ao[sl * 48 + lv * K + k];
+      float S[6];
+#pragma unroll
+      for (int q = 0; q < 6; q++) S[q] = sC[q * kTC + cc];
+      const float ih = sC[6 * kTC + cc];
+      float cf[9];
+      cwenoz_mx<ND>(aoc, b, S, a, cf);
+      write_var<9>(sOut + cc * CS + lv * (K + 1), lv, hi_i, lo_i, cf, S, ih, a);
+    }
+  }
+}
+
 // One block per tile of kTC cells, thread = (cell c of the tile, variable v).
 // A single thread starts bulk copies of the tile's central pseudo-inverse rows
 // and stencil, its cell rows and (CWENOZ) its directional rows and stencils
 // into shared memory; meanwhile every thread loads its own state.  The
 // coefficient rows are assembled in shared memory and written back with one
-// bulk copy.  GATED (linear weights, first pass of a gated P2 CWENOZ
-// reconstruction): the central coefficients of the flagged cells also go to
-// a.ao_s for k_recon_fix_mx.
+// bulk copy.  GATED (WENO = false, P2): a gated CWENOZ reconstruction, linear
+// weights for every cell first, then gated_cwenoz for the flagged ones.
 template <int ORDER, bool WENO, int ND, bool GATED>
 __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx a) {
   using T = ReconTile<ORDER, WENO, ND>;
@@ -225,10 +304,10 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
     bar_wait(bar, 0);  // the copies into this block's shared memory end before it exits
     return;
   }
-  if (live) {
-    float ao[K];
+  float ao[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = 0.f;
+  for (int k = 0; k < K; k++) ao[k] = 0.f;
+  if (live) {
     const int2* sS2 = reinterpret_cast<const int2*>(sS);
     const float2* sP2 = reinterpret_cast<const float2*>(sP);
 #pragma unroll 3
@@ -239,13 +318,6 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
       for (int k = 0; k < K; k++) {
         const float2 P = sP2[(k * (MC / 2) + mp) * kTC + c];
         ao[k] = fmaf(P.y, d1, fmaf(P.x, d0, ao[k]));
-      }
-    }
-    if (GATED) {
-      const int p = __ldg(&a.pos[i]);
-      if (p >= 0) {
-#pragma unroll
-        for (int k = 0; k < K; k++) a.ao_s[(size_t)p * 48 + v * K + k] = ao[k];
       }
     }
     float S[6];
@@ -282,93 +354,10 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
       for (int q = 5 * (K + 1); q < CS; q++) sOut[c * CS + q] = 0.f;
     }
   }
+  if constexpr (GATED) gated_cwenoz<ND>(a, ao, live && a.gate[i], c, v, i0, sP, sC, sOut);
   fence_smem_to_async();
   __syncthreads();
   if (t == 0) bulk_store(a.coef + (size_t)i0 * CS, sOut, (uint32_t)(nc * CS * 4));
-}
-
-// CWENOZ entries of the flagged cells (P2), overwriting the linear ones that
-// k_recon_mx<2, false, ., true> wrote for them: the central coefficients come from
-// that pass, the directional stencils and rows from cell-contiguous copies;
-// the arithmetic and its order are those of the CWENOZ tile kernel.
-// thread = (list entry, variable), grid-stride over the device-side count
-template <int ND>
-__global__ void __launch_bounds__(256) k_recon_fix_mx(ReconArgsMx a) {
-  using T = ReconTile<2, true, ND>;
-  constexpr int K = 9, MD = T::MD, CS = T::CS;
-  const float* __restrict__ hl = a.Uhl;
-  const int n5 = 5 * __ldg(a.nlist);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n5; t += gridDim.x * blockDim.x) {
-    const int e = t / 5, v = t - 5 * (t / 5);
-    const int i = __ldg(&a.list[e]);
-    const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
-    float ao[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = __ldg(&a.ao_s[(size_t)e * 48 + v * K + k]);
-    float b[ND][3];
-#pragma unroll
-    for (int s = 0; s < ND; s++) {
-      // stencil s: 6 members (three 8-byte loads), 18 rows (nine 8-byte loads)
-      const int2* js = reinterpret_cast<const int2*>(a.sda + (size_t)i * T::SD + s * MD);
-      const float2* ps = reinterpret_cast<const float2*>(a.Pda + (size_t)i * T::RD + s * 3 * MD);
-      int jj[MD];
-      float P[3 * MD];
-#pragma unroll
-      for (int q = 0; q < MD / 2; q++) {
-        const int2 w = __ldg(js + q);
-        jj[2 * q] = w.x;
-        jj[2 * q + 1] = w.y;
-      }
-#pragma unroll
-      for (int q = 0; q < 3 * MD / 2; q++) {
-        const float2 w = __ldg(ps + q);
-        P[2 * q] = w.x;
-        P[2 * q + 1] = w.y;
-      }
-      b[s][0] = b[s][1] = b[s][2] = 0.f;
-#pragma unroll
-      for (int r = 0; r < MD; r++) {
-        const float d = pair_diff(hl, jj[r], v, hi_i, lo_i);
-#pragma unroll
-        for (int k = 0; k < 3; k++) b[s][k] = fmaf(P[k * MD + r], d, b[s][k]);
-      }
-    }
-    float S[6];
-#pragma unroll
-    for (int q = 0; q < 6; q++) S[q] = __ldg(&a.cell[blk(q, kCellRows, i)]);
-    const float ih = __ldg(&a.cell[blk(6, kCellRows, i)]);
-    float cf[9];
-    cwenoz_mx<ND>(ao, b, S, a, cf);
-    write_var<9>(a.coef + (size_t)i * CS + v * (K + 1), v, hi_i, lo_i, cf, S, ih, a);
-  }
-}
-
-// compacted list of the cells whose gate flag is set (order within a block
-// kept, blocks in any order) and every cell's position in it (-1: not
-// flagged); *count must be zero on entry
-__global__ void __launch_bounds__(256) k_flag_list(const uint8_t* __restrict__ flag, int N, int32_t* __restrict__ list,
-                                                   int32_t* __restrict__ pos, int32_t* __restrict__ count) {
-  __shared__ int warp_n[8];
-  __shared__ int base;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool f = i < N && flag[i];
-  const unsigned bal = __ballot_sync(0xffffffffu, f);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) warp_n[w] = __popc(bal);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
-    for (int q = 0; q < 8; q++) {
-      const int n = warp_n[q];
-      warp_n[q] = tot;
-      tot += n;
-    }
-    base = tot ? atomicAdd(count, tot) : 0;
-  }
-  __syncthreads();
-  const int p = base + warp_n[w] + __popc(bal & ((1u << lane) - 1u));
-  if (f) list[p] = i;
-  if (i < N) pos[i] = f ? p : -1;
 }
 
 // float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5

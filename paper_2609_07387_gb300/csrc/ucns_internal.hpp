@@ -100,10 +100,6 @@ struct ucns_mesh {
   void* gate_X = nullptr;              // [N][32] BF16 features
   uint8_t* gate_flag = nullptr;        // [N]
   unsigned long long* gate_count = nullptr;
-  int32_t* gate_list = nullptr;        // [N] flagged cells (mixed form), built with the flags
-  int32_t* gate_nlist = nullptr;       // [1] their number
-  int32_t* gate_pos = nullptr;         // [N] position in the list, -1 if not flagged
-  float* gate_ao = nullptr;            // [N][48] central coefficients of the listed cells
   bool gate_eval_active = false;       // flags valid for the reconstructions of this call
   int gate_check_every = 0;
   int gate_eval_every = 1;

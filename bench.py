@@ -278,13 +278,11 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> tuple[float
     else:
         # per cell: central pseudo-inverse and ids, moments and 1/h (FP32 rows in the mixed form), the
         # state (or its float pair), the coefficient row; per flagged (or CWENOZ) cell: the directional
-        # pseudo-inverses and ids, and in the gated mixed form also the central coefficients handed to the
-        # second pass (written and read) and the row rewritten
+        # pseudo-inverses and ids
         flops = N * (5 * 354 + frac_dir * (FLOPS_RECON_P2_CWENOZ_PER_CELL - 5 * 354))
         cell = 7 * 4 if mixed else 7 * 8
-        gated_extra = 2 * 45 * 4 + row if (mixed and frac_dir < 1.0) else 0
         nbytes = N * (m.K * m.Mc * w + m.Mc * 4 + cell + 5 * 8 + row
-                      + frac_dir * (m.nd * 3 * m.Md * w + m.nd * m.Md * 4 + gated_extra))
+                      + frac_dir * (m.nd * 3 * m.Md * w + m.nd * m.Md * 4))
     return flops, nbytes
 
 
@@ -299,7 +297,7 @@ def roofline(m, prof: dict, mixed: bool, peak64, hbm_gbs: float, n: int, frac_di
     name = {("face", False): "k_face<2,true>", ("recon", False): "k_recon<2,true,6>",
             ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,6>"}[(kind, mixed)]
     if kind == "recon" and mixed and frac_dir < 1.0:
-        name = "k_recon_mx<2,false,6,gated>+k_recon_fix_mx<6>"
+        name = "k_recon_mx<2,false,6,gated>"
     if mixed:
         alu_peak, alu_src = FP32_PEAK_TFLOPS, "FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz"
     elif peak64 and 0.3 < peak64 < 5.0:

@@ -446,38 +446,41 @@ __device__ __forceinline__ void hllc_flux_mx(const float WL[5], const float WR[5
   const float SR = fmaxf(unR + aR, utn + at);
   const float mL = rL * (SL - unL), mR = rR * (SR - unR);
   const float Ss = fdiv(ppR - ppL + unL * mL - unR * mR, mL - mR);
-  // physical flux of the upwind side (momentum with p', energy with the full E + p)
-  auto phys = [&](const float W[5], float r, const float u[3], float pp, float un) {
-    F[0] = r * un;
-    F[1] = W[1] * un + pp * n[0];
-    F[2] = W[2] * un + pp * n[1];
-    F[3] = W[3] * un + pp * n[2];
-    F[4] = (W[4] + pp) * un + c.H_ref * un;
-  };
-  auto star = [&](const float W[5], float r, const float u[3], float p, float un, float S, float m) {
-    // U* - U with r* = (S* - u_n)/(S - S*): d_rho = rho r*, d_m = r* m + rho*(S* - u_n) n,
-    // d_E = r* E + rho* (S* - u_n)(S* + p/(rho (S - u_n)))
-    const float ds = Ss - un;
-    const float rs = fdiv(ds, S - Ss);
-    const float rho_s = r + r * rs;
-    const float E = (c.H_ref - c.p_ref) + W[4];
-    F[0] += S * (r * rs);
-    F[1] += S * fmaf(rho_s * ds, n[0], rs * W[1]);
-    F[2] += S * fmaf(rho_s * ds, n[1], rs * W[2]);
-    F[3] += S * fmaf(rho_s * ds, n[2], rs * W[3]);
-    F[4] += S * fmaf(rho_s * ds, Ss + fdiv(p, m), rs * E);
-  };
-  if (0.f <= SL) {
-    phys(WL, rL, uL, ppL, unL);
-  } else if (0.f <= Ss) {
-    phys(WL, rL, uL, ppL, unL);
-    star(WL, rL, uL, pL, unL, SL, mL);
-  } else if (0.f <= SR) {
-    phys(WR, rR, uR, ppR, unR);
-    star(WR, rR, uR, pR, unR, SR, mR);
-  } else {
-    phys(WR, rR, uR, ppR, unR);
-  }
+  // The flux is that of the upwind side (left when S_L >= 0 or S* >= 0),
+  // plus S (U* - U) of that side in the star region (S_L < 0 on the left,
+  // S_R >= 0 on the right).  Written without branches: the side's
+  // quantities are selected first, so a warp whose faces fall on different
+  // sides runs one path.  Physical flux: momentum with p', energy with the
+  // full E + p.  U* - U with r* = (S* - u_n)/(S - S*): d_rho = rho r*,
+  // d_m = r* m + rho* (S* - u_n) n, d_E = r* E + rho* (S* - u_n)(S* + p/(rho (S - u_n))).
+  const bool left = 0.f <= SL || 0.f <= Ss;
+  const float W0 = left ? WL[0] : WR[0], W1 = left ? WL[1] : WR[1], W2 = left ? WL[2] : WR[2];
+  const float W3 = left ? WL[3] : WR[3], W4 = left ? WL[4] : WR[4];
+  (void)W0;
+  const float r = left ? rL : rR, un = left ? unL : unR, pp = left ? ppL : ppR, p = left ? pL : pR;
+  const float S = left ? SL : SR, m = left ? mL : mR;
+  const bool in_star = left ? SL < 0.f : 0.f <= SR;
+  F[0] = r * un;
+  F[1] = W1 * un + pp * n[0];
+  F[2] = W2 * un + pp * n[1];
+  F[3] = W3 * un + pp * n[2];
+  F[4] = (W4 + pp) * un + c.H_ref * un;
+  const float ds = Ss - un;
+  const float rs = fdiv(ds, S - Ss);
+  const float rho_s = r + r * rs;
+  const float E = (c.H_ref - c.p_ref) + W4;
+  const float t = rho_s * ds;
+  const float d0 = S * (r * rs);
+  const float d1 = S * fmaf(t, n[0], rs * W1);
+  const float d2 = S * fmaf(t, n[1], rs * W2);
+  const float d3 = S * fmaf(t, n[2], rs * W3);
+  const float d4 = S * fmaf(t, Ss + fdiv(p, m), rs * E);
+  // outside the star region these terms may be inf or NaN (S = S*): selected away
+  F[0] += in_star ? d0 : 0.f;
+  F[1] += in_star ? d1 : 0.f;
+  F[2] += in_star ? d2 : 0.f;
+  F[3] += in_star ? d3 : 0.f;
+  F[4] += in_star ? d4 : 0.f;
 }
 
 // viscous flux in FP32 from the reference-relative face state

@@ -676,7 +676,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
         (rc = upload_blocked(&d.cellb, cellrows, kCellRows, m->N, false)) ||
         (rc = upload_cellwise(&d.sda, h.sd, m->nd * m->Md, m->N)) ||
         (rc = upload_cellwise(&d.Pda, h.Pd, rd_rows, m->N)) ||
-        (rc = upload_f32(&d.fqf, h.fq)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
+        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);

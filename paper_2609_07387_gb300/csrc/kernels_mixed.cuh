@@ -97,7 +97,7 @@ struct ReconArgsMx {
 
 struct FaceArgsMx {
   const float* __restrict__ coef;  // [N][cs] cell rows, 16-byte aligned
-  const float* __restrict__ fq;    // [nq][10][F]
+  const float* __restrict__ fq;    // [F][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
   const float* __restrict__ fpen;
   const int32_t* __restrict__ fo;
   const int32_t* __restrict__ fn;
@@ -525,11 +525,13 @@ __global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
   const bool live = f < a.F;
   const int fc = live ? f : a.F - 1;
   const size_t F = a.F;
-  const float* __restrict__ fq = a.fq + (size_t)q * 10 * F + fc;
-  const float xl = fq[0], yl = fq[F], zl = fq[2 * F];
-  const float xr = fq[3 * F], yr = fq[4 * F], zr = fq[5 * F];
-  const float n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
-  const float area = fq[9 * F];
+  // the point's 10 floats, contiguous: five 8-byte loads from one address
+  const float2* __restrict__ fq = reinterpret_cast<const float2*>(a.fq + ((size_t)fc * NQ + q) * 10);
+  const float2 q0 = __ldg(fq), q1 = __ldg(fq + 1), q2 = __ldg(fq + 2), q3 = __ldg(fq + 3), q4 = __ldg(fq + 4);
+  const float xl = q0.x, yl = q0.y, zl = q1.x;
+  const float xr = q1.y, yr = q2.x, zr = q2.y;
+  const float n[3] = {q3.x, q3.y, q4.x};
+  const float area = q4.y;
   const int o = a.fo[fc], nb = a.fn[fc];
   float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
   eval_side_mx<ORDER, false>(a.coef, o, xl, yl, zl, WL, gs);

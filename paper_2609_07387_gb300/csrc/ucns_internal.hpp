@@ -52,7 +52,7 @@ struct DeviceMesh {
   int32_t* fo = nullptr;      // [F] owner
   int32_t* fn = nullptr;      // [F] neighbour
   double* fq = nullptr;       // [nq][10][F] x-x_L(3) x-x_R'(3) n(3) |dS|(1), physical offsets
-  float* fqf = nullptr;       // FP32 copy
+  float* fqf = nullptr;       // FP32 copy, point-contiguous [F][nq][10]
   double* fpen = nullptr;     // [F] alpha / L_int
   // scratch owned by the handle
   double* coef = nullptr;     // [NC][N][5] reconstructed monomial coefficients

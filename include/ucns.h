@@ -99,7 +99,8 @@ typedef struct ucns_mesh ucns_mesh; /* opaque, library-owned */
  *              node.  Every element face must pair with exactly one other
  *              (closed periodic meshes only: UCNS_ERR_MESH otherwise).
  *  out         receives the handle; free it with ucns_mesh_destroy.
- * Errors: INVALID_ARG, MESH (bad node id, non-positive volume, unpaired or
+ * Errors: INVALID_ARG (also n_cells >= 2^31 / 10 = 214,748,364: device
+ * indexing is 32-bit), MESH (bad node id, non-positive volume, unpaired or
  * non-manifold face), NOMEM. */
 int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_nodes,
                      int64_t n_cells, int32_t nodes_per_cell, const double* periodic_box,

@@ -553,7 +553,7 @@ int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_n
     return fail(UCNS_ERR_INVALID_ARG, "nodes/cells must be non-NULL and non-empty");
   if (nodes_per_cell != 8 && nodes_per_cell != 4)
     return fail(UCNS_ERR_INVALID_ARG, "nodes_per_cell must be 8 (hex) or 4 (tet)");
-  if (n_cells >= (int64_t(1) << 31) / 5)
+  if (n_cells >= (int64_t(1) << 31) / 10)
     return fail(UCNS_ERR_INVALID_ARG, "too many cells for 32-bit device indexing");
   if (!periodic_box) return fail(UCNS_ERR_INVALID_ARG, "periodic_box is required (closed periodic meshes only)");
   for (int d = 0; d < 3; d++)

@@ -111,7 +111,10 @@ struct FaceArgsMx {
 // same-sign values within a factor 2 (Sterbenz), so the difference carries no
 // cancellation error beyond the final FP32 rounding, as an FP64 subtraction would
 __device__ __forceinline__ float pair_diff(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
-  return (hl[(size_t)j * 10 + v] - hi_i) + (hl[(size_t)j * 10 + 5 + v] - lo_i);
+  // 32-bit row offset (N < 2^31 / 10, checked on the host): one wide multiply-add
+  // forms the address, the lo part is at a constant 20-byte offset from it
+  const float* r = hl + v + j * 10;
+  return (r[0] - hi_i) + (r[5] - lo_i);
 }
 
 // CWENOZ combination of the central coefficients ao (K = 9, xi units) with the

@@ -105,8 +105,14 @@ def test_features_and_labels_match_oracle(prec):
     assert np.abs(dev - odev).max() <= 1e-6
 
 
-def test_gated_residual_extremes_equal_the_plain_schemes():
-    nodes, cells, box = I.hex_lattice(12, jitter=0.1, seed=6)
+@pytest.mark.parametrize("tets", [False, True])
+def test_gated_residual_extremes_equal_the_plain_schemes(tets):
+    """Hexahedra (6 directional stencils) and tetrahedra (4): a gate that flags
+    every cell gives the ungated CWENOZ residual bit for bit, one that flags
+    none the linear-weight residual, in the FP64 and the mixed form."""
+    nodes, cells, box = I.hex_lattice(12 if not tets else 7, jitter=0.1, seed=6)
+    if tets:
+        cells = I.split_tets(cells)
     U = I.tgv_perturbed_state(nodes, cells, 1.25, 0.05, seed=2)
     for prec in (0, 1):
         mw = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, Mach=1.25, precision=prec))

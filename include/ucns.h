@@ -175,6 +175,18 @@ int ucns_check_state(ucns_mesh* mesh, void* stream);
  * Errors: INVALID_ARG, STATE, CUDA. */
 int ucns_time_step_static(const ucns_mesh* mesh, const double* U, double* dt, void* stream);
 
+/* The float pair of FP64 values as the mixed form stores its states (no
+ * counterpart in the paper, which computes in FP64 only; its Sec. 7 names
+ * mixed precision as future work): hi[k] = fl32(u[k]) and lo[k] =
+ * fl32(u[k] - hi[k]), both rounded to nearest even, so that hi + lo carries
+ * u to about 2^-48 relative and the difference of two pairs taken leading
+ * part first is exact up to its final rounding.  Formed from the bit patterns
+ * with one FP64 -> FP32 rounding (the routine the solver's kernels use);
+ * lo = 0 where |u| < 2^-74 or hi is not a normal FP32 number.
+ *  u      device [n] float64 (input);  hi, lo  device [n] float32 (output).
+ *  n      >= 0.   Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+int ucns_float_pair(const double* u, float* hi, float* lo, int64_t n, void* stream);
+
 /* Diagnostics of U (device [5][n_cells]) into *out (host).  Synchronises. */
 int ucns_diagnostics(ucns_mesh* mesh, const double* U, ucns_diag* out, void* stream);
 

@@ -324,10 +324,24 @@ int launch_dt_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   return UCNS_OK;
 }
 
-// the CFL time step of U into m->d.dt at the start of a Runge-Kutta step, one
-// fused kernel; the mixed form also leaves the float pair of U in m->d.Uhl
-// (returned in *split)
-int launch_dt_step(ucns_mesh* m, const double* U, cudaStream_t s, bool* split) {
+// The CFL time step of U into m->d.dt at the start of a Runge-Kutta step, on
+// the mesh's side stream: it waits for U on s, and s waits for it (join_dt)
+// only before the first use of dt (the first RK stage), so the reduction
+// overlaps the float pair, the gate and the first reconstruction.
+int launch_dt_async(ucns_mesh* m, const double* U, cudaStream_t s) {
+  if (!m->aux) {
+    cudaStream_t st;
+    cudaEvent_t e1, e2;
+    UCNS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    m->aux = (void*)st;
+    UCNS_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+    m->ev_u = (void*)e1;
+    UCNS_CUDA(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    m->ev_dt = (void*)e2;
+  }
+  cudaStream_t aux = (cudaStream_t)m->aux;
+  UCNS_CUDA(cudaEventRecord((cudaEvent_t)m->ev_u, s));
+  UCNS_CUDA(cudaStreamWaitEvent(aux, (cudaEvent_t)m->ev_u, 0));
   const ucns_params& p = m->P;
   DtArgs a;
   a.U = U;
@@ -335,19 +349,23 @@ int launch_dt_step(ucns_mesh* m, const double* U, cudaStream_t s, bool* split) {
   a.part = m->d.dt_part;
   a.count = m->d.dt_count;
   a.dt = m->d.dt;
-  a.hl = m->d.Uhl;
   a.err = m->d.err;
   a.N = (int)m->N;
   a.gam = p.gamma;
   a.visc = p.reynolds > 0.0 ? p.prandtl / (2.0 * p.gamma * (1.0 / p.reynolds)) : 0.0;
   a.cfl = p.cfl;
-  *split = mixed(m);
-  return timed(m, kKindDt, s, [&] {
-    if (mixed(m)) k_dt_fused<true><<<nblocks((size_t)m->N), kRedThreads, 0, s>>>(a);
-    else k_dt_fused<false><<<nblocks((size_t)m->N), kRedThreads, 0, s>>>(a);
+  int rc = timed(m, kKindDt, aux, [&] {
+    k_dt_fused<<<nblocks((size_t)m->N), kRedThreads, 0, aux>>>(a);
     UCNS_CUDA(cudaGetLastError());
     return UCNS_OK;
   });
+  if (rc) return rc;
+  UCNS_CUDA(cudaEventRecord((cudaEvent_t)m->ev_dt, aux));
+  return UCNS_OK;
+}
+int join_dt(ucns_mesh* m, cudaStream_t s) {
+  UCNS_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)m->ev_dt, 0));
+  return UCNS_OK;
 }
 
 int launch_recon(ucns_mesh* m, const double* U, cudaStream_t s) {
@@ -375,7 +393,7 @@ int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
 
 // the indicator features of U into X (BF16) and Xf (FP32, or null); the
 // mixed form reads U through its float pair, split here
-int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s, bool split = true) {
+int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s) {
   FeatArgs a;
   a.U = U;
   a.Uhl = m->d.Uhl;
@@ -389,7 +407,7 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
   a.N = (int)m->N;
   a.gam = (float)m->P.gamma;
   if (mixed(m)) {
-    int rc = split ? launch_split_raw(m, U, s) : UCNS_OK;
+    int rc = launch_split_raw(m, U, s);
     if (rc) return rc;
     k_features_mx<<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
   } else {
@@ -400,12 +418,11 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
 }
 
 // features of U and the network's flags, once per call of the solver; for the
-// mixed form this leaves the float pair of U in m->d.Uhl (split_fresh: it is
-// there already)
-int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr, bool split_fresh = false) {
+// mixed form this leaves the float pair of U in m->d.Uhl
+int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr) {
   m->gate_eval_active = false;
   if (!m->gate_on || !m->mlp) return UCNS_OK;
-  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s, !split_fresh); });
+  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s); });
   if (rc) return rc;
   if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
@@ -454,8 +471,8 @@ int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
   return UCNS_OK;
 }
 
-// split_fresh: m->d.Uhl already holds the float pair of U (mixed form)
-int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool split_fresh = false) {
+// dt_pending: m->d.dt is being computed on the side stream (join before use)
+int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = false) {
   int rc;
   double* W = m->d.Ustage;
   const int64_t step = m->gate_steps;
@@ -465,15 +482,15 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool split_fresh = f
     m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  bool split_done = split_fresh;
+  bool split_done = false;
   if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
     m->gate_eval_active = true;  // reuse the flags of the last evaluation
   } else {
-    if ((rc = gate_eval(m, U, s, &split_done, split_fresh))) return rc;  // flags of U^n serve all three stages
+    if ((rc = gate_eval(m, U, s, &split_done))) return rc;  // flags of U^n serve all three stages
     m->gate_flags_valid = m->gate_eval_active;
   }
   if ((!split_done && (rc = launch_split(m, U, s))) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
-      (rc = launch_rk(m, 1, U, U, W, s)))
+      (dt_pending && (rc = join_dt(m, s))) || (rc = launch_rk(m, 1, U, U, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
     return rc;
@@ -720,14 +737,13 @@ int ucns_rk_step(ucns_mesh* m, double* U, double* dt_inout, void* stream) {
   if (!U) return fail(UCNS_ERR_INVALID_ARG, "U is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const bool given = dt_inout && *dt_inout > 0.0;
-  bool split = false;
   if (given) {
     k_set_scalar<<<1, 1, 0, s>>>(m->d.dt, *dt_inout);  // by value: no host buffer outlives the call
     UCNS_CUDA(cudaGetLastError());
-  } else if ((rc = launch_dt_step(m, U, s, &split))) {
+  } else if ((rc = launch_dt_async(m, U, s))) {
     return rc;
   }
-  if ((rc = rk_step_device(m, U, s, split))) return rc;
+  if ((rc = rk_step_device(m, U, s, !given))) return rc;
   if (dt_inout && !given) {
     UCNS_CUDA(cudaMemcpyAsync(dt_inout, m->d.dt, sizeof(double), cudaMemcpyDeviceToHost, s));
     return read_error_word(m, s);
@@ -746,10 +762,8 @@ int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_
   double* tacc = m->d.dt + 1;  // device accumulator of the simulated time
   k_set_scalar<<<1, 1, 0, s>>>(tacc, 0.0);
   for (int k = 0; k < n_steps; k++) {
-    bool split = false;
-    if ((rc = launch_dt_step(m, m->d.Uhost, s, &split))) return rc;
-    k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);
-    if ((rc = rk_step_device(m, m->d.Uhost, s, split))) return rc;
+    if ((rc = launch_dt_async(m, m->d.Uhost, s)) || (rc = rk_step_device(m, m->d.Uhost, s, true))) return rc;
+    k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);  // after the step, which joined the time step
   }
   UCNS_CUDA(cudaGetLastError());
   double t = 0.0;
@@ -757,6 +771,16 @@ int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_
   UCNS_CUDA(cudaMemcpyAsync(&t, tacc, sizeof(double), cudaMemcpyDeviceToHost, s));
   if ((rc = read_error_word(m, s))) return rc;
   if (t_inout) *t_inout += t;
+  return UCNS_OK;
+}
+
+int ucns_float_pair(const double* u, float* hi, float* lo, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!u || !hi || !lo))) return fail(UCNS_ERR_INVALID_ARG, "u, hi, lo must be non-NULL, n >= 0");
+  if (n == 0) return UCNS_OK;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > INT32_MAX) return fail(UCNS_ERR_INVALID_ARG, "n too large");
+  k_float_pair<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(u, hi, lo, n);
+  UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
 
@@ -952,6 +976,9 @@ int ucns_mesh_info(const ucns_mesh* m, int64_t* info) {
 void ucns_mesh_destroy(ucns_mesh* m) {
   if (!m) return;
   device_free(m);
+  if (m->aux) cudaStreamDestroy((cudaStream_t)m->aux);
+  if (m->ev_u) cudaEventDestroy((cudaEvent_t)m->ev_u);
+  if (m->ev_dt) cudaEventDestroy((cudaEvent_t)m->ev_dt);
   delete m;
 }
 

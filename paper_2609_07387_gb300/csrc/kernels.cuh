@@ -599,7 +599,6 @@ struct DtArgs {
   double* part;                      // [gridDim.x] block minima
   unsigned* count;                   // blocks done (zero between launches)
   double* dt;                        // [1] CFL * minimum
-  float* hl;                         // [N][10] float pair of U (SPLIT)
   int* err;
   int N;
   double gam, visc, cfl;
@@ -608,10 +607,9 @@ struct DtArgs {
 // One thread per cell: the block's minimum of the CFL limit, equal bit for
 // bit to that of dt_limit_v (FP32 estimates first, the FP64 limit only near
 // the block's minimum estimate or where the estimate is not sure, as in
-// k_dt_partial, here with the state held in registers); SPLIT also writes the
-// state's float pair (as k_split).  The last block to finish (a counter, no
-// waiting) reduces the block minima in index order and writes dt.
-template <bool SPLIT>
+// k_dt_partial, here with the state held in registers).  The last block to
+// finish (a counter, no waiting) reduces the block minima in index order and
+// writes dt.
 __global__ void __launch_bounds__(kRedThreads) k_dt_fused(DtArgs a) {
   __shared__ double sm[kRedThreads];
   __shared__ float smf[kRedThreads];
@@ -624,10 +622,6 @@ __global__ void __launch_bounds__(kRedThreads) k_dt_fused(DtArgs a) {
   if (live) {
     load_state(a.U, n, i, u);
     h = a.dtlen[i];
-    if (SPLIT) {
-#pragma unroll
-      for (int v = 0; v < 5; v++) split_pair(u[v], a.hl[(size_t)i * 10 + v], a.hl[(size_t)i * 10 + 5 + v]);
-    }
   }
   bool sure = false;
   float e = INFINITY;

@@ -369,10 +369,14 @@ __global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, flo
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= 5 * N) return;
   const int i = k / 5, v = k - 5 * (k / 5);
-  const double u = U[(size_t)v * N + i];
-  const float h = (float)u;
-  hl[(size_t)i * 10 + v] = h;
-  hl[(size_t)i * 10 + 5 + v] = (float)(u - (double)h);
+  split_pair(U[(size_t)v * N + i], hl[(size_t)i * 10 + v], hl[(size_t)i * 10 + 5 + v]);
+}
+
+// float pairs of a flat array (the C ABI's ucns_float_pair)
+__global__ void __launch_bounds__(256) k_float_pair(const double* __restrict__ u, float* __restrict__ hi,
+                                                    float* __restrict__ lo, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) split_pair(u[k], hi[k], lo[k]);
 }
 
 // value at the physical offset (x, y, z) from the centroid into U; gradient

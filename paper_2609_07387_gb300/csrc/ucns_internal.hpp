@@ -108,6 +108,12 @@ struct ucns_mesh {
   int64_t gate_steps = 0;
   double* gate_R = nullptr;            // [2][5][N] residuals of the check
   float* label_out = nullptr;          // set only inside ucns_gate_labels
+  // side stream of the time-step reduction (it overlaps the first stage's
+  // reconstruction) and its two events (cudaStream_t / cudaEvent_t), created
+  // on first use, released by ucns_mesh_destroy
+  void* aux = nullptr;
+  void* ev_u = nullptr;
+  void* ev_dt = nullptr;
   // opt-in kernel timing
   bool prof = false;
   struct ProfRec {

@@ -43,7 +43,7 @@ EXPORTS = (
     "ucns_mlp_create", "ucns_mlp_destroy", "ucns_mlp_get_params", "ucns_mlp_set_params", "ucns_mlp_forward",
     "ucns_mlp_grad", "ucns_mlp_train", "ucns_mlp_check",
     "ucns_gate_features", "ucns_gate_labels", "ucns_gate_attach", "ucns_gate_enable", "ucns_gate_flagged",
-    "ucns_gate_configure", "ucns_gate_check",
+    "ucns_gate_configure", "ucns_gate_check", "ucns_float_pair",
 )
 MLP_PARAMS = 6337
 
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = True):
         lib.ucns_gate_flagged.argtypes = [P, P, P]
         lib.ucns_gate_configure.argtypes = [P, I32, I32, C.c_double]
         lib.ucns_gate_check.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(I32), P]
+        lib.ucns_float_pair.argtypes = [P, P, P, I64, P]
         for name in EXPORTS:
             if name not in ("ucns_last_error", "ucns_mesh_destroy", "ucns_mlp_destroy"):
                 getattr(lib, name).restype = C.c_int
@@ -148,6 +149,21 @@ def _dev_ptr(t, n_cells: int) -> int:
             and tuple(t.shape) == (5, n_cells)):
         raise ValueError(f"expected a contiguous cuda float64 tensor of shape (5, {n_cells})")
     return t.data_ptr()
+
+
+def float_pair(u, stream=None):
+    """(hi, lo) float32 device tensors of a float64 device tensor u (any shape,
+    contiguous): hi = fl32(u), lo = fl32(u - hi), as the mixed form stores its
+    states (ucns_float_pair)."""
+    import torch
+
+    if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()):
+        raise ValueError("u must be a contiguous float64 CUDA tensor")
+    lib = load()
+    hi = torch.empty(u.shape, dtype=torch.float32, device=u.device)
+    lo = torch.empty_like(hi)
+    _check(lib, lib.ucns_float_pair(u.data_ptr(), hi.data_ptr(), lo.data_ptr(), u.numel(), _stream_ptr(stream)))
+    return hi, lo
 
 
 @dataclass

@@ -82,20 +82,23 @@ def test_mixed_deterministic():
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("perturbed", [False, True])
-def test_float_pair_from_bit_patterns_equals_fp64_split(perturbed):
-    """The float pair (hi, lo) of the state is formed in FP64 (hi = fl32(U),
-    lo = fl32(U - hi)) when the caller gives dt, and from bit patterns in the
-    fused time-step kernel and the RK stages otherwise: one step each way from
-    the same state, with the same dt, must give the same state bit for bit.
-    The plain Taylor-Green state has exact zeros (w = 0) and both signs."""
-    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=3)
-    m = _mesh(nodes, cells, box, 1, Mach=0.1)
-    U = (I.tgv_perturbed_state(nodes, cells, 0.1, 0.05, seed=8) if perturbed
-         else I.tgv_state(nodes, cells, 0.1))
-    a = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
-    b = a.clone()
-    dt = m.rk_step(a, return_dt=True)
-    m.rk_step(b, dt=dt)
-    m.check_state()
-    assert torch.equal(a, b)
+def test_float_pair_equals_its_definition():
+    """The float pair the mixed form's kernels form from bit patterns is
+    hi = fl32(u), lo = fl32(u - hi) (round to nearest even) bit for bit:
+    values over 40 decades of both signs, exact zeros, ties to even, values
+    just below powers of two (hi rounds up across the binade), the largest
+    finite floats, and the documented lo = 0 below 2^-74."""
+    rng = np.random.default_rng(12)
+    u = np.concatenate([
+        rng.normal(size=200000) * 10.0 ** rng.integers(-20, 20, 200000),
+        np.array([0.0, -0.0, 1.0, -1.0, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, -(1 + 2.0 ** -24), 2 - 2.0 ** -30,
+                  np.nextafter(4.0, 0.0), 178.57142857142858, 3.0e38, -3.0e38, 2.0 ** -74, 2.0 ** -73, 1e-30]),
+    ])
+    hi, lo = ucns.float_pair(torch.from_numpy(u).cuda())
+    hi, lo = hi.cpu().numpy(), lo.cpu().numpy()
+    hi_ref = u.astype(np.float32)
+    lo_ref = (u - hi_ref.astype(np.float64)).astype(np.float32)
+    lo_ref[np.abs(u) < 2.0 ** -74] = 0.0
+    assert np.array_equal(hi.view(np.uint32), hi_ref.view(np.uint32))
+    assert np.array_equal(lo.view(np.uint32) & 0x7fffffff, lo_ref.view(np.uint32) & 0x7fffffff)  # +-0 alike
+    assert np.array_equal(lo, lo_ref)

@@ -361,15 +361,23 @@ __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
 }
 
 // ------------------------------------------- residual + Runge-Kutta stage
+// the cell's face ids (face << 1 | 1 where the cell is the neighbour), read
+// once for all five variables
 template <int NFC>
-__device__ __forceinline__ double face_sum(const RKArgs& a, const double* __restrict__ G, int i, int v) {
+__device__ __forceinline__ void cell_faces(const RKArgs& a, int i, int (&e)[NFC]) {
+#pragma unroll
+  for (int j = 0; j < NFC; j++) e[j] = __ldg(&a.cf[(size_t)j * a.N + i]);
+}
+
+template <int NFC>
+__device__ __forceinline__ double face_sum(const RKArgs& a, const double* __restrict__ G, const int (&e)[NFC],
+                                           int v) {
   double s = 0.0;
 #pragma unroll
   for (int j = 0; j < NFC; j++) {
-    const int e = __ldg(&a.cf[(size_t)j * a.N + i]);
     // sigma G_f: the neighbour side flips the sign bit (an integer XOR, not an FP64 op)
-    const long long gb = __double_as_longlong(__ldg(&G[(size_t)v * a.F + (e >> 1)]));
-    s += __longlong_as_double(gb ^ ((long long)(e & 1) << 63));
+    const long long gb = __double_as_longlong(__ldg(&G[(size_t)v * a.F + (e[j] >> 1)]));
+    s += __longlong_as_double(gb ^ ((long long)(e[j] & 1) << 63));
   }
   return s;
 }
@@ -378,11 +386,12 @@ __device__ __forceinline__ double face_sum(const RKArgs& a, const double* __rest
 // by error-free transformations (Knuth's TwoSum), so that it keeps the
 // accuracy of a double-length sum (errors of order u^2 sum |G|, u = 2^-24)
 template <int NFC>
-__device__ __forceinline__ float2 face_sum_pair(const RKArgs& a, const float* __restrict__ G, int i, int v) {
+__device__ __forceinline__ float2 face_sum_pair(const RKArgs& a, const float* __restrict__ G, const int (&ce)[NFC],
+                                                int v) {
   float s = 0.f, e = 0.f;
 #pragma unroll
   for (int j = 0; j < NFC; j++) {
-    const int c = __ldg(&a.cf[(size_t)j * a.N + i]);
+    const int c = ce[j];
     const int gb = __float_as_int(__ldg(&G[(size_t)v * a.F + (c >> 1)]));
     const float x = __int_as_float(gb ^ ((c & 1) << 31));
     const float t = s + x, z = t - s;
@@ -446,16 +455,18 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
   const GT* __restrict__ G = reinterpret_cast<const GT*>(a.G);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
+  int fe[NFC];
+  cell_faces<NFC>(a, i, fe);
   const double ivol = a.inv_vol[i];
   const size_t N = a.N;
   if (STAGE == 0) {
 #pragma unroll
     for (int v = 0; v < 5; v++) {
       if constexpr (sizeof(GT) == 4) {
-        const float2 sp = face_sum_pair<NFC>(a, G, i, v);
+        const float2 sp = face_sum_pair<NFC>(a, G, fe, v);
         a.out[v * N + i] = -(f2d(sp.x) + f2d(sp.y)) * ivol;
       } else {
-        a.out[v * N + i] = -face_sum<NFC>(a, G, i, v) * ivol;
+        a.out[v * N + i] = -face_sum<NFC>(a, G, fe, v) * ivol;
       }
     }
     return;
@@ -472,10 +483,10 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
     else if (STAGE == 2) base = fma(0.75, u0, 0.25 * a.Us[v * N + i]);     // 3/4 U0 + 1/4 (U1 + dt R)
     else base = fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]);         // 1/3 U0 + 2/3 (U2 + dt R)
     if constexpr (sizeof(GT) == 4) {
-      const float2 sp = face_sum_pair<NFC>(a, G, i, v);  // s = s.x + s.y
+      const float2 sp = face_sum_pair<NFC>(a, G, fe, v);  // s = s.x + s.y
       Un[v] = fma(cw, f2d(sp.x), fma(cw, f2d(sp.y), base));
     } else {
-      Un[v] = fma(cw, face_sum<NFC>(a, G, i, v), base);
+      Un[v] = fma(cw, face_sum<NFC>(a, G, fe, v), base);
     }
   }
 #pragma unroll

@@ -547,19 +547,23 @@ __global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
   hllc_flux_mx(WL, WR, n, a.c, Fc);
   float flux[5];
   if (VISC) {
-    const float pen = a.fpen[fc];
-    float Wf[5], gf[5][3];
+    // twice the penalised face gradient, 2 alpha/L [U] n + (grad U_L + grad U_R):
+    // the viscous flux is linear in the gradient and scaling by 2 is exact, so
+    // the flux of this gradient is exactly 2 F_v (and the halving of grad U_L +
+    // grad U_R drops out)
+    const float pen2 = 2.f * a.fpen[fc];
+    float Wf[5], gf2[5][3];
 #pragma unroll
     for (int v = 0; v < 5; v++) {
-      const float jump = pen * (WR[v] - WL[v]);
+      const float jump2 = pen2 * (WR[v] - WL[v]);
       Wf[v] = 0.5f * (WL[v] + WR[v]);
 #pragma unroll
-      for (int j = 0; j < 3; j++) gf[v][j] = fmaf(jump, n[j], 0.5f * gs[v][j]);
+      for (int j = 0; j < 3; j++) gf2[v][j] = fmaf(jump2, n[j], gs[v][j]);
     }
-    float Fv[5];
-    viscous_flux_mx(Wf, gf, n, a.c, Fv);
+    float Fv2[5];
+    viscous_flux_mx(Wf, gf2, n, a.c, Fv2);
 #pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] = (Fc[v] - Fv[v]) * area;
+    for (int v = 0; v < 5; v++) flux[v] = fmaf(-0.5f, Fv2[v], Fc[v]) * area;
   } else {
 #pragma unroll
     for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;

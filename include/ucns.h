@@ -144,6 +144,16 @@ int ucns_residual(ucns_mesh* mesh, const double* U, double* R, void* stream);
  * ucns_check_state().  Errors: STATE, INVALID_ARG, CUDA, NONPHYSICAL. */
 int ucns_rk_step(ucns_mesh* mesh, double* U, double* dt_inout, void* stream);
 
+/* n_steps SSP-RK3 steps of U (device [5][n_cells], internal order, updated in
+ * place), each with the CFL time step computed on the device, in one call:
+ * the same arithmetic as n_steps calls of ucns_rk_step(dt_inout = NULL), bit
+ * for bit, with less per-step work around the kernels (the mixed form carries
+ * its float pair of the state from one step to the next, since nothing can
+ * modify U in between).  *t_inout (host, may be NULL) is advanced by the total
+ * simulated time.  Synchronises (reads the time and the error word).
+ * Errors: STATE, INVALID_ARG, CUDA, NONPHYSICAL. */
+int ucns_rk_steps(ucns_mesh* mesh, double* U, int32_t n_steps, double* t_inout, void* stream);
+
 /* Host-buffer variant: copies U_host (pinned or pageable [5][n_cells], internal
  * order) to a library-owned device buffer, runs n_steps SSP-RK3 steps with the
  * CFL time step, copies the result back and synchronises.  *t_inout (may be

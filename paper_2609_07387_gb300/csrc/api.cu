@@ -278,7 +278,7 @@ int launch_face_raw(ucns_mesh* m, cudaStream_t s) {
 }
 
 int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out,
-                  cudaStream_t s) {
+                  cudaStream_t s, bool keep_pair = false) {
   RKArgs a;
   a.U0 = U0;
   a.Us = Us;
@@ -288,7 +288,8 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
   a.inv_vol = m->d.inv_vol;
   a.dt = m->d.dt;
   a.err = m->d.err;
-  a.hl = (mixed(m) && (stage == 1 || stage == 2)) ? m->d.Uhl : nullptr;  // next stage reconstructs out
+  // the next stage (or, keep_pair, the next step) reconstructs out from its float pair
+  a.hl = (mixed(m) && (stage == 1 || stage == 2 || (stage == 3 && keep_pair))) ? m->d.Uhl : nullptr;
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.gm1 = m->P.gamma - 1.0;
@@ -384,8 +385,9 @@ int launch_split(ucns_mesh* m, const double* U, cudaStream_t s) {
 int launch_face(ucns_mesh* m, cudaStream_t s) {
   return timed(m, kKindFace, s, [&] { return launch_face_raw(m, s); });
 }
-int launch_rk(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out, cudaStream_t s) {
-  return timed(m, kKindRK, s, [&] { return launch_rk_raw(m, stage, U0, Us, out, s); });
+int launch_rk(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out, cudaStream_t s,
+              bool keep_pair = false) {
+  return timed(m, kKindRK, s, [&] { return launch_rk_raw(m, stage, U0, Us, out, s, keep_pair); });
 }
 int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindDt, s, [&] { return launch_dt_raw(m, U, s); });
@@ -393,7 +395,7 @@ int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
 
 // the indicator features of U into X (BF16) and Xf (FP32, or null); the
 // mixed form reads U through its float pair, split here
-int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s) {
+int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStream_t s, bool split = true) {
   FeatArgs a;
   a.U = U;
   a.Uhl = m->d.Uhl;
@@ -407,7 +409,7 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
   a.N = (int)m->N;
   a.gam = (float)m->P.gamma;
   if (mixed(m)) {
-    int rc = launch_split_raw(m, U, s);
+    int rc = split ? launch_split_raw(m, U, s) : UCNS_OK;
     if (rc) return rc;
     k_features_mx<<<nblocks((size_t)m->N, 128), 128, 0, s>>>(a);
   } else {
@@ -422,7 +424,8 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
 int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr) {
   m->gate_eval_active = false;
   if (!m->gate_on || !m->mlp) return UCNS_OK;
-  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s); });
+  const bool have_pair = split_done && *split_done;
+  int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s, !have_pair); });
   if (rc) return rc;
   if (split_done) *split_done = mixed(m);
   rc = timed(m, kKindMlp, s, [&] {
@@ -471,8 +474,12 @@ int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
   return UCNS_OK;
 }
 
-// dt_pending: m->d.dt is being computed on the side stream (join before use)
-int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = false) {
+// dt_pending: m->d.dt is being computed on the side stream (join before use).
+// pair_fresh: m->d.Uhl already holds the float pair of U (mixed form; the
+// previous step of the same call wrote it).  keep_pair: the last stage also
+// writes the float pair of the new state, for the next step of the same call.
+int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = false, bool pair_fresh = false,
+                   bool keep_pair = false) {
   int rc;
   double* W = m->d.Ustage;
   const int64_t step = m->gate_steps;
@@ -482,7 +489,7 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
     m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  bool split_done = false;
+  bool split_done = pair_fresh;
   if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
     m->gate_eval_active = true;  // reuse the flags of the last evaluation
   } else {
@@ -494,7 +501,7 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
     return rc;
-  if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 3, U, W, U, s)))
+  if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 3, U, W, U, s, keep_pair)))
     return rc;
   return UCNS_OK;
 }
@@ -751,6 +758,34 @@ int ucns_rk_step(ucns_mesh* m, double* U, double* dt_inout, void* stream) {
   return UCNS_OK;
 }
 
+// n_steps CFL steps of a device state within one call: the float pair of the
+// state carries from one step to the next (the caller cannot touch U in
+// between); the simulated time accumulates on the device
+int rk_steps_device(ucns_mesh* m, double* U, int32_t n_steps, cudaStream_t s) {
+  int rc;
+  double* tacc = m->d.dt + 1;  // device accumulator of the simulated time
+  k_set_scalar<<<1, 1, 0, s>>>(tacc, 0.0);
+  for (int k = 0; k < n_steps; k++) {
+    if ((rc = launch_dt_async(m, U, s)) || (rc = rk_step_device(m, U, s, true, k > 0, k + 1 < n_steps))) return rc;
+    k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);  // after the step, which joined the time step
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int ucns_rk_steps(ucns_mesh* m, double* U, int32_t n_steps, double* t_inout, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!U || n_steps < 0) return fail(UCNS_ERR_INVALID_ARG, "U is NULL or n_steps < 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = rk_steps_device(m, U, n_steps, s))) return rc;
+  double t = 0.0;
+  UCNS_CUDA(cudaMemcpyAsync(&t, m->d.dt + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if ((rc = read_error_word(m, s))) return rc;
+  if (t_inout) *t_inout += t;
+  return UCNS_OK;
+}
+
 int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_inout, void* stream) {
   int rc = check_ready(m);
   if (rc) return rc;
@@ -759,16 +794,10 @@ int ucns_rk_steps_host(ucns_mesh* m, double* U_host, int32_t n_steps, double* t_
   const size_t bytes = (size_t)5 * m->N * sizeof(double);
   if (!m->d.Uhost && (rc = alloc(&m->d.Uhost, (size_t)5 * m->N))) return rc;
   UCNS_CUDA(cudaMemcpyAsync(m->d.Uhost, U_host, bytes, cudaMemcpyHostToDevice, s));
-  double* tacc = m->d.dt + 1;  // device accumulator of the simulated time
-  k_set_scalar<<<1, 1, 0, s>>>(tacc, 0.0);
-  for (int k = 0; k < n_steps; k++) {
-    if ((rc = launch_dt_async(m, m->d.Uhost, s)) || (rc = rk_step_device(m, m->d.Uhost, s, true))) return rc;
-    k_add_scalar<<<1, 1, 0, s>>>(tacc, m->d.dt);  // after the step, which joined the time step
-  }
-  UCNS_CUDA(cudaGetLastError());
+  if ((rc = rk_steps_device(m, m->d.Uhost, n_steps, s))) return rc;
   double t = 0.0;
   UCNS_CUDA(cudaMemcpyAsync(U_host, m->d.Uhost, bytes, cudaMemcpyDeviceToHost, s));
-  UCNS_CUDA(cudaMemcpyAsync(&t, tacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  UCNS_CUDA(cudaMemcpyAsync(&t, m->d.dt + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   if ((rc = read_error_word(m, s))) return rc;
   if (t_inout) *t_inout += t;
   return UCNS_OK;

@@ -35,7 +35,7 @@ ERRORS = {
 
 # every entry point declared in include/ucns.h
 EXPORTS = (
-    "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps_host",
+    "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps", "ucns_rk_steps_host",
     "ucns_check_state", "ucns_diagnostics", "ucns_time_step", "ucns_time_step_static", "ucns_profile",
     "ucns_profile_read",
     "ucns_cell_order", "ucns_mesh_info",
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         lib.ucns_stencil.argtypes = [P, I64, I32, P, P]
         lib.ucns_residual.argtypes = [P, P, P, P]
         lib.ucns_rk_step.argtypes = [P, P, C.POINTER(C.c_double), P]
+        lib.ucns_rk_steps.argtypes = [P, P, I32, C.POINTER(C.c_double), P]
         lib.ucns_rk_steps_host.argtypes = [P, P, I32, C.POINTER(C.c_double), P]
         lib.ucns_check_state.argtypes = [P, P]
         lib.ucns_diagnostics.argtypes = [P, P, C.POINTER(_Diag), P]
@@ -280,6 +281,14 @@ class Mesh:
             return d.value
         _check(self._lib, self._lib.ucns_rk_step(self._h, ptr, None, _stream_ptr(stream)))
         return None
+
+    def rk_steps(self, U, n_steps: int, stream=None) -> float:
+        """n_steps CFL steps of a device state U (in place) in one call; returns
+        the simulated time.  Synchronises."""
+        t = C.c_double(0.0)
+        _check(self._lib, self._lib.ucns_rk_steps(self._h, _dev_ptr(U, self.n_cells), int(n_steps), C.byref(t),
+                                                  _stream_ptr(stream)))
+        return t.value
 
     def rk_steps_host(self, U_host, n_steps: int, stream=None) -> float:
         """n_steps on a host [5, N] float64 array/tensor (copied in and out)."""

@@ -160,6 +160,22 @@ def test_diagnostics_and_time_step_parity():
     assert abs(dtg - dtc) <= 1e-14 * dtc  # per-cell limits round differently; the min is exact
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multi_step_entry_point_equals_single_steps(prec):
+    """ucns_rk_steps (several steps in one call; the mixed form carries its
+    float pair of the state between them) gives the state and the simulated
+    time of as many ucns_rk_step calls, bit for bit."""
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=9)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=prec))
+    U = np.ascontiguousarray(m.to_internal(I.noisy_state(nodes, cells, 0.1, 0.03, seed=4)))
+    a = torch.from_numpy(U.copy()).cuda()
+    b = torch.from_numpy(U.copy()).cuda()
+    t = sum(m.rk_step(a, return_dt=True) for _ in range(4))
+    tb = m.rk_steps(b, 4)
+    assert torch.equal(a, b)
+    assert tb == t or abs(tb - t) <= 1e-15 * t  # the device adds the same dts in the same order
+
+
 def test_deterministic_and_host_entry_point():
     nodes, cells, box = I.hex_lattice(14, jitter=0.1, seed=9)
     m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1))

@@ -57,7 +57,7 @@ struct RKArgs {
   const double* __restrict__ inv_vol;
   const double* __restrict__ dt;
   int* err;
-  float* hl;  // optional [N][10] float pair of the new state (mixed form)
+  float* hl;  // optional [N][5][2] float pairs (hi, lo) of the new state (mixed form)
   int N, F;
   double gm1;
 };
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
   for (int v = 0; v < 5; v++) a.out[v * N + i] = Un[v];
   if (a.hl) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) split_pair(Un[v], a.hl[i * 10 + v], a.hl[i * 10 + 5 + v]);
+    for (int v = 0; v < 5; v++) split_pair(Un[v], a.hl[i * 10 + 2 * v], a.hl[i * 10 + 2 * v + 1]);
   }
   if (!physical(Un)) atomicOr(a.err, 1);
 }

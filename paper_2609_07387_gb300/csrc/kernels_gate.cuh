@@ -12,7 +12,7 @@ namespace ucns {
 
 struct FeatArgs {
   const double* __restrict__ U;    // [5][N] (FP64 form)
-  const float* __restrict__ Uhl;   // [N][10] float pair of U (mixed form)
+  const float* __restrict__ Uhl;   // [N][5][2] float pairs of U (mixed form)
   const int32_t* __restrict__ sc;  // [18][N] (FP64 form) or pair-blocked (mixed form)
   const void* __restrict__ Pc;     // [9][18][N] double (FP64 form) or pair-blocked float (mixed form)
   const double* __restrict__ mom;    // [6][N] (FP64 form)
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
   if (i >= a.N) return;
   const size_t N = a.N;
   const float* __restrict__ Pc = reinterpret_cast<const float*>(a.Pc);
-  const float2* __restrict__ hl2 = reinterpret_cast<const float2*>(a.Uhl);  // a row is 5 float2
+  const float2* __restrict__ hl2 = reinterpret_cast<const float2*>(a.Uhl);  // a row: (hi, lo) of 5 variables
   const float g = a.gam;
   float hi[5], lo[5];
   {
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
     }
 #pragma unroll
     for (int v = 0; v < 5; v++) {
-      hi[v] = t[v];
-      lo[v] = t[5 + v];
+      hi[v] = t[2 * v];
+      lo[v] = t[2 * v + 1];
     }
   }
   const float r = hi[0] + lo[0], ir = 1.f / r;
@@ -171,11 +171,11 @@ __global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
     }
     float d[5];
 #pragma unroll
-    for (int v = 0; v < 5; v++) d[v] = (t[v] - hi[v]) + (t[5 + v] - lo[v]);
+    for (int v = 0; v < 5; v++) d[v] = (t[2 * v] - hi[v]) + (t[2 * v + 1] - lo[v]);
     F[m] = d[0] * ir;
     if (m < 6) {
-      const float rj = t[0] + t[5], mjx = t[1] + t[6], mjy = t[2] + t[7], mjz = t[3] + t[8];
-      const float pj = (g - 1.f) * ((t[4] + t[9]) - 0.5f * (mjx * mjx + mjy * mjy + mjz * mjz) / rj);
+      const float rj = t[0] + t[1], mjx = t[2] + t[3], mjy = t[4] + t[5], mjz = t[6] + t[7];
+      const float pj = (g - 1.f) * ((t[8] + t[9]) - 0.5f * (mjx * mjx + mjy * mjy + mjz * mjz) / rj);
       F[18 + m] = (pj - p) * ip;
     }
 #pragma unroll

@@ -76,7 +76,7 @@ struct ReconTile {
 };
 
 struct ReconArgsMx {
-  const float* __restrict__ Uhl;  // [N][10]: hi = fl(U) of the 5 variables, then lo = fl(U - hi)
+  const float* __restrict__ Uhl;  // [N][5][2]: (hi, lo) = (fl(U), fl(U - hi)) of each variable
   const int32_t* __restrict__ sc;  // pair-blocked, rows m (MC)
   const float* __restrict__ Pc;    // pair-blocked, rows k MC + m (K MC)
   const int32_t* __restrict__ sd;  // pair-blocked, rows s Md + r (nd Md)
@@ -111,10 +111,9 @@ struct FaceArgsMx {
 // same-sign values within a factor 2 (Sterbenz), so the difference carries no
 // cancellation error beyond the final FP32 rounding, as an FP64 subtraction would
 __device__ __forceinline__ float pair_diff(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
-  // 32-bit row offset (N < 2^31 / 10, checked on the host): one wide multiply-add
-  // forms the address, the lo part is at a constant 20-byte offset from it
-  const float* r = hl + v + j * 10;
-  return (r[0] - hi_i) + (r[5] - lo_i);
+  // one 8-byte load of (hi, lo); 32-bit row offset (N < 2^31 / 10, checked on the host)
+  const float2 p = *reinterpret_cast<const float2*>(hl + j * 10 + 2 * v);
+  return (p.x - hi_i) + (p.y - lo_i);
 }
 
 // CWENOZ combination of the central coefficients ao (K = 9, xi units) with the
@@ -221,7 +220,8 @@ __device__ __forceinline__ void gated_cwenoz(const ReconArgsMx& a, const float (
   const int vv = act ? lv : 0, ss = act ? lsn : 0;
   for (int sl = t >> 5; sl < nf; sl += blockDim.x >> 5) {
     const int cc = s_cell[sl], ii = i0 + cc;
-    const float hi_i = hl[(size_t)ii * 10 + vv], lo_i = hl[(size_t)ii * 10 + 5 + vv];
+    const float2 pi = *reinterpret_cast<const float2*>(hl + (size_t)ii * 10 + 2 * vv);
+    const float hi_i = pi.x, lo_i = pi.y;
     const int2* js = reinterpret_cast<const int2*>(a.sda + (size_t)ii * T::SD + ss * MD);
     const float2* ps = reinterpret_cast<const float2*>(a.Pda + (size_t)ii * T::RD + ss * 3 * MD);
     int jj[MD];
@@ -300,7 +300,8 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
   const bool live = c < nc;
   const int i = i0 + (live ? c : 0);
   const float* __restrict__ hl = a.Uhl;
-  const float hi_i = hl[(size_t)i * 10 + v], lo_i = hl[(size_t)i * 10 + 5 + v];
+  const float2 pi = *reinterpret_cast<const float2*>(hl + (size_t)i * 10 + 2 * v);
+  const float hi_i = pi.x, lo_i = pi.y;
   const bool ok = bar_wait(bar, 0);
   if (__syncthreads_or(!ok)) {
     if (t == 0) atomicOr(a.err, 2);
@@ -363,13 +364,13 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
   if (t == 0) bulk_store(a.coef + (size_t)i0 * CS, sOut, (uint32_t)(nc * CS * 4));
 }
 
-// float pair of an FP64 state, cell-contiguous [N][10]: hi = fl(U) for the 5
-// variables, then lo = fl(U - hi); thread = (cell, variable)
+// float pairs of an FP64 state, cell-contiguous [N][5][2]: (hi, lo) =
+// (fl(U), fl(U - hi)) of each variable; thread = (cell, variable)
 __global__ void __launch_bounds__(256) k_split(const double* __restrict__ U, float* __restrict__ hl, int N) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= 5 * N) return;
   const int i = k / 5, v = k - 5 * (k / 5);
-  split_pair(U[(size_t)v * N + i], hl[(size_t)i * 10 + v], hl[(size_t)i * 10 + 5 + v]);
+  split_pair(U[(size_t)v * N + i], hl[(size_t)i * 10 + 2 * v], hl[(size_t)i * 10 + 2 * v + 1]);
 }
 
 // float pairs of a flat array (the C ABI's ucns_float_pair)

@@ -57,7 +57,7 @@ struct DeviceMesh {
   // scratch owned by the handle
   double* coef = nullptr;     // [NC][N][5] reconstructed monomial coefficients
   float* coeff = nullptr;     // FP32 coefficients (mixed)
-  float* Uhl = nullptr;       // [2][5][N] float pair of the state being reconstructed (mixed)
+  float* Uhl = nullptr;       // [N][5][2] float pairs (hi, lo) of the state being reconstructed (mixed)
   double* G = nullptr;        // [5][F] face flux integrals (mixed form: [5][F] floats in the first half)
   double* Ustage = nullptr;   // [5][N] Runge-Kutta stage state
   double* Uhost = nullptr;    // [5][N] device copy for the host-buffer entry point

@@ -1,7 +1,7 @@
 """What the learned indicator gains: Mach 1.25 Taylor-Green with a 5 %
 random-phase perturbation on 48^3 jittered hexahedra (the 128^3
 configuration scaled down).  Labels come from 30 plain FP64 CWENOZ steps;
-the network is trained on the GPU; then 60 steps of plain FP64, mixed,
+the network is trained on the GPU (60 epochs); then 60 steps of plain FP64, mixed,
 learned + mixed, all-linear + mixed and a hand-set jump rule + mixed run from
 the same state with the same dt sequence.  The learned form must stay within
 1e-4 of the plain FP64 kinetic-energy and dissipation history and beat plain
@@ -30,7 +30,7 @@ def setup():
     S = gate.collect(m64, U, COLLECT, every=5)
     N = m64.n_cells
     y = (S.dev > gate.LABEL_THRESHOLD).float()
-    net = gate.train(S.X[: 5 * N].contiguous(), y[: 5 * N].contiguous(), epochs=6, seed=0)
+    net = gate.train(S.X[: 5 * N].contiguous(), y[: 5 * N].contiguous(), epochs=60, lr=1e-3, batch=4096, seed=0)
     thr = gate.threshold_for_recall(net, S.X[5 * N: 6 * N].contiguous(), y[5 * N: 6 * N].contiguous(), 0.999)
     held = gate.confusion(net, S.X[6 * N:].contiguous(), y[6 * N:].contiguous(), thr)
     return dict(nodes=nodes, cells=cells, box=box, base=base, m64=m64, U0=U0, net=net, thr=thr, held=held, y=y)

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128) k_features(FeatArgs a) {
 // mixed form: stencil differences from the float pair of the state (exact
 // leading-part subtraction, as in the reconstruction), FP32 arithmetic,
 // blocked FP32 pseudo-inverse rows
-__global__ void __launch_bounds__(128) k_features_mx(FeatArgs a) {
+__global__ void __launch_bounds__(128, 4) k_features_mx(FeatArgs a) {
   constexpr int K = 9, MC = 18;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;

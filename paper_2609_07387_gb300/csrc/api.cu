@@ -483,15 +483,18 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
   int rc;
   double* W = m->d.Ustage;
   const int64_t step = m->gate_steps;
+  bool split_done = pair_fresh, checked = false;
   if (m->gate_on && m->mlp && m->gate_check_every > 0 && step % m->gate_check_every == 0) {
     double rel = 0.0;
     if ((rc = gate_check(m, U, &rel, s))) return rc;
-    m->gate_flags_valid = false;  // the check re-evaluated the flags on this state
+    // the check evaluated the flags on this very state (and left its float pair in place)
+    checked = m->gate_on;
+    m->gate_flags_valid = checked;
+    split_done = split_done || mixed(m);
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  bool split_done = pair_fresh;
-  if (m->gate_on && m->mlp && m->gate_flags_valid && step % m->gate_eval_every != 0) {
-    m->gate_eval_active = true;  // reuse the flags of the last evaluation
+  if (m->gate_on && m->mlp && m->gate_flags_valid && (checked || step % m->gate_eval_every != 0)) {
+    m->gate_eval_active = true;  // the flags of the check, or of the last evaluation
   } else {
     if ((rc = gate_eval(m, U, s, &split_done))) return rc;  // flags of U^n serve all three stages
     m->gate_flags_valid = m->gate_eval_active;

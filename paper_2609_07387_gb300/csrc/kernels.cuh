@@ -418,34 +418,54 @@ __device__ __forceinline__ double f2d(float x) {
                                           ((unsigned long long)(b & 0x7fffffu) << 29)));
 }
 
-// Float pair of an FP64 value: hi = fl32(u), lo = fl32(u - hi), with one FP64
-// instruction (the rounding to FP32).  u - hi is exact in FP64 and, for
-// same-sign finite doubles, equals the integer difference of their bit
-// patterns (magnitude order) times 2^(e_u - 52), e_u the unbiased exponent of
-// u (the doubles between u and hi all lie in u's binade, or the one below
-// when hi rounded up to a power of two); converting that integer to FP32
-// rounds to nearest exactly as fl32(u - hi) does, and the power-of-two scale
-// is exact for |u| >= 2^-74.  Below that, and for non-finite hi, lo = 0.
+// Float pair of an FP64 value: hi = fl32(u), lo = fl32(u - hi), from integer
+// operations on the bit pattern, no FP64 instruction, for 2^-74 <= |u| < 2^128.
+// The pattern without its sign, rebiased by (1023 - 127) << 52, holds the FP32
+// exponent and mantissa of |u| in its bits 29 and up; rounding the 29 bits
+// below to nearest even gives fl32(|u|) (a carry into the exponent is the
+// round-up across the binade, up to infinity).  u - hi is then the signed
+// remainder r (the dropped bits, less 2^29 when hi rounded up) times 2^(e-1075),
+// e the biased exponent of u, |r| <= 2^28; converting r to FP32 rounds to
+// nearest as fl32(u - hi) does, and the power-of-two scale is exact for
+// e >= 949 (|u| >= 2^-74).  Outside that range (zeros, tiny values, non-finite
+// u) hi is the hardware rounding; there, and where hi overflows, lo = 0.
 __device__ __forceinline__ void split_pair(double u, float& hi, float& lo) {
-  hi = __double2float_rn(u);
-  const unsigned fb = __float_as_uint(hi);
-  const unsigned ef = (fb >> 23) & 0xffu;
-  const long long ub = __double_as_longlong(u);
-  const int eu = (int)((ub >> 52) & 0x7ff);
-  if (ef == 0u || ef == 255u || eu < 949) {
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(u);
+  const unsigned sgn = (unsigned)(ub >> 32) & 0x80000000u;
+  const unsigned eu = (unsigned)(ub >> 52) & 0x7ffu;
+  if (eu - 949u > 1150u - 949u) {
+    hi = __double2float_rn(u);
     lo = 0.f;
     return;
   }
-  const long long hb = __double_as_longlong(f2d(hi));
-  long long n = ub - hb;  // |n| < 2^30
-  if (ub < 0) n = -n;     // negative values: the patterns order by magnitude
-  lo = (float)(int)n * __uint_as_float((unsigned)(eu - 948) << 23);
+  const unsigned long long x = (ub & 0x7fffffffffffffffull) - (896ull << 52);
+  const unsigned rem = (unsigned)x & 0x1fffffffu;
+  unsigned t = (unsigned)(x >> 29);
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (t & 1u));
+  t += up ? 1u : 0u;
+  hi = __uint_as_float(t | sgn);
+  const int r = (int)rem - (up ? 0x20000000 : 0);
+  lo = t >= 0x7f800000u ? 0.f : (float)r * __uint_as_float(((eu - 948u) << 23) | sgn);
 }
 
 // rho > 0 and p > 0 (p > 0  <=>  2 rho E - |m|^2 > 0 for rho > 0), all finite
 __device__ __forceinline__ bool physical(const double U[5]) {
   const double q = 2.0 * U[0] * U[4] - (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
   return U[0] > 0.0 && q > 0.0 && isfinite(U[0]) && isfinite(U[4]) && isfinite(q);
+}
+
+// physical(U) decided in FP32 from h = fl32(U) where that is safe: with
+// e2 = 2 h_rho h_E in [2^-100, inf) and h_rho >= 2^-60, the FP32 value of
+// q = e2 - |h_m|^2 is within about 9 u e2 of the exact q (u = 2^-24: the
+// rounding of h and of the five products and sums), so q > 2^-20 e2 = 16 u e2
+// implies the exact q, and FP64's, are positive (and every U finite); any
+// other case, non-finite ones included, takes the FP64 test.  Same answer as
+// physical(U).
+__device__ __forceinline__ bool physical_fast(const double U[5], const float (&h)[5]) {
+  const float e2 = 2.f * h[0] * h[4];
+  const float q = e2 - (h[1] * h[1] + h[2] * h[2] + h[3] * h[3]);
+  if (h[0] >= 0x1p-60f && e2 >= 0x1p-100f && q > 0x1p-20f * e2) return true;
+  return physical(U);
 }
 
 // STAGE 0: plain residual R = -(1/V) sum sigma G -> out
@@ -471,31 +491,50 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
     }
     return;
   }
-  // dt R = w s with w = -dt/|V_i| and s the signed face sum
-  const double w = -(*a.dt) * ivol;
-  const double cw = STAGE == 1 ? w : (STAGE == 2 ? 0.25 * w : (2.0 / 3.0) * w);
+  // dt R = w s with w = -dt/|V_i| and s the signed face sum; cw = w times the
+  // stage's weight of dt R
+  const double cdt = STAGE == 1 ? *a.dt : (STAGE == 2 ? 0.25 * *a.dt : (2.0 / 3.0) * *a.dt);
+  const double cw = -cdt * ivol;
   double Un[5];
+  if constexpr (sizeof(GT) == 4) {
+    // FP64 instructions are few on this chip: the small part cw s.y of the
+    // pair's product is formed in FP32 (its relative error ~2^-23 is 2^-47 of
+    // the face fluxes' magnitude, far below their own FP32 rounding) and enters
+    // the FP64 combination of the earlier states as an addend
+    const float cwf = __double2float_rn(cw);
 #pragma unroll
-  for (int v = 0; v < 5; v++) {
-    const double u0 = a.U0[v * N + i];
-    double base;  // the stage's combination of the earlier states
-    if (STAGE == 1) base = u0;                                              // U1 = U0 + dt R
-    else if (STAGE == 2) base = fma(0.75, u0, 0.25 * a.Us[v * N + i]);     // 3/4 U0 + 1/4 (U1 + dt R)
-    else base = fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]);         // 1/3 U0 + 2/3 (U2 + dt R)
-    if constexpr (sizeof(GT) == 4) {
+    for (int v = 0; v < 5; v++) {
       const float2 sp = face_sum_pair<NFC>(a, G, fe, v);  // s = s.x + s.y
-      Un[v] = fma(cw, f2d(sp.x), fma(cw, f2d(sp.y), base));
-    } else {
+      const double u0 = a.U0[v * N + i], p = f2d(cwf * sp.y);
+      double base;  // the stage's combination of the earlier states, plus cw s.y
+      if (STAGE == 1) base = u0 + p;                                               // U1 = U0 + dt R
+      else if (STAGE == 2) base = fma(0.75, u0, fma(0.25, a.Us[v * N + i], p));    // 3/4 U0 + 1/4 (U1 + dt R)
+      else base = fma(1.0 / 3.0, u0, fma(2.0 / 3.0, a.Us[v * N + i], p));          // 1/3 U0 + 2/3 (U2 + dt R)
+      Un[v] = fma(cw, f2d(sp.x), base);
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const double u0 = a.U0[v * N + i];
+      double base;
+      if (STAGE == 1) base = u0;
+      else if (STAGE == 2) base = fma(0.75, u0, 0.25 * a.Us[v * N + i]);
+      else base = fma(1.0 / 3.0, u0, (2.0 / 3.0) * a.Us[v * N + i]);
       Un[v] = fma(cw, face_sum<NFC>(a, G, fe, v), base);
     }
   }
+  float h[5], l[5];
 #pragma unroll
-  for (int v = 0; v < 5; v++) a.out[v * N + i] = Un[v];
-  if (a.hl) {
-#pragma unroll
-    for (int v = 0; v < 5; v++) split_pair(Un[v], a.hl[i * 10 + 2 * v], a.hl[i * 10 + 2 * v + 1]);
+  for (int v = 0; v < 5; v++) {
+    a.out[v * N + i] = Un[v];
+    split_pair(Un[v], h[v], l[v]);
   }
-  if (!physical(Un)) atomicOr(a.err, 1);
+  if (a.hl) {
+    float2* hl2 = reinterpret_cast<float2*>(a.hl) + (size_t)i * 5;
+#pragma unroll
+    for (int v = 0; v < 5; v++) hl2[v] = make_float2(h[v], l[v]);
+  }
+  if (!physical_fast(Un, h)) atomicOr(a.err, 1);
 }
 
 // ------------------------------------------------------------ reductions

@@ -87,18 +87,28 @@ def test_float_pair_equals_its_definition():
     hi = fl32(u), lo = fl32(u - hi) (round to nearest even) bit for bit:
     values over 40 decades of both signs, exact zeros, ties to even, values
     just below powers of two (hi rounds up across the binade), the largest
-    finite floats, and the documented lo = 0 below 2^-74."""
+    finite floats and the rounding to infinity, FP32 denormals, random bit
+    patterns over the whole exponent range, and the documented lo = 0 below
+    2^-74 and where hi is infinite."""
     rng = np.random.default_rng(12)
+    bits = rng.integers(0, 2 ** 63, 100000, dtype=np.int64).view(np.float64)
+    bits = bits[~np.isnan(bits)] * rng.choice([-1.0, 1.0], 100000)[: (~np.isnan(bits)).sum()]
     u = np.concatenate([
         rng.normal(size=200000) * 10.0 ** rng.integers(-20, 20, 200000),
         np.array([0.0, -0.0, 1.0, -1.0, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, -(1 + 2.0 ** -24), 2 - 2.0 ** -30,
-                  np.nextafter(4.0, 0.0), 178.57142857142858, 3.0e38, -3.0e38, 2.0 ** -74, 2.0 ** -73, 1e-30]),
+                  np.nextafter(4.0, 0.0), 178.57142857142858, 3.0e38, -3.0e38, 2.0 ** -74, 2.0 ** -73, 1e-30,
+                  2.0 ** 127, np.nextafter(2.0 ** 128, 0.0), -np.nextafter(2.0 ** 128, 0.0), 2.0 ** 128, 1e39,
+                  float(np.finfo(np.float32).max) * (1 + 2.0 ** -25), -float(np.finfo(np.float32).max),
+                  1e-40, -1e-42, 2.0 ** -75, np.inf, -np.inf, 1e300, -1e-300]),
+        bits,  # random bit patterns (NaN left out) across the whole exponent range
     ])
     hi, lo = ucns.float_pair(torch.from_numpy(u).cuda())
     hi, lo = hi.cpu().numpy(), lo.cpu().numpy()
-    hi_ref = u.astype(np.float32)
-    lo_ref = (u - hi_ref.astype(np.float64)).astype(np.float32)
-    lo_ref[np.abs(u) < 2.0 ** -74] = 0.0
+    with np.errstate(over="ignore"):
+        hi_ref = u.astype(np.float32)
+    with np.errstate(invalid="ignore", over="ignore"):
+        lo_ref = (u - hi_ref.astype(np.float64)).astype(np.float32)
+    lo_ref[(np.abs(u) < 2.0 ** -74) | ~np.isfinite(hi_ref)] = 0.0
     assert np.array_equal(hi.view(np.uint32), hi_ref.view(np.uint32))
     assert np.array_equal(lo.view(np.uint32) & 0x7fffffff, lo_ref.view(np.uint32) & 0x7fffffff)  # +-0 alike
     assert np.array_equal(lo, lo_ref)

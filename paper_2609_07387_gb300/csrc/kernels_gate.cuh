@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(128, 4) k_features_mx(FeatArgs a) {
   constexpr int K = 9, MC = 18;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
-  const size_t N = a.N;
   const float* __restrict__ Pc = reinterpret_cast<const float*>(a.Pc);
   const float2* __restrict__ hl2 = reinterpret_cast<const float2*>(a.Uhl);  // a row: (hi, lo) of 5 variables
   const float g = a.gam;

@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="lattice cells per direction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--train-epochs", type=int, default=60,
+                    help="indicator training epochs of the learned form (fewer: faster setup, more flagged cells)")
     ap.add_argument("--forms", default="fp64,mixed,learned",
                     help="comma list of forms to time: fp64, mixed, learned (indicator + mixed)")
     return ap.parse_args()
@@ -373,11 +375,13 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         S = gate.collect(m64, Uc, 50, every=5)
         y = (S.dev > gate.LABEL_THRESHOLD).float()
         # 60 epochs: at full held-out recall the network then flags ~1 % of the cells (3 epochs: ~8 %)
-        net = gate.train(S.X[: 9 * N].contiguous(), y[: 9 * N].contiguous(), epochs=60, lr=1e-3, batch=4096, seed=0)
+        net = gate.train(S.X[: 9 * N].contiguous(), y[: 9 * N].contiguous(), epochs=args.train_epochs, lr=1e-3,
+                         batch=4096, seed=0)
         thr = gate.threshold_for_recall(net, S.X[9 * N:].contiguous(), y[9 * N:].contiguous(), 0.999)
         held = gate.confusion(net, S.X[10 * N:].contiguous(), y[10 * N:].contiguous(), thr)
         gated = gate.GatedRun(meshes["learned"], net, thr, check_every=50, bound=1e-3, eval_every=5)
-        gate_info = {"train_samples": 9 * N, "troubled_fraction": float(y.mean().item()), "threshold": thr,
+        gate_info = {"train_samples": 9 * N, "train_epochs": args.train_epochs,
+                     "troubled_fraction": float(y.mean().item()), "threshold": thr,
                      "held_out_last_snapshot": held, "setup_s": time.perf_counter() - t0,
                      "eval_every": 5, "check_every": 50, "check_bound": 1e-3, "_net": net, "_gated": gated}
     bus = None

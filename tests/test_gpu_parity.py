@@ -207,6 +207,37 @@ def test_nonphysical_state_reported():
     m.check_state()  # the error word was cleared
 
 
+def test_physicality_test_near_zero_pressure():
+    """The RK stage decides rho > 0, p > 0 in FP32 from the float pair where
+    the sign of q = 2 rho E - |m|^2 has a margin of 2^-20 of 2 rho E, and in
+    FP64 otherwise.  Cells at p = +-1e-8 of their kinetic energy (far inside
+    that margin) after a step of dt = 1e-12: the positive ones are physical,
+    a negative one is reported.  (FP64 form: the mixed form shares the test,
+    but its FP32 flux cannot resolve such pressures against p_ref.)"""
+    nodes, cells, box = I.hex_lattice(8)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=1, scheme=0, precision=0))
+    U = np.ascontiguousarray(m.to_internal(I.tgv_state(nodes, cells, 0.1)))
+
+    def set_cell(i, delta):
+        U[1, i], U[2, i], U[3, i] = 3.0 * U[0, i], -2.0 * U[0, i], 1.0 * U[0, i]
+        ke2 = (U[1, i] ** 2 + U[2, i] ** 2 + U[3, i] ** 2) / U[0, i]  # |m|^2 / rho = 2 KE
+        U[4, i] = 0.5 * ke2 * (1.0 + delta)
+
+    for i in (3, 100, 400):
+        set_cell(i, 1e-8)
+    a = torch.from_numpy(U.copy()).cuda()
+    m.rk_step(a, dt=1e-12)
+    m.check_state()  # nothing reported
+    assert torch.isfinite(a).all()
+    set_cell(100, -1e-8)
+    b = torch.from_numpy(U.copy()).cuda()
+    m.rk_step(b, dt=1e-12)
+    with pytest.raises(ucns.UcnsError) as e:
+        m.check_state()
+    assert e.value.code == -5
+    m.check_state()  # the error word was cleared
+
+
 def test_residual_requires_device_tensors():
     nodes, cells, box = I.hex_lattice(6)
     m = ucns.Mesh(nodes, cells, box, ucns.Params(order=1, scheme=0))

@@ -56,6 +56,12 @@ __host__ __device__ __forceinline__ size_t blk2(int row, int rows, int64_t i) {
   return (((size_t)(i / kTC) * (rows / 2) + row / 2) * kTC + (size_t)(i % kTC)) * 2 + (row & 1);
 }
 
+// index of entry k (0: the constant term) of variable v in a mixed-form
+// coefficient row with ncf = K + 1 entries per variable: variables 0-3
+// interleaved per entry (k 4 + v, so one 16-byte load brings entry k of all
+// four, as two packed FP32x2 pairs), variable 4 after them (4 ncf + k)
+__host__ __device__ constexpr int cidx(int v, int k, int ncf) { return v < 4 ? k * 4 + v : 4 * ncf + k; }
+
 // blocked per-cell FP32 rows of the mixed form: the six second moments
 // (1/V) int xi_a xi_b (xx yy zz xy xz yz), then 1/h
 constexpr int kCellRows = 7;
@@ -82,7 +88,7 @@ struct ReconArgsMx {
   const int32_t* __restrict__ sd;  // pair-blocked, rows s Md + r (nd Md)
   const float* __restrict__ Pd;    // pair-blocked, rows (s 3 + k) Md + r (nd 3 Md)
   const float* __restrict__ cell;  // blocked [tiles][kCellRows][kTC]
-  float* __restrict__ coef;        // [N][cs]: variable-major, coefficient k of variable v at v (K+1) + k,
+  float* __restrict__ coef;        // [N][cs]: entry k of variable v at cidx(v, k, K + 1),
                                    // k = 0 the constant term relative to U_ref
   // gated reconstruction (P2 CWENOZ on the flagged cells only)
   const uint8_t* __restrict__ gate;  // [N] flags (nonzero: CWENOZ)
@@ -162,9 +168,9 @@ __device__ __forceinline__ void cwenoz_mx(const float (&ao)[9], const float (&b)
 // the K + 1 row entries of variable v: the constant term relative to the
 // reference state U_ref = (1, 0, 0, 0, E_ref) (the cell mean minus the mean
 // of the non-constant monomials), then the coefficients in physical units
-// (linear / h, quadratic / h^2); out points at the variable's first entry
+// (linear / h, quadratic / h^2); row points at the cell's row
 template <int K>
-__device__ __forceinline__ void write_var(float* out, int v, float hi_i, float lo_i, const float (&cf)[K],
+__device__ __forceinline__ void write_var(float* row, int v, float hi_i, float lo_i, const float (&cf)[K],
                                           const float (&S)[6], float ih, const ReconArgsMx& a) {
   float c0 = v == 0 ? (hi_i - 1.f) + lo_i : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
   if (K == 9) {
@@ -172,9 +178,9 @@ __device__ __forceinline__ void write_var(float* out, int v, float hi_i, float l
     for (int q = 0; q < 6; q++) c0 = fmaf(-cf[3 + q], S[q], c0);
   }
   const float ih2 = ih * ih;
-  out[0] = c0;
+  row[cidx(v, 0, K + 1)] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[k + 1] = cf[k] * (k < 3 ? ih : ih2);
+  for (int k = 0; k < K; k++) row[cidx(v, k + 1, K + 1)] = cf[k] * (k < 3 ? ih : ih2);
 }
 
 // Second phase of a gated P2 CWENOZ tile (after its linear rows are in
@@ -256,7 +262,7 @@ __device__ __forceinline__ void gated_cwenoz(const ReconArgsMx& a, const float (
       const float ih = sC[6 * kTC + cc];
       float cf[9];
       cwenoz_mx<ND>(aoc, b, S, a, cf);
-      write_var<9>(sOut + cc * CS + lv * (K + 1), lv, hi_i, lo_i, cf, S, ih, a);
+      write_var<9>(sOut + cc * CS, lv, hi_i, lo_i, cf, S, ih, a);
     }
   }
 }
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(kTC * 5, WENO ? 2 : 3) k_recon_mx(ReconArgsMx 
 #pragma unroll
     for (int q = 0; q < 6; q++) S[q] = sC[q * kTC + c];
     const float ih = sC[6 * kTC + c];
-    float* out = sOut + c * CS + v * (K + 1);
+    float* out = sOut + c * CS;
     if constexpr (WENO) {
       float b[ND][3];
       const int2* sSd2 = reinterpret_cast<const int2*>(sSd);
@@ -382,51 +388,80 @@ __global__ void __launch_bounds__(256) k_float_pair(const double* __restrict__ u
 
 // value at the physical offset (x, y, z) from the centroid into U; gradient
 // written (ACC = false) or added (ACC = true) into g; the cell's coefficient
-// row is read with 16-byte loads
+// row is read with 16-byte loads.  Variables 0-3 are evaluated in packed
+// FP32x2 pairs (0, 1) and (2, 3), whose lanes round exactly as the scalar
+// operations of variable 4 (the same FMA sequence per variable).
 template <int ORDER, bool ACC>
 __device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int cell, float x, float y, float z,
                                              float U[5], float g[5][3]) {
   constexpr int CS = ORDER == 1 ? 20 : 52;
-  float cf[CS];
+  constexpr int NCF = ORDER == 1 ? 4 : 10;  // entries per variable
+  float4 q[CS / 4];
   const float4* row = reinterpret_cast<const float4*>(coef + (size_t)cell * CS);
 #pragma unroll
-  for (int q = 0; q < CS / 4; q++) {
-    const float4 t = __ldg(row + q);
-    cf[4 * q] = t.x;
-    cf[4 * q + 1] = t.y;
-    cf[4 * q + 2] = t.z;
-    cf[4 * q + 3] = t.w;
-  }
+  for (int i = 0; i < CS / 4; i++) q[i] = __ldg(row + i);
+  const float2 X = make_float2(x, x), Y = make_float2(y, y), Z = make_float2(z, z);
 #pragma unroll
-  for (int v = 0; v < 5; v++) {
-    constexpr int NCF = ORDER == 1 ? 4 : 10;  // entries per variable
-    const float c0 = cf[v * NCF], c1 = cf[v * NCF + 1], c2 = cf[v * NCF + 2], c3 = cf[v * NCF + 3];
-    float gx, gy, gz;
+  for (int p = 0; p < 2; p++) {
+    auto c = [&](int k) { return p == 0 ? make_float2(q[k].x, q[k].y) : make_float2(q[k].z, q[k].w); };
+    float2 u, gx, gy, gz;
     if (ORDER == 1) {
-      U[v] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
-      gx = c1;
-      gy = c2;
-      gz = c3;
+      u = __ffma2_rn(c(1), X, __ffma2_rn(c(2), Y, __ffma2_rn(c(3), Z, c(0))));
+      gx = c(1);
+      gy = c(2);
+      gz = c(3);
     } else {
-      const float c4 = cf[v * NCF + 4], c5 = cf[v * NCF + 5], c6 = cf[v * NCF + 6];
-      const float c7 = cf[v * NCF + 7], c8 = cf[v * NCF + 8], c9 = cf[v * NCF + 9];
-      const float tx = fmaf(c4, x, fmaf(c7, y, fmaf(c8, z, c1)));
-      const float ty = fmaf(c5, y, fmaf(c9, z, c2));
-      const float tz = fmaf(c6, z, c3);
-      U[v] = fmaf(x, tx, fmaf(y, ty, fmaf(z, tz, c0)));
-      gx = fmaf(c4, x, tx);
-      gy = fmaf(c7, x, fmaf(c5, y, ty));
-      gz = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz)));
+      const float2 tx = __ffma2_rn(c(4), X, __ffma2_rn(c(7), Y, __ffma2_rn(c(8), Z, c(1))));
+      const float2 ty = __ffma2_rn(c(5), Y, __ffma2_rn(c(9), Z, c(2)));
+      const float2 tz = __ffma2_rn(c(6), Z, c(3));
+      u = __ffma2_rn(X, tx, __ffma2_rn(Y, ty, __ffma2_rn(Z, tz, c(0))));
+      gx = __ffma2_rn(c(4), X, tx);
+      gy = __ffma2_rn(c(7), X, __ffma2_rn(c(5), Y, ty));
+      gz = __ffma2_rn(c(8), X, __ffma2_rn(c(9), Y, __ffma2_rn(c(6), Z, tz)));
     }
+    const int v = 2 * p;
+    U[v] = u.x;
+    U[v + 1] = u.y;
     if (ACC) {
-      g[v][0] += gx;
-      g[v][1] += gy;
-      g[v][2] += gz;
-    } else {
-      g[v][0] = gx;
-      g[v][1] = gy;
-      g[v][2] = gz;
+      gx = __fadd2_rn(make_float2(g[v][0], g[v + 1][0]), gx);
+      gy = __fadd2_rn(make_float2(g[v][1], g[v + 1][1]), gy);
+      gz = __fadd2_rn(make_float2(g[v][2], g[v + 1][2]), gz);
     }
+    g[v][0] = gx.x;
+    g[v + 1][0] = gx.y;
+    g[v][1] = gy.x;
+    g[v + 1][1] = gy.y;
+    g[v][2] = gz.x;
+    g[v + 1][2] = gz.y;
+  }
+  // variable 4: entries 4 NCF + k
+  const float* f = reinterpret_cast<const float*>(q);
+  const float c0 = f[4 * NCF], c1 = f[4 * NCF + 1], c2 = f[4 * NCF + 2], c3 = f[4 * NCF + 3];
+  float gx, gy, gz;
+  if (ORDER == 1) {
+    U[4] = fmaf(c1, x, fmaf(c2, y, fmaf(c3, z, c0)));
+    gx = c1;
+    gy = c2;
+    gz = c3;
+  } else {
+    const float c4 = f[4 * NCF + 4], c5 = f[4 * NCF + 5], c6 = f[4 * NCF + 6];
+    const float c7 = f[4 * NCF + 7], c8 = f[4 * NCF + 8], c9 = f[4 * NCF + 9];
+    const float tx = fmaf(c4, x, fmaf(c7, y, fmaf(c8, z, c1)));
+    const float ty = fmaf(c5, y, fmaf(c9, z, c2));
+    const float tz = fmaf(c6, z, c3);
+    U[4] = fmaf(x, tx, fmaf(y, ty, fmaf(z, tz, c0)));
+    gx = fmaf(c4, x, tx);
+    gy = fmaf(c7, x, fmaf(c5, y, ty));
+    gz = fmaf(c8, x, fmaf(c9, y, fmaf(c6, z, tz)));
+  }
+  if (ACC) {
+    g[4][0] += gx;
+    g[4][1] += gy;
+    g[4][2] += gz;
+  } else {
+    g[4][0] = gx;
+    g[4][1] = gy;
+    g[4][2] = gz;
   }
 }
 
@@ -593,7 +628,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + v * ncf + j + 1];
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(size_t)i * cs + cidx(v, j + 1, ncf)];
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

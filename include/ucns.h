@@ -7,8 +7,9 @@
  * nonlinear weights over central and directional stencils (Eqs. 5-6),
  * gradients at face Gauss points, HLLC inviscid flux and viscous flux with
  * the interface jump penalty (Eq. 7), periodic boundaries, an owner-side
- * residual sum, and the explicit SSP Runge-Kutta update (Eq. 8; three-stage
- * Shu-Osher form).
+ * residual sum, and the explicit SSP Runge-Kutta update (Eq. 8; the
+ * three-stage third-order Shu-Osher form by default, or the paper's
+ * five-stage fourth-order scheme, ucns_params.integrator).
  *
  * Conventions shared by every call
  *  - Every function returns an int status: UCNS_OK (0) or a negative
@@ -59,12 +60,17 @@ extern "C" {
                               (exact leading-part subtraction); FP64 state, face
                               totals, RK accumulation and reductions */
 
+/* Explicit SSP Runge-Kutta integrator of the semi-discrete system (Eq. 8). */
+#define UCNS_RK_SSP3 0   /* three-stage third-order SSP-RK (Shu-Osher form), the default */
+#define UCNS_RK_SSP54 1  /* five-stage fourth-order SSP-RK of Spiteri and Ruuth, the
+                            paper's integrator (SSP coefficient 1.508) */
+
 /* Scheme parameters (Sec. 2.2). */
 typedef struct ucns_params {
   int32_t order;      /* reconstruction degree r: 1 (P1) or 2 (P2) */
   int32_t scheme;     /* UCNS_SCHEME_*; CWENOZ needs order 2 */
   int32_t precision;  /* UCNS_PREC_* */
-  int32_t reserved;   /* must be 0 */
+  int32_t integrator; /* UCNS_RK_* (0: SSP-RK3) */
   double gamma;       /* ratio of specific heats (1.4) */
   double prandtl;     /* Pr (0.71) */
   double reynolds;    /* Re; <= 0 selects the inviscid (Euler) flux only */
@@ -133,7 +139,8 @@ int ucns_stencil(const ucns_mesh* mesh, int64_t cell, int32_t which, int64_t* me
  * internal order, must not overlap.  Errors: STATE, INVALID_ARG, CUDA. */
 int ucns_residual(ucns_mesh* mesh, const double* U, double* R, void* stream);
 
-/* One SSP-RK3 step (three residual evaluations) of U in place.
+/* One step of the mesh's SSP Runge-Kutta integrator (three residual
+ * evaluations for UCNS_RK_SSP3, five for UCNS_RK_SSP54) of U in place.
  *  dt_inout  NULL: dt = CFL condition evaluated on the device from U, kept on
  *            the device (no host synchronisation);
  *            *dt_inout > 0: use that dt;
@@ -144,7 +151,7 @@ int ucns_residual(ucns_mesh* mesh, const double* U, double* R, void* stream);
  * ucns_check_state().  Errors: STATE, INVALID_ARG, CUDA, NONPHYSICAL. */
 int ucns_rk_step(ucns_mesh* mesh, double* U, double* dt_inout, void* stream);
 
-/* n_steps SSP-RK3 steps of U (device [5][n_cells], internal order, updated in
+/* n_steps SSP-RK steps of U (device [5][n_cells], internal order, updated in
  * place), each with the CFL time step computed on the device, in one call:
  * the same arithmetic as n_steps calls of ucns_rk_step(dt_inout = NULL), bit
  * for bit, with less per-step work around the kernels (the mixed form carries
@@ -155,7 +162,7 @@ int ucns_rk_step(ucns_mesh* mesh, double* U, double* dt_inout, void* stream);
 int ucns_rk_steps(ucns_mesh* mesh, double* U, int32_t n_steps, double* t_inout, void* stream);
 
 /* Host-buffer variant: copies U_host (pinned or pageable [5][n_cells], internal
- * order) to a library-owned device buffer, runs n_steps SSP-RK3 steps with the
+ * order) to a library-owned device buffer, runs n_steps SSP-RK steps with the
  * CFL time step, copies the result back and synchronises.  *t_inout (may be
  * NULL) is advanced by the total simulated time. */
 int ucns_rk_steps_host(ucns_mesh* mesh, double* U_host, int32_t n_steps, double* t_inout,

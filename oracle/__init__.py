@@ -1,4 +1,5 @@
-"""CPU oracle for the explicit finite-volume residual and SSP-RK3 update.
+"""CPU oracle for the explicit finite-volume residual and SSP Runge-Kutta update
+(SSP-RK3 and SSP(5,4)).
 
 TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may use it; the product path never does.
@@ -73,6 +74,13 @@ def _load():
             lib.orc_viscous_flux.argtypes = [P, P, P, D, D, D, D, P]
             lib.orc_ssprk3_linear.restype = D
             lib.orc_ssprk3_linear.argtypes = [D, D, D]
+            lib.orc_ssp54_linear.restype = D
+            lib.orc_ssp54_linear.argtypes = [D, D, D]
+            lib.orc_ssp54_coeffs.argtypes = [P]
+            lib.orc_ssp54_logistic.restype = D
+            lib.orc_ssp54_logistic.argtypes = [D, D, C.c_int]
+            lib.orc_ssprk3_logistic.restype = D
+            lib.orc_ssprk3_logistic.argtypes = [D, D, C.c_int]
             _lib = lib
     return _lib
 
@@ -99,10 +107,11 @@ class Params:
     lam_central: float = 1000.0
     eps: float = 1e-6
     alpha: float = 4.0 / 3.0
+    integrator: int = 0      # 0 SSP-RK3, 1 SSP(5,4)
 
     def array(self) -> np.ndarray:
         return np.array([self.order, self.scheme, self.gamma, self.Pr, self.Re, self.Mach, self.cfl,
-                         self.lam_central, self.eps, self.alpha], dtype=np.float64)
+                         self.lam_central, self.eps, self.alpha, self.integrator], dtype=np.float64)
 
 
 class OracleError(RuntimeError):
@@ -281,3 +290,22 @@ def viscous_flux(Uf, gradU, n, gamma=1.4, Re=1600.0, Pr=0.71, Mach=0.1):
 
 def ssprk3_linear(lam: float, dt: float, u0: float = 1.0) -> float:
     return float(_load().orc_ssprk3_linear(lam, dt, u0))
+
+
+def ssp54_linear(lam: float, dt: float, u0: float = 1.0) -> float:
+    """One SSP(5,4) step of du/dt = lam u from u0."""
+    return float(_load().orc_ssp54_linear(lam, dt, u0))
+
+
+def ssp54_coefficients():
+    """The oracle's SSP(5,4) Shu-Osher coefficients (alpha, beta), each [6][5]:
+    row i gives u_i in terms of u_j, L(u_j), j < i."""
+    out = np.zeros(60)
+    _load().orc_ssp54_coeffs(_p(out))
+    return out[:30].reshape(6, 5), out[30:].reshape(6, 5)
+
+
+def logistic(u0: float, T: float, n: int, integrator: int) -> float:
+    """n steps of u' = u (1 - u) to time T (integrator 0: SSP-RK3, 1: SSP(5,4))."""
+    f = _load().orc_ssp54_logistic if integrator == 1 else _load().orc_ssprk3_logistic
+    return float(f(u0, T, n))

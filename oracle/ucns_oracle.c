@@ -1,6 +1,7 @@
 /*
  * ucns_oracle.c -- plain, slow FP64 CPU oracle of the explicit residual and
- * SSP-RK3 update of the high-order cell-centred finite-volume scheme
+ * SSP Runge-Kutta update (SSP-RK3, SSP(5,4)) of the high-order cell-centred
+ * finite-volume scheme
  * (Sec. 2.2: Eq. 1 conservation law, Eq. 2 semi-discretisation, Eqs. 3-4
  * k-exact least-squares reconstruction, Eqs. 5-6 CWENOZ, Eq. 7 viscous
  * interface gradient, HLLC inviscid flux, Eq. 8 explicit SSP Runge-Kutta).
@@ -44,6 +45,7 @@ typedef struct {
   int64_t *canon;  /* node -> canonical (periodic) node id */
   /* parameters */
   int order, scheme, inviscid;
+  int rk;  /* 0: SSP-RK3, 1: SSP(5,4) */
   double gam, Pr, Re, Mach, cfl, lamc, eps, alpha;
   int K, nq, Mc, nd, Md;
   /* geometry */
@@ -1025,6 +1027,78 @@ double orc_ssprk3_linear(double lambda, double dt, double u0) {
   return u;
 }
 
+/* ------------------------------------------------------------------------ */
+/* SSP(5,4) of Spiteri and Ruuth (the fourth-order SSP scheme of Eq. 8) in   */
+/* Shu-Osher form: u_0 = U^n and, for i = 1..5,                              */
+/*   u_i = sum_{j<i} ( alpha_ij u_j + dt beta_ij L(u_j) ),  U^{n+1} = u_5,    */
+/* with the published 15-digit coefficients (zero entries omitted there).    */
+/* ------------------------------------------------------------------------ */
+static const double SSP54_ALPHA[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
+static const double SSP54_BETA[6][5] = {
+    {0, 0, 0, 0, 0},
+    {0.391752226571890, 0, 0, 0, 0},
+    {0, 0.368410593050371, 0, 0, 0},
+    {0, 0, 0.251891774271694, 0, 0},
+    {0, 0, 0, 0.544974750228521, 0},
+    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
+
+int orc_ssp54_generic(res_fn f, void *ctx, double *U, int64_t n, double dt) {
+  double *u[5], *L[5];
+  int rc = 0;
+  for (int j = 0; j < 5; j++) {
+    u[j] = (double *)malloc(sizeof(double) * n);
+    L[j] = (double *)malloc(sizeof(double) * n);
+  }
+  memcpy(u[0], U, sizeof(double) * n);
+  for (int i = 1; i <= 5 && !rc; i++) {
+    rc = f(ctx, u[i - 1], L[i - 1]);  /* every stage value is needed once its stage exists */
+    double *dst = i < 5 ? u[i] : U;
+    for (int64_t k = 0; k < n && !rc; k++) {
+      double v = 0.0;
+      for (int j = 0; j < i; j++) v += SSP54_ALPHA[i][j] * u[j][k] + dt * SSP54_BETA[i][j] * L[j][k];
+      dst[k] = v;
+    }
+  }
+  for (int j = 0; j < 5; j++) { free(u[j]); free(L[j]); }
+  return rc;
+}
+
+/* the Shu-Osher coefficients as stored, alpha then beta, row-major [6][5] each */
+void orc_ssp54_coeffs(double *out) {
+  memcpy(out, SSP54_ALPHA, sizeof SSP54_ALPHA);
+  memcpy(out + 30, SSP54_BETA, sizeof SSP54_BETA);
+}
+
+double orc_ssp54_linear(double lambda, double dt, double u0) {
+  double u = u0;
+  orc_ssp54_generic(lin_res, &lambda, &u, 1, dt);
+  return u;
+}
+
+/* logistic equation u' = u (1 - u), a nonlinear scalar test problem:
+   n steps of size T/n from u0 with SSP(5,4) */
+static int logistic_res(void *ctx, const double *U, double *R) {
+  (void)ctx;
+  R[0] = U[0] * (1.0 - U[0]);
+  return 0;
+}
+double orc_ssp54_logistic(double u0, double T, int n) {
+  double u = u0;
+  for (int k = 0; k < n; k++) orc_ssp54_generic(logistic_res, NULL, &u, 1, T / n);
+  return u;
+}
+double orc_ssprk3_logistic(double u0, double T, int n) {
+  double u = u0;
+  for (int k = 0; k < n; k++) orc_ssprk3_generic(logistic_res, NULL, &u, 1, T / n);
+  return u;
+}
+
 static int case_res(void *ctx, const double *U, double *R) { return residual((orc_case *)ctx, U, R); }
 
 /* ------------------------------------------------------------------------ */
@@ -1050,7 +1124,9 @@ orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int6
   c->inviscid = !(params[4] > 0);
   c->Mach = params[5]; c->cfl = params[6]; c->lamc = params[7]; c->eps = params[8];
   c->alpha = params[9];
+  c->rk = (int)params[10];
   if (c->order < 1 || c->order > 2) { set_err("order must be 1 or 2"); free(c); return NULL; }
+  if (c->rk != 0 && c->rk != 1) { set_err("integrator must be 0 (SSP-RK3) or 1 (SSP(5,4))"); free(c); return NULL; }
   c->K = c->order == 1 ? 3 : 9;
   c->Mc = 2 * c->K;
   c->nd = (c->order == 2 && c->scheme == 1) ? c->nfc : 0;
@@ -1148,11 +1224,14 @@ int orc_residual_terms(orc_case *c, const double *U, double *R, double *S) {
   return residual_terms(c, U, R, S);
 }
 
-/* one SSP-RK3 step; dt <= 0 computes it from the CFL condition; returns dt */
+/* one step of the case's integrator (SSP-RK3 or SSP(5,4)); dt <= 0 computes
+   it from the CFL condition; returns dt */
 double orc_rk_step(orc_case *c, double *U, double dt) {
   if (ensure_all(c)) return -1.0;
   if (!(dt > 0)) dt = time_step(c, U);
-  if (orc_ssprk3_generic(case_res, c, U, 5 * c->N, dt)) return -1.0;
+  int rc = c->rk == 1 ? orc_ssp54_generic(case_res, c, U, 5 * c->N, dt)
+                      : orc_ssprk3_generic(case_res, c, U, 5 * c->N, dt);
+  if (rc) return -1.0;
   return dt;
 }
 

@@ -290,6 +290,7 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
   a.err = m->d.err;
   // the next stage (or, keep_pair, the next step) reconstructs out from its float pair
   a.hl = (mixed(m) && (stage == 1 || stage == 2 || (stage == 3 && keep_pair))) ? m->d.Uhl : nullptr;
+  a.acc = nullptr;
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.gm1 = m->P.gamma - 1.0;
@@ -311,6 +312,46 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
     default: UCNS_RK(3); break;
   }
 #undef UCNS_RK
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+// stage 1..5 of SSP(5,4) (k_rk54): U0 = U^n, Us = the stage's input, out = its result
+int launch_rk54_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out, cudaStream_t s,
+                    bool keep_pair = false) {
+  RKArgs a;
+  a.U0 = U0;
+  a.Us = Us;
+  a.out = out;
+  a.G = m->d.G;
+  a.cf = m->d.cf;
+  a.inv_vol = m->d.inv_vol;
+  a.dt = m->d.dt;
+  a.err = m->d.err;
+  a.hl = (mixed(m) && (stage < 5 || keep_pair)) ? m->d.Uhl : nullptr;
+  a.acc = m->d.Uacc;
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.gm1 = m->P.gamma - 1.0;
+  const unsigned g = nblocks((size_t)m->N);
+#define UCNS_RK54(ST)                                                         \
+  do {                                                                        \
+    if (mixed(m)) {                                                           \
+      if (m->nfc == 6) k_rk54<ST, 6, float><<<g, 256, 0, s>>>(a);             \
+      else k_rk54<ST, 4, float><<<g, 256, 0, s>>>(a);                         \
+    } else {                                                                  \
+      if (m->nfc == 6) k_rk54<ST, 6, double><<<g, 256, 0, s>>>(a);            \
+      else k_rk54<ST, 4, double><<<g, 256, 0, s>>>(a);                        \
+    }                                                                         \
+  } while (0)
+  switch (stage) {
+    case 1: UCNS_RK54(1); break;
+    case 2: UCNS_RK54(2); break;
+    case 3: UCNS_RK54(3); break;
+    case 4: UCNS_RK54(4); break;
+    default: UCNS_RK54(5); break;
+  }
+#undef UCNS_RK54
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -391,6 +432,10 @@ int launch_rk(ucns_mesh* m, int stage, const double* U0, const double* Us, doubl
 }
 int launch_dt(ucns_mesh* m, const double* U, cudaStream_t s) {
   return timed(m, kKindDt, s, [&] { return launch_dt_raw(m, U, s); });
+}
+int launch_rk54(ucns_mesh* m, int stage, const double* U0, const double* Us, double* out, cudaStream_t s,
+                bool keep_pair = false) {
+  return timed(m, kKindRK, s, [&] { return launch_rk54_raw(m, stage, U0, Us, out, s, keep_pair); });
 }
 
 // the indicator features of U into X (BF16) and Xf (FP32, or null); the
@@ -500,8 +545,18 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
     m->gate_flags_valid = m->gate_eval_active;
   }
   if ((!split_done && (rc = launch_split(m, U, s))) || (rc = launch_recon(m, U, s)) || (rc = launch_face(m, s)) ||
-      (dt_pending && (rc = join_dt(m, s))) || (rc = launch_rk(m, 1, U, U, W, s)))
+      (dt_pending && (rc = join_dt(m, s))))
     return rc;
+  if (m->P.integrator == UCNS_RK_SSP54) {
+    // u_1..u_4 in W (in place), the last stage into U
+    if ((rc = launch_rk54(m, 1, U, U, W, s))) return rc;
+    for (int st = 2; st <= 5; st++)
+      if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) ||
+          (rc = launch_rk54(m, st, U, W, st == 5 ? U : W, s, keep_pair)))
+        return rc;
+    return UCNS_OK;
+  }
+  if ((rc = launch_rk(m, 1, U, U, W, s))) return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 2, U, W, W, s)))
     return rc;
   if ((rc = launch_recon(m, W, s)) || (rc = launch_face(m, s)) || (rc = launch_rk(m, 3, U, W, U, s, keep_pair)))
@@ -557,7 +612,7 @@ void device_free(ucns_mesh* m) {
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
-                  d.Ustage, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
+                  d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   d = DeviceMesh{};
@@ -622,7 +677,8 @@ static int check_params(const ucns_mesh* m, const ucns_params* p) {
     return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2");
   if (p->precision != UCNS_PREC_FP64 && p->precision != UCNS_PREC_MIXED)
     return fail(UCNS_ERR_INVALID_ARG, "unknown precision mode");
-  if (p->reserved != 0) return fail(UCNS_ERR_INVALID_ARG, "reserved must be 0");
+  if (p->integrator != UCNS_RK_SSP3 && p->integrator != UCNS_RK_SSP54)
+    return fail(UCNS_ERR_INVALID_ARG, "unknown integrator");
   if (!(p->gamma > 1.0) || !(p->mach > 0.0) || !(p->cfl > 0.0) || !(p->lambda_central > 0.0) ||
       !(p->epsilon > 0.0) || (p->reynolds > 0.0 && !(p->prandtl > 0.0)))
     return fail(UCNS_ERR_INVALID_ARG, "invalid physical parameter");
@@ -717,6 +773,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   d.red_blocks = 4 * 152;
   if ((rc = alloc(&d.G, (size_t)5 * m->F)) ||
       (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)4 * d.red_blocks)) ||
+      (p->integrator == UCNS_RK_SSP54 && (rc = alloc(&d.Uacc, (size_t)5 * m->N))) ||
       (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1)) || (rc = alloc(&d.dt_part, (size_t)nblocks(m->N))) ||
       (rc = alloc(&d.dt_count, 1))) {
     device_free(m);

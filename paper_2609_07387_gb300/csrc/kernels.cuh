@@ -58,6 +58,7 @@ struct RKArgs {
   const double* __restrict__ dt;
   int* err;
   float* hl;  // optional [N][5][2] float pairs (hi, lo) of the new state (mixed form)
+  double* acc;  // [5][N] SSP(5,4) accumulator of the last stage's combination (k_rk54)
   int N, F;
   double gm1;
 };
@@ -468,6 +469,24 @@ __device__ __forceinline__ bool physical_fast(const double U[5], const float (&h
   return physical(U);
 }
 
+// a stage's new state: stored, split into its float pair (written when the
+// next reconstruction reads it), and checked for physicality
+__device__ __forceinline__ void store_stage(const RKArgs& a, int i, const double (&Un)[5]) {
+  const size_t N = a.N;
+  float h[5], l[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    a.out[v * N + i] = Un[v];
+    split_pair(Un[v], h[v], l[v]);
+  }
+  if (a.hl) {
+    float2* hl2 = reinterpret_cast<float2*>(a.hl) + (size_t)i * 5;
+#pragma unroll
+    for (int v = 0; v < 5; v++) hl2[v] = make_float2(h[v], l[v]);
+  }
+  if (!physical_fast(Un, h)) atomicOr(a.err, 1);
+}
+
 // STAGE 0: plain residual R = -(1/V) sum sigma G -> out
 // STAGE 1: U1 = U0 + dt R;  2: U2 = 3/4 U0 + 1/4 (U1 + dt R);  3: U = 1/3 U0 + 2/3 (U2 + dt R)
 template <int STAGE, int NFC, typename GT>
@@ -523,18 +542,72 @@ __global__ void __launch_bounds__(256) k_rk(RKArgs a) {
       Un[v] = fma(cw, face_sum<NFC>(a, G, fe, v), base);
     }
   }
-  float h[5], l[5];
+  store_stage(a, i, Un);
+}
+
+// SSP(5,4) of Spiteri and Ruuth, the fourth-order SSP scheme of Eq. 8, in
+// Shu-Osher form (u_0 = U^n, L = R):
+//   u_1 = u_0 + b10 dt L(u_0)
+//   u_2 = a20 u_0 + a21 u_1 + b21 dt L(u_1)
+//   u_3 = a30 u_0 + a32 u_2 + b32 dt L(u_2)
+//   u_4 = a40 u_0 + a43 u_3 + b43 dt L(u_3)
+//   U^{n+1} = a52 u_2 + a53 u_3 + b53 dt L(u_3) + a54 u_4 + b54 dt L(u_4).
+// The last line is accumulated in acc as its terms become available: acc =
+// a52 u_2 (stage 2), acc += a53 u_3 + b53 dt L(u_3) (stage 4), U^{n+1} = acc +
+// a54 u_4 + b54 dt L(u_4) (stage 5); so the stages need U^n, the stage state
+// and acc.  Coefficients as published (15 digits).
+struct SSP54 {
+  static constexpr double b10 = 0.391752226571890;
+  static constexpr double a20 = 0.444370493651235, a21 = 0.555629506348765, b21 = 0.368410593050371;
+  static constexpr double a30 = 0.620101851488403, a32 = 0.379898148511597, b32 = 0.251891774271694;
+  static constexpr double a40 = 0.178079954393132, a43 = 0.821920045606868, b43 = 0.544974750228521;
+  static constexpr double a52 = 0.517231671970585, a53 = 0.096059710526147, b53 = 0.063692468666290;
+  static constexpr double a54 = 0.386708617503269, b54 = 0.226007483236906;
+};
+
+// stage STAGE (1..5) of SSP(5,4): U0 = U^n, Us = the stage's input state
+// (u_0 at stage 1), out = the next stage state (U^{n+1} at stage 5); out may
+// alias Us (each thread reads and writes its own cell)
+template <int STAGE, int NFC, typename GT>
+__global__ void __launch_bounds__(256) k_rk54(RKArgs a) {
+  using C = SSP54;
+  const GT* __restrict__ G = reinterpret_cast<const GT*>(a.G);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  int fe[NFC];
+  cell_faces<NFC>(a, i, fe);
+  const size_t N = a.N;
+  // dt L = w s with w = -dt/|V_i| and s the signed face sum
+  const double w = -(*a.dt) * a.inv_vol[i];
+  constexpr double B = STAGE == 1 ? C::b10 : STAGE == 2 ? C::b21 : STAGE == 3 ? C::b32 : STAGE == 4 ? C::b43 : C::b54;
+  const double cw = B * w, cw53 = C::b53 * w;
+  double Un[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
-    a.out[v * N + i] = Un[v];
-    split_pair(Un[v], h[v], l[v]);
+    const double us = STAGE == 1 ? a.U0[v * N + i] : a.Us[v * N + i];
+    const double u0 = (STAGE >= 2 && STAGE <= 4) ? a.U0[v * N + i] : 0.0;
+    const double ac = STAGE >= 4 ? a.acc[v * N + i] : 0.0;
+    double s, p = 0.0, p53 = 0.0;  // s: the face sum (mixed: its leading part; the small part enters as p)
+    if constexpr (sizeof(GT) == 4) {
+      // as in k_rk: the small part of the FP32 pair's product in FP32
+      const float2 sp = face_sum_pair<NFC>(a, G, fe, v);
+      s = f2d(sp.x);
+      p = f2d(__double2float_rn(cw) * sp.y);
+      if (STAGE == 4) p53 = f2d(__double2float_rn(cw53) * sp.y);
+    } else {
+      s = face_sum<NFC>(a, G, fe, v);
+    }
+    double base;
+    if (STAGE == 1) base = us + p;
+    else if (STAGE == 2) base = fma(C::a20, u0, fma(C::a21, us, p));
+    else if (STAGE == 3) base = fma(C::a30, u0, fma(C::a32, us, p));
+    else if (STAGE == 4) base = fma(C::a40, u0, fma(C::a43, us, p));
+    else base = fma(C::a54, us, ac + p);
+    Un[v] = fma(cw, s, base);
+    if (STAGE == 2) a.acc[v * N + i] = C::a52 * Un[v];
+    if (STAGE == 4) a.acc[v * N + i] = fma(cw53, s, fma(C::a53, us, ac + p53));
   }
-  if (a.hl) {
-    float2* hl2 = reinterpret_cast<float2*>(a.hl) + (size_t)i * 5;
-#pragma unroll
-    for (int v = 0; v < 5; v++) hl2[v] = make_float2(h[v], l[v]);
-  }
-  if (!physical_fast(Un, h)) atomicOr(a.err, 1);
+  store_stage(a, i, Un);
 }
 
 // ------------------------------------------------------------ reductions

@@ -60,6 +60,7 @@ struct DeviceMesh {
   float* Uhl = nullptr;       // [N][5][2] float pairs (hi, lo) of the state being reconstructed (mixed)
   double* G = nullptr;        // [5][F] face flux integrals (mixed form: [5][F] floats in the first half)
   double* Ustage = nullptr;   // [5][N] Runge-Kutta stage state
+  double* Uacc = nullptr;     // [5][N] SSP(5,4) accumulator of the last stage's combination
   double* Uhost = nullptr;    // [5][N] device copy for the host-buffer entry point
   double* red = nullptr;      // reduction partials
   double* dt = nullptr;       // [1] device time step

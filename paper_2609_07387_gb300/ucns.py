@@ -56,7 +56,7 @@ class UcnsError(RuntimeError):
 
 class _Params(C.Structure):
     _fields_ = [
-        ("order", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("order", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("integrator", C.c_int32),
         ("gamma", C.c_double), ("prandtl", C.c_double), ("reynolds", C.c_double), ("mach", C.c_double),
         ("cfl", C.c_double), ("lambda_central", C.c_double), ("epsilon", C.c_double), ("alpha", C.c_double),
     ]
@@ -182,10 +182,11 @@ class Params:
     lam_central: float = 1000.0
     eps: float = 1e-6
     alpha: float = 4.0 / 3.0
+    integrator: int = 0       # 0 SSP-RK3, 1 SSP(5,4)
 
     def c_struct(self) -> _Params:
-        return _Params(self.order, self.scheme, self.precision, 0, self.gamma, self.Pr, self.Re, self.Mach,
-                       self.cfl, self.lam_central, self.eps, self.alpha)
+        return _Params(self.order, self.scheme, self.precision, self.integrator, self.gamma, self.Pr, self.Re,
+                       self.Mach, self.cfl, self.lam_central, self.eps, self.alpha)
 
 
 class Mesh:

@@ -44,7 +44,7 @@ def _term_err(a, b, S):
 def _pair(nodes, cells, box, **kw):
     p = ucns.Params(**kw)
     op = O.Params(order=p.order, scheme=p.scheme, gamma=p.gamma, Pr=p.Pr, Re=p.Re, Mach=p.Mach, cfl=p.cfl,
-                  lam_central=p.lam_central, eps=p.eps, alpha=p.alpha)
+                  lam_central=p.lam_central, eps=p.eps, alpha=p.alpha, integrator=p.integrator)
     return ucns.Mesh(nodes, cells, box, p), O.Case(nodes, cells, box, op)
 
 
@@ -122,6 +122,49 @@ def test_rk_steps_and_time_step_parity():
     assert np.all(err <= 1e-12), err
 
 
+@pytest.mark.parametrize("order,scheme,n,tets", [(1, 0, 12, False), (2, 1, 10, False), (2, 1, 6, True)])
+def test_ssp54_steps_parity(order, scheme, n, tets):
+    """The paper's fourth-order SSP scheme (integrator 1: SSP(5,4), five
+    residual evaluations per step): 5 steps with the CFL time step on both
+    sides from a noisy state; dt equal, the state within 1e-12 of the oracle's
+    (norm-wise per component)."""
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=2)
+    if tets:
+        cells = I.split_tets(cells)
+    m, oc = _pair(nodes, cells, box, order=order, scheme=scheme, Re=1600.0, Mach=0.1, cfl=0.5, integrator=1)
+    U0 = I.noisy_state(nodes, cells, 0.1, 0.03, seed=5)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U0))).cuda()
+    Uc = U0.copy()
+    for _ in range(5):
+        dtg = m.rk_step(Ug, return_dt=True)
+        Uc, dtc = oc.rk_step(Uc, 0.0)
+        assert dtg == dtc or abs(dtg - dtc) <= 1e-14 * dtc
+    err = _norm_err(m.to_user(Ug.cpu().numpy()), Uc)
+    assert np.all(err <= 1e-12), err
+
+
+def test_ssp54_mixed_history_vs_fp64():
+    """SSP(5,4) in the mixed form against the FP64 form, 40 steps from the
+    Taylor-Green state with the same dt sequence: kinetic energy and
+    solenoidal dissipation within 1e-6 relative."""
+    nodes, cells, box = I.hex_lattice(12, jitter=0.1, seed=1)
+    m64 = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=0, integrator=1))
+    m32 = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=1, integrator=1))
+    U0 = np.ascontiguousarray(m64.to_internal(I.tgv_state(nodes, cells, 0.1)))
+    a = torch.from_numpy(U0.copy()).cuda()
+    b = torch.from_numpy(U0.copy()).cuda()
+    worst = 0.0
+    for step in range(40):
+        dt = m64.time_step(a)
+        m64.rk_step(a, dt=dt)
+        m32.rk_step(b, dt=dt)
+        if step % 10 == 9:
+            d64, d32 = m64.diagnostics(a), m32.diagnostics(b)
+            worst = max(worst, abs(d32["ke"] - d64["ke"]) / d64["ke"], abs(d32["eps_s"] - d64["eps_s"]) / d64["eps_s"])
+    m32.check_state()
+    assert worst <= 1e-6, worst
+
+
 @pytest.mark.parametrize("order,scheme,n,jit", [(1, 0, 16, 0.0), (2, 1, 10, 0.1)])
 def test_ke_history_100_steps(order, scheme, n, jit):
     """Kinetic-energy (and dissipation) history over 100 steps with the CFL
@@ -160,13 +203,13 @@ def test_diagnostics_and_time_step_parity():
     assert abs(dtg - dtc) <= 1e-14 * dtc  # per-cell limits round differently; the min is exact
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_multi_step_entry_point_equals_single_steps(prec):
+@pytest.mark.parametrize("prec,integrator", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_multi_step_entry_point_equals_single_steps(prec, integrator):
     """ucns_rk_steps (several steps in one call; the mixed form carries its
     float pair of the state between them) gives the state and the simulated
-    time of as many ucns_rk_step calls, bit for bit."""
+    time of as many ucns_rk_step calls, bit for bit, with either integrator."""
     nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=9)
-    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=prec))
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=prec, integrator=integrator))
     U = np.ascontiguousarray(m.to_internal(I.noisy_state(nodes, cells, 0.1, 0.03, seed=4)))
     a = torch.from_numpy(U.copy()).cuda()
     b = torch.from_numpy(U.copy()).cuda()

@@ -59,6 +59,9 @@ def test_error_codes_without_gpu():
     with pytest.raises(ucns.UcnsError) as e:
         m.precompute_host(ucns.Params(order=1, scheme=1))
     assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:
+        m.precompute_host(ucns.Params(order=1, scheme=0, integrator=2))
+    assert e.value.code == -1
     # 2 cells across a periodic box: each face tuple appears 4 times (non-manifold)
     with pytest.raises(ucns.UcnsError) as e:
         ucns.Mesh(*I.hex_lattice(2))

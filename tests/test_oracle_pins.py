@@ -378,6 +378,67 @@ def test_ssprk3_stability_polynomial():
         assert math.isclose(O.ssprk3_linear(z, 1.0, 1.0), ref, rel_tol=1e-15)
 
 
+def _tableau_from_shu_osher(alpha, beta):
+    """u_i = sum_j (alpha_ij u_j + dt beta_ij L(u_j)) rewritten as
+    u_i = u_0 + dt sum_k A_ik L(u_k): the Butcher matrix (rows of the stages
+    u_0..u_{s-1}) and the weights (the row of u_s)."""
+    s = alpha.shape[0] - 1
+    A = np.zeros((s + 1, s))
+    for i in range(1, s + 1):
+        for j in range(i):
+            A[i] += alpha[i, j] * A[j]
+            A[i, j] += beta[i, j]
+    return A[:s], A[s]
+
+
+def test_ssp54_coefficients_meet_the_order_conditions():
+    """The fourth-order SSP scheme of Eq. 8 (Spiteri-Ruuth SSP(5,4)) as stored
+    in the oracle, against the mathematics of Runge-Kutta methods: every stage
+    is consistent (its alpha row sums to 1), all coefficients are nonnegative,
+    the weights satisfy the eight order conditions of the rooted trees with at
+    most four nodes, an order-5 condition fails (order exactly 4), and the SSP
+    coefficient min alpha/beta is 1.508."""
+    alpha, beta = O.ssp54_coefficients()
+    for i in range(1, 6):
+        assert abs(alpha[i, :i].sum() - 1.0) < 3e-15, i
+    assert (alpha >= 0).all() and (beta >= 0).all()
+    A, b = _tableau_from_shu_osher(alpha, beta)
+    c = A.sum(axis=1)
+    conditions = [
+        (b.sum(), 1.0), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ (A @ c), 1 / 6),
+        (b @ c ** 3, 1 / 4), (b @ (c * (A @ c)), 1 / 8), (b @ (A @ c ** 2), 1 / 12), (b @ (A @ (A @ c)), 1 / 24),
+    ]
+    for k, (got, want) in enumerate(conditions):
+        assert abs(got - want) < 1e-14, (k, got, want)
+    assert abs(b @ c ** 4 - 1 / 5) > 1e-4
+    ssp = min(alpha[i, j] / beta[i, j] for i in range(6) for j in range(5) if beta[i, j] > 0)
+    assert 1.5081 < ssp < 1.5082
+
+
+def test_ssp54_stability_polynomial():
+    """One SSP(5,4) step of du/dt = z u is the degree-5 polynomial whose terms
+    up to z^4 are those of e^z and whose z^5 coefficient is b A^3 c of the
+    tableau (the stepper combines the stages as the coefficients say)."""
+    A, b = _tableau_from_shu_osher(*O.ssp54_coefficients())
+    c = A.sum(axis=1)
+    g = b @ (A @ (A @ (A @ c)))
+    assert 0.004 < g < 0.005
+    for z in (-0.3, -1.0, -2.5, 0.7, 0.05):
+        ref = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24 + g * z ** 5
+        assert math.isclose(O.ssp54_linear(z, 1.0, 1.0), ref, rel_tol=1e-14), z
+
+
+def test_rk_orders_on_a_nonlinear_ode():
+    """Logistic equation u' = u (1 - u), u(0) = 0.2, to T = 2 against its
+    closed form 1 / (1 + 4 e^-T): halving dt divides the error by 2^4 with
+    SSP(5,4) and by 2^3 with SSP-RK3."""
+    exact = 1.0 / (1.0 + 4.0 * math.exp(-2.0))
+    for integrator, order in ((1, 4), (0, 3)):
+        e = [abs(O.logistic(0.2, 2.0, n, integrator) - exact) for n in (16, 32, 64, 128)]
+        rates = [math.log2(e[k] / e[k + 1]) for k in range(3)]
+        assert all(abs(r - order) < 0.25 for r in rates), (integrator, rates)
+
+
 # ---------------------------------------------------------- Taylor-Green ---
 def test_tgv_initial_diagnostics_converge_to_closed_forms():
     gold = _golden("tgv_initial.txt")

@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(256) k_rk54(RKArgs a) {
   const double w = -(*a.dt) * a.inv_vol[i];
   constexpr double B = STAGE == 1 ? C::b10 : STAGE == 2 ? C::b21 : STAGE == 3 ? C::b32 : STAGE == 4 ? C::b43 : C::b54;
   const double cw = B * w, cw53 = C::b53 * w;
+  const float cwf = __double2float_rn(cw), cwf53 = __double2float_rn(cw53);
   double Un[5];
 #pragma unroll
   for (int v = 0; v < 5; v++) {
@@ -592,8 +593,8 @@ __global__ void __launch_bounds__(256) k_rk54(RKArgs a) {
       // as in k_rk: the small part of the FP32 pair's product in FP32
       const float2 sp = face_sum_pair<NFC>(a, G, fe, v);
       s = f2d(sp.x);
-      p = f2d(__double2float_rn(cw) * sp.y);
-      if (STAGE == 4) p53 = f2d(__double2float_rn(cw53) * sp.y);
+      p = f2d(cwf * sp.y);
+      if (STAGE == 4) p53 = f2d(cwf53 * sp.y);
     } else {
       s = face_sum<NFC>(a, G, fe, v);
     }

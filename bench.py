@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""Throughput of the explicit residual + SSP-RK3 path in cell-RK-stages/s.
+"""Throughput of the explicit residual + SSP Runge-Kutta path in cell-RK-stages/s.
 
 Workload (default): compressible Taylor-Green vortex, Mach 0.1, Re 1600, on
 64^3 hexahedra of [0, 2 pi]^3 with interior nodes jittered by a seeded
@@ -7,9 +7,10 @@ uniform +-10 % of the spacing, P2 least-squares reconstruction with CWENOZ
 weights over central + directional stencils, FP64, SSP-RK3 at CFL 0.5 with
 the CFL time step computed on the device every step.  One "step" is one full
 SSP-RK3 step (3 residual evaluations + the time step reduction); the metric
-counts cells x 3 stages per second.
+counts cells x 3 stages per second.  ``--integrator 1`` times the paper's
+SSP(5,4) instead (5 stages per step).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ucns|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ucns|reference] [--integrator 0|1]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
 replica of the workload on its own GPU (the path is replicated, not sharded:
@@ -58,6 +59,8 @@ def parse():
     ap.add_argument("--n", type=int, default=64, help="lattice cells per direction")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--integrator", type=int, default=0, choices=[0, 1],
+                    help="0: SSP-RK3 (the benchmark configuration), 1: the paper's SSP(5,4) (5 stages per step)")
     ap.add_argument("--train-epochs", type=int, default=60,
                     help="indicator training epochs of the learned form (fewer: faster setup, more flagged cells)")
     ap.add_argument("--forms", default="fp64,mixed,learned",
@@ -73,10 +76,14 @@ def workload(n: int):
     return nodes, cells, box, U
 
 
+def rk_name() -> str:
+    return "SSP(5,4)" if STAGES == 5 else "SSP-RK3"
+
+
 def config(n: int, N: int, world: int) -> dict:
     return {
         "workload": f"TGV M0.1 Re1600, {n}^3 jittered (+-10% h, seed 1) hex = {N} cells, P2 CWENOZ, "
-                    "SSP-RK3 CFL 0.5, device CFL dt every step; plain FP64 and the mixed form timed",
+                    f"{rk_name()} CFL 0.5, device CFL dt every step; plain FP64 and the mixed form timed",
         "cells": N,
         "stages_per_step": STAGES,
         "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -193,15 +200,29 @@ def oracle_sample(nodes, cells, box, U, n: int, layers: int):
     of the lattice (layers * n^2 cells)."""
     import oracle as O
 
-    oc = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5))
+    oc = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5,
+                                            integrator=1 if STAGES == 5 else 0))
     sel = np.arange(layers * n * n, dtype=np.int64)
     oc.residual_subset(U, sel[:8])  # warm the lazy precompute path
     return oc, sel
 
 
 def oracle_rk_step_on_sample(oc, U, sel, dt):
-    """Three SSP-RK3 stages on the sample cells (residual of the sample +
-    Shu-Osher combination), the oracle's arithmetic per stage."""
+    """The stages of one step on the sample cells (residual of the sample +
+    Shu-Osher combination), the oracle's arithmetic per stage: SSP-RK3, or
+    SSP(5,4) with the oracle's coefficients."""
+    if STAGES == 5:
+        import oracle as O
+
+        alpha, beta = O.ssp54_coefficients()
+        Uw = U.copy()
+        u, L = [U[:, sel].copy()], []
+        for i in range(1, 6):
+            L.append(oc.residual_subset(Uw, sel))
+            ui = sum(alpha[i, j] * u[j] + dt * beta[i, j] * L[j] for j in range(i))
+            u.append(ui)
+            Uw[:, sel] = ui
+        return u[5]
     U0 = U[:, sel].copy()
     Uw = U.copy()
     R = oc.residual_subset(Uw, sel)
@@ -227,7 +248,7 @@ def cpu_baseline(nodes, cells, box, U, n: int) -> dict:
     oracle_rk_step_on_sample(oc, U, sel, dt)
     t = time.perf_counter() - t0
     return {"value": sel.size * STAGES / t, "unit": UNIT, "cores": omp_threads(), "kind": "oracle",
-            "sample": f"one SSP-RK3 step (3 residual evaluations + updates) of {sel.size} of the "
+            "sample": f"one {rk_name()} step ({STAGES} residual evaluations + updates) of {sel.size} of the "
                       f"{len(cells)} cells (8 z-layers of the {n}^3 workload), precompute excluded",
             "seconds": t}
 
@@ -246,7 +267,7 @@ def run_reference(args, rank: int, world: int):
         oracle_rk_step_on_sample(oc, U, sel, dt)
     t = time.perf_counter() - t0
     value = sel.size * STAGES * args.steps / t
-    sample = (f"each step: one SSP-RK3 step (3 residual evaluations + updates) of {sel.size} of the "
+    sample = (f"each step: one {rk_name()} step ({STAGES} residual evaluations + updates) of {sel.size} of the "
               f"{len(cells)} cells (4 z-layers of the {n}^3 workload)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -359,7 +380,7 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     nodes, cells, box, U_user = workload(n)
     N = len(cells)
     stream = torch.cuda.current_stream()
-    base = dict(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5)
+    base = dict(order=2, scheme=1, Re=1600.0, Mach=0.1, cfl=0.5, integrator=args.integrator)
     forms = [f for f in args.forms.split(",") if f]
     prec = {"fp64": 0, "mixed": 1, "learned": 1}
     meshes = {f: ucns.Mesh(nodes, cells, box, ucns.Params(precision=prec[f], **base)) for f in forms}
@@ -505,7 +526,9 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
 
 
 def main():
+    global STAGES
     args = parse()
+    STAGES = 5 if args.integrator == 1 else 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -219,6 +219,27 @@ def test_multi_step_entry_point_equals_single_steps(prec, integrator):
     assert tb == t or abs(tb - t) <= 1e-15 * t  # the device adds the same dts in the same order
 
 
+@pytest.mark.parametrize("prec,integrator", [(0, 0), (1, 0), (1, 1)])
+def test_resume_from_a_saved_state_is_bitwise(prec, integrator):
+    """Checkpoint / resume: 3 steps, the state saved to the host and loaded
+    into a freshly built mesh, 3 more steps there, equals 6 uninterrupted
+    steps bit for bit (time included)."""
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=11)
+    p = ucns.Params(order=2, scheme=1, precision=prec, integrator=integrator)
+    m = ucns.Mesh(nodes, cells, box, p)
+    U = np.ascontiguousarray(m.to_internal(I.noisy_state(nodes, cells, 0.1, 0.03, seed=6)))
+    a = torch.from_numpy(U.copy()).cuda()
+    ta = m.rk_steps(a, 6)
+    b = torch.from_numpy(U.copy()).cuda()
+    tb = m.rk_steps(b, 3)
+    saved = b.cpu().numpy()
+    m2 = ucns.Mesh(nodes, cells, box, p)
+    c = torch.from_numpy(saved).cuda()
+    tb += m2.rk_steps(c, 3)
+    assert torch.equal(a, c)
+    assert abs(ta - tb) <= 1e-15 * ta  # the same dts, summed in two groups
+
+
 def test_deterministic_and_host_entry_point():
     nodes, cells, box = I.hex_lattice(14, jitter=0.1, seed=9)
     m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1))

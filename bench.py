@@ -432,10 +432,9 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
         barrier()
         ms = e0.elapsed_time(e1)
         m.check_state()
-        # per-kernel times from a separate run on a copy of the state: the events
-        # the library records around each launch when profiling would also break
-        # the overlap of consecutive kernels (programmatic dependent launch) that
-        # the timed run has
+        # per-kernel times from a separate run on a copy of the state: the
+        # events the library records around each launch when profiling cost
+        # ~40 us per step, which the timed run must not include
         Up = U.clone()
         m.profile(True)
         m.rk_steps(Up, prof_steps)
@@ -449,6 +448,15 @@ def run_ucns(args, rank: int, world: int, local_rank: int):
     res = {k: timed(m) for k, m in meshes.items()}
     if gate_info is not None:
         gate_info["flagged_fraction_last_step"] = meshes["learned"].gate_flagged() / N
+        # the library switches the gate off for good when a plain-scheme check
+        # fails; a gate still on after the timed and the profiled steps was on
+        # throughout the timed run
+        try:
+            rel, _ = meshes["learned"].gate_check(res["learned"]["U"].clone())
+            gate_info["gate_on_after_runs"] = True
+            gate_info["check_rel_diff_after_runs"] = rel
+        except ucns.UcnsError:
+            gate_info["gate_on_after_runs"] = False
     # the fixed-error comparison: every form ran warmup + steps from the same state
     errs = {}
     if "fp64" in res:

@@ -1,4 +1,4 @@
-"""GB300-native explicit residual + SSP-RK3 of a high-order unstructured
+"""GB300-native explicit residual + SSP Runge-Kutta update of a high-order unstructured
 finite-volume scheme for the compressible Navier-Stokes equations.
 
 The compute path is libucns.so (CUDA kernels for sm_103a behind a C ABI,

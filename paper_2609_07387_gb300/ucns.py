@@ -269,8 +269,8 @@ class Mesh:
         return R
 
     def rk_step(self, U, dt: float | None = None, stream=None, return_dt: bool = False):
-        """One SSP-RK3 step in place.  dt=None: CFL dt on the device (no
-        sync unless return_dt); dt>0: fixed."""
+        """One step of the mesh's integrator (SSP-RK3 or SSP(5,4), Params.integrator)
+        in place.  dt=None: CFL dt on the device (no sync unless return_dt); dt>0: fixed."""
         ptr = _dev_ptr(U, self.n_cells)
         if dt is not None and dt > 0:
             d = C.c_double(dt)

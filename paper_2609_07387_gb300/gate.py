@@ -93,15 +93,16 @@ def train(X, y, epochs: int = 4, batch: int = 8192, lr: float = 2e-3, seed: int 
 
 
 def threshold_for_recall(net: ucns.Net, X, y, recall: float = 0.999) -> float:
-    """Largest logit threshold whose recall of y = 1 on (X, y) is >= recall."""
-    import torch
-
+    """Largest FP32 logit threshold whose recall of y = 1 on (X, y) is >= recall
+    (a cell is flagged when its logit exceeds the threshold): with the troubled
+    samples' logits sorted, at most m = floor((1 - recall) n) of them may lie at
+    or below it, so it sits just below the (m+1)-th smallest."""
     z = net.forward(X)
-    zp = z[y > 0.5].float()
-    if zp.numel() == 0:
+    zp = np.sort(z[y > 0.5].float().cpu().numpy().astype(np.float32))
+    if zp.size == 0:
         return float("inf")
-    q = torch.quantile(zp.cpu(), 1.0 - recall).item()
-    return float(np.nextafter(np.float32(q), np.float32(-np.inf)))
+    m = int(np.floor((1.0 - recall) * zp.size + 1e-9))
+    return float(np.nextafter(zp[min(m, zp.size - 1)], np.float32(-np.inf)))
 
 
 def confusion(net: ucns.Net, X, y, thr: float) -> dict:

@@ -239,6 +239,104 @@ def test_smoothness_indicator_closed_forms():
     assert math.isclose(c.smoothness(3, a, 2), 2.0 / 12.0 + 1.0, rel_tol=1e-13)
 
 
+# ------------------------------------------------------------------ P3 ---
+# Cubic reconstruction on hexahedra (the TGV-P3 row of Table 4): K = 19
+# modes, central stencils of 2K = 38 cells, 6 linear directional stencils,
+# 3 x 3 Gauss points per face.
+def _cubic_monomials(x):
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    return np.stack([np.ones_like(X), X, Y, Z, X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z,
+                     X ** 3, Y ** 3, Z ** 3, X * X * Y, X * X * Z, X * Y * Y, Y * Y * Z, X * Z * Z, Y * Z * Z,
+                     X * Y * Z], axis=1)
+
+
+def _cubic_gradients(x):
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    o, z = np.ones_like(X), np.zeros_like(X)
+    gx = [z, o, z, z, 2 * X, z, z, Y, Z, z, 3 * X * X, z, z, 2 * X * Y, 2 * X * Z, Y * Y, z, Z * Z, z, Y * Z]
+    gy = [z, z, o, z, z, 2 * Y, z, X, z, Z, z, 3 * Y * Y, z, X * X, z, 2 * X * Y, 2 * Y * Z, z, Z * Z, X * Z]
+    gz = [z, z, z, o, z, z, 2 * Z, z, X, Y, z, z, 3 * Z * Z, z, X * X, z, Y * Y, 2 * X * Z, 2 * Y * Z, X * Y]
+    return np.stack([np.stack(gx, 1), np.stack(gy, 1), np.stack(gz, 1)], axis=2)  # [n, 20, 3]
+
+
+def test_counts_p3_match_benchmark_matrix():
+    """Table 4 (TGV-P3): 74M/2M = 37 reconstructed DoF per cell and variable
+    (19 cubic central + 6 linear directional x 3), 54M/6M = 9 quadrature
+    points per face; Eq. 3's K(3, 3) = 20 terms with the mean -> 19 modes."""
+    cells_, faces, dof, qps = _golden("benchmark_matrix.txt")["TGV-P3"]
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=3)
+    c = O.Case(nodes, cells, box, O.Params(order=3, scheme=1))
+    assert c.K == math.comb(3 + 3, 3) - 1 == 19
+    assert c.K + c.nd * 3 == round(dof / cells_)
+    assert c.nq == round(qps / faces) == 9
+    assert c.Mc == 2 * c.K and c.nd == 6 and c.Md == 6
+    assert c.n_faces == 3 * c.n_cells
+
+
+@pytest.mark.parametrize("scheme,degree", [(0, 3), (1, 1)])
+def test_k_exact_p3(scheme, degree):
+    """Cell averages of a random polynomial of degree <= 3: the central cubic
+    reconstruction reproduces it (value and gradient) at arbitrary points,
+    including cells whose stencils cross the periodic wrap; CWENOZ at P3 is
+    exact for degree <= 1 (every candidate is)."""
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=5)
+    c = O.Case(nodes, cells, box, O.Params(order=3, scheme=scheme))
+    rng = np.random.default_rng(degree)
+    poly = rng.normal(size=(5, 20)) * 0.2
+    if degree == 1:
+        poly[:, 4:] = 0.0
+    for i in (0, 77, 511):
+        x = I.cell_vertex_means(nodes, cells)[i:i + 1] + rng.uniform(-0.3, 0.3, size=(4, 3))
+        val, grad = c.kexact_probe(i, poly, x)
+        ref = _cubic_monomials(x) @ poly.T
+        gref = np.einsum("nkj,vk->nvj", _cubic_gradients(x), poly)
+        assert np.abs(val - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), (i, np.abs(val - ref).max())
+        assert np.abs(grad - gref).max() <= 1e-9 * max(1.0, np.abs(gref).max()), (i, np.abs(grad - gref).max())
+
+
+def test_smoothness_indicator_cubic_closed_forms():
+    """SI with the |beta| = 3 terms (weight V^1), on a cube of side h with
+    xi = (x - x_c)/h: p = xi^3 gives int (3 xi^2)^2 + int (6 xi)^2 + 6^2 =
+    9/80 + 3 + 36, p = xi eta zeta gives 3/144 + 3/12 + 1, and p = xi^2 eta
+    gives 4/144 + 1/80 + 2/3 + 4."""
+    nodes, cells, box = I.hex_lattice(8)
+    c = O.Case(nodes, cells, box, O.Params(order=3, scheme=1))
+    a = np.zeros(19); a[9] = 1.0
+    assert math.isclose(c.smoothness(5, a, 3), 9 / 80 + 3 + 36, rel_tol=1e-13)
+    a = np.zeros(19); a[18] = 1.0
+    assert math.isclose(c.smoothness(5, a, 3), 3 / 144 + 3 / 12 + 1, rel_tol=1e-13)
+    a = np.zeros(19); a[12] = 1.0  # xi^2 eta: 4/144 + 1/80, then (2 eta)^2 + (2 xi)^2 -> 2/3, then 2^2
+    assert math.isclose(c.smoothness(5, a, 3), 4 / 144 + 1 / 80 + 2 / 3 + 4, rel_tol=1e-13)
+    a = np.zeros(19); a[0] = 0.7  # a linear p: the first-derivative term only, as at P1
+    assert math.isclose(c.smoothness(5, a, 3), 0.49, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_free_stream_and_conservation_p3(scheme):
+    """Uniform flow gives a zero residual; any state's volume-weighted
+    residual sums to zero on the periodic box (P3 on jittered hexahedra)."""
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=4)
+    c = O.Case(nodes, cells, box, O.Params(order=3, scheme=scheme))
+    n = len(cells)
+    U = I.primitive_to_conserved(np.ones(n), 0.3 * np.ones(n), -0.2 * np.ones(n), 0.1 * np.ones(n),
+                                 np.ones(n) / (1.4 * 0.01))
+    R, S = c.residual_terms(U)
+    assert np.abs(R).max() <= 1e-12 * S.max()
+    U = I.noisy_state(nodes, cells, 0.1, 0.05, seed=2)
+    R, S = c.residual_terms(U)
+    vol, _, _ = c.geometry()
+    tot = np.abs((R * vol).sum(axis=1))
+    assert np.all(tot <= 1e-12 * (S * vol).sum(axis=1)), tot
+
+
+def test_order_density_wave_p3():
+    """Smooth density wave (exact Euler solution), P3 linear reconstruction
+    with the fourth-order SSP(5,4): L1 error order -> 4 (n = 8, 16, 32)."""
+    e = [_density_wave_error(n, 3, 0, integrator=1) for n in (8, 16, 32)]
+    rates = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert all(r > 3.6 for r in rates), rates
+
+
 # ------------------------------------------------------------ invariants ---
 @pytest.mark.parametrize("kind", ["hex", "tet"])
 def test_free_stream_preservation(kind, jhex8_p2, jtet_p2):
@@ -465,9 +563,9 @@ def test_tgv_initial_ke_mach_independent():
 
 
 # ---------------------------------------------------- order of accuracy ---
-def _density_wave_error(n, order, scheme, T=0.05):
+def _density_wave_error(n, order, scheme, T=0.05, integrator=0):
     nodes, cells, box = I.hex_lattice(n)
-    c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=0.0))
+    c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=0.0, integrator=integrator))
     p = [1.0, 0.2, 1.0, 0.5, 0.25, 1.0, 0.0, 1.4]
     U = c.cell_average("density_wave", p)
     nst = int(math.ceil(T / c.time_step(U)))

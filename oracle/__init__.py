@@ -67,7 +67,7 @@ def _load():
             lib.orc_smoothness.restype = D
             lib.orc_smoothness.argtypes = [P, I64, P, C.c_int]
             lib.orc_kexact_probe.argtypes = [P, I64, P, C.c_int, P, P, P]
-            lib.orc_kexact_probe3.argtypes = [P, I64, P, C.c_int, P, P, P]
+            lib.orc_kexact_probeN.argtypes = [P, I64, P, C.c_int, C.c_int, P, P, P]
             lib.orc_cell_average.argtypes = [P, C.c_int, P, C.c_int, P]
             lib.orc_diagnostics.argtypes = [P, P, P]
             lib.orc_features.argtypes = [P, P, P]
@@ -173,7 +173,7 @@ class Case:
 
     def stencil(self, i: int, which: int = -1):
         M = self.Mc if which < 0 else self.Md
-        K = self.K if which < 0 else 3
+        K = self.K if which < 0 else self.Md // 2
         mem, sh = np.zeros(M, np.int64), np.zeros((M, 3), np.int32)
         A, P = np.zeros((M, K)), np.zeros((K, M))
         self._check(self._lib.orc_stencil(self._h, i, which, _p(mem), _p(sh), _p(A), _p(P)))
@@ -240,12 +240,16 @@ class Case:
 
     def kexact_probe(self, i: int, poly, x):
         """Reconstruct cell i from the cell averages of a polynomial in the
-        physical coordinates (poly [5][10]: up to quadratic, or [5][20]: up to
-        cubic, terms as in the C source) and evaluate it at the points x."""
+        physical coordinates (poly [5][10]: up to quadratic, [5][20]: up to
+        cubic, [5][35]: up to quartic; terms as in the C source) and evaluate
+        it at the points x."""
         poly, x = _f64(poly), _f64(np.atleast_2d(x))
         val, grad = np.zeros((x.shape[0], 5)), np.zeros((x.shape[0], 5, 3))
-        f = self._lib.orc_kexact_probe3 if poly.shape[-1] == 20 else self._lib.orc_kexact_probe
-        self._check(f(self._h, i, _p(poly), x.shape[0], _p(x), _p(val), _p(grad)))
+        if poly.shape[-1] == 10:
+            self._check(self._lib.orc_kexact_probe(self._h, i, _p(poly), x.shape[0], _p(x), _p(val), _p(grad)))
+        else:
+            self._check(self._lib.orc_kexact_probeN(self._h, i, _p(poly), poly.shape[-1], x.shape[0], _p(x),
+                                                    _p(val), _p(grad)))
         return val, grad
 
     def cell_average(self, kind: str, p, nq1d: int = 5):

@@ -28,10 +28,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_MAXK 19     /* non-constant modes of a cubic in 3-D (Eq. 3, K-1; P3) */
-#define ORC_MAXM 38     /* central stencil size 2K */
+#define ORC_MAXK 34     /* non-constant modes of a quartic in 3-D (Eq. 3, K-1; P4) */
+#define ORC_MAXM 68     /* central stencil size 2K */
 #define ORC_MAXD 6      /* directional stencils: one per element face */
-#define ORC_MD 6        /* directional stencil size 2*K(linear) */
+#define ORC_MD 18       /* largest directional stencil: 2 x 9 (quadratic candidates at P4) */
 
 typedef struct {
   int64_t N, nn;
@@ -48,6 +48,7 @@ typedef struct {
   int rk;  /* 0: SSP-RK3, 1: SSP(5,4) */
   double gam, Pr, Re, Mach, cfl, lamc, eps, alpha;
   int K, nq, Mc, nd, Md;
+  int Kd;  /* modes of a directional candidate: 3 (linear, P2 and P3) or 9 (quadratic, P4) */
   /* geometry */
   double *vol, *cen, *hh, *psib; /* psib [N][ORC_MAXK]: (1/V) int psi_k */
   /* faces */
@@ -192,7 +193,36 @@ static void cell_quad(const orc_case *c, int64_t i, int n, cell_fn f, void *ctx)
 /* xxx, yyy, zzz, xxy, xxz, xyy, yyz, xzz, yzz, xyz (P3: 19);                */
 /* phi_k = psi_k - (1/V_i) int psi_k.                                        */
 /* ------------------------------------------------------------------------ */
-static void psi_eval(const double xi[3], double p[ORC_MAXK]) {
+/* exponents of every basis monomial, in basis order */
+static const int MONO[ORC_MAXK][3] = {
+    {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+    {3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1},
+    {4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1}, {1, 3, 0}, {0, 3, 1}, {1, 0, 3}, {0, 1, 3},
+    {2, 2, 0}, {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+/* d^b of the monomial with exponents e at xi: the falling-factorial
+   coefficient, then the remaining powers of x, y and z in that order */
+static double mono_d(const int e[3], const int b[3], const double xi[3]) {
+  double v = 1.0;
+  for (int d = 0; d < 3; d++) {
+    if (b[d] > e[d]) return 0.0;
+    for (int j = 0; j < b[d]; j++) v *= (double)(e[d] - j);
+  }
+  for (int d = 0; d < 3; d++)
+    for (int j = 0; j < e[d] - b[d]; j++) v *= xi[d];
+  return v;
+}
+/* the derivative multi-indices of order 1..4, each once, in a fixed order */
+static const int DER1[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+static const int DER3[10][3] = {{3, 0, 0}, {0, 3, 0}, {0, 0, 3}, {2, 1, 0}, {2, 0, 1},
+                                {1, 2, 0}, {0, 2, 1}, {1, 0, 2}, {0, 1, 2}, {1, 1, 1}};
+static const int DER4[15][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {3, 1, 0}, {3, 0, 1}, {1, 3, 0}, {0, 3, 1}, {1, 0, 3},
+                                {0, 1, 3}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};
+static const int DER2[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+static const int ZERO3[3] = {0, 0, 0};
+
+/* psi_eval / psi_grad / psi_hess fill the first nk entries (nk <= ORC_MAXK;
+   the explicit P1-P3 entries are always written) */
+static void psi_eval(const double xi[3], double p[ORC_MAXK], int nk) {
   const double x = xi[0], y = xi[1], z = xi[2];
   p[0] = x; p[1] = y; p[2] = z;
   p[3] = x * x; p[4] = y * y; p[5] = z * z;
@@ -200,9 +230,10 @@ static void psi_eval(const double xi[3], double p[ORC_MAXK]) {
   p[9] = x * x * x; p[10] = y * y * y; p[11] = z * z * z;
   p[12] = x * x * y; p[13] = x * x * z; p[14] = x * y * y;
   p[15] = y * y * z; p[16] = x * z * z; p[17] = y * z * z; p[18] = x * y * z;
+  for (int k = 19; k < nk; k++) p[k] = mono_d(MONO[k], ZERO3, xi);  /* quartics (P4) */
 }
 /* d psi_k / d xi_j */
-static void psi_grad(const double xi[3], double g[ORC_MAXK][3]) {
+static void psi_grad(const double xi[3], double g[ORC_MAXK][3], int nk) {
   const double x = xi[0], y = xi[1], z = xi[2];
   memset(g, 0, sizeof(double) * ORC_MAXK * 3);
   g[0][0] = 1; g[1][1] = 1; g[2][2] = 1;
@@ -218,9 +249,11 @@ static void psi_grad(const double xi[3], double g[ORC_MAXK][3]) {
   g[16][0] = z * z; g[16][2] = 2 * x * z;
   g[17][1] = z * z; g[17][2] = 2 * y * z;
   g[18][0] = y * z; g[18][1] = x * z; g[18][2] = x * y;
+  for (int k = 19; k < nk; k++)
+    for (int j = 0; j < 3; j++) g[k][j] = mono_d(MONO[k], DER1[j], xi);
 }
 /* second derivatives d2 psi_k / d xi_a d xi_b in the order xx,yy,zz,xy,xz,yz */
-static void psi_hess(const double xi[3], double H[ORC_MAXK][6]) {
+static void psi_hess(const double xi[3], double H[ORC_MAXK][6], int nk) {
   const double x = xi[0], y = xi[1], z = xi[2];
   memset(H, 0, sizeof(double) * ORC_MAXK * 6);
   H[3][0] = 2; H[4][1] = 2; H[5][2] = 2;
@@ -233,15 +266,9 @@ static void psi_hess(const double xi[3], double H[ORC_MAXK][6]) {
   H[16][2] = 2 * x; H[16][4] = 2 * z;              /* xzz */
   H[17][2] = 2 * y; H[17][5] = 2 * z;              /* yzz */
   H[18][3] = z; H[18][4] = y; H[18][5] = x;        /* xyz */
+  for (int k = 19; k < nk; k++)
+    for (int j = 0; j < 6; j++) H[k][j] = mono_d(MONO[k], DER2[j], xi);
 }
-/* third derivatives (constants) in the order xxx,yyy,zzz,xxy,xxz,xyy,yyz,xzz,yzz,xyz */
-static void psi_d3(double T[ORC_MAXK][10]) {
-  memset(T, 0, sizeof(double) * ORC_MAXK * 10);
-  T[9][0] = 6; T[10][1] = 6; T[11][2] = 6;
-  T[12][3] = 2; T[13][4] = 2; T[14][5] = 2; T[15][6] = 2; T[16][7] = 2; T[17][8] = 2;
-  T[18][9] = 1;
-}
-
 /* ------------------------------------------------------------------------ */
 /* Geometry: volume, centroid, h, mean of each monomial.                     */
 /* ------------------------------------------------------------------------ */
@@ -256,7 +283,7 @@ static void f_psibar(void *ctx, const double x[3], double w) {
   pb_ctx *q = (pb_ctx *)ctx;
   double xi[3], p[ORC_MAXK];
   for (int d = 0; d < 3; d++) xi[d] = (x[d] - q->c[d]) / q->h;
-  psi_eval(xi, p);
+  psi_eval(xi, p, ORC_MAXK);
   for (int k = 0; k < ORC_MAXK; k++) q->s[k] += w * p[k];
 }
 
@@ -529,7 +556,7 @@ static void f_arow(void *ctx, const double x[3], double w) {
   am_ctx *q = (am_ctx *)ctx;
   double xi[3], p[ORC_MAXK];
   for (int d = 0; d < 3; d++) xi[d] = (x[d] + q->sh[d] - q->c[d]) / q->h;
-  psi_eval(xi, p);
+  psi_eval(xi, p, q->K);
   for (int k = 0; k < q->K; k++) q->s[k] += w * (p[k] - q->pb[k]);
 }
 
@@ -592,7 +619,7 @@ static int lsq_pinv(const double *A, int M, int K, const double *Vm, double *P) 
 static int ensure_cell(orc_case *c, int64_t i) {
   if (c->ready[i]) return 0;
   cand buf[256];
-  int n = bfs(c, i, -1, 3, buf, 256);
+  int n = bfs(c, i, -1, c->order == 4 ? 4 : 3, buf, 256);  /* 2K = 68 members at P4 need 4 layers */
   if (n < 0) { set_err("stencil search overflow"); return -1; }
   for (int q = 1; q < n; q++) buf[q].shared = shared_nodes(c, i, buf[q].id);
   qsort(buf + 1, n - 1, sizeof(cand), cmp_central);
@@ -609,7 +636,7 @@ static int ensure_cell(orc_case *c, int64_t i) {
   if (lsq_pinv(A, c->Mc, c->K, Vm, &c->Pc[i * c->K * c->Mc])) return -1;
   for (int s = 0; s < c->nd; s++) {
     int64_t nf = face_nbr(c, i, s);
-    int m = bfs(c, nf, i, 2, buf, 256);
+    int m = bfs(c, nf, i, c->Kd == 3 ? 2 : 3, buf, 256);
     if (m < 0) { set_err("stencil search overflow"); return -1; }
     qsort(buf + 1, m - 1, sizeof(cand), cmp_dir);
     if (m < c->Md) { set_err("too few cells for a directional stencil"); return -1; }
@@ -620,8 +647,8 @@ static int ensure_cell(orc_case *c, int64_t i) {
       image_shift(c, i, sd[r], &ds[3 * r]);
       Vm[r] = c->vol[sd[r]];
     }
-    lsq_matrix(c, i, c->Md, sd, ds, 3, A);
-    if (lsq_pinv(A, c->Md, 3, Vm, &c->Pd[(i * c->nd + s) * 3 * c->Md])) return -1;
+    lsq_matrix(c, i, c->Md, sd, ds, c->Kd, A);
+    if (lsq_pinv(A, c->Md, c->Kd, Vm, &c->Pd[(i * c->nd + s) * c->Kd * c->Md])) return -1;
   }
   c->ready[i] = 1;
   return 0;
@@ -639,14 +666,14 @@ static int ensure_all(orc_case *c) {
 /* Smoothness indicator (reading of Eq. 6): SI = sum over 1<=|beta|<=r of   */
 /* V^(2|beta|/3 - 1) int_V (d^beta p)^2 dV, integrated by quadrature.        */
 /* ------------------------------------------------------------------------ */
-typedef struct { double c[3], h, w1, w2, w3; const double *a; int deg; double s; } si_ctx;
+typedef struct { double c[3], h, w1, w2, w3, w4; const double *a; int deg; double s; } si_ctx;
 static void f_si(void *ctx, const double x[3], double w) {
   si_ctx *q = (si_ctx *)ctx;
   double xi[3], g[ORC_MAXK][3], H[ORC_MAXK][6];
   for (int d = 0; d < 3; d++) xi[d] = (x[d] - q->c[d]) / q->h;
-  psi_grad(xi, g);
-  psi_hess(xi, H);
-  int K = q->deg == 1 ? 3 : (q->deg == 2 ? 9 : 19);
+  int K = q->deg == 1 ? 3 : (q->deg == 2 ? 9 : (q->deg == 3 ? 19 : 34));
+  psi_grad(xi, g, K);
+  psi_hess(xi, H, K);
   for (int j = 0; j < 3; j++) {
     double d = 0;
     for (int k = 0; k < K; k++) d += q->a[k] * g[k][j] / q->h;
@@ -658,15 +685,18 @@ static void f_si(void *ctx, const double x[3], double w) {
       for (int k = 0; k < K; k++) d += q->a[k] * H[k][j] / (q->h * q->h);
       q->s += w * q->w2 * d * d;
     }
-  if (q->deg == 3) {
-    double T[ORC_MAXK][10];
-    psi_d3(T);
+  if (q->deg >= 3)
     for (int j = 0; j < 10; j++) {
       double d = 0;
-      for (int k = 0; k < K; k++) d += q->a[k] * T[k][j] / (q->h * q->h * q->h);
+      for (int k = 0; k < K; k++) d += q->a[k] * mono_d(MONO[k], DER3[j], xi) / (q->h * q->h * q->h);
       q->s += w * q->w3 * d * d;
     }
-  }
+  if (q->deg == 4)
+    for (int j = 0; j < 15; j++) {
+      double d = 0;
+      for (int k = 0; k < K; k++) d += q->a[k] * mono_d(MONO[k], DER4[j], xi) / (q->h * q->h * q->h * q->h);
+      q->s += w * q->w4 * d * d;
+    }
 }
 static double smoothness(const orc_case *c, int64_t i, const double *a, int deg) {
   si_ctx q;
@@ -675,11 +705,12 @@ static double smoothness(const orc_case *c, int64_t i, const double *a, int deg)
   q.w1 = pow(c->vol[i], 2.0 / 3.0 - 1.0);  /* |beta| = 1 */
   q.w2 = pow(c->vol[i], 4.0 / 3.0 - 1.0);  /* |beta| = 2 */
   q.w3 = c->vol[i];                        /* |beta| = 3: V^(6/3 - 1) */
+  q.w4 = pow(c->vol[i], 8.0 / 3.0 - 1.0);  /* |beta| = 4 */
   q.a = a;
   q.deg = deg;
   q.s = 0;
-  /* (d p)^2 of a cubic is of degree 4: one more point per direction */
-  cell_quad(c, i, deg == 3 ? c->ngeo + 1 : c->ngeo, f_si, &q);
+  /* (d p)^2 of a cubic (quartic) is of degree 4 (6): one more point per direction */
+  cell_quad(c, i, deg >= 3 ? c->ngeo + 1 : c->ngeo, f_si, &q);
   return q.s;
 }
 
@@ -710,16 +741,16 @@ static void recon_from_values(const orc_case *c, int64_t i, const double Ui[5],
     lam[0] = c->lamc / lsum;
     for (int s = 1; s < st; s++) lam[s] = 1.0 / lsum;
     for (int s = 1; s < st; s++) {
-      const double *Pd = &c->Pd[(i * c->nd + (s - 1)) * 3 * c->Md];
+      const double *Pd = &c->Pd[(i * c->nd + (s - 1)) * c->Kd * c->Md];
       for (int k = 0; k < c->K; k++) as[s][k] = 0.0;
-      for (int k = 0; k < 3; k++) {
+      for (int k = 0; k < c->Kd; k++) {
         double t = 0;
         for (int r = 0; r < c->Md; r++) t += Pd[k * c->Md + r] * (Ud[((s - 1) * c->Md + r) * 5 + v] - Ui[v]);
         as[s][k] = t;
       }
     }
     SI[0] = smoothness(c, i, aopt, c->order);
-    for (int s = 1; s < st; s++) SI[s] = smoothness(c, i, as[s], 1);
+    for (int s = 1; s < st; s++) SI[s] = smoothness(c, i, as[s], c->Kd == 3 ? 1 : 2);
     /* central candidate p_1 = (p_opt - sum_{s>=2} lam_s p_s) / lam_1 */
     for (int k = 0; k < c->K; k++) {
       double t = aopt[k];
@@ -764,8 +795,8 @@ static void eval_poly(const orc_case *c, int64_t i, const double Ui[5], double c
                       const double x[3], double val[5], double grad[5][3]) {
   double xi[3], p[ORC_MAXK], g[ORC_MAXK][3];
   for (int d = 0; d < 3; d++) xi[d] = (x[d] - c->cen[3 * i + d]) / c->hh[i];
-  psi_eval(xi, p);
-  psi_grad(xi, g);
+  psi_eval(xi, p, c->K);
+  psi_grad(xi, g, c->K);
   const double *pb = &c->psib[ORC_MAXK * i];
   for (int v = 0; v < 5; v++) {
     double s = Ui[v];
@@ -1167,15 +1198,16 @@ orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int6
   c->Mach = params[5]; c->cfl = params[6]; c->lamc = params[7]; c->eps = params[8];
   c->alpha = params[9];
   c->rk = (int)params[10];
-  if (c->order < 1 || c->order > 3) { set_err("order must be 1, 2 or 3"); free(c); return NULL; }
-  if (c->order == 3 && npc != 8) { set_err("order 3 is built for hexahedra only"); free(c); return NULL; }
+  if (c->order < 1 || c->order > 4) { set_err("order must be 1, 2, 3 or 4"); free(c); return NULL; }
+  if (c->order >= 3 && npc != 8) { set_err("orders 3 and 4 are built for hexahedra only"); free(c); return NULL; }
   if (c->rk != 0 && c->rk != 1) { set_err("integrator must be 0 (SSP-RK3) or 1 (SSP(5,4))"); free(c); return NULL; }
-  c->K = c->order == 1 ? 3 : (c->order == 2 ? 9 : 19);
+  c->K = c->order == 1 ? 3 : (c->order == 2 ? 9 : (c->order == 3 ? 19 : 34));
   c->Mc = 2 * c->K;
   c->nd = (c->order >= 2 && c->scheme == 1) ? c->nfc : 0;  /* directional candidates: linear (P2, P3) */
-  c->Md = ORC_MD;
+  c->Kd = c->order == 4 ? 9 : 3;  /* quadratic directional candidates at P4 (Sec. 2.2) */
+  c->Md = 2 * c->Kd;
   c->nq = c->order * c->order;
-  c->ngeo = npc == 8 ? 3 : 4;
+  c->ngeo = npc == 8 ? (c->order == 4 ? 4 : 3) : 4;  /* exact for the A-matrix integrands */
   c->X = (double *)malloc(sizeof(double) * 3 * nn);
   memcpy(c->X, nodes, sizeof(double) * 3 * nn);
   c->C = (int64_t *)malloc(sizeof(int64_t) * npc * N);
@@ -1195,7 +1227,7 @@ orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int6
   if (c->nd) {
     c->sd = (int64_t *)malloc(sizeof(int64_t) * c->nd * c->Md * N);
     c->sdsh = (signed char *)malloc(3 * c->nd * c->Md * N);
-    c->Pd = (double *)malloc(sizeof(double) * c->nd * 3 * c->Md * N);
+    c->Pd = (double *)malloc(sizeof(double) * c->nd * c->Kd * c->Md * N);
   }
   c->ready = (unsigned char *)calloc(N, 1);
   compute_canon(c);
@@ -1249,10 +1281,10 @@ void orc_surface_sums(const orc_case *c, double *out /* [N][3] */) {
 /* stencil members and operators of one cell (which = -1 central, s >= 0 directional) */
 int orc_stencil(orc_case *c, int64_t i, int which, int64_t *mem, int32_t *sh, double *A, double *P) {
   if (ensure_cell(c, i)) return -1;
-  int M = which < 0 ? c->Mc : c->Md, K = which < 0 ? c->K : 3;
+  int M = which < 0 ? c->Mc : c->Md, K = which < 0 ? c->K : c->Kd;
   const int64_t *m = which < 0 ? &c->sc[i * c->Mc] : &c->sd[(i * c->nd + which) * c->Md];
   const signed char *s = which < 0 ? &c->scsh[i * c->Mc * 3] : &c->sdsh[(i * c->nd + which) * c->Md * 3];
-  const double *PP = which < 0 ? &c->Pc[i * c->K * c->Mc] : &c->Pd[(i * c->nd + which) * 3 * c->Md];
+  const double *PP = which < 0 ? &c->Pc[i * c->K * c->Mc] : &c->Pd[(i * c->nd + which) * c->Kd * c->Md];
   for (int r = 0; r < M; r++) {
     mem[r] = m[r];
     for (int d = 0; d < 3; d++) sh[3 * r + d] = s[3 * r + d];
@@ -1335,39 +1367,44 @@ static void poly_avg(const orc_case *c, int64_t m, const signed char *sh, const 
   for (int v = 0; v < 5; v++) out[v] = q.s[v] / q.v;
 }
 
-/* the same with a cubic in the physical coordinates: 20 terms per variable,
-   1, X, Y, Z, XX, YY, ZZ, XY, XZ, YZ, then XXX, YYY, ZZZ, XXY, XXZ, XYY, YYZ, XZZ, YZZ, XYZ */
-static void f_polyavg3(void *ctx, const double x[3], double w) {
-  pa_ctx *q = (pa_ctx *)ctx;
-  double X = x[0] + q->sh[0], Y = x[1] + q->sh[1], Z = x[2] + q->sh[2];
-  double m[20] = {1, X, Y, Z, X * X, Y * Y, Z * Z, X * Y, X * Z, Y * Z,
-                  X * X * X, Y * Y * Y, Z * Z * Z, X * X * Y, X * X * Z, X * Y * Y, Y * Y * Z, X * Z * Z, Y * Z * Z,
-                  X * Y * Z};
+/* the same with a polynomial of degree <= 4 in the physical coordinates:
+   nterm = 20 (cubic) or 35 (quartic) terms per variable, 1 then the basis
+   monomials in basis order (MONO) of (X, Y, Z) */
+typedef struct { const double *poly; int nterm; double sh[3], s[5], v; } pan_ctx;
+static void f_polyavgN(void *ctx, const double x[3], double w) {
+  pan_ctx *q = (pan_ctx *)ctx;
+  double X[3] = {x[0] + q->sh[0], x[1] + q->sh[1], x[2] + q->sh[2]}, m[ORC_MAXK + 1];
+  m[0] = 1.0;
+  for (int k = 0; k + 1 < q->nterm; k++) m[k + 1] = mono_d(MONO[k], ZERO3, X);
   for (int v = 0; v < 5; v++) {
     double t = 0;
-    for (int k = 0; k < 20; k++) t += q->poly[v * 20 + k] * m[k];
+    for (int k = 0; k < q->nterm; k++) t += q->poly[v * q->nterm + k] * m[k];
     q->s[v] += w * t;
   }
   q->v += w;
 }
-static void poly_avg3(const orc_case *c, int64_t m, const signed char *sh, const double *poly, double out[5]) {
-  pa_ctx q;
+static void poly_avgN(const orc_case *c, int64_t m, const signed char *sh, const double *poly, int nterm,
+                      double out[5]) {
+  pan_ctx q;
   memset(&q, 0, sizeof q);
   q.poly = poly;
+  q.nterm = nterm;
   for (int d = 0; d < 3; d++) q.sh[d] = sh ? sh[d] * c->L[d] : 0.0;
-  cell_quad(c, m, 5, f_polyavg3, &q);
+  cell_quad(c, m, 6, f_polyavgN, &q);
   for (int v = 0; v < 5; v++) out[v] = q.s[v] / q.v;
 }
-int orc_kexact_probe3(orc_case *c, int64_t i, const double *poly, int npts, const double *x,
+int orc_kexact_probeN(orc_case *c, int64_t i, const double *poly, int nterm, int npts, const double *x,
                       double *val, double *grad) {
+  if (nterm != 20 && nterm != 35) { set_err("nterm must be 20 or 35"); return -1; }
   if (ensure_cell(c, i)) return -1;
   double Ui[5], Uc[ORC_MAXM * 5], Ud[ORC_MAXD * ORC_MD * 5], cc[5][ORC_MAXK], g[5][3];
-  poly_avg3(c, i, NULL, poly, Ui);
-  for (int r = 0; r < c->Mc; r++) poly_avg3(c, c->sc[i * c->Mc + r], &c->scsh[(i * c->Mc + r) * 3], poly, &Uc[5 * r]);
+  poly_avgN(c, i, NULL, poly, nterm, Ui);
+  for (int r = 0; r < c->Mc; r++)
+    poly_avgN(c, c->sc[i * c->Mc + r], &c->scsh[(i * c->Mc + r) * 3], poly, nterm, &Uc[5 * r]);
   for (int s = 0; s < c->nd; s++)
     for (int r = 0; r < c->Md; r++) {
       int64_t k = (i * c->nd + s) * c->Md + r;
-      poly_avg3(c, c->sd[k], &c->sdsh[3 * k], poly, &Ud[(s * c->Md + r) * 5]);
+      poly_avgN(c, c->sd[k], &c->sdsh[3 * k], poly, nterm, &Ud[(s * c->Md + r) * 5]);
     }
   recon_from_values(c, i, Ui, Uc, Ud, cc, NULL);
   for (int p = 0; p < npts; p++) eval_poly(c, i, Ui, cc, &x[3 * p], &val[5 * p], g), memcpy(&grad[15 * p], g, sizeof g);

@@ -337,6 +337,85 @@ def test_order_density_wave_p3():
     assert all(r > 3.6 for r in rates), rates
 
 
+# ------------------------------------------------------------------ P4 ---
+# Quartic reconstruction on hexahedra (the TGV-P4 row of Table 4): K = 34
+# modes, central stencils of 68 cells, 6 quadratic directional candidates
+# (Sec. 2.2) of 18 cells each, 4 x 4 Gauss points per face.
+_QUARTIC_EXP = [(4, 0, 0), (0, 4, 0), (0, 0, 4), (3, 1, 0), (3, 0, 1), (1, 3, 0), (0, 3, 1), (1, 0, 3), (0, 1, 3),
+                (2, 2, 0), (2, 0, 2), (0, 2, 2), (2, 1, 1), (1, 2, 1), (1, 1, 2)]
+
+
+def _quartic_monomials(x):
+    X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+    return np.concatenate([_cubic_monomials(x), np.stack([X ** a * Y ** b * Z ** c for a, b, c in _QUARTIC_EXP], 1)],
+                          axis=1)
+
+
+def test_counts_p4_match_benchmark_matrix():
+    """Table 4 (TGV-P4): 176M/2M = 88 reconstructed DoF per cell and
+    variable (34 quartic central + 6 quadratic directional x 9), 96M/6M = 16
+    quadrature points per face; K(4, 3) = 35 terms with the mean -> 34."""
+    cells_, faces, dof, qps = _golden("benchmark_matrix.txt")["TGV-P4"]
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=3)
+    c = O.Case(nodes, cells, box, O.Params(order=4, scheme=1))
+    assert c.K == math.comb(4 + 3, 3) - 1 == 34
+    assert c.K + c.nd * (c.Md // 2) == round(dof / cells_)
+    assert c.nq == round(qps / faces) == 16
+    assert c.Mc == 68 and c.nd == 6 and c.Md == 18
+
+
+@pytest.mark.parametrize("scheme,degree", [(0, 4), (1, 2)])
+def test_k_exact_p4(scheme, degree):
+    """Cell averages of a random polynomial: the central quartic
+    reconstruction reproduces degree <= 4 (values), and CWENOZ at P4, whose
+    directional candidates are quadratic, reproduces degree <= 2."""
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=5)
+    c = O.Case(nodes, cells, box, O.Params(order=4, scheme=scheme))
+    rng = np.random.default_rng(degree + 10)
+    poly = rng.normal(size=(5, 35)) * 0.05
+    if degree == 2:
+        poly[:, 10:] = 0.0
+    for i in (0, 333, 999):
+        x = I.cell_vertex_means(nodes, cells)[i:i + 1] + rng.uniform(-0.3, 0.3, size=(4, 3))
+        val, _ = c.kexact_probe(i, poly, x)
+        ref = _quartic_monomials(x) @ poly.T
+        assert np.abs(val - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), (i, np.abs(val - ref).max())
+
+
+def test_smoothness_indicator_quartic_closed_form():
+    """The |beta| = 4 term (weight V^(5/3)): on a cube, p = xi^4 gives
+    int (4 xi^3)^2 + int (12 xi^2)^2 + int (24 xi)^2 + 24^2 = 16/448 + 144/80
+    + 576/12 + 576."""
+    nodes, cells, box = I.hex_lattice(10)
+    c = O.Case(nodes, cells, box, O.Params(order=4, scheme=1))
+    a = np.zeros(34); a[19] = 1.0
+    assert math.isclose(c.smoothness(5, a, 4), 16 / 448 + 144 / 80 + 576 / 12 + 576, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_free_stream_and_conservation_p4(scheme):
+    nodes, cells, box = I.hex_lattice(10, jitter=0.1, seed=4)
+    c = O.Case(nodes, cells, box, O.Params(order=4, scheme=scheme))
+    n = len(cells)
+    U = I.primitive_to_conserved(np.ones(n), 0.3 * np.ones(n), -0.2 * np.ones(n), 0.1 * np.ones(n),
+                                 np.ones(n) / (1.4 * 0.01))
+    R, S = c.residual_terms(U)
+    assert np.abs(R).max() <= 1e-12 * S.max()
+    U = I.noisy_state(nodes, cells, 0.1, 0.05, seed=2)
+    R, S = c.residual_terms(U)
+    vol, _, _ = c.geometry()
+    assert np.all(np.abs((R * vol).sum(axis=1)) <= 1e-12 * (S * vol).sum(axis=1))
+
+
+def test_order_density_wave_p4():
+    """P4 linear reconstruction with SSP(5,4) on the density wave: the L1
+    error falls at rates near 5 (n = 8, 12, 16; the time error is negligible
+    there: a 4x smaller dt changes the error by < 1e-6 relative)."""
+    e = [_density_wave_error(n, 4, 0, integrator=1) for n in (8, 12, 16)]
+    rates = [math.log(e[0] / e[1]) / math.log(12 / 8), math.log(e[1] / e[2]) / math.log(16 / 12)]
+    assert all(r > 4.4 for r in rates), rates
+
+
 # ------------------------------------------------------------ invariants ---
 @pytest.mark.parametrize("kind", ["hex", "tet"])
 def test_free_stream_preservation(kind, jhex8_p2, jtet_p2):

@@ -5,6 +5,8 @@
  * (Sec. 2.2: Eq. 1 conservation law, Eq. 2 semi-discretisation, Eqs. 3-4
  * k-exact least-squares reconstruction, Eqs. 5-6 CWENOZ, Eq. 7 viscous
  * interface gradient, HLLC inviscid flux, Eq. 8 explicit SSP Runge-Kutta).
+ * Reconstruction degrees P1 and P2 on hexahedra and tetrahedra, P3 and P4
+ * (quadratic directional candidates) on hexahedra.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark load this library; the product path

@@ -68,6 +68,8 @@ typedef struct {
   signed char *sdsh; /* [N][nd][Md][3] */
   double *Pd;        /* [N][nd][3][Md] */
   unsigned char *ready;
+  unsigned char *dvalid;  /* [N][nd]: directional candidate s exists (no wall on face s) */
+  int walls;              /* some box axis is not periodic: its unpaired faces are slip walls */
   /* quadrature on [0,1] */
   int ngeo;
   double gx[8], gw[8];
@@ -396,25 +398,36 @@ static int build_faces(orc_case *c) {
       f->lf = lf;
     }
   qsort(a, nk, sizeof(fkey), cmp_fkey);
-  if (nk % 2) { free(a); set_err("unpaired face"); return -1; }
-  c->F = nk / 2;
+  if (nk % 2 && !c->walls) { free(a); set_err("unpaired face"); return -1; }
+  /* pairs sorted by key; faces then ordered by (owner, local face).  With a
+     non-periodic box axis, a face whose key occurs once lies on the box
+     boundary: a slip wall, neighbour -1 */
+  typedef struct { int64_t o, n; int lf, nlf; } pr;
+  pr *p = (pr *)malloc(sizeof(pr) * nk);
+  int64_t F = 0;
+  for (int64_t j = 0; j < nk;) {
+    fkey *x = &a[j];
+    if (j + 1 < nk && memcmp(x->k, a[j + 1].k, sizeof x->k) == 0) {
+      fkey *y = &a[j + 1];
+      if (j + 2 < nk && memcmp(y->k, a[j + 2].k, sizeof y->k) == 0) {
+        free(a); free(p); set_err("unpaired or non-manifold face"); return -1;
+      }
+      if (x->cell == y->cell) { free(a); free(p); set_err("cell is its own neighbour"); return -1; }
+      p[F].o = x->cell; p[F].lf = x->lf; p[F].n = y->cell; p[F].nlf = y->lf;
+      j += 2;
+    } else {
+      if (!c->walls) { free(a); free(p); set_err("unpaired or non-manifold face"); return -1; }
+      p[F].o = x->cell; p[F].lf = x->lf; p[F].n = -1; p[F].nlf = -1;
+      j += 1;
+    }
+    F++;
+  }
+  free(a);
+  c->F = F;
   c->fo = (int64_t *)malloc(sizeof(int64_t) * c->F);
   c->fn = (int64_t *)malloc(sizeof(int64_t) * c->F);
   c->flf = (int *)malloc(sizeof(int) * c->F);
   c->fsh = (signed char *)malloc(3 * c->F);
-  /* pairs sorted by key; faces then ordered by (owner, local face) */
-  typedef struct { int64_t o, n; int lf, nlf; } pr;
-  pr *p = (pr *)malloc(sizeof(pr) * c->F);
-  for (int64_t f = 0; f < c->F; f++) {
-    fkey *x = &a[2 * f], *y = &a[2 * f + 1];
-    if (memcmp(x->k, y->k, sizeof x->k) != 0 ||
-        (2 * f + 2 < nk && memcmp(y->k, a[2 * f + 2].k, sizeof y->k) == 0)) {
-      free(a); free(p); set_err("unpaired or non-manifold face"); return -1;
-    }
-    if (x->cell == y->cell) { free(a); free(p); set_err("cell is its own neighbour"); return -1; }
-    p[f].o = x->cell; p[f].lf = x->lf; p[f].n = y->cell; p[f].nlf = y->lf;
-  }
-  free(a);
   /* order by owner then owner-local face: counting sort on owner */
   int64_t *cnt = (int64_t *)calloc(c->N * c->nfc, sizeof(int64_t));
   for (int64_t f = 0; f < c->F; f++) cnt[p[f].o * c->nfc + p[f].lf] = f + 1;
@@ -424,8 +437,12 @@ static int build_faces(orc_case *c) {
       pr *q = &p[cnt[s] - 1];
       c->fo[k] = q->o; c->fn[k] = q->n; c->flf[k] = q->lf;
       c->cf[q->o * c->nfc + q->lf] = k; c->cs[q->o * c->nfc + q->lf] = 1;
-      c->cf[q->n * c->nfc + q->nlf] = k; c->cs[q->n * c->nfc + q->nlf] = -1;
-      image_shift(c, q->o, q->n, &c->fsh[3 * k]);
+      if (q->n >= 0) {
+        c->cf[q->n * c->nfc + q->nlf] = k; c->cs[q->n * c->nfc + q->nlf] = -1;
+        image_shift(c, q->o, q->n, &c->fsh[3 * k]);
+      } else {
+        for (int d = 0; d < 3; d++) c->fsh[3 * k + d] = 0;
+      }
       k++;
     }
   free(cnt);
@@ -536,7 +553,7 @@ static int bfs(const orc_case *c, int64_t start, int64_t avoid, int maxd, cand *
     if (cur.depth == maxd) continue;
     for (int lf = 0; lf < c->nfc; lf++) {
       int64_t m = face_nbr(c, cur.id, lf);
-      if (m == avoid) continue;
+      if (m < 0 || m == avoid) continue;  /* a wall, or the cell a directional search avoids */
       int seen = 0;
       for (int q = 0; q < n; q++)
         if (out[q].id == m) { seen = 1; break; }
@@ -638,6 +655,8 @@ static int ensure_cell(orc_case *c, int64_t i) {
   if (lsq_pinv(A, c->Mc, c->K, Vm, &c->Pc[i * c->K * c->Mc])) return -1;
   for (int s = 0; s < c->nd; s++) {
     int64_t nf = face_nbr(c, i, s);
+    c->dvalid[i * c->nd + s] = nf >= 0;
+    if (nf < 0) continue;  /* a wall face: no directional candidate there */
     int m = bfs(c, nf, i, c->Kd == 3 ? 2 : 3, buf, 256);
     if (m < 0) { set_err("stencil search overflow"); return -1; }
     qsort(buf + 1, m - 1, sizeof(cand), cmp_dir);
@@ -739,10 +758,16 @@ static void recon_from_values(const orc_case *c, int64_t i, const double Ui[5],
     /* CWENOZ: s = 0 central (p_opt defines SI_1), s = 1..nd directional */
     int st = c->nd + 1;
     double as[ORC_MAXD + 1][ORC_MAXK], lam[ORC_MAXD + 1], SI[ORC_MAXD + 1], wt[ORC_MAXD + 1];
-    double lsum = c->lamc + c->nd * 1.0;
+    /* candidates: the central one and the directional ones that exist (a
+       wall face has none); linear weights normalised over those */
+    const unsigned char *dv = &c->dvalid[i * c->nd];
+    int nv = 0;
+    for (int s = 1; s < st; s++) nv += dv[s - 1];
+    double lsum = c->lamc + nv * 1.0;
     lam[0] = c->lamc / lsum;
-    for (int s = 1; s < st; s++) lam[s] = 1.0 / lsum;
+    for (int s = 1; s < st; s++) lam[s] = dv[s - 1] ? 1.0 / lsum : 0.0;
     for (int s = 1; s < st; s++) {
+      if (!dv[s - 1]) continue;
       const double *Pd = &c->Pd[(i * c->nd + (s - 1)) * c->Kd * c->Md];
       for (int k = 0; k < c->K; k++) as[s][k] = 0.0;
       for (int k = 0; k < c->Kd; k++) {
@@ -752,25 +777,28 @@ static void recon_from_values(const orc_case *c, int64_t i, const double Ui[5],
       }
     }
     SI[0] = smoothness(c, i, aopt, c->order);
-    for (int s = 1; s < st; s++) SI[s] = smoothness(c, i, as[s], c->Kd == 3 ? 1 : 2);
+    for (int s = 1; s < st; s++) SI[s] = dv[s - 1] ? smoothness(c, i, as[s], c->Kd == 3 ? 1 : 2) : 0.0;
     /* central candidate p_1 = (p_opt - sum_{s>=2} lam_s p_s) / lam_1 */
     for (int k = 0; k < c->K; k++) {
       double t = aopt[k];
-      for (int s = 1; s < st; s++) t -= lam[s] * as[s][k];
+      for (int s = 1; s < st; s++)
+        if (dv[s - 1]) t -= lam[s] * as[s][k];
       as[0][k] = t / lam[0];
     }
     double tau = 0;
-    for (int s = 1; s < st; s++) tau += fabs(SI[0] - SI[s]);
-    tau /= (double)(st - 1);
+    for (int s = 1; s < st; s++)
+      if (dv[s - 1]) tau += fabs(SI[0] - SI[s]);
+    tau /= (double)nv;
     double wsum = 0;
     for (int s = 0; s < st; s++) {
-      wt[s] = lam[s] * (1.0 + tau / (c->eps + SI[s]));
+      wt[s] = (s == 0 || dv[s - 1]) ? lam[s] * (1.0 + tau / (c->eps + SI[s])) : 0.0;
       wsum += wt[s];
     }
     for (int s = 0; s < st; s++) wt[s] /= wsum;
     for (int k = 0; k < c->K; k++) {
       double t = 0;
-      for (int s = 0; s < st; s++) t += wt[s] * as[s][k];
+      for (int s = 0; s < st; s++)
+        if (s == 0 || dv[s - 1]) t += wt[s] * as[s][k];
       coef[v][k] = t;
     }
     if (wout)
@@ -786,9 +814,10 @@ static void recon_cell(const orc_case *c, int64_t i, const double *U, double coe
   for (int r = 0; r < c->Mc; r++)
     for (int v = 0; v < 5; v++) Uc[r * 5 + v] = U[v * N + c->sc[i * c->Mc + r]];
   for (int s = 0; s < c->nd; s++)
-    for (int r = 0; r < c->Md; r++)
-      for (int v = 0; v < 5; v++)
-        Ud[(s * c->Md + r) * 5 + v] = U[v * N + c->sd[(i * c->nd + s) * c->Md + r]];
+    if (c->dvalid[i * c->nd + s])
+      for (int r = 0; r < c->Md; r++)
+        for (int v = 0; v < 5; v++)
+          Ud[(s * c->Md + r) * 5 + v] = U[v * N + c->sd[(i * c->nd + s) * c->Md + r]];
   recon_from_values(c, i, Ui, Uc, Ud, coef, wout);
 }
 
@@ -909,6 +938,26 @@ static void face_flux(const orc_case *c, int64_t f, const double *U, const doubl
   int64_t N = c->N, o = c->fo[f], nb = c->fn[f];
   double x[32][3], dS[32][3], Uo[5], Un[5], shv[3];
   for (int v = 0; v < 5; v++) g[v] = 0.0;
+  if (nb < 0) {
+    /* slip wall: the ghost state mirrors the owner's reconstructed state in
+       the wall (same density and energy, normal momentum reversed); HLLC
+       between the two (inviscid flows only) */
+    for (int v = 0; v < 5; v++) Uo[v] = U[v * N + o];
+    face_quad(c, f, x, dS);
+    for (int q = 0; q < c->nq; q++) {
+      double UL[5], UR[5], gL[5][3], nh[3], A, Fc[5];
+      eval_poly(c, o, Uo, (double(*)[ORC_MAXK]) & coef[o * 5 * ORC_MAXK], x[q], UL, gL);
+      A = sqrt(dS[q][0] * dS[q][0] + dS[q][1] * dS[q][1] + dS[q][2] * dS[q][2]);
+      for (int d = 0; d < 3; d++) nh[d] = dS[q][d] / A;
+      double mn = UL[1] * nh[0] + UL[2] * nh[1] + UL[3] * nh[2];
+      UR[0] = UL[0];
+      for (int d = 0; d < 3; d++) UR[1 + d] = UL[1 + d] - 2.0 * mn * nh[d];
+      UR[4] = UL[4];
+      orc_hllc(UL, UR, nh, c->gam, Fc);
+      for (int v = 0; v < 5; v++) g[v] += Fc[v] * A;
+    }
+    return;
+  }
   for (int d = 0; d < 3; d++) shv[d] = c->fsh[3 * f + d] * c->L[d];
   for (int v = 0; v < 5; v++) { Uo[v] = U[v * N + o]; Un[v] = U[v * N + nb]; }
   face_quad(c, f, x, dS);
@@ -986,7 +1035,10 @@ int orc_residual_subset_terms(orc_case *c, const double *U, int64_t ns, const in
   for (int64_t k = 0; k < ns; k++) {
     if (sel[k] < 0 || sel[k] >= N) { free(need); set_err("cell id out of range"); return -1; }
     need[sel[k]] = 1;
-    for (int j = 0; j < c->nfc; j++) need[face_nbr(c, sel[k], j)] = 1;
+    for (int j = 0; j < c->nfc; j++) {
+      int64_t m = face_nbr(c, sel[k], j);
+      if (m >= 0) need[m] = 1;
+    }
   }
   int64_t nl = 0;
   int64_t *list = (int64_t *)malloc(sizeof(int64_t) * N);
@@ -1232,6 +1284,9 @@ orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int6
     c->Pd = (double *)malloc(sizeof(double) * c->nd * c->Kd * c->Md * N);
   }
   c->ready = (unsigned char *)calloc(N, 1);
+  c->dvalid = (unsigned char *)calloc(c->nd > 0 ? c->nd * N : 1, 1);
+  c->walls = !(c->per[0] && c->per[1] && c->per[2]);
+  if (c->walls && !c->inviscid) { set_err("slip walls are built for inviscid flows (Re <= 0) only"); orc_destroy(c); return NULL; }
   compute_canon(c);
   if (compute_geometry(c) || build_faces(c)) { orc_destroy(c); return NULL; }
   return c;
@@ -1241,7 +1296,7 @@ void orc_destroy(orc_case *c) {
   if (!c) return;
   free(c->X); free(c->C); free(c->canon); free(c->vol); free(c->cen); free(c->hh); free(c->psib);
   free(c->fo); free(c->fn); free(c->flf); free(c->fsh); free(c->cf); free(c->cs);
-  free(c->sc); free(c->scsh); free(c->Pc); free(c->sd); free(c->sdsh); free(c->Pd); free(c->ready);
+  free(c->sc); free(c->scsh); free(c->Pc); free(c->sd); free(c->sdsh); free(c->Pd); free(c->ready); free(c->dvalid);
   free(c);
 }
 
@@ -1275,7 +1330,7 @@ void orc_surface_sums(const orc_case *c, double *out /* [N][3] */) {
     for (int q = 0; q < c->nq; q++)
       for (int d = 0; d < 3; d++) {
         out[3 * c->fo[f] + d] += dS[q][d];
-        out[3 * c->fn[f] + d] -= dS[q][d];
+        if (c->fn[f] >= 0) out[3 * c->fn[f] + d] -= dS[q][d];
       }
   }
 }
@@ -1283,6 +1338,7 @@ void orc_surface_sums(const orc_case *c, double *out /* [N][3] */) {
 /* stencil members and operators of one cell (which = -1 central, s >= 0 directional) */
 int orc_stencil(orc_case *c, int64_t i, int which, int64_t *mem, int32_t *sh, double *A, double *P) {
   if (ensure_cell(c, i)) return -1;
+  if (which >= 0 && !c->dvalid[i * c->nd + which]) { set_err("no directional candidate on a wall face"); return -1; }
   int M = which < 0 ? c->Mc : c->Md, K = which < 0 ? c->K : c->Kd;
   const int64_t *m = which < 0 ? &c->sc[i * c->Mc] : &c->sd[(i * c->nd + which) * c->Md];
   const signed char *s = which < 0 ? &c->scsh[i * c->Mc * 3] : &c->sdsh[(i * c->nd + which) * c->Md * 3];
@@ -1404,7 +1460,7 @@ int orc_kexact_probeN(orc_case *c, int64_t i, const double *poly, int nterm, int
   for (int r = 0; r < c->Mc; r++)
     poly_avgN(c, c->sc[i * c->Mc + r], &c->scsh[(i * c->Mc + r) * 3], poly, nterm, &Uc[5 * r]);
   for (int s = 0; s < c->nd; s++)
-    for (int r = 0; r < c->Md; r++) {
+    for (int r = 0; r < c->Md && c->dvalid[i * c->nd + s]; r++) {
       int64_t k = (i * c->nd + s) * c->Md + r;
       poly_avgN(c, c->sd[k], &c->sdsh[3 * k], poly, nterm, &Ud[(s * c->Md + r) * 5]);
     }
@@ -1422,7 +1478,7 @@ int orc_kexact_probe(orc_case *c, int64_t i, const double *poly, int npts, const
   poly_avg(c, i, NULL, poly, Ui);
   for (int r = 0; r < c->Mc; r++) poly_avg(c, c->sc[i * c->Mc + r], &c->scsh[(i * c->Mc + r) * 3], poly, &Uc[5 * r]);
   for (int s = 0; s < c->nd; s++)
-    for (int r = 0; r < c->Md; r++) {
+    for (int r = 0; r < c->Md && c->dvalid[i * c->nd + s]; r++) {
       int64_t k = (i * c->nd + s) * c->Md + r;
       poly_avg(c, c->sd[k], &c->sdsh[3 * k], poly, &Ud[(s * c->Md + r) * 5]);
     }

@@ -416,6 +416,96 @@ def test_order_density_wave_p4():
     assert all(r > 4.4 for r in rates), rates
 
 
+# ------------------------------------------------------- slip walls ---
+# Boundary treatment beyond the periodic wrap: a box axis given length 0 is
+# not periodic, and the faces on its two planes are slip walls (inviscid):
+# the ghost state mirrors the owner's reconstructed state (normal momentum
+# reversed), and a wall face has no directional candidate.
+def _walled(n=8, order=2, scheme=1, jitter=0.1):
+    nodes, cells, box = I.hex_lattice(n, jitter=jitter, seed=3)
+    c = O.Case(nodes, cells, np.array([box[0], box[1], 0.0]), O.Params(order=order, scheme=scheme, Re=0.0))
+    return nodes, cells, c
+
+
+def test_wall_flux_of_the_mirror_state():
+    """HLLC between a state and its mirror image in a wall of normal n: no
+    mass, tangential-momentum or energy flux; the normal momentum flux is the
+    star pressure, at least the state's own pressure when it moves into the
+    wall and at most that when it moves away."""
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        n = rng.normal(size=3); n /= np.linalg.norm(n)
+        rho, p = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+        u = rng.normal(size=3)
+        UL = np.array([rho, *(rho * u), p / 0.4 + 0.5 * rho * u @ u])
+        mn = UL[1:4] @ n
+        UR = UL.copy(); UR[1:4] = UL[1:4] - 2 * mn * n
+        F = O.hllc(UL, UR, n)
+        scale = abs(F[1:4] @ n) + p
+        assert abs(F[0]) <= 1e-14 * scale * 10 and abs(F[4]) <= 1e-13 * scale * 10
+        Ft = F[1:4] - (F[1:4] @ n) * n
+        assert np.abs(Ft).max() <= 1e-13 * scale
+        if mn > 0:  # moving into the wall: compression, p* >= p
+            assert F[1:4] @ n >= p * (1 - 1e-12)
+        else:  # moving away: an expansion, p* <= p (it may even be negative for a strong one)
+            assert F[1:4] @ n <= p * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("order,scheme", [(1, 0), (2, 0), (2, 1), (3, 1), (4, 1)])
+def test_walls_free_stream_and_conservation(order, scheme):
+    """Walls on z = 0 and z = L, periodic in x and y: a uniform flow parallel
+    to the walls gives a zero residual; for any state, mass, x- and
+    y-momentum and energy are conserved to round-off (the walls exert only a
+    normal force), and the face count is the periodic one minus the wrapped
+    z faces plus the wall faces."""
+    nodes, cells, c = _walled(order=order, scheme=scheme)
+    n = len(cells)
+    assert c.n_faces == 3 * n - 64 + 2 * 64
+    U = I.primitive_to_conserved(np.ones(n), 0.3 * np.ones(n), -0.2 * np.ones(n), np.zeros(n), np.ones(n) / 0.014)
+    R, S = c.residual_terms(U)
+    assert np.abs(R).max() <= 1e-12 * S.max()
+    U = I.noisy_state(nodes, cells, 0.1, 0.05, seed=2)
+    R, S = c.residual_terms(U)
+    vol, _, _ = c.geometry()
+    tot = np.abs((R * vol).sum(axis=1)) / (S * vol).sum(axis=1)
+    assert np.all(tot[[0, 1, 2, 4]] <= 1e-12), tot
+    assert tot[3] > 1e-8  # the wall pressure changes the normal momentum
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_walls_k_exact_and_candidate_weights(order):
+    """Cells on the walls have one-sided stencils and still reproduce
+    polynomials of their degree; their wall faces carry no directional
+    candidate (weight 0), and the remaining CWENOZ weights sum to 1."""
+    nodes, cells, c = _walled(order=order, scheme=0)
+    rng = np.random.default_rng(order)
+    nt = 10 if order == 2 else 20
+    poly = rng.normal(size=(5, nt)) * 0.2
+    xm = I.cell_vertex_means(nodes, cells)
+    bottom, top = 3, len(cells) - 5  # cells touching z = 0 and z = L
+    for i in (bottom, top):
+        x = xm[i:i + 1] + rng.uniform(-0.3, 0.3, size=(4, 3))
+        val, _ = c.kexact_probe(i, poly, x)
+        ref = (_cubic_monomials(x)[:, :nt]) @ poly.T
+        assert np.abs(val - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), i
+    _, _, cw = _walled(order=order, scheme=1)
+    U = I.noisy_state(nodes, cells, 0.1, 0.05, seed=1)
+    _, w = cw.reconstruct(U, weights=True)
+    assert np.allclose(w.sum(axis=2), 1.0, atol=1e-14)
+    fo, fn, _ = cw.faces()
+    walls = fn < 0
+    assert walls.sum() == 128
+    # a bottom cell: exactly one of its six candidate slots is a wall face, weight 0
+    zeros = (w[bottom] == 0.0).all(axis=0)
+    assert zeros[1:].sum() == 1 and not zeros[0]
+
+
+def test_walls_need_an_inviscid_flow():
+    nodes, cells, box = I.hex_lattice(6)
+    with pytest.raises(O.OracleError):
+        O.Case(nodes, cells, np.array([box[0], box[1], 0.0]), O.Params(order=1, scheme=0, Re=1600.0))
+
+
 # ------------------------------------------------------------ invariants ---
 @pytest.mark.parametrize("kind", ["hex", "tet"])
 def test_free_stream_preservation(kind, jhex8_p2, jtet_p2):

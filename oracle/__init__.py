@@ -109,10 +109,16 @@ class Params:
     eps: float = 1e-6
     alpha: float = 4.0 / 3.0
     integrator: int = 0      # 0 SSP-RK3, 1 SSP(5,4)
+    # boundary kind of each box side x-, x+, y-, y+, z-, z+ of a non-periodic
+    # axis (box length 0): 0 or 1 slip wall, 2 supersonic outflow, 3 supersonic
+    # inflow of the conserved state `inflow`
+    bc: tuple = (0, 0, 0, 0, 0, 0)
+    inflow: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)
 
     def array(self) -> np.ndarray:
         return np.array([self.order, self.scheme, self.gamma, self.Pr, self.Re, self.Mach, self.cfl,
-                         self.lam_central, self.eps, self.alpha, self.integrator], dtype=np.float64)
+                         self.lam_central, self.eps, self.alpha, self.integrator, *self.bc, *self.inflow],
+                        dtype=np.float64)
 
 
 class OracleError(RuntimeError):

@@ -48,6 +48,9 @@ typedef struct {
   /* parameters */
   int order, scheme, inviscid;
   int rk;  /* 0: SSP-RK3, 1: SSP(5,4) */
+  int bc[6];         /* per box side x-, x+, y-, y+, z-, z+ of a non-periodic axis:
+                        0 or 1 slip wall, 2 supersonic outflow, 3 supersonic inflow */
+  double uinf[5];    /* conserved inflow state */
   double gam, Pr, Re, Mach, cfl, lamc, eps, alpha;
   int K, nq, Mc, nd, Md;
   int Kd;  /* modes of a directional candidate: 3 (linear, P2 and P3) or 9 (quadratic, P4) */
@@ -934,25 +937,46 @@ void orc_viscous_flux(const double Uf[5], const double gU[15], const double n[3]
 /* then R_i = -(1/|V_i|) sum_f sigma_if G_f.                                 */
 /* ------------------------------------------------------------------------ */
 /* flux integral G_f of face f (owner-outward), from the reconstructions */
+/* the box side of a boundary face from its outward area vector (the axis of
+   its largest component and that component's sign), and that side's kind */
+static int boundary_kind(const orc_case *c, double dS[][3]) {
+  double s[3] = {0, 0, 0};
+  for (int q = 0; q < c->nq; q++)
+    for (int d = 0; d < 3; d++) s[d] += dS[q][d];
+  int ax = 0;
+  for (int d = 1; d < 3; d++)
+    if (fabs(s[d]) > fabs(s[ax])) ax = d;
+  return c->bc[2 * ax + (s[ax] > 0 ? 1 : 0)];
+}
+
 static void face_flux(const orc_case *c, int64_t f, const double *U, const double *coef, double g[5]) {
   int64_t N = c->N, o = c->fo[f], nb = c->fn[f];
   double x[32][3], dS[32][3], Uo[5], Un[5], shv[3];
   for (int v = 0; v < 5; v++) g[v] = 0.0;
   if (nb < 0) {
-    /* slip wall: the ghost state mirrors the owner's reconstructed state in
-       the wall (same density and energy, normal momentum reversed); HLLC
-       between the two (inviscid flows only) */
+    /* a boundary face: the ghost state at each Gauss point is, by the kind of
+       its box side, the mirror of the owner's reconstructed state (slip wall:
+       same density and energy, normal momentum reversed), that state itself
+       (supersonic outflow: extrapolation), or the given inflow state
+       (supersonic inflow); HLLC between the two (inviscid flows only) */
     for (int v = 0; v < 5; v++) Uo[v] = U[v * N + o];
     face_quad(c, f, x, dS);
+    const int kind = boundary_kind(c, dS);
     for (int q = 0; q < c->nq; q++) {
       double UL[5], UR[5], gL[5][3], nh[3], A, Fc[5];
       eval_poly(c, o, Uo, (double(*)[ORC_MAXK]) & coef[o * 5 * ORC_MAXK], x[q], UL, gL);
       A = sqrt(dS[q][0] * dS[q][0] + dS[q][1] * dS[q][1] + dS[q][2] * dS[q][2]);
       for (int d = 0; d < 3; d++) nh[d] = dS[q][d] / A;
-      double mn = UL[1] * nh[0] + UL[2] * nh[1] + UL[3] * nh[2];
-      UR[0] = UL[0];
-      for (int d = 0; d < 3; d++) UR[1 + d] = UL[1 + d] - 2.0 * mn * nh[d];
-      UR[4] = UL[4];
+      if (kind == 2) {
+        for (int v = 0; v < 5; v++) UR[v] = UL[v];
+      } else if (kind == 3) {
+        for (int v = 0; v < 5; v++) UR[v] = c->uinf[v];
+      } else {
+        double mn = UL[1] * nh[0] + UL[2] * nh[1] + UL[3] * nh[2];
+        UR[0] = UL[0];
+        for (int d = 0; d < 3; d++) UR[1 + d] = UL[1 + d] - 2.0 * mn * nh[d];
+        UR[4] = UL[4];
+      }
       orc_hllc(UL, UR, nh, c->gam, Fc);
       for (int v = 0; v < 5; v++) g[v] += Fc[v] * A;
     }
@@ -1252,6 +1276,8 @@ orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int6
   c->Mach = params[5]; c->cfl = params[6]; c->lamc = params[7]; c->eps = params[8];
   c->alpha = params[9];
   c->rk = (int)params[10];
+  for (int k = 0; k < 6; k++) c->bc[k] = (int)params[11 + k];
+  for (int v = 0; v < 5; v++) c->uinf[v] = params[17 + v];
   if (c->order < 1 || c->order > 4) { set_err("order must be 1, 2, 3 or 4"); free(c); return NULL; }
   if (c->order >= 3 && npc != 8) { set_err("orders 3 and 4 are built for hexahedra only"); free(c); return NULL; }
   if (c->rk != 0 && c->rk != 1) { set_err("integrator must be 0 (SSP-RK3) or 1 (SSP(5,4))"); free(c); return NULL; }

@@ -500,6 +500,32 @@ def test_walls_k_exact_and_candidate_weights(order):
     assert zeros[1:].sum() == 1 and not zeros[0]
 
 
+@pytest.mark.parametrize("order,scheme", [(1, 0), (2, 1), (3, 1)])
+def test_supersonic_inflow_outflow(order, scheme):
+    """x not periodic, inflow of a Mach-2 uniform state at x = 0 and
+    extrapolation outflow at x = L (y, z periodic): that state is steady
+    (zero residual); an inflow state different from the interior changes
+    only the cells whose stencils reach the inflow faces (one-sided
+    neighbourhood of x = 0), not those near the outflow."""
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=6)
+    n = len(cells)
+    rho, p, u = 1.4, 1.0, 2.0  # sound speed 1
+    Uinf = (rho, rho * u, 0.0, 0.0, p / 0.4 + 0.5 * rho * u * u)
+    prm = O.Params(order=order, scheme=scheme, Re=0.0, bc=(3, 2, 0, 0, 0, 0), inflow=Uinf)
+    c = O.Case(nodes, cells, np.array([0.0, box[1], box[2]]), prm)
+    U = np.tile(np.array(Uinf)[:, None], (1, n))
+    R, S = c.residual_terms(U)
+    assert np.abs(R).max() <= 1e-12 * S.max()
+    prm2 = O.Params(order=order, scheme=scheme, Re=0.0, bc=(3, 2, 0, 0, 0, 0),
+                    inflow=(1.1 * rho, 1.1 * rho * u, 0.0, 0.0, 1.1 * Uinf[4]))
+    c2 = O.Case(nodes, cells, np.array([0.0, box[1], box[2]]), prm2)
+    R2, _ = c2.residual_terms(U)
+    x = I.cell_vertex_means(nodes, cells)[:, 0]
+    h = 2 * math.pi / 8
+    assert np.abs(R2[:, x < h]).max() > 1e-3 * S.max()      # the inflow cells feel it
+    assert np.abs(R2[:, x > 5 * h]).max() <= 1e-12 * S.max()  # downstream, beyond the stencils: unchanged
+
+
 def test_walls_need_an_inviscid_flow():
     nodes, cells, box = I.hex_lattice(6)
     with pytest.raises(O.OracleError):

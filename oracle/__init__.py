@@ -42,7 +42,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = C.CDLL(build())
+            # UCNS_ORACLE_LIB: a library compiled from a modified copy of the
+            # source (the mutation tests check that the pins reject it)
+            lib = C.CDLL(os.environ.get("UCNS_ORACLE_LIB") or build())
             P, I64, D = C.c_void_p, C.c_int64, C.c_double
             lib.orc_create.restype = P
             lib.orc_create.argtypes = [P, I64, P, I64, C.c_int, P, P]

@@ -1,0 +1,64 @@
+"""The oracle's pins are strong enough to reject plausible mistakes (CPU):
+each case copies the oracle's source, plants one error of the kind a
+transcription makes (a dropped term, a wrong sign, a swapped or mistyped
+coefficient, a wrong factor), compiles that copy with gcc, and runs the pins
+that should catch it against it (in a child process, through the oracle's
+UCNS_ORACLE_LIB override); they must fail.  The unmodified oracle passes the
+same pins in the ordinary suite."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ucns_oracle.c")
+
+MUTANTS = [
+    # name, (original text, planted mistake), pins that must catch it
+    ("hllc_pressure_dropped", ("F[1 + d] = r * u[d] * un + p * n[d];", "F[1 + d] = r * u[d] * un;"),
+     "test_hllc_consistency_contact_upwind_symmetry"),
+    ("stokes_factor", ("(a == j ? 2.0 / 3.0 * mu * div : 0.0)", "(a == j ? 1.0 / 3.0 * mu * div : 0.0)"),
+     "test_viscous_flux_linear_velocity_uniform_temperature"),
+    ("lsq_volume_weight_dropped", ("P[k * M + r] = s * Vm[r];", "P[k * M + r] = s;"),
+     "test_k_exact_reconstruction"),
+    ("rk3_stage_weights_swapped", ("U1[k] = 0.75 * U0[k] + 0.25 * (U1[k] + dt * R[k]);",
+                                   "U1[k] = 0.25 * U0[k] + 0.75 * (U1[k] + dt * R[k]);"),
+     "test_ssprk3_stability_polynomial"),
+    ("ssp54_digits_transposed", ("{0, 0.368410593050371, 0, 0, 0},", "{0, 0.368410593050317, 0, 0, 0},"),
+     "test_ssp54_coefficients_meet_the_order_conditions"),
+    ("face_normal_flipped", ("dS[q][d] = gw[ia] * gw[ib] * nrm[d];", "dS[q][d] = -gw[ia] * gw[ib] * nrm[d];"),
+     "test_face_area_vectors_point_from_owner_to_neighbour"),
+    ("si_second_derivative_weight", ("q.w2 = pow(c->vol[i], 4.0 / 3.0 - 1.0);", "q.w2 = pow(c->vol[i], 2.0 / 3.0 - 1.0);"),
+     "test_smoothness_indicator_closed_forms"),
+    ("cubic_gradient_entry", ("g[14][0] = y * y;", "g[14][0] = 2 * y * y;"), "test_k_exact_p3"),
+    ("wall_mirror_half", ("UR[1 + d] = UL[1 + d] - 2.0 * mn * nh[d];", "UR[1 + d] = UL[1 + d] - mn * nh[d];"),
+     "test_walls_free_stream_and_conservation"),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    return tmp_path_factory.mktemp("mutants")
+
+
+@pytest.mark.parametrize("name,edit,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_the_mutant(name, edit, pins, workdir):
+    src = open(SRC).read()
+    old, new = edit
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    msrc = os.path.join(workdir, f"{name}.c")
+    with open(msrc, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(workdir, f"{name}.so")
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                    "-D_GNU_SOURCE", "-o", lib, msrc, "-lm"], check=True)
+    env = dict(os.environ, UCNS_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
+                        "-x", "-p", "no:cacheprovider", "-k", pins], env=env, capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr  # the pins ran
+    assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"

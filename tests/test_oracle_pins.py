@@ -87,6 +87,20 @@ def test_geometry_closed_surfaces_and_volume(kind, jhex8_p2, jtet_p2):
     assert np.linalg.norm(d, axis=1).max() < 2.0 * hh.max()
 
 
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_face_area_vectors_point_from_owner_to_neighbour(kind, jhex8_p2, jtet_p2):
+    """Eq. 2 sums sigma G_f with G_f taken through dS oriented from the owner
+    to the neighbour: every face's total area vector has a positive
+    component along the owner -> neighbour (periodic image) centroid offset."""
+    nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
+    fo, fn, sh = c.faces()
+    _, cen, _ = c.geometry()
+    for f in range(0, c.n_faces, 7):
+        _, dS = c.face_quad(f)
+        d = cen[fn[f]] + sh[f] * box - cen[fo[f]]
+        assert dS.sum(axis=0) @ d > 0, f
+
+
 def test_uniform_lattice_centroids_exact():
     n = 6
     nodes, cells, box = I.hex_lattice(n)

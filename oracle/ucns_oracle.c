@@ -7,11 +7,7 @@
  * interface gradient, HLLC inviscid flux, Eq. 8 explicit SSP Runge-Kutta).
  * Reconstruction degrees P1 and P2 on hexahedra and tetrahedra, P3 and P4
  * (quadratic directional candidates) on hexahedra.
- *
- * Parity unpinned: the exact constants of the CWENOZ weight formula (the
- * averaging of tau, epsilon); the test suite pins the weights' properties
- * (normalisation, tendency to the linear weights, non-oscillatory steps) but
- * no independent value of them exists in the paper.
+
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark load this library; the product path

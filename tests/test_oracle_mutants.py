@@ -35,6 +35,11 @@ MUTANTS = [
     ("cubic_gradient_entry", ("g[14][0] = y * y;", "g[14][0] = 2 * y * y;"), "test_k_exact_p3"),
     ("wall_mirror_half", ("UR[1 + d] = UL[1 + d] - 2.0 * mn * nh[d];", "UR[1 + d] = UL[1 + d] - mn * nh[d];"),
      "test_walls_free_stream_and_conservation"),
+    ("cwenoz_tau_summed", ("    tau /= (double)nv;\n", "\n"), "test_cwenoz_weights_worked_example"),
+    ("cwenoz_eps_dropped", ("lam[s] * (1.0 + tau / (c->eps + SI[s]))", "lam[s] * (1.0 + tau / (SI[s] + 1e-300))"),
+     "test_cwenoz_weights_worked_example"),
+    ("cwenoz_central_candidate_undivided", ("      as[0][k] = t / lam[0];", "      as[0][k] = t;"),
+     "test_k_exact_reconstruction"),
 ]
 
 

@@ -819,6 +819,36 @@ def test_order_isentropic_vortex(order, scheme, lo):
 
 
 # ------------------------------------------------------ CWENOZ behaviour ---
+def test_cwenoz_weights_worked_example():
+    """The CWENOZ weights (Eq. 6 as printed, tau the mean |SI_1 - SI_s|) on a
+    closed-form example: U = (x - x_i)^2 on a uniform lattice of spacing h
+    (cell averages (x - x_i)^2 + h^2/12), P2.  The central polynomial is exact,
+    SI_1 = V^(-1/3) int (2x)^2 + V^(1/3) int 2^2 = h^4 (1/3 + 4).  The linear
+    directional candidate of face +x fits the differences a^2 h^2 of its six
+    cells (offsets (1,0,0), (2,0,0), (1,+-1,0), (1,0,+-1) in h) with
+    gradient 13 h / 9 (normal equations diag(9, 2, 2), right side 13 h^2),
+    SI = 169 h^4 / 81; those of the y and z faces (offsets (0,1,0), (+-1,1,0),
+    (0,2,0), (0,1,+-1)) have gradient 2 h / 9, SI = 4 h^4 / 81; -x, -y, -z
+    mirror them.  The weights follow from these by Eq. 6 with lambda =
+    (1000, 1, ..., 1)/1006 and eps = 1e-6."""
+    n = 8
+    h = 2 * math.pi / n
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+    xm = I.cell_vertex_means(nodes, cells)
+    i = 4 + n * (4 + n * 4)  # a central cell: its stencils do not reach the periodic seam
+    u = (xm[:, 0] - xm[i, 0]) ** 2 + h * h / 12.0
+    _, w = c.reconstruct(np.tile(u, (5, 1)), weights=True)
+    S0, Sx, Syz = h ** 4 * (1 / 3 + 4), 169 * h ** 4 / 81, 4 * h ** 4 / 81
+    S = np.array([S0, Sx, Sx, Syz, Syz, Syz, Syz])  # central, then faces -x, +x, -y, +y, -z, +z
+    lam = np.array([1000.0] + [1.0] * 6) / 1006.0
+    tau = np.abs(S0 - S[1:]).mean()
+    wt = lam * (1.0 + tau / (1e-6 + S))
+    wt /= wt.sum()
+    for v in range(5):
+        assert np.abs(w[i, v] - wt).max() <= 1e-13, (w[i, v], wt)
+
+
 def test_cwenoz_weights_normalised_and_tend_to_linear():
     """Eq. 5: the nonlinear weights are positive and sum to one; on smooth
     data they approach the linear weights as the mesh is refined (mean

@@ -5,9 +5,11 @@ printed in the paper's benchmark matrix, closed forms, exact invariants
 (free-stream preservation, discrete conservation, closed-surface sums),
 k-exactness of the least-squares reconstruction (Eqs. 3-4), library
 least-squares on the same systems, textbook properties of the HLLC and
-Newtonian viscous fluxes, the SSP-RK3 stability polynomial, the design
-order of accuracy on exact Euler solutions, and the Taylor-Green initial
-diagnostics.  None of these touch the GPU.
+Newtonian viscous fluxes, the jump-penalised face gradient of Eq. 7 on an
+odd-even mode (exact) and a shear wave (convergent), the SSP-RK3 stability
+polynomial, the design order of accuracy on exact Euler solutions, the
+Taylor-Green initial diagnostics and pressure (pressure Poisson equation),
+and the dissipation diagnostics of plane waves.  None of these touch the GPU.
 """
 import math
 import os
@@ -678,6 +680,76 @@ def test_viscous_flux_heat_conduction_and_rest():
     assert np.all(F == 0.0)
 
 
+def _viscous_part(nodes, cells, box, U, **kw):
+    """The residual with viscosity minus the Euler residual of the same state
+    and reconstruction: the viscous flux integral alone, +(1/V) sum sigma F_v A."""
+    cv = O.Case(nodes, cells, box, O.Params(**kw))
+    ci = O.Case(nodes, cells, box, O.Params(**{**kw, "Re": 0.0}))
+    return cv.residual(U) - ci.residual(U)
+
+
+def _shear_state(n, comp, eps, p, g=1.4):
+    """Exact cell averages on the uniform n^3 lattice of rho = 1, uniform p and
+    the velocity component comp (1: u, 2: v) = eps sin x; also the cell
+    averages of sin x and cos 2x."""
+    nodes, cells, box = I.hex_lattice(n)
+    h = 2 * math.pi / n
+    c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
+    _, cen, _ = c.geometry()
+    a = cen[:, 0] - h / 2
+    s = (np.cos(a) - np.cos(a + h)) / h
+    c2 = (np.sin(2 * (a + h)) - np.sin(2 * a)) / (2 * h)
+    U = np.zeros((5, c.n_cells))
+    U[0] = 1.0
+    U[comp] = eps * s
+    U[4] = p / (g - 1) + 0.5 * eps ** 2 * (0.5 - 0.5 * c2)
+    return (nodes, cells, box), U, s, c2
+
+
+def test_jump_penalty_on_the_odd_even_mode():
+    """Eq. 7 on the odd-even shear mode v = eps (-1)^i (i the cell's x index),
+    rho and p uniform, on a uniform cube lattice at P1. The mode is even about
+    every cell, so each symmetric least-squares gradient of it vanishes and the
+    averaged face gradient is zero: only the penalty alpha (U_R - U_L) n / L_int,
+    L_int = h, acts. The viscous residual is then alpha mu times the discrete
+    Laplacian (v_{i+1} - 2 v_i + v_{i-1}) / h^2 = -4 v_i / h^2 in the y
+    momentum and zero in the rest (zero face-average velocity, no jump in rho
+    or E), exactly."""
+    n, eps, Re, M, g = 8, 0.1, 10.0, 0.5, 1.4
+    nodes, cells, box = I.hex_lattice(n)
+    h = 2 * math.pi / n
+    c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
+    _, cen, _ = c.geometry()
+    v = eps * (-1.0) ** np.floor(cen[:, 0] / h)
+    p = 1.0 / (g * M * M)
+    U = np.zeros((5, c.n_cells))
+    U[0], U[2], U[4] = 1.0, v, p / (g - 1) + 0.5 * v * v
+    Rv = _viscous_part(nodes, cells, box, U, order=1, scheme=0, Mach=M, Re=Re)
+    ref = np.zeros_like(Rv)
+    ref[2] = -4.0 * (4.0 / 3.0) / Re * v / h ** 2
+    assert np.abs(Rv - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_viscous_residual_of_a_shear_wave():
+    """v = eps sin x, rho and p uniform (T uniform), on uniform cube lattices at
+    P2: the viscous residual tends at second order to the cell averages of
+    div F_v = (0, 0, mu v'', 0, (mu v v')') = (0, 0, -mu eps sin x, 0,
+    mu eps^2 cos 2x) (Newtonian stress and its work, Eq. 7 gradients; no
+    heat flux). The density, x and z rows stay zero to round-off."""
+    eps, Re, M, g = 0.1, 10.0, 0.5, 1.4
+    mu = 1.0 / Re
+    err = []
+    for n in (16, 32):
+        mesh, U, s, c2 = _shear_state(n, 2, eps, 1.0 / (g * M * M))
+        Rv = _viscous_part(*mesh, U, order=2, scheme=0, Mach=M, Re=Re)
+        assert np.abs(Rv[[0, 1, 3]]).max() < 1e-14
+        err.append((np.abs(Rv[2] + mu * eps * s).max() / (mu * eps),
+                    np.abs(Rv[4] - mu * eps ** 2 * c2).max() / (mu * eps ** 2)))
+    (m16, e16), (m32, e32) = err
+    assert m32 < 0.35 * m16 and m32 < 0.01, err
+    assert e32 < 0.5 * e16 and e32 < 0.05, err
+
+
 # -------------------------------------------------------------------- RK ---
 def test_ssprk3_stability_polynomial():
     for z in (-0.3, -1.0, -2.5, 0.7, 0.05):
@@ -769,6 +841,63 @@ def test_tgv_initial_ke_mach_independent():
         c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0, Mach=M))
         kes.append(c.diagnostics(c.cell_average("tgv", [M, 1.4]))[0])
     assert abs(kes[0] - kes[1]) < 2e-3 * 0.125
+
+
+def test_tgv_initial_pressure_solves_the_poisson_equation():
+    """Sec. 4.2 Taylor-Green initial state: for the given velocity, the
+    pressure perturbation is the zero-mean periodic solution of the
+    incompressible pressure Poisson equation lap p = -d_i u_j d_j u_i =
+    -(1 + cos 2z)(cos 2x + cos 2y)/2 (rho_0 = 1), and the temperature is
+    uniform, rho = gamma M^2 p, so the mean density is 1. The 7-point
+    Laplacian of the cell pressures converges to that right side at second
+    order (Mach 0.01: the density is 1 to 1e-4)."""
+    g, M = 1.4, 0.01
+    err = []
+    for n in (16, 32):
+        nodes, cells, box = I.hex_lattice(n)
+        h = 2 * math.pi / n
+        c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0, Mach=M))
+        U = c.cell_average("tgv", [M, g])
+        _, cen, _ = c.geometry()
+        p = (g - 1) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+        assert abs(U[0].mean() - 1.0) < 1e-12
+        assert np.abs(g * M * M * p / U[0] - 1.0).max() < 1e-6
+        ijk = np.floor(cen / h).astype(int)
+        P = np.zeros((n, n, n))
+        P[ijk[:, 0], ijk[:, 1], ijk[:, 2]] = p
+        lap = (sum(np.roll(P, 1, d) + np.roll(P, -1, d) for d in range(3)) - 6 * P) / h ** 2
+        x = (np.arange(n) + 0.5) * h
+        X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+        rhs = -(1 + np.cos(2 * Z)) * (np.cos(2 * X) + np.cos(2 * Y)) / 2
+        err.append(np.abs(lap - rhs).max() / np.abs(rhs).max())
+    assert err[1] < 0.35 * err[0] and err[1] < 0.05, err
+
+
+def test_dissipation_diagnostics_of_plane_waves():
+    """Sec. 4.2 diagnostics at P2 on plane waves, rho and p uniform, Re = 10:
+    u = eps sin x is pure dilatation, eps_d -> (4/3) mu <(eps cos x)^2> =
+    2 mu eps^2/3 and eps_s = 0; v = eps sin x is pure shear, eps_s -> mu
+    <(eps cos x)^2> = mu eps^2/2 and eps_d = 0. KE from the cell averages is
+    exactly eps^2/4 (sin(h/2)/(h/2))^2 on the uniform lattice. The two
+    dissipations converge at second order."""
+    eps, Re, M, g = 0.1, 10.0, 0.5, 1.4
+    mu = 1.0 / Re
+    err = []
+    for n in (8, 16, 32):
+        h = 2 * math.pi / n
+        ke = eps ** 2 / 4 * (math.sin(h / 2) / (h / 2)) ** 2
+        row = []
+        for comp, k, ref in ((1, 2, 2 * mu * eps ** 2 / 3), (2, 1, mu * eps ** 2 / 2)):
+            mesh, U, _, _ = _shear_state(n, comp, eps, 1.0 / (g * M * M))
+            c = O.Case(*mesh, O.Params(order=2, scheme=0, Mach=M, Re=Re))
+            d = c.diagnostics(U)
+            assert math.isclose(d[0], ke, rel_tol=1e-12)
+            assert d[3 - k] < 1e-25  # the other dissipation vanishes
+            row.append(abs(d[k] - ref) / ref)
+        err.append(row)
+    for j in range(2):
+        assert err[1][j] < 0.3 * err[0][j] and err[2][j] < 0.3 * err[1][j], err
+    assert max(err[2]) < 0.02, err
 
 
 # ---------------------------------------------------- order of accuracy ---
@@ -906,5 +1035,11 @@ def test_cfl_time_step_closed_form():
     U[4] = p / 0.4 + 0.5 * r * u @ u
     h = 2 * math.pi / n / 3
     a = math.sqrt(1.4 * p / r)
-    ref = 0.5 * min(h / (np.linalg.norm(u) + a), r * h * h * 0.71 / (2 * 1.4 / 1600.0))
-    assert math.isclose(c.time_step(U), ref, rel_tol=1e-13)
+    conv, visc = h / (np.linalg.norm(u) + a), r * h * h * 0.71 / (2 * 1.4 / 1600.0)
+    assert conv < visc
+    assert math.isclose(c.time_step(U), 0.5 * conv, rel_tol=1e-13)
+    # Re = 1: the viscous limit binds
+    c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0, Re=1.0, cfl=0.5))
+    visc = r * h * h * 0.71 / (2 * 1.4 / 1.0)
+    assert visc < conv
+    assert math.isclose(c.time_step(U), 0.5 * visc, rel_tol=1e-13)

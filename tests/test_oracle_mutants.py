@@ -4,7 +4,10 @@ transcription makes (a dropped term, a wrong sign, a swapped or mistyped
 coefficient, a wrong factor), compiles that copy with gcc, and runs the pins
 that should catch it against it (in a child process, through the oracle's
 UCNS_ORACLE_LIB override); they must fail.  The unmodified oracle passes the
-same pins in the ordinary suite."""
+same pins in the ordinary suite.  The network's reference (oracle/mlp.py,
+Python) is mutated the same way in a copy of the source tree, where the
+pins import the mutated copy.  Left out as equivalent: a ReLU mask taken
+as a >= 0 instead of a > 0, which differs only at exact zeros."""
 import os
 import shutil
 import subprocess
@@ -14,6 +17,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ucns_oracle.c")
+MLP = os.path.join(ROOT, "oracle", "mlp.py")
 
 MUTANTS = [
     # name, (original text, planted mistake), pins that must catch it
@@ -61,6 +65,29 @@ MUTANTS = [
      "test_tgv_initial_pressure_solves_the_poisson_equation"),
     ("tgv_density_gamma_dropped", ("    r = g * M * M * pr;\n", "    r = M * M * pr;\n"),
      "test_tgv_initial_pressure_solves_the_poisson_equation"),
+    ("feature_density_jump_unnormalised", ("F[m] = (U[j] - r) / r;", "F[m] = (U[j] - r);"),
+     "test_features_of_linear_density_and_pressure"),
+    ("feature_smoothness_scale", ("q = 0.1 * sc[v];", "q = 0.01 * sc[v];"),
+     "test_features_of_linear_density_and_pressure"),
+    ("feature_energy_scale", ("double sc[5] = {r, r * a, r * a, r * a, r * a * a};",
+                              "double sc[5] = {r, r * a, r * a, r * a, r * a};"),
+     "test_features_of_linear_density_and_pressure"),
+    ("feature_dilatation_unscaled", ("F[30] = c->hh[i] * fabs(dv) / a;", "F[30] = fabs(dv) / a;"),
+     "test_features_closed_forms"),
+]
+
+MLP_MUTANTS = [
+    ("adam_bias_correction_dropped", ("    mh = m / (1 - b1 ** t)\n", "    mh = m\n"),
+     "test_adam_bias_correction_closed_forms"),
+    ("adam_eps_inside_the_root", ("np.sqrt(vh) + eps", "np.sqrt(vh + eps)"), "test_adam_bias_correction_closed_forms"),
+    ("class_weights_swapped", ("c = np.where(y > 0.5, w_pos, w_neg)\n    # -y", "c = np.where(y > 0.5, w_neg, w_pos)\n    # -y"),
+     "test_gradient_matches_finite_differences"),
+    ("bf16_truncates", ("u = ((u + 0x7FFF + lsb) >> 16) << 16", "u = (u >> 16) << 16"),
+     "test_bf16_rounding_is_nearest_even"),
+    ("bf16_hidden_activation_not_rounded", ("    h1r = r(h1)\n", "    h1r = h1\n"),
+     "test_bf16_rounding_places_worked_example"),
+    ("bias_gradient_from_the_rounded_dh2", ('g["b2"] = dh2.sum(axis=0)', 'g["b2"] = dh2r.sum(axis=0)'),
+     "test_bf16_rounding_places_worked_example"),
 ]
 
 
@@ -83,8 +110,36 @@ def test_pins_reject_the_mutant(name, edit, pins, workdir):
     subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                     "-D_GNU_SOURCE", "-o", lib, msrc, "-lm"], check=True)
     env = dict(os.environ, UCNS_ORACLE_LIB=lib)
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-q",
-                        "-x", "-p", "no:cacheprovider", "-k", pins], env=env, capture_output=True, text=True,
-                       timeout=600, cwd=ROOT)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_mlp.py"), "-q", "-x", "-p", "no:cacheprovider",
+                        "-k", pins], env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr  # the pins ran
+    assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"
+
+
+def _run_network_pins(tree, mlp_source, pins):
+    """Copy the Python sources into tree with oracle/mlp.py replaced, and run
+    the named network pins there (they import the copy)."""
+    skip = shutil.ignore_patterns("_build", "_lib", "csrc", "__pycache__", "*.so")
+    for d in ("oracle", "paper_2609_07387_gb300", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(tree, d), ignore=skip)
+    with open(os.path.join(tree, "oracle", "mlp.py"), "w") as f:
+        f.write(mlp_source)
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(tree, "tests", "test_oracle_mlp.py"), "-q",
+                           "-p", "no:cacheprovider", "-k", pins], capture_output=True, text=True, timeout=600, cwd=tree)
+
+
+def test_network_pins_pass_on_an_unmodified_copy(workdir):
+    pins = " or ".join(sorted({m[2] for m in MLP_MUTANTS}))
+    r = _run_network_pins(os.path.join(workdir, "tree_unmodified"), open(MLP).read(), pins)
+    assert r.returncode == 0 and "failed" not in r.stdout, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("name,edit,pins", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_pins_reject_the_network_mutant(name, edit, pins, workdir):
+    src = open(MLP).read()
+    old, new = edit
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    r = _run_network_pins(os.path.join(workdir, f"tree_{name}"), src.replace(old, new), pins)
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr  # the pins ran
     assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"

@@ -6,8 +6,13 @@ that should catch it against it (in a child process, through the oracle's
 UCNS_ORACLE_LIB override); they must fail.  The unmodified oracle passes the
 same pins in the ordinary suite.  The network's reference (oracle/mlp.py,
 Python) is mutated the same way in a copy of the source tree, where the
-pins import the mutated copy.  Left out as equivalent: a ReLU mask taken
-as a >= 0 instead of a > 0, which differs only at exact zeros."""
+pins import the mutated copy.
+
+Left out as equivalent: a ReLU mask taken as >= 0 instead of > 0 (it
+differs only at exact zeros), and one Gauss point fewer in the smoothness
+indicator of a cubic (on affine cells three points per direction are
+already exact, and on trilinear cells neither rule is, so no closed form
+tells the two apart)."""
 import os
 import shutil
 import subprocess
@@ -74,6 +79,23 @@ MUTANTS = [
      "test_features_of_linear_density_and_pressure"),
     ("feature_dilatation_unscaled", ("F[30] = c->hh[i] * fabs(dv) / a;", "F[30] = fabs(dv) / a;"),
      "test_features_closed_forms"),
+    ("tet_jacobian_power", ("*detJ = a * a * b * det3(v1, v2, v3);", "*detJ = a * b * det3(v1, v2, v3);"),
+     "test_geometry_closed_surfaces_and_volume"),
+    ("tet_map_last_term", ("+ a * b * cc * e3[d];", "+ a * cc * e3[d];"), "test_face_quadrature_integrates_bilinear_exactly"),
+    ("triangle_collapsed_weight", ("dS[q][d] = gw[ia] * gw[ib] * a * n[d];", "dS[q][d] = gw[ia] * gw[ib] * n[d];"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("triangle_centroid_rule_area", ("dS[0][d] = 0.5 * n[d];", "dS[0][d] = n[d];"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("triangle_collapsed_point", ("x[q][d] = Q[0][d] + a * e1[d] + a * b * e2[d];", "x[q][d] = Q[0][d] + a * e1[d] + b * e2[d];"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("central_stencil_shared_nodes_ascending", ("return q->shared - p->shared;", "return p->shared - q->shared;"),
+     "test_stencil_membership_hex_lattice"),
+    ("directional_search_enters_the_cell", ("if (m < 0 || m == avoid) continue;", "if (m < 0) continue;"),
+     "test_stencil_membership_hex_lattice"),
+    ("directional_linear_weight", ("lam[s] = dv[s - 1] ? 1.0 / lsum : 0.0;", "lam[s] = dv[s - 1] ? 2.0 / lsum : 0.0;"),
+     "test_cwenoz_weights_worked_example"),
+    ("nonlinear_weights_not_normalised", ("for (int s = 0; s < st; s++) wt[s] /= wsum;", "for (int s = 0; s < st; s++) wt[s] /= 1.0;"),
+     "test_cwenoz_weights_normalised_and_tend_to_linear"),
 ]
 
 MLP_MUTANTS = [

@@ -118,21 +118,34 @@ def test_uniform_lattice_centroids_exact():
     assert np.isclose(np.linalg.norm(dS), h * h, rtol=1e-14)
 
 
-def test_face_quadrature_integrates_bilinear_exactly(jhex8_p2):
-    """2x2 Gauss points on each (bilinear) face: sum_alpha f(x_alpha) dS_alpha
-    is exact for f linear in x; the divergence theorem then gives
-    oint x_j dS_i = V delta_ij per cell."""
-    nodes, cells, box, c = jhex8_p2
+@pytest.mark.parametrize("kind", ["hex", "tet", "tet_p1"])
+def test_face_quadrature_integrates_bilinear_exactly(kind, jhex8_p2, jtet_p2):
+    """The face rules against the independent volume quadrature, through the
+    divergence theorem on every cell: with y = x - x_c (x_c the centroid),
+    oint y_j dS_i = V delta_ij and oint y_j y_k dS_i = 0. The 2x2 Gauss rule
+    on a bilinear face and the collapsed rule on a triangle at P2 are exact
+    for both integrands; the P1 triangle's centroid rule for the linear one."""
+    if kind == "tet_p1":
+        nodes, cells, box = I.hex_lattice(6, jitter=0.1, seed=3)
+        cells = I.split_tets(cells)
+        c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
+    else:
+        nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
     vol, cen, hh = c.geometry()
     fo, fn, sh = c.faces()
     acc = np.zeros((c.n_cells, 3, 3))
+    quad = np.zeros((c.n_cells, 3, 3, 3))
     for f in range(c.n_faces):
         x, dS = c.face_quad(f)
-        acc[fo[f]] += np.einsum("qi,qj->ij", dS, x - cen[fo[f]])
-        xn = x - sh[f] * box - cen[fn[f]]
-        acc[fn[f]] -= np.einsum("qi,qj->ij", dS, xn)
+        yo, yn = x - cen[fo[f]], x - sh[f] * box - cen[fn[f]]
+        acc[fo[f]] += np.einsum("qi,qj->ij", dS, yo)
+        acc[fn[f]] -= np.einsum("qi,qj->ij", dS, yn)
+        quad[fo[f]] += np.einsum("qi,qj,qk->ijk", dS, yo, yo)
+        quad[fn[f]] -= np.einsum("qi,qj,qk->ijk", dS, yn, yn)
     ref = vol[:, None, None] * np.eye(3)[None]
     assert np.abs(acc - ref).max() < 1e-12 * vol.max()
+    if kind != "tet_p1":
+        assert np.abs(quad).max() < 1e-12 * (vol * hh).max()
 
 
 # ------------------------------------------------------ least squares ---

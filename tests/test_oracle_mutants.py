@@ -96,6 +96,20 @@ MUTANTS = [
      "test_cwenoz_weights_worked_example"),
     ("nonlinear_weights_not_normalised", ("for (int s = 0; s < st; s++) wt[s] /= wsum;", "for (int s = 0; s < st; s++) wt[s] /= 1.0;"),
      "test_cwenoz_weights_normalised_and_tend_to_linear"),
+    ("roe_sound_speed", ("double at = sqrt((g - 1.0) * (Ht - 0.5 * q2));", "double at = sqrt((g - 1.0) * (Ht - q2));"),
+     "test_hllc_resolves_an_isolated_shock_exactly"),
+    ("roe_weights_swapped", ("ut[d] = (sL * uL[d] + sR * uR[d]) / (sL + sR);", "ut[d] = (sR * uL[d] + sL * uR[d]) / (sL + sR);"),
+     "test_hllc_resolves_an_isolated_shock_exactly"),
+    ("right_star_energy_sign", ("(Ss - unR) * (Ss + pR / (rR * (SR - unR))));", "(Ss - unR) * (Ss - pR / (rR * (SR - unR))));"),
+     "test_hllc_consistency_contact_upwind_symmetry"),
+    ("cubic_hessian_entry", ("H[18][3] = z; H[18][4] = y; H[18][5] = x;", "H[18][3] = z; H[18][4] = z; H[18][5] = x;"),
+     "test_smoothness_indicator_cubic_on_a_stretched_cell"),
+    ("derivative_falling_factorial", ("v *= (double)(e[d] - j);", "v *= (double)(e[d]);"),
+     "test_smoothness_indicator_cubic_closed_forms"),
+    ("sampled_residual_volume", ("R[v * ns + k] = -s[v] / c->vol[i];", "R[v * ns + k] = -s[v] / c->vol[i] / c->vol[i];"),
+     "test_residual_of_sampled_cells_equals_the_full_residual"),
+    ("boundary_sides_swapped", ("return c->bc[2 * ax + (s[ax] > 0 ? 1 : 0)];", "return c->bc[2 * ax + (s[ax] > 0 ? 0 : 1)];"),
+     "test_supersonic_inflow_outflow"),
 ]
 
 MLP_MUTANTS = [

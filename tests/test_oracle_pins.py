@@ -340,6 +340,29 @@ def test_smoothness_indicator_cubic_closed_forms():
     assert math.isclose(c.smoothness(5, a, 3), 0.49, rel_tol=1e-13)
 
 
+def test_smoothness_indicator_cubic_on_a_stretched_cell():
+    """The cubic SI closed form on an a x a x 2a cell, where the cube's
+    symmetry no longer hides which coordinate a derivative leaves: with
+    h = V^(1/3) and xi = (x - x_c)/h the cell spans half-widths
+    (alpha, alpha, 2 alpha), alpha = a/(2h), and the cell means of xi^2 are
+    m = (alpha^2/3)(1, 1, 4). For p = xi eta zeta the three derivative orders
+    give (with V^(2|beta|/3) h^(-2|beta|) = 1) m_y m_z + m_x m_z + m_x m_y,
+    then m_z + m_y + m_x (from zeta, eta, xi), then 1."""
+    nodes, cells, box = I.hex_lattice(8)
+    nodes = nodes * np.array([1.0, 1.0, 2.0])
+    box = box * np.array([1.0, 1.0, 2.0])
+    c = O.Case(nodes, cells, box, O.Params(order=3, scheme=1))
+    vol, _, hh = c.geometry()
+    a_side = 2 * math.pi / 8
+    assert math.isclose(vol[5], 2 * a_side ** 3, rel_tol=1e-13)
+    alpha = a_side / (2 * hh[5])
+    mx, my, mz = alpha ** 2 / 3, alpha ** 2 / 3, 4 * alpha ** 2 / 3
+    a = np.zeros(19)
+    a[18] = 1.0
+    ref = (my * mz + mx * mz + mx * my) + (mx + my + mz) + 1.0
+    assert math.isclose(c.smoothness(5, a, 3), ref, rel_tol=1e-13)
+
+
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_free_stream_and_conservation_p3(scheme):
     """Uniform flow gives a zero residual; any state's volume-weighted
@@ -582,6 +605,20 @@ def test_discrete_conservation(kind, jhex8_p2, jtet_p2):
     assert np.all(np.abs(tot) <= 1e-13 * scale)
 
 
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_residual_of_sampled_cells_equals_the_full_residual(kind, jhex8_p2, jtet_p2):
+    """The sampled-cell residual (the path the CPU baseline and the full-size
+    parity samples take) equals the full residual's columns bit for bit, and
+    so do the summed-term magnitudes S."""
+    nodes, cells, box, c = jhex8_p2 if kind == "hex" else jtet_p2
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=6)
+    R, S = c.residual_terms(U)
+    sel = np.random.default_rng(4).choice(c.n_cells, 37, replace=False)
+    Rs, Ss = c.residual_subset_terms(U, sel)
+    assert np.array_equal(Rs, R[:, sel]) and np.array_equal(Ss, S[:, sel])
+    assert np.array_equal(c.residual_subset(U, sel), R[:, sel])
+
+
 def test_residual_deterministic(jhex8_p2):
     nodes, cells, box, c = jhex8_p2
     U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=5)
@@ -627,6 +664,47 @@ def test_hllc_consistency_contact_upwind_symmetry():
         rot = lambda U: np.concatenate([[U[0]], Q @ U[1:4], [U[4]]])
         F1 = O.hllc(rot(UL), rot(UR), Q @ n)
         assert np.allclose(F1, rot(O.hllc(UL, UR, n)), rtol=1e-12, atol=1e-12)
+
+
+def test_hllc_resolves_an_isolated_shock_exactly():
+    """An isolated shock of speed s between U_L and U_R (Rankine-Hugoniot:
+    F(U_R) - F(U_L) = s (U_R - U_L)) is an eigenvector of the Roe matrix, so
+    the Roe-averaged speed u~ + a~ (u~ - a~ for a left-running shock) is s
+    exactly, Einfeldt's bound selects it, the contact speed is the post-shock
+    normal velocity and both star states are the post-shock state: HLLC
+    returns the exact interface flux, F(U_L) for s > 0 and F(U_R) for s < 0,
+    here to round-off. Normal-shock relations at shock Mach 1.2-3, oblique
+    normals, tangential velocity continuous, the post-shock gas moving
+    against the shock (star branch on the shock's side), with the shock
+    running right and its mirror image running left."""
+    rng = np.random.default_rng(7)
+    g = 1.4
+
+    def mirror(U, n):
+        V = U.copy()
+        V[1:4] = U[1:4] - 2 * (U[1:4] @ n) * n
+        return V
+
+    for Ms in (1.2, 1.5, 3.0):
+        for s in (0.3, -0.4, 2.5):
+            n = rng.normal(size=3)
+            n /= np.linalg.norm(n)
+            t = rng.normal(size=3)
+            t = 0.3 * (t - (t @ n) * n)
+            w = math.sqrt(g) * Ms                     # s - u_R, pre-shock state rho = p = 1
+            rL = (g + 1) * Ms ** 2 / ((g - 1) * Ms ** 2 + 2)
+            pL = 1 + 2 * g / (g + 1) * (Ms ** 2 - 1)
+            UL = _cons(rL, (s - w / rL) * n + t, pL)
+            UR = _cons(1.0, (s - w) * n + t, 1.0)
+            rh = _phys(UR, n) - _phys(UL, n) - s * (UR - UL)
+            assert np.abs(rh).max() < 1e-13
+            F = O.hllc(UL, UR, n)
+            ref = _phys(UL, n) if s > 0 else _phys(UR, n)
+            assert np.abs(F - ref).max() <= 1e-14 * np.abs(ref).max(), (Ms, s)
+            A, B = mirror(UR, n), mirror(UL, n)       # the left-running shock, speed -s
+            F = O.hllc(A, B, n)
+            ref = _phys(B, n) if s > 0 else _phys(A, n)
+            assert np.abs(F - ref).max() <= 1e-14 * np.abs(ref).max(), (Ms, -s)
 
 
 def test_hllc_sod_interface_flux():

@@ -17,6 +17,7 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -110,6 +111,20 @@ MUTANTS = [
      "test_residual_of_sampled_cells_equals_the_full_residual"),
     ("boundary_sides_swapped", ("return c->bc[2 * ax + (s[ax] > 0 ? 1 : 0)];", "return c->bc[2 * ax + (s[ax] > 0 ? 0 : 1)];"),
      "test_supersonic_inflow_outflow"),
+    ("integrator_selection_swapped", ("int rc = c->rk == 1 ? orc_ssp54_generic", "int rc = c->rk == 0 ? orc_ssp54_generic"),
+     "test_rk_step_composes_the_residual"),
+    ("fourth_derivative_index_repeated", ("{0, 1, 3}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 1, 2}};",
+                                          "{0, 1, 3}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}, {2, 1, 1}, {1, 2, 1}, {1, 2, 1}};"),
+     "test_smoothness_indicator_quartic_closed_form"),
+    ("quartic_basis_entry", ("{0, 1, 3},\n    {2, 2, 0}", "{0, 1, 3},\n    {2, 1, 0}"), "test_k_exact_p4"),
+    ("p4_directional_candidates_linear", ("c->Kd = c->order == 4 ? 9 : 3;", "c->Kd = 3;"),
+     "test_counts_p4_match_benchmark_matrix"),
+    ("inflow_state_offset", ("c->uinf[v] = params[17 + v];", "c->uinf[v] = params[16 + v];"),
+     "test_supersonic_inflow_outflow"),
+    ("time_step_face_missing", ("for (int j = 0; j < c->nfc; j++) asum += face_area", "for (int j = 0; j < c->nfc - 1; j++) asum += face_area"),
+     "test_cfl_time_step_closed_form"),
+    ("kinetic_energy_half_dropped", ("ke += V * 0.5 * r * (", "ke += V * r * ("),
+     "test_dissipation_diagnostics_of_plane_waves"),
 ]
 
 MLP_MUTANTS = [
@@ -134,21 +149,46 @@ def workdir(tmp_path_factory):
     return tmp_path_factory.mktemp("mutants")
 
 
-@pytest.mark.parametrize("name,edit,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_reject_the_mutant(name, edit, pins, workdir):
+def _run_c_mutant(mutant, workdir, threads):
+    """Plant the mistake in a copy of the oracle's C source, compile it, and
+    run the named pins against it; returns (completed process, error)."""
+    name, (old, new), pins = mutant
     src = open(SRC).read()
-    old, new = edit
-    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    if src.count(old) != 1:
+        return None, f"mutation site of {name} not unique"
     msrc = os.path.join(workdir, f"{name}.c")
     with open(msrc, "w") as f:
         f.write(src.replace(old, new))
     lib = os.path.join(workdir, f"{name}.so")
-    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                    "-D_GNU_SOURCE", "-o", lib, msrc, "-lm"], check=True)
-    env = dict(os.environ, UCNS_ORACLE_LIB=lib)
+    cc = subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                         "-std=c11", "-D_GNU_SOURCE", "-o", lib, msrc, "-lm"], capture_output=True, text=True)
+    if cc.returncode:
+        return None, f"{name} does not compile:\n{cc.stderr[-2000:]}"
+    env = dict(os.environ, UCNS_ORACLE_LIB=lib, OMP_NUM_THREADS=str(threads))
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_mlp.py"), "-q", "-x", "-p", "no:cacheprovider",
                         "-k", pins], env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    return r, None
+
+
+@pytest.fixture(scope="module")
+def c_results(workdir, request):
+    """Every selected C mutant, built and checked concurrently (one child
+    pytest per mutant, the cores shared out among them)."""
+    wanted = {it.callspec.params["name"] for it in request.session.items
+              if getattr(it, "originalname", "") == "test_pins_reject_the_mutant" and hasattr(it, "callspec")}
+    todo = [m for m in MUTANTS if m[0] in wanted]
+    cores = os.cpu_count() or 1
+    workers = max(1, min(8, cores, len(todo)))
+    with ThreadPoolExecutor(workers) as ex:
+        done = ex.map(lambda m: _run_c_mutant(m, workdir, max(1, cores // workers)), todo)
+        return {m[0]: res for m, res in zip(todo, done)}
+
+
+@pytest.mark.parametrize("name,edit,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_the_mutant(name, edit, pins, c_results):
+    r, err = c_results[name]
+    assert err is None, err
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr  # the pins ran
     assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"
 

@@ -437,11 +437,19 @@ def test_k_exact_p4(scheme, degree):
 def test_smoothness_indicator_quartic_closed_form():
     """The |beta| = 4 term (weight V^(5/3)): on a cube, p = xi^4 gives
     int (4 xi^3)^2 + int (12 xi^2)^2 + int (24 xi)^2 + 24^2 = 16/448 + 144/80
-    + 576/12 + 576."""
+    + 576/12 + 576; a mixed quartic checks that every derivative multi-index
+    of each order is taken once."""
     nodes, cells, box = I.hex_lattice(10)
     c = O.Case(nodes, cells, box, O.Params(order=4, scheme=1))
     a = np.zeros(34); a[19] = 1.0
     assert math.isclose(c.smoothness(5, a, 4), 16 / 448 + 144 / 80 + 576 / 12 + 576, rel_tol=1e-13)
+    # a mixed quartic, p = xi eta zeta^2 (cell means of xi^2, xi^4: 1/12, 1/80):
+    # |beta| = 1: (eta zeta^2)^2, (xi zeta^2)^2, (2 xi eta zeta)^2 -> 1/960 + 1/960 + 4/1728;
+    # |beta| = 2: (zeta^2)^2, (2 eta zeta)^2, (2 xi zeta)^2, (2 xi eta)^2 -> 1/80 + 3 (4/144);
+    # |beta| = 3: (2 zeta)^2, (2 eta)^2, (2 xi)^2 -> 3 (4/12); |beta| = 4: d_xyzz p = 2 -> 4
+    a = np.zeros(34); a[33] = 1.0
+    ref = (2 / 960 + 4 / 1728) + (1 / 80 + 12 / 144) + 1.0 + 4.0
+    assert math.isclose(c.smoothness(5, a, 4), ref, rel_tol=1e-13)
 
 
 @pytest.mark.parametrize("scheme", [0, 1])
@@ -896,6 +904,35 @@ def test_ssp54_stability_polynomial():
     for z in (-0.3, -1.0, -2.5, 0.7, 0.05):
         ref = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24 + g * z ** 5
         assert math.isclose(O.ssp54_linear(z, 1.0, 1.0), ref, rel_tol=1e-14), z
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_rk_step_composes_the_residual(integrator):
+    """One step of the case's integrator is its Shu-Osher combination of the
+    case's own residual L = residual(.): SSP-RK3 u1 = u + dt L(u), u2 = 3/4 u
+    + 1/4 (u1 + dt L(u1)), u' = 1/3 u + 2/3 (u2 + dt L(u2)); SSP(5,4) with the
+    coefficients pinned above; and dt <= 0 takes the CFL time step."""
+    nodes, cells, box = I.hex_lattice(6, jitter=0.1, seed=8)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, integrator=integrator))
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=9)
+    dt = 0.5 * c.time_step(U)
+    L = c.residual
+    if integrator == 0:
+        u1 = U + dt * L(U)
+        u2 = 0.75 * U + 0.25 * (u1 + dt * L(u1))
+        ref = U / 3.0 + 2.0 / 3.0 * (u2 + dt * L(u2))
+    else:
+        al, be = O.ssp54_coefficients()
+        u, Ls = [U], []
+        for i in range(1, 6):
+            Ls.append(L(u[i - 1]))
+            u.append(sum(al[i][j] * u[j] + dt * be[i][j] * Ls[j] for j in range(i)))
+        ref = u[5]
+    got, used = c.rk_step(U, dt)
+    assert used == dt
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(U).max()
+    got2, used2 = c.rk_step(U)
+    assert used2 == c.time_step(U)
 
 
 def test_rk_orders_on_a_nonlinear_ode():

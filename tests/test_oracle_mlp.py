@@ -165,3 +165,28 @@ def test_bf16_rounding_places_worked_example():
     assert g["b2"][0] == s1 and g["b3"][0] == s1
     assert g["W2"][0, 0] == mlp.bf16(s1) and g["w3"][0] == 1.0 * s1
     assert np.count_nonzero(g["W2"]) == 1 and np.count_nonzero(g["b2"]) == 1
+
+
+def test_labels_vanish_on_a_uniform_flow_and_flag_a_step():
+    """The label is the largest deviation of the CWENOZ weights from the
+    linear ones (lambda_1 = lambda_c / (lambda_c + nd), the rest 1 / (lambda_c
+    + nd)). On a uniform flow every smoothness indicator is zero, so the
+    weights equal the linear ones and every deviation is zero (to rounding); a
+    density step flags the cells whose stencils straddle it and only those
+    (the step is two lattice planes, the stencils reach at most three
+    cells)."""
+    n = 16
+    nodes, cells, box = I.hex_lattice(n)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1))
+    U = np.zeros((5, c.n_cells))
+    U[0], U[1], U[4] = 1.0, 0.2, 2.5
+    dev, lab = c.labels(U)
+    assert dev.max() < 1e-15 and not lab.any()      # zero up to the normalisation's rounding
+    _, cen, _ = c.geometry()
+    ix = np.floor(cen[:, 0] / (2 * math.pi / n)).astype(int)
+    U[0] = np.where(ix < n // 2, 1.0, 0.5)
+    U[1] = 0.2 * U[0]
+    dev, lab = c.labels(U)
+    dist = np.minimum(np.abs(ix - (n // 2 - 0.5)), np.abs((ix + n // 2) % n - (n // 2 - 0.5)))  # to either step plane
+    assert lab[dist < 1].all()                        # cells next to a step
+    assert (dist > 3).sum() == 4 * n * n and not lab[dist > 3].any()  # beyond every stencil's reach

@@ -4,9 +4,10 @@ transcription makes (a dropped term, a wrong sign, a swapped or mistyped
 coefficient, a wrong factor), compiles that copy with gcc, and runs the pins
 that should catch it against it (in a child process, through the oracle's
 UCNS_ORACLE_LIB override); they must fail.  The unmodified oracle passes the
-same pins in the ordinary suite.  The network's reference (oracle/mlp.py,
-Python) is mutated the same way in a copy of the source tree, where the
-pins import the mutated copy.
+same pins in the ordinary suite.  The oracle's Python parts (the network's
+reference oracle/mlp.py, the parameter array and the labels in
+oracle/__init__.py) are mutated the same way in a copy of the source tree,
+where the pins import the mutated copy.
 
 Left out as equivalent: a ReLU mask taken as >= 0 instead of > 0 (it
 differs only at exact zeros), and one Gauss point fewer in the smoothness
@@ -23,7 +24,6 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ucns_oracle.c")
-MLP = os.path.join(ROOT, "oracle", "mlp.py")
 
 MUTANTS = [
     # name, (original text, planted mistake), pins that must catch it
@@ -127,18 +127,23 @@ MUTANTS = [
      "test_dissipation_diagnostics_of_plane_waves"),
 ]
 
-MLP_MUTANTS = [
-    ("adam_bias_correction_dropped", ("    mh = m / (1 - b1 ** t)\n", "    mh = m\n"),
+PY_MUTANTS = [
+    # name, file under oracle/, (original text, planted mistake), pins that must catch it
+    ("adam_bias_correction_dropped", "mlp.py", ("    mh = m / (1 - b1 ** t)\n", "    mh = m\n"),
      "test_adam_bias_correction_closed_forms"),
-    ("adam_eps_inside_the_root", ("np.sqrt(vh) + eps", "np.sqrt(vh + eps)"), "test_adam_bias_correction_closed_forms"),
-    ("class_weights_swapped", ("c = np.where(y > 0.5, w_pos, w_neg)\n    # -y", "c = np.where(y > 0.5, w_neg, w_pos)\n    # -y"),
+    ("adam_eps_inside_the_root", "mlp.py", ("np.sqrt(vh) + eps", "np.sqrt(vh + eps)"), "test_adam_bias_correction_closed_forms"),
+    ("class_weights_swapped", "mlp.py", ("c = np.where(y > 0.5, w_pos, w_neg)\n    # -y", "c = np.where(y > 0.5, w_neg, w_pos)\n    # -y"),
      "test_gradient_matches_finite_differences"),
-    ("bf16_truncates", ("u = ((u + 0x7FFF + lsb) >> 16) << 16", "u = (u >> 16) << 16"),
+    ("bf16_truncates", "mlp.py", ("u = ((u + 0x7FFF + lsb) >> 16) << 16", "u = (u >> 16) << 16"),
      "test_bf16_rounding_is_nearest_even"),
-    ("bf16_hidden_activation_not_rounded", ("    h1r = r(h1)\n", "    h1r = h1\n"),
+    ("bf16_hidden_activation_not_rounded", "mlp.py", ("    h1r = r(h1)\n", "    h1r = h1\n"),
      "test_bf16_rounding_places_worked_example"),
-    ("bias_gradient_from_the_rounded_dh2", ('g["b2"] = dh2.sum(axis=0)', 'g["b2"] = dh2r.sum(axis=0)'),
+    ("bias_gradient_from_the_rounded_dh2", "mlp.py", ('g["b2"] = dh2.sum(axis=0)', 'g["b2"] = dh2r.sum(axis=0)'),
      "test_bf16_rounding_places_worked_example"),
+    ("label_linear_weights", "__init__.py", ("/ (self.params.lam_central + self.nd)", "/ (self.params.lam_central + self.nd + 1)"),
+     "test_labels_vanish_on_a_uniform_flow_and_flag_a_step"),
+    ("parameter_order_eps_alpha", "__init__.py", ("self.lam_central, self.eps, self.alpha,", "self.lam_central, self.alpha, self.eps,"),
+     "test_cwenoz_weights_worked_example"),
 ]
 
 
@@ -193,29 +198,31 @@ def test_pins_reject_the_mutant(name, edit, pins, c_results):
     assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"
 
 
-def _run_network_pins(tree, mlp_source, pins):
-    """Copy the Python sources into tree with oracle/mlp.py replaced, and run
-    the named network pins there (they import the copy)."""
+def _run_python_pins(tree, fname, source, pins):
+    """Copy the Python sources into tree with oracle/<fname> replaced by
+    source, and run the named pins there (they import the copy)."""
     skip = shutil.ignore_patterns("_build", "_lib", "csrc", "__pycache__", "*.so")
     for d in ("oracle", "paper_2609_07387_gb300", "tests"):
         shutil.copytree(os.path.join(ROOT, d), os.path.join(tree, d), ignore=skip)
-    with open(os.path.join(tree, "oracle", "mlp.py"), "w") as f:
-        f.write(mlp_source)
-    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(tree, "tests", "test_oracle_mlp.py"), "-q",
-                           "-p", "no:cacheprovider", "-k", pins], capture_output=True, text=True, timeout=600, cwd=tree)
+    with open(os.path.join(tree, "oracle", fname), "w") as f:
+        f.write(source)
+    tests = [os.path.join(tree, "tests", t) for t in ("test_oracle_mlp.py", "test_oracle_pins.py")]
+    return subprocess.run([sys.executable, "-m", "pytest", *tests, "-q", "-p", "no:cacheprovider", "-k", pins],
+                          capture_output=True, text=True, timeout=600, cwd=tree)
 
 
-def test_network_pins_pass_on_an_unmodified_copy(workdir):
-    pins = " or ".join(sorted({m[2] for m in MLP_MUTANTS}))
-    r = _run_network_pins(os.path.join(workdir, "tree_unmodified"), open(MLP).read(), pins)
+def test_python_pins_pass_on_an_unmodified_copy(workdir):
+    pins = " or ".join(sorted({m[3] for m in PY_MUTANTS}))
+    src = open(os.path.join(ROOT, "oracle", "mlp.py")).read()
+    r = _run_python_pins(os.path.join(workdir, "tree_unmodified"), "mlp.py", src, pins)
     assert r.returncode == 0 and "failed" not in r.stdout, r.stdout + r.stderr
 
 
-@pytest.mark.parametrize("name,edit,pins", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
-def test_pins_reject_the_network_mutant(name, edit, pins, workdir):
-    src = open(MLP).read()
+@pytest.mark.parametrize("name,fname,edit,pins", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_reject_the_python_mutant(name, fname, edit, pins, workdir):
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
     old, new = edit
     assert src.count(old) == 1, f"mutation site of {name} not unique"
-    r = _run_network_pins(os.path.join(workdir, f"tree_{name}"), src.replace(old, new), pins)
+    r = _run_python_pins(os.path.join(workdir, f"tree_{name}"), fname, src.replace(old, new), pins)
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr  # the pins ran
     assert r.returncode != 0, f"mutant {name} survived {pins}:\n{r.stdout[-2000:]}"

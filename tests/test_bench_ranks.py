@@ -73,3 +73,13 @@ def test_reference_arm_line_per_integrator(integrator, stages, name):
     assert line["config"]["stages_per_step"] == stages
     assert name in line["config"]["workload"] and name in line["cpu_baseline"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # every key of the line's contract, with its type
+    for k, t in (("metric", str), ("value", float), ("unit", str), ("n_gpus", int), ("steps", int),
+                 ("warmup", int), ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str),
+                 ("dtype", str), ("data", str), ("config", dict), ("cpu_baseline", dict), ("e2e", dict)):
+        assert isinstance(line[k], t), (k, line.get(k))
+    assert "vs_baseline" in line and line["n_gpus"] == 1 and line["steps"] == 1 and line["warmup"] == 0
+    assert line["higher_is_better"] is True and line["unit"] == line["e2e"]["unit"] == line["cpu_baseline"]["unit"]
+    assert line["e2e"]["value"] == line["value"] == line["cpu_baseline"]["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["d2h_bytes_per_step"] == 0

@@ -125,6 +125,12 @@ MUTANTS = [
      "test_cfl_time_step_closed_form"),
     ("kinetic_energy_half_dropped", ("ke += V * 0.5 * r * (", "ke += V * r * ("),
      "test_dissipation_diagnostics_of_plane_waves"),
+    ("velocity_gradient_without_density_term",
+     ("gu[a][j] = (gU[(1 + a) * 3 + j] - u[a] * gU[j]) / r;\n  for (int j = 0; j < 3; j++) {\n    double de",
+      "gu[a][j] = (gU[(1 + a) * 3 + j]) / r;\n  for (int j = 0; j < 3; j++) {\n    double de"),
+     "test_viscous_flux_of_a_general_state"),
+    ("face_gradient_owner_only", ("gf[v * 3 + j] = 0.5 * (gL[v][j] + gR[v][j])", "gf[v * 3 + j] = gL[v][j]"),
+     "test_residual_independent_of_cell_numbering"),
 ]
 
 PY_MUTANTS = [

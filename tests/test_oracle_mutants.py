@@ -131,6 +131,16 @@ MUTANTS = [
      "test_viscous_flux_of_a_general_state"),
     ("face_gradient_owner_only", ("gf[v * 3 + j] = 0.5 * (gL[v][j] + gR[v][j])", "gf[v * 3 + j] = gL[v][j]"),
      "test_residual_independent_of_cell_numbering"),
+    ("gauss_weight_doubled", ("w[i] = 1.0 / ((1.0 - z * z) * dp * dp);", "w[i] = 2.0 / ((1.0 - z * z) * dp * dp);"),
+     "test_geometry_closed_surfaces_and_volume"),
+    ("hex_face_inward", ("{{0,4,7,3},{1,2,6,5}", "{{0,3,7,4},{1,2,6,5}"), "test_geometry_closed_surfaces_and_volume"),
+    ("tet_face_inward", ("{{0,2,1},{0,1,3}", "{{0,1,2},{0,1,3}"), "test_geometry_closed_surfaces_and_volume"),
+    ("neighbour_orientation_sign", ("c->cs[q->n * c->nfc + q->nlf] = -1;", "c->cs[q->n * c->nfc + q->nlf] = 1;"),
+     "test_discrete_conservation"),
+    ("hex_map_corners_swapped", ("{{0,0,0},{1,0,0},{1,1,0},{0,1,0}", "{{0,0,0},{1,0,0},{0,1,0},{1,1,0}"),
+     "test_geometry_closed_surfaces_and_volume"),
+    ("tet_map_edge", ("e2[d] = P[2][d] - P[1][d];\n      e3[d]", "e2[d] = P[2][d] - P[0][d];\n      e3[d]"),
+     "test_face_area_vectors_point_from_owner_to_neighbour"),
 ]
 
 PY_MUTANTS = [

@@ -97,3 +97,33 @@ def test_host_precompute_matches_oracle(kind, order, scheme):
             pos = {c: k for k, c in enumerate(omem)}
             oPm = oP[:, [pos[c] for c in mem]]
             assert np.abs(P - oPm).max() <= 1e-12 * np.abs(oPm).max(), (i, which)
+
+
+def test_product_path_never_touches_the_oracle():
+    """The oracle is test infrastructure: no module of the package imports
+    it, no library source names it, importing the package does not load it,
+    and libucns.so neither exports nor needs one of its symbols."""
+    import ast
+    import subprocess
+    import sys
+
+    pkg = os.path.join(ROOT, "paper_2609_07387_gb300")
+    for f in sorted(os.listdir(pkg)):
+        if f.endswith(".py"):
+            tree = ast.parse(open(os.path.join(pkg, f)).read())
+            for node in ast.walk(tree):
+                mods = [a.name for a in node.names] if isinstance(node, ast.Import) else \
+                    [node.module or ""] if isinstance(node, ast.ImportFrom) else []
+                assert not any(m.split(".")[0] == "oracle" for m in mods), (f, mods)
+    csrc = os.path.join(pkg, "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".hpp", ".h", ".c")):
+            txt = open(os.path.join(csrc, f)).read()
+            assert "ucns_oracle" not in txt and not re.search(r"\borc_\w+\s*\(", txt), f
+    code = "import sys, paper_2609_07387_gb300 as p; from paper_2609_07387_gb300 import gate, inputs; " \
+           "p.load(); print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "False", r.stdout + r.stderr
+    nm = subprocess.run(["nm", "-D", ucns.library_path()], capture_output=True, text=True)
+    if nm.returncode == 0:
+        assert not re.search(r"\borc_\w+", nm.stdout)

@@ -127,3 +127,16 @@ def test_product_path_never_touches_the_oracle():
     nm = subprocess.run(["nm", "-D", ucns.library_path()], capture_output=True, text=True)
     if nm.returncode == 0:
         assert not re.search(r"\borc_\w+", nm.stdout)
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="checks the behaviour without a CUDA device")
+def test_compute_without_a_device_fails_loudly():
+    """There is no CPU fallback: without a CUDA device the device half of
+    ucns_precompute returns an error (its first device allocation fails, so
+    the status is UCNS_ERR_NOMEM naming cudaMalloc, or UCNS_ERR_CUDA), the
+    Python layer raises it, and the mesh stays unusable for compute calls."""
+    m = ucns.Mesh(*I.hex_lattice(4))
+    with pytest.raises(ucns.UcnsError) as e:
+        m.precompute(ucns.Params())
+    assert e.value.code in (-4, -8)
+    assert m._lib.ucns_residual(m._h, None, None, None) != 0

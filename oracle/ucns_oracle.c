@@ -5,8 +5,8 @@
  * (Sec. 2.2: Eq. 1 conservation law, Eq. 2 semi-discretisation, Eqs. 3-4
  * k-exact least-squares reconstruction, Eqs. 5-6 CWENOZ, Eq. 7 viscous
  * interface gradient, HLLC inviscid flux, Eq. 8 explicit SSP Runge-Kutta).
- * Reconstruction degrees P1 and P2 on hexahedra and tetrahedra, P3 and P4
- * (quadratic directional candidates) on hexahedra.
+ * Reconstruction degrees P1 and P2 on hexahedra, tetrahedra and triangular
+ * prisms, P3 and P4 (quadratic directional candidates) on hexahedra.
 
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
@@ -38,9 +38,8 @@
 
 typedef struct {
   int64_t N, nn;
-  int npc;  /* nodes per cell: 8 hex, 4 tet */
-  int nfc;  /* faces per cell: 6 hex, 4 tet */
-  int nfn;  /* nodes per face: 4 quad, 3 triangle */
+  int npc;  /* nodes per cell: 8 hex, 6 prism, 4 tet */
+  int nfc;  /* faces per cell: 6 hex, 5 prism, 4 tet */
   double L[3];
   int per[3];
   double *X;       /* [nn][3] */
@@ -119,12 +118,17 @@ static void gauss_legendre01(int n, double *x, double *w) {
 /* ------------------------------------------------------------------------ */
 /* Element maps.  Hex: trilinear map of the unit cube (VTK node order).      */
 /* Tet: collapsed (Duffy) map of the unit cube onto the tetrahedron.         */
+/* Prism (nodes 0,1,2 counter-clockwise seen from the top triangle 3,4,5,   */
+/* node 3+k above node k): the collapsed map of the base triangle times a   */
+/* linear map in height, so its side faces are the bilinear quad patches.   */
 /* ------------------------------------------------------------------------ */
 static const int HEXO[8][3] = {{0,0,0},{1,0,0},{1,1,0},{0,1,0},{0,0,1},{1,0,1},{1,1,1},{0,1,1}};
 /* local faces, node lists ordered so (p2-p0)x(p3-p1) points outward */
 static const int HEXF[6][4] = {{0,4,7,3},{1,2,6,5},{0,1,5,4},{3,7,6,2},{0,3,2,1},{4,5,6,7}};
 /* tet faces ordered so (p1-p0)x(p2-p0) points outward for positive tets */
 static const int TETF[4][3] = {{0,2,1},{0,1,3},{1,2,3},{0,3,2}};
+/* prism faces: two triangles, then three quads, each ordered by the rules above */
+static const int PRISMF[5][4] = {{0,2,1,-1},{3,4,5,-1},{0,1,4,3},{1,2,5,4},{2,0,3,5}};
 
 static void cell_nodes(const orc_case *c, int64_t i, double P[8][3]) {
   for (int a = 0; a < c->npc; a++)
@@ -163,6 +167,19 @@ static void cell_map(const orc_case *c, const double P[8][3], const double r[3],
       }
     }
     *detJ = det3(dx[0], dx[1], dx[2]);
+  } else if (c->npc == 6) {
+    /* x = (1 - w) B(a, b) + w T(a, b), B = P0 + a e1 + a b e2 on the base,
+       T = P3 + a f1 + a b f2 on the top */
+    double a = r[0], b = r[1], w = r[2], da[3], db[3], dw[3];
+    for (int d = 0; d < 3; d++) {
+      double e1 = P[1][d] - P[0][d], e2 = P[2][d] - P[1][d], f1 = P[4][d] - P[3][d], f2 = P[5][d] - P[4][d];
+      double B = P[0][d] + a * e1 + a * b * e2, T = P[3][d] + a * f1 + a * b * f2;
+      x[d] = (1.0 - w) * B + w * T;
+      da[d] = (1.0 - w) * (e1 + b * e2) + w * (f1 + b * f2);
+      db[d] = (1.0 - w) * a * e2 + w * a * f2;
+      dw[d] = T - B;
+    }
+    *detJ = det3(da, db, dw);
   } else {
     double a = r[0], b = r[1], cc = r[2];
     double e1[3], e2[3], e3[3], v1[3], v2[3], v3[3];
@@ -374,7 +391,11 @@ static int cmp_i64(const void *a, const void *b) {
 }
 
 static const int *face_nodes(const orc_case *c, int lf) {
-  return c->npc == 8 ? HEXF[lf] : TETF[lf];
+  return c->npc == 8 ? HEXF[lf] : (c->npc == 6 ? PRISMF[lf] : TETF[lf]);
+}
+/* nodes of local face lf: 4 (quad) or 3 (triangle) */
+static int face_nn(const orc_case *c, int lf) {
+  return c->npc == 8 ? 4 : (c->npc == 6 ? (lf < 2 ? 3 : 4) : 3);
 }
 
 /* nearest periodic image of cell m seen from cell i, as integer box shifts */
@@ -396,8 +417,9 @@ static int build_faces(orc_case *c) {
       fkey *f = &a[i * c->nfc + lf];
       const int *fnl = face_nodes(c, lf);
       for (int q = 0; q < 4; q++) f->k[q] = -1;
-      for (int q = 0; q < c->nfn; q++) f->k[q] = c->canon[c->C[i * c->npc + fnl[q]]];
-      qsort(f->k, c->nfn, sizeof(int64_t), cmp_i64);
+      const int nn = face_nn(c, lf);
+      for (int q = 0; q < nn; q++) f->k[q] = c->canon[c->C[i * c->npc + fnl[q]]];
+      qsort(f->k, nn, sizeof(int64_t), cmp_i64);
       f->cell = i;
       f->lf = lf;
     }
@@ -460,7 +482,7 @@ static void face_quad(const orc_case *c, int64_t f, double x[][3], double dS[][3
   double P[8][3];
   cell_nodes(c, c->fo[f], P);
   const int *fnl = face_nodes(c, c->flf[f]);
-  if (c->nfn == 4) {
+  if (face_nn(c, c->flf[f]) == 4) {
     double Q[4][3];
     for (int a = 0; a < 4; a++)
       for (int d = 0; d < 3; d++) Q[a][d] = P[fnl[a]][d];
@@ -1261,11 +1283,10 @@ static int case_res(void *ctx, const double *U, double *R) { return residual((or
 void orc_destroy(orc_case *c);
 orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int64_t N, int npc,
                      const double *box, const double *params) {
-  if (!(npc == 8 || npc == 4) || N < 1 || nn < 1) { set_err("bad arguments"); return NULL; }
+  if (!(npc == 8 || npc == 6 || npc == 4) || N < 1 || nn < 1) { set_err("bad arguments"); return NULL; }
   orc_case *c = (orc_case *)calloc(1, sizeof(orc_case));
   c->N = N; c->nn = nn; c->npc = npc;
-  c->nfc = npc == 8 ? 6 : 4;
-  c->nfn = npc == 8 ? 4 : 3;
+  c->nfc = npc == 8 ? 6 : (npc == 6 ? 5 : 4);
   for (int d = 0; d < 3; d++) {
     c->L[d] = box ? box[d] : 0.0;
     c->per[d] = box && box[d] > 0;

@@ -93,6 +93,20 @@ def split_tets(cells: np.ndarray) -> np.ndarray:
     return cells[:, _KUHN_TETS].reshape(-1, 4)
 
 
+# the two triangular prisms of a VTK hexahedron, split through the base and
+# top diagonals 0-2 and 4-6: base triangle counter-clockwise seen from the top,
+# top node k+3 above base node k
+_WEDGES = np.array([[0, 1, 2, 4, 5, 6], [0, 2, 3, 4, 6, 7]], dtype=np.int64)
+
+
+def split_prisms(cells: np.ndarray) -> np.ndarray:
+    """Split VTK hexahedra [n, 8] into 2 triangular prisms each -> [2n, 6]
+    (hex-major), every hexahedron along the same diagonal so that the
+    triangles of periodic neighbours match."""
+    cells = np.asarray(cells, dtype=np.int64)
+    return cells[:, _WEDGES].reshape(-1, 6)
+
+
 def cell_vertex_means(nodes: np.ndarray, cells: np.ndarray) -> np.ndarray:
     """Mean of each cell's node coordinates [n_cells, 3] (a sampling point only)."""
     return np.asarray(nodes)[np.asarray(cells)].mean(axis=1)

@@ -56,6 +56,25 @@ def test_tets_positive_and_fill_the_box():
     assert math.isclose(vol.sum(), (2 * math.pi) ** 3, rel_tol=1e-12)
 
 
+def test_prisms_oriented_and_fill_the_box():
+    """Each prism of the split: base triangle counter-clockwise seen from
+    the top (its normal points at the top triangle), top node k+3 above base
+    node k; the prisms of a lattice hexahedron fill it, all along the same
+    diagonal."""
+    nodes, cells, _ = I.hex_lattice(4)
+    pr = I.split_prisms(cells)
+    assert pr.shape == (2 * 64, 6)
+    p = nodes[pr]
+    nb = np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])
+    up = p[:, 3:].mean(axis=1) - p[:, :3].mean(axis=1)
+    assert np.all(np.einsum("ij,ij->i", nb, up) > 0)
+    assert np.allclose(p[:, 3:, :2], p[:, :3, :2]) and np.all(p[:, 3:, 2] > p[:, :3, 2])
+    h = 2 * math.pi / 4
+    area = 0.5 * np.linalg.norm(nb, axis=1)
+    assert np.allclose(area, 0.5 * h * h) and math.isclose((area * h).sum(), (2 * math.pi) ** 3, rel_tol=1e-12)
+    assert np.array_equal(pr[0::2, [0, 2]], pr[1::2, [0, 1]])  # both share the diagonal 0-2
+
+
 @pytest.mark.parametrize("mach", [0.1, 1.25])
 def test_tgv_closed_form_and_uniform_temperature(mach):
     nodes, cells, _ = I.hex_lattice(6)

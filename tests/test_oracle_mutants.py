@@ -141,6 +141,15 @@ MUTANTS = [
      "test_geometry_closed_surfaces_and_volume"),
     ("tet_map_edge", ("e2[d] = P[2][d] - P[1][d];\n      e3[d]", "e2[d] = P[2][d] - P[0][d];\n      e3[d]"),
      "test_face_area_vectors_point_from_owner_to_neighbour"),
+    ("prism_base_inward", ("{{0,2,1,-1},{3,4,5,-1},{0,1,4,3}", "{{0,1,2,-1},{3,4,5,-1},{0,1,4,3}"),
+     "test_geometry_closed_surfaces_and_volume"),
+    ("prism_side_face_nodes", ("{1,2,5,4},{2,0,3,5}}", "{1,2,5,4},{2,0,5,3}}"), "test_counts_prisms"),
+    ("prism_map_base_derivative", ("db[d] = (1.0 - w) * a * e2 + w * a * f2;", "db[d] = (1.0 - w) * a * e2 + w * f2;"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("prism_map_top_triangle", ("T = P[3][d] + a * f1 + a * b * f2;", "T = P[3][d] + a * f1 + b * f2;"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("prism_one_triangle", ("(c->npc == 6 ? (lf < 2 ? 3 : 4) : 3)", "(c->npc == 6 ? (lf < 1 ? 3 : 4) : 3)"),
+     "test_k_exact_reconstruction"),
 ]
 
 PY_MUTANTS = [

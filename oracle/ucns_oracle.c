@@ -5,8 +5,9 @@
  * (Sec. 2.2: Eq. 1 conservation law, Eq. 2 semi-discretisation, Eqs. 3-4
  * k-exact least-squares reconstruction, Eqs. 5-6 CWENOZ, Eq. 7 viscous
  * interface gradient, HLLC inviscid flux, Eq. 8 explicit SSP Runge-Kutta).
- * Reconstruction degrees P1 and P2 on hexahedra, tetrahedra and triangular
- * prisms, P3 and P4 (quadratic directional candidates) on hexahedra.
+ * Reconstruction degrees P1 and P2 on hexahedra, tetrahedra, triangular
+ * prisms and pyramids, P3 and P4 (quadratic directional candidates) on
+ * hexahedra.
 
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
@@ -38,8 +39,8 @@
 
 typedef struct {
   int64_t N, nn;
-  int npc;  /* nodes per cell: 8 hex, 6 prism, 4 tet */
-  int nfc;  /* faces per cell: 6 hex, 5 prism, 4 tet */
+  int npc;  /* nodes per cell: 8 hex, 6 prism, 5 pyramid, 4 tet */
+  int nfc;  /* faces per cell: 6 hex, 5 prism or pyramid, 4 tet */
   double L[3];
   int per[3];
   double *X;       /* [nn][3] */
@@ -121,6 +122,8 @@ static void gauss_legendre01(int n, double *x, double *w) {
 /* Prism (nodes 0,1,2 counter-clockwise seen from the top triangle 3,4,5,   */
 /* node 3+k above node k): the collapsed map of the base triangle times a   */
 /* linear map in height, so its side faces are the bilinear quad patches.   */
+/* Pyramid (base 0,1,2,3 counter-clockwise seen from the apex 4): the base's */
+/* bilinear map shrunk linearly onto the apex, x = (1 - w) Q(a, b) + w x_4.   */
 /* ------------------------------------------------------------------------ */
 static const int HEXO[8][3] = {{0,0,0},{1,0,0},{1,1,0},{0,1,0},{0,0,1},{1,0,1},{1,1,1},{0,1,1}};
 /* local faces, node lists ordered so (p2-p0)x(p3-p1) points outward */
@@ -129,6 +132,8 @@ static const int HEXF[6][4] = {{0,4,7,3},{1,2,6,5},{0,1,5,4},{3,7,6,2},{0,3,2,1}
 static const int TETF[4][3] = {{0,2,1},{0,1,3},{1,2,3},{0,3,2}};
 /* prism faces: two triangles, then three quads, each ordered by the rules above */
 static const int PRISMF[5][4] = {{0,2,1,-1},{3,4,5,-1},{0,1,4,3},{1,2,5,4},{2,0,3,5}};
+/* pyramid faces: the base quad, then four triangles */
+static const int PYRF[5][4] = {{0,3,2,1},{0,1,4,-1},{1,2,4,-1},{2,3,4,-1},{3,0,4,-1}};
 
 static void cell_nodes(const orc_case *c, int64_t i, double P[8][3]) {
   for (int a = 0; a < c->npc; a++)
@@ -167,6 +172,18 @@ static void cell_map(const orc_case *c, const double P[8][3], const double r[3],
       }
     }
     *detJ = det3(dx[0], dx[1], dx[2]);
+  } else if (c->npc == 5) {
+    double a = r[0], b = r[1], w = r[2], da[3], db[3], dw[3];
+    for (int d = 0; d < 3; d++) {
+      double Q = (1 - a) * (1 - b) * P[0][d] + a * (1 - b) * P[1][d] + a * b * P[2][d] + (1 - a) * b * P[3][d];
+      double Qa = (1 - b) * (P[1][d] - P[0][d]) + b * (P[2][d] - P[3][d]);
+      double Qb = (1 - a) * (P[3][d] - P[0][d]) + a * (P[2][d] - P[1][d]);
+      x[d] = (1.0 - w) * Q + w * P[4][d];
+      da[d] = (1.0 - w) * Qa;
+      db[d] = (1.0 - w) * Qb;
+      dw[d] = P[4][d] - Q;
+    }
+    *detJ = det3(da, db, dw);
   } else if (c->npc == 6) {
     /* x = (1 - w) B(a, b) + w T(a, b), B = P0 + a e1 + a b e2 on the base,
        T = P3 + a f1 + a b f2 on the top */
@@ -391,11 +408,11 @@ static int cmp_i64(const void *a, const void *b) {
 }
 
 static const int *face_nodes(const orc_case *c, int lf) {
-  return c->npc == 8 ? HEXF[lf] : (c->npc == 6 ? PRISMF[lf] : TETF[lf]);
+  return c->npc == 8 ? HEXF[lf] : (c->npc == 6 ? PRISMF[lf] : (c->npc == 5 ? PYRF[lf] : TETF[lf]));
 }
 /* nodes of local face lf: 4 (quad) or 3 (triangle) */
 static int face_nn(const orc_case *c, int lf) {
-  return c->npc == 8 ? 4 : (c->npc == 6 ? (lf < 2 ? 3 : 4) : 3);
+  return c->npc == 8 ? 4 : (c->npc == 6 ? (lf < 2 ? 3 : 4) : (c->npc == 5 ? (lf == 0 ? 4 : 3) : 3));
 }
 
 /* nearest periodic image of cell m seen from cell i, as integer box shifts */
@@ -626,6 +643,15 @@ static void lsq_matrix(const orc_case *c, int64_t i, int M, const int64_t *mem,
 static int lsq_pinv(const double *A, int M, int K, const double *Vm, double *P) {
   double Q[ORC_MAXM * ORC_MAXK], R[ORC_MAXK * ORC_MAXK];
   memset(R, 0, sizeof R);
+  /* rank test against the largest column: a column that vanishes (every
+     member shares the cell's mean of that mode) is as deficient as one that
+     depends on the others */
+  double amax = 0;
+  for (int j = 0; j < K; j++) {
+    double n = 0;
+    for (int r = 0; r < M; r++) n += A[r * K + j] * A[r * K + j];
+    amax = fmax(amax, n);
+  }
   for (int j = 0; j < K; j++) {
     double v[ORC_MAXM], n0 = 0;
     for (int r = 0; r < M; r++) { v[r] = A[r * K + j]; n0 += v[r] * v[r]; }
@@ -639,7 +665,10 @@ static int lsq_pinv(const double *A, int M, int K, const double *Vm, double *P) 
     double nv = 0;
     for (int r = 0; r < M; r++) nv += v[r] * v[r];
     nv = sqrt(nv);
-    if (!(nv > 1e-10 * sqrt(n0))) { set_err("rank-deficient least-squares stencil"); return -1; }
+    if (!(nv > 1e-10 * sqrt(n0)) || !(nv > 1e-8 * sqrt(amax))) {
+      set_err("rank-deficient least-squares stencil");
+      return -1;
+    }
     R[j * K + j] = nv;
     for (int r = 0; r < M; r++) Q[r * K + j] = v[r] / nv;
   }
@@ -1283,10 +1312,10 @@ static int case_res(void *ctx, const double *U, double *R) { return residual((or
 void orc_destroy(orc_case *c);
 orc_case *orc_create(const double *nodes, int64_t nn, const int64_t *cells, int64_t N, int npc,
                      const double *box, const double *params) {
-  if (!(npc == 8 || npc == 6 || npc == 4) || N < 1 || nn < 1) { set_err("bad arguments"); return NULL; }
+  if (!(npc == 8 || npc == 6 || npc == 5 || npc == 4) || N < 1 || nn < 1) { set_err("bad arguments"); return NULL; }
   orc_case *c = (orc_case *)calloc(1, sizeof(orc_case));
   c->N = N; c->nn = nn; c->npc = npc;
-  c->nfc = npc == 8 ? 6 : (npc == 6 ? 5 : 4);
+  c->nfc = npc == 8 ? 6 : (npc == 6 || npc == 5 ? 5 : 4);
   for (int d = 0; d < 3; d++) {
     c->L[d] = box ? box[d] : 0.0;
     c->per[d] = box && box[d] > 0;

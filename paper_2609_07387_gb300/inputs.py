@@ -107,6 +107,26 @@ def split_prisms(cells: np.ndarray) -> np.ndarray:
     return cells[:, _WEDGES].reshape(-1, 6)
 
 
+# the six faces of a VTK hexahedron, each ordered counter-clockwise seen from
+# the hexahedron's inside (the pyramid bases below)
+_HEX_FACES_INWARD = np.array([[0, 3, 7, 4], [1, 5, 6, 2], [0, 4, 5, 1], [3, 2, 6, 7], [0, 1, 2, 3],
+                              [4, 7, 6, 5]], dtype=np.int64)
+
+
+def split_pyramids(nodes: np.ndarray, cells: np.ndarray):
+    """Split VTK hexahedra [n, 8] into 6 pyramids each, one per face, with
+    the apex at the hexahedron's vertex mean (a node appended per
+    hexahedron): -> (nodes [n_nodes + n, 3], pyramids [6n, 5], hex-major),
+    base counter-clockwise seen from the apex, apex last."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    cells = np.asarray(cells, dtype=np.int64)
+    apex = nodes.shape[0] + np.arange(cells.shape[0], dtype=np.int64)
+    out = np.concatenate([nodes, nodes[cells].mean(axis=1)])
+    base = cells[:, _HEX_FACES_INWARD]                    # [n, 6, 4]
+    pyr = np.concatenate([base, np.broadcast_to(apex[:, None, None], (cells.shape[0], 6, 1))], axis=2)
+    return out, pyr.reshape(-1, 5)
+
+
 def cell_vertex_means(nodes: np.ndarray, cells: np.ndarray) -> np.ndarray:
     """Mean of each cell's node coordinates [n_cells, 3] (a sampling point only)."""
     return np.asarray(nodes)[np.asarray(cells)].mean(axis=1)

@@ -75,6 +75,24 @@ def test_prisms_oriented_and_fill_the_box():
     assert np.array_equal(pr[0::2, [0, 2]], pr[1::2, [0, 1]])  # both share the diagonal 0-2
 
 
+def test_pyramids_oriented_and_fill_the_box():
+    """Each hexahedron's six pyramids: one per face, the apex (an appended
+    node) at the hexahedron's vertex mean, the base counter-clockwise seen
+    from the apex; on the lattice each has volume h^3/6 and they fill it."""
+    nodes, cells, _ = I.hex_lattice(3)
+    n2, pyr = I.split_pyramids(nodes, cells)
+    assert n2.shape == (nodes.shape[0] + 27, 3) and pyr.shape == (6 * 27, 5)
+    assert np.array_equal(pyr[:, 4], np.repeat(nodes.shape[0] + np.arange(27), 6))
+    assert np.allclose(n2[nodes.shape[0]:], nodes[cells].mean(axis=1))
+    p = n2[pyr]
+    nb = np.cross(p[:, 2] - p[:, 0], p[:, 3] - p[:, 1])          # base normal
+    toward = p[:, 4] - p[:, :4].mean(axis=1)
+    assert np.all(np.einsum("ij,ij->i", nb, toward) > 0)
+    h = 2 * math.pi / 3
+    vol = 0.5 * np.linalg.norm(nb, axis=1) * np.abs(np.einsum("ij,ij->i", nb, toward)) / np.linalg.norm(nb, axis=1) / 3
+    assert np.allclose(vol, h ** 3 / 6) and math.isclose(vol.sum(), (2 * math.pi) ** 3, rel_tol=1e-12)
+
+
 @pytest.mark.parametrize("mach", [0.1, 1.25])
 def test_tgv_closed_form_and_uniform_temperature(mach):
     nodes, cells, _ = I.hex_lattice(6)

@@ -148,8 +148,14 @@ MUTANTS = [
      "test_face_quadrature_integrates_bilinear_exactly"),
     ("prism_map_top_triangle", ("T = P[3][d] + a * f1 + a * b * f2;", "T = P[3][d] + a * f1 + b * f2;"),
      "test_face_quadrature_integrates_bilinear_exactly"),
-    ("prism_one_triangle", ("(c->npc == 6 ? (lf < 2 ? 3 : 4) : 3)", "(c->npc == 6 ? (lf < 1 ? 3 : 4) : 3)"),
+    ("prism_one_triangle", ("(lf < 2 ? 3 : 4)", "(lf < 1 ? 3 : 4)"),
      "test_k_exact_reconstruction"),
+    ("pyramid_base_inward", ("{{0,3,2,1},{0,1,4,-1}", "{{0,1,2,3},{0,1,4,-1}"),
+     "test_geometry_closed_surfaces_and_volume"),
+    ("pyramid_map_apex", ("dw[d] = P[4][d] - Q;", "dw[d] = P[4][d] - P[0][d];"),
+     "test_face_quadrature_integrates_bilinear_exactly"),
+    ("rank_test_per_column_only", ("|| !(nv > 1e-8 * sqrt(amax))", ""),
+     "test_degenerate_pyramid_stencils_are_rejected"),
 ]
 
 PY_MUTANTS = [

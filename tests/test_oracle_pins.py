@@ -49,6 +49,13 @@ def jtet_p2():
 
 
 @pytest.fixture(scope="module")
+def jpyr_p2():
+    nodes, cells, box = I.hex_lattice(4, jitter=0.1, seed=6)
+    nodes, pyr = I.split_pyramids(nodes, cells)
+    return nodes, pyr, box, O.Case(nodes, pyr, box, O.Params(order=2, scheme=1))
+
+
+@pytest.fixture(scope="module")
 def jprism_p2():
     nodes, cells, box = I.hex_lattice(5, jitter=0.1, seed=5)
     prisms = I.split_prisms(cells)
@@ -80,6 +87,33 @@ def test_counts_p1_and_tets(jtet_p2):
     assert (ct.K, ct.Mc, ct.nd, ct.Md, ct.nq) == (9, 18, 4, 6, 4)
 
 
+def test_counts_pyramids(jpyr_p2):
+    """Six pyramids per hexahedron (apex at its vertex mean, one per face),
+    five faces each (the base quad, four triangles), every face shared:
+    N = 6n^3, F = 15n^3, of which 3n^3 quads (the hexahedra's faces)."""
+    nodes, cells, box, c = jpyr_p2
+    assert c.n_cells == 6 * 64 and c.n_faces == 15 * 64
+    assert (c.nfc, c.K, c.Mc, c.nd, c.Md, c.nq) == (5, 9, 18, 5, 6, 4)
+    n = np.array([c.face_quad(f)[1].sum(axis=0) for f in range(c.n_faces)])
+    axis = np.abs(n).max(axis=1) / np.linalg.norm(n, axis=1)
+    assert (axis > 0.95).sum() == 3 * 64 and (axis < 0.8).sum() == 12 * 64
+
+
+def test_degenerate_pyramid_stencils_are_rejected():
+    """On the unjittered lattice every member of a pyramid's P2 central
+    stencil has the same mean of one quadratic mode as the cell itself (a
+    zero column of the least-squares matrix): the rank test, taken against
+    the matrix's largest column, rejects it instead of returning a
+    polynomial with 1e13 coefficients; P1 and the jittered lattice pass."""
+    nodes, cells, box = I.hex_lattice(4)
+    nodes, pyr = I.split_pyramids(nodes, cells)
+    U = np.zeros((5, pyr.shape[0]))
+    U[0], U[4] = 1.0, 2.5
+    with pytest.raises(O.OracleError, match="rank-deficient"):
+        O.Case(nodes, pyr, box, O.Params(order=2, scheme=0)).residual(U)
+    assert np.abs(O.Case(nodes, pyr, box, O.Params(order=1, scheme=0)).residual(U)).max() < 1e-13
+
+
 def test_counts_prisms(jprism_p2):
     """Two prisms per hexahedron, five faces each (two triangles, three
     quads), every face shared: N = 2n^3, F = 5n^3, of which 2n^3 triangles;
@@ -94,9 +128,9 @@ def test_counts_prisms(jprism_p2):
 
 
 # ------------------------------------------------------------- geometry ---
-@pytest.mark.parametrize("kind", ["hex", "tet", "prism"])
-def test_geometry_closed_surfaces_and_volume(kind, jhex8_p2, jtet_p2, jprism_p2):
-    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_geometry_closed_surfaces_and_volume(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
+    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     vol, cen, hh = c.geometry()
     assert abs(vol.sum() - (2 * math.pi) ** 3) <= 1e-12 * (2 * math.pi) ** 3
     assert np.all(vol > 0)
@@ -109,12 +143,12 @@ def test_geometry_closed_surfaces_and_volume(kind, jhex8_p2, jtet_p2, jprism_p2)
     assert np.linalg.norm(d, axis=1).max() < 2.0 * hh.max()
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet", "prism"])
-def test_face_area_vectors_point_from_owner_to_neighbour(kind, jhex8_p2, jtet_p2, jprism_p2):
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_face_area_vectors_point_from_owner_to_neighbour(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
     """Eq. 2 sums sigma G_f with G_f taken through dS oriented from the owner
     to the neighbour: every face's total area vector has a positive
     component along the owner -> neighbour (periodic image) centroid offset."""
-    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     fo, fn, sh = c.faces()
     _, cen, _ = c.geometry()
     for f in range(0, c.n_faces, 7):
@@ -138,8 +172,8 @@ def test_uniform_lattice_centroids_exact():
     assert np.isclose(np.linalg.norm(dS), h * h, rtol=1e-14)
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet", "tet_p1", "prism"])
-def test_face_quadrature_integrates_bilinear_exactly(kind, jhex8_p2, jtet_p2, jprism_p2):
+@pytest.mark.parametrize("kind", ["hex", "tet", "tet_p1", "prism", "pyramid"])
+def test_face_quadrature_integrates_bilinear_exactly(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
     """The face rules against the independent volume quadrature, through the
     divergence theorem on every cell: with y = x - x_c (x_c the centroid),
     oint y_j dS_i = V delta_ij and oint y_j y_k dS_i = 0. The 2x2 Gauss rule
@@ -150,7 +184,7 @@ def test_face_quadrature_integrates_bilinear_exactly(kind, jhex8_p2, jtet_p2, jp
         cells = I.split_tets(cells)
         c = O.Case(nodes, cells, box, O.Params(order=1, scheme=0))
     else:
-        nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+        nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     vol, cen, hh = c.geometry()
     fo, fn, sh = c.faces()
     acc = np.zeros((c.n_cells, 3, 3))
@@ -233,7 +267,8 @@ def _poly_eval(p, x):
 @pytest.mark.parametrize(
     "order,scheme,degree,kind",
     [(1, 0, 1, "hex"), (2, 0, 2, "hex"), (2, 1, 1, "hex"), (2, 0, 2, "tet"), (2, 1, 1, "tet"),
-     (1, 0, 1, "prism"), (2, 0, 2, "prism"), (2, 1, 1, "prism")],
+     (1, 0, 1, "prism"), (2, 0, 2, "prism"), (2, 1, 1, "prism"),
+     (1, 0, 1, "pyramid"), (2, 0, 2, "pyramid"), (2, 1, 1, "pyramid")],
 )
 def test_k_exact_reconstruction(order, scheme, degree, kind):
     """Cell averages of any polynomial of degree <= r are reproduced exactly
@@ -245,6 +280,8 @@ def test_k_exact_reconstruction(order, scheme, degree, kind):
         cells = I.split_tets(cells)
     elif kind == "prism":
         cells = I.split_prisms(cells)
+    elif kind == "pyramid":
+        nodes, cells = I.split_pyramids(nodes, cells)
     c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme))
     rng = np.random.default_rng(7)
     vol, cen, hh = c.geometry()
@@ -616,18 +653,18 @@ def test_walls_need_an_inviscid_flow():
 
 
 # ------------------------------------------------------------ invariants ---
-@pytest.mark.parametrize("kind", ["hex", "tet", "prism"])
-def test_free_stream_preservation(kind, jhex8_p2, jtet_p2, jprism_p2):
-    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_free_stream_preservation(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
+    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     U = np.zeros((5, c.n_cells))
     U[0], U[1], U[2], U[3], U[4] = 1.1, 0.3, -0.2, 0.15, 75.0
     R = c.residual(U)
     assert np.abs(R).max() <= 1e-13 * 75.0
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet", "prism"])
-def test_discrete_conservation(kind, jhex8_p2, jtet_p2, jprism_p2):
-    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_discrete_conservation(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
+    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=4)
     R = c.residual(U)
     vol, _, _ = c.geometry()
@@ -636,12 +673,12 @@ def test_discrete_conservation(kind, jhex8_p2, jtet_p2, jprism_p2):
     assert np.all(np.abs(tot) <= 1e-13 * scale)
 
 
-@pytest.mark.parametrize("kind", ["hex", "tet", "prism"])
-def test_residual_of_sampled_cells_equals_the_full_residual(kind, jhex8_p2, jtet_p2, jprism_p2):
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_residual_of_sampled_cells_equals_the_full_residual(kind, jhex8_p2, jtet_p2, jprism_p2, jpyr_p2):
     """The sampled-cell residual (the path the CPU baseline and the full-size
     parity samples take) equals the full residual's columns bit for bit, and
     so do the summed-term magnitudes S."""
-    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2}[kind]
+    nodes, cells, box, c = {"hex": jhex8_p2, "tet": jtet_p2, "prism": jprism_p2, "pyramid": jpyr_p2}[kind]
     U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=6)
     R, S = c.residual_terms(U)
     sel = np.random.default_rng(4).choice(c.n_cells, 37, replace=False)
@@ -1105,7 +1142,9 @@ def test_dissipation_diagnostics_of_plane_waves():
 # ---------------------------------------------------- order of accuracy ---
 def _density_wave_error(n, order, scheme, T=0.05, integrator=0, split=None):
     nodes, cells, box = I.hex_lattice(n)
-    if split is not None:
+    if split is I.split_pyramids:
+        nodes, cells = split(nodes, cells)
+    elif split is not None:
         cells = split(cells)
     c = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=0.0, integrator=integrator))
     p = [1.0, 0.2, 1.0, 0.5, 0.25, 1.0, 0.0, 1.4]
@@ -1139,6 +1178,15 @@ def test_order_density_wave(order, scheme, lo):
     solution): L1 error order -> 2 (P1), -> 3 (P2)."""
     e = [_density_wave_error(n, order, scheme) for n in (8, 16, 32)]
     assert math.log2(e[1] / e[2]) > lo
+
+
+def test_order_density_wave_pyramids_p1():
+    """P1 on pyramids (n = 4, 8, 16): rates 0.96 -> 1.17, rising like the
+    other diagonal splits' (the unjittered lattice's pyramid stencils are
+    rank-deficient at P2, see above)."""
+    e = [_density_wave_error(n, 1, 0, split=I.split_pyramids) for n in (4, 8, 16)]
+    rates = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert rates[1] > rates[0] and rates[1] > 1.1, rates
 
 
 @pytest.mark.parametrize("order,lo", [(1, 1.4), (2, 2.4)])

@@ -57,6 +57,7 @@ def _load():
             lib.orc_surface_sums.argtypes = [P, P]
             lib.orc_stencil.argtypes = [P, I64, C.c_int, P, P, P, P]
             lib.orc_residual.argtypes = [P, P, P]
+            lib.orc_set_scheme_mask.argtypes = [P, P]
             lib.orc_residual_subset.argtypes = [P, P, I64, P, P]
             lib.orc_residual_subset_terms.argtypes = [P, P, I64, P, P, P]
             lib.orc_residual_terms.argtypes = [P, P, P, P]
@@ -186,6 +187,22 @@ class Case:
         A, P = np.zeros((M, K)), np.zeros((K, M))
         self._check(self._lib.orc_stencil(self._h, i, which, _p(mem), _p(sh), _p(A), _p(P)))
         return mem, sh, A, P
+
+    def set_scheme_mask(self, mask):
+        """Per-cell scheme of a CWENOZ case (Sec. 2.2, Eqs. 5-6): cells with a
+        nonzero mask entry keep CWENOZ, the others take the optimal central
+        polynomial p_opt (linear weights).  mask: [n_cells] in the caller's
+        cell order, or None for CWENOZ everywhere.  Every later residual,
+        reconstruction and step of the case follows it."""
+        if mask is None:
+            self._check(self._lib.orc_set_scheme_mask(self._h, None))
+            self._mask = None
+            return
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        if m.shape != (self.n_cells,):
+            raise ValueError(f"mask must have shape ({self.n_cells},)")
+        self._check(self._lib.orc_set_scheme_mask(self._h, _p(m)))
+        self._mask = m
 
     def residual(self, U):
         U = _f64(U)

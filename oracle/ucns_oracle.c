@@ -74,6 +74,8 @@ typedef struct {
   unsigned char *ready;
   unsigned char *dvalid;  /* [N][nd]: directional candidate s exists (no wall on face s) */
   int walls;              /* some box axis is not periodic: its unpaired faces are slip walls */
+  unsigned char *mask;    /* [N] or NULL: per-cell scheme of a CWENOZ case (0: p_opt, the
+                             linear weights; nonzero: CWENOZ), Sec. 2.2, Eqs. 5-6 */
   /* quadrature on [0,1] */
   int ngeo;
   double gx[8], gw[8];
@@ -805,7 +807,9 @@ static void recon_from_values(const orc_case *c, int64_t i, const double Ui[5],
       for (int r = 0; r < c->Mc; r++) s += Pc[k * c->Mc + r] * (Uc[r * 5 + v] - Ui[v]);
       aopt[k] = s;
     }
-    if (c->scheme == 0 || c->nd == 0) {
+    /* a cell that the mask routes to the linear weights keeps p_opt itself
+       (omega_s = lambda_s makes sum_s lambda_s p_s = p_opt, Sec. 2.2) */
+    if (c->scheme == 0 || c->nd == 0 || (c->mask && !c->mask[i])) {
       for (int k = 0; k < c->K; k++) coef[v][k] = aopt[k];
       if (wout) { wout[v * (c->nd + 1)] = 1.0; for (int s = 0; s < c->nd; s++) wout[v * (c->nd + 1) + 1 + s] = 0.0; }
       continue;
@@ -1374,6 +1378,7 @@ void orc_destroy(orc_case *c) {
   free(c->X); free(c->C); free(c->canon); free(c->vol); free(c->cen); free(c->hh); free(c->psib);
   free(c->fo); free(c->fn); free(c->flf); free(c->fsh); free(c->cf); free(c->cs);
   free(c->sc); free(c->scsh); free(c->Pc); free(c->sd); free(c->sdsh); free(c->Pd); free(c->ready); free(c->dvalid);
+  free(c->mask);
   free(c);
 }
 
@@ -1426,6 +1431,21 @@ int orc_stencil(orc_case *c, int64_t i, int which, int64_t *mem, int32_t *sh, do
   }
   lsq_matrix(c, i, M, m, s, K, A);
   memcpy(P, PP, sizeof(double) * K * M);
+  return 0;
+}
+
+/* Per-cell choice of the reconstruction in a CWENOZ case (Sec. 2.2, Eqs.
+   5-6): mask[i] != 0 keeps cell i's CWENOZ polynomial, mask[i] == 0 gives it
+   the optimal central polynomial p_opt (the linear weights).  Copied; NULL
+   restores CWENOZ everywhere.  Every later residual, reconstruction and step
+   of the case follows it. */
+int orc_set_scheme_mask(orc_case *c, const unsigned char *mask) {
+  free(c->mask);
+  c->mask = NULL;
+  if (!mask) return 0;
+  if (c->nd == 0) { set_err("a scheme mask needs a CWENOZ case"); return -1; }
+  c->mask = (unsigned char *)malloc(c->N);
+  memcpy(c->mask, mask, c->N);
   return 0;
 }
 

@@ -26,6 +26,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ucns_oracle.c")
 
 MUTANTS = [
+    ("scheme_mask_sense_inverted", ("(c->mask && !c->mask[i])", "(c->mask && c->mask[i])"),
+     "test_scheme_mask_routes_each_cell"),
+    ("scheme_mask_of_a_stencil_member", ("(c->mask && !c->mask[i])", "(c->mask && !c->mask[c->sc[i * c->Mc]])"),
+     "test_scheme_mask_routes_each_cell"),
     # name, (original text, planted mistake), pins that must catch it
     ("hllc_pressure_dropped", ("F[1 + d] = r * u[d] * un + p * n[d];", "F[1 + d] = r * u[d] * un;"),
      "test_hllc_consistency_contact_upwind_symmetry"),

@@ -313,6 +313,74 @@ def test_cwenoz_degree2_not_exact_but_linear_weights_are():
     assert np.abs(v1 - rv).max() > 1e-9 * np.abs(rv).max()
 
 
+# ------------------------------------------------ per-cell scheme mask ---
+def _face_neighbours(c):
+    fo, fn, _ = c.faces()
+    nb = [[] for _ in range(c.n_cells)]
+    for o, n in zip(fo, fn):
+        nb[o].append(n)
+        nb[n].append(o)
+    return nb
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_scheme_mask_routes_each_cell(kind):
+    """Sec. 2.2, Eqs. 5-6 with a per-cell choice of the polynomial: a flagged
+    cell reconstructs with its CWENOZ weights, an unflagged one takes p_opt,
+    which is the polynomial of the linear scheme (a separate case built with
+    scheme 0, pinned by quadratic k-exactness); so a cell whose own flag and
+    its face neighbours' flags agree has that scheme's residual, bit for bit,
+    and all flags set (none set) give the CWENOZ (linear) residual.  The mask
+    is a half box plus scattered cells, so both kinds of agreeing cells and
+    mixed ones occur."""
+    nodes, cells, box = I.hex_lattice(7 if kind == "hex" else 5, jitter=0.1, seed=8)
+    if kind == "tet":
+        cells = I.split_tets(cells)
+    prm = dict(order=2, Re=1600.0, Mach=0.3)
+    cw = O.Case(nodes, cells, box, O.Params(scheme=1, **prm))
+    cl = O.Case(nodes, cells, box, O.Params(scheme=0, **prm))
+    cm = O.Case(nodes, cells, box, O.Params(scheme=1, **prm))
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=2)
+    assert np.all(np.isfinite(cw.residual(U))) and np.all(np.isfinite(cl.residual(U)))
+    _, cen, _ = cw.geometry()
+    rng = np.random.default_rng(12)
+    mask = (cen[:, 0] < np.pi) | (rng.random(cw.n_cells) < 0.1)
+    cm.set_scheme_mask(mask)
+    kw, kl, km = cw.reconstruct(U), cl.reconstruct(U), cm.reconstruct(U)
+    assert np.array_equal(km[mask], kw[mask]) and np.array_equal(km[~mask], kl[~mask])
+    assert not np.array_equal(kw[mask], kl[mask])  # the two schemes differ on the flagged cells
+    Rw, Rl, Rm = cw.residual(U), cl.residual(U), cm.residual(U)
+    nb = _face_neighbours(cw)
+    all_w = np.array([mask[i] and all(mask[j] for j in nb[i]) for i in range(cw.n_cells)])
+    all_l = np.array([not mask[i] and not any(mask[j] for j in nb[i]) for i in range(cw.n_cells)])
+    assert all_w.sum() > 5 and all_l.sum() > 5
+    assert np.array_equal(Rm[:, all_w], Rw[:, all_w]) and np.array_equal(Rm[:, all_l], Rl[:, all_l])
+    mixed = ~all_w & ~all_l
+    assert np.any(Rm[:, mixed] != Rw[:, mixed]) and np.any(Rm[:, mixed] != Rl[:, mixed])
+    cm.set_scheme_mask(np.ones(cw.n_cells))
+    assert np.array_equal(cm.residual(U), Rw)
+    cm.set_scheme_mask(np.zeros(cw.n_cells))
+    assert np.array_equal(cm.residual(U), Rl)
+    cm.set_scheme_mask(None)
+    assert np.array_equal(cm.residual(U), Rw)
+
+
+def test_scheme_mask_keeps_free_stream_and_conservation():
+    """Any mask: the face fluxes are shared by both sides, so the volume-
+    weighted residual still sums to zero, and a uniform state still has a
+    zero residual (every candidate reproduces a constant)."""
+    nodes, cells, box = I.hex_lattice(6, jitter=0.1, seed=9)
+    c = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Re=1600.0, Mach=0.3))
+    c.set_scheme_mask(np.random.default_rng(2).random(c.n_cells) < 0.4)
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=4)
+    vol, _, _ = c.geometry()
+    R = c.residual(U)
+    assert np.all(np.abs((R * vol).sum(axis=1)) <= 1e-13 * (np.abs(R) * vol).sum(axis=1))
+    U1 = np.zeros((5, c.n_cells))
+    U1[0], U1[1], U1[2], U1[3], U1[4] = 1.1, 0.3, -0.2, 0.15, 75.0
+    assert np.abs(c.residual(U1)).max() <= 1e-13 * 75.0
+
+
 # -------------------------------------------------- smoothness indicator ---
 def test_smoothness_indicator_closed_forms():
     """SI = sum_{1<=|b|<=r} V^(2|b|/3-1) int (d^b p)^2: on a cube of side h

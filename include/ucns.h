@@ -67,8 +67,10 @@ extern "C" {
 
 /* Scheme parameters (Sec. 2.2). */
 typedef struct ucns_params {
-  int32_t order;      /* reconstruction degree r: 1 (P1) or 2 (P2) */
-  int32_t scheme;     /* UCNS_SCHEME_*; CWENOZ needs order 2 */
+  int32_t order;      /* reconstruction degree r: 1 (P1) to 4 (P4); orders 3 and 4
+                         on hexahedra, in the FP64 form */
+  int32_t scheme;     /* UCNS_SCHEME_*; CWENOZ needs order 2 or more (linear
+                         directional candidates at P2 and P3, quadratic at P4) */
   int32_t precision;  /* UCNS_PREC_* */
   int32_t integrator; /* UCNS_RK_* (0: SSP-RK3) */
   double gamma;       /* ratio of specific heats (1.4) */
@@ -129,9 +131,15 @@ int ucns_precompute_host(ucns_mesh* mesh, const ucns_params* params);
  * from the host data of ucns_precompute_host.
  *  which    -1: central stencil (M = central size, K modes);
  *           s in [0, directional stencils): the directional stencil of the
- *           cell's local face s (M = 6, 3 modes).
+ *           cell's local face s (M = directional size, M/2 modes: linear, or
+ *           quadratic at P4).
  *  members  host int64 [M]: caller's cell ids, in the library's order.
- *  P        host float64 [K][M] row-major: P' = A^+ diag(|V_m|) of Eq. 4.
+ *  P        host float64 [modes][M] row-major: P' = A^+ diag(|V_m|) of Eq. 4.
+ *           Row k belongs to the basis monomial psi_k = xi^e_k, xi =
+ *           (x - x_i)/|V_i|^(1/3): x y z xx yy zz xy xz yz (P2), then the
+ *           cubics xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz (P3), then the
+ *           quartics xxxx xxxy xxxz xxyy xxyz xxzz xyyy xyyz xyzz xzzz yyyy
+ *           yyyz yyzz yzzz zzzz (P4).
  * Errors: STATE (no host precompute), INVALID_ARG. */
 int ucns_stencil(const ucns_mesh* mesh, int64_t cell, int32_t which, int64_t* members, double* P);
 
@@ -172,6 +180,23 @@ int ucns_rk_steps_host(ucns_mesh* mesh, double* U_host, int32_t n_steps, double*
  * (synchronises the stream).  UCNS_OK or UCNS_ERR_NONPHYSICAL. */
 int ucns_check_state(ucns_mesh* mesh, void* stream);
 
+/* Measured arithmetic throughput of this GPU (no counterpart in the paper;
+ * the denominators of the kernels' ALU rooflines): which = 0 FP32 FMA
+ * (scalar), 1 FP64 FMA, 2 FP32 FMA in packed pairs; *flops_per_s (host)
+ * receives the best of three timed launches of 8 blocks per SM x 256 threads,
+ * each thread running 8 independent FMA chains (an FMA = 2 flops); *n_sm
+ * (may be NULL) the SM count.  Synchronises.  Errors: INVALID_ARG, CUDA. */
+int ucns_alu_peak(int32_t which, double* flops_per_s, int32_t* n_sm, void* stream);
+
+/* Exercises the give-up path of the reconstruction's bounded waits (no
+ * counterpart in the paper): one thread waits about a millisecond for a phase
+ * of a fresh mbarrier that nothing completes -- no copy or MMA is in flight --
+ * then sets the timeout bit of the mesh's device error word, which this call
+ * reads and clears.  Returns UCNS_ERR_TIMEOUT, the status a real stalled bulk
+ * copy gives at the next synchronising call; a following ucns_check_state
+ * returns UCNS_OK.  Errors: STATE, INVALID_ARG, CUDA. */
+int ucns_probe_bounded_wait(ucns_mesh* mesh, void* stream);
+
 /* The CFL time step of U written to device memory, allocating nothing.
  * No counterpart in the paper: this serves callers that must not allocate
  * device memory on their call path -- code running under a fixed device-memory
@@ -185,8 +210,10 @@ int ucns_check_state(ucns_mesh* mesh, void* stream);
  * process exits; meshes above 8,388,608 cells are rejected with
  * UCNS_ERR_INVALID_ARG.  The first call on a device (with that device
  * current) resolves the array's device address, so make that first call
- * before any stream capture.  Every call shares the array; each call writes
- * the partials it reads, so nothing needs clearing, but calls that overlap on
+ * before any stream capture; the address is kept for the life of the process,
+ * so do not use this call after a context reset (cudaDeviceReset).  Every
+ * call shares the array; each call writes the partials it reads, so nothing
+ * needs clearing, but calls that overlap on
  * the GPU (e.g. on two streams) race on it.  A non-physical state sets the
  * mesh's error word as in ucns_time_step (read it with ucns_check_state).
  * Errors: INVALID_ARG, STATE, CUDA. */
@@ -233,6 +260,12 @@ int ucns_mlp_get_params(const ucns_mlp* mlp, float* theta);
 int ucns_mlp_set_params(ucns_mlp* mlp, const float* theta);
 /* Logits z (device float[n]) of n feature rows X (device BF16 [n][32]). */
 int ucns_mlp_forward(ucns_mlp* mlp, const void* X, int64_t n, float* z, void* stream);
+/* The same forward pass, also writing the first hidden layer as the second
+ * layer's product reads it: h1 = bf16(relu(W1 x + b1)) (device BF16
+ * [n][64], 16-byte aligned), with the logits z (device float[n]).  For
+ * inspecting the network, e.g. counting where its FP32 accumulation rounds
+ * h1 to the other BF16 neighbour than an exact evaluation would. */
+int ucns_mlp_hidden(ucns_mlp* mlp, const void* X, int64_t n, void* h1, float* z, void* stream);
 /* Gradient (device float[UCNS_MLP_PARAMS]) of the class-weighted binary
  * cross-entropy L = (1/n) sum_i c(y_i) [softplus(z_i) - y_i z_i], c(1) = w_pos,
  * c(0) = w_neg, over n rows X with labels y (device float[n], 0 or 1).
@@ -247,6 +280,12 @@ int ucns_mlp_train(ucns_mlp* mlp, const void* X, const float* y, int64_t n, int6
 /* Read and clear the network's device error word (synchronises): UCNS_OK or
  * UCNS_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
 int ucns_mlp_check(ucns_mlp* mlp, void* stream);
+/* Exercises the give-up path of the network's bounded mbarrier waits: one
+ * thread waits about a millisecond for a phase of a fresh mbarrier that no
+ * MMA commit completes (nothing is issued), sets the network's error word,
+ * and ucns_mlp_check reads and clears it.  Returns UCNS_ERR_TIMEOUT; a
+ * following ucns_mlp_check returns UCNS_OK.  Errors: INVALID_ARG, CUDA. */
+int ucns_mlp_probe_bounded_wait(ucns_mlp* mlp, void* stream);
 
 /* The 32 features of every cell of U (device [5][n_cells]), as BF16 rows into
  * X (device [n_cells][32], internal order) and, if Xf is not NULL, as FP32
@@ -271,16 +310,60 @@ int ucns_gate_enable(ucns_mesh* mesh, int32_t enable);
  * the gate's error).  The features and the network are evaluated at the first
  * gated step and then every eval_every-th ucns_rk_step (>= 1); the flags in
  * between are reused.  With check_every > 0, every check_every-th gated
- * ucns_rk_step first evaluates the gated and the full residual of its input
- * state and their kinetic-energy rates dKE/dt = sum_i V_i (u_i . R_m,i -
- * |u_i|^2 R_rho,i / 2) / sum_i V_i; if they differ by more than bound
- * (relative), the gate is switched off for the rest of the run.  A check
- * synchronises the stream.  check_every = 0 disables the checks.  Defaults:
- * eval_every 1, check_every 0. */
-int ucns_gate_configure(ucns_mesh* mesh, int32_t eval_every, int32_t check_every, double bound);
-/* Run one check now on U: *rel_diff (host) receives the relative difference
- * of the two rates, *disabled (may be NULL) whether the gate is now off. */
-int ucns_gate_check(ucns_mesh* mesh, const double* U, double* rel_diff, int32_t* disabled, void* stream);
+ * ucns_rk_step first reconstructs its input state both gated and with the
+ * full scheme, evaluates both residuals, and forms four measures of their
+ * difference, with r_i = V_i (u_i . R_m,i - |u_i|^2 R_rho,i / 2) the cells'
+ * kinetic-energy rates under each:
+ *   [0] |sum r_gated - sum r_full| / |sum r_full|, the relative error of
+ *       dKE/dt (ill-conditioned where dKE/dt is near zero);
+ *   [1] sum |r_gated - r_full| / sum |r_full|, the local difference, which
+ *       differences of opposite sign cannot hide;
+ *   [2] a running estimate of the relative error the gate puts into the
+ *       kinetic-energy history: each check adds |sum r_gated - sum r_full| /
+ *       sum V (the difference of the volume-averaged dKE/dt) times
+ *       check_every times the CFL time step of the state, divided by the
+ *       volume-averaged kinetic energy (KE's drift from the full scheme's
+ *       until the next check, to first order);
+ *   [3] |eps_gated - eps_full| / eps_full, eps = eps_s + eps_d the total
+ *       dissipation (ucns_diag) of the two reconstructions of the state: the
+ *       gate's error in the dissipation history at that state.
+ * The gate is switched off for the rest of the run when [2] or [3] exceeds
+ * `bound` (the target error of the kinetic-energy and dissipation
+ * histories), or [0] exceeds bound_rate (bound_rate = 0: not used).  A check
+ * synchronises the stream.  check_every = 0 disables the checks.  Resets the
+ * step and check counters and the running estimate.  Defaults: eval_every 1,
+ * check_every 0, bound 1e-4, bound_rate 0. */
+int ucns_gate_configure(ucns_mesh* mesh, int32_t eval_every, int32_t check_every, double bound,
+                        double bound_rate);
+/* Run one check now on U (counted as check_every steps, at least 1): the four
+ * measures above into host double[4] `measures`, and *disabled (may be NULL)
+ * whether the gate is now off. */
+int ucns_gate_check(ucns_mesh* mesh, const double* U, double* measures, int32_t* disabled, void* stream);
+/* State of the gate (host outputs, each may be NULL): *enabled whether it is
+ * on (a network attached and not switched off); counts[0..2] = gated steps
+ * and checks since ucns_gate_configure, and the gated step at which a check
+ * switched it off (-1: none); last[0..3] = the four measures of the last
+ * check (-1 before the first).  No device work. */
+int ucns_gate_status(const ucns_mesh* mesh, int32_t* enabled, int64_t* counts, double* last);
+
+/* Caller-given flags in place of the network (Sec. 2.2, Eqs. 5-6 with a
+ * per-cell choice of the polynomial): flags is device uint8 [n_cells] in the
+ * internal order, nonzero = the cell keeps CWENOZ, 0 = the cell takes the
+ * optimal central polynomial p_opt (linear weights).  Copied on `stream`
+ * (asynchronous; the caller's buffer may be reused once the stream has passed
+ * this point).  While set, every ucns_residual / ucns_rk_step(s) of the mesh
+ * uses these flags and neither the features, the network nor the plain-scheme
+ * check run (an attached network is kept but idle); ucns_diagnostics and
+ * ucns_gate_labels still use the full scheme.  flags = NULL returns to the
+ * network (or to CWENOZ everywhere without one).  Lets a caller supply its
+ * own troubled-cell indicator, and a test drive the gated kernels with any
+ * mask.  Needs a P2 CWENOZ mesh; allocates the gate's buffers on first use.
+ * Errors: STATE, INVALID_ARG, NOMEM, CUDA. */
+int ucns_gate_set_flags(ucns_mesh* mesh, const uint8_t* flags, void* stream);
+/* Copy the flags of the last gate evaluation (or the caller's flags) to
+ * device uint8 [n_cells] `flags` (internal order), asynchronously on
+ * `stream`.  Errors: STATE (no flags yet), INVALID_ARG, CUDA. */
+int ucns_gate_flags(ucns_mesh* mesh, uint8_t* flags, void* stream);
 
 /* Number of cells the last gate evaluation routed to CWENOZ (synchronises). */
 int ucns_gate_flagged(ucns_mesh* mesh, int64_t* n_flagged, void* stream);

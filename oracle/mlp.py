@@ -46,14 +46,15 @@ def flatten(p: dict) -> np.ndarray:
     return np.concatenate([np.asarray(p[n], dtype=np.float64).ravel() for n in ORDER])
 
 
-def forward(theta, X, bf16_round: bool = False):
-    """Logits z [n] and the activations needed by backward."""
+def forward(theta, X, bf16_round: bool = False, h1=None):
+    """Logits z [n] and the activations needed by backward.  h1, if given,
+    replaces the rounded first hidden layer fed to the second layer (e.g. a
+    device's own BF16 rounding of it)."""
     p = unflatten(theta)
     r = bf16 if bf16_round else (lambda a: np.asarray(a, dtype=np.float64))
     x = r(X)
     a1 = x @ r(p["W1"]).T + p["b1"]
-    h1 = np.maximum(a1, 0.0)
-    h1r = r(h1)
+    h1r = r(np.maximum(a1, 0.0)) if h1 is None else np.asarray(h1, dtype=np.float64)
     a2 = h1r @ r(p["W2"]).T + p["b2"]
     h2 = np.maximum(a2, 0.0)
     z = h2 @ r(p["w3"]) + p["b3"][0]
@@ -68,26 +69,30 @@ def loss(theta, X, y, w_pos=1.0, w_neg=1.0, bf16_round=False) -> float:
     return float(np.mean(c * (sp - y * z)))
 
 
-def grad(theta, X, y, w_pos=1.0, w_neg=1.0, bf16_round=False) -> np.ndarray:
-    """Gradient of loss() with respect to the flat parameter vector."""
+def grad(theta, X, y, w_pos=1.0, w_neg=1.0, bf16_round=False, h1=None, terms=False) -> np.ndarray:
+    """Gradient of loss() with respect to the flat parameter vector (h1 as in
+    forward()).  terms=True returns instead, per parameter, the sum of the
+    magnitudes of the per-sample terms whose signed sum is that gradient
+    entry (the scale of its rounding error)."""
     p = unflatten(theta)
     r = bf16 if bf16_round else (lambda a: np.asarray(a, dtype=np.float64))
-    z, a = forward(theta, X, bf16_round)
+    z, a = forward(theta, X, bf16_round, h1)
     n = X.shape[0]
     c = np.where(y > 0.5, w_pos, w_neg)
     s = 1.0 / (1.0 + np.exp(-z))
     dz = c * (s - y) / n
+    f = np.abs if terms else (lambda v: v)
     g = {}
-    g["w3"] = a["h2"].T @ dz
-    g["b3"] = np.array([dz.sum()])
+    g["w3"] = f(a["h2"]).T @ f(dz)
+    g["b3"] = np.array([f(dz).sum()])
     dh2 = np.outer(dz, r(p["w3"])) * (a["a2"] > 0)
     dh2r = r(dh2)
-    g["W2"] = dh2r.T @ a["h1r"]
-    g["b2"] = dh2.sum(axis=0)
+    g["W2"] = f(dh2r).T @ f(a["h1r"])
+    g["b2"] = f(dh2).sum(axis=0)
     dh1 = (dh2r @ r(p["W2"])) * (a["a1"] > 0)
     dh1r = r(dh1)
-    g["W1"] = dh1r.T @ a["x"]
-    g["b1"] = dh1.sum(axis=0)
+    g["W1"] = f(dh1r).T @ f(a["x"])
+    g["b1"] = f(dh1).sum(axis=0)
     return flatten(g)
 
 

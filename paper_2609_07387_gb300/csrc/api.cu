@@ -12,6 +12,7 @@
 #include "kernels.cuh"
 #include "kernels_mixed.cuh"
 #include "kernels_gate.cuh"
+#include "kernels_ho.cuh"
 #include "mlp_internal.hpp"
 #include "ucns_internal.hpp"
 
@@ -215,8 +216,66 @@ int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   return UCNS_OK;
 }
 
+// P3 / P4 (FP64, hexahedra)
+int launch_recon_ho(ucns_mesh* m, const double* U, cudaStream_t s) {
+  ReconArgsHO a;
+  a.U = U;
+  a.sc = m->d.sc;
+  a.Pc = m->d.Pc;
+  a.sd = m->d.sd;
+  a.Pd = m->d.Pd;
+  a.Msi = m->d.Msi;
+  a.psib = m->d.psib;
+  a.inv_h = m->d.inv_h;
+  a.coef = m->d.coef;
+  a.N = (int)m->N;
+  const double lsum = m->P.lambda_central + m->nd;
+  a.lam0 = m->P.lambda_central / lsum;
+  a.lams = 1.0 / lsum;
+  a.eps = m->P.epsilon;
+  const unsigned g = nblocks((size_t)m->N * 5, 128);
+  const bool weno = m->nd > 0;
+  if (m->K == 19) {
+    if (weno) k_recon_ho<3, true><<<g, 128, 0, s>>>(a);
+    else k_recon_ho<3, false><<<g, 128, 0, s>>>(a);
+  } else {
+    if (weno) k_recon_ho<4, true><<<g, 128, 0, s>>>(a);
+    else k_recon_ho<4, false><<<g, 128, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_face_ho(ucns_mesh* m, cudaStream_t s) {
+  FaceArgs a;
+  a.coef = m->d.coef;
+  a.fq = m->d.fq;
+  a.fpen = m->d.fpen;
+  a.fo = m->d.fo;
+  a.fn = m->d.fn;
+  a.inv_h = m->d.inv_h;
+  a.G = m->d.G;
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.c = flux_const(m->P);
+  const bool visc = m->P.reynolds > 0.0;
+  const int fpw = 32 / m->nq;  // faces per warp
+  const size_t threads = (size_t)((m->F + fpw - 1) / fpw) * 32;
+  const unsigned g = nblocks(threads, 128);
+  if (m->K == 19) {
+    if (visc) k_face_ho<3, true><<<g, 128, 0, s>>>(a);
+    else k_face_ho<3, false><<<g, 128, 0, s>>>(a);
+  } else {
+    if (visc) k_face_ho<4, true><<<g, 128, 0, s>>>(a);
+    else k_face_ho<4, false><<<g, 128, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   if (mixed(m)) return launch_recon_mx(m, U, s);
+  if (m->K > 9) return launch_recon_ho(m, U, s);
   ReconArgs a;
   a.U = U;
   a.sc = m->d.sc;
@@ -253,6 +312,7 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
 
 int launch_face_raw(ucns_mesh* m, cudaStream_t s) {
   if (mixed(m)) return launch_face_mx(m, s);
+  if (m->K > 9) return launch_face_ho(m, s);
   FaceArgs a;
   a.coef = m->d.coef;
   a.fq = m->d.fq;
@@ -352,6 +412,16 @@ int launch_rk54_raw(ucns_mesh* m, int stage, const double* U0, const double* Us,
     default: UCNS_RK54(5); break;
   }
 #undef UCNS_RK54
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+// the CFL time step of U into out[0] (device), partial minima in m->d.red
+int launch_dt_to(ucns_mesh* m, const double* U, double* out, cudaStream_t s) {
+  const ucns_params& p = m->P;
+  const double vc = p.reynolds > 0.0 ? p.prandtl / (2.0 * p.gamma * (1.0 / p.reynolds)) : 0.0;
+  k_dt_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.dtlen, (int)m->N, p.gamma, vc, m->d.red, m->d.err);
+  k_dt_final<<<1, kRedThreads, 0, s>>>(m->d.red, m->d.red_blocks, p.cfl, out);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -468,6 +538,10 @@ int launch_features(ucns_mesh* m, const double* U, void* X, float* Xf, cudaStrea
 // mixed form this leaves the float pair of U in m->d.Uhl
 int gate_eval(ucns_mesh* m, const double* U, cudaStream_t s, bool* split_done = nullptr) {
   m->gate_eval_active = false;
+  if (m->gate_fixed) {  // the caller's flags stand in for the network's
+    m->gate_eval_active = true;
+    return UCNS_OK;
+  }
   if (!m->gate_on || !m->mlp) return UCNS_OK;
   const bool have_pair = split_done && *split_done;
   int rc = timed(m, kKindFeatures, s, [&] { return launch_features(m, U, m->gate_X, nullptr, s, !have_pair); });
@@ -495,27 +569,73 @@ int residual_into(ucns_mesh* m, const double* U, double* R, cudaStream_t s) {
   return UCNS_OK;
 }
 
-// gated vs full residual of U through their kinetic-energy rates
-int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s) {
+// Diagnostic sums [V KE, V |curl u|^2, V (div u)^2, V] of the coefficients
+// the last reconstruction left, into out[0..3] (device)
+int diag_sums_into(ucns_mesh* m, const double* U, double* out, cudaStream_t s) {
+  if (mixed(m))
+    k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC, m->d.vol,
+                                                             (int)m->N, m->d.red);
+  else
+    k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h, (int)m->N, m->d.red);
+  k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, out);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+// The plain-scheme check of the gate on the state U: the gated and the full
+// reconstruction and residual of U, and four measures of their difference:
+//  rel[0]  |sum r_gated - sum r_full| / |sum r_full|, r_i = V_i (u . R_m -
+//          |u|^2 R_rho / 2) the cells' kinetic-energy rates (the relative error
+//          of dKE/dt; ill-conditioned where dKE/dt is near zero);
+//  rel[1]  sum |r_gated - r_full| / sum |r_full| (local, cannot cancel);
+//  rel[2]  the running estimate of the KE history's relative error: every
+//          check adds |sum r_gated - sum r_full| / sum V, the difference of
+//          the volume-averaged dKE/dt, times (steps until the next check) * dt
+//          / KE, the drift of KE from the full scheme's over that interval to
+//          first order;
+//  rel[3]  |eps_gated - eps_full| / eps_full, eps = eps_s + eps_d the total
+//          dissipation of the two reconstructions of U (the dissipation
+//          history's error from the gate at this state).
+// The gate goes off when rel[2] or rel[3] exceeds the bound, or rel[0] exceeds
+// the optional rate bound (> 0).  `steps` is the interval to the next check.
+int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s, int steps) {
   int rc;
   const size_t n5 = (size_t)5 * m->N;
-  if (!m->gate_R && (rc = alloc(&m->gate_R, 2 * n5))) return rc;
+  if (!m->gate_R && (rc = alloc(&m->gate_R, 2 * n5 + 16))) return rc;
+  double* sums = m->gate_R + 2 * n5;  // [0..3] gated diagnostics, [4..7] full, [8..12] KE rates, [13] dt
   if ((rc = gate_eval(m, U, s)) || (rc = residual_into(m, U, m->gate_R, s))) return rc;
+  rc = timed(m, kKindOther, s, [&] { return diag_sums_into(m, U, sums, s); });
+  if (rc) return rc;
   m->gate_eval_active = false;
   if ((rc = residual_into(m, U, m->gate_R + n5, s))) return rc;
   rc = timed(m, kKindOther, s, [&] {
+    int r = diag_sums_into(m, U, sums + 4, s);
+    if (r) return r;
     k_ke_rate_partial<<<m->d.red_blocks, 256, 0, s>>>(U, m->gate_R, m->gate_R + n5, m->d.vol, (int)m->N, m->d.red);
-    k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, m->d.G);
+    k_sum_partials<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, kRedStride, kKeRateSums, sums + 8);
     UCNS_CUDA(cudaGetLastError());
-    return UCNS_OK;
+    return launch_dt_to(m, U, sums + 13, s);  // the CFL time step of U, apart from the solver's own
   });
   if (rc) return rc;
-  double h[4];
-  UCNS_CUDA(cudaMemcpyAsync(h, m->d.G, sizeof h, cudaMemcpyDeviceToHost, s));
+  double h[14];
+  UCNS_CUDA(cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, s));
   UCNS_CUDA(cudaStreamSynchronize(s));
-  const double a = h[0] / h[2], b = h[1] / h[2];
-  *rel = std::fabs(a - b) / std::fmax(std::fabs(b), 1e-300);
-  if (!(*rel <= m->gate_bound)) m->gate_on = false;
+  const double a = h[8] / h[10], b = h[9] / h[10];
+  rel[0] = std::fabs(a - b) / std::fmax(std::fabs(b), 1e-300);
+  rel[1] = h[11] / std::fmax(h[12], 1e-300);
+  const double ke = h[4] / h[7];
+  m->gate_ke_err += std::fabs(a - b) * (double)std::max(steps, 1) * h[13] / std::fmax(ke, 1e-300);
+  rel[2] = m->gate_ke_err;
+  const double eg = h[1] + (4.0 / 3.0) * h[2], ef = h[5] + (4.0 / 3.0) * h[6];  // (Re and volume cancel)
+  rel[3] = std::fabs(eg - ef) / std::fmax(std::fabs(ef), 1e-300);
+  for (int q = 0; q < 4; q++) m->gate_last[q] = rel[q];
+  m->gate_checks++;
+  const bool bad = !(rel[2] <= m->gate_bound) || !(rel[3] <= m->gate_bound) ||
+                   (m->gate_bound_rate > 0.0 && !(rel[0] <= m->gate_bound_rate));
+  if (bad) {
+    m->gate_on = false;
+    m->gate_off_step = m->gate_steps;
+  }
   return UCNS_OK;
 }
 
@@ -529,16 +649,16 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
   double* W = m->d.Ustage;
   const int64_t step = m->gate_steps;
   bool split_done = pair_fresh, checked = false;
-  if (m->gate_on && m->mlp && m->gate_check_every > 0 && step % m->gate_check_every == 0) {
-    double rel = 0.0;
-    if ((rc = gate_check(m, U, &rel, s))) return rc;
+  if (!m->gate_fixed && m->gate_on && m->mlp && m->gate_check_every > 0 && step % m->gate_check_every == 0) {
+    double rel[4];
+    if ((rc = gate_check(m, U, rel, s, m->gate_check_every))) return rc;
     // the check evaluated the flags on this very state (and left its float pair in place)
     checked = m->gate_on;
     m->gate_flags_valid = checked;
     split_done = split_done || mixed(m);
   }
   if (m->gate_on && m->mlp) m->gate_steps++;
-  if (m->gate_on && m->mlp && m->gate_flags_valid && (checked || step % m->gate_eval_every != 0)) {
+  if (!m->gate_fixed && m->gate_on && m->mlp && m->gate_flags_valid && (checked || step % m->gate_eval_every != 0)) {
     m->gate_eval_active = true;  // the flags of the check, or of the last evaluation
   } else {
     if ((rc = gate_eval(m, U, s, &split_done))) return rc;  // flags of U^n serve all three stages
@@ -581,6 +701,7 @@ int read_error_word(ucns_mesh* m, cudaStream_t s) {
 // The time-step reduction into caller-chosen scratch and output (used by the
 // allocation-free entry point in noalloc.cu): one partial per block of
 // kRedThreads cells, nblocks of them, then the CFL minimum into dt_out[0].
+static_assert(kRedThreads == kDtBlockCells, "noalloc.cu sizes its partials by the reduction's block size");
 int launch_dt_into(const ucns_mesh* m, const double* U, double* partials, int nblocks, double* dt_out,
                    cudaStream_t s) {
   const ucns_params& p = m->P;
@@ -609,8 +730,9 @@ void device_free(ucns_mesh* m) {
   m->gate_flag = nullptr;
   m->gate_count = nullptr;
   m->gate_eval_active = false;
+  m->gate_fixed = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
+  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
@@ -670,13 +792,16 @@ int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_n
 
 static int check_params(const ucns_mesh* m, const ucns_params* p) {
   if (!m || !p) return fail(UCNS_ERR_INVALID_ARG, "mesh or params is NULL");
-  if (p->order != 1 && p->order != 2) return fail(UCNS_ERR_INVALID_ARG, "order must be 1 or 2");
+  if (p->order < 1 || p->order > 4) return fail(UCNS_ERR_INVALID_ARG, "order must be 1, 2, 3 or 4");
   if (p->scheme != UCNS_SCHEME_LINEAR && p->scheme != UCNS_SCHEME_CWENOZ)
     return fail(UCNS_ERR_INVALID_ARG, "unknown scheme");
-  if (p->scheme == UCNS_SCHEME_CWENOZ && p->order != 2)
-    return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2");
+  if (p->scheme == UCNS_SCHEME_CWENOZ && p->order < 2)
+    return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2 or more");
   if (p->precision != UCNS_PREC_FP64 && p->precision != UCNS_PREC_MIXED)
     return fail(UCNS_ERR_INVALID_ARG, "unknown precision mode");
+  if (p->precision == UCNS_PREC_MIXED && p->order > 2)
+    return fail(UCNS_ERR_INVALID_ARG, "the mixed form is built for orders 1 and 2");
+  if (p->order > 2 && m->npc != 8) return fail(UCNS_ERR_INVALID_ARG, "orders 3 and 4 are built for hexahedra only");
   if (p->integrator != UCNS_RK_SSP3 && p->integrator != UCNS_RK_SSP54)
     return fail(UCNS_ERR_INVALID_ARG, "unknown integrator");
   if (!(p->gamma > 1.0) || !(p->mach > 0.0) || !(p->cfl > 0.0) || !(p->lambda_central > 0.0) ||
@@ -714,7 +839,7 @@ int ucns_stencil(const ucns_mesh* m, int64_t cell, int32_t which, int64_t* membe
   } else {
     for (int r = 0; r < m->Md; r++) {
       members[r] = m->perm[h.sd[((size_t)which * m->Md + r) * N + i]];
-      for (int k = 0; k < 3; k++) P[k * m->Md + r] = h.Pd[(((size_t)which * 3 + k) * m->Md + r) * N + i];
+      for (int k = 0; k < m->Kd; k++) P[k * m->Md + r] = h.Pd[(((size_t)which * m->Kd + k) * m->Md + r) * N + i];
     }
   }
   return UCNS_OK;
@@ -766,13 +891,14 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
       return rc;
     }
   } else if ((rc = upload(&d.Pc, h.Pc)) || (rc = upload(&d.Pd, h.Pd)) || (rc = upload(&d.fq, h.fq)) ||
-             (rc = upload(&d.fpen, h.fpen)) || (rc = alloc(&d.coef, (size_t)m->NC * m->N * 5))) {
+             (rc = upload(&d.fpen, h.fpen)) || (rc = upload(&d.Msi, h.Msi)) || (rc = upload(&d.psib, h.psib)) ||
+             (rc = alloc(&d.coef, (size_t)m->NC * m->N * 5))) {
     device_free(m);
     return rc;
   }
   d.red_blocks = 4 * 152;
   if ((rc = alloc(&d.G, (size_t)5 * m->F)) ||
-      (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)4 * d.red_blocks)) ||
+      (rc = alloc(&d.Ustage, (size_t)5 * m->N)) || (rc = alloc(&d.red, (size_t)kRedStride * d.red_blocks)) ||
       (p->integrator == UCNS_RK_SSP54 && (rc = alloc(&d.Uacc, (size_t)5 * m->N))) ||
       (rc = alloc(&d.dt, 2)) || (rc = alloc(&d.err, 1)) || (rc = alloc(&d.dt_part, (size_t)nblocks(m->N))) ||
       (rc = alloc(&d.dt_count, 1))) {
@@ -879,6 +1005,52 @@ int ucns_check_state(ucns_mesh* m, void* stream) {
   return read_error_word(m, (cudaStream_t)stream);
 }
 
+int ucns_alu_peak(int32_t which, double* flops_per_s, int32_t* n_sm, void* stream) {
+  if (which < 0 || which > 2 || !flops_per_s) return fail(UCNS_ERR_INVALID_ARG, "which in 0..2, flops_per_s non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  UCNS_CUDA(cudaGetDevice(&dev));
+  UCNS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (n_sm) *n_sm = sms;
+  const int blocks = sms * 8, threads = 256;
+  const int iters = which == 1 ? 1 << 12 : 1 << 15;
+  cudaEvent_t e0, e1;
+  UCNS_CUDA(cudaEventCreate(&e0));
+  UCNS_CUDA(cudaEventCreate(&e1));
+  double best = 0.0;
+  for (int rep = 0; rep < 4; rep++) {  // the first launch warms up
+    cudaEventRecord(e0, s);
+    if (which == 0) k_peak_ffma<<<blocks, threads, 0, s>>>(iters, 1.000001f);
+    else if (which == 1) k_peak_dfma<<<blocks, threads, 0, s>>>(iters, 1.000001);
+    else k_peak_ffma2<<<blocks, threads, 0, s>>>(iters, 1.000001f);
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(UCNS_ERR_CUDA, std::string("peak kernel: ") + cudaGetErrorString(e));
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double fl = 2.0 * kPeakChains * (which == 2 ? 2.0 : 1.0) * (double)iters * blocks * threads;
+    if (rep > 0) best = std::fmax(best, fl / (ms * 1e-3));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  UCNS_CUDA(cudaGetLastError());
+  *flops_per_s = best;
+  return UCNS_OK;
+}
+
+int ucns_probe_bounded_wait(ucns_mesh* m, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_bulk_wait_probe<<<1, 32, 0, s>>>(m->d.err, 1ll << 21);  // ~1 ms at 2 GHz
+  UCNS_CUDA(cudaGetLastError());
+  return read_error_word(m, s);
+}
+
 int ucns_time_step(ucns_mesh* m, const double* U, double* dt, void* stream) {
   int rc = check_ready(m);
   if (rc) return rc;
@@ -969,7 +1141,7 @@ int ucns_gate_labels(ucns_mesh* m, const double* U, float* dev, void* stream) {
   int rc = check_ready(m);
   if (rc) return rc;
   if (!U || !dev) return fail(UCNS_ERR_INVALID_ARG, "U or dev is NULL");
-  if (mixed(m) || m->nd == 0) return fail(UCNS_ERR_INVALID_ARG, "labels need an FP64 CWENOZ mesh");
+  if (mixed(m) || m->nd == 0 || m->K != 9) return fail(UCNS_ERR_INVALID_ARG, "labels need an FP64 P2 CWENOZ mesh");
   cudaStream_t s = (cudaStream_t)stream;
   UCNS_CUDA(cudaMemsetAsync(dev, 0, sizeof(float) * m->N, s));
   m->gate_eval_active = false;
@@ -979,15 +1151,22 @@ int ucns_gate_labels(ucns_mesh* m, const double* U, float* dev, void* stream) {
   return rc;
 }
 
-int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
-  int rc = check_ready(m);
-  if (rc) return rc;
-  if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
-  if (mlp && !m->gate_X) {
+// the gate's device buffers (features, flags, counter), once per mesh
+static int gate_buffers(ucns_mesh* m) {
+  int rc;
+  if (!m->gate_X) {
     if ((rc = alloc((uint8_t**)&m->gate_X, (size_t)m->N * 64)) || (rc = alloc(&m->gate_flag, (size_t)m->N)) ||
         (rc = alloc(&m->gate_count, 1)))
       return rc;
   }
+  return UCNS_OK;
+}
+
+int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
+  if (mlp && (rc = gate_buffers(m))) return rc;
   m->mlp = mlp;
   m->gate_thr = threshold;
   m->gate_flags_valid = false;
@@ -1001,19 +1180,25 @@ int ucns_gate_enable(ucns_mesh* m, int32_t enable) {
   if (enable && !m->mlp) return fail(UCNS_ERR_STATE, "no network attached");
   m->gate_on = enable != 0;
   m->gate_flags_valid = false;
+  if (m->gate_on) m->gate_off_step = -1;
   return UCNS_OK;
 }
 
-int ucns_gate_configure(ucns_mesh* m, int32_t eval_every, int32_t check_every, double bound) {
+int ucns_gate_configure(ucns_mesh* m, int32_t eval_every, int32_t check_every, double bound, double bound_rate) {
   int rc = check_ready(m);
   if (rc) return rc;
-  if (eval_every < 1 || check_every < 0 || !(bound > 0.0))
-    return fail(UCNS_ERR_INVALID_ARG, "eval_every >= 1, check_every >= 0 and bound > 0");
+  if (eval_every < 1 || check_every < 0 || !(bound > 0.0) || !(bound_rate >= 0.0))
+    return fail(UCNS_ERR_INVALID_ARG, "eval_every >= 1, check_every >= 0, bound > 0 and bound_rate >= 0");
   m->gate_eval_every = eval_every;
   m->gate_flags_valid = false;
   m->gate_check_every = check_every;
   m->gate_bound = bound;
+  m->gate_bound_rate = bound_rate;
   m->gate_steps = 0;
+  m->gate_checks = 0;
+  m->gate_off_step = -1;
+  m->gate_ke_err = 0.0;
+  for (int q = 0; q < 4; q++) m->gate_last[q] = -1.0;
   return UCNS_OK;
 }
 
@@ -1022,9 +1207,47 @@ int ucns_gate_check(ucns_mesh* m, const double* U, double* rel_diff, int32_t* di
   if (rc) return rc;
   if (!U || !rel_diff) return fail(UCNS_ERR_INVALID_ARG, "U or rel_diff is NULL");
   if (!m->mlp || !m->gate_on) return fail(UCNS_ERR_STATE, "the gate is not enabled");
-  rc = gate_check(m, U, rel_diff, (cudaStream_t)stream);
+  rc = gate_check(m, U, rel_diff, (cudaStream_t)stream, m->gate_check_every);
   if (rc) return rc;
   if (disabled) *disabled = m->gate_on ? 0 : 1;
+  return UCNS_OK;
+}
+
+int ucns_gate_status(const ucns_mesh* m, int32_t* enabled, int64_t* counts, double* last) {
+  if (!m) return fail(UCNS_ERR_INVALID_ARG, "mesh handle is NULL");
+  if (enabled) *enabled = (m->gate_on && m->mlp) ? 1 : 0;
+  if (counts) {
+    counts[0] = m->gate_steps;
+    counts[1] = m->gate_checks;
+    counts[2] = m->gate_off_step;
+  }
+  if (last)
+    for (int q = 0; q < 4; q++) last[q] = m->gate_last[q];
+  return UCNS_OK;
+}
+
+int ucns_gate_set_flags(ucns_mesh* m, const uint8_t* flags, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!flags) {
+    m->gate_fixed = false;
+    m->gate_flags_valid = false;
+    return UCNS_OK;
+  }
+  if (m->K != 9 || m->nd == 0) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
+  if ((rc = gate_buffers(m))) return rc;
+  UCNS_CUDA(cudaMemcpyAsync(m->gate_flag, flags, (size_t)m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  m->gate_fixed = true;
+  m->gate_flags_valid = false;
+  return UCNS_OK;
+}
+
+int ucns_gate_flags(ucns_mesh* m, uint8_t* flags, void* stream) {
+  int rc = check_ready(m);
+  if (rc) return rc;
+  if (!flags) return fail(UCNS_ERR_INVALID_ARG, "flags is NULL");
+  if (!m->gate_flag) return fail(UCNS_ERR_STATE, "no flags: neither a network nor caller flags were set");
+  UCNS_CUDA(cudaMemcpyAsync(flags, m->gate_flag, (size_t)m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return UCNS_OK;
 }
 

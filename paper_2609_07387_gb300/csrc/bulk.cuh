@@ -33,7 +33,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // bounded wait for the phase with the given parity; false if it gave up
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+// after `limit` cycles
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, long long limit = kBulkWaitCycles) {
   const long long t0 = clock64();
   for (uint32_t it = 0;; it++) {
     uint32_t done;
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63u) == 63u && clock64() - t0 > kBulkWaitCycles) return false;
+    if ((it & 63u) == 63u && clock64() - t0 > limit) return false;
   }
 }
 
@@ -58,6 +59,17 @@ __device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t 
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// The give-up path of bar_wait, exercised on its own: one thread waits, with
+// a short limit, for a phase of a fresh mbarrier that nothing arrives on and
+// no copy completes (nothing is in flight), then reports the timeout as the
+// reconstruction does (bit 1 of the error word).
+__global__ void k_bulk_wait_probe(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  bar_init(&bar);
+  if (!bar_wait(&bar, 0, limit)) atomicOr(err, 2);
 }
 
 }  // namespace ucns

@@ -12,7 +12,9 @@ struct HostArrays {
   std::vector<int32_t> sc;                               // [Mc][N]
   std::vector<double> Pc;                                // [K][Mc][N]
   std::vector<int32_t> sd;                               // [nd][Md][N]
-  std::vector<double> Pd;                                // [nd][3][Md][N]
+  std::vector<double> Pd;                                // [nd][Kd][Md][N]
+  std::vector<double> Msi;                               // P3/P4: [K(K+1)/2][N]
+  std::vector<double> psib;                              // P3/P4: [K-3][N]
   std::vector<double> fq;                                // [nq][10][F] x-x_L, x-x_R', n, |dS|
   std::vector<double> fpen;                              // [F]
 };

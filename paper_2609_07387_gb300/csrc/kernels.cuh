@@ -840,6 +840,49 @@ __global__ void k_diag_final(const double* __restrict__ part, int nb, double* __
   for (int q = 0; q < 4; q++) out[q] = s[q];
 }
 
+// ALU throughput probes: kPeakChains independent FMA chains per thread (the
+// pipeline stays full), `iters` rounds; the result is kept live through a
+// conditional store to a device variable that the compiler cannot prove dead
+constexpr int kPeakChains = 8;
+static __device__ double g_peak_sink;
+__global__ void __launch_bounds__(256) k_peak_ffma(int iters, float m) {
+  float a[kPeakChains];
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) a[c] = (float)(threadIdx.x + c);
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) a[c] = fmaf(a[c], m, 0.5f);
+  float t = 0.f;
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) t += a[c];
+  if (t == 0.123f) g_peak_sink = t;
+}
+__global__ void __launch_bounds__(256) k_peak_ffma2(int iters, float m) {
+  float2 a[kPeakChains];
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) a[c] = make_float2((float)(threadIdx.x + c), (float)c);
+  const float2 mm = make_float2(m, m), h = make_float2(0.5f, 0.5f);
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) a[c] = __ffma2_rn(a[c], mm, h);
+  float t = 0.f;
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) t += a[c].x + a[c].y;
+  if (t == 0.123f) g_peak_sink = t;
+}
+__global__ void __launch_bounds__(256) k_peak_dfma(int iters, double m) {
+  double a[kPeakChains];
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) a[c] = (double)(threadIdx.x + c);
+  for (int i = 0; i < iters; i++)
+#pragma unroll
+    for (int c = 0; c < kPeakChains; c++) a[c] = fma(a[c], m, 0.5);
+  double t = 0.0;
+#pragma unroll
+  for (int c = 0; c < kPeakChains; c++) t += a[c];
+  if (t == 0.123) g_peak_sink = t;
+}
+
 __global__ void k_set_scalar(double* __restrict__ dst, double v) { dst[0] = v; }
 __global__ void k_add_scalar(double* __restrict__ acc, const double* __restrict__ v) { acc[0] += v[0]; }
 

@@ -204,34 +204,52 @@ __global__ void k_count_flags(const uint8_t* __restrict__ flag, int N, unsigned 
   if (threadIdx.x == 0) atomicAdd(count, (unsigned long long)sm[0]);
 }
 
-// per-block sums of V (u . R_m - |u|^2 R_rho / 2) for two residuals, and V
+// per-block sums, for two residuals R1 (gated) and R2 (full) of the state U,
+// of the cell kinetic-energy rates r = V (u . R_m - |u|^2 R_rho / 2): [sum r1,
+// sum r2, sum V, sum |r1 - r2|, sum |r2|] at part[8 b + q] (the fourth is the
+// local difference, which cannot cancel between cells)
+constexpr int kKeRateSums = 5, kRedStride = 8;
 __global__ void __launch_bounds__(256) k_ke_rate_partial(const double* __restrict__ U, const double* __restrict__ R1,
                                                          const double* __restrict__ R2, const double* __restrict__ vol,
                                                          int N, double* __restrict__ part) {
-  __shared__ double sm[3][256];
-  double acc[3] = {0, 0, 0};
+  __shared__ double sm[kKeRateSums][256];
+  double acc[kKeRateSums] = {0, 0, 0, 0, 0};
   const size_t n = N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double ir = 1.0 / U[i];
     const double u0 = U[n + i] * ir, u1 = U[2 * n + i] * ir, u2 = U[3 * n + i] * ir;
     const double q = 0.5 * (u0 * u0 + u1 * u1 + u2 * u2);
     const double V = vol[i];
-    acc[0] += V * (u0 * R1[n + i] + u1 * R1[2 * n + i] + u2 * R1[3 * n + i] - q * R1[i]);
-    acc[1] += V * (u0 * R2[n + i] + u1 * R2[2 * n + i] + u2 * R2[3 * n + i] - q * R2[i]);
+    const double r1 = V * (u0 * R1[n + i] + u1 * R1[2 * n + i] + u2 * R1[3 * n + i] - q * R1[i]);
+    const double r2 = V * (u0 * R2[n + i] + u1 * R2[2 * n + i] + u2 * R2[3 * n + i] - q * R2[i]);
+    acc[0] += r1;
+    acc[1] += r2;
     acc[2] += V;
+    acc[3] += fabs(r1 - r2);
+    acc[4] += fabs(r2);
   }
 #pragma unroll
-  for (int q = 0; q < 3; q++) sm[q][threadIdx.x] = acc[q];
+  for (int q = 0; q < kKeRateSums; q++) sm[q][threadIdx.x] = acc[q];
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
     if (threadIdx.x < s)
 #pragma unroll
-      for (int q = 0; q < 3; q++) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
+      for (int q = 0; q < kKeRateSums; q++) sm[q][threadIdx.x] += sm[q][threadIdx.x + s];
     __syncthreads();
   }
   if (threadIdx.x == 0)
 #pragma unroll
-    for (int q = 0; q < 3; q++) part[(size_t)blockIdx.x * 4 + q] = sm[q][0];
+    for (int q = 0; q < kKeRateSums; q++) part[(size_t)blockIdx.x * kRedStride + q] = sm[q][0];
+}
+
+// out[q] = sum over blocks, in block order, of part[stride b + q], q < nq
+__global__ void k_sum_partials(const double* __restrict__ part, int nb, int stride, int nq, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int q = 0; q < nq; q++) {
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += part[(size_t)b * stride + q];
+    out[q] = s;
+  }
 }
 
 }  // namespace ucns

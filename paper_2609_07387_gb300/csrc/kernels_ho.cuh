@@ -1,0 +1,263 @@
+// P3 and P4 reconstruction and face kernels (FP64), hexahedra.
+//
+//   k_recon_ho  thread = (cell, variable): central least-squares contraction
+//               (K = 19 or 34 modes over 2K members, Eq. 4); with CWENOZ the
+//               six directional candidates (linear at P3, quadratic over 18
+//               members at P4, Sec. 2.2), the smoothness indicators as the
+//               quadratic forms a^T M a of each cell's precomputed matrix M
+//               (Eq. 6 reading), the nonlinear weights and the combination.
+//               The directional contractions run twice (once for the
+//               indicators, once for the combination) rather than holding all
+//               six candidates in registers.
+//   k_face_ho   ORDER^2 Gauss points per face on ORDER^2 lanes (9 at P3, 16
+//               at P4; 32 / ORDER^2 faces per warp); values and gradients of
+//               the monomial-form polynomials, HLLC, penalised viscous flux
+//               (Eq. 7), and the face total summed by the group's first lane
+//               over its lanes in point order (deterministic).
+#pragma once
+
+#include "basis.hpp"
+#include "kernels.cuh"
+
+namespace ucns {
+
+template <int ORDER>
+struct HO {
+  static constexpr int K = basis_count(ORDER);
+  static constexpr int MC = 2 * K;
+  static constexpr int KD = ORDER == 4 ? 9 : 3;  // modes of a directional candidate
+  static constexpr int MD = 2 * KD;
+  static constexpr int NQ = ORDER * ORDER;
+};
+
+struct ReconArgsHO {
+  const double* __restrict__ U;     // [5][N]
+  const int32_t* __restrict__ sc;   // [MC][N]
+  const double* __restrict__ Pc;    // [K][MC][N]
+  const int32_t* __restrict__ sd;   // [6][MD][N]
+  const double* __restrict__ Pd;    // [6][KD][MD][N]
+  const double* __restrict__ Msi;   // [K(K+1)/2][N]: smoothness-indicator matrix, upper triangle by rows
+  const double* __restrict__ psib;  // [K-3][N]: cell means of the basis monomials of degree >= 2
+  const double* __restrict__ inv_h; // [N]
+  double* __restrict__ coef;        // [K+1][N][5] physical-unit monomial coefficients
+  int N;
+  double lam0, lams, eps;
+};
+
+// a^T M a over the first KK modes (M: K x K symmetric, upper triangle stored
+// by rows: entry (k, l >= k) at q = k K - k (k - 1) / 2 + l - k)
+template <int K, int KK>
+__device__ __forceinline__ double si_form(const double* __restrict__ M, size_t N, int i, const double (&a)[KK]) {
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < KK; k++) {
+    double t = 0.0;
+#pragma unroll
+    for (int l = k + 1; l < KK; l++) t = fma(__ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]), a[l], t);
+    const double mkk = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2) * N + i]);
+    s = fma(a[k], fma(2.0, t, mkk * a[k]), s);
+  }
+  return s;
+}
+
+// directional candidate s of variable v: b = P_s (U_m - U_i) over its members
+template <int ORDER>
+__device__ __forceinline__ void dir_coeffs(const ReconArgsHO& a, const double* __restrict__ Uv, double ui, int i, int s,
+                                           double (&b)[HO<ORDER>::KD]) {
+  using H = HO<ORDER>;
+  const size_t N = a.N;
+#pragma unroll
+  for (int k = 0; k < H::KD; k++) b[k] = 0.0;
+#pragma unroll 2
+  for (int r = 0; r < H::MD; r++) {
+    const int j = __ldg(&a.sd[((size_t)s * H::MD + r) * N + i]);
+    const double d = Uv[j] - ui;
+#pragma unroll
+    for (int k = 0; k < H::KD; k++) b[k] = fma(__ldg(&a.Pd[(((size_t)s * H::KD + k) * H::MD + r) * N + i]), d, b[k]);
+  }
+}
+
+template <int ORDER, bool WENO>
+__global__ void __launch_bounds__(128) k_recon_ho(ReconArgsHO a) {
+  using H = HO<ORDER>;
+  constexpr int K = H::K, MC = H::MC, KD = H::KD, ND = 6;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid / 5, v = tid - 5 * (tid / 5);
+  if (i >= a.N) return;
+  const size_t N = a.N;
+  const double* __restrict__ Uv = a.U + (size_t)v * N;
+  const double ui = Uv[i];
+  double ao[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) ao[k] = 0.0;
+#pragma unroll 2
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[(size_t)m * N + i]);
+    const double d = Uv[j] - ui;
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[k] = fma(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+  }
+  double c[K];
+  if constexpr (!WENO) {
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = ao[k];
+  } else {
+    const double SI0 = si_form<K, K>(a.Msi, N, i, ao);
+    double SI[ND];
+    double tau = 0.0;
+#pragma unroll 1
+    for (int s = 0; s < ND; s++) {
+      double b[KD];
+      dir_coeffs<ORDER>(a, Uv, ui, i, s, b);
+      SI[s] = si_form<K, KD>(a.Msi, N, i, b);
+      tau += fabs(SI0 - SI[s]);
+    }
+    tau *= (1.0 / ND);
+    // omega~_s = lambda_s (1 + tau / (eps + SI_s)), normalised
+    const double w0 = a.lam0 * (1.0 + tau / (a.eps + SI0));
+    double ws[ND];
+    double wsum = w0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      ws[s] = a.lams * (1.0 + tau / (a.eps + SI[s]));
+      wsum += ws[s];
+    }
+    const double iws = 1.0 / wsum;
+    // p = omega_0 p_1 + sum_s omega_s p_s with p_1 = (p_opt - sum lambda_s p_s)/lambda_0
+    const double r0 = (w0 * iws) / a.lam0;
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
+#pragma unroll 1
+    for (int s = 0; s < ND; s++) {
+      double b[KD];
+      dir_coeffs<ORDER>(a, Uv, ui, i, s, b);
+      const double e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+      for (int k = 0; k < KD; k++) c[k] = fma(e, b[k], c[k]);
+    }
+  }
+  // monomial form in physical units: p = c0 + sum_k (c_k / h^deg_k) (x - x_i)^e_k,
+  // c0 = U_i - sum_{deg >= 2} c_k mean(psi_k)
+  double c0 = ui;
+#pragma unroll
+  for (int k = 3; k < K; k++) c0 = fma(-c[k], __ldg(&a.psib[(size_t)(k - 3) * N + i]), c0);
+  const double ih = __ldg(&a.inv_h[i]);
+  double ihp[ORDER + 1];
+  ihp[0] = 1.0;
+#pragma unroll
+  for (int e = 1; e <= ORDER; e++) ihp[e] = ihp[e - 1] * ih;
+  double* out = a.coef + (size_t)i * 5 + v;
+  const size_t st = N * 5;
+  out[0] = c0;
+#pragma unroll
+  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k] * ihp[basis_degree(k)];
+}
+
+// value at the physical offset (x, y, z) from the centroid into U and the
+// gradient written (ACC = false) or added (ACC = true) into g
+template <int ORDER, bool ACC>
+__device__ __forceinline__ void eval_side_ho(const double* __restrict__ coef, int N, int cell, double x, double y,
+                                             double z, double U[5], double g[5][3]) {
+  constexpr int K = basis_count(ORDER);
+  const size_t st = (size_t)N * 5;
+  const double* p = coef + (size_t)cell * 5;
+  double px[ORDER + 1], py[ORDER + 1], pz[ORDER + 1];
+  px[0] = py[0] = pz[0] = 1.0;
+#pragma unroll
+  for (int e = 1; e <= ORDER; e++) {
+    px[e] = px[e - 1] * x;
+    py[e] = py[e - 1] * y;
+    pz[e] = pz[e - 1] * z;
+  }
+  double gx[5], gy[5], gz[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    U[v] = p[v];
+    gx[v] = gy[v] = gz[v] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const int ex = basis_exp(k, 0), ey = basis_exp(k, 1), ez = basis_exp(k, 2);
+    const double mv = px[ex] * py[ey] * pz[ez];
+    const double mx = ex ? ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez] : 0.0;
+    const double my = ey ? ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez] : 0.0;
+    const double mz = ez ? ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0] : 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const double c = p[(k + 1) * st + v];
+      U[v] = fma(c, mv, U[v]);
+      if (ex) gx[v] = fma(c, mx, gx[v]);
+      if (ey) gy[v] = fma(c, my, gy[v]);
+      if (ez) gz[v] = fma(c, mz, gz[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    if (ACC) {
+      g[v][0] += gx[v];
+      g[v][1] += gy[v];
+      g[v][2] += gz[v];
+    } else {
+      g[v][0] = gx[v];
+      g[v][1] = gy[v];
+      g[v][2] = gz[v];
+    }
+  }
+}
+
+template <int ORDER, bool VISC>
+__global__ void __launch_bounds__(128) k_face_ho(FaceArgs a) {
+  constexpr int NQ = ORDER * ORDER, FPW = 32 / NQ;  // faces per warp
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / NQ, q = lane - NQ * (lane / NQ);
+  const bool in_group = grp < FPW;
+  const int f = gw * FPW + (in_group ? grp : 0);
+  const bool live = in_group && f < a.F;
+  const int fc = live ? f : a.F - 1, qc = in_group ? q : 0;
+  const size_t F = a.F;
+  const double* __restrict__ fq = a.fq + (size_t)qc * 10 * F + fc;
+  const double xl = fq[0], yl = fq[F], zl = fq[2 * F];
+  const double xr = fq[3 * F], yr = fq[4 * F], zr = fq[5 * F];
+  const double n[3] = {fq[6 * F], fq[7 * F], fq[8 * F]};
+  const double area = fq[9 * F];
+  const int o = a.fo[fc], nb = a.fn[fc];
+  double UL[5], UR[5], gs[5][3];  // gs = grad U_L + grad U_R
+  eval_side_ho<ORDER, false>(a.coef, a.N, o, xl, yl, zl, UL, gs);
+  eval_side_ho<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, UR, gs);
+  double Fc[5];
+  hllc_flux(UL, UR, n, a.c, Fc);
+  double flux[5];
+  if (VISC) {
+    // as in k_face: twice the face state and the penalised face gradient
+    const double pen2 = 2.0 * a.fpen[fc];
+    double Uf2[5], gf2[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const double jump2 = pen2 * (UR[v] - UL[v]);
+      Uf2[v] = UL[v] + UR[v];
+#pragma unroll
+      for (int j = 0; j < 3; j++) gf2[v][j] = fma(jump2, n[j], gs[v][j]);
+    }
+    double Fv[5];
+    viscous_flux(Uf2, gf2, n, a.c, Fv);
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = (Fc[v] - Fv[v]) * area;
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+  }
+  // the group's first lane sums its NQ points in point order (every lane takes
+  // part in the shuffles; lanes outside a group read group 0 and store nothing)
+  const int base = (in_group ? grp : 0) * NQ;
+  double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int t = 0; t < NQ; t++)
+#pragma unroll
+    for (int v = 0; v < 5; v++) tot[v] += __shfl_sync(0xffffffffu, flux[v], base + t);
+  if (live && q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = tot[v];
+  }
+}
+
+}  // namespace ucns

@@ -10,6 +10,7 @@
 #include <numeric>
 #include <unordered_map>
 
+#include "basis.hpp"
 #include "host_arrays.hpp"
 #include "ucns_internal.hpp"
 
@@ -39,7 +40,9 @@ inline V3 cross(V3 a, V3 b) {
 }
 inline double comp(V3 a, int d) { return d == 0 ? a.x : (d == 1 ? a.y : a.z); }
 
-// Gauss-Legendre points/weights on [0,1] in closed form (n = 1, 2, 3).
+// Gauss-Legendre points/weights on [0,1]: closed form for n = 1, 2, 3; for
+// larger n the roots of P_n by Newton's iteration from Chebyshev guesses,
+// w = 2 / ((1 - t^2) P_n'(t)^2) on [-1, 1], mapped to [0, 1].
 void gauss01(int n, double* x, double* w) {
   if (n == 1) {
     x[0] = 0.5;
@@ -48,10 +51,36 @@ void gauss01(int n, double* x, double* w) {
     double d = 0.5 / std::sqrt(3.0);
     x[0] = 0.5 - d; x[1] = 0.5 + d;
     w[0] = w[1] = 0.5;
-  } else {
+  } else if (n == 3) {
     double d = 0.5 * std::sqrt(0.6);
     x[0] = 0.5 - d; x[1] = 0.5; x[2] = 0.5 + d;
     w[0] = 5.0 / 18.0; w[1] = 4.0 / 9.0; w[2] = 5.0 / 18.0;
+  } else {
+    for (int i = 0; i < n; i++) {
+      double t = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+      for (int it = 0; it < 100; it++) {
+        double p0 = 1.0, p1 = t;  // P_0, P_1; recurrence (k+1) P_{k+1} = (2k+1) t P_k - k P_{k-1}
+        for (int k = 1; k < n; k++) {
+          const double p2 = ((2 * k + 1) * t * p1 - k * p0) / (k + 1);
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        const double dt = p1 / dp;
+        t -= dt;
+        if (std::fabs(dt) < 1e-16) break;
+      }
+      // recompute the derivative at the converged root
+      double p0 = 1.0, p1 = t;
+      for (int k = 1; k < n; k++) {
+        const double p2 = ((2 * k + 1) * t * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (t * p1 - p0) / (t * t - 1.0);
+      x[n - 1 - i] = 0.5 * (1.0 + t);
+      w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);
+    }
   }
 }
 
@@ -135,13 +164,62 @@ Geom cell_geometry(const ucns_mesh* m, int64_t user) {
   return g;
 }
 
+// Central moments of a cell up to degree kMomDeg: mean over the cell of
+// (x - c)^b, indexed by mom_index(b); degree kMomDeg = 6 suffices for the
+// smoothness indicators of a quartic (products of two cubic derivatives).
+constexpr int kMomDeg = 6;
+int mom_index(int a, int b, int c) { return (a * (kMomDeg + 1) + b) * (kMomDeg + 1) + c; }
+constexpr int kMomSlots = (kMomDeg + 1) * (kMomDeg + 1) * (kMomDeg + 1);
+
+// mean over the cell of (x - c)^b for every |b| <= kMomDeg (slots with a
+// larger total degree stay zero), by a 5-point Gauss rule per direction:
+// exact for a degree-6 monomial times the trilinear Jacobian (degree <= 8
+// per direction on the unit cube)
+void central_moments(const ucns_mesh* m, int64_t user, const Geom& g, double* mu) {
+  CellPts cp = load_cell(m, user);
+  double gx[5], gw[5];
+  gauss01(5, gx, gw);
+  for (int k = 0; k < kMomSlots; k++) mu[k] = 0.0;
+  for (int a = 0; a < 5; a++)
+    for (int b = 0; b < 5; b++)
+      for (int q = 0; q < 5; q++) {
+        V3 x;
+        double j;
+        map_point(m->npc, cp, gx[a], gx[b], gx[q], &x, &j);
+        const double w = gw[a] * gw[b] * gw[q] * j / g.V;
+        const V3 y = x - g.c;
+        double px[kMomDeg + 1], py[kMomDeg + 1], pz[kMomDeg + 1];
+        px[0] = py[0] = pz[0] = 1.0;
+        for (int e = 1; e <= kMomDeg; e++) {
+          px[e] = px[e - 1] * y.x;
+          py[e] = py[e - 1] * y.y;
+          pz[e] = pz[e - 1] * y.z;
+        }
+        for (int ea = 0; ea <= kMomDeg; ea++)
+          for (int eb = 0; ea + eb <= kMomDeg; eb++)
+            for (int ec = 0; ea + eb + ec <= kMomDeg; ec++) mu[mom_index(ea, eb, ec)] += w * px[ea] * py[eb] * pz[ec];
+      }
+}
+
+double binom(int n, int k) {
+  double r = 1.0;
+  for (int j = 1; j <= k; j++) r = r * (n - k + j) / j;
+  return r;
+}
+// n (n-1) ... (n-k+1)
+double falling(int n, int k) {
+  double r = 1.0;
+  for (int j = 0; j < k; j++) r *= (double)(n - j);
+  return r;
+}
+
 // Face quadrature of an owner-local face: points and owner-outward area vectors.
 int face_points(const ucns_mesh* m, int64_t owner_user, int lf, int order, V3* x, V3* dS) {
   CellPts cp = load_cell(m, owner_user);
   const int* fl = face_local_nodes(m->npc, lf);
   if (m->nfn == 4) {
     V3 Q0 = cp.p[fl[0]], Q1 = cp.p[fl[1]], Q2 = cp.p[fl[2]], Q3 = cp.p[fl[3]];
-    double gx[3], gw[3];
+    double gx[kMaxOrder], gw[kMaxOrder];
     gauss01(order, gx, gw);
     int q = 0;
     for (int ia = 0; ia < order; ia++)
@@ -415,19 +493,31 @@ bool pinv_householder(const double* Ain, int M, int K, const double* w, double* 
 int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   const int64_t N = m->N, F = m->F;
   const int order = p->order;
-  const int K = order == 1 ? 3 : 9;
+  const int K = basis_count(order);
   const int Mc = 2 * K;
-  const int nd = (order == 2 && p->scheme == UCNS_SCHEME_CWENOZ) ? m->nfc : 0;
-  const int Md = kMd;
+  const int nd = (order >= 2 && p->scheme == UCNS_SCHEME_CWENOZ) ? m->nfc : 0;
+  // directional candidates: linear at P2 and P3, quadratic at P4 (Sec. 2.2)
+  const int Kd = order == 4 ? 9 : 3;
+  const int Md = 2 * Kd;
   const int nq = order * order;
-  if ((int64_t)F * nq >= (int64_t(1) << 31) || N * 5 >= (int64_t(1) << 31))
+  if (order >= 3 && m->npc != 8) return fail(UCNS_ERR_INVALID_ARG, "orders 3 and 4 are built for hexahedra only");
+  if ((int64_t)F * nq >= (int64_t(1) << 31) || N * 5 >= (int64_t(1) << 31) ||
+      (int64_t)(K + 1) * N * 5 >= (int64_t(1) << 31))
     return fail(UCNS_ERR_INVALID_ARG, "mesh too large for 32-bit kernel indexing");
-  m->K = K; m->Mc = Mc; m->nd = nd; m->Md = Md; m->nq = nq; m->NC = K + 1;
+  m->K = K; m->Mc = Mc; m->nd = nd; m->Md = Md; m->Kd = Kd; m->nq = nq; m->NC = K + 1;
   std::vector<Geom> g(N);  // internal order
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < N; i++) g[i] = cell_geometry(m, m->perm[i]);
   for (int64_t i = 0; i < N; i++)
     if (!(g[i].V > 0)) return fail(UCNS_ERR_MESH, "cell with non-positive volume");
+  // P3/P4: central moments of every cell (moment-form least-squares rows and
+  // smoothness-indicator matrices)
+  std::vector<double> cm;
+  if (order >= 3) {
+    cm.assign((size_t)N * kMomSlots, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) central_moments(m, m->perm[i], g[i], &cm[(size_t)i * kMomSlots]);
+  }
   auto shift_of = [&](int64_t i, int64_t j, double s[3]) {  // nearest image of j seen from i
     for (int d = 0; d < 3; d++) {
       s[d] = 0.0;
@@ -477,7 +567,40 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   h->sc.assign((size_t)Mc * N, 0);
   h->Pc.assign((size_t)K * Mc * N, 0.0);
   h->sd.assign((size_t)nd * Md * N, 0);
-  h->Pd.assign((size_t)nd * 3 * Md * N, 0.0);
+  h->Pd.assign((size_t)nd * Kd * Md * N, 0.0);
+  if (order >= 3) {
+    // per cell: the means of the non-linear basis monomials (xi units) and
+    // the smoothness-indicator matrix of Eq. 6's reading, SI(a) = a^T M a,
+    // M_kl = sum_{1 <= |b|} (1/V) int d^b psi_k d^b psi_l (derivatives in xi,
+    // each multi-index b once), from the xi-moments of the cell
+    const int nm = K * (K + 1) / 2;
+    h->psib.assign((size_t)(K - 3) * N, 0.0);
+    h->Msi.assign((size_t)nm * N, 0.0);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; i++) {
+      const double* mu = &cm[(size_t)i * kMomSlots];
+      const double ih = 1.0 / g[i].h;
+      auto xmu = [&](int a, int b, int c) { return mu[mom_index(a, b, c)] * std::pow(ih, a + b + c); };
+      for (int k = 3; k < K; k++)
+        h->psib[(size_t)(k - 3) * N + i] = xmu(basis_exp(k, 0), basis_exp(k, 1), basis_exp(k, 2));
+      int q = 0;
+      for (int k = 0; k < K; k++)
+        for (int l = k; l < K; l++, q++) {
+          const int ak[3] = {basis_exp(k, 0), basis_exp(k, 1), basis_exp(k, 2)};
+          const int al[3] = {basis_exp(l, 0), basis_exp(l, 1), basis_exp(l, 2)};
+          double t = 0.0;
+          for (int b0 = 0; b0 <= std::min(ak[0], al[0]); b0++)
+            for (int b1 = 0; b1 <= std::min(ak[1], al[1]); b1++)
+              for (int b2 = 0; b2 <= std::min(ak[2], al[2]); b2++) {
+                if (b0 + b1 + b2 == 0) continue;
+                const double f = falling(ak[0], b0) * falling(ak[1], b1) * falling(ak[2], b2) * falling(al[0], b0) *
+                                 falling(al[1], b1) * falling(al[2], b2);
+                t += f * xmu(ak[0] + al[0] - 2 * b0, ak[1] + al[1] - 2 * b1, ak[2] + al[2] - 2 * b2);
+              }
+          h->Msi[(size_t)q * N + i] = t;
+        }
+    }
+  }
   int bad = 0;
   // A row of cell i's basis integrated over member j's image (moment form):
   // int_{V_j} phi_k = V_j [psi_k(d) + (h_j/h_i)^2 S_j,k - S_i,k], d = (c_j' - c_i)/h_i
@@ -500,10 +623,35 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
       row[8] = V * (d[1] * d[2] + r2 * Sj[5] - Si[5]);
     }
   };
+  // P3/P4 rows (moment form from the member's central moments): the mean of
+  // ((x - c_i)/h_i)^a over the member's image, expanded about its centroid c_j'
+  // by the binomial theorem, less cell i's own mean of that monomial, times |V_j|
+  auto arow_ho = [&](int64_t i, int64_t j, int KK, double* row) {
+    double s[3];
+    shift_of(i, j, s);
+    double d[3];
+    for (int q = 0; q < 3; q++) d[q] = comp(g[j].c, q) + s[q] - comp(g[i].c, q);
+    const double* muj = &cm[(size_t)j * kMomSlots];
+    const double* mui = &cm[(size_t)i * kMomSlots];
+    for (int k = 0; k < KK; k++) {
+      const int a[3] = {basis_exp(k, 0), basis_exp(k, 1), basis_exp(k, 2)};
+      double t = 0.0;
+      for (int b0 = 0; b0 <= a[0]; b0++)
+        for (int b1 = 0; b1 <= a[1]; b1++)
+          for (int b2 = 0; b2 <= a[2]; b2++)
+            t += binom(a[0], b0) * binom(a[1], b1) * binom(a[2], b2) * std::pow(d[0], a[0] - b0) *
+                 std::pow(d[1], a[1] - b1) * std::pow(d[2], a[2] - b2) * muj[mom_index(b0, b1, b2)];
+      row[k] = g[j].V * (t - mui[mom_index(a[0], a[1], a[2])]) * std::pow(1.0 / g[i].h, a[0] + a[1] + a[2]);
+    }
+  };
+  auto row_of = [&](int64_t i, int64_t j, int KK, double* row) {
+    if (order >= 3) arow_ho(i, j, KK, row);
+    else arow(i, j, KK, row);
+  };
 #pragma omp parallel for schedule(dynamic, 256) reduction(| : bad)
   for (int64_t i = 0; i < N; i++) {
     std::vector<Cand> c;
-    if (!bfs(m, i, -1, 3, c)) { bad |= 1; continue; }
+    if (!bfs(m, i, -1, order == 4 ? 4 : 3, c)) { bad |= 1; continue; }
     for (size_t q = 1; q < c.size(); q++) c[q].shared = shared_nodes(m, m->perm[i], c[q].user);
     std::sort(c.begin() + 1, c.end(), [](const Cand& a, const Cand& b) {
       if (a.depth != b.depth) return a.depth < b.depth;
@@ -515,7 +663,7 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
     for (int r = 0; r < Mc; r++) {
       int64_t j = c[1 + r].id;
       h->sc[(size_t)r * N + i] = (int32_t)j;
-      arow(i, j, K, &A[r * K]);
+      row_of(i, j, K, &A[r * K]);
       w[r] = g[j].V;
     }
     if (!pinv_householder(A, Mc, K, w, P)) { bad |= 4; continue; }
@@ -523,7 +671,7 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
       for (int r = 0; r < Mc; r++) h->Pc[((size_t)k * Mc + r) * N + i] = P[k * Mc + r];
     for (int s = 0; s < nd; s++) {
       int64_t nb = face_nbr(m, i, s);
-      if (!bfs(m, nb, i, 2, c)) { bad |= 1; break; }
+      if (!bfs(m, nb, i, Kd == 3 ? 2 : 3, c)) { bad |= 1; break; }
       std::sort(c.begin() + 1, c.end(), [](const Cand& a, const Cand& b) {
         if (a.depth != b.depth) return a.depth < b.depth;
         return a.user < b.user;
@@ -532,12 +680,12 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
       for (int r = 0; r < Md; r++) {
         int64_t j = c[r].id;
         h->sd[((size_t)s * Md + r) * N + i] = (int32_t)j;
-        arow(i, j, 3, &A[r * 3]);
+        row_of(i, j, Kd, &A[r * Kd]);
         w[r] = g[j].V;
       }
-      if (!pinv_householder(A, Md, 3, w, P)) { bad |= 4; break; }
-      for (int k = 0; k < 3; k++)
-        for (int r = 0; r < Md; r++) h->Pd[(((size_t)s * 3 + k) * Md + r) * N + i] = P[k * Md + r];
+      if (!pinv_householder(A, Md, Kd, w, P)) { bad |= 4; break; }
+      for (int k = 0; k < Kd; k++)
+        for (int r = 0; r < Md; r++) h->Pd[(((size_t)s * Kd + k) * Md + r) * N + i] = P[k * Md + r];
     }
   }
   if (bad & 1) return fail(UCNS_ERR_STENCIL, "stencil search overflow");

@@ -83,7 +83,7 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 // bounded wait for the phase with the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kMbarCycles) {
   const long long t0 = clock64();
   for (uint32_t it = 0;; it++) {
     uint32_t done;
@@ -94,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 63u) == 63u && clock64() - t0 > kMbarCycles) return false;
+    if ((it & 63u) == 63u && clock64() - t0 > limit) return false;
   }
 }
 
@@ -174,6 +174,7 @@ struct FwdArgs {
   const float* __restrict__ w3r;
   float* __restrict__ z;        // [n] logits (may be null)
   uint8_t* __restrict__ flag;   // [n] z > threshold (may be null)
+  bf16* __restrict__ h1;        // [n][64] first hidden layer as fed to layer 2 (may be null)
   float threshold;
   int64_t n;
   int* err;
@@ -217,7 +218,7 @@ __device__ __forceinline__ void stage_params(uint8_t* sm, const bf16* W, const f
 template <bool TRAIN>
 __device__ __forceinline__ bool forward_tile(uint8_t* sm, uint32_t tmem, uint32_t lane, const bf16* X, int64_t n,
                                              int64_t row, uint64_t* bar, uint32_t& phase, float* h2out,
-                                             uint64_t& m1, uint64_t& m2, float& z) {
+                                             uint64_t& m1, uint64_t& m2, float& z, bf16* h1out = nullptr) {
   const int tid = threadIdx.x;
   const uint32_t sbase = smem_u32(sm);
   const float* par = reinterpret_cast<const float*>(sm + kOffPar);
@@ -257,7 +258,11 @@ __device__ __forceinline__ bool forward_tile(uint8_t* sm, uint32_t tmem, uint32_
     h[j] = fmaxf(a, 0.f);
   }
 #pragma unroll
-  for (int c = 0; c < 8; c++) *reinterpret_cast<uint4*>(sm + kOffH1 + kmaj(tid, 8 * c, 64)) = pack8(h + 8 * c);
+  for (int c = 0; c < 8; c++) {
+    const uint4 hp = pack8(h + 8 * c);
+    *reinterpret_cast<uint4*>(sm + kOffH1 + kmaj(tid, 8 * c, 64)) = hp;
+    if (h1out && row < n) reinterpret_cast<uint4*>(h1out + row * 64)[c] = hp;
+  }
   if (TRAIN) {
 #pragma unroll
     for (int j = 0; j < 64; j++) *reinterpret_cast<bf16*>(sm + kOffB4 + kmaj(j, tid, 128)) = __float2bfloat16_rn(h[j]);
@@ -309,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward(FwdArgs a) {
     const int64_t row = t * 128 + tid;
     uint64_t m1, m2;
     float z;
-    ok = forward_tile<false>(sm, tmem, lane, a.X, a.n, row, bar, phase, nullptr, m1, m2, z) && ok;
+    ok = forward_tile<false>(sm, tmem, lane, a.X, a.n, row, bar, phase, nullptr, m1, m2, z, a.h1) && ok;
     if (row < a.n) {
       if (a.z) a.z[row] = z;
       if (a.flag) a.flag[row] = z > a.threshold ? 1 : 0;
@@ -322,6 +327,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_forward(FwdArgs a) {
   __syncthreads();
   fence_after();
   if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+// The give-up path of mbar_wait, exercised on its own: one thread waits, with
+// a short limit, for a phase of a fresh mbarrier that no MMA commit and no
+// thread arrives on (no MMA is issued, no TMEM is allocated), then reports
+// it as the network's kernels do (bit 1 of the network's error word).
+__global__ void k_mlp_wait_probe(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar);
+  if (!mbar_wait(&bar, 0, limit)) atomicOr(err, 2);
 }
 
 // per-CTA partial gradients of the class-weighted BCE over its tiles
@@ -595,10 +611,12 @@ int grad_into(ucns_mlp* m, const bf16* X, const float* y, int64_t n, float w_pos
 
 namespace ucnsnet {
 // forward used by the gated residual (mesh side): logits and flags of n rows
-int forward(ucns_mlp* m, const void* X, int64_t n, float* z, uint8_t* flag, float threshold, void* stream) {
+int forward(ucns_mlp* m, const void* X, int64_t n, float* z, uint8_t* flag, float threshold, void* stream,
+            void* h1) {
   int rc = mlp_setup_attrs();
   if (rc) return rc;
   FwdArgs a;
+  a.h1 = reinterpret_cast<bf16*>(h1);
   a.X = reinterpret_cast<const bf16*>(X);
   a.W = m->W;
   a.theta = m->theta;
@@ -686,6 +704,13 @@ int ucns_mlp_forward(ucns_mlp* m, const void* X, int64_t n, float* z, void* stre
   return ucnsnet::forward(m, X, n, z, nullptr, 0.f, stream);
 }
 
+int ucns_mlp_hidden(ucns_mlp* m, const void* X, int64_t n, void* h1, float* z, void* stream) {
+  if (!m || !X || !h1 || !z || n < 0) return ucns::fail(UCNS_ERR_INVALID_ARG, "bad argument");
+  if (((uintptr_t)X & 15) != 0 || ((uintptr_t)h1 & 15) != 0)
+    return ucns::fail(UCNS_ERR_INVALID_ARG, "X and h1 must be 16-byte aligned");
+  return ucnsnet::forward(m, X, n, z, nullptr, 0.f, stream, h1);
+}
+
 int ucns_mlp_grad(ucns_mlp* m, const void* X, const float* y, int64_t n, float w_pos, float w_neg, float* grad,
                   void* stream) {
   if (!m || !X || !y || !grad || n <= 0) return ucns::fail(UCNS_ERR_INVALID_ARG, "bad argument");
@@ -713,6 +738,13 @@ int ucns_mlp_train(ucns_mlp* m, const void* X, const float* y, int64_t n, int64_
   }
   MLP_CUDA(cudaGetLastError());
   return UCNS_OK;
+}
+
+int ucns_mlp_probe_bounded_wait(ucns_mlp* m, void* stream) {
+  if (!m) return ucns::fail(UCNS_ERR_INVALID_ARG, "NULL argument");
+  k_mlp_wait_probe<<<1, 32, 0, (cudaStream_t)stream>>>(m->err, 1ll << 21);
+  MLP_CUDA(cudaGetLastError());
+  return ucns_mlp_check(m, stream);
 }
 
 int ucns_mlp_check(ucns_mlp* m, void* stream) {

@@ -11,6 +11,8 @@ namespace ucnsnet {
 constexpr int kOffW1 = 0, kOffB1 = 2048, kOffW2 = 2112, kOffB2 = 6208, kOffW3 = 6272, kOffB3 = 6336;
 constexpr int kParams = 6337;
 constexpr int kFeatures = 32;
-// logits z (optional) and flags z > threshold (optional) of n BF16 feature rows
-int forward(ucns_mlp* m, const void* X, int64_t n, float* z, uint8_t* flag, float threshold, void* stream);
+// logits z (optional), flags z > threshold (optional) and the BF16 first
+// hidden layer h1 [n][64] (optional) of n BF16 feature rows
+int forward(ucns_mlp* m, const void* X, int64_t n, float* z, uint8_t* flag, float threshold, void* stream,
+            void* h1 = nullptr);
 }  // namespace ucnsnet

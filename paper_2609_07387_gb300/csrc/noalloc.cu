@@ -18,7 +18,7 @@ int launch_dt_into(const ucns_mesh* m, const double* U, double* partials, int nb
 
 namespace {
 
-constexpr int kDtBlockCells = 256;                 // cells per partial minimum
+using ucns::kDtBlockCells;                         // cells per partial minimum (the kernel's block size)
 constexpr int kStaticDtPartials = 32768;           // 256 KiB of doubles
 constexpr int64_t kStaticDtMaxCells = (int64_t)kStaticDtPartials * kDtBlockCells;  // 8,388,608
 
@@ -27,7 +27,11 @@ static __device__ __align__(256) double g_dt_scratch[kStaticDtPartials];
 
 constexpr int kMaxDevices = 128;
 std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};  // device address of g_dt_scratch, per device
+// device address of g_dt_scratch per device ordinal, resolved once for the
+// life of the process: it belongs to the device's primary context, so a
+// context reset (cudaDeviceReset) invalidates it, and this entry point must
+// not be used after one
+void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
 

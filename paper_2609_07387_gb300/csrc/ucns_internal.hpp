@@ -14,10 +14,10 @@
 namespace ucns {
 
 struct HostArrays;
-constexpr int kMaxK = 9;    // non-constant modes of a quadratic in 3-D
-constexpr int kMaxMc = 18;  // central stencil size 2K
+constexpr int kMaxK = 34;   // non-constant modes of a quartic in 3-D (P4)
+constexpr int kMaxMc = 68;  // central stencil size 2K
 constexpr int kMaxDir = 6;  // directional stencils = faces of the element
-constexpr int kMd = 6;      // directional stencil size 2*K(linear)
+constexpr int kDtBlockCells = 256;  // cells per partial minimum of the time-step reduction
 
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
@@ -34,7 +34,9 @@ struct DeviceMesh {
   int32_t* sc = nullptr;      // [Mc][N] central stencil
   double* Pc = nullptr;       // [K][Mc][N] central pseudo-inverse
   int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
-  double* Pd = nullptr;       // [nd][3][Md][N]
+  double* Pd = nullptr;       // [nd][Kd][Md][N]
+  double* Msi = nullptr;      // P3/P4: [K(K+1)/2][N] smoothness-indicator matrix (upper triangle, row-major)
+  double* psib = nullptr;     // P3/P4: [K-3][N] cell means of the non-linear basis monomials (xi units)
   // mixed precision: FP32 pseudo-inverses and the stencils in the pair-blocked
   // layout [ceil(N/64)][rows/2][64][2] (tiles of 64 consecutive cells, row
   // pairs of a cell adjacent), the cell rows blocked [ceil(N/64)][rows][64]
@@ -91,7 +93,7 @@ struct ucns_mesh {
   // ---- precompute ----
   bool precomputed = false;
   ucns_params P{};
-  int K = 0, Mc = 0, nd = 0, Md = 0, nq = 0, NC = 0;
+  int K = 0, Mc = 0, nd = 0, Md = 0, Kd = 0, nq = 0, NC = 0;  // Kd: modes of a directional candidate
   ucns::DeviceMesh d;
   std::shared_ptr<ucns::HostArrays> host;  // kept only by ucns_precompute_host
   // learned troubled-cell gate
@@ -102,11 +104,18 @@ struct ucns_mesh {
   uint8_t* gate_flag = nullptr;        // [N]
   unsigned long long* gate_count = nullptr;
   bool gate_eval_active = false;       // flags valid for the reconstructions of this call
+  bool gate_fixed = false;             // flags given by the caller (ucns_gate_set_flags), no network
   int gate_check_every = 0;
   int gate_eval_every = 1;
   bool gate_flags_valid = false;       // flags of an earlier step may be reused
-  double gate_bound = 1e-3;
-  int64_t gate_steps = 0;
+  double gate_bound = 1e-4;            // on the estimated KE history error and the dissipation difference
+  double gate_bound_rate = 0.0;        // on the relative difference of the total KE rates (0: not used)
+  int64_t gate_steps = 0;              // gated steps since ucns_gate_configure
+  int64_t gate_checks = 0;             // plain-scheme checks run
+  int64_t gate_off_step = -1;          // gated step at which a check switched the gate off
+  double gate_ke_err = 0.0;            // running estimate of the KE history's relative error
+  double gate_last[4] = {-1.0, -1.0, -1.0, -1.0};  // the last check's four measures
+  // gate_R below: [2][5][N] residuals of the check, then 16 doubles of its sums
   double* gate_R = nullptr;            // [2][5][N] residuals of the check
   float* label_out = nullptr;          // set only inside ucns_gate_labels
   // side stream of the time-step reduction (it overlaps the first stage's

@@ -9,10 +9,12 @@
    the troubled cells on held-out samples.
 4. ``GatedRun``: a mesh with the trained network attached, plus the safety
    check of the plain scheme (run by the library): every ``check_every`` steps
-   the gated and the full residual of the same state are compared through the
-   kinetic-energy rate dKE/dt = sum_i V_i (u_i . R_m,i - |u_i|^2 R_rho,i / 2) /
-   sum_i V_i, and the gate is switched off for good if they differ by more
-   than ``bound`` relative.
+   the gated and the full reconstruction of the same state are compared, and
+   the gate is switched off for good when the estimated error it puts into the
+   kinetic-energy history (the difference of the dKE/dt rates, accumulated over
+   the check intervals) or the relative difference of the total dissipation
+   eps_s + eps_d of the two reconstructions (local errors do not cancel there)
+   exceeds ``bound`` (see ucns_gate_configure).
 """
 from __future__ import annotations
 
@@ -121,19 +123,21 @@ def confusion(net: ucns.Net, X, y, thr: float) -> dict:
 class GatedRun:
     """A mixed or FP64 mesh with the trained indicator attached; the library
     runs the plain-scheme check every `check_every` steps and switches the
-    gate off if the kinetic-energy rates of the gated and the full residual
-    differ by more than `bound` (relative)."""
+    gate off when its estimated kinetic-energy history error or the
+    dissipation difference exceeds `bound` (or, with `bound_rate` > 0, the
+    total KE-rate difference exceeds that)."""
 
     mesh: ucns.Mesh
     net: ucns.Net
     threshold: float
     check_every: int = 10
-    bound: float = 1e-3
+    bound: float = 1e-4
     eval_every: int = 1
+    bound_rate: float = 0.0
 
     def __post_init__(self):
         self.mesh.gate_attach(self.net, self.threshold)
-        self.mesh.gate_configure(self.eval_every, self.check_every, self.bound)
+        self.mesh.gate_configure(self.eval_every, self.check_every, self.bound, self.bound_rate)
         self.mesh.gate_enable(True)
 
     def step(self, U, dt=None):
@@ -142,3 +146,49 @@ class GatedRun:
     def detach(self):
         self.mesh.gate_enable(False)
         self.mesh.gate_attach(None, 0.0)
+
+
+def reference_history(mesh64: ucns.Mesh, U0, steps: int, every: int = 10):
+    """Plain FP64 run of `steps` CFL steps from the host state U0 (internal
+    order): (the dt sequence, diagnostics [KE, eps_s, eps_d] after every
+    `every`-th step, the final device state)."""
+    import torch
+
+    U = torch.from_numpy(np.array(U0, copy=True)).cuda()
+    dts, hist = [], []
+    for k in range(steps):
+        dts.append(mesh64.rk_step(U, return_dt=True))
+        if k % every == every - 1:
+            d = mesh64.diagnostics(U)
+            hist.append((d["ke"], d["eps_s"], d["eps_d"]))
+    mesh64.check_state()
+    return dts, np.array(hist), U
+
+
+def replay_history(mesh: ucns.Mesh, U0, dts, every: int = 10):
+    """The same steps with a given dt sequence on another form of the scheme:
+    (diagnostics as in reference_history, milliseconds of the steps alone by
+    CUDA events, the final device state)."""
+    import torch
+
+    U = torch.from_numpy(np.array(U0, copy=True)).cuda()
+    hist, ms = [], 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k, dt in enumerate(dts):
+        e0.record()
+        mesh.rk_step(U, dt=dt)
+        e1.record()
+        if k % every == every - 1:
+            torch.cuda.synchronize()
+            d = mesh.diagnostics(U)
+            hist.append((d["ke"], d["eps_s"], d["eps_d"]))
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    mesh.check_state()
+    return np.array(hist), ms, U
+
+
+def history_error(h, h_ref) -> list:
+    """max over the history of the relative error of KE, eps_s and eps_d."""
+    return (np.abs(h - h_ref) / np.abs(h_ref)).max(axis=0).tolist()
+

@@ -36,14 +36,14 @@ ERRORS = {
 # every entry point declared in include/ucns.h
 EXPORTS = (
     "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps", "ucns_rk_steps_host",
-    "ucns_check_state", "ucns_diagnostics", "ucns_time_step", "ucns_time_step_static", "ucns_profile",
+    "ucns_check_state", "ucns_probe_bounded_wait", "ucns_alu_peak", "ucns_diagnostics", "ucns_time_step", "ucns_time_step_static", "ucns_profile",
     "ucns_profile_read",
     "ucns_cell_order", "ucns_mesh_info",
     "ucns_last_error", "ucns_mesh_destroy",
     "ucns_mlp_create", "ucns_mlp_destroy", "ucns_mlp_get_params", "ucns_mlp_set_params", "ucns_mlp_forward",
-    "ucns_mlp_grad", "ucns_mlp_train", "ucns_mlp_check",
+    "ucns_mlp_grad", "ucns_mlp_train", "ucns_mlp_check", "ucns_mlp_hidden", "ucns_mlp_probe_bounded_wait",
     "ucns_gate_features", "ucns_gate_labels", "ucns_gate_attach", "ucns_gate_enable", "ucns_gate_flagged",
-    "ucns_gate_configure", "ucns_gate_check", "ucns_float_pair",
+    "ucns_gate_configure", "ucns_gate_check", "ucns_gate_status", "ucns_gate_set_flags", "ucns_gate_flags", "ucns_float_pair",
 )
 MLP_PARAMS = 6337
 
@@ -95,6 +95,9 @@ def load(build_if_missing: bool = True):
         lib.ucns_rk_steps.argtypes = [P, P, I32, C.POINTER(C.c_double), P]
         lib.ucns_rk_steps_host.argtypes = [P, P, I32, C.POINTER(C.c_double), P]
         lib.ucns_check_state.argtypes = [P, P]
+        lib.ucns_probe_bounded_wait.argtypes = [P, P]
+        lib.ucns_alu_peak.argtypes = [I32, C.POINTER(C.c_double), C.POINTER(I32), P]
+        lib.ucns_mlp_probe_bounded_wait.argtypes = [P, P]
         lib.ucns_diagnostics.argtypes = [P, P, C.POINTER(_Diag), P]
         lib.ucns_time_step.argtypes = [P, P, C.POINTER(C.c_double), P]
         lib.ucns_time_step_static.argtypes = [P, P, P, P]
@@ -111,6 +114,7 @@ def load(build_if_missing: bool = True):
         lib.ucns_mlp_set_params.argtypes = [P, P]
         lib.ucns_mlp_forward.argtypes = [P, P, I64, P, P]
         lib.ucns_mlp_grad.argtypes = [P, P, P, I64, F32, F32, P, P]
+        lib.ucns_mlp_hidden.argtypes = [P, P, I64, P, P, P]
         lib.ucns_mlp_train.argtypes = [P, P, P, I64, I64, F32, F32, F32, P]
         lib.ucns_mlp_check.argtypes = [P, P]
         lib.ucns_gate_features.argtypes = [P, P, P, P, P]
@@ -118,8 +122,11 @@ def load(build_if_missing: bool = True):
         lib.ucns_gate_attach.argtypes = [P, P, F32]
         lib.ucns_gate_enable.argtypes = [P, I32]
         lib.ucns_gate_flagged.argtypes = [P, P, P]
-        lib.ucns_gate_configure.argtypes = [P, I32, I32, C.c_double]
-        lib.ucns_gate_check.argtypes = [P, P, C.POINTER(C.c_double), C.POINTER(I32), P]
+        lib.ucns_gate_configure.argtypes = [P, I32, I32, C.c_double, C.c_double]
+        lib.ucns_gate_check.argtypes = [P, P, P, C.POINTER(I32), P]
+        lib.ucns_gate_status.argtypes = [P, C.POINTER(I32), P, P]
+        lib.ucns_gate_set_flags.argtypes = [P, P, P]
+        lib.ucns_gate_flags.argtypes = [P, P, P]
         lib.ucns_float_pair.argtypes = [P, P, P, I64, P]
         for name in EXPORTS:
             if name not in ("ucns_last_error", "ucns_mesh_destroy", "ucns_mlp_destroy"):
@@ -150,6 +157,16 @@ def _dev_ptr(t, n_cells: int) -> int:
             and tuple(t.shape) == (5, n_cells)):
         raise ValueError(f"expected a contiguous cuda float64 tensor of shape (5, {n_cells})")
     return t.data_ptr()
+
+
+def alu_peak(which: int, stream=None) -> tuple[float, int]:
+    """(measured FLOP/s, SM count) of this GPU: which 0 FP32 FMA, 1 FP64 FMA,
+    2 FP32 FMA in packed pairs (ucns_alu_peak)."""
+    lib = load()
+    f = C.c_double(0.0)
+    n = C.c_int32(0)
+    _check(lib, lib.ucns_alu_peak(int(which), C.byref(f), C.byref(n), _stream_ptr(stream)))
+    return f.value, n.value
 
 
 def float_pair(u, stream=None):
@@ -244,7 +261,7 @@ class Mesh:
     def stencil(self, cell: int, which: int = -1):
         """(members [M] caller ids, P [K, M]) of one stencil (after precompute_host)."""
         M = self.Mc if which < 0 else self.Md
-        K = self.K if which < 0 else 3
+        K = self.K if which < 0 else self.Md // 2
         mem = np.zeros(M, dtype=np.int64)
         P = np.zeros((K, M))
         _check(self._lib, self._lib.ucns_stencil(self._h, int(cell), int(which), mem.ctypes.data, P.ctypes.data))
@@ -353,17 +370,56 @@ class Mesh:
     def gate_enable(self, on: bool = True):
         _check(self._lib, self._lib.ucns_gate_enable(self._h, 1 if on else 0))
 
-    def gate_configure(self, eval_every: int = 1, check_every: int = 10, bound: float = 1e-3):
+    def gate_configure(self, eval_every: int = 1, check_every: int = 10, bound: float = 1e-4,
+                       bound_rate: float = 0.0):
         """Gate evaluated every `eval_every` steps; plain-scheme check every
-        `check_every` steps, gate off if the dKE/dt rates differ by > bound."""
-        _check(self._lib, self._lib.ucns_gate_configure(self._h, int(eval_every), int(check_every), float(bound)))
+        `check_every` steps, gate off when the estimated kinetic-energy history
+        error or the dissipation difference exceeds `bound`, or the total
+        KE-rate difference exceeds `bound_rate` (0: not used)."""
+        _check(self._lib, self._lib.ucns_gate_configure(self._h, int(eval_every), int(check_every), float(bound),
+                                                        float(bound_rate)))
 
-    def gate_check(self, U, stream=None) -> tuple[float, bool]:
-        rel = C.c_double(0.0)
+    def gate_check(self, U, stream=None) -> tuple[list, bool]:
+        """One plain-scheme check on U: ([total KE-rate difference, local
+        KE-rate difference, estimated KE history error, dissipation
+        difference], gate now off)."""
+        rel = np.zeros(4)
         dis = C.c_int32(0)
-        _check(self._lib, self._lib.ucns_gate_check(self._h, _dev_ptr(U, self.n_cells), C.byref(rel), C.byref(dis),
-                                                    _stream_ptr(stream)))
-        return rel.value, bool(dis.value)
+        _check(self._lib, self._lib.ucns_gate_check(self._h, _dev_ptr(U, self.n_cells), rel.ctypes.data,
+                                                    C.byref(dis), _stream_ptr(stream)))
+        return rel.tolist(), bool(dis.value)
+
+    def gate_status(self) -> dict:
+        """{"enabled", "steps", "checks", "off_step" (-1: never), "last": the four measures}."""
+        en = C.c_int32(0)
+        cnt = np.zeros(3, dtype=np.int64)
+        last = np.zeros(4)
+        _check(self._lib, self._lib.ucns_gate_status(self._h, C.byref(en), cnt.ctypes.data, last.ctypes.data))
+        return {"enabled": bool(en.value), "steps": int(cnt[0]), "checks": int(cnt[1]), "off_step": int(cnt[2]),
+                "last": last.tolist()}
+
+    def gate_set_flags(self, flags, stream=None):
+        """Use caller flags (cuda uint8/bool tensor [N], internal order; nonzero:
+        CWENOZ, 0: linear weights) in place of the network; None returns to it."""
+        import torch
+
+        if flags is None:
+            _check(self._lib, self._lib.ucns_gate_set_flags(self._h, None, _stream_ptr(stream)))
+            self._fixed_flags = None
+            return
+        f = flags.to(torch.uint8).contiguous()
+        if not (f.is_cuda and tuple(f.shape) == (self.n_cells,)):
+            raise ValueError(f"flags must be a cuda tensor of shape ({self.n_cells},)")
+        self._fixed_flags = f  # kept alive until the stream has copied it
+        _check(self._lib, self._lib.ucns_gate_set_flags(self._h, f.data_ptr(), _stream_ptr(stream)))
+
+    def gate_flags(self, stream=None):
+        """The flags of the last gate evaluation (cuda uint8 [N], internal order)."""
+        import torch
+
+        f = torch.empty(self.n_cells, dtype=torch.uint8, device="cuda")
+        _check(self._lib, self._lib.ucns_gate_flags(self._h, f.data_ptr(), _stream_ptr(stream)))
+        return f
 
     def gate_flagged(self, stream=None) -> int:
         n = C.c_int64(0)
@@ -420,6 +476,17 @@ class Net:
         z = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
         _check(self._lib, self._lib.ucns_mlp_forward(self._h, self._x(X), X.shape[0], z.data_ptr(), _stream_ptr(stream)))
         return z
+
+    def hidden(self, X, stream=None):
+        """(h1 bf16 [n, 64], z float32 [n]): the first hidden layer as fed to
+        the second layer's product, and the logits."""
+        import torch
+
+        h1 = torch.empty((X.shape[0], 64), dtype=torch.bfloat16, device=X.device)
+        z = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(self._lib, self._lib.ucns_mlp_hidden(self._h, self._x(X), X.shape[0], h1.data_ptr(), z.data_ptr(),
+                                                    _stream_ptr(stream)))
+        return h1, z
 
     def grad(self, X, y, w_pos: float = 1.0, w_neg: float = 1.0, stream=None):
         import torch

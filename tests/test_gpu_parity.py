@@ -64,6 +64,15 @@ CASES = [
     ("p2_cwenoz_jitter_12_M125", 12, 0.1, False, 2, 1, 1600.0, 1.25, "perturbed"),
     ("p2_cwenoz_tets_6", 6, 0.1, True, 2, 1, 1600.0, 0.1, "noisy"),
     ("p2_cwenoz_tets_7_inviscid", 7, 0.1, True, 2, 1, 0.0, 0.5, "noisy"),
+    # P3 / P4 (Sec. 2.2; Table 4 TGV-P3/P4): K = 19 / 34 modes over 38 / 68
+    # members, 6 linear / 18-member quadratic directional candidates, 9 / 16
+    # Gauss points per face; 10^3, 11^3 and 12^3 cells span many blocks with
+    # ragged tails (the face kernel packs 3 / 2 faces per warp)
+    ("p3_linear_jitter_10", 10, 0.1, False, 3, 0, 1600.0, 0.3, "noisy"),
+    ("p3_cwenoz_jitter_11", 11, 0.1, False, 3, 1, 1600.0, 0.3, "noisy"),
+    ("p3_cwenoz_jitter_10_M125", 10, 0.1, False, 3, 1, 1600.0, 1.25, "perturbed"),
+    ("p4_linear_jitter_10_inviscid", 10, 0.1, False, 4, 0, 0.0, 0.3, "noisy"),
+    ("p4_cwenoz_jitter_12", 12, 0.1, False, 4, 1, 1600.0, 0.3, "noisy"),
 ]
 
 
@@ -122,7 +131,8 @@ def test_rk_steps_and_time_step_parity():
     assert np.all(err <= 1e-12), err
 
 
-@pytest.mark.parametrize("order,scheme,n,tets", [(1, 0, 12, False), (2, 1, 10, False), (2, 1, 6, True)])
+@pytest.mark.parametrize("order,scheme,n,tets", [(1, 0, 12, False), (2, 1, 10, False), (2, 1, 6, True),
+                                                (3, 1, 10, False), (4, 1, 10, False)])
 def test_ssp54_steps_parity(order, scheme, n, tets):
     """The paper's fourth-order SSP scheme (integrator 1: SSP(5,4), five
     residual evaluations per step): 5 steps with the CFL time step on both
@@ -340,3 +350,32 @@ def test_time_step_equal_limits_and_low_pressure(Re):
         m.time_step(Ug)
     assert e.value.code == -5
     m.check_state()
+
+
+def test_bounded_wait_timeout_reaches_the_caller():
+    """The give-up path of the bounded mbarrier waits, on a phase that
+    nothing completes (no copy, no MMA in flight, a ~1 ms limit): the
+    reconstruction's wait sets the mesh's error word, the call returns
+    UCNS_ERR_TIMEOUT and clears it, and the mesh keeps working (a following
+    check is clean and a residual matches the one before); the network's wait
+    likewise through its own error word."""
+    nodes, cells, box = I.hex_lattice(8, jitter=0.1, seed=2)
+    m = ucns.Mesh(nodes, cells, box, ucns.Params(order=2, scheme=1, precision=1))
+    U = torch.from_numpy(np.ascontiguousarray(m.to_internal(I.tgv_state(nodes, cells, 0.1)))).cuda()
+    R0 = m.residual(U).clone()
+    lib = m._lib
+    s = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        assert lib.ucns_probe_bounded_wait(m._h, s) == -6  # UCNS_ERR_TIMEOUT
+        assert "bounded wait" in lib.ucns_last_error().decode()
+        m.check_state()  # cleared
+    assert torch.equal(m.residual(U), R0)
+    m.check_state()
+    net = ucns.Net(seed=2)
+    for _ in range(2):
+        assert lib.ucns_mlp_probe_bounded_wait(net._h, s) == -6
+        net.check()  # cleared
+    X = torch.zeros((256, 32), dtype=torch.bfloat16, device="cuda")
+    z = net.forward(X)
+    net.check()
+    assert torch.isfinite(z).all()

@@ -54,7 +54,13 @@ def test_error_codes_without_gpu():
     rc = lib.ucns_residual(m._h, None, None, None)
     assert rc == -7
     with pytest.raises(ucns.UcnsError) as e:
-        m.precompute_host(ucns.Params(order=3))
+        m.precompute_host(ucns.Params(order=5))
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:
+        m.precompute_host(ucns.Params(order=3, precision=1))  # the mixed form is built for P1 and P2
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:  # orders 3 and 4 on hexahedra only
+        ucns.Mesh(nodes, I.split_tets(cells), box).precompute_host(ucns.Params(order=3))
     assert e.value.code == -1
     with pytest.raises(ucns.UcnsError) as e:
         m.precompute_host(ucns.Params(order=1, scheme=1))
@@ -79,9 +85,29 @@ def test_cell_order_is_a_locality_permutation():
     assert np.median(d) < 1.5 * (2 * np.pi / 16)
 
 
-@pytest.mark.parametrize("kind,order,scheme", [("hex", 1, 0), ("hex", 2, 1), ("tet", 2, 1)])
+# basis monomials (exponents of x, y, z) in each side's row order: the
+# library's as include/ucns.h states it, the oracle's as its source states it
+_LIB_BASIS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1),
+              (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2),
+              (0, 0, 3), (4, 0, 0), (3, 1, 0), (3, 0, 1), (2, 2, 0), (2, 1, 1), (2, 0, 2), (1, 3, 0), (1, 2, 1),
+              (1, 1, 2), (1, 0, 3), (0, 4, 0), (0, 3, 1), (0, 2, 2), (0, 1, 3), (0, 0, 4)]
+_ORC_BASIS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1),
+              (3, 0, 0), (0, 3, 0), (0, 0, 3), (2, 1, 0), (2, 0, 1), (1, 2, 0), (0, 2, 1), (1, 0, 2), (0, 1, 2),
+              (1, 1, 1), (4, 0, 0), (0, 4, 0), (0, 0, 4), (3, 1, 0), (3, 0, 1), (1, 3, 0), (0, 3, 1), (1, 0, 3),
+              (0, 1, 3), (2, 2, 0), (2, 0, 2), (0, 2, 2), (2, 1, 1), (1, 2, 1), (1, 1, 2)]
+
+
+@pytest.mark.parametrize("kind,order,scheme", [("hex", 1, 0), ("hex", 2, 1), ("tet", 2, 1), ("hex", 3, 1),
+                                               ("hex", 4, 1)])
 def test_host_precompute_matches_oracle(kind, order, scheme):
-    nodes, cells, box = I.hex_lattice(6 if kind == "hex" else 5, jitter=0.1, seed=11)
+    """The library's host precompute (moment-form least-squares rows from each
+    cell's central moments, Householder QR) against the oracle's (rows by
+    quadrature, Gram-Schmidt QR): the same stencil members and the same
+    pseudo-inverse P' = A^+ diag(|V_m|) of Eq. 4, row by row after matching the
+    two bases' monomials, for central and directional stencils (P4: 18-member
+    quadratic candidates)."""
+    nodes, cells, box = I.hex_lattice(6 if kind == "hex" and order <= 2 else (8 if kind == "hex" else 5),
+                                      jitter=0.1, seed=11)
     if kind == "tet":
         cells = I.split_tets(cells)
     params = ucns.Params(order=order, scheme=scheme)
@@ -95,8 +121,9 @@ def test_host_precompute_matches_oracle(kind, order, scheme):
             omem, _, _, oP = oc.stencil(int(i), which)
             assert sorted(mem) == sorted(omem), (i, which)
             pos = {c: k for k, c in enumerate(omem)}
-            oPm = oP[:, [pos[c] for c in mem]]
-            assert np.abs(P - oPm).max() <= 1e-12 * np.abs(oPm).max(), (i, which)
+            rows = [_ORC_BASIS.index(e) for e in _LIB_BASIS[:P.shape[0]]]
+            oPm = oP[rows][:, [pos[c] for c in mem]]
+            assert np.abs(P - oPm).max() <= 1e-12 * np.abs(oPm).max(), (i, which, np.abs(P - oPm).max())
 
 
 def test_product_path_never_touches_the_oracle():

@@ -101,11 +101,17 @@ typedef struct ucns_mesh ucns_mesh; /* opaque, library-owned */
  * place of the halo exchange).
  *  nodes       host [n_nodes][3] float64, copied.
  *  cell_nodes  host [n_cells][nodes_per_cell] int64 node ids, copied.
- *              nodes_per_cell = 8 (hexahedron, VTK node order) or 4
- *              (tetrahedron, positive orientation).
- *  periodic_box host [3] box lengths; nodes equal modulo these lengths are one
- *              node.  Every element face must pair with exactly one other
- *              (closed periodic meshes only: UCNS_ERR_MESH otherwise).
+ *              nodes_per_cell = 8 (hexahedron, VTK node order), 6 (triangular
+ *              prism: base 0 1 2 counter-clockwise seen from the top 3 4 5,
+ *              node k + 3 above node k), 5 (pyramid: base 0 1 2 3
+ *              counter-clockwise seen from the apex 4) or 4 (tetrahedron,
+ *              positive orientation); one element type per mesh (Sec. 2.2's
+ *              element types).
+ *  periodic_box host [3] box lengths (NULL: none); an axis of length > 0 is
+ *              periodic (nodes equal modulo the length are one node), an axis
+ *              of length 0 is not: the element faces on its two planes are
+ *              boundary faces, of the kinds ucns_mesh_set_boundary sets.  Every
+ *              other element face must pair with exactly one other.
  *  out         receives the handle; free it with ucns_mesh_destroy.
  * Errors: INVALID_ARG (also n_cells >= 2^31 / 10 = 214,748,364: device
  * indexing is 32-bit), MESH (bad node id, non-positive volume, unpaired or
@@ -114,11 +120,36 @@ int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_n
                      int64_t n_cells, int32_t nodes_per_cell, const double* periodic_box,
                      ucns_mesh** out);
 
+/* Boundary kinds of the box sides of non-periodic axes (the paper's
+ * boundary-condition kernel, Sec. 3.6: ghost states at the boundary Gauss
+ * points), for inviscid flows: the ghost state of a boundary Gauss point is
+ * the mirror image of the owner's reconstructed state (UCNS_BC_SLIP_WALL, and
+ * UCNS_BC_SYMMETRY, the same for a symmetry plane: density and energy kept,
+ * normal momentum reversed), that state itself (UCNS_BC_SUPERSONIC_OUTFLOW:
+ * extrapolation), or the given state (UCNS_BC_SUPERSONIC_INFLOW); the face
+ * flux is HLLC between the two.  A boundary face's side is the axis of the
+ * largest component of its outward area vector and that component's sign.
+ * Stencils stop at boundary faces (one-sided), and a cell has no directional
+ * candidate across a boundary face, its linear weights being normalised over
+ * the candidates it has.
+ *  kinds   host int32 [6]: the kinds of the sides x-, x+, y-, y+, z-, z+
+ *          (sides of periodic axes are ignored); default all UCNS_BC_SLIP_WALL.
+ *  inflow  host [5] conserved inflow state, needed when a side is an inflow.
+ * Takes effect at the next ucns_precompute (the mesh needs one again).
+ * Errors: INVALID_ARG. */
+#define UCNS_BC_SLIP_WALL 0
+#define UCNS_BC_SYMMETRY 1
+#define UCNS_BC_SUPERSONIC_OUTFLOW 2
+#define UCNS_BC_SUPERSONIC_INFLOW 3
+int ucns_mesh_set_boundary(ucns_mesh* mesh, const int32_t* kinds, const double* inflow);
+
 /* Geometry, quadrature, stencils and least-squares pseudo-inverses
  * (Eq. 4: P' = A^+ diag(|V_m|), A_mk = int_{V_m} phi_k, by Householder QR in
  * FP64 on the host), uploaded to the current CUDA device once.  May be called
- * again with other parameters (re-uploads).  Errors: INVALID_ARG, STENCIL,
- * CUDA, NOMEM. */
+ * again with other parameters (re-uploads).  Meshes with boundary faces need
+ * an inviscid flow (reynolds <= 0); boundary faces, prisms and pyramids are
+ * built in the FP64 form at P1 and P2.  Errors: INVALID_ARG, STENCIL, CUDA,
+ * NOMEM. */
 int ucns_precompute(ucns_mesh* mesh, const ucns_params* params);
 
 /* Host half of ucns_precompute only (no CUDA call): geometry, stencils and
@@ -324,25 +355,30 @@ int ucns_gate_enable(ucns_mesh* mesh, int32_t enable);
  *       check_every times the CFL time step of the state, divided by the
  *       volume-averaged kinetic energy (KE's drift from the full scheme's
  *       until the next check, to first order);
- *   [3] |eps_gated - eps_full| / eps_full, eps = eps_s + eps_d the total
- *       dissipation (ucns_diag) of the two reconstructions of the state: the
- *       gate's error in the dissipation history at that state.
- * The gate is switched off for the rest of the run when [2] or [3] exceeds
- * `bound` (the target error of the kinetic-energy and dissipation
- * histories), or [0] exceeds bound_rate (bound_rate = 0: not used).  A check
+ *   [3] |eps_s,gated - eps_s,full| / eps_s,full, the solenoidal dissipation
+ *       (ucns_diag) of the two reconstructions of the state;
+ *   [4] |eps_d,gated - eps_d,full| / max(eps_d,full, 1e-3 eps_s,full), the
+ *       dilatational one (against a thousandth of the solenoidal one where
+ *       it is smaller: at low Mach numbers it lies below the arithmetic's
+ *       resolution of the dissipation);
+ *   [3] and [4] are the gate's error in the dissipation histories at that
+ *   state.  The gate is switched off for the rest of the run when [2], [3] or
+ * [4] exceeds `bound` (the target error of the kinetic-energy and
+ * dissipation histories), or [0] exceeds bound_rate (bound_rate = 0: not
+ * used).  A check
  * synchronises the stream.  check_every = 0 disables the checks.  Resets the
  * step and check counters and the running estimate.  Defaults: eval_every 1,
  * check_every 0, bound 1e-4, bound_rate 0. */
 int ucns_gate_configure(ucns_mesh* mesh, int32_t eval_every, int32_t check_every, double bound,
                         double bound_rate);
-/* Run one check now on U (counted as check_every steps, at least 1): the four
- * measures above into host double[4] `measures`, and *disabled (may be NULL)
+/* Run one check now on U (counted as check_every steps, at least 1): the five
+ * measures above into host double[5] `measures`, and *disabled (may be NULL)
  * whether the gate is now off. */
 int ucns_gate_check(ucns_mesh* mesh, const double* U, double* measures, int32_t* disabled, void* stream);
 /* State of the gate (host outputs, each may be NULL): *enabled whether it is
  * on (a network attached and not switched off); counts[0..2] = gated steps
  * and checks since ucns_gate_configure, and the gated step at which a check
- * switched it off (-1: none); last[0..3] = the four measures of the last
+ * switched it off (-1: none); last[0..4] = the five measures of the last
  * check (-1 before the first).  No device work. */
 int ucns_gate_status(const ucns_mesh* mesh, int32_t* enabled, int64_t* counts, double* last);
 

@@ -287,17 +287,28 @@ int launch_recon_raw(ucns_mesh* m, const double* U, cudaStream_t s) {
   a.coef = m->d.coef;
   a.gate = m->gate_eval_active ? m->gate_flag : nullptr;
   a.dev = m->label_out;
+  a.dvalid = m->d.dvalid;
   a.N = (int)m->N;
   const double lsum = m->P.lambda_central + m->nd;
   a.lam0 = m->P.lambda_central / lsum;
   a.lams = 1.0 / lsum;
+  a.lamc = m->P.lambda_central;
   a.eps = m->P.epsilon;
   const unsigned g = nblocks((size_t)m->N * 5);
   const bool gated = a.gate != nullptr;
+  const bool walls = m->n_boundary > 0;
   if (m->K == 3)
     k_recon<1, false, 6, false><<<g, 256, 0, s>>>(a);
   else if (m->nd == 0)
     k_recon<2, false, 6, false><<<g, 256, 0, s>>>(a);
+  else if (walls && m->nd == 6)
+    k_recon<2, true, 6, false, true><<<g, 256, 0, s>>>(a);
+  else if (walls && m->nd == 5)
+    k_recon<2, true, 5, false, true><<<g, 256, 0, s>>>(a);
+  else if (walls)
+    k_recon<2, true, 4, false, true><<<g, 256, 0, s>>>(a);
+  else if (m->nd == 5)
+    k_recon<2, true, 5, false><<<g, 256, 0, s>>>(a);
   else if (m->nd == 6 && gated)
     k_recon<2, true, 6, true><<<g, 256, 0, s>>>(a);
   else if (m->nd == 6)
@@ -324,9 +335,13 @@ int launch_face_raw(ucns_mesh* m, cudaStream_t s) {
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.c = flux_const(m->P);
+  for (int v = 0; v < 5; v++) a.uinf[v] = m->uinf[v];
   const bool visc = m->P.reynolds > 0.0;
   const unsigned g = nblocks((size_t)m->F * m->nq);
-  if (m->K == 3) {
+  if (m->n_boundary > 0) {  // inviscid (checked at precompute)
+    if (m->K == 3) k_face<1, false, true><<<g, 256, 0, s>>>(a);
+    else k_face<2, false, true><<<g, 256, 0, s>>>(a);
+  } else if (m->K == 3) {
     if (visc) k_face<1, true><<<g, 256, 0, s>>>(a);
     else k_face<1, false><<<g, 256, 0, s>>>(a);
   } else {
@@ -362,6 +377,7 @@ int launch_rk_raw(ucns_mesh* m, int stage, const double* U0, const double* Us, d
       else k_rk<ST, 4, float><<<g, 256, 0, s>>>(a);                           \
     } else {                                                                  \
       if (m->nfc == 6) k_rk<ST, 6, double><<<g, 256, 0, s>>>(a);              \
+      else if (m->nfc == 5) k_rk<ST, 5, double><<<g, 256, 0, s>>>(a);         \
       else k_rk<ST, 4, double><<<g, 256, 0, s>>>(a);                          \
     }                                                                         \
   } while (0)
@@ -401,6 +417,7 @@ int launch_rk54_raw(ucns_mesh* m, int stage, const double* U0, const double* Us,
       else k_rk54<ST, 4, float><<<g, 256, 0, s>>>(a);                         \
     } else {                                                                  \
       if (m->nfc == 6) k_rk54<ST, 6, double><<<g, 256, 0, s>>>(a);            \
+      else if (m->nfc == 5) k_rk54<ST, 5, double><<<g, 256, 0, s>>>(a);       \
       else k_rk54<ST, 4, double><<<g, 256, 0, s>>>(a);                        \
     }                                                                         \
   } while (0)
@@ -593,11 +610,15 @@ int diag_sums_into(ucns_mesh* m, const double* U, double* out, cudaStream_t s) {
 //          the volume-averaged dKE/dt, times (steps until the next check) * dt
 //          / KE, the drift of KE from the full scheme's over that interval to
 //          first order;
-//  rel[3]  |eps_gated - eps_full| / eps_full, eps = eps_s + eps_d the total
-//          dissipation of the two reconstructions of U (the dissipation
-//          history's error from the gate at this state).
-// The gate goes off when rel[2] or rel[3] exceeds the bound, or rel[0] exceeds
-// the optional rate bound (> 0).  `steps` is the interval to the next check.
+//  rel[3]  |eps_s,gated - eps_s,full| / eps_s,full, the solenoidal
+//          dissipation of the two reconstructions of U;
+//  rel[4]  |eps_d,gated - eps_d,full| / max(eps_d,full, 1e-3 eps_s,full), the
+//          dilatational one (measured against a thousandth of the solenoidal
+//          one where it is smaller: at low Mach number it is below the
+//          arithmetic's resolution of the dissipation).
+// The gate goes off when rel[2], rel[3] or rel[4] exceeds the bound, or rel[0]
+// exceeds the optional rate bound (> 0).  `steps` is the interval to the next
+// check.
 int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s, int steps) {
   int rc;
   const size_t n5 = (size_t)5 * m->N;
@@ -626,11 +647,13 @@ int gate_check(ucns_mesh* m, const double* U, double* rel, cudaStream_t s, int s
   const double ke = h[4] / h[7];
   m->gate_ke_err += std::fabs(a - b) * (double)std::max(steps, 1) * h[13] / std::fmax(ke, 1e-300);
   rel[2] = m->gate_ke_err;
-  const double eg = h[1] + (4.0 / 3.0) * h[2], ef = h[5] + (4.0 / 3.0) * h[6];  // (Re and volume cancel)
-  rel[3] = std::fabs(eg - ef) / std::fmax(std::fabs(ef), 1e-300);
-  for (int q = 0; q < 4; q++) m->gate_last[q] = rel[q];
+  // eps_s ~ sum V |curl u|^2, eps_d ~ 4/3 sum V (div u)^2 (1/Re and the volume cancel in the ratios)
+  const double sg = h[1], sf = h[5], dg = (4.0 / 3.0) * h[2], df = (4.0 / 3.0) * h[6];
+  rel[3] = std::fabs(sg - sf) / std::fmax(std::fabs(sf), 1e-300);
+  rel[4] = std::fabs(dg - df) / std::fmax(std::fmax(std::fabs(df), 1e-3 * std::fabs(sf)), 1e-300);
+  for (int q = 0; q < kGateMeasures; q++) m->gate_last[q] = rel[q];
   m->gate_checks++;
-  const bool bad = !(rel[2] <= m->gate_bound) || !(rel[3] <= m->gate_bound) ||
+  const bool bad = !(rel[2] <= m->gate_bound) || !(rel[3] <= m->gate_bound) || !(rel[4] <= m->gate_bound) ||
                    (m->gate_bound_rate > 0.0 && !(rel[0] <= m->gate_bound_rate));
   if (bad) {
     m->gate_on = false;
@@ -650,7 +673,7 @@ int rk_step_device(ucns_mesh* m, double* U, cudaStream_t s, bool dt_pending = fa
   const int64_t step = m->gate_steps;
   bool split_done = pair_fresh, checked = false;
   if (!m->gate_fixed && m->gate_on && m->mlp && m->gate_check_every > 0 && step % m->gate_check_every == 0) {
-    double rel[4];
+    double rel[kGateMeasures];
     if ((rc = gate_check(m, U, rel, s, m->gate_check_every))) return rc;
     // the check evaluated the flags on this very state (and left its float pair in place)
     checked = m->gate_on;
@@ -733,7 +756,7 @@ void device_free(ucns_mesh* m) {
   m->gate_fixed = false;
   DeviceMesh& d = m->d;
   void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
-                  d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
+                  d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.dvalid, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -755,25 +778,23 @@ int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_n
   *out = nullptr;
   if (!nodes || !cell_nodes || n_nodes <= 0 || n_cells <= 0)
     return fail(UCNS_ERR_INVALID_ARG, "nodes/cells must be non-NULL and non-empty");
-  if (nodes_per_cell != 8 && nodes_per_cell != 4)
-    return fail(UCNS_ERR_INVALID_ARG, "nodes_per_cell must be 8 (hex) or 4 (tet)");
+  if (nodes_per_cell != 8 && nodes_per_cell != 6 && nodes_per_cell != 5 && nodes_per_cell != 4)
+    return fail(UCNS_ERR_INVALID_ARG, "nodes_per_cell must be 8 (hexahedron), 6 (prism), 5 (pyramid) or 4 (tetrahedron)");
   if (n_cells >= (int64_t(1) << 31) / 10)
     return fail(UCNS_ERR_INVALID_ARG, "too many cells for 32-bit device indexing");
-  if (!periodic_box) return fail(UCNS_ERR_INVALID_ARG, "periodic_box is required (closed periodic meshes only)");
-  for (int d = 0; d < 3; d++)
-    if (!(periodic_box[d] > 0.0) || !std::isfinite(periodic_box[d]))
-      return fail(UCNS_ERR_INVALID_ARG, "periodic box lengths must be positive and finite");
+  for (int d = 0; periodic_box && d < 3; d++)
+    if (!(periodic_box[d] >= 0.0) || !std::isfinite(periodic_box[d]))
+      return fail(UCNS_ERR_INVALID_ARG, "box lengths must be finite and >= 0 (0: the axis is not periodic)");
   ucns_mesh* m = new (std::nothrow) ucns_mesh();
   if (!m) return fail(UCNS_ERR_NOMEM, "out of host memory");
   try {
     m->N = n_cells;
     m->nn = n_nodes;
     m->npc = nodes_per_cell;
-    m->nfc = nodes_per_cell == 8 ? 6 : 4;
-    m->nfn = nodes_per_cell == 8 ? 4 : 3;
+    m->nfc = nodes_per_cell == 8 ? 6 : (nodes_per_cell == 4 ? 4 : 5);
     for (int d = 0; d < 3; d++) {
-      m->L[d] = periodic_box[d];
-      m->per[d] = 1;
+      m->L[d] = periodic_box ? periodic_box[d] : 0.0;
+      m->per[d] = m->L[d] > 0.0;
     }
     m->X.assign(nodes, nodes + 3 * n_nodes);
     m->C.assign(cell_nodes, cell_nodes + nodes_per_cell * n_cells);
@@ -790,6 +811,23 @@ int ucns_mesh_create(const double* nodes, int64_t n_nodes, const int64_t* cell_n
   return UCNS_OK;
 }
 
+int ucns_mesh_set_boundary(ucns_mesh* m, const int32_t* kinds, const double* inflow) {
+  if (!m || !kinds) return fail(UCNS_ERR_INVALID_ARG, "mesh or kinds is NULL");
+  for (int k = 0; k < 6; k++)
+    if (kinds[k] < UCNS_BC_SLIP_WALL || kinds[k] > UCNS_BC_SUPERSONIC_INFLOW)
+      return fail(UCNS_ERR_INVALID_ARG, "unknown boundary kind");
+  bool need_inflow = false;
+  for (int k = 0; k < 6; k++) need_inflow = need_inflow || kinds[k] == UCNS_BC_SUPERSONIC_INFLOW;
+  if (need_inflow && !inflow) return fail(UCNS_ERR_INVALID_ARG, "an inflow side needs the inflow state");
+  if (need_inflow)
+    for (int v = 0; v < 5; v++)
+      if (!std::isfinite(inflow[v])) return fail(UCNS_ERR_INVALID_ARG, "inflow state must be finite");
+  for (int k = 0; k < 6; k++) m->bc[k] = kinds[k];
+  for (int v = 0; v < 5; v++) m->uinf[v] = need_inflow ? inflow[v] : 0.0;
+  m->precomputed = false;  // the boundary kinds enter the precompute
+  return UCNS_OK;
+}
+
 static int check_params(const ucns_mesh* m, const ucns_params* p) {
   if (!m || !p) return fail(UCNS_ERR_INVALID_ARG, "mesh or params is NULL");
   if (p->order < 1 || p->order > 4) return fail(UCNS_ERR_INVALID_ARG, "order must be 1, 2, 3 or 4");
@@ -802,6 +840,10 @@ static int check_params(const ucns_mesh* m, const ucns_params* p) {
   if (p->precision == UCNS_PREC_MIXED && p->order > 2)
     return fail(UCNS_ERR_INVALID_ARG, "the mixed form is built for orders 1 and 2");
   if (p->order > 2 && m->npc != 8) return fail(UCNS_ERR_INVALID_ARG, "orders 3 and 4 are built for hexahedra only");
+  if (m->n_boundary > 0 && p->reynolds > 0.0)
+    return fail(UCNS_ERR_INVALID_ARG, "boundary faces are built for inviscid flows (Re <= 0) only");
+  if ((m->n_boundary > 0 || m->npc == 6 || m->npc == 5) && (p->precision != UCNS_PREC_FP64 || p->order > 2))
+    return fail(UCNS_ERR_INVALID_ARG, "boundary faces, prisms and pyramids are built in the FP64 form at P1 and P2");
   if (p->integrator != UCNS_RK_SSP3 && p->integrator != UCNS_RK_SSP54)
     return fail(UCNS_ERR_INVALID_ARG, "unknown integrator");
   if (!(p->gamma > 1.0) || !(p->mach > 0.0) || !(p->cfl > 0.0) || !(p->lambda_central > 0.0) ||
@@ -865,10 +907,13 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   std::vector<int32_t> fo(m->fo), fn(m->fn), cf((size_t)m->nfc * m->N);
   for (int64_t i = 0; i < m->N; i++)
     for (int j = 0; j < m->nfc; j++) cf[(size_t)j * m->N + i] = m->cf[(size_t)i * m->nfc + j];
+  for (int64_t f = 0; f < m->F; f++)
+    if (fn[f] < 0) fn[f] = -1 - (int32_t)h.fkind[f];  // a boundary face carries its kind
   if ((rc = upload(&d.vol, h.vol)) || (rc = upload(&d.inv_vol, h.inv_vol)) ||
       (rc = upload(&d.inv_h, h.inv_h)) || (rc = upload(&d.dtlen, h.dtlen)) ||
       (rc = upload(&d.mom, h.mom)) || (rc = upload(&d.sc, h.sc)) || (rc = upload(&d.sd, h.sd)) ||
-      (rc = upload(&d.cf, cf)) || (rc = upload(&d.fo, fo)) || (rc = upload(&d.fn, fn))) {
+      (rc = upload(&d.cf, cf)) || (rc = upload(&d.fo, fo)) || (rc = upload(&d.fn, fn)) ||
+      (m->n_boundary > 0 && (rc = upload(&d.dvalid, h.dvalid)))) {
     device_free(m);
     return rc;
   }
@@ -1133,7 +1178,8 @@ int ucns_gate_features(ucns_mesh* m, const double* U, void* X, float* Xf, void* 
   if (rc) return rc;
   if (!U || !X) return fail(UCNS_ERR_INVALID_ARG, "U or X is NULL");
   if (((uintptr_t)X & 15) != 0) return fail(UCNS_ERR_INVALID_ARG, "X must be 16-byte aligned");
-  if (m->K != 9) return fail(UCNS_ERR_INVALID_ARG, "features need order 2");
+  if (m->K != 9 || m->nfc == 5 || m->n_boundary > 0)
+    return fail(UCNS_ERR_INVALID_ARG, "features need a periodic P2 mesh of hexahedra or tetrahedra");
   return launch_features(m, U, X, Xf, (cudaStream_t)stream);
 }
 
@@ -1141,7 +1187,8 @@ int ucns_gate_labels(ucns_mesh* m, const double* U, float* dev, void* stream) {
   int rc = check_ready(m);
   if (rc) return rc;
   if (!U || !dev) return fail(UCNS_ERR_INVALID_ARG, "U or dev is NULL");
-  if (mixed(m) || m->nd == 0 || m->K != 9) return fail(UCNS_ERR_INVALID_ARG, "labels need an FP64 P2 CWENOZ mesh");
+  if (mixed(m) || m->nd == 0 || m->K != 9 || m->n_boundary > 0 || m->nfc == 5)
+    return fail(UCNS_ERR_INVALID_ARG, "labels need a periodic FP64 P2 CWENOZ mesh of hexahedra or tetrahedra");
   cudaStream_t s = (cudaStream_t)stream;
   UCNS_CUDA(cudaMemsetAsync(dev, 0, sizeof(float) * m->N, s));
   m->gate_eval_active = false;
@@ -1165,7 +1212,8 @@ static int gate_buffers(ucns_mesh* m) {
 int ucns_gate_attach(ucns_mesh* m, ucns_mlp* mlp, float threshold) {
   int rc = check_ready(m);
   if (rc) return rc;
-  if (mlp && (m->K != 9 || m->nd == 0)) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
+  if (mlp && (m->K != 9 || m->nd == 0 || m->n_boundary > 0 || m->nfc == 5))
+    return fail(UCNS_ERR_INVALID_ARG, "the gate needs a periodic P2 CWENOZ mesh of hexahedra or tetrahedra");
   if (mlp && (rc = gate_buffers(m))) return rc;
   m->mlp = mlp;
   m->gate_thr = threshold;
@@ -1198,7 +1246,7 @@ int ucns_gate_configure(ucns_mesh* m, int32_t eval_every, int32_t check_every, d
   m->gate_checks = 0;
   m->gate_off_step = -1;
   m->gate_ke_err = 0.0;
-  for (int q = 0; q < 4; q++) m->gate_last[q] = -1.0;
+  for (int q = 0; q < kGateMeasures; q++) m->gate_last[q] = -1.0;
   return UCNS_OK;
 }
 
@@ -1222,7 +1270,7 @@ int ucns_gate_status(const ucns_mesh* m, int32_t* enabled, int64_t* counts, doub
     counts[2] = m->gate_off_step;
   }
   if (last)
-    for (int q = 0; q < 4; q++) last[q] = m->gate_last[q];
+    for (int q = 0; q < kGateMeasures; q++) last[q] = m->gate_last[q];
   return UCNS_OK;
 }
 
@@ -1234,7 +1282,8 @@ int ucns_gate_set_flags(ucns_mesh* m, const uint8_t* flags, void* stream) {
     m->gate_flags_valid = false;
     return UCNS_OK;
   }
-  if (m->K != 9 || m->nd == 0) return fail(UCNS_ERR_INVALID_ARG, "the gate needs a P2 CWENOZ mesh");
+  if (m->K != 9 || m->nd == 0 || m->n_boundary > 0 || m->nfc == 5)
+    return fail(UCNS_ERR_INVALID_ARG, "the gate needs a periodic P2 CWENOZ mesh of hexahedra or tetrahedra");
   if ((rc = gate_buffers(m))) return rc;
   UCNS_CUDA(cudaMemcpyAsync(m->gate_flag, flags, (size_t)m->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   m->gate_fixed = true;

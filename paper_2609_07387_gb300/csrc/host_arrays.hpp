@@ -16,7 +16,9 @@ struct HostArrays {
   std::vector<double> Msi;                               // P3/P4: [K(K+1)/2][N]
   std::vector<double> psib;                              // P3/P4: [K-3][N]
   std::vector<double> fq;                                // [nq][10][F] x-x_L, x-x_R', n, |dS|
-  std::vector<double> fpen;                              // [F]
+  std::vector<double> fpen;                              // [F] (0 on boundary faces)
+  std::vector<int8_t> fkind;                             // [F] -1 interior, else the boundary kind
+  std::vector<uint8_t> dvalid;                           // [N] bit s: directional candidate s exists
 };
 
 }  // namespace ucns

@@ -32,8 +32,10 @@ struct ReconArgs {
   double* __restrict__ coef;       // [NC][N][5] physical-unit monomial coefficients
   const uint8_t* __restrict__ gate;  // [N]: 0 -> linear weights (null: every cell CWENOZ)
   float* __restrict__ dev;           // [N]: max |omega - lambda| (null: not wanted)
+  const uint8_t* __restrict__ dvalid;  // [N] bit s: directional candidate s exists (WALLS kernels)
   int N;
   double lam0, lams, eps;  // normalised linear weights, epsilon
+  double lamc;             // the central stencil's linear weight before normalisation (WALLS kernels)
 };
 
 struct FaceArgs {
@@ -46,7 +48,11 @@ struct FaceArgs {
   double* __restrict__ G;  // [5][F]
   int N, F;
   FluxConst c;
+  double uinf[5];  // the supersonic inflow state (boundary faces of that kind)
 };
+
+// boundary kinds of the sides of a non-periodic box axis (UCNS_BC_* of the C ABI)
+constexpr int kBcSlipWall = 0, kBcSymmetry = 1, kBcOutflow = 2, kBcInflow = 3;
 
 struct RKArgs {
   const double* U0;  // U^n        (may alias out in stage 3)
@@ -160,7 +166,7 @@ __device__ __forceinline__ void viscous_flux(const double U[5], const double g[5
 
 // ------------------------------------------------------- reconstruction
 // thread = (cell i, variable v); tid = 5 i + v
-template <int ORDER, bool WENO, int ND, bool GATED>
+template <int ORDER, bool WENO, int ND, bool GATED, bool WALLS = false>
 __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
   constexpr int K = ORDER == 1 ? 3 : 9;
   constexpr int MC = 2 * K;
@@ -193,10 +199,14 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = ao[k];
   } else {
+    // WALLS: a cell on a boundary has no directional candidate across it;
+    // the linear weights are normalised over the candidates it has
+    const unsigned valid = WALLS ? (unsigned)a.dvalid[i] : (1u << ND) - 1u;
     double b[ND][3];
 #pragma unroll
     for (int s = 0; s < ND; s++) {
       b[s][0] = b[s][1] = b[s][2] = 0.0;
+      if (WALLS && !((valid >> s) & 1u)) continue;
 #pragma unroll
       for (int r = 0; r < MD; r++) {
         const int j = __ldg(&a.sd[((size_t)s * MD + r) * N + i]);
@@ -224,32 +234,41 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 #pragma unroll
     for (int s = 0; s < ND; s++) {
       SI[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
-      tau += fabs(SI0 - SI[s]);
+      if (!WALLS || ((valid >> s) & 1u)) tau += fabs(SI0 - SI[s]);
     }
-    tau *= (1.0 / ND);
+    double lam0 = a.lam0, lams = a.lams;
+    if (WALLS) {
+      const int nv = __popc(valid);
+      lam0 = a.lamc / (a.lamc + nv);
+      lams = 1.0 / (a.lamc + nv);
+      tau /= (double)nv;
+    } else {
+      tau *= (1.0 / ND);
+    }
     // omega~_s = lambda_s (1 + tau / (eps + SI_s)), normalised
-    const double w0 = a.lam0 * (1.0 + tau / (a.eps + SI0));
+    const double w0 = lam0 * (1.0 + tau / (a.eps + SI0));
     double ws[ND];
     double wsum = w0;
 #pragma unroll
     for (int s = 0; s < ND; s++) {
-      ws[s] = a.lams * (1.0 + tau / (a.eps + SI[s]));
+      ws[s] = (!WALLS || ((valid >> s) & 1u)) ? lams * (1.0 + tau / (a.eps + SI[s])) : 0.0;
       wsum += ws[s];
     }
     const double iws = 1.0 / wsum;
     if (a.dev) {  // deviation of the nonlinear from the linear weights (training labels)
-      double dv = fabs(w0 * iws - a.lam0);
+      double dv = fabs(w0 * iws - lam0);
 #pragma unroll
-      for (int s = 0; s < ND; s++) dv = fmax(dv, fabs(ws[s] * iws - a.lams));
+      for (int s = 0; s < ND; s++) dv = fmax(dv, fabs(ws[s] * iws - lams));
       atomicMax(reinterpret_cast<unsigned int*>(a.dev) + i, __float_as_uint((float)dv));
     }
     // p = omega_0 p_1 + sum_s omega_s p_s with p_1 = (p_opt - sum lambda_s p_s)/lambda_0
-    const double r0 = (w0 * iws) / a.lam0;
+    const double r0 = (w0 * iws) / lam0;
 #pragma unroll
     for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
 #pragma unroll
     for (int s = 0; s < ND; s++) {
-      const double e = ws[s] * iws - r0 * a.lams;
+      if (WALLS && !((valid >> s) & 1u)) continue;
+      const double e = ws[s] * iws - r0 * lams;
 #pragma unroll
       for (int k = 0; k < 3; k++) c[k] = fma(e, b[s][k], c[k]);
     }
@@ -309,8 +328,31 @@ __device__ __forceinline__ void eval_side(const double* __restrict__ coef, int N
   }
 }
 
-// thread = (face f, Gauss point q), NQ consecutive lanes per face
-template <int ORDER, bool VISC>
+// the ghost state of a boundary face at a Gauss point from the owner's state
+// UL and the unit outward normal n: the mirror image (slip wall or symmetry
+// plane: density and energy kept, normal momentum reversed), UL itself
+// (supersonic outflow: extrapolation), or the given inflow state
+__device__ __forceinline__ void ghost_state(int kind, const double UL[5], const double n[3], const double uinf[5],
+                                            double UR[5]) {
+  if (kind == kBcOutflow) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) UR[v] = UL[v];
+  } else if (kind == kBcInflow) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) UR[v] = uinf[v];
+  } else {
+    const double mn = UL[1] * n[0] + UL[2] * n[1] + UL[3] * n[2];
+    UR[0] = UL[0];
+#pragma unroll
+    for (int d = 0; d < 3; d++) UR[1 + d] = fma(-2.0 * mn, n[d], UL[1 + d]);
+    UR[4] = UL[4];
+  }
+}
+
+// thread = (face f, Gauss point q), NQ consecutive lanes per face.  BND: the
+// mesh has boundary faces (neighbour id -1 - kind), whose flux is HLLC
+// between the owner's state and its ghost state (inviscid flows only)
+template <int ORDER, bool VISC, bool BND = false>
 __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
   constexpr int NQ = ORDER * ORDER;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -326,11 +368,12 @@ __global__ void __launch_bounds__(256) k_face(FaceArgs a) {
   const int o = a.fo[fc], nb = a.fn[fc];
   double UL[5], UR[5], gs[5][3];  // gs = grad U_L + grad U_R
   eval_side<ORDER, false>(a.coef, a.N, o, xl, yl, zl, UL, gs);
-  eval_side<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, UR, gs);
+  if (BND && nb < 0) ghost_state(-1 - nb, UL, n, a.uinf, UR);
+  else eval_side<ORDER, true>(a.coef, a.N, nb, xr, yr, zr, UR, gs);
   double Fc[5];
   hllc_flux(UL, UR, n, a.c, Fc);
   double flux[5];
-  if (VISC) {
+  if (VISC && !BND) {
     // 2 U_f = U_L + U_R and 2 grad U_f = gs + 2 (alpha/L)(U_R - U_L) n: the viscous
     // flux depends on the face state only through ratios (u = m/rho, e = E/rho,
     // grad u = (grad m - u grad rho)/rho), so the common factor 2 cancels

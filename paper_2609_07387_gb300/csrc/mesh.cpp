@@ -25,8 +25,31 @@ const int kHexFace[6][4] = {{0, 4, 7, 3}, {1, 2, 6, 5}, {0, 1, 5, 4},
                             {3, 7, 6, 2}, {0, 3, 2, 1}, {4, 5, 6, 7}};
 // tetrahedron faces ordered so (p1-p0)x(p2-p0) points out of a positive tet
 const int kTetFace[4][3] = {{0, 2, 1}, {0, 1, 3}, {1, 2, 3}, {0, 3, 2}};
+// triangular prism (base 0 1 2 counter-clockwise seen from the top 3 4 5,
+// node k + 3 above node k): two triangles, then the three side quads, each
+// ordered so that its area vector points out of the cell
+const int kPrismFace[5][4] = {{0, 2, 1, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+// pyramid (base 0 1 2 3 counter-clockwise seen from the apex 4): the base
+// quad, then the four side triangles, outward
+const int kPyramidFace[5][4] = {{0, 3, 2, 1}, {0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}};
 
-const int* face_local_nodes(int npc, int lf) { return npc == 8 ? kHexFace[lf] : kTetFace[lf]; }
+const int* face_local_nodes(int npc, int lf) {
+  switch (npc) {
+    case 8: return kHexFace[lf];
+    case 6: return kPrismFace[lf];
+    case 5: return kPyramidFace[lf];
+    default: return kTetFace[lf];
+  }
+}
+// nodes of local face lf: 4 (quadrilateral) or 3 (triangle)
+int face_node_count(int npc, int lf) {
+  switch (npc) {
+    case 8: return 4;
+    case 6: return lf < 2 ? 3 : 4;
+    case 5: return lf == 0 ? 4 : 3;
+    default: return 3;
+  }
+}
 
 struct V3 {
   double x, y, z;
@@ -113,6 +136,23 @@ void map_point(int npc, const CellPts& c, double s, double t, double u, V3* x, d
     }
     *x = xs;
     *jac = dot(ds, cross(dt, du));
+  } else if (npc == 6) {
+    // prism: the base and top triangles' collapsed maps B(s, t) = P0 + s e1 +
+    // s t e2 (and T likewise), linear in between: x = (1 - u) B + u T
+    const V3 e1 = c.p[1] - c.p[0], e2 = c.p[2] - c.p[1], f1 = c.p[4] - c.p[3], f2 = c.p[5] - c.p[4];
+    const V3 B = c.p[0] + s * e1 + (s * t) * e2, T = c.p[3] + s * f1 + (s * t) * f2;
+    *x = (1 - u) * B + u * T;
+    const V3 ds = (1 - u) * (e1 + t * e2) + u * (f1 + t * f2);
+    const V3 dt = (1 - u) * (s * e2) + u * (s * f2);
+    const V3 du = T - B;
+    *jac = dot(ds, cross(dt, du));
+  } else if (npc == 5) {
+    // pyramid: the base's bilinear map Q(s, t) shrunk onto the apex: x = (1 - u) Q + u P4
+    const V3 Q = ((1 - s) * (1 - t)) * c.p[0] + (s * (1 - t)) * c.p[1] + (s * t) * c.p[2] + ((1 - s) * t) * c.p[3];
+    const V3 Qs = (1 - t) * (c.p[1] - c.p[0]) + t * (c.p[2] - c.p[3]);
+    const V3 Qt = (1 - s) * (c.p[3] - c.p[0]) + s * (c.p[2] - c.p[1]);
+    *x = (1 - u) * Q + u * c.p[4];
+    *jac = dot((1 - u) * Qs, cross((1 - u) * Qt, c.p[4] - Q));
   } else {
     V3 e1 = c.p[1] - c.p[0], e2 = c.p[2] - c.p[1], e3 = c.p[3] - c.p[2];
     *x = c.p[0] + s * e1 + (s * t) * e2 + (s * t * u) * e3;
@@ -217,7 +257,7 @@ double falling(int n, int k) {
 int face_points(const ucns_mesh* m, int64_t owner_user, int lf, int order, V3* x, V3* dS) {
   CellPts cp = load_cell(m, owner_user);
   const int* fl = face_local_nodes(m->npc, lf);
-  if (m->nfn == 4) {
+  if (face_node_count(m->npc, lf) == 4) {
     V3 Q0 = cp.p[fl[0]], Q1 = cp.p[fl[1]], Q2 = cp.p[fl[2]], Q3 = cp.p[fl[3]];
     double gx[kMaxOrder], gw[kMaxOrder];
     gauss01(order, gx, gw);
@@ -346,9 +386,10 @@ int build_topology(ucns_mesh* m) {
     for (int lf = 0; lf < m->nfc; lf++) {
       FE& e = fe[(size_t)c * m->nfc + lf];
       const int* fl = face_local_nodes(npc, lf);
+      const int nfn = face_node_count(npc, lf);
       e.k = {-1, -1, -1, -1};
-      for (int q = 0; q < m->nfn; q++) e.k[q] = m->canon[m->C[c * npc + fl[q]]];
-      std::sort(e.k.begin(), e.k.begin() + m->nfn);
+      for (int q = 0; q < nfn; q++) e.k[q] = m->canon[m->C[c * npc + fl[q]]];
+      std::sort(e.k.begin(), e.k.begin() + nfn);
       e.user = c;
       e.lf = lf;
     }
@@ -357,23 +398,32 @@ int build_topology(ucns_mesh* m) {
     return a.user < b.user;
   });
   const size_t ne = fe.size();
-  if (ne % 2) return fail(UCNS_ERR_MESH, "unpaired face (only closed periodic meshes are supported)");
-  m->F = (int64_t)(ne / 2);
-  if (m->F >= (int64_t(1) << 30)) return fail(UCNS_ERR_MESH, "too many faces");
+  const bool open = !(m->per[0] && m->per[1] && m->per[2]);
   struct FP {
     int64_t o_int;
     int lf, nlf;
-    int64_t n_int;
+    int64_t n_int;  // -1: a face on a non-periodic side of the box
   };
-  std::vector<FP> fp(m->F);
-  for (int64_t f = 0; f < m->F; f++) {
-    const FE& a = fe[2 * f];
-    const FE& b = fe[2 * f + 1];
-    if (a.k != b.k || (2 * f + 2 < (int64_t)ne && fe[2 * f + 2].k == b.k))
-      return fail(UCNS_ERR_MESH, "unpaired or non-manifold face");
-    if (a.user == b.user) return fail(UCNS_ERR_MESH, "a cell is its own face neighbour");
-    fp[f] = {m->iperm[a.user], a.lf, b.lf, m->iperm[b.user]};  // a.user < b.user: owner
+  std::vector<FP> fp;
+  fp.reserve(ne / 2 + 1);
+  for (size_t j = 0; j < ne;) {
+    const FE& a = fe[j];
+    if (j + 1 < ne && fe[j + 1].k == a.k) {
+      const FE& b = fe[j + 1];
+      if (j + 2 < ne && fe[j + 2].k == a.k) return fail(UCNS_ERR_MESH, "unpaired or non-manifold face");
+      if (a.user == b.user) return fail(UCNS_ERR_MESH, "a cell is its own face neighbour");
+      fp.push_back({m->iperm[a.user], a.lf, b.lf, m->iperm[b.user]});  // a.user < b.user: owner
+      j += 2;
+    } else {
+      if (!open) return fail(UCNS_ERR_MESH, "unpaired face (every axis of the box is periodic)");
+      fp.push_back({m->iperm[a.user], a.lf, -1, -1});
+      j += 1;
+    }
   }
+  m->F = (int64_t)fp.size();
+  if (m->F >= (int64_t(1) << 30)) return fail(UCNS_ERR_MESH, "too many faces");
+  m->n_boundary = 0;
+  for (const FP& q : fp) m->n_boundary += q.n_int < 0;
   std::sort(fp.begin(), fp.end(), [](const FP& a, const FP& b) {
     return a.o_int != b.o_int ? a.o_int < b.o_int : a.lf < b.lf;
   });
@@ -386,7 +436,7 @@ int build_topology(ucns_mesh* m) {
     m->fn[f] = (int32_t)fp[f].n_int;
     m->flf[f] = (int8_t)fp[f].lf;
     m->cf[(size_t)fp[f].o_int * m->nfc + fp[f].lf] = (int32_t)(f << 1);
-    m->cf[(size_t)fp[f].n_int * m->nfc + fp[f].nlf] = (int32_t)((f << 1) | 1);
+    if (fp[f].n_int >= 0) m->cf[(size_t)fp[f].n_int * m->nfc + fp[f].nlf] = (int32_t)((f << 1) | 1);
   }
   for (int32_t e : m->cf)
     if (e < 0) return fail(UCNS_ERR_MESH, "element face without a partner");
@@ -401,6 +451,7 @@ struct Cand {
   int64_t user;
 };
 
+// the cell across local face lf of cell i, -1 on a boundary face
 int64_t face_nbr(const ucns_mesh* m, int64_t i, int lf) {
   int32_t e = m->cf[(size_t)i * m->nfc + lf];
   int32_t f = e >> 1;
@@ -416,7 +467,7 @@ bool bfs(const ucns_mesh* m, int64_t start, int64_t avoid, int maxd, std::vector
     if (cur.depth == maxd) continue;
     for (int lf = 0; lf < m->nfc; lf++) {
       int64_t n = face_nbr(m, cur.id, lf);
-      if (n == avoid) continue;
+      if (n < 0 || n == avoid) continue;  // a boundary face, or the cell a directional search avoids
       bool seen = false;
       for (const Cand& c : out)
         if (c.id == n) { seen = true; break; }
@@ -536,27 +587,41 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   h->fq.assign((size_t)nq * 10 * F, 0.0);
   h->fpen.resize(F);
   std::vector<double> area(F);
+  h->fkind.assign(F, -1);
 #pragma omp parallel for schedule(static)
   for (int64_t f = 0; f < F; f++) {
     int64_t o = m->fo[f], n = m->fn[f];
     V3 x[16], dS[16];
     face_points(m, m->perm[o], m->flf[f], order, x, dS);
-    double s[3];
-    shift_of(o, n, s);
+    double s[3] = {0.0, 0.0, 0.0};
+    if (n >= 0) shift_of(o, n, s);
     V3 sv{s[0], s[1], s[2]};
     V3 tot{0, 0, 0};
     for (int q = 0; q < nq; q++) {
       double a = std::sqrt(dot(dS[q], dS[q]));
       V3 nh = (1.0 / a) * dS[q];
-      V3 xl = x[q] - g[o].c;       // offset from the owner's centroid
-      V3 xr = x[q] - sv - g[n].c;  // offset from the neighbour image's centroid
+      V3 xl = x[q] - g[o].c;  // offset from the owner's centroid
+      // offset from the neighbour image's centroid (a boundary face has none)
+      V3 xr = n >= 0 ? x[q] - sv - g[n].c : V3{0, 0, 0};
       double vals[10] = {xl.x, xl.y, xl.z, xr.x, xr.y, xr.z, nh.x, nh.y, nh.z, a};
       for (int c = 0; c < 10; c++) h->fq[((size_t)q * 10 + c) * F + f] = vals[c];
       tot = tot + dS[q];
     }
     area[f] = std::sqrt(dot(tot, tot));
-    V3 dc = g[n].c + sv - g[o].c;
-    h->fpen[f] = p->alpha / std::sqrt(dot(dc, dc));
+    if (n >= 0) {
+      V3 dc = g[n].c + sv - g[o].c;
+      h->fpen[f] = p->alpha / std::sqrt(dot(dc, dc));
+    } else {
+      // a face on a non-periodic side of the box: that side (the axis of the
+      // largest component of its outward area vector, and its sign) and the
+      // side's boundary kind
+      const double t3[3] = {tot.x, tot.y, tot.z};
+      int ax = 0;
+      for (int d = 1; d < 3; d++)
+        if (std::fabs(t3[d]) > std::fabs(t3[ax])) ax = d;
+      h->fkind[f] = (int8_t)m->bc[2 * ax + (t3[ax] > 0 ? 1 : 0)];
+      h->fpen[f] = 0.0;
+    }
   }
   for (int64_t i = 0; i < N; i++) {
     double asum = 0;
@@ -568,6 +633,7 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   h->Pc.assign((size_t)K * Mc * N, 0.0);
   h->sd.assign((size_t)nd * Md * N, 0);
   h->Pd.assign((size_t)nd * Kd * Md * N, 0.0);
+  h->dvalid.assign(nd ? N : 0, (uint8_t)((1u << nd) - 1u));
   if (order >= 3) {
     // per cell: the means of the non-linear basis monomials (xi units) and
     // the smoothness-indicator matrix of Eq. 6's reading, SI(a) = a^T M a,
@@ -671,6 +737,13 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
       for (int r = 0; r < Mc; r++) h->Pc[((size_t)k * Mc + r) * N + i] = P[k * Mc + r];
     for (int s = 0; s < nd; s++) {
       int64_t nb = face_nbr(m, i, s);
+      if (nb < 0) {
+        // a boundary face: no directional candidate there (its slot keeps the
+        // cell itself as members and zero rows, and is marked invalid)
+        h->dvalid[i] &= (uint8_t)~(1u << s);
+        for (int r = 0; r < Md; r++) h->sd[((size_t)s * Md + r) * N + i] = (int32_t)i;
+        continue;
+      }
       if (!bfs(m, nb, i, Kd == 3 ? 2 : 3, c)) { bad |= 1; break; }
       std::sort(c.begin() + 1, c.end(), [](const Cand& a, const Cand& b) {
         if (a.depth != b.depth) return a.depth < b.depth;

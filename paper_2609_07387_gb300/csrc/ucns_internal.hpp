@@ -17,6 +17,7 @@ struct HostArrays;
 constexpr int kMaxK = 34;   // non-constant modes of a quartic in 3-D (P4)
 constexpr int kMaxMc = 68;  // central stencil size 2K
 constexpr int kMaxDir = 6;  // directional stencils = faces of the element
+constexpr int kGateMeasures = 5;  // measures of the gate's plain-scheme check
 constexpr int kDtBlockCells = 256;  // cells per partial minimum of the time-step reduction
 
 void set_error(const std::string& msg);
@@ -52,7 +53,8 @@ struct DeviceMesh {
   int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)
   // faces
   int32_t* fo = nullptr;      // [F] owner
-  int32_t* fn = nullptr;      // [F] neighbour
+  int32_t* fn = nullptr;      // [F] neighbour; on a boundary face -1 - its boundary kind
+  uint8_t* dvalid = nullptr;  // [N] bit s: directional candidate s exists (meshes with boundary faces)
   double* fq = nullptr;       // [nq][10][F] x-x_L(3) x-x_R'(3) n(3) |dS|(1), physical offsets
   float* fqf = nullptr;       // FP32 copy, point-contiguous [F][nq][10]
   double* fpen = nullptr;     // [F] alpha / L_int
@@ -77,9 +79,13 @@ struct DeviceMesh {
 struct ucns_mesh {
   // ---- topology (host) ----
   int64_t N = 0, nn = 0;
-  int npc = 0, nfc = 0, nfn = 0;
+  int npc = 0, nfc = 0;  // nodes and faces per cell: 8/6 hexahedron, 6/5 prism, 5/5 pyramid, 4/4 tetrahedron
   double L[3] = {0, 0, 0};
-  int per[3] = {0, 0, 0};
+  int per[3] = {0, 0, 0};  // periodic axes (box length > 0)
+  int64_t n_boundary = 0;  // faces on non-periodic sides of the box
+  // boundary kind of each box side x-, x+, y-, y+, z-, z+ (UCNS_BC_*) and the inflow state
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double uinf[5] = {0, 0, 0, 0, 0};
   std::vector<double> X;        // [nn][3]
   std::vector<int64_t> C;       // [N][npc] (user order)
   std::vector<int64_t> canon;   // node -> canonical node
@@ -114,7 +120,7 @@ struct ucns_mesh {
   int64_t gate_checks = 0;             // plain-scheme checks run
   int64_t gate_off_step = -1;          // gated step at which a check switched the gate off
   double gate_ke_err = 0.0;            // running estimate of the KE history's relative error
-  double gate_last[4] = {-1.0, -1.0, -1.0, -1.0};  // the last check's four measures
+  double gate_last[5] = {-1.0, -1.0, -1.0, -1.0, -1.0};  // the last check's measures (kGateMeasures)
   // gate_R below: [2][5][N] residuals of the check, then 16 doubles of its sums
   double* gate_R = nullptr;            // [2][5][N] residuals of the check
   float* label_out = nullptr;          // set only inside ucns_gate_labels

@@ -35,7 +35,7 @@ ERRORS = {
 
 # every entry point declared in include/ucns.h
 EXPORTS = (
-    "ucns_mesh_create", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps", "ucns_rk_steps_host",
+    "ucns_mesh_create", "ucns_mesh_set_boundary", "ucns_precompute", "ucns_precompute_host", "ucns_stencil", "ucns_residual", "ucns_rk_step", "ucns_rk_steps", "ucns_rk_steps_host",
     "ucns_check_state", "ucns_probe_bounded_wait", "ucns_alu_peak", "ucns_diagnostics", "ucns_time_step", "ucns_time_step_static", "ucns_profile",
     "ucns_profile_read",
     "ucns_cell_order", "ucns_mesh_info",
@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
         for name in EXPORTS:
             getattr(lib, name)  # raises AttributeError if an export is missing
         lib.ucns_mesh_create.argtypes = [P, I64, P, I64, I32, P, C.POINTER(P)]
+        lib.ucns_mesh_set_boundary.argtypes = [P, P, P]
         lib.ucns_precompute.argtypes = [P, C.POINTER(_Params)]
         lib.ucns_precompute_host.argtypes = [P, C.POINTER(_Params)]
         lib.ucns_stencil.argtypes = [P, I64, I32, P, P]
@@ -206,10 +207,16 @@ class Params:
                        self.Mach, self.cfl, self.lam_central, self.eps, self.alpha)
 
 
-class Mesh:
-    """A periodic hex or tet mesh with its device-resident precompute."""
+BC_SLIP_WALL, BC_SYMMETRY, BC_SUPERSONIC_OUTFLOW, BC_SUPERSONIC_INFLOW = 0, 1, 2, 3
 
-    def __init__(self, nodes, cells, box, params: Params | None = None):
+
+class Mesh:
+    """A mesh of hexahedra, prisms, pyramids or tetrahedra in a box whose axes
+    are periodic (length > 0) or bounded (length 0: boundary faces of the
+    kinds `bc` gives for the sides x-, x+, y-, y+, z-, z+, with the state
+    `inflow` for supersonic inflow sides), with its device-resident precompute."""
+
+    def __init__(self, nodes, cells, box, params: Params | None = None, bc=None, inflow=None):
         lib = load()
         self._lib = lib
         nodes = np.ascontiguousarray(nodes, dtype=np.float64)
@@ -218,6 +225,13 @@ class Mesh:
         h = C.c_void_p()
         _check(lib, lib.ucns_mesh_create(nodes.ctypes.data, nodes.shape[0], cells.ctypes.data, cells.shape[0],
                                          cells.shape[1], box.ctypes.data, C.byref(h)))
+        if bc is not None:
+            kinds = np.ascontiguousarray(bc, dtype=np.int32)
+            inf = None if inflow is None else np.ascontiguousarray(inflow, dtype=np.float64)
+            rc = lib.ucns_mesh_set_boundary(h, kinds.ctypes.data, None if inf is None else inf.ctypes.data)
+            if rc != UCNS_OK:
+                lib.ucns_mesh_destroy(h)
+                _check(lib, rc)
         self._h = h
         self.n_cells = int(cells.shape[0])
         perm = np.zeros(self.n_cells, dtype=np.int64)
@@ -381,19 +395,19 @@ class Mesh:
 
     def gate_check(self, U, stream=None) -> tuple[list, bool]:
         """One plain-scheme check on U: ([total KE-rate difference, local
-        KE-rate difference, estimated KE history error, dissipation
-        difference], gate now off)."""
-        rel = np.zeros(4)
+        KE-rate difference, estimated KE history error, solenoidal and
+        dilatational dissipation differences], gate now off)."""
+        rel = np.zeros(5)
         dis = C.c_int32(0)
         _check(self._lib, self._lib.ucns_gate_check(self._h, _dev_ptr(U, self.n_cells), rel.ctypes.data,
                                                     C.byref(dis), _stream_ptr(stream)))
         return rel.tolist(), bool(dis.value)
 
     def gate_status(self) -> dict:
-        """{"enabled", "steps", "checks", "off_step" (-1: never), "last": the four measures}."""
+        """{"enabled", "steps", "checks", "off_step" (-1: never), "last": the five measures}."""
         en = C.c_int32(0)
         cnt = np.zeros(3, dtype=np.int64)
-        last = np.zeros(4)
+        last = np.zeros(5)
         _check(self._lib, self._lib.ucns_gate_status(self._h, C.byref(en), cnt.ctypes.data, last.ctypes.data))
         return {"enabled": bool(en.value), "steps": int(cnt[0]), "checks": int(cnt[1]), "off_step": int(cnt[2]),
                 "last": last.tolist()}

@@ -379,3 +379,63 @@ def test_bounded_wait_timeout_reaches_the_caller():
     z = net.forward(X)
     net.check()
     assert torch.isfinite(z).all()
+
+
+# ---- boundary faces and mixed elements (NEXT-3): prisms and pyramids in the
+# periodic box, slip walls on z = 0 and z = L, supersonic inflow at x = 0 with
+# outflow at x = L; inviscid wherever a boundary face exists
+UINF = (1.4, 2.8, 0.0, 0.0, 5.3)  # Mach 2 (rho 1.4, u 2, p 1)
+NEXT3 = [
+    # name, element, boundary, lattice n, order, scheme, Re
+    ("prism_p1", "prism", None, 7, 1, 0, 1600.0),
+    ("prism_p2_cwenoz", "prism", None, 7, 2, 1, 1600.0),
+    ("pyramid_p2_cwenoz", "pyramid", None, 5, 2, 1, 1600.0),
+    ("walls_p1", "hex", "walls", 9, 1, 0, 0.0),
+    ("walls_p2_cwenoz", "hex", "walls", 9, 2, 1, 0.0),
+    ("walls_tets_p2_cwenoz", "tet", "walls", 6, 2, 1, 0.0),
+    ("walls_prism_p2_cwenoz", "prism", "walls", 7, 2, 1, 0.0),
+    ("inflow_outflow_p2_cwenoz", "hex", "inflow", 9, 2, 1, 0.0),
+]
+
+
+def _next3_mesh(element, boundary, n):
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=13)
+    if element == "tet":
+        cells = I.split_tets(cells)
+    elif element == "prism":
+        cells = I.split_prisms(cells)
+    elif element == "pyramid":
+        nodes, cells = I.split_pyramids(nodes, cells)
+    if boundary == "walls":
+        return nodes, cells, np.array([box[0], box[1], 0.0]), None
+    if boundary == "inflow":
+        return nodes, cells, np.array([0.0, box[1], box[2]]), (3, 2, 0, 0, 0, 0)
+    return nodes, cells, box, None
+
+
+@pytest.mark.parametrize("case", NEXT3, ids=[c[0] for c in NEXT3])
+def test_boundaries_and_mixed_elements_parity(case):
+    """The residual (1e-12 of the summed-term scale) and one SSP-RK3 step with
+    the CFL time step (dt to 1e-14, the state to 1e-12 norm-wise) against the
+    oracle: prisms and pyramids (5 faces and 5 directional candidates, bilinear
+    quad and collapsed triangle faces in one mesh), boundary faces with the
+    ghost state of their side's kind, one-sided stencils and no directional
+    candidate across a boundary."""
+    name, element, boundary, n, order, scheme, Re = case
+    nodes, cells, box, bc = _next3_mesh(element, boundary, n)
+    m = ucns.Mesh(nodes, cells, box, bc=bc, inflow=UINF if bc else None)
+    m.precompute(ucns.Params(order=order, scheme=scheme, Re=Re, Mach=0.3))
+    oc = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=Re, Mach=0.3, inflow=UINF,
+                                            **({"bc": bc} if bc else {})))
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=3)
+    Rg = _gpu_residual(m, U)
+    Rc, S = oc.residual_terms(U)
+    err = _term_err(Rg, Rc, S)
+    print(name, "residual err/S", err)
+    assert np.all(err <= TOL_R), err
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    dtg = m.rk_step(Ug, return_dt=True)
+    Uc, dtc = oc.rk_step(U, 0.0)
+    assert abs(dtg - dtc) <= 1e-14 * dtc
+    e2 = _norm_err(m.to_user(Ug.cpu().numpy()), Uc)
+    assert np.all(e2 <= TOL_R), e2

@@ -35,7 +35,22 @@ def test_error_codes_without_gpu():
     lib = ucns.load()
     nodes, cells, box = I.hex_lattice(4)
     with pytest.raises(ucns.UcnsError) as e:
-        ucns.Mesh(nodes, cells[:, :5], box)
+        ucns.Mesh(nodes, cells[:, :3], box)  # no element has 3 nodes
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:
+        ucns.Mesh(nodes, cells, np.array([box[0], -1.0, box[2]]))
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:  # an unknown boundary kind
+        ucns.Mesh(nodes, cells, np.array([box[0], box[1], 0.0]), bc=[0, 0, 0, 0, 7, 0])
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:  # an inflow side without the inflow state
+        ucns.Mesh(nodes, cells, np.array([0.0, box[1], box[2]]), bc=[3, 2, 0, 0, 0, 0])
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:  # boundary faces need an inviscid flow
+        ucns.Mesh(nodes, cells, np.array([box[0], box[1], 0.0])).precompute_host(ucns.Params(order=1, scheme=0))
+    assert e.value.code == -1
+    with pytest.raises(ucns.UcnsError) as e:  # prisms are built in the FP64 form
+        ucns.Mesh(nodes, I.split_prisms(cells), box).precompute_host(ucns.Params(order=2, precision=1))
     assert e.value.code == -1
     bad = cells.copy()
     bad[3, 2] = nodes.shape[0] + 7
@@ -95,6 +110,57 @@ _ORC_BASIS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), 
               (3, 0, 0), (0, 3, 0), (0, 0, 3), (2, 1, 0), (2, 0, 1), (1, 2, 0), (0, 2, 1), (1, 0, 2), (0, 1, 2),
               (1, 1, 1), (4, 0, 0), (0, 4, 0), (0, 0, 4), (3, 1, 0), (3, 0, 1), (1, 3, 0), (0, 3, 1), (1, 0, 3),
               (0, 1, 3), (2, 2, 0), (2, 0, 2), (0, 2, 2), (2, 1, 1), (1, 2, 1), (1, 1, 2)]
+
+
+def _mesh_kind(kind, n, seed):
+    """(nodes, cells, box, oracle params extra, library boundary kinds) of a test mesh."""
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=seed)
+    if kind == "tet":
+        cells = I.split_tets(cells)
+    elif kind == "prism":
+        cells = I.split_prisms(cells)
+    elif kind == "pyramid":
+        nodes, cells = I.split_pyramids(nodes, cells)
+    if kind == "walls":  # z not periodic: slip walls on z = 0 and z = L
+        return nodes, cells, np.array([box[0], box[1], 0.0]), {}, None
+    if kind == "inflow":  # x not periodic: supersonic inflow at x = 0, outflow at x = L
+        return nodes, cells, np.array([0.0, box[1], box[2]]), {"bc": (3, 2, 0, 0, 0, 0)}, [3, 2, 0, 0, 0, 0]
+    return nodes, cells, box, {}, None
+
+
+@pytest.mark.parametrize("kind,order,scheme", [("prism", 1, 0), ("prism", 2, 1), ("pyramid", 2, 1), ("walls", 2, 1),
+                                               ("walls", 1, 0), ("inflow", 2, 1)])
+def test_host_precompute_matches_oracle_mixed_elements_and_boundaries(kind, order, scheme):
+    """Prisms, pyramids (5 faces, 5 directional candidates) and boxes with
+    boundary faces: the library's stencils and pseudo-inverses equal the
+    oracle's; a cell on a boundary has one-sided stencils and no directional
+    candidate across the boundary."""
+    nodes, cells, box, extra, bc = _mesh_kind(kind, 6 if kind != "pyramid" else 5, 12)
+    re = 0.0 if kind in ("walls", "inflow") else 1600.0
+    params = ucns.Params(order=order, scheme=scheme, Re=re)
+    m = ucns.Mesh(nodes, cells, box, bc=bc, inflow=(1.4, 2.8, 0.0, 0.0, 5.3) if bc else None).precompute_host(params)
+    oc = O.Case(nodes, cells, box, O.Params(order=order, scheme=scheme, Re=re,
+                                            inflow=(1.4, 2.8, 0.0, 0.0, 5.3), **extra))
+    assert (m.n_faces, m.K, m.Mc, m.nd, m.Md, m.nq, m.nfc) == (oc.n_faces, oc.K, oc.Mc, oc.nd, oc.Md, oc.nq, oc.nfc)
+    rng = np.random.default_rng(1)
+    fo, fn, _ = oc.faces()
+    bcells = set(fo[fn < 0].tolist())
+    sample = list(rng.choice(len(cells), size=10, replace=False)) + sorted(bcells)[:6]
+    invalid = 0
+    for i in sample:
+        for which in [-1] + list(range(m.nd)):
+            mem, P = m.stencil(int(i), which)
+            try:
+                omem, _, _, oP = oc.stencil(int(i), which)
+            except O.OracleError:  # no candidate across a boundary face
+                invalid += 1
+                assert np.all(mem == i) and np.all(P == 0.0), (i, which)
+                continue
+            assert sorted(mem) == sorted(omem), (i, which)
+            pos = {c: k for k, c in enumerate(omem)}
+            oPm = oP[:, [pos[c] for c in mem]]
+            assert np.abs(P - oPm).max() <= 1e-12 * np.abs(oPm).max(), (i, which)
+    assert (invalid > 0) == (kind in ("walls", "inflow") and m.nd > 0)
 
 
 @pytest.mark.parametrize("kind,order,scheme", [("hex", 1, 0), ("hex", 2, 1), ("tet", 2, 1), ("hex", 3, 1),

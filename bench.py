@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--check-bound", type=float, default=1e-4,
                     help="plain-scheme check: largest relative difference of the gated and full KE rates")
     ap.add_argument("--forms", default="", help="comma list of forms to time (default: the configuration's)")
+    ap.add_argument("--order", type=int, default=2, choices=[2, 3, 4],
+                    help="reconstruction degree (3, 4: CWENOZ on the hexahedral configurations, FP64 form only)")
     return ap.parse_args()
 
 
@@ -132,9 +134,12 @@ def rk_name() -> str:
     return "SSP(5,4)" if STAGES == 5 else "SSP-RK3"
 
 
-def config_json(cfg: Config, n: int, N: int, world: int) -> dict:
+def config_json(cfg: Config, n: int, N: int, world: int, order: int = 2) -> dict:
+    wl = f"{cfg.key.upper()}: " + cfg.describe(n, N)
+    if order != 2:
+        wl = wl.replace("P2 CWENOZ", f"P{order} CWENOZ")
     return {
-        "workload": f"{cfg.key.upper()}: " + cfg.describe(n, N),
+        "workload": wl,
         "cells": N,
         "stages_per_step": STAGES,
         "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
@@ -224,13 +229,13 @@ def measured_traffic(kernel: str, workload: str):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_sample(nodes, cells, box, U, cfg: Config, n: int, n_cells: int):
+def oracle_sample(nodes, cells, box, U, cfg: Config, n: int, n_cells: int, order: int = 2):
     """Build the oracle on the workload and pick a sample of about n_cells
     cells: whole z-layers of the lattice (for tetrahedra, 6 per hexahedron,
     consecutive in the split's numbering)."""
     import oracle as O
 
-    oc = O.Case(nodes, cells, box, O.Params(order=2, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5,
+    oc = O.Case(nodes, cells, box, O.Params(order=order, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5,
                                             integrator=1 if STAGES == 5 else 0))
     per_layer = n * n * (6 if cfg.tets else 1)
     layers = max(1, n_cells // per_layer)
@@ -278,8 +283,8 @@ def sample_text(cfg: Config, sel, N: int, layers: int, n: int) -> str:
             f"({what}), precompute excluded")
 
 
-def cpu_baseline(nodes, cells, box, U, cfg: Config, n: int) -> dict:
-    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 65536)
+def cpu_baseline(nodes, cells, box, U, cfg: Config, n: int, order: int = 2) -> dict:
+    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 65536 if order == 2 else 4096, order)
     dt = 1e-4
     t0 = time.perf_counter()
     oracle_rk_step_on_sample(oc, U, sel, dt)
@@ -292,7 +297,7 @@ def run_reference(args, cfg: Config, n: int, rank: int, world: int):
     if rank != 0:
         return
     nodes, cells, box, U = workload(cfg, n)
-    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 32768)
+    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 32768 if args.order == 2 else 2048, args.order)
     dt = 1e-4
     for _ in range(args.warmup):
         oracle_rk_step_on_sample(oc, U, sel, dt)
@@ -306,7 +311,7 @@ def run_reference(args, cfg: Config, n: int, rank: int, world: int):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": config_json(cfg, n, len(cells), 1),
+        "config": config_json(cfg, n, len(cells), 1, args.order),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": omp_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -330,6 +335,8 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> dict:
     w = 4 if mixed else 8
     N, F, nq = m.n_cells, m.n_faces, m.nq
     coef = (m.K + 1) * 5 * w
+    if m.K > 9:
+        return algorithmic_ho(m, kind)
     if kind == "face":
         flops = FLOPS_FACE_P2_VISC_PER_QP * nq * F
         face_common = 4 + 2 * 4 + 5 * w            # penalty (FP32 in both forms' count), ids, totals
@@ -350,6 +357,39 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> dict:
     return {"flops": flops, "alg": alg, "layout": layout}
 
 
+# exponents of the basis monomials beyond P2 (the kernels' order), for the P3/P4 flop counts
+_BASIS_HO = [(3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2),
+             (0, 0, 3), (4, 0, 0), (3, 1, 0), (3, 0, 1), (2, 2, 0), (2, 1, 1), (2, 0, 2), (1, 3, 0), (1, 2, 1),
+             (1, 1, 2), (1, 0, 3), (0, 4, 0), (0, 3, 1), (0, 2, 2), (0, 1, 3), (0, 0, 4)]
+_BASIS_P2 = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+
+
+def algorithmic_ho(m, kind: str) -> dict:
+    """Flops and bytes of one launch of the P3/P4 (FP64) kernels, counted
+    from their source: face, per Gauss point, 2 sides x 5 variables x 2 flops
+    x (K value terms + one gradient term per nonzero exponent), the
+    monomials' products (4 per mode and side), HLLC 138, viscous 120,
+    penalty/averages 80, scaling and sum 20; reconstruction, per cell, the
+    central contraction and differences, the directional contractions twice,
+    the smoothness forms (K^2 central, Kd^2 per candidate) and the weights."""
+    basis = (_BASIS_P2 + _BASIS_HO)[:m.K]
+    N, F, nq, K = m.n_cells, m.n_faces, m.nq, m.K
+    kd = m.Md // 2
+    if kind == "face":
+        g = sum(sum(1 for e in b if e) for b in basis)
+        flops = F * nq * (2 * 5 * 2 * (K + g) + 2 * 4 * K + 358)
+        alg = F * (nq * 6 * 8 + 3 * 8 + 4 + 2 * 4 + 5 * 8) + N * (K + 1) * 5 * 8
+        layout = F * (nq * 10 * 8 + 8 + 2 * 4 + 5 * 8) + N * (K + 1) * 5 * 8
+    else:
+        cen = 5 * (2 * K * m.Mc + m.Mc)
+        dirf = 5 * 2 * (2 * m.nd * kd * m.Md + m.nd * m.Md) + 5 * 2 * (K * K + m.nd * kd * kd) + 5 * 60
+        flops = N * (cen + (dirf if m.nd else 0) + 5 * 2 * K)
+        alg = N * (K * m.Mc * 8 + m.Mc * 4 + m.nd * (kd * m.Md * 8 + m.Md * 4) + (K * (K + 1) // 2) * 8 * (m.nd > 0)
+                   + (K - 3) * 8 + 8 + 5 * 8 + (K + 1) * 5 * 8)
+        layout = alg
+    return {"flops": flops, "alg": alg, "layout": layout}
+
+
 def roofline(m, prof: dict, form: str, peaks: dict, workload_key: str, frac_dir: float = 1.0) -> dict:
     mixed = form != "fp64"
     kinds = {k: v for k, v in prof.items() if v[1] > 0 and k in ("recon", "face")}
@@ -360,6 +400,8 @@ def roofline(m, prof: dict, form: str, peaks: dict, workload_key: str, frac_dir:
     names = {("face", False): "k_face<2,true>", ("recon", False): "k_recon<2,true,nd>",
              ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,nd>"}
     name = names[(dom, mixed)]
+    if m.K > 9:
+        name = {"face": "k_face_ho<%d,true>", "recon": "k_recon_ho<%d,true>"}[dom] % (3 if m.K == 19 else 4)
     if dom == "recon" and mixed and frac_dir < 1.0:
         name = "k_recon_mx<2,false,nd,gated>"
     alu_peak = peaks["fp32"] if mixed else peaks["fp64"]
@@ -420,8 +462,10 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
     nodes, cells, box, U_user = workload(cfg, n)
     N = len(cells)
     stream = torch.cuda.current_stream()
-    base = dict(order=2, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5, integrator=args.integrator)
+    base = dict(order=args.order, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5, integrator=args.integrator)
     forms = [f for f in (args.forms.split(",") if args.forms else cfg.forms) if f]
+    if args.order > 2:
+        forms = ["fp64"]  # the mixed form and the gate are built for P1 and P2
     # one FP64 mesh and one mixed mesh: the learned form is the mixed mesh with the gate attached
     m64 = ucns.Mesh(nodes, cells, box, ucns.Params(precision=0, **base))
     mx = ucns.Mesh(nodes, cells, box, ucns.Params(precision=1, **base)) if set(forms) - {"fp64"} else None
@@ -483,9 +527,11 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(bus) as clk:
+            torch.cuda.nvtx.range_push(f"timed {form}")  # lets a profiler select the timed kernels
             e0.record(stream)
             m.rk_steps(U, args.steps)  # the library's multi-step call: K steps, dt on the device
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
         barrier()
         ms = e0.elapsed_time(e1)
@@ -572,7 +618,7 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
     frac_dir = r["flagged"] if (chosen == "learned" and r["flagged"] is not None) else 1.0
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(nodes, cells, box, U_user, cfg, n)
+        cpu = cpu_baseline(nodes, cells, box, U_user, cfg, n, args.order)
     dtype = {"fp64": "f64", "mixed": "f32+f64", "learned": "f32+f64+bf16"}[chosen]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "form": chosen,
@@ -584,7 +630,7 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic (seeded mesh jitter and initial state; no dataset)",
         "impl": "ucns",
-        "config": config_json(cfg, n, N, world),
+        "config": config_json(cfg, n, N, world, args.order),
         "clocks": r["clocks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 5 * N * 8, "d2h_bytes_per_step": 5 * N * 8 + 16,
                 "steps": args.e2e_steps, "via": "ucns_rk_steps_host, pinned host buffer"},

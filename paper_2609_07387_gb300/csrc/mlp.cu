@@ -509,18 +509,26 @@ __global__ void k_mlp_reduce(const float* __restrict__ partial, int nctas, float
   grad[p] = s;
 }
 
-// Adam on the FP32 master weights, then the BF16 / rounded copies
-__global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
-                           const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1,
-                           float c2) {
+// One training step after the per-CTA partial gradients: per parameter, the
+// gradient summed over the CTAs in order (as k_mlp_reduce), the Adam update
+// (beta 0.9 / 0.999, bias corrections c1, c2) and the rounded copies (as
+// k_mlp_cast), in one launch
+__global__ void k_mlp_step(const float* __restrict__ partial, int nctas, float* __restrict__ theta,
+                           float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float eps,
+                           float c1, float c2, bf16* __restrict__ W, float* __restrict__ w3r) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= kParams) return;
-  const float gp = g[p];
+  float gp = 0.f;
+  for (int c = 0; c < nctas; c++) gp += partial[(size_t)c * kParams + p];
   const float mp = b1 * m[p] + (1.f - b1) * gp;
   const float vp = b2 * v[p] + (1.f - b2) * gp * gp;
   m[p] = mp;
   v[p] = vp;
-  theta[p] -= lr * (mp / c1) / (sqrtf(vp / c2) + eps);
+  const float th = theta[p] - lr * (mp / c1) / (sqrtf(vp / c2) + eps);
+  theta[p] = th;
+  if (p >= kOffW1 && p < kOffW1 + 2048) W[p - kOffW1] = __float2bfloat16_rn(th);
+  if (p >= kOffW2 && p < kOffW2 + 4096) W[2048 + (p - kOffW2)] = __float2bfloat16_rn(th);
+  if (p >= kOffW3 && p < kOffW3 + 64) w3r[p - kOffW3] = bf16r(th);
 }
 
 __global__ void k_mlp_cast(const float* __restrict__ theta, bf16* __restrict__ W, float* __restrict__ w3r) {
@@ -585,8 +593,9 @@ int cast(ucns_mlp* m, cudaStream_t s) {
   return UCNS_OK;
 }
 
-int grad_into(ucns_mlp* m, const bf16* X, const float* y, int64_t n, float w_pos, float w_neg, float* grad,
-              cudaStream_t s) {
+// the per-CTA partial gradients of n rows into m->partial; returns the CTA count in *nctas
+int grad_partials(ucns_mlp* m, const bf16* X, const float* y, int64_t n, float w_pos, float w_neg, int* nctas,
+                  cudaStream_t s) {
   GradArgs a;
   a.X = X;
   a.y = y;
@@ -602,7 +611,17 @@ int grad_into(ucns_mlp* m, const bf16* X, const float* y, int64_t n, float w_pos
   const int64_t ntiles = (n + 127) / 128;
   const int grid = (int)std::min<int64_t>(ntiles, m->nsm);
   k_mlp_grad<<<grid, kThreads, kTrainSmem, s>>>(a);
-  k_mlp_reduce<<<(kParams + 255) / 256, 256, 0, s>>>(m->partial, grid, grad);
+  MLP_CUDA(cudaGetLastError());
+  *nctas = grid;
+  return UCNS_OK;
+}
+
+int grad_into(ucns_mlp* m, const bf16* X, const float* y, int64_t n, float w_pos, float w_neg, float* grad,
+              cudaStream_t s) {
+  int nctas = 0;
+  int rc = grad_partials(m, X, y, n, w_pos, w_neg, &nctas, s);
+  if (rc) return rc;
+  k_mlp_reduce<<<(kParams + 255) / 256, 256, 0, s>>>(m->partial, nctas, grad);
   MLP_CUDA(cudaGetLastError());
   return UCNS_OK;
 }
@@ -727,14 +746,15 @@ int ucns_mlp_train(ucns_mlp* m, const void* X, const float* y, int64_t n, int64_
   const bf16* Xb = reinterpret_cast<const bf16*>(X);
   for (int64_t b0 = 0; b0 < n; b0 += batch) {
     const int64_t nb = std::min(batch, n - b0);
-    int rc = grad_into(m, Xb + b0 * 32, y + b0, nb, w_pos, w_neg, m->grad, s);
+    int nctas = 0;
+    int rc = grad_partials(m, Xb + b0 * 32, y + b0, nb, w_pos, w_neg, &nctas, s);
     if (rc) return rc;
     m->t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = (float)(1.0 - std::pow(0.9, (double)m->t)), c2 = (float)(1.0 - std::pow(0.999, (double)m->t));
-    k_mlp_adam<<<(kParams + 255) / 256, 256, 0, s>>>(m->theta, m->m, m->v, m->grad, lr, b1, b2, 1e-8f, c1, c2);
-    rc = cast(m, s);
-    if (rc) return rc;
+    // the summed gradient, Adam and the BF16 copies in one launch
+    k_mlp_step<<<(kParams + 255) / 256, 256, 0, s>>>(m->partial, nctas, m->theta, m->m, m->v, lr, b1, b2, 1e-8f,
+                                                      c1, c2, m->W, m->w3r);
   }
   MLP_CUDA(cudaGetLastError());
   return UCNS_OK;

@@ -113,7 +113,7 @@ def parse():
                     help="plain-scheme check: largest relative difference of the gated and full KE rates")
     ap.add_argument("--forms", default="", help="comma list of forms to time (default: the configuration's)")
     ap.add_argument("--order", type=int, default=2, choices=[2, 3, 4],
-                    help="reconstruction degree (3, 4: CWENOZ on the hexahedral configurations, FP64 form only)")
+                    help="reconstruction degree (3, 4: CWENOZ on the hexahedral configurations; FP64 and mixed forms)")
     return ap.parse_args()
 
 
@@ -238,8 +238,8 @@ def oracle_sample(nodes, cells, box, U, cfg: Config, n: int, n_cells: int, order
     oc = O.Case(nodes, cells, box, O.Params(order=order, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5,
                                             integrator=1 if STAGES == 5 else 0))
     per_layer = n * n * (6 if cfg.tets else 1)
-    layers = max(1, n_cells // per_layer)
-    sel = np.arange(min(layers * per_layer, len(cells)), dtype=np.int64)
+    layers = n_cells / per_layer if n_cells < per_layer else n_cells // per_layer
+    sel = np.arange(min(int(layers * per_layer), len(cells)), dtype=np.int64)
     oc.residual_subset(U, sel)  # untimed: the lazy precompute of the sample's stencils
     return oc, sel, layers
 
@@ -277,14 +277,16 @@ def omp_threads() -> int:
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
-def sample_text(cfg: Config, sel, N: int, layers: int, n: int) -> str:
-    what = f"{layers} z-layers of the {n}^3 lattice" + (", 6 tetrahedra per hexahedron" if cfg.tets else "")
+def sample_text(cfg: Config, sel, N: int, layers, n: int) -> str:
+    what = (f"{layers:g} z-layers of the {n}^3 lattice" if layers >= 1 else
+            f"the first {sel.size} cells of one z-layer of the {n}^3 lattice") + \
+        (", 6 tetrahedra per hexahedron" if cfg.tets else "")
     return (f"one {rk_name()} step ({STAGES} residual evaluations + updates) of {sel.size} of the {N} cells "
             f"({what}), precompute excluded")
 
 
 def cpu_baseline(nodes, cells, box, U, cfg: Config, n: int, order: int = 2) -> dict:
-    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 65536 if order == 2 else 4096, order)
+    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 65536 if order == 2 else 2048, order)
     dt = 1e-4
     t0 = time.perf_counter()
     oracle_rk_step_on_sample(oc, U, sel, dt)
@@ -297,7 +299,7 @@ def run_reference(args, cfg: Config, n: int, rank: int, world: int):
     if rank != 0:
         return
     nodes, cells, box, U = workload(cfg, n)
-    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 32768 if args.order == 2 else 2048, args.order)
+    oc, sel, layers = oracle_sample(nodes, cells, box, U, cfg, n, 32768 if args.order == 2 else 1024, args.order)
     dt = 1e-4
     for _ in range(args.warmup):
         oracle_rk_step_on_sample(oc, U, sel, dt)
@@ -336,7 +338,7 @@ def algorithmic(m, kind: str, mixed: bool, frac_dir: float = 1.0) -> dict:
     N, F, nq = m.n_cells, m.n_faces, m.nq
     coef = (m.K + 1) * 5 * w
     if m.K > 9:
-        return algorithmic_ho(m, kind)
+        return algorithmic_ho(m, kind, w)
     if kind == "face":
         flops = FLOPS_FACE_P2_VISC_PER_QP * nq * F
         face_common = 4 + 2 * 4 + 5 * w            # penalty (FP32 in both forms' count), ids, totals
@@ -364,8 +366,9 @@ _BASIS_HO = [(3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (
 _BASIS_P2 = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
 
 
-def algorithmic_ho(m, kind: str) -> dict:
-    """Flops and bytes of one launch of the P3/P4 (FP64) kernels, counted
+def algorithmic_ho(m, kind: str, w: int = 8) -> dict:
+    """Flops and bytes of one launch of the P3/P4 kernels (w: bytes per word,
+    8 in the FP64 form, 4 in the mixed one; ids 4, the state 8), counted
     from their source: face, per Gauss point, 2 sides x 5 variables x 2 flops
     x (K value terms + one gradient term per nonzero exponent), the
     monomials' products (4 per mode and side), HLLC 138, viscous 120,
@@ -378,14 +381,14 @@ def algorithmic_ho(m, kind: str) -> dict:
     if kind == "face":
         g = sum(sum(1 for e in b if e) for b in basis)
         flops = F * nq * (2 * 5 * 2 * (K + g) + 2 * 4 * K + 358)
-        alg = F * (nq * 6 * 8 + 3 * 8 + 4 + 2 * 4 + 5 * 8) + N * (K + 1) * 5 * 8
-        layout = F * (nq * 10 * 8 + 8 + 2 * 4 + 5 * 8) + N * (K + 1) * 5 * 8
+        alg = F * (nq * 6 * w + 3 * w + 4 + 2 * 4 + 5 * w) + N * (K + 1) * 5 * w
+        layout = F * (nq * 10 * w + w + 2 * 4 + 5 * w) + N * (K + 1) * 5 * w
     else:
         cen = 5 * (2 * K * m.Mc + m.Mc)
         dirf = 5 * 2 * (2 * m.nd * kd * m.Md + m.nd * m.Md) + 5 * 2 * (K * K + m.nd * kd * kd) + 5 * 60
         flops = N * (cen + (dirf if m.nd else 0) + 5 * 2 * K)
-        alg = N * (K * m.Mc * 8 + m.Mc * 4 + m.nd * (kd * m.Md * 8 + m.Md * 4) + (K * (K + 1) // 2) * 8 * (m.nd > 0)
-                   + (K - 3) * 8 + 8 + 5 * 8 + (K + 1) * 5 * 8)
+        alg = N * (K * m.Mc * w + m.Mc * 4 + m.nd * (kd * m.Md * w + m.Md * 4) + (K * (K + 1) // 2) * w * (m.nd > 0)
+                   + (K - 3) * w + w + 5 * 8 + (K + 1) * 5 * w)
         layout = alg
     return {"flops": flops, "alg": alg, "layout": layout}
 
@@ -401,7 +404,8 @@ def roofline(m, prof: dict, form: str, peaks: dict, workload_key: str, frac_dir:
              ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,nd>"}
     name = names[(dom, mixed)]
     if m.K > 9:
-        name = {"face": "k_face_ho<%d,true>", "recon": "k_recon_ho<%d,true>"}[dom] % (3 if m.K == 19 else 4)
+        name = {"face": "k_face_ho%s<%d,true>", "recon": "k_recon_ho%s<%d,true>"}[dom] % (
+            "_mx" if mixed else "", 3 if m.K == 19 else 4)
     if dom == "recon" and mixed and frac_dir < 1.0:
         name = "k_recon_mx<2,false,nd,gated>"
     alu_peak = peaks["fp32"] if mixed else peaks["fp64"]
@@ -465,7 +469,7 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
     base = dict(order=args.order, scheme=1, Re=1600.0, Mach=cfg.mach, cfl=0.5, integrator=args.integrator)
     forms = [f for f in (args.forms.split(",") if args.forms else cfg.forms) if f]
     if args.order > 2:
-        forms = ["fp64"]  # the mixed form and the gate are built for P1 and P2
+        forms = [f for f in forms if f != "learned"]  # the gate is built for P2
     # one FP64 mesh and one mixed mesh: the learned form is the mixed mesh with the gate attached
     m64 = ucns.Mesh(nodes, cells, box, ucns.Params(precision=0, **base))
     mx = ucns.Mesh(nodes, cells, box, ucns.Params(precision=1, **base)) if set(forms) - {"fp64"} else None

@@ -161,7 +161,67 @@ int launch_recon_tiles(const ReconArgsMx& a, cudaStream_t s) {
   return UCNS_OK;
 }
 
+// P3 / P4, mixed form
+int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
+  ReconArgsHOMx a;
+  a.Uhl = m->d.Uhl;
+  a.sc = m->d.sc;
+  a.Pc = m->d.Pcf;
+  a.sd = m->d.sd;
+  a.Pd = m->d.Pdf;
+  a.Msi = m->d.Msif;
+  a.psib = m->d.psibf;
+  a.inv_h = m->d.inv_hf;
+  a.coef = m->d.coeff;
+  a.N = (int)m->N;
+  const double lsum = m->P.lambda_central + m->nd;
+  a.lam0 = (float)(m->P.lambda_central / lsum);
+  a.lams = (float)(1.0 / lsum);
+  a.eps = (float)m->P.epsilon;
+  const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
+  a.eref_hi = (float)eref;
+  a.eref_lo = (float)(eref - (double)a.eref_hi);
+  const unsigned g = nblocks((size_t)m->N * 5, 128);
+  const bool weno = m->nd > 0;
+  if (m->K == 19) {
+    if (weno) k_recon_ho_mx<3, true><<<g, 128, 0, s>>>(a);
+    else k_recon_ho_mx<3, false><<<g, 128, 0, s>>>(a);
+  } else {
+    if (weno) k_recon_ho_mx<4, true><<<g, 128, 0, s>>>(a);
+    else k_recon_ho_mx<4, false><<<g, 128, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
+int launch_face_ho_mx(ucns_mesh* m, cudaStream_t s) {
+  FaceArgsHOMx a;
+  a.coef = m->d.coeff;
+  a.fq = m->d.fqf;
+  a.fpen = m->d.fpenf;
+  a.fo = m->d.fo;
+  a.fn = m->d.fn;
+  a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
+  a.N = (int)m->N;
+  a.F = (int)m->F;
+  a.c = flux_const_f(m->P);
+  const bool visc = m->P.reynolds > 0.0;
+  const int fpw = 32 / m->nq;
+  const size_t threads = (size_t)((m->F + fpw - 1) / fpw) * 32;
+  const unsigned g = nblocks(threads, 128);
+  if (m->K == 19) {
+    if (visc) k_face_ho_mx<3, true><<<g, 128, 0, s>>>(a);
+    else k_face_ho_mx<3, false><<<g, 128, 0, s>>>(a);
+  } else {
+    if (visc) k_face_ho_mx<4, true><<<g, 128, 0, s>>>(a);
+    else k_face_ho_mx<4, false><<<g, 128, 0, s>>>(a);
+  }
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
+  if (m->K > 9) return launch_recon_ho_mx(m, s);
   ReconArgsMx a;
   (void)U;  // read through its float pair m->d.Uhl, written by k_split or the RK stage
   a.Uhl = m->d.Uhl;
@@ -192,6 +252,7 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
 }
 
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
+  if (m->K > 9) return launch_face_ho_mx(m, s);
   FaceArgsMx a;
   a.coef = m->d.coeff;
   a.fq = m->d.fqf;
@@ -589,11 +650,13 @@ int residual_into(ucns_mesh* m, const double* U, double* R, cudaStream_t s) {
 // Diagnostic sums [V KE, V |curl u|^2, V (div u)^2, V] of the coefficients
 // the last reconstruction left, into out[0..3] (device)
 int diag_sums_into(ucns_mesh* m, const double* U, double* out, cudaStream_t s) {
-  if (mixed(m))
+  if (mixed(m) && m->K > 9)
+    k_diag_partial<float><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, (int)m->N, m->d.red);
+  else if (mixed(m))
     k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC, m->d.vol,
                                                              (int)m->N, m->d.red);
   else
-    k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h, (int)m->N, m->d.red);
+    k_diag_partial<double><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, (int)m->N, m->d.red);
   k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, out);
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;
@@ -755,7 +818,7 @@ void device_free(ucns_mesh* m) {
   m->gate_eval_active = false;
   m->gate_fixed = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
+  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcf, d.Pdf, d.Msif, d.psibf, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.dvalid, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
@@ -837,8 +900,6 @@ static int check_params(const ucns_mesh* m, const ucns_params* p) {
     return fail(UCNS_ERR_INVALID_ARG, "CWENOZ needs order 2 or more");
   if (p->precision != UCNS_PREC_FP64 && p->precision != UCNS_PREC_MIXED)
     return fail(UCNS_ERR_INVALID_ARG, "unknown precision mode");
-  if (p->precision == UCNS_PREC_MIXED && p->order > 2)
-    return fail(UCNS_ERR_INVALID_ARG, "the mixed form is built for orders 1 and 2");
   if (p->order > 2 && m->npc != 8) return fail(UCNS_ERR_INVALID_ARG, "orders 3 and 4 are built for hexahedra only");
   if (m->n_boundary > 0 && p->reynolds > 0.0)
     return fail(UCNS_ERR_INVALID_ARG, "boundary faces are built for inviscid flows (Re <= 0) only");
@@ -917,7 +978,15 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     device_free(m);
     return rc;
   }
-  if (p->precision == UCNS_PREC_MIXED) {
+  if (p->precision == UCNS_PREC_MIXED && m->K > 9) {
+    if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) || (rc = upload_f32(&d.Msif, h.Msi)) ||
+        (rc = upload_f32(&d.psibf, h.psib)) || (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
+        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
+        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
+      device_free(m);
+      return rc;
+    }
+  } else if (p->precision == UCNS_PREC_MIXED) {
     const int rc_rows = m->K * m->Mc, rd_rows = m->nd * 3 * m->Md;
     std::vector<double> cellrows((size_t)kCellRows * m->N);
     std::copy(h.mom.begin(), h.mom.begin() + (size_t)6 * m->N, cellrows.begin());
@@ -1114,12 +1183,13 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   m->gate_eval_active = false;  // diagnostics always use the full scheme
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
-    if (mixed(m))
+    if (mixed(m) && m->K > 9)
+      k_diag_partial<float><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, (int)m->N, m->d.red);
+    else if (mixed(m))
       k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC,
                                                                  m->d.vol, (int)m->N, m->d.red);
     else
-      k_diag_partial<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, m->d.inv_h,
-                                                              (int)m->N, m->d.red);
+      k_diag_partial<double><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coef, m->d.vol, (int)m->N, m->d.red);
     // the final sums land in the first 4 doubles of G (free between residuals)
     k_diag_final<<<1, 32, 0, s>>>(m->d.red, m->d.red_blocks, m->d.G);
     UCNS_CUDA(cudaGetLastError());

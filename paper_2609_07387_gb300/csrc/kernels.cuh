@@ -832,10 +832,11 @@ __global__ void __launch_bounds__(kRedThreads) k_dt_fused(DtArgs a) {
   }
 }
 
-// per-block sums [V KE, V |curl u|^2, V (div u)^2, V] in a fixed tree order
+// per-block sums [V KE, V |curl u|^2, V (div u)^2, V] in a fixed tree order, from
+// coefficients [K+1][N][5] (T = double: the FP64 form; float: the mixed form at P3/P4)
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-    k_diag_partial(const double* __restrict__ U, const double* __restrict__ coef,
-                   const double* __restrict__ vol, const double* __restrict__ inv_h, int N,
+    k_diag_partial(const double* __restrict__ U, const T* __restrict__ coef, const double* __restrict__ vol, int N,
                    double* __restrict__ part) {
   __shared__ double sm[4][kRedThreads];
   double acc[4] = {0, 0, 0, 0};
@@ -847,7 +848,7 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
     for (int v = 0; v < 4; v++)
 #pragma unroll
-      for (int j = 0; j < 3; j++) g[v][j] = coef[(j + 1) * st + (size_t)i * 5 + v];
+      for (int j = 0; j < 3; j++) g[v][j] = (double)coef[(j + 1) * st + (size_t)i * 5 + v];
     double gu[3][3];
 #pragma unroll
     for (int q = 0; q < 3; q++)

@@ -14,10 +14,12 @@
 //               the monomial-form polynomials, HLLC, penalised viscous flux
 //               (Eq. 7), and the face total summed by the group's first lane
 //               over its lanes in point order (deterministic).
+//   k_recon_ho_mx / k_face_ho_mx  the same in the mixed form.
 #pragma once
 
 #include "basis.hpp"
 #include "kernels.cuh"
+#include "kernels_mixed.cuh"
 
 namespace ucns {
 
@@ -250,6 +252,253 @@ __global__ void __launch_bounds__(128) k_face_ho(FaceArgs a) {
   // part in the shuffles; lanes outside a group read group 0 and store nothing)
   const int base = (in_group ? grp : 0) * NQ;
   double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int t = 0; t < NQ; t++)
+#pragma unroll
+    for (int v = 0; v < 5; v++) tot[v] += __shfl_sync(0xffffffffu, flux[v], base + t);
+  if (live && q == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = tot[v];
+  }
+}
+
+
+
+// ------------------------------------------------------- mixed P3 / P4
+// The mixed form at P3 / P4 (the arithmetic split of the mixed form at P2):
+// stencil differences from the float pairs of the FP64 state, FP32
+// pseudo-inverses, contractions, smoothness forms and weights; the constant
+// term written relative to the reference state U_ref; coefficients FP32
+// [K+1][N][5]; FP32 HLLC and viscous flux on reference-relative states, FP32
+// face totals (k_rk<s, nfc, float> sums them as float pairs into FP64).
+struct ReconArgsHOMx {
+  const float* __restrict__ Uhl;    // [N][5][2] float pairs (hi, lo) of the state
+  const int32_t* __restrict__ sc;   // [MC][N]
+  const float* __restrict__ Pc;     // [K][MC][N]
+  const int32_t* __restrict__ sd;   // [6][MD][N]
+  const float* __restrict__ Pd;     // [6][KD][MD][N]
+  const float* __restrict__ Msi;    // [K(K+1)/2][N]
+  const float* __restrict__ psib;   // [K-3][N]
+  const float* __restrict__ inv_h;  // [N]
+  float* __restrict__ coef;         // [K+1][N][5]: entry 0 relative to U_ref, then physical-unit coefficients
+  int N;
+  float lam0, lams, eps;
+  float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair
+};
+
+template <int K, int KK>
+__device__ __forceinline__ float si_form_f(const float* __restrict__ M, size_t N, int i, const float (&a)[KK]) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < KK; k++) {
+    float t = 0.f;
+#pragma unroll
+    for (int l = k + 1; l < KK; l++) t = fmaf(__ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]), a[l], t);
+    const float mkk = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2) * N + i]);
+    s = fmaf(a[k], fmaf(2.f, t, mkk * a[k]), s);
+  }
+  return s;
+}
+
+// U_j - U_i of variable v from the float pairs (the leading parts subtract exactly)
+__device__ __forceinline__ float pair_diff_ho(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
+  const float2 p = __ldg(reinterpret_cast<const float2*>(hl + (size_t)j * 10 + 2 * v));
+  return (p.x - hi_i) + (p.y - lo_i);
+}
+
+template <int ORDER>
+__device__ __forceinline__ void dir_coeffs_mx(const ReconArgsHOMx& a, int v, float hi_i, float lo_i, int i, int s,
+                                              float (&b)[HO<ORDER>::KD]) {
+  using H = HO<ORDER>;
+  const size_t N = a.N;
+#pragma unroll
+  for (int k = 0; k < H::KD; k++) b[k] = 0.f;
+#pragma unroll 2
+  for (int r = 0; r < H::MD; r++) {
+    const int j = __ldg(&a.sd[((size_t)s * H::MD + r) * N + i]);
+    const float d = pair_diff_ho(a.Uhl, j, v, hi_i, lo_i);
+#pragma unroll
+    for (int k = 0; k < H::KD; k++) b[k] = fmaf(__ldg(&a.Pd[(((size_t)s * H::KD + k) * H::MD + r) * N + i]), d, b[k]);
+  }
+}
+
+template <int ORDER, bool WENO>
+__global__ void __launch_bounds__(128) k_recon_ho_mx(ReconArgsHOMx a) {
+  using H = HO<ORDER>;
+  constexpr int K = H::K, MC = H::MC, KD = H::KD, ND = 6;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = tid / 5, v = tid - 5 * (tid / 5);
+  if (i >= a.N) return;
+  const size_t N = a.N;
+  const float2 pi = __ldg(reinterpret_cast<const float2*>(a.Uhl + (size_t)i * 10 + 2 * v));
+  const float hi_i = pi.x, lo_i = pi.y;
+  float ao[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) ao[k] = 0.f;
+#pragma unroll 2
+  for (int m = 0; m < MC; m++) {
+    const int j = __ldg(&a.sc[(size_t)m * N + i]);
+    const float d = pair_diff_ho(a.Uhl, j, v, hi_i, lo_i);
+#pragma unroll
+    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+  }
+  float c[K];
+  if constexpr (!WENO) {
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = ao[k];
+  } else {
+    const float SI0 = si_form_f<K, K>(a.Msi, N, i, ao);
+    float SI[ND];
+    float tau = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < ND; s++) {
+      float b[KD];
+      dir_coeffs_mx<ORDER>(a, v, hi_i, lo_i, i, s, b);
+      SI[s] = si_form_f<K, KD>(a.Msi, N, i, b);
+      tau += fabsf(SI0 - SI[s]);
+    }
+    tau *= (1.f / ND);
+    const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
+    float ws[ND];
+    float wsum = w0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
+      wsum += ws[s];
+    }
+    const float iws = fdiv(1.f, wsum);
+    const float r0 = fdiv(w0 * iws, a.lam0);
+#pragma unroll
+    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
+#pragma unroll 1
+    for (int s = 0; s < ND; s++) {
+      float b[KD];
+      dir_coeffs_mx<ORDER>(a, v, hi_i, lo_i, i, s, b);
+      const float e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+      for (int k = 0; k < KD; k++) c[k] = fmaf(e, b[k], c[k]);
+    }
+  }
+  // the constant term relative to U_ref = (1, 0, 0, 0, E_ref), less the means of
+  // the non-linear monomials; coefficients in physical units
+  float c0 = v == 0 ? (hi_i - 1.f) + lo_i : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
+#pragma unroll
+  for (int k = 3; k < K; k++) c0 = fmaf(-c[k], __ldg(&a.psib[(size_t)(k - 3) * N + i]), c0);
+  const float ih = __ldg(&a.inv_h[i]);
+  float ihp[ORDER + 1];
+  ihp[0] = 1.f;
+#pragma unroll
+  for (int e = 1; e <= ORDER; e++) ihp[e] = ihp[e - 1] * ih;
+  float* out = a.coef + (size_t)i * 5 + v;
+  const size_t st = N * 5;
+  out[0] = c0;
+#pragma unroll
+  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k] * ihp[basis_degree(k)];
+}
+
+template <int ORDER, bool ACC>
+__device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ coef, int N, int cell, float x, float y,
+                                                float z, float U[5], float g[5][3]) {
+  constexpr int K = basis_count(ORDER);
+  const size_t st = (size_t)N * 5;
+  const float* p = coef + (size_t)cell * 5;
+  float px[ORDER + 1], py[ORDER + 1], pz[ORDER + 1];
+  px[0] = py[0] = pz[0] = 1.f;
+#pragma unroll
+  for (int e = 1; e <= ORDER; e++) {
+    px[e] = px[e - 1] * x;
+    py[e] = py[e - 1] * y;
+    pz[e] = pz[e - 1] * z;
+  }
+  float gx[5], gy[5], gz[5];
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    U[v] = __ldg(p + v);
+    gx[v] = gy[v] = gz[v] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const int ex = basis_exp(k, 0), ey = basis_exp(k, 1), ez = basis_exp(k, 2);
+    const float mv = px[ex] * py[ey] * pz[ez];
+    const float mx = ex ? ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez] : 0.f;
+    const float my = ey ? ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez] : 0.f;
+    const float mz = ez ? ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0] : 0.f;
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const float cc = __ldg(p + (k + 1) * st + v);
+      U[v] = fmaf(cc, mv, U[v]);
+      if (ex) gx[v] = fmaf(cc, mx, gx[v]);
+      if (ey) gy[v] = fmaf(cc, my, gy[v]);
+      if (ez) gz[v] = fmaf(cc, mz, gz[v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    if (ACC) {
+      g[v][0] += gx[v];
+      g[v][1] += gy[v];
+      g[v][2] += gz[v];
+    } else {
+      g[v][0] = gx[v];
+      g[v][1] = gy[v];
+      g[v][2] = gz[v];
+    }
+  }
+}
+
+struct FaceArgsHOMx {
+  const float* __restrict__ coef;  // [K+1][N][5]
+  const float* __restrict__ fq;    // [F][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
+  const float* __restrict__ fpen;
+  const int32_t* __restrict__ fo;
+  const int32_t* __restrict__ fn;
+  float* __restrict__ G;  // [5][F] FP32 face totals
+  int N, F;
+  FluxConstF c;
+};
+
+template <int ORDER, bool VISC>
+__global__ void __launch_bounds__(128) k_face_ho_mx(FaceArgsHOMx a) {
+  constexpr int NQ = ORDER * ORDER, FPW = 32 / NQ;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / NQ, q = lane - NQ * (lane / NQ);
+  const bool in_group = grp < FPW;
+  const int f = gw * FPW + (in_group ? grp : 0);
+  const bool live = in_group && f < a.F;
+  const int fc = live ? f : a.F - 1, qc = in_group ? q : 0;
+  const size_t F = a.F;
+  const float2* __restrict__ fq = reinterpret_cast<const float2*>(a.fq + ((size_t)fc * NQ + qc) * 10);
+  const float2 q0 = __ldg(fq), q1 = __ldg(fq + 1), q2 = __ldg(fq + 2), q3 = __ldg(fq + 3), q4 = __ldg(fq + 4);
+  const float n[3] = {q3.x, q3.y, q4.x};
+  const float area = q4.y;
+  const int o = a.fo[fc], nb = a.fn[fc];
+  float WL[5], WR[5], gs[5][3];
+  eval_side_ho_mx<ORDER, false>(a.coef, a.N, o, q0.x, q0.y, q1.x, WL, gs);
+  eval_side_ho_mx<ORDER, true>(a.coef, a.N, nb, q1.y, q2.x, q2.y, WR, gs);
+  float Fc[5];
+  hllc_flux_mx(WL, WR, n, a.c, Fc);
+  float flux[5];
+  if (VISC) {
+    // as in k_face_mx: twice the penalised face gradient, the flux of which is twice F_v
+    const float pen2 = 2.f * a.fpen[fc];
+    float Wf[5], gf2[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const float jump2 = pen2 * (WR[v] - WL[v]);
+      Wf[v] = 0.5f * (WL[v] + WR[v]);
+#pragma unroll
+      for (int j = 0; j < 3; j++) gf2[v][j] = fmaf(jump2, n[j], gs[v][j]);
+    }
+    float Fv2[5];
+    viscous_flux_mx(Wf, gf2, n, a.c, Fv2);
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = fmaf(-0.5f, Fv2[v], Fc[v]) * area;
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+  }
+  const int base = (in_group ? grp : 0) * NQ;
+  float tot[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int t = 0; t < NQ; t++)
 #pragma unroll

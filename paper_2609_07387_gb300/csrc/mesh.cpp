@@ -645,8 +645,10 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; i++) {
       const double* mu = &cm[(size_t)i * kMomSlots];
-      const double ih = 1.0 / g[i].h;
-      auto xmu = [&](int a, int b, int c) { return mu[mom_index(a, b, c)] * std::pow(ih, a + b + c); };
+      double ihp[2 * kMaxOrder + 1];  // (1/h)^e
+      ihp[0] = 1.0;
+      for (int e = 1; e <= 2 * kMaxOrder; e++) ihp[e] = ihp[e - 1] / g[i].h;
+      auto xmu = [&](int a, int b, int c) { return mu[mom_index(a, b, c)] * ihp[a + b + c]; };
       for (int k = 3; k < K; k++)
         h->psib[(size_t)(k - 3) * N + i] = xmu(basis_exp(k, 0), basis_exp(k, 1), basis_exp(k, 2));
       int q = 0;
@@ -692,11 +694,21 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
   // P3/P4 rows (moment form from the member's central moments): the mean of
   // ((x - c_i)/h_i)^a over the member's image, expanded about its centroid c_j'
   // by the binomial theorem, less cell i's own mean of that monomial, times |V_j|
+  double bin[kMaxOrder + 1][kMaxOrder + 1];  // binomial coefficients C(n, k)
+  for (int n = 0; n <= kMaxOrder; n++)
+    for (int k = 0; k <= kMaxOrder; k++) bin[n][k] = k <= n ? binom(n, k) : 0.0;
   auto arow_ho = [&](int64_t i, int64_t j, int KK, double* row) {
     double s[3];
     shift_of(i, j, s);
-    double d[3];
-    for (int q = 0; q < 3; q++) d[q] = comp(g[j].c, q) + s[q] - comp(g[i].c, q);
+    double dp[3][kMaxOrder + 1];  // powers of the centroid offset, per coordinate
+    for (int q = 0; q < 3; q++) {
+      const double d = comp(g[j].c, q) + s[q] - comp(g[i].c, q);
+      dp[q][0] = 1.0;
+      for (int e = 1; e <= kMaxOrder; e++) dp[q][e] = dp[q][e - 1] * d;
+    }
+    double ihp[kMaxOrder + 1];
+    ihp[0] = 1.0;
+    for (int e = 1; e <= kMaxOrder; e++) ihp[e] = ihp[e - 1] / g[i].h;
     const double* muj = &cm[(size_t)j * kMomSlots];
     const double* mui = &cm[(size_t)i * kMomSlots];
     for (int k = 0; k < KK; k++) {
@@ -705,9 +717,9 @@ int host_precompute(ucns_mesh* m, const ucns_params* p, HostArrays* h) {
       for (int b0 = 0; b0 <= a[0]; b0++)
         for (int b1 = 0; b1 <= a[1]; b1++)
           for (int b2 = 0; b2 <= a[2]; b2++)
-            t += binom(a[0], b0) * binom(a[1], b1) * binom(a[2], b2) * std::pow(d[0], a[0] - b0) *
-                 std::pow(d[1], a[1] - b1) * std::pow(d[2], a[2] - b2) * muj[mom_index(b0, b1, b2)];
-      row[k] = g[j].V * (t - mui[mom_index(a[0], a[1], a[2])]) * std::pow(1.0 / g[i].h, a[0] + a[1] + a[2]);
+            t += bin[a[0]][b0] * bin[a[1]][b1] * bin[a[2]][b2] * dp[0][a[0] - b0] * dp[1][a[1] - b1] *
+                 dp[2][a[2] - b2] * muj[mom_index(b0, b1, b2)];
+      row[k] = g[j].V * (t - mui[mom_index(a[0], a[1], a[2])]) * ihp[a[0] + a[1] + a[2]];
     }
   };
   auto row_of = [&](int64_t i, int64_t j, int KK, double* row) {

@@ -37,6 +37,10 @@ struct DeviceMesh {
   int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
   double* Pd = nullptr;       // [nd][Kd][Md][N]
   double* Msi = nullptr;      // P3/P4: [K(K+1)/2][N] smoothness-indicator matrix (upper triangle, row-major)
+  float* Pcf = nullptr;       // P3/P4 mixed form: FP32 copies of Pc, Pd, Msi, psib
+  float* Pdf = nullptr;
+  float* Msif = nullptr;
+  float* psibf = nullptr;
   double* psib = nullptr;     // P3/P4: [K-3][N] cell means of the non-linear basis monomials (xi units)
   // mixed precision: FP32 pseudo-inverses and the stencils in the pair-blocked
   // layout [ceil(N/64)][rows/2][64][2] (tiles of 64 consecutive cells, row

@@ -27,7 +27,9 @@ def _mesh(nodes, cells, box, prec, **kw):
 @pytest.mark.parametrize("tets,mach,order,scheme,n", [
     (False, 0.1, 2, 1, 10), (False, 1.25, 2, 1, 10), (True, 0.1, 2, 1, 6),
     # 9^3 = 729 cells: 11 full tiles of 64 cells and a ragged one of 25
-    (False, 0.1, 1, 0, 9), (False, 0.1, 2, 0, 9), (False, 1.25, 2, 1, 9)])
+    (False, 0.1, 1, 0, 9), (False, 0.1, 2, 0, 9), (False, 1.25, 2, 1, 9),
+    # P3 / P4 (thread-per-cell kernels, 3 / 2 faces per warp)
+    (False, 0.3, 3, 1, 10), (False, 1.25, 3, 1, 10), (False, 0.3, 4, 0, 10), (False, 0.3, 4, 1, 11)])
 def test_mixed_residual_error_vs_oracle(tets, mach, order, scheme, n):
     nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=5)
     if tets:
@@ -46,18 +48,19 @@ def test_mixed_residual_error_vs_oracle(tets, mach, order, scheme, n):
     assert np.all(tot <= 1e-12 * (S * vol).sum(axis=1)), tot
 
 
-def test_mixed_ke_and_dissipation_history_vs_fp64():
-    """16^3 jittered hexahedra, P2 CWENOZ, TGV Mach 0.1: 100 SSP-RK3 steps of
-    the mixed form against the FP64 form from the same state with the same
+@pytest.mark.parametrize("order,steps", [(2, 100), (3, 40), (4, 20)])
+def test_mixed_ke_and_dissipation_history_vs_fp64(order, steps):
+    """16^3 jittered hexahedra, P2 (P3, P4) CWENOZ, TGV Mach 0.1: SSP-RK3 steps
+    of the mixed form against the FP64 form from the same state with the same
     dt sequence."""
     nodes, cells, box = I.hex_lattice(16, jitter=0.1, seed=1)
-    m64 = _mesh(nodes, cells, box, 0)
-    m32 = _mesh(nodes, cells, box, 1)
+    m64 = _mesh(nodes, cells, box, 0, order=order)
+    m32 = _mesh(nodes, cells, box, 1, order=order)
     U0 = np.ascontiguousarray(m64.to_internal(I.tgv_state(nodes, cells, 0.1)))
     a = torch.from_numpy(U0.copy()).cuda()
     b = torch.from_numpy(U0.copy()).cuda()
     worst = {"ke": 0.0, "eps_s": 0.0, "eps_d": 0.0}
-    for step in range(100):
+    for step in range(steps):
         dt = m64.time_step(a)
         m64.rk_step(a, dt=dt)
         m32.rk_step(b, dt=dt)

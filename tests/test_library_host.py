@@ -71,9 +71,6 @@ def test_error_codes_without_gpu():
     with pytest.raises(ucns.UcnsError) as e:
         m.precompute_host(ucns.Params(order=5))
     assert e.value.code == -1
-    with pytest.raises(ucns.UcnsError) as e:
-        m.precompute_host(ucns.Params(order=3, precision=1))  # the mixed form is built for P1 and P2
-    assert e.value.code == -1
     with pytest.raises(ucns.UcnsError) as e:  # orders 3 and 4 on hexahedra only
         ucns.Mesh(nodes, I.split_tets(cells), box).precompute_host(ucns.Params(order=3))
     assert e.value.code == -1

@@ -43,16 +43,17 @@ int upload(T** dst, const std::vector<T>& src) {
   return UCNS_OK;
 }
 
-int upload_f32(float** dst, const std::vector<double>& src) {
+int upload_f32(float** dst, const std::vector<double>& src, size_t npad = 0) {
   std::vector<float> f(src.begin(), src.end());
+  if (f.size() < npad) f.resize(npad, 0.f);
   return upload(dst, f);
 }
 
 // [rows][N] -> cell-contiguous [N][rows], converted to T
 template <typename T, typename S>
-int upload_cellwise(T** dst, const std::vector<S>& src, int rows, int64_t N) {
+int upload_cellwise(T** dst, const std::vector<S>& src, int rows, int64_t N, int64_t Npad = 0) {
   if (src.empty()) return UCNS_OK;
-  std::vector<T> b((size_t)N * rows);
+  std::vector<T> b((size_t)std::max(N, Npad) * rows, T(0));
   for (int r = 0; r < rows; r++)
     for (int64_t i = 0; i < N; i++) b[(size_t)i * rows + r] = (T)src[(size_t)r * N + i];
   return upload(dst, b);
@@ -251,30 +252,49 @@ int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   return gated ? launch_recon_tiles<2, false, 4, true>(a, s) : launch_recon_tiles<2, true, 4>(a, s);
 }
 
+// persistent blocks (as many as fit at once, at most one per batch), as many
+// pipeline stages as the shared memory holds
+template <int ORDER, bool VISC>
+int launch_face_tiles(FaceArgsMx a, cudaStream_t s) {
+  using T = FaceTileMx<ORDER>;
+  if (a.cs != T::CS) return fail(UCNS_ERR_INVALID_ARG, "coefficient row size mismatch");
+  int dev = 0, sms = 0, optin = 0, per_sm = 0;
+  UCNS_CUDA(cudaGetDevice(&dev));
+  UCNS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  UCNS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  a.stages = kFaceMaxStages;
+  while (a.stages > 2 && T::smem(a.nu, a.stages) > (size_t)optin) a.stages--;
+  const size_t sm = T::smem(a.nu, a.stages);
+  if (sm > (size_t)optin) return fail(UCNS_ERR_INVALID_ARG, "face batch rows exceed shared memory");
+  UCNS_CUDA(cudaFuncSetAttribute(k_face_mx<ORDER, VISC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  UCNS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_face_mx<ORDER, VISC>, kFaceThreads, sm));
+  const int64_t batches = ((int64_t)a.F + T::FB - 1) / T::FB;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(batches, (int64_t)sms * std::max(per_sm, 1)));
+  k_face_mx<ORDER, VISC><<<g, kFaceThreads, sm, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   if (m->K > 9) return launch_face_ho_mx(m, s);
   FaceArgsMx a;
   a.coef = m->d.coeff;
   a.fq = m->d.fqf;
   a.fpen = m->d.fpenf;
-  a.fo = m->d.fo;
-  a.fn = m->d.fn;
   a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
+  a.fslot = m->d.fslot;
+  a.bcell = m->d.bcell;
+  a.bcount = m->d.bcount;
+  a.err = m->d.err;
   a.N = (int)m->N;
   a.F = (int)m->F;
   a.cs = coef_row_floats(m);
+  a.nu = m->d.fnu;
+  a.stages = 2;
   a.c = flux_const_f(m->P);
   const bool visc = m->P.reynolds > 0.0;
-  const unsigned g = nblocks((size_t)m->F * m->nq);
-  if (m->K == 3) {
-    if (visc) k_face_mx<1, true><<<g, 256, 0, s>>>(a);
-    else k_face_mx<1, false><<<g, 256, 0, s>>>(a);
-  } else {
-    if (visc) k_face_mx<2, true><<<g, 256, 0, s>>>(a);
-    else k_face_mx<2, false><<<g, 256, 0, s>>>(a);
-  }
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
+  if (m->K == 3) return visc ? launch_face_tiles<1, true>(a, s) : launch_face_tiles<1, false>(a, s);
+  return visc ? launch_face_tiles<2, true>(a, s) : launch_face_tiles<2, false>(a, s);
 }
 
 // P3 / P4 (FP64, hexahedra)
@@ -818,7 +838,7 @@ void device_free(ucns_mesh* m) {
   m->gate_eval_active = false;
   m->gate_fixed = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcf, d.Pdf, d.Msif, d.psibf, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
+  void* ptrs[] = {d.fslot, d.bcell, d.bcount, d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcf, d.Pdf, d.Msif, d.psibf, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.dvalid, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
@@ -948,6 +968,46 @@ int ucns_stencil(const ucns_mesh* m, int64_t cell, int32_t which, int64_t* membe
   return UCNS_OK;
 }
 
+// Batches of the P1/P2 mixed face kernel (fb faces each): per batch the
+// distinct cells of its faces' owners and neighbours in order of first use,
+// per face the slots of its two rows (owner | neighbour << 16); arrays padded
+// to fpad faces.  nu = the largest count, rounded up to a multiple of 4.
+void face_batches(const std::vector<int32_t>& fo, const std::vector<int32_t>& fn, int64_t N, int fb, int64_t fpad,
+                  std::vector<int32_t>& fslot, std::vector<int32_t>& bcell, std::vector<int32_t>& bcount, int& nu) {
+  const int64_t F = (int64_t)fo.size(), nbat = (F + fb - 1) / fb;
+  std::vector<int64_t> stamp((size_t)N, -1);
+  std::vector<int32_t> slot((size_t)N, 0);
+  fslot.assign((size_t)fpad, 0);
+  bcount.assign((size_t)nbat, 0);
+  std::vector<int32_t> order;
+  order.reserve((size_t)F * 2);
+  for (int64_t b = 0; b < nbat; b++) {
+    int32_t c = 0;
+    for (int64_t f = b * fb; f < std::min(F, (b + 1) * fb); f++) {
+      int32_t sl[2];
+      const int32_t cells[2] = {fo[f], fn[f]};
+      for (int e = 0; e < 2; e++) {
+        const int32_t i = cells[e];
+        if (stamp[i] != b) {
+          stamp[i] = b;
+          slot[i] = c++;
+          order.push_back(i);
+        }
+        sl[e] = slot[i];
+      }
+      fslot[f] = sl[0] | (sl[1] << 16);
+    }
+    bcount[b] = c;
+  }
+  int mx = 1;
+  for (int32_t c : bcount) mx = std::max(mx, (int)c);
+  nu = (mx + 3) / 4 * 4;
+  bcell.assign((size_t)nbat * nu, 0);
+  size_t o = 0;
+  for (int64_t b = 0; b < nbat; b++)
+    for (int32_t u = 0; u < bcount[b]; u++) bcell[(size_t)b * nu + u] = order[o++];
+}
+
 int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   int rc = check_params(m, p);
   if (rc) return rc;
@@ -988,6 +1048,11 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     }
   } else if (p->precision == UCNS_PREC_MIXED) {
     const int rc_rows = m->K * m->Mc, rd_rows = m->nd * 3 * m->Md;
+    const int64_t fpad = (m->F + kFacePad - 1) / kFacePad * kFacePad;  // whole batches for the face kernel's copies
+    std::vector<int32_t> fslot, bcell, bcount;
+    int nu = 0;
+    face_batches(fo, fn, m->N, kFacePts / m->nq, fpad, fslot, bcell, bcount, nu);
+    d.fnu = nu;
     std::vector<double> cellrows((size_t)kCellRows * m->N);
     std::copy(h.mom.begin(), h.mom.begin() + (size_t)6 * m->N, cellrows.begin());
     std::copy(h.inv_h.begin(), h.inv_h.end(), cellrows.begin() + (size_t)6 * m->N);
@@ -998,7 +1063,8 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
         (rc = upload_blocked(&d.cellb, cellrows, kCellRows, m->N, false)) ||
         (rc = upload_cellwise(&d.sda, h.sd, m->nd * m->Md, m->N)) ||
         (rc = upload_cellwise(&d.Pda, h.Pd, rd_rows, m->N)) ||
-        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
+        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F, fpad)) || (rc = upload_f32(&d.fpenf, h.fpen, fpad)) ||
+        (rc = upload(&d.fslot, fslot)) || (rc = upload(&d.bcell, bcell)) || (rc = upload(&d.bcount, bcount)) ||
         (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);

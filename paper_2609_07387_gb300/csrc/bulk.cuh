@@ -13,9 +13,14 @@ constexpr long long kBulkWaitCycles = 1ll << 30;  // ~0.5 s at 2 GHz: a wait giv
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void bar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+__device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count = 1) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one plain arrival (no bytes announced)
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // the single arrival of the phase, announcing `bytes` of incoming copies
@@ -47,6 +52,17 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, long lo
     if (done) return true;
     if ((it & 63u) == 63u && clock64() - t0 > limit) return false;
   }
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), tracked per thread
+__device__ __forceinline__ void async_copy16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// one arrival on `bar` once this thread's earlier async_copy16 copies have
+// landed (the arrival is one of the barrier's expected count)
+__device__ __forceinline__ void async_copies_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 // make this thread's generic-proxy shared-memory writes visible to the bulk copy unit

@@ -102,15 +102,50 @@ struct ReconArgsMx {
 };
 
 struct FaceArgsMx {
-  const float* __restrict__ coef;  // [N][cs] cell rows, 16-byte aligned
-  const float* __restrict__ fq;    // [F][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
-  const float* __restrict__ fpen;
-  const int32_t* __restrict__ fo;
-  const int32_t* __restrict__ fn;
-  float* __restrict__ G;  // [5][F] FP32 face totals
-  int N, F;
+  const float* __restrict__ coef;     // [N][cs] cell rows, 16-byte aligned
+  const float* __restrict__ fq;       // [F'][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
+  const float* __restrict__ fpen;     // [F']
+  const int32_t* __restrict__ fslot;  // [F']: slots of the owner's (low 16 bits) and neighbour's rows in the batch
+  const int32_t* __restrict__ bcell;  // [batches][nu]: the batch's distinct cells, slot order
+  const int32_t* __restrict__ bcount; // [batches]: how many
+  float* __restrict__ G;              // [5][F] FP32 face totals
+  int* err;                           // bit 1: a copy wait gave up
+  int N, F;                           // F' = F rounded up to whole batches (zero entries)
   int cs;
+  int nu;      // slots per batch (at least the largest count)
+  int stages;  // pipeline depth, 2 .. kFaceMaxStages
   FluxConstF c;
+};
+
+// The face kernel's pipeline.  A persistent block has kFaceWarps warps that
+// evaluate (thread = one Gauss point, kFacePts points a batch) and
+// kFaceCopyWarps warps that copy, batch by batch in turn.  Faces are taken in
+// batches of kFacePts / nq; a copying warp brings each batch's Gauss points, penalty factors and row slots (bulk
+// copies) and the coefficient rows of its distinct cells (each once, a cell
+// shared by several of the batch's faces included; 16-byte asynchronous
+// copies spread over the lanes) into one of `stages` shared-memory stages, up
+// to stages - 1 batches ahead of the evaluating warps, which hand a stage
+// back through its "empty" barrier.
+constexpr int kFaceWarps = 16;
+constexpr int kFaceCopyWarps = 3;  // copying warp w takes the block's batches k = w mod 3
+constexpr int kFaceThreads = 32 * (kFaceWarps + kFaceCopyWarps);
+constexpr int kFacePts = 32 * kFaceWarps;
+constexpr int kFacePad = kFacePts;  // the per-face arrays hold whole batches at every order
+constexpr int kFaceMaxStages = 6;
+
+template <int ORDER>
+struct FaceTileMx {
+  static constexpr int NQ = ORDER * ORDER;
+  static constexpr int CS = ORDER == 1 ? 20 : 52;  // floats per coefficient row
+  static constexpr int FB = kFacePts / NQ;         // faces per batch
+  static constexpr int PTS = kFacePts * 10;        // the batch's Gauss points
+  static constexpr int NUR = 2 * FB / 32;          // slot registers per lane of a copying warp
+  // a stage: Gauss points, penalties, slot words, then nu rows
+  __host__ __device__ static constexpr int stage_floats(int nu) { return PTS + 2 * FB + nu * CS; }
+  __host__ __device__ static constexpr size_t smem(int nu, int stages) {
+    return (size_t)stages * stage_floats(nu) * 4 + (size_t)2 * kFaceMaxStages * 8;
+  }
+  static_assert(kFacePad % FB == 0 && (PTS + 2 * FB) % 4 == 0 && CS % 4 == 0, "whole 16-byte copies");
 };
 
 // U_j - U_i of variable v from the float pairs: hi_j - hi_i is exact for
@@ -392,14 +427,14 @@ __global__ void __launch_bounds__(256) k_float_pair(const double* __restrict__ u
 // FP32x2 pairs (0, 1) and (2, 3), whose lanes round exactly as the scalar
 // operations of variable 4 (the same FMA sequence per variable).
 template <int ORDER, bool ACC>
-__device__ __forceinline__ void eval_side_mx(const float* __restrict__ coef, int cell, float x, float y, float z,
-                                             float U[5], float g[5][3]) {
+__device__ __forceinline__ void eval_side_mx(const float* row_, float x, float y, float z, float U[5],
+                                             float g[5][3]) {
   constexpr int CS = ORDER == 1 ? 20 : 52;
   constexpr int NCF = ORDER == 1 ? 4 : 10;  // entries per variable
   float4 q[CS / 4];
-  const float4* row = reinterpret_cast<const float4*>(coef + (size_t)cell * CS);
+  const float4* row = reinterpret_cast<const float4*>(row_);
 #pragma unroll
-  for (int i = 0; i < CS / 4; i++) q[i] = __ldg(row + i);
+  for (int i = 0; i < CS / 4; i++) q[i] = row[i];
   const float2 X = make_float2(x, x), Y = make_float2(y, y), Z = make_float2(z, z);
 #pragma unroll
   for (int p = 0; p < 2; p++) {
@@ -561,56 +596,142 @@ __device__ __forceinline__ void viscous_flux_mx(const float W[5], const float g[
 }
 
 template <int ORDER, bool VISC>
-__global__ void __launch_bounds__(256, 4) k_face_mx(FaceArgsMx a) {
-  constexpr int NQ = ORDER * ORDER;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = tid / NQ, q = tid - NQ * (tid / NQ);
-  const bool live = f < a.F;
-  const int fc = live ? f : a.F - 1;
-  const size_t F = a.F;
-  // the point's 10 floats, contiguous: five 8-byte loads from one address
-  const float2* __restrict__ fq = reinterpret_cast<const float2*>(a.fq + ((size_t)fc * NQ + q) * 10);
-  const float2 q0 = __ldg(fq), q1 = __ldg(fq + 1), q2 = __ldg(fq + 2), q3 = __ldg(fq + 3), q4 = __ldg(fq + 4);
-  const float xl = q0.x, yl = q0.y, zl = q1.x;
-  const float xr = q1.y, yr = q2.x, zr = q2.y;
-  const float n[3] = {q3.x, q3.y, q4.x};
-  const float area = q4.y;
-  const int o = a.fo[fc], nb = a.fn[fc];
-  float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
-  eval_side_mx<ORDER, false>(a.coef, o, xl, yl, zl, WL, gs);
-  eval_side_mx<ORDER, true>(a.coef, nb, xr, yr, zr, WR, gs);
-  float Fc[5];
-  hllc_flux_mx(WL, WR, n, a.c, Fc);
-  float flux[5];
-  if (VISC) {
-    // twice the penalised face gradient, 2 alpha/L [U] n + (grad U_L + grad U_R):
-    // the viscous flux is linear in the gradient and scaling by 2 is exact, so
-    // the flux of this gradient is exactly 2 F_v (and the halving of grad U_L +
-    // grad U_R drops out)
-    const float pen2 = 2.f * a.fpen[fc];
-    float Wf[5], gf2[5][3];
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float jump2 = pen2 * (WR[v] - WL[v]);
-      Wf[v] = 0.5f * (WL[v] + WR[v]);
-#pragma unroll
-      for (int j = 0; j < 3; j++) gf2[v][j] = fmaf(jump2, n[j], gs[v][j]);
-    }
-    float Fv2[5];
-    viscous_flux_mx(Wf, gf2, n, a.c, Fv2);
-#pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] = fmaf(-0.5f, Fv2[v], Fc[v]) * area;
-  } else {
-#pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+__global__ void __launch_bounds__(kFaceThreads, 1) k_face_mx(FaceArgsMx a) {
+  using T = FaceTileMx<ORDER>;
+  constexpr int NQ = T::NQ, CS = T::CS, FB = T::FB;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int S = a.stages, SF = T::stage_floats(a.nu);
+  float* st = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(st + (size_t)S * SF);
+  uint64_t* empty = full + kFaceMaxStages;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nbat = (a.F + FB - 1) / FB;
+  const int mine = (int)blockIdx.x < nbat ? (nbat - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (t < S) {
+    bar_init(&full[t], 33);  // the bulk copies' announcing arrival and the 32 lanes' row-copy arrivals
+    bar_init(&empty[t], kFaceWarps);
   }
+  __syncthreads();
+  if (warp >= kFaceWarps) {
+    // a copying warp: the next batch's distinct cells, loaded one batch ahead
+    int cell[T::NUR];
+    int cnt = 0;
+    auto load_cells = [&](int k) {
+      const size_t b = (size_t)blockIdx.x + (size_t)k * gridDim.x;
+      cnt = __ldg(&a.bcount[b]);
 #pragma unroll
-  for (int off = 1; off < NQ; off <<= 1)
+      for (int r = 0; r < T::NUR; r++) {
+        const int u = lane + 32 * r;
+        cell[r] = u < cnt ? __ldg(&a.bcell[b * a.nu + u]) : 0;
+      }
+    };
+    constexpr int PC = CS / 4;  // 16-byte pieces per row
+    int sq[PC], pq[PC];
 #pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
-  if (live && q == 0) {
+    for (int i = 0; i < PC; i++) {
+      sq[i] = (32 * i + lane) / PC;
+      pq[i] = (32 * i + lane) % PC;
+    }
+    const int w0 = warp - kFaceWarps;
+    int k = w0;
+    bool ok = true;
+    if (k < mine) load_cells(k);
+    for (; k < mine; k += kFaceCopyWarps) {
+      const int s = k % S;
+      if (k >= S && !bar_wait(&empty[s], (uint32_t)(k / S + 1) & 1u)) {  // batch k - S handed back
+        ok = false;
+        break;
+      }
+      const int f0 = ((int)blockIdx.x + k * (int)gridDim.x) * FB;
+      float* sr = st + (size_t)s * SF;
+      if (lane == 0) {
+        bar_expect(&full[s], (uint32_t)(T::PTS + 2 * FB) * 4u);  // the rows arrive through the lanes' arrivals
+        bulk_load(sr, a.fq + (size_t)f0 * NQ * 10, T::PTS * 4, &full[s]);
+        bulk_load(sr + T::PTS, a.fpen + f0, FB * 4, &full[s]);
+        bulk_load(sr + T::PTS + FB, a.fslot + f0, FB * 4, &full[s]);
+      }
+      // the rows in 16-byte pieces: slots 32 r .. 32 r + 31 are PC x 32 pieces,
+      // piece 32 i + lane being piece pq[i] of slot 32 r + sq[i] (consecutive
+      // pieces on consecutive lanes); the slot's cell comes from its lane
+      float4* dst = reinterpret_cast<float4*>(sr + T::PTS + 2 * FB);
+      const float4* src = reinterpret_cast<const float4*>(a.coef);
 #pragma unroll
-    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = flux[v];
+      for (int r = 0; r < T::NUR; r++) {
+        if (32 * r >= cnt) break;
+#pragma unroll
+        for (int i = 0; i < PC; i++) {
+          const int c = __shfl_sync(0xffffffffu, cell[r], sq[i]);
+          if (32 * r + sq[i] < cnt) async_copy16(dst + (32 * r + sq[i]) * PC + pq[i], src + (size_t)c * PC + pq[i]);
+        }
+      }
+      async_copies_arrive(&full[s]);
+      if (k + kFaceCopyWarps < mine) load_cells(k + kFaceCopyWarps);
+    }
+    if (!ok && lane == 0) atomicOr(a.err, 2);
+    // the copies this warp started into the stages' last batches land before
+    // the block's shared memory is released (after a give-up: the batches
+    // before the one it gave up on)
+    const int hi = ok ? mine : k;
+    if (lane == 0)
+      for (int kk = max(hi - S, 0); kk < hi; kk++)
+        if ((kk - w0) % kFaceCopyWarps == 0) bar_wait(&full[kk % S], (uint32_t)(kk / S) & 1u);
+    return;
+  }
+  const int j = t / NQ, q = t - NQ * (t / NQ);
+  for (int k = 0; k < mine; k++) {
+    const int s = k % S;
+    const bool ok = __all_sync(0xffffffffu, bar_wait(&full[s], (uint32_t)(k / S) & 1u));
+    if (!ok) {
+      if (lane == 0) atomicOr(a.err, 2);
+      return;
+    }
+    const int f = ((int)blockIdx.x + k * (int)gridDim.x) * FB + j;
+    const float* sr = st + (size_t)s * SF;
+    // the point's 10 floats: five 8-byte loads
+    const float2* fq = reinterpret_cast<const float2*>(sr + t * 10);
+    const float2 q0 = fq[0], q1 = fq[1], q2 = fq[2], q3 = fq[3], q4 = fq[4];
+    const float n[3] = {q3.x, q3.y, q4.x};
+    const float area = q4.y;
+    const int slots = reinterpret_cast<const int*>(sr + T::PTS + FB)[j];
+    const float* rows = sr + T::PTS + 2 * FB;
+    float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
+    eval_side_mx<ORDER, false>(rows + (slots & 0xffff) * CS, q0.x, q0.y, q1.x, WL, gs);
+    eval_side_mx<ORDER, true>(rows + (slots >> 16) * CS, q1.y, q2.x, q2.y, WR, gs);
+    const float pen2 = 2.f * sr[T::PTS + j];
+    __syncwarp();
+    if (lane == 0) bar_arrive(&empty[s]);  // this warp is done reading the stage
+    float Fc[5];
+    hllc_flux_mx(WL, WR, n, a.c, Fc);
+    float flux[5];
+    if (VISC) {
+      // twice the penalised face gradient, 2 alpha/L [U] n + (grad U_L + grad U_R):
+      // the viscous flux is linear in the gradient and scaling by 2 is exact, so
+      // the flux of this gradient is exactly 2 F_v (and the halving of grad U_L +
+      // grad U_R drops out)
+      float Wf[5], gf2[5][3];
+#pragma unroll
+      for (int v = 0; v < 5; v++) {
+        const float jump2 = pen2 * (WR[v] - WL[v]);
+        Wf[v] = 0.5f * (WL[v] + WR[v]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) gf2[v][d] = fmaf(jump2, n[d], gs[v][d]);
+      }
+      float Fv2[5];
+      viscous_flux_mx(Wf, gf2, n, a.c, Fv2);
+#pragma unroll
+      for (int v = 0; v < 5; v++) flux[v] = fmaf(-0.5f, Fv2[v], Fc[v]) * area;
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
+    }
+#pragma unroll
+    for (int off = 1; off < NQ; off <<= 1)
+#pragma unroll
+      for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
+    if (f < a.F && q == 0) {
+#pragma unroll
+      for (int v = 0; v < 5; v++) a.G[(size_t)v * a.F + f] = flux[v];
+    }
   }
 }
 

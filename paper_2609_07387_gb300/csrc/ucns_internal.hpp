@@ -53,7 +53,11 @@ struct DeviceMesh {
   int32_t* sda = nullptr;     // [N][nd Md] directional stencils, cell-contiguous (gated CWENOZ)
   float* Pda = nullptr;       // [N][nd 3 Md] directional rows, cell-contiguous
   float* inv_hf = nullptr;    // [N]
-  float* fpenf = nullptr;     // [F]
+  float* fpenf = nullptr;     // [F] ([F'] padded to whole face batches in the P1/P2 mixed form)
+  int32_t* fslot = nullptr;   // [F'] mixed face batches: owner | neighbour << 16 row slots
+  int32_t* bcell = nullptr;   // [batches][fnu] the batch's distinct cells
+  int32_t* bcount = nullptr;  // [batches]
+  int32_t fnu = 0;            // slots per batch
   int32_t* cf = nullptr;      // [nfc][N] face id << 1 | (cell is the neighbour)
   // faces
   int32_t* fo = nullptr;      // [F] owner

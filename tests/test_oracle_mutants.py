@@ -171,9 +171,10 @@ PY_MUTANTS = [
      "test_gradient_matches_finite_differences"),
     ("bf16_truncates", "mlp.py", ("u = ((u + 0x7FFF + lsb) >> 16) << 16", "u = (u >> 16) << 16"),
      "test_bf16_rounding_is_nearest_even"),
-    ("bf16_hidden_activation_not_rounded", "mlp.py", ("    h1r = r(h1)\n", "    h1r = h1\n"),
+    ("bf16_hidden_activation_not_rounded", "mlp.py",
+     ("h1r = r(np.maximum(a1, 0.0)) if h1 is None", "h1r = np.maximum(a1, 0.0) if h1 is None"),
      "test_bf16_rounding_places_worked_example"),
-    ("bias_gradient_from_the_rounded_dh2", "mlp.py", ('g["b2"] = dh2.sum(axis=0)', 'g["b2"] = dh2r.sum(axis=0)'),
+    ("bias_gradient_from_the_rounded_dh2", "mlp.py", ('g["b2"] = f(dh2).sum(axis=0)', 'g["b2"] = f(dh2r).sum(axis=0)'),
      "test_bf16_rounding_places_worked_example"),
     ("label_linear_weights", "__init__.py", ("/ (self.params.lam_central + self.nd)", "/ (self.params.lam_central + self.nd + 1)"),
      "test_labels_vanish_on_a_uniform_flow_and_flag_a_step"),

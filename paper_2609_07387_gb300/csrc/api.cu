@@ -182,14 +182,16 @@ int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const unsigned g = nblocks((size_t)m->N * 5, 128);
+  const unsigned g = (unsigned)((m->N + kHoCells - 1) / kHoCells);
   const bool weno = m->nd > 0;
   if (m->K == 19) {
-    if (weno) k_recon_ho_mx<3, true><<<g, 128, 0, s>>>(a);
-    else k_recon_ho_mx<3, false><<<g, 128, 0, s>>>(a);
+    constexpr size_t sm = recon_ho_mx_smem<3>();
+    if (weno) k_recon_ho_mx<3, true><<<g, kHoCells, sm, s>>>(a);
+    else k_recon_ho_mx<3, false><<<g, kHoCells, sm, s>>>(a);
   } else {
-    if (weno) k_recon_ho_mx<4, true><<<g, 128, 0, s>>>(a);
-    else k_recon_ho_mx<4, false><<<g, 128, 0, s>>>(a);
+    constexpr size_t sm = recon_ho_mx_smem<4>();
+    if (weno) k_recon_ho_mx<4, true><<<g, kHoCells, sm, s>>>(a);
+    else k_recon_ho_mx<4, false><<<g, kHoCells, sm, s>>>(a);
   }
   UCNS_CUDA(cudaGetLastError());
   return UCNS_OK;

@@ -286,114 +286,192 @@ struct ReconArgsHOMx {
   float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair
 };
 
-template <int K, int KK>
-__device__ __forceinline__ float si_form_f(const float* __restrict__ M, size_t N, int i, const float (&a)[KK]) {
-  float s = 0.f;
+// a^T M a of each of the five variables over the first KK modes (M as in
+// si_form; at(l, v) = a_l of variable v); per variable the same operations in
+// the same order as si_form in FP32
+template <int K, int KK, class A>
+__device__ __forceinline__ void si_form5(const float* __restrict__ M, size_t N, int i, A at, float s[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; v++) s[v] = 0.f;
 #pragma unroll
   for (int k = 0; k < KK; k++) {
-    float t = 0.f;
+    float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int l = k + 1; l < KK; l++) t = fmaf(__ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]), a[l], t);
+    for (int l = k + 1; l < KK; l++) {
+      const float m = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]);
+#pragma unroll
+      for (int v = 0; v < 5; v++) t[v] = fmaf(m, at(l, v), t[v]);
+    }
     const float mkk = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2) * N + i]);
-    s = fmaf(a[k], fmaf(2.f, t, mkk * a[k]), s);
+#pragma unroll
+    for (int v = 0; v < 5; v++) {
+      const float ak = at(k, v);
+      s[v] = fmaf(ak, fmaf(2.f, t[v], mkk * ak), s[v]);
+    }
   }
-  return s;
 }
 
-// U_j - U_i of variable v from the float pairs (the leading parts subtract exactly)
-__device__ __forceinline__ float pair_diff_ho(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
-  const float2 p = __ldg(reinterpret_cast<const float2*>(hl + (size_t)j * 10 + 2 * v));
-  return (p.x - hi_i) + (p.y - lo_i);
+// U_j - U_i of the five variables from the float pairs (the leading parts subtract exactly)
+__device__ __forceinline__ void pair_diff5(const float* __restrict__ hl, int j, const float hi_i[5],
+                                           const float lo_i[5], float d[5]) {
+  const float2* p = reinterpret_cast<const float2*>(hl + (size_t)j * 10);
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    const float2 q = __ldg(p + v);
+    d[v] = (q.x - hi_i[v]) + (q.y - lo_i[v]);
+  }
 }
 
+// directional candidate s of the five variables: b[k][v] = sum_r Pd[s][k][r] (U_r - U_i)_v
 template <int ORDER>
-__device__ __forceinline__ void dir_coeffs_mx(const ReconArgsHOMx& a, int v, float hi_i, float lo_i, int i, int s,
-                                              float (&b)[HO<ORDER>::KD]) {
+__device__ __forceinline__ void dir_coeffs5(const ReconArgsHOMx& a, const float hi_i[5], const float lo_i[5], int i,
+                                            int s, float (&b)[HO<ORDER>::KD][5]) {
   using H = HO<ORDER>;
   const size_t N = a.N;
 #pragma unroll
-  for (int k = 0; k < H::KD; k++) b[k] = 0.f;
+  for (int k = 0; k < H::KD; k++)
+#pragma unroll
+    for (int v = 0; v < 5; v++) b[k][v] = 0.f;
 #pragma unroll 2
   for (int r = 0; r < H::MD; r++) {
-    const int j = __ldg(&a.sd[((size_t)s * H::MD + r) * N + i]);
-    const float d = pair_diff_ho(a.Uhl, j, v, hi_i, lo_i);
+    float d[5];
+    pair_diff5(a.Uhl, __ldg(&a.sd[((size_t)s * H::MD + r) * N + i]), hi_i, lo_i, d);
 #pragma unroll
-    for (int k = 0; k < H::KD; k++) b[k] = fmaf(__ldg(&a.Pd[(((size_t)s * H::KD + k) * H::MD + r) * N + i]), d, b[k]);
+    for (int k = 0; k < H::KD; k++) {
+      const float p = __ldg(&a.Pd[(((size_t)s * H::KD + k) * H::MD + r) * N + i]);
+#pragma unroll
+      for (int v = 0; v < 5; v++) b[k][v] = fmaf(p, d[v], b[k][v]);
+    }
   }
 }
 
+// One thread per cell, all five variables: every per-cell array load ([row][N]
+// layouts) is one coalesced 128-byte warp access and feeds five FMAs.  The
+// central coefficients accumulate in registers, a share of the modes per pass over
+// the stencil, and are kept in shared memory ([K][5][kHoCells]) for the
+// indicators and the combination.  Per variable the arithmetic is that of the
+// thread-per-(cell, variable) form, in the same order.
+constexpr int kHoCells = 64;
+template <int ORDER>
+constexpr size_t recon_ho_mx_smem() { return (size_t)HO<ORDER>::K * 5 * kHoCells * 4; }
+
 template <int ORDER, bool WENO>
-__global__ void __launch_bounds__(128) k_recon_ho_mx(ReconArgsHOMx a) {
+__global__ void __launch_bounds__(kHoCells, ORDER == 4 ? 6 : 8) k_recon_ho_mx(ReconArgsHOMx a) {
   using H = HO<ORDER>;
   constexpr int K = H::K, MC = H::MC, KD = H::KD, ND = 6;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = tid / 5, v = tid - 5 * (tid / 5);
-  if (i >= a.N) return;
+  constexpr int KC = ORDER == 4 ? 12 : (K + 1) / 2;  // modes per pass (P3: 2 passes, P4: 3)
+  extern __shared__ float s_ao[];
+  const int c = threadIdx.x, i0 = blockIdx.x * kHoCells + c;
+  const bool live = i0 < a.N;
+  const int i = live ? i0 : a.N - 1;  // a lane past the end repeats the last cell and writes nothing
   const size_t N = a.N;
-  const float2 pi = __ldg(reinterpret_cast<const float2*>(a.Uhl + (size_t)i * 10 + 2 * v));
-  const float hi_i = pi.x, lo_i = pi.y;
-  float ao[K];
+  auto sa = [&](int k, int v) -> float& { return s_ao[(k * 5 + v) * kHoCells + c]; };
+  float hi_i[5], lo_i[5];
+  {
+    const float2* p = reinterpret_cast<const float2*>(a.Uhl + (size_t)i * 10);
 #pragma unroll
-  for (int k = 0; k < K; k++) ao[k] = 0.f;
+    for (int v = 0; v < 5; v++) {
+      const float2 q = __ldg(p + v);
+      hi_i[v] = q.x;
+      lo_i[v] = q.y;
+    }
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    float acc[KC][5];
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++)
+#pragma unroll
+      for (int v = 0; v < 5; v++) acc[kk][v] = 0.f;
 #pragma unroll 2
-  for (int m = 0; m < MC; m++) {
-    const int j = __ldg(&a.sc[(size_t)m * N + i]);
-    const float d = pair_diff_ho(a.Uhl, j, v, hi_i, lo_i);
+    for (int m = 0; m < MC; m++) {
+      float d[5];
+      pair_diff5(a.Uhl, __ldg(&a.sc[(size_t)m * N + i]), hi_i, lo_i, d);
 #pragma unroll
-    for (int k = 0; k < K; k++) ao[k] = fmaf(__ldg(&a.Pc[((size_t)k * MC + m) * N + i]), d, ao[k]);
+      for (int kk = 0; kk < KC; kk++) {
+        if (k0 + kk < K) {
+          const float p = __ldg(&a.Pc[((size_t)(k0 + kk) * MC + m) * N + i]);
+#pragma unroll
+          for (int v = 0; v < 5; v++) acc[kk][v] = fmaf(p, d[v], acc[kk][v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < KC; kk++)
+      if (k0 + kk < K)
+#pragma unroll
+        for (int v = 0; v < 5; v++) sa(k0 + kk, v) = acc[kk][v];
   }
-  float c[K];
-  if constexpr (!WENO) {
-#pragma unroll
-    for (int k = 0; k < K; k++) c[k] = ao[k];
-  } else {
-    const float SI0 = si_form_f<K, K>(a.Msi, N, i, ao);
-    float SI[ND];
-    float tau = 0.f;
+  if constexpr (WENO) {
+    float SI0[5], SI[ND][5], tau[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    si_form5<K, K>(a.Msi, N, i, [&](int l, int v) { return sa(l, v); }, SI0);
 #pragma unroll 1
     for (int s = 0; s < ND; s++) {
-      float b[KD];
-      dir_coeffs_mx<ORDER>(a, v, hi_i, lo_i, i, s, b);
-      SI[s] = si_form_f<K, KD>(a.Msi, N, i, b);
-      tau += fabsf(SI0 - SI[s]);
-    }
-    tau *= (1.f / ND);
-    const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
-    float ws[ND];
-    float wsum = w0;
+      float b[KD][5];
+      dir_coeffs5<ORDER>(a, hi_i, lo_i, i, s, b);
+      float si[5];
+      si_form5<K, KD>(a.Msi, N, i, [&](int l, int v) { return b[l][v]; }, si);
 #pragma unroll
-    for (int s = 0; s < ND; s++) {
-      ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
-      wsum += ws[s];
+      for (int v = 0; v < 5; v++) {
+        SI[s][v] = si[v];
+        tau[v] += fabsf(SI0[v] - si[v]);
+      }
     }
-    const float iws = fdiv(1.f, wsum);
-    const float r0 = fdiv(w0 * iws, a.lam0);
+    float r0[5], e[ND][5];
 #pragma unroll
-    for (int k = 0; k < K; k++) c[k] = r0 * ao[k];
+    for (int v = 0; v < 5; v++) {
+      const float tv = tau[v] * (1.f / ND);
+      const float w0 = a.lam0 * (1.f + fdiv(tv, a.eps + SI0[v]));
+      float ws[ND];
+      float wsum = w0;
+#pragma unroll
+      for (int s = 0; s < ND; s++) {
+        ws[s] = a.lams * (1.f + fdiv(tv, a.eps + SI[s][v]));
+        wsum += ws[s];
+      }
+      const float iws = fdiv(1.f, wsum);
+      r0[v] = fdiv(w0 * iws, a.lam0);
+#pragma unroll
+      for (int s = 0; s < ND; s++) e[s][v] = ws[s] * iws - r0[v] * a.lams;
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+      for (int v = 0; v < 5; v++) sa(k, v) = r0[v] * sa(k, v);
 #pragma unroll 1
     for (int s = 0; s < ND; s++) {
-      float b[KD];
-      dir_coeffs_mx<ORDER>(a, v, hi_i, lo_i, i, s, b);
-      const float e = ws[s] * iws - r0 * a.lams;
+      float b[KD][5];
+      dir_coeffs5<ORDER>(a, hi_i, lo_i, i, s, b);
 #pragma unroll
-      for (int k = 0; k < KD; k++) c[k] = fmaf(e, b[k], c[k]);
+      for (int k = 0; k < KD; k++)
+#pragma unroll
+        for (int v = 0; v < 5; v++) sa(k, v) = fmaf(e[s][v], b[k][v], sa(k, v));
     }
   }
+  if (!live) return;
   // the constant term relative to U_ref = (1, 0, 0, 0, E_ref), less the means of
   // the non-linear monomials; coefficients in physical units
-  float c0 = v == 0 ? (hi_i - 1.f) + lo_i : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
+  float c0[5] = {(hi_i[0] - 1.f) + lo_i[0], hi_i[1] + lo_i[1], hi_i[2] + lo_i[2], hi_i[3] + lo_i[3],
+                 (hi_i[4] - a.eref_hi) + (lo_i[4] - a.eref_lo)};
 #pragma unroll
-  for (int k = 3; k < K; k++) c0 = fmaf(-c[k], __ldg(&a.psib[(size_t)(k - 3) * N + i]), c0);
+  for (int k = 3; k < K; k++) {
+    const float pb = __ldg(&a.psib[(size_t)(k - 3) * N + i]);
+#pragma unroll
+    for (int v = 0; v < 5; v++) c0[v] = fmaf(-sa(k, v), pb, c0[v]);
+  }
   const float ih = __ldg(&a.inv_h[i]);
   float ihp[ORDER + 1];
   ihp[0] = 1.f;
 #pragma unroll
   for (int e = 1; e <= ORDER; e++) ihp[e] = ihp[e - 1] * ih;
-  float* out = a.coef + (size_t)i * 5 + v;
+  float* out = a.coef + (size_t)i * 5;
   const size_t st = N * 5;
-  out[0] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * st] = c[k] * ihp[basis_degree(k)];
+  for (int v = 0; v < 5; v++) out[v] = c0[v];
+#pragma unroll
+  for (int k = 0; k < K; k++)
+#pragma unroll
+    for (int v = 0; v < 5; v++) out[(k + 1) * st + v] = sa(k, v) * ihp[basis_degree(k)];
 }
 
 template <int ORDER, bool ACC>

@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(kHoCells, ORDER == 4 ? 6 : 8) k_recon_ho_mx(Re
   using H = HO<ORDER>;
   constexpr int K = H::K, MC = H::MC, KD = H::KD, ND = 6;
   constexpr int KC = ORDER == 4 ? 12 : (K + 1) / 2;  // modes per pass (P3: 2 passes, P4: 3)
+  constexpr int U = ORDER == 4 ? 4 : 2;               // stencil members in flight (measured best)
   extern __shared__ float s_ao[];
   const int c = threadIdx.x, i0 = blockIdx.x * kHoCells + c;
   const bool live = i0 < a.N;
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kHoCells, ORDER == 4 ? 6 : 8) k_recon_ho_mx(Re
     for (int kk = 0; kk < KC; kk++)
 #pragma unroll
       for (int v = 0; v < 5; v++) acc[kk][v] = 0.f;
-#pragma unroll 2
+#pragma unroll U
     for (int m = 0; m < MC; m++) {
       float d[5];
       pair_diff5(a.Uhl, __ldg(&a.sc[(size_t)m * N + i]), hi_i, lo_i, d);

@@ -48,6 +48,24 @@ def test_mixed_residual_error_vs_oracle(tets, mach, order, scheme, n):
     assert np.all(tot <= 1e-12 * (S * vol).sum(axis=1)), tot
 
 
+@pytest.mark.parametrize("order,n", [(2, 4), (2, 5), (2, 8), (1, 8), (1, 9)])
+def test_mixed_face_batches(order, n):
+    """The face kernel takes faces in batches (128 at P2, 512 at P1, 3 n^3 faces
+    on the periodic lattice): one full batch and a part (P2, n = 4), a ragged
+    last batch (P2 n = 5: 375 = 2 x 128 + 119; P1 n = 9), an exact multiple
+    (n = 8: 1536 faces); each batch's distinct cells are copied once."""
+    nodes, cells, box = I.hex_lattice(n, jitter=0.1, seed=7)
+    m = _mesh(nodes, cells, box, 1, Mach=0.3, order=order, scheme=1 if order == 2 else 0)
+    oc = O.Case(nodes, cells, box, O.Params(Mach=0.3, order=order, scheme=1 if order == 2 else 0))
+    U = I.noisy_state(nodes, cells, 0.3, 0.05, seed=8)
+    Ug = torch.from_numpy(np.ascontiguousarray(m.to_internal(U))).cuda()
+    R = m.to_user(m.residual(Ug).cpu().numpy())
+    Rc, S = oc.residual_terms(U)
+    err = np.abs(R - Rc).max(axis=1) / S.max(axis=1)
+    print("faces", 3 * n ** 3, "mixed residual error / S:", err)
+    assert np.all(err <= 2e-5), err
+
+
 @pytest.mark.parametrize("order,steps", [(2, 100), (3, 40), (4, 20)])
 def test_mixed_ke_and_dissipation_history_vs_fp64(order, steps):
     """16^3 jittered hexahedra, P2 (P3, P4) CWENOZ, TGV Mach 0.1: SSP-RK3 steps

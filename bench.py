@@ -419,7 +419,7 @@ def roofline(m, prof: dict, form: str, peaks: dict, workload_key: str, frac_dir:
                 "peak_source": alu_src}
     else:
         roof = {"bound": "hbm", "achieved": bw, "peak": peaks["hbm"], "unit": "GB/s", "frac": hbm_frac,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs, burst copy (of measured)"}
+                "peak_source": peaks["hbm_source"]}
     roof.update({"kernel": name, "traffic": measured_traffic(name, f"{workload_key}/{form}"),
                  "avg_launch_ms": avg_s * 1e3, "algorithmic_flops_per_launch": a["flops"],
                  "algorithmic_bytes_per_launch": a["alg"], "layout_bytes_per_launch": a["layout"],
@@ -447,12 +447,13 @@ def job_throughput(t_local: float, cells_per_rank: int, steps: int, world: int, 
     return t, world * cells_per_rank * STAGES * steps / t
 
 
-def hbm_peak() -> float:
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth, else the recipe's fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs, burst copy (of measured)"
     except (OSError, ValueError, KeyError):
-        return 6800.0
+        return 6800.0, "6.8 TB/s, an earlier GB300 measurement (of fallback: MEASURED_PEAKS.json absent)"
 
 
 def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
@@ -601,7 +602,8 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
     fp32, sms = ucns.alu_peak(0)
     fp32x2, _ = ucns.alu_peak(2)
     fp64, _ = ucns.alu_peak(1)
-    peaks = {"hbm": hbm_peak(), "fp32": max(fp32, fp32x2) / 1e12, "fp64": fp64 / 1e12}
+    hbm, hbm_src = hbm_peak()
+    peaks = {"hbm": hbm, "hbm_source": hbm_src, "fp32": max(fp32, fp32x2) / 1e12, "fp64": fp64 / 1e12}
 
     def shares(prof):
         # the time step runs on a side stream, overlapped with the first stage's kernels: its event
@@ -652,7 +654,7 @@ def run_ucns(args, cfg: Config, n: int, rank: int, world: int, local_rank: int):
             "roofline": roofline(m64, res["fp64"]["prof"], "fp64", peaks, cfg.key, 1.0)},
         "peaks": {"hbm_gbs": peaks["hbm"], "fp32_tflops": peaks["fp32"], "fp32_scalar_tflops": fp32 / 1e12,
                   "fp32_packed_tflops": fp32x2 / 1e12, "fp64_tflops": peaks["fp64"], "sm_count": sms,
-                  "source": "HBM: MEASURED_PEAKS.json; FP32/FP64: FMA microbenchmarks of this run"},
+                  "source": "HBM: " + hbm_src + "; FP32/FP64: FMA microbenchmarks of this run"},
         "setup_s": setup_s,
         "kernel_source_hash": kernel_source_hash(),
     }

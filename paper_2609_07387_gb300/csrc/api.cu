@@ -163,17 +163,26 @@ int launch_recon_tiles(const ReconArgsMx& a, cudaStream_t s) {
 }
 
 // P3 / P4, mixed form
+template <int ORDER, bool WENO>
+int launch_recon_ho_tiles(const ReconArgsHOMx& a, cudaStream_t s) {
+  using T = HOTile<ORDER>;
+  constexpr size_t sm = T::smem();
+  UCNS_CUDA(cudaFuncSetAttribute(k_recon_ho_mx<ORDER, WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const unsigned g = (unsigned)((a.N + T::TC - 1) / T::TC);
+  k_recon_ho_mx<ORDER, WENO><<<g, T::THREADS, sm, s>>>(a);
+  UCNS_CUDA(cudaGetLastError());
+  return UCNS_OK;
+}
+
 int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
   ReconArgsHOMx a;
   a.Uhl = m->d.Uhl;
-  a.sc = m->d.sc;
-  a.Pc = m->d.Pcf;
-  a.sd = m->d.sd;
-  a.Pd = m->d.Pdf;
+  a.tiles = m->d.hot;
   a.Msi = m->d.Msif;
   a.psib = m->d.psibf;
   a.inv_h = m->d.inv_hf;
   a.coef = m->d.coeff;
+  a.err = m->d.err;
   a.N = (int)m->N;
   const double lsum = m->P.lambda_central + m->nd;
   a.lam0 = (float)(m->P.lambda_central / lsum);
@@ -182,19 +191,52 @@ int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
   const double eref = 1.0 / (m->P.gamma * m->P.mach * m->P.mach) / (m->P.gamma - 1.0);
   a.eref_hi = (float)eref;
   a.eref_lo = (float)(eref - (double)a.eref_hi);
-  const unsigned g = (unsigned)((m->N + kHoCells - 1) / kHoCells);
   const bool weno = m->nd > 0;
-  if (m->K == 19) {
-    constexpr size_t sm = recon_ho_mx_smem<3>();
-    if (weno) k_recon_ho_mx<3, true><<<g, kHoCells, sm, s>>>(a);
-    else k_recon_ho_mx<3, false><<<g, kHoCells, sm, s>>>(a);
-  } else {
-    constexpr size_t sm = recon_ho_mx_smem<4>();
-    if (weno) k_recon_ho_mx<4, true><<<g, kHoCells, sm, s>>>(a);
-    else k_recon_ho_mx<4, false><<<g, kHoCells, sm, s>>>(a);
+  if (m->K == 19) return weno ? launch_recon_ho_tiles<3, true>(a, s) : launch_recon_ho_tiles<3, false>(a, s);
+  return weno ? launch_recon_ho_tiles<4, true>(a, s) : launch_recon_ho_tiles<4, false>(a, s);
+}
+
+// the P3/P4 mixed reconstruction's tiles (HOTile): stencil ids and FP32
+// pseudo-inverse entries chunk by chunk, zero past N
+template <int ORDER>
+int upload_ho_tiles(const ucns_mesh* m, const HostArrays& h, bool weno, float** dst) {
+  using T = HOTile<ORDER>;
+  constexpr int TC = T::TC, K = T::K, MC = T::MC, KD = T::KD, MD = T::MD;
+  const int64_t N = m->N, tiles = (N + TC - 1) / TC;
+  const int TF = T::tile_floats(weno);
+  std::vector<float> b((size_t)tiles * TF, 0.f);
+  auto put_id = [](float* at, int32_t id) { std::memcpy(at, &id, 4); };
+#pragma omp parallel for schedule(static)
+  for (int64_t t = 0; t < tiles; t++) {
+    float* base = b.data() + (size_t)t * TF;
+    for (int c = 0; c < TC; c++) {
+      const int64_t i = t * TC + c;
+      if (i >= N) break;
+      for (int ch = 0; ch < T::NCC; ch++) {
+        float* chunk = base + (size_t)ch * T::CCS;
+        for (int mm = 0; mm < T::MCH; mm++) {
+          const int mg = ch * T::MCH + mm;
+          put_id(chunk + mm * TC + c, h.sc[(size_t)mg * N + i]);
+          for (int k = 0; k < K; k++)
+            chunk[T::MCH * TC + ((k * (T::MCH / 2) + mm / 2) * TC + c) * 2 + (mm & 1)] =
+                (float)h.Pc[((size_t)k * MC + mg) * N + i];
+        }
+      }
+      if (!weno) continue;
+      for (int sd = 0; sd < 6; sd++)
+        for (int hh = 0; hh < T::NDC; hh++) {
+          float* chunk = base + T::CENTRAL + (size_t)(sd * T::NDC + hh) * T::DCS;
+          for (int rr = 0; rr < T::MDH; rr++) {
+            const int r = hh * T::MDH + rr;
+            put_id(chunk + rr * TC + c, h.sd[((size_t)sd * MD + r) * N + i]);
+            for (int k = 0; k < KD; k++)
+              chunk[T::MDH * TC + ((k * (T::MDH / 2) + rr / 2) * TC + c) * 2 + (rr & 1)] =
+                  (float)h.Pd[(((size_t)sd * KD + k) * MD + r) * N + i];
+          }
+        }
+    }
   }
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
+  return upload(dst, b);
 }
 
 int launch_face_ho_mx(ucns_mesh* m, cudaStream_t s) {
@@ -840,7 +882,7 @@ void device_free(ucns_mesh* m) {
   m->gate_eval_active = false;
   m->gate_fixed = false;
   DeviceMesh& d = m->d;
-  void* ptrs[] = {d.fslot, d.bcell, d.bcount, d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.Pcf, d.Pdf, d.Msif, d.psibf, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
+  void* ptrs[] = {d.fslot, d.bcell, d.bcount, d.inv_vol, d.vol, d.inv_h, d.dtlen, d.mom, d.sc, d.Pc, d.sd, d.Pd, d.Msi, d.psib, d.hot, d.Msif, d.psibf, d.Pcb, d.Pdb, d.scb, d.sdb, d.cellb, d.sda, d.Pda,
                   d.inv_hf, d.fpenf, d.cf, d.fo, d.fn, d.dvalid, d.fq, d.fqf, d.fpen, d.coef, d.coeff, d.Uhl, d.G,
                   d.Ustage, d.Uacc, d.Uhost, d.red, d.dt, d.err, d.dt_part, d.dt_count};
   for (void* p : ptrs)
@@ -1041,7 +1083,9 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     return rc;
   }
   if (p->precision == UCNS_PREC_MIXED && m->K > 9) {
-    if ((rc = upload_f32(&d.Pcf, h.Pc)) || (rc = upload_f32(&d.Pdf, h.Pd)) || (rc = upload_f32(&d.Msif, h.Msi)) ||
+    const bool weno = m->nd > 0;
+    rc = m->K == 19 ? upload_ho_tiles<3>(m, h, weno, &d.hot) : upload_ho_tiles<4>(m, h, weno, &d.hot);
+    if (rc || (rc = upload_f32(&d.Msif, h.Msi)) ||
         (rc = upload_f32(&d.psibf, h.psib)) || (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
         (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {

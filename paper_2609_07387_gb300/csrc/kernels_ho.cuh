@@ -14,7 +14,10 @@
 //               the monomial-form polynomials, HLLC, penalised viscous flux
 //               (Eq. 7), and the face total summed by the group's first lane
 //               over its lanes in point order (deterministic).
-//   k_recon_ho_mx / k_face_ho_mx  the same in the mixed form.
+//   k_recon_ho_mx the same in the mixed form, tile by tile (64 cells): the
+//               stencil ids and FP32 pseudo-inverses stream through shared
+//               memory in bulk-copied chunks, thread = (cell, variable).
+//   k_face_ho_mx  k_face_ho in the mixed form.
 #pragma once
 
 #include "basis.hpp"
@@ -273,206 +276,228 @@ __global__ void __launch_bounds__(128) k_face_ho(FaceArgs a) {
 // face totals (k_rk<s, nfc, float> sums them as float pairs into FP64).
 struct ReconArgsHOMx {
   const float* __restrict__ Uhl;    // [N][5][2] float pairs (hi, lo) of the state
-  const int32_t* __restrict__ sc;   // [MC][N]
-  const float* __restrict__ Pc;     // [K][MC][N]
-  const int32_t* __restrict__ sd;   // [6][MD][N]
-  const float* __restrict__ Pd;     // [6][KD][MD][N]
+  const float* __restrict__ tiles;  // per 64-cell tile its stencil chunks (HOTile)
   const float* __restrict__ Msi;    // [K(K+1)/2][N]
   const float* __restrict__ psib;   // [K-3][N]
   const float* __restrict__ inv_h;  // [N]
   float* __restrict__ coef;         // [K+1][N][5]: entry 0 relative to U_ref, then physical-unit coefficients
+  int* err;                         // bit 1: a copy wait gave up
   int N;
   float lam0, lams, eps;
   float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair
 };
 
-// a^T M a of each of the five variables over the first KK modes (M as in
-// si_form; at(l, v) = a_l of variable v); per variable the same operations in
-// the same order as si_form in FP32
-template <int K, int KK, class A>
-__device__ __forceinline__ void si_form5(const float* __restrict__ M, size_t N, int i, A at, float s[5]) {
-#pragma unroll
-  for (int v = 0; v < 5; v++) s[v] = 0.f;
+// The P3/P4 mixed reconstruction's data, tile by tile (64 cells): the central
+// stencil in NCC chunks of MCH members, then each of the six directional
+// stencils in NDC chunks of MDH members.  A chunk is [members][64] stencil ids
+// (int32) followed by its pseudo-inverse entries as pairs of consecutive
+// members, [modes][members / 2][64][2]; every chunk is one bulk copy.  Cells
+// past N in the last tile have ids 0 and zero entries.
+template <int ORDER>
+struct HOTile {
+  using H = HO<ORDER>;
+  static constexpr int K = H::K, MC = H::MC, KD = H::KD, MD = H::MD;
+  static constexpr int TC = 64;
+  static constexpr int MCH = ORDER == 4 ? 4 : 2, MDH = 6;
+  static constexpr int NCC = MC / MCH, NDC = MD / MDH;
+  static constexpr int CCS = MCH * TC + K * MCH * TC;  // floats per central chunk
+  static constexpr int DCS = MDH * TC + KD * MDH * TC;  // floats per directional chunk
+  static constexpr int CENTRAL = NCC * CCS;
+  UCNS_HD static constexpr int tile_floats(bool weno) { return CENTRAL + (weno ? 6 * NDC * DCS : 0); }
+  static constexpr int STAGE = CCS > DCS ? CCS : DCS;
+  static constexpr int S = ORDER == 4 ? 3 : 4;  // stages of the copy ring (6 at P4 measured slower)
+  static constexpr int THREADS = 5 * TC + 32;   // (cell, variable) threads and one copying warp
+  static constexpr size_t smem() { return (size_t)S * STAGE * 4 + (size_t)2 * S * 8; }
+  static_assert(MC % MCH == 0 && MD % MDH == 0 && MCH % 2 == 0 && MDH % 2 == 0, "whole member pairs");
+  static_assert(CCS % 4 == 0 && DCS % 4 == 0, "16-byte chunks");
+};
+
+// a^T M a over the first KK modes of one variable (M as in si_form), FP32
+template <int K, int KK>
+__device__ __forceinline__ float si_form_f(const float* __restrict__ M, size_t N, int i, const float (&a)[KK]) {
+  float s = 0.f;
 #pragma unroll
   for (int k = 0; k < KK; k++) {
-    float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float t = 0.f;
 #pragma unroll
-    for (int l = k + 1; l < KK; l++) {
-      const float m = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]);
-#pragma unroll
-      for (int v = 0; v < 5; v++) t[v] = fmaf(m, at(l, v), t[v]);
-    }
+    for (int l = k + 1; l < KK; l++) t = fmaf(__ldg(&M[(size_t)(k * K - k * (k - 1) / 2 + l - k) * N + i]), a[l], t);
     const float mkk = __ldg(&M[(size_t)(k * K - k * (k - 1) / 2) * N + i]);
+    s = fmaf(a[k], fmaf(2.f, t, mkk * a[k]), s);
+  }
+  return s;
+}
+
+// U_j - U_i of variable v from the float pairs (the leading parts subtract exactly)
+__device__ __forceinline__ float pair_diff_ho(const float* __restrict__ hl, int j, int v, float hi_i, float lo_i) {
+  const float2 p = __ldg(reinterpret_cast<const float2*>(hl + (size_t)j * 10 + 2 * v));
+  return (p.x - hi_i) + (p.y - lo_i);
+}
+
+// one chunk's contraction into acc[0 .. KK): members in pairs, in order
+template <int KK, int MM>
+__device__ __forceinline__ void chunk_contract(const float* chunk, int c, const float* __restrict__ hl, int v,
+                                               float hi_i, float lo_i, float (&acc)[KK]) {
+  constexpr int TC = 64;
+  const float2* P = reinterpret_cast<const float2*>(chunk + MM * TC);
 #pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float ak = at(k, v);
-      s[v] = fmaf(ak, fmaf(2.f, t[v], mkk * ak), s[v]);
+  for (int mp = 0; mp < MM / 2; mp++) {
+    const int j0 = reinterpret_cast<const int*>(chunk)[(2 * mp) * TC + c];
+    const int j1 = reinterpret_cast<const int*>(chunk)[(2 * mp + 1) * TC + c];
+    const float d0 = pair_diff_ho(hl, j0, v, hi_i, lo_i), d1 = pair_diff_ho(hl, j1, v, hi_i, lo_i);
+#pragma unroll
+    for (int k = 0; k < KK; k++) {
+      const float2 p = P[(k * (MM / 2) + mp) * TC + c];
+      acc[k] = fmaf(p.y, d1, fmaf(p.x, d0, acc[k]));
     }
   }
 }
 
-// U_j - U_i of the five variables from the float pairs (the leading parts subtract exactly)
-__device__ __forceinline__ void pair_diff5(const float* __restrict__ hl, int j, const float hi_i[5],
-                                           const float lo_i[5], float d[5]) {
-  const float2* p = reinterpret_cast<const float2*>(hl + (size_t)j * 10);
-#pragma unroll
-  for (int v = 0; v < 5; v++) {
-    const float2 q = __ldg(p + v);
-    d[v] = (q.x - hi_i[v]) + (q.y - lo_i[v]);
-  }
-}
-
-// directional candidate s of the five variables: b[k][v] = sum_r Pd[s][k][r] (U_r - U_i)_v
-template <int ORDER>
-__device__ __forceinline__ void dir_coeffs5(const ReconArgsHOMx& a, const float hi_i[5], const float lo_i[5], int i,
-                                            int s, float (&b)[HO<ORDER>::KD][5]) {
-  using H = HO<ORDER>;
-  const size_t N = a.N;
-#pragma unroll
-  for (int k = 0; k < H::KD; k++)
-#pragma unroll
-    for (int v = 0; v < 5; v++) b[k][v] = 0.f;
-#pragma unroll 2
-  for (int r = 0; r < H::MD; r++) {
-    float d[5];
-    pair_diff5(a.Uhl, __ldg(&a.sd[((size_t)s * H::MD + r) * N + i]), hi_i, lo_i, d);
-#pragma unroll
-    for (int k = 0; k < H::KD; k++) {
-      const float p = __ldg(&a.Pd[(((size_t)s * H::KD + k) * H::MD + r) * N + i]);
-#pragma unroll
-      for (int v = 0; v < 5; v++) b[k][v] = fmaf(p, d[v], b[k][v]);
-    }
-  }
-}
-
-// One thread per cell, all five variables: every per-cell array load ([row][N]
-// layouts) is one coalesced 128-byte warp access and feeds five FMAs.  The
-// central coefficients accumulate in registers, a share of the modes per pass over
-// the stencil, and are kept in shared memory ([K][5][kHoCells]) for the
-// indicators and the combination.  Per variable the arithmetic is that of the
-// thread-per-(cell, variable) form, in the same order.
-constexpr int kHoCells = 64;
-template <int ORDER>
-constexpr size_t recon_ho_mx_smem() { return (size_t)HO<ORDER>::K * 5 * kHoCells * 4; }
-
+// One block per 64-cell tile: thread (cell c, variable v) = 5 c + v, plus a
+// copying warp that streams the tile's chunks (central; with CWENOZ the
+// directional ones twice, once for the indicators and once for the
+// combination) through a ring of S shared-memory stages, every wait bounded.
+// Per variable the arithmetic is that of the FP64 form in FP32, members and
+// modes in the same order.  Blocks per SM: P3 three, P4 two (linear) or one
+// (CWENOZ: its smoothness forms need 168 registers a thread without spills).
 template <int ORDER, bool WENO>
-__global__ void __launch_bounds__(kHoCells, ORDER == 4 ? 6 : 8) k_recon_ho_mx(ReconArgsHOMx a) {
-  using H = HO<ORDER>;
-  constexpr int K = H::K, MC = H::MC, KD = H::KD, ND = 6;
-  constexpr int KC = ORDER == 4 ? 12 : (K + 1) / 2;  // modes per pass (P3: 2 passes, P4: 3)
-  constexpr int U = ORDER == 4 ? 4 : 2;               // stencil members in flight (measured best)
-  extern __shared__ float s_ao[];
-  const int c = threadIdx.x, i0 = blockIdx.x * kHoCells + c;
+__global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1 : 2) : 3) k_recon_ho_mx(ReconArgsHOMx a) {
+  using T = HOTile<ORDER>;
+  constexpr int K = T::K, KD = T::KD, ND = 6, TC = T::TC, S = T::S;
+  constexpr int NQ = T::NCC + (WENO ? 2 * ND * T::NDC : 0);  // chunks streamed per tile
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* st = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(st + S * T::STAGE);
+  uint64_t* empty = full + S;
+  const int t = threadIdx.x, lane = t & 31, tile = blockIdx.x;
+  if (t < S) {
+    bar_init(&full[t]);
+    bar_init(&empty[t], 5 * TC / 32);
+  }
+  __syncthreads();
+  if (t >= 5 * TC) {  // the copying warp
+    if (lane != 0) return;
+    const float* base = a.tiles + (size_t)tile * T::tile_floats(WENO);
+    int q = 0;
+    bool ok = true;
+    for (; q < NQ; q++) {
+      if (q >= S && !bar_wait(&empty[q % S], (uint32_t)(q / S + 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      // chunk q: central chunks first, then the directional ones in two rounds
+      const int qd = q - T::NCC;
+      const float* src = q < T::NCC ? base + (size_t)q * T::CCS : base + T::CENTRAL + (size_t)(qd % (ND * T::NDC)) * T::DCS;
+      const uint32_t bytes = (q < T::NCC ? T::CCS : T::DCS) * 4u;
+      bar_expect(&full[q % S], bytes);
+      bulk_load(st + (q % S) * T::STAGE, src, bytes, &full[q % S]);
+    }
+    if (!ok) atomicOr(a.err, 2);
+    // the last copies into each stage land before the block's shared memory is released
+    for (int qq = q - 1; qq >= 0 && qq >= q - S; qq--) bar_wait(&full[qq % S], (uint32_t)(qq / S) & 1u);
+    return;
+  }
+  const int c = t / 5, v = t - 5 * (t / 5);
+  const int i0 = tile * TC + c;
   const bool live = i0 < a.N;
-  const int i = live ? i0 : a.N - 1;  // a lane past the end repeats the last cell and writes nothing
+  const int i = live ? i0 : a.N - 1;
   const size_t N = a.N;
-  auto sa = [&](int k, int v) -> float& { return s_ao[(k * 5 + v) * kHoCells + c]; };
-  float hi_i[5], lo_i[5];
-  {
-    const float2* p = reinterpret_cast<const float2*>(a.Uhl + (size_t)i * 10);
+  const float* __restrict__ hl = a.Uhl;
+  const float2 pi = __ldg(reinterpret_cast<const float2*>(hl + (size_t)i * 10 + 2 * v));
+  const float hi_i = pi.x, lo_i = pi.y;
+  int q = 0;
+  bool ok = true;
+  auto take = [&]() -> const float* {  // wait for chunk q
+    ok = ok && __all_sync(0xffffffffu, bar_wait(&full[q % S], (uint32_t)(q / S) & 1u));
+    return st + (q % S) * T::STAGE;
+  };
+  auto give = [&]() {  // this warp is done with chunk q
+    __syncwarp();
+    if (lane == 0) bar_arrive(&empty[q % S]);
+    q++;
+  };
+  float ao[K];
 #pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float2 q = __ldg(p + v);
-      hi_i[v] = q.x;
-      lo_i[v] = q.y;
+  for (int k = 0; k < K; k++) ao[k] = 0.f;
+#pragma unroll 1
+  for (int ch = 0; ch < T::NCC; ch++) {
+    const float* chunk = take();
+    if (!ok) break;
+    chunk_contract<K, T::MCH>(chunk, c, hl, v, hi_i, lo_i, ao);
+    give();
+  }
+  float cf[K];
+  if constexpr (!WENO) {
+#pragma unroll
+    for (int k = 0; k < K; k++) cf[k] = ao[k];
+  } else {
+    const float SI0 = si_form_f<K, K>(a.Msi, N, i, ao);
+    float SI[ND];
+    float tau = 0.f;
+#pragma unroll 1
+    for (int s = 0; s < ND && ok; s++) {
+      float b[KD];
+#pragma unroll
+      for (int k = 0; k < KD; k++) b[k] = 0.f;
+#pragma unroll 1
+      for (int h = 0; h < T::NDC; h++) {
+        const float* chunk = take();
+        if (!ok) break;
+        chunk_contract<KD, T::MDH>(chunk, c, hl, v, hi_i, lo_i, b);
+        give();
+      }
+      SI[s] = si_form_f<K, KD>(a.Msi, N, i, b);
+      tau += fabsf(SI0 - SI[s]);
+    }
+    tau *= (1.f / ND);
+    const float w0 = a.lam0 * (1.f + fdiv(tau, a.eps + SI0));
+    float ws[ND];
+    float wsum = w0;
+#pragma unroll
+    for (int s = 0; s < ND; s++) {
+      ws[s] = a.lams * (1.f + fdiv(tau, a.eps + SI[s]));
+      wsum += ws[s];
+    }
+    const float iws = fdiv(1.f, wsum);
+    const float r0 = fdiv(w0 * iws, a.lam0);
+#pragma unroll
+    for (int k = 0; k < K; k++) cf[k] = r0 * ao[k];
+#pragma unroll 1
+    for (int s = 0; s < ND && ok; s++) {
+      float b[KD];
+#pragma unroll
+      for (int k = 0; k < KD; k++) b[k] = 0.f;
+#pragma unroll 1
+      for (int h = 0; h < T::NDC; h++) {
+        const float* chunk = take();
+        if (!ok) break;
+        chunk_contract<KD, T::MDH>(chunk, c, hl, v, hi_i, lo_i, b);
+        give();
+      }
+      const float e = ws[s] * iws - r0 * a.lams;
+#pragma unroll
+      for (int k = 0; k < KD; k++) cf[k] = fmaf(e, b[k], cf[k]);
     }
   }
-#pragma unroll
-  for (int k0 = 0; k0 < K; k0 += KC) {
-    float acc[KC][5];
-#pragma unroll
-    for (int kk = 0; kk < KC; kk++)
-#pragma unroll
-      for (int v = 0; v < 5; v++) acc[kk][v] = 0.f;
-#pragma unroll U
-    for (int m = 0; m < MC; m++) {
-      float d[5];
-      pair_diff5(a.Uhl, __ldg(&a.sc[(size_t)m * N + i]), hi_i, lo_i, d);
-#pragma unroll
-      for (int kk = 0; kk < KC; kk++) {
-        if (k0 + kk < K) {
-          const float p = __ldg(&a.Pc[((size_t)(k0 + kk) * MC + m) * N + i]);
-#pragma unroll
-          for (int v = 0; v < 5; v++) acc[kk][v] = fmaf(p, d[v], acc[kk][v]);
-        }
-      }
-    }
-#pragma unroll
-    for (int kk = 0; kk < KC; kk++)
-      if (k0 + kk < K)
-#pragma unroll
-        for (int v = 0; v < 5; v++) sa(k0 + kk, v) = acc[kk][v];
-  }
-  if constexpr (WENO) {
-    float SI0[5], SI[ND][5], tau[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    si_form5<K, K>(a.Msi, N, i, [&](int l, int v) { return sa(l, v); }, SI0);
-#pragma unroll 1
-    for (int s = 0; s < ND; s++) {
-      float b[KD][5];
-      dir_coeffs5<ORDER>(a, hi_i, lo_i, i, s, b);
-      float si[5];
-      si_form5<K, KD>(a.Msi, N, i, [&](int l, int v) { return b[l][v]; }, si);
-#pragma unroll
-      for (int v = 0; v < 5; v++) {
-        SI[s][v] = si[v];
-        tau[v] += fabsf(SI0[v] - si[v]);
-      }
-    }
-    float r0[5], e[ND][5];
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float tv = tau[v] * (1.f / ND);
-      const float w0 = a.lam0 * (1.f + fdiv(tv, a.eps + SI0[v]));
-      float ws[ND];
-      float wsum = w0;
-#pragma unroll
-      for (int s = 0; s < ND; s++) {
-        ws[s] = a.lams * (1.f + fdiv(tv, a.eps + SI[s][v]));
-        wsum += ws[s];
-      }
-      const float iws = fdiv(1.f, wsum);
-      r0[v] = fdiv(w0 * iws, a.lam0);
-#pragma unroll
-      for (int s = 0; s < ND; s++) e[s][v] = ws[s] * iws - r0[v] * a.lams;
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++)
-#pragma unroll
-      for (int v = 0; v < 5; v++) sa(k, v) = r0[v] * sa(k, v);
-#pragma unroll 1
-    for (int s = 0; s < ND; s++) {
-      float b[KD][5];
-      dir_coeffs5<ORDER>(a, hi_i, lo_i, i, s, b);
-#pragma unroll
-      for (int k = 0; k < KD; k++)
-#pragma unroll
-        for (int v = 0; v < 5; v++) sa(k, v) = fmaf(e[s][v], b[k][v], sa(k, v));
-    }
+  if (!ok) {
+    if (lane == 0) atomicOr(a.err, 2);
+    return;
   }
   if (!live) return;
   // the constant term relative to U_ref = (1, 0, 0, 0, E_ref), less the means of
   // the non-linear monomials; coefficients in physical units
-  float c0[5] = {(hi_i[0] - 1.f) + lo_i[0], hi_i[1] + lo_i[1], hi_i[2] + lo_i[2], hi_i[3] + lo_i[3],
-                 (hi_i[4] - a.eref_hi) + (lo_i[4] - a.eref_lo)};
+  float c0 = v == 0 ? (hi_i - 1.f) + lo_i : (v == 4 ? (hi_i - a.eref_hi) + (lo_i - a.eref_lo) : hi_i + lo_i);
 #pragma unroll
-  for (int k = 3; k < K; k++) {
-    const float pb = __ldg(&a.psib[(size_t)(k - 3) * N + i]);
-#pragma unroll
-    for (int v = 0; v < 5; v++) c0[v] = fmaf(-sa(k, v), pb, c0[v]);
-  }
+  for (int k = 3; k < K; k++) c0 = fmaf(-cf[k], __ldg(&a.psib[(size_t)(k - 3) * N + i]), c0);
   const float ih = __ldg(&a.inv_h[i]);
   float ihp[ORDER + 1];
   ihp[0] = 1.f;
 #pragma unroll
   for (int e = 1; e <= ORDER; e++) ihp[e] = ihp[e - 1] * ih;
-  float* out = a.coef + (size_t)i * 5;
-  const size_t st = N * 5;
+  float* out = a.coef + (size_t)i * 5 + v;
+  const size_t st5 = N * 5;
+  out[0] = c0;
 #pragma unroll
-  for (int v = 0; v < 5; v++) out[v] = c0[v];
-#pragma unroll
-  for (int k = 0; k < K; k++)
-#pragma unroll
-    for (int v = 0; v < 5; v++) out[(k + 1) * st + v] = sa(k, v) * ihp[basis_degree(k)];
+  for (int k = 0; k < K; k++) out[(k + 1) * st5] = cf[k] * ihp[basis_degree(k)];
 }
 
 template <int ORDER, bool ACC>

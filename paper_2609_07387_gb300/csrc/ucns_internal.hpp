@@ -37,8 +37,7 @@ struct DeviceMesh {
   int32_t* sd = nullptr;      // [nd][Md][N] directional stencils
   double* Pd = nullptr;       // [nd][Kd][Md][N]
   double* Msi = nullptr;      // P3/P4: [K(K+1)/2][N] smoothness-indicator matrix (upper triangle, row-major)
-  float* Pcf = nullptr;       // P3/P4 mixed form: FP32 copies of Pc, Pd, Msi, psib
-  float* Pdf = nullptr;
+  float* hot = nullptr;       // P3/P4 mixed form: stencil ids and FP32 pseudo-inverses in 64-cell tiles; FP32 Msi, psib
   float* Msif = nullptr;
   float* psibf = nullptr;
   double* psib = nullptr;     // P3/P4: [K-3][N] cell means of the non-linear basis monomials (xi units)

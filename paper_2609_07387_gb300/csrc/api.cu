@@ -182,6 +182,7 @@ int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
   a.psib = m->d.psibf;
   a.inv_h = m->d.inv_hf;
   a.coef = m->d.coeff;
+  a.cs = coef_row_floats(m);
   a.err = m->d.err;
   a.N = (int)m->N;
   const double lsum = m->P.lambda_central + m->nd;
@@ -249,6 +250,7 @@ int launch_face_ho_mx(ucns_mesh* m, cudaStream_t s) {
   a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
   a.N = (int)m->N;
   a.F = (int)m->F;
+  a.cs = coef_row_floats(m);
   a.c = flux_const_f(m->P);
   const bool visc = m->P.reynolds > 0.0;
   const int fpw = 32 / m->nq;
@@ -714,9 +716,7 @@ int residual_into(ucns_mesh* m, const double* U, double* R, cudaStream_t s) {
 // Diagnostic sums [V KE, V |curl u|^2, V (div u)^2, V] of the coefficients
 // the last reconstruction left, into out[0..3] (device)
 int diag_sums_into(ucns_mesh* m, const double* U, double* out, cudaStream_t s) {
-  if (mixed(m) && m->K > 9)
-    k_diag_partial<float><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, (int)m->N, m->d.red);
-  else if (mixed(m))
+  if (mixed(m))
     k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC, m->d.vol,
                                                              (int)m->N, m->d.red);
   else
@@ -1088,7 +1088,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     if (rc || (rc = upload_f32(&d.Msif, h.Msi)) ||
         (rc = upload_f32(&d.psibf, h.psib)) || (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
         (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
-        (rc = alloc(&d.coeff, (size_t)m->NC * m->N * 5)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
+        (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);
       return rc;
     }
@@ -1295,9 +1295,7 @@ int ucns_diagnostics(ucns_mesh* m, const double* U, ucns_diag* out, void* stream
   m->gate_eval_active = false;  // diagnostics always use the full scheme
   if ((rc = launch_split(m, U, s)) || (rc = launch_recon(m, U, s))) return rc;
   rc = timed(m, kKindDiag, s, [&] {
-    if (mixed(m) && m->K > 9)
-      k_diag_partial<float><<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, m->d.vol, (int)m->N, m->d.red);
-    else if (mixed(m))
+    if (mixed(m))
       k_diag_partial_mx<<<m->d.red_blocks, kRedThreads, 0, s>>>(U, m->d.coeff, coef_row_floats(m), m->NC,
                                                                  m->d.vol, (int)m->N, m->d.red);
     else

@@ -280,9 +280,10 @@ struct ReconArgsHOMx {
   const float* __restrict__ Msi;    // [K(K+1)/2][N]
   const float* __restrict__ psib;   // [K-3][N]
   const float* __restrict__ inv_h;  // [N]
-  float* __restrict__ coef;         // [K+1][N][5]: entry 0 relative to U_ref, then physical-unit coefficients
+  float* __restrict__ coef;         // [N][cs] rows, entries cidx(v, k, K + 1): k = 0 relative to U_ref,
+                                    // then the physical-unit coefficients
   int* err;                         // bit 1: a copy wait gave up
-  int N;
+  int N, cs;
   float lam0, lams, eps;
   float eref_hi, eref_lo;  // E_ref = p_ref/(gamma-1) as a float pair
 };
@@ -493,19 +494,20 @@ __global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1
   ihp[0] = 1.f;
 #pragma unroll
   for (int e = 1; e <= ORDER; e++) ihp[e] = ihp[e - 1] * ih;
-  float* out = a.coef + (size_t)i * 5 + v;
-  const size_t st5 = N * 5;
-  out[0] = c0;
+  float* out = a.coef + (size_t)i * a.cs;
+  out[cidx(v, 0, K + 1)] = c0;
 #pragma unroll
-  for (int k = 0; k < K; k++) out[(k + 1) * st5] = cf[k] * ihp[basis_degree(k)];
+  for (int k = 0; k < K; k++) out[cidx(v, k + 1, K + 1)] = cf[k] * ihp[basis_degree(k)];
 }
 
+// value and gradient at (x, y, z) of a cell's polynomial from its row
+// (entries cidx(v, k, K + 1)): variables 0-3 in packed FP32x2 pairs from one
+// 16-byte load per mode, variable 4 from four modes per 16-byte load
 template <int ORDER, bool ACC>
-__device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ coef, int N, int cell, float x, float y,
-                                                float z, float U[5], float g[5][3]) {
-  constexpr int K = basis_count(ORDER);
-  const size_t st = (size_t)N * 5;
-  const float* p = coef + (size_t)cell * 5;
+__device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ row, float x, float y, float z, float U[5],
+                                                float g[5][3]) {
+  constexpr int K = basis_count(ORDER), NCF = K + 1;
+  const float4* r4 = reinterpret_cast<const float4*>(row);
   float px[ORDER + 1], py[ORDER + 1], pz[ORDER + 1];
   px[0] = py[0] = pz[0] = 1.f;
 #pragma unroll
@@ -514,30 +516,54 @@ __device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ coef, 
     py[e] = py[e - 1] * y;
     pz[e] = pz[e - 1] * z;
   }
-  float gx[5], gy[5], gz[5];
+  float e4[4 * ((NCF + 3) / 4)];  // variable 4's entries
 #pragma unroll
-  for (int v = 0; v < 5; v++) {
-    U[v] = __ldg(p + v);
-    gx[v] = gy[v] = gz[v] = 0.f;
+  for (int j = 0; j < (NCF + 3) / 4; j++) {
+    const float4 t = __ldg(r4 + NCF + j);
+    e4[4 * j] = t.x;
+    e4[4 * j + 1] = t.y;
+    e4[4 * j + 2] = t.z;
+    e4[4 * j + 3] = t.w;
   }
+  const float4 c0 = __ldg(r4);
+  float2 u01 = make_float2(c0.x, c0.y), u23 = make_float2(c0.z, c0.w);
+  float2 gx01 = make_float2(0.f, 0.f), gx23 = gx01, gy01 = gx01, gy23 = gx01, gz01 = gx01, gz23 = gx01;
+  float u4 = e4[0], gx4 = 0.f, gy4 = 0.f, gz4 = 0.f;
 #pragma unroll
   for (int k = 0; k < K; k++) {
     const int ex = basis_exp(k, 0), ey = basis_exp(k, 1), ez = basis_exp(k, 2);
     const float mv = px[ex] * py[ey] * pz[ez];
-    const float mx = ex ? ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez] : 0.f;
-    const float my = ey ? ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez] : 0.f;
-    const float mz = ez ? ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0] : 0.f;
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float cc = __ldg(p + (k + 1) * st + v);
-      U[v] = fmaf(cc, mv, U[v]);
-      if (ex) gx[v] = fmaf(cc, mx, gx[v]);
-      if (ey) gy[v] = fmaf(cc, my, gy[v]);
-      if (ez) gz[v] = fmaf(cc, mz, gz[v]);
+    const float4 cq = __ldg(r4 + k + 1);
+    const float2 c01 = make_float2(cq.x, cq.y), c23 = make_float2(cq.z, cq.w);
+    const float c4 = e4[k + 1];
+    u01 = __ffma2_rn(c01, make_float2(mv, mv), u01);
+    u23 = __ffma2_rn(c23, make_float2(mv, mv), u23);
+    u4 = fmaf(c4, mv, u4);
+    if (ex) {
+      const float m = ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez];
+      gx01 = __ffma2_rn(c01, make_float2(m, m), gx01);
+      gx23 = __ffma2_rn(c23, make_float2(m, m), gx23);
+      gx4 = fmaf(c4, m, gx4);
+    }
+    if (ey) {
+      const float m = ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez];
+      gy01 = __ffma2_rn(c01, make_float2(m, m), gy01);
+      gy23 = __ffma2_rn(c23, make_float2(m, m), gy23);
+      gy4 = fmaf(c4, m, gy4);
+    }
+    if (ez) {
+      const float m = ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0];
+      gz01 = __ffma2_rn(c01, make_float2(m, m), gz01);
+      gz23 = __ffma2_rn(c23, make_float2(m, m), gz23);
+      gz4 = fmaf(c4, m, gz4);
     }
   }
+  const float u[5] = {u01.x, u01.y, u23.x, u23.y, u4};
+  const float gx[5] = {gx01.x, gx01.y, gx23.x, gx23.y, gx4}, gy[5] = {gy01.x, gy01.y, gy23.x, gy23.y, gy4},
+              gz[5] = {gz01.x, gz01.y, gz23.x, gz23.y, gz4};
 #pragma unroll
   for (int v = 0; v < 5; v++) {
+    U[v] = u[v];
     if (ACC) {
       g[v][0] += gx[v];
       g[v][1] += gy[v];
@@ -551,13 +577,13 @@ __device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ coef, 
 }
 
 struct FaceArgsHOMx {
-  const float* __restrict__ coef;  // [K+1][N][5]
+  const float* __restrict__ coef;  // [N][cs] rows as the reconstruction writes them
   const float* __restrict__ fq;    // [F][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
   const float* __restrict__ fpen;
   const int32_t* __restrict__ fo;
   const int32_t* __restrict__ fn;
   float* __restrict__ G;  // [5][F] FP32 face totals
-  int N, F;
+  int N, F, cs;
   FluxConstF c;
 };
 
@@ -577,8 +603,8 @@ __global__ void __launch_bounds__(128) k_face_ho_mx(FaceArgsHOMx a) {
   const float area = q4.y;
   const int o = a.fo[fc], nb = a.fn[fc];
   float WL[5], WR[5], gs[5][3];
-  eval_side_ho_mx<ORDER, false>(a.coef, a.N, o, q0.x, q0.y, q1.x, WL, gs);
-  eval_side_ho_mx<ORDER, true>(a.coef, a.N, nb, q1.y, q2.x, q2.y, WR, gs);
+  eval_side_ho_mx<ORDER, false>(a.coef + (size_t)o * a.cs, q0.x, q0.y, q1.x, WL, gs);
+  eval_side_ho_mx<ORDER, true>(a.coef + (size_t)nb * a.cs, q1.y, q2.x, q2.y, WR, gs);
   float Fc[5];
   hllc_flux_mx(WL, WR, n, a.c, Fc);
   float flux[5];
@@ -601,15 +627,20 @@ __global__ void __launch_bounds__(128) k_face_ho_mx(FaceArgsHOMx a) {
 #pragma unroll
     for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
   }
-  const int base = (in_group ? grp : 0) * NQ;
-  float tot[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  // the group's sum on its first lane, a fixed tree over the point order
+  // (lanes past the group contribute nothing)
 #pragma unroll
-  for (int t = 0; t < NQ; t++)
+  for (int off = 8; off >= 1; off >>= 1) {
+    if (off >= NQ) continue;
 #pragma unroll
-    for (int v = 0; v < 5; v++) tot[v] += __shfl_sync(0xffffffffu, flux[v], base + t);
+    for (int v = 0; v < 5; v++) {
+      const float o = __shfl_down_sync(0xffffffffu, flux[v], off);
+      if (q + off < NQ) flux[v] += o;
+    }
+  }
   if (live && q == 0) {
 #pragma unroll
-    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = tot[v];
+    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = flux[v];
   }
 }
 

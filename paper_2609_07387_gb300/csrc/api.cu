@@ -197,8 +197,8 @@ int launch_recon_ho_mx(ucns_mesh* m, cudaStream_t s) {
   return weno ? launch_recon_ho_tiles<4, true>(a, s) : launch_recon_ho_tiles<4, false>(a, s);
 }
 
-// the P3/P4 mixed reconstruction's tiles (HOTile): stencil ids and FP32
-// pseudo-inverse entries chunk by chunk, zero past N
+// the P3/P4 mixed reconstruction's tiles (HOTile): stencil ids, FP32
+// pseudo-inverse entries and (CWENOZ) smoothness matrices, zero past N
 template <int ORDER>
 int upload_ho_tiles(const ucns_mesh* m, const HostArrays& h, bool weno, float** dst) {
   using T = HOTile<ORDER>;
@@ -224,9 +224,10 @@ int upload_ho_tiles(const ucns_mesh* m, const HostArrays& h, bool weno, float** 
         }
       }
       if (!weno) continue;
+      for (int q = 0; q < T::NQS; q++) base[T::CENTRAL + (size_t)q * TC + c] = (float)h.Msi[(size_t)q * N + i];
       for (int sd = 0; sd < 6; sd++)
         for (int hh = 0; hh < T::NDC; hh++) {
-          float* chunk = base + T::CENTRAL + (size_t)(sd * T::NDC + hh) * T::DCS;
+          float* chunk = base + T::CENTRAL + T::SMAT + (size_t)(sd * T::NDC + hh) * T::DCS;
           for (int rr = 0; rr < T::MDH; rr++) {
             const int r = hh * T::MDH + rr;
             put_id(chunk + rr * TC + c, h.sd[((size_t)sd * MD + r) * N + i]);

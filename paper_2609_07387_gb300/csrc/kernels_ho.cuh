@@ -304,8 +304,12 @@ struct HOTile {
   static constexpr int CCS = MCH * TC + K * MCH * TC;  // floats per central chunk
   static constexpr int DCS = MDH * TC + KD * MDH * TC;  // floats per directional chunk
   static constexpr int CENTRAL = NCC * CCS;
-  UCNS_HD static constexpr int tile_floats(bool weno) { return CENTRAL + (weno ? 6 * NDC * DCS : 0); }
   static constexpr int STAGE = CCS > DCS ? CCS : DCS;
+  // with CWENOZ the smoothness matrices follow the central chunks: [K(K+1)/2][64]
+  // entries in chunks of MSR rows, then the directional chunks
+  static constexpr int NQS = K * (K + 1) / 2, MSR = STAGE / TC, NMC = (NQS + MSR - 1) / MSR;
+  static constexpr int SMAT = NQS * TC;
+  UCNS_HD static constexpr int tile_floats(bool weno) { return CENTRAL + (weno ? SMAT + 6 * NDC * DCS : 0); }
   static constexpr int S = ORDER == 4 ? 3 : 4;  // stages of the copy ring (6 at P4 measured slower)
   static constexpr int THREADS = 5 * TC + 32;   // (cell, variable) threads and one copying warp
   static constexpr size_t smem() { return (size_t)S * STAGE * 4 + (size_t)2 * S * 8; }
@@ -355,16 +359,18 @@ __device__ __forceinline__ void chunk_contract(const float* chunk, int c, const 
 
 // One block per 64-cell tile: thread (cell c, variable v) = 5 c + v, plus a
 // copying warp that streams the tile's chunks (central; with CWENOZ the
-// directional ones twice, once for the indicators and once for the
-// combination) through a ring of S shared-memory stages, every wait bounded.
+// smoothness matrices, then the directional chunks twice, once for the
+// indicators and once for the combination) through a ring of S shared-memory
+// stages, every wait bounded.
 // Per variable the arithmetic is that of the FP64 form in FP32, members and
 // modes in the same order.  Blocks per SM: P3 three, P4 two (linear) or one
-// (CWENOZ: its smoothness forms need 168 registers a thread without spills).
+// (CWENOZ: 168 registers a thread without spills; two blocks at 80 registers
+// spill and measured no faster).
 template <int ORDER, bool WENO>
 __global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1 : 2) : 3) k_recon_ho_mx(ReconArgsHOMx a) {
   using T = HOTile<ORDER>;
   constexpr int K = T::K, KD = T::KD, ND = 6, TC = T::TC, S = T::S;
-  constexpr int NQ = T::NCC + (WENO ? 2 * ND * T::NDC : 0);  // chunks streamed per tile
+  constexpr int NQ = T::NCC + (WENO ? T::NMC + 2 * ND * T::NDC : 0);  // chunks streamed per tile
   extern __shared__ __align__(128) unsigned char smem[];
   float* st = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(st + S * T::STAGE);
@@ -386,9 +392,20 @@ __global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1
         break;
       }
       // chunk q: central chunks first, then the directional ones in two rounds
-      const int qd = q - T::NCC;
-      const float* src = q < T::NCC ? base + (size_t)q * T::CCS : base + T::CENTRAL + (size_t)(qd % (ND * T::NDC)) * T::DCS;
-      const uint32_t bytes = (q < T::NCC ? T::CCS : T::DCS) * 4u;
+      const float* src;
+      uint32_t bytes;
+      if (q < T::NCC) {
+        src = base + (size_t)q * T::CCS;
+        bytes = T::CCS * 4u;
+      } else if (q < T::NCC + T::NMC) {
+        const int r0 = (q - T::NCC) * T::MSR;
+        src = base + T::CENTRAL + (size_t)r0 * TC;
+        bytes = (uint32_t)(min(T::MSR, T::NQS - r0) * TC) * 4u;
+      } else {
+        const int qd = (q - T::NCC - T::NMC) % (ND * T::NDC);
+        src = base + T::CENTRAL + T::SMAT + (size_t)qd * T::DCS;
+        bytes = T::DCS * 4u;
+      }
       bar_expect(&full[q % S], bytes);
       bulk_load(st + (q % S) * T::STAGE, src, bytes, &full[q % S]);
     }
@@ -431,7 +448,30 @@ __global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1
 #pragma unroll
     for (int k = 0; k < K; k++) cf[k] = ao[k];
   } else {
-    const float SI0 = si_form_f<K, K>(a.Msi, N, i, ao);
+    // a^T M a of the central coefficients, M's entries from the streamed
+    // chunks in row order (each row's diagonal entry read first; the
+    // arithmetic as in si_form)
+    float SI0 = 0.f;
+    {
+      const float* mc = take();
+#pragma unroll
+      for (int k = 0; k < K; k++) {
+        const int q0 = k * K - k * (k - 1) / 2;
+        auto M = [&](int qq) -> float {
+          if (qq % T::MSR == 0 && qq != 0) {
+            give();
+            mc = take();
+          }
+          return mc[(qq % T::MSR) * TC + c];
+        };
+        const float mkk = M(q0);
+        float tk = 0.f;
+#pragma unroll
+        for (int l = k + 1; l < K; l++) tk = fmaf(M(q0 + l - k), ao[l], tk);
+        SI0 = fmaf(ao[k], fmaf(2.f, tk, mkk * ao[k]), SI0);
+      }
+      give();
+    }
     float SI[ND];
     float tau = 0.f;
 #pragma unroll 1

@@ -404,8 +404,11 @@ def roofline(m, prof: dict, form: str, peaks: dict, workload_key: str, frac_dir:
              ("face", True): "k_face_mx<2,true>", ("recon", True): "k_recon_mx<2,true,nd>"}
     name = names[(dom, mixed)]
     if m.K > 9:
-        name = {"face": "k_face_ho%s<%d,true>", "recon": "k_recon_ho%s<%d,true>"}[dom] % (
-            "_mx" if mixed else "", 3 if m.K == 19 else 4)
+        o = 3 if m.K == 19 else 4
+        if dom == "face":  # the mixed face kernel is one kernel for every order
+            name = "k_face_mx<%d,true>" % o if mixed else "k_face_ho<%d,true>" % o
+        else:
+            name = "k_recon_ho%s<%d,true>" % ("_mx" if mixed else "", o)
     if dom == "recon" and mixed and frac_dir < 1.0:
         name = "k_recon_mx<2,false,nd,gated>"
     alu_peak = peaks["fp32"] if mixed else peaks["fp64"]

@@ -241,33 +241,6 @@ int upload_ho_tiles(const ucns_mesh* m, const HostArrays& h, bool weno, float** 
   return upload(dst, b);
 }
 
-int launch_face_ho_mx(ucns_mesh* m, cudaStream_t s) {
-  FaceArgsHOMx a;
-  a.coef = m->d.coeff;
-  a.fq = m->d.fqf;
-  a.fpen = m->d.fpenf;
-  a.fo = m->d.fo;
-  a.fn = m->d.fn;
-  a.G = reinterpret_cast<float*>(m->d.G);  // FP32 totals in the first half
-  a.N = (int)m->N;
-  a.F = (int)m->F;
-  a.cs = coef_row_floats(m);
-  a.c = flux_const_f(m->P);
-  const bool visc = m->P.reynolds > 0.0;
-  const int fpw = 32 / m->nq;
-  const size_t threads = (size_t)((m->F + fpw - 1) / fpw) * 32;
-  const unsigned g = nblocks(threads, 128);
-  if (m->K == 19) {
-    if (visc) k_face_ho_mx<3, true><<<g, 128, 0, s>>>(a);
-    else k_face_ho_mx<3, false><<<g, 128, 0, s>>>(a);
-  } else {
-    if (visc) k_face_ho_mx<4, true><<<g, 128, 0, s>>>(a);
-    else k_face_ho_mx<4, false><<<g, 128, 0, s>>>(a);
-  }
-  UCNS_CUDA(cudaGetLastError());
-  return UCNS_OK;
-}
-
 int launch_recon_mx(ucns_mesh* m, const double* U, cudaStream_t s) {
   if (m->K > 9) return launch_recon_ho_mx(m, s);
   ReconArgsMx a;
@@ -323,7 +296,6 @@ int launch_face_tiles(FaceArgsMx a, cudaStream_t s) {
 }
 
 int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
-  if (m->K > 9) return launch_face_ho_mx(m, s);
   FaceArgsMx a;
   a.coef = m->d.coeff;
   a.fq = m->d.fqf;
@@ -340,8 +312,12 @@ int launch_face_mx(ucns_mesh* m, cudaStream_t s) {
   a.stages = 2;
   a.c = flux_const_f(m->P);
   const bool visc = m->P.reynolds > 0.0;
-  if (m->K == 3) return visc ? launch_face_tiles<1, true>(a, s) : launch_face_tiles<1, false>(a, s);
-  return visc ? launch_face_tiles<2, true>(a, s) : launch_face_tiles<2, false>(a, s);
+  switch (m->K) {
+    case 3: return visc ? launch_face_tiles<1, true>(a, s) : launch_face_tiles<1, false>(a, s);
+    case 9: return visc ? launch_face_tiles<2, true>(a, s) : launch_face_tiles<2, false>(a, s);
+    case 19: return visc ? launch_face_tiles<3, true>(a, s) : launch_face_tiles<3, false>(a, s);
+    default: return visc ? launch_face_tiles<4, true>(a, s) : launch_face_tiles<4, false>(a, s);
+  }
 }
 
 // P3 / P4 (FP64, hexahedra)
@@ -1085,10 +1061,16 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   }
   if (p->precision == UCNS_PREC_MIXED && m->K > 9) {
     const bool weno = m->nd > 0;
+    const int64_t fpad = (m->F + kFacePad - 1) / kFacePad * kFacePad;  // whole batches for the face kernel's copies
+    std::vector<int32_t> fslot, bcell, bcount;
+    int nu = 0;
+    face_batches(fo, fn, m->N, face_batch_faces(m->nq), fpad, fslot, bcell, bcount, nu);
+    d.fnu = nu;
     rc = m->K == 19 ? upload_ho_tiles<3>(m, h, weno, &d.hot) : upload_ho_tiles<4>(m, h, weno, &d.hot);
     if (rc || (rc = upload_f32(&d.Msif, h.Msi)) ||
         (rc = upload_f32(&d.psibf, h.psib)) || (rc = upload_f32(&d.inv_hf, h.inv_h)) ||
-        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F)) || (rc = upload_f32(&d.fpenf, h.fpen)) ||
+        (rc = upload_cellwise(&d.fqf, h.fq, m->nq * 10, m->F, fpad)) || (rc = upload_f32(&d.fpenf, h.fpen, fpad)) ||
+        (rc = upload(&d.fslot, fslot)) || (rc = upload(&d.bcell, bcell)) || (rc = upload(&d.bcount, bcount)) ||
         (rc = alloc(&d.coeff, (size_t)coef_row_floats(m) * m->N)) || (rc = alloc(&d.Uhl, (size_t)10 * m->N))) {
       device_free(m);
       return rc;
@@ -1098,7 +1080,7 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
     const int64_t fpad = (m->F + kFacePad - 1) / kFacePad * kFacePad;  // whole batches for the face kernel's copies
     std::vector<int32_t> fslot, bcell, bcount;
     int nu = 0;
-    face_batches(fo, fn, m->N, kFacePts / m->nq, fpad, fslot, bcell, bcount, nu);
+    face_batches(fo, fn, m->N, face_batch_faces(m->nq), fpad, fslot, bcell, bcount, nu);
     d.fnu = nu;
     std::vector<double> cellrows((size_t)kCellRows * m->N);
     std::copy(h.mom.begin(), h.mom.begin() + (size_t)6 * m->N, cellrows.begin());

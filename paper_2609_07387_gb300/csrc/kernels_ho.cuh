@@ -17,7 +17,7 @@
 //   k_recon_ho_mx the same in the mixed form, tile by tile (64 cells): the
 //               stencil ids and FP32 pseudo-inverses stream through shared
 //               memory in bulk-copied chunks, thread = (cell, variable).
-//   k_face_ho_mx  k_face_ho in the mixed form.
+//   (the mixed face kernel of every order is k_face_mx, kernels_mixed.cuh)
 #pragma once
 
 #include "basis.hpp"
@@ -538,150 +538,6 @@ __global__ void __launch_bounds__(HOTile<ORDER>::THREADS, ORDER == 4 ? (WENO ? 1
   out[cidx(v, 0, K + 1)] = c0;
 #pragma unroll
   for (int k = 0; k < K; k++) out[cidx(v, k + 1, K + 1)] = cf[k] * ihp[basis_degree(k)];
-}
-
-// value and gradient at (x, y, z) of a cell's polynomial from its row
-// (entries cidx(v, k, K + 1)): variables 0-3 in packed FP32x2 pairs from one
-// 16-byte load per mode, variable 4 from four modes per 16-byte load
-template <int ORDER, bool ACC>
-__device__ __forceinline__ void eval_side_ho_mx(const float* __restrict__ row, float x, float y, float z, float U[5],
-                                                float g[5][3]) {
-  constexpr int K = basis_count(ORDER), NCF = K + 1;
-  const float4* r4 = reinterpret_cast<const float4*>(row);
-  float px[ORDER + 1], py[ORDER + 1], pz[ORDER + 1];
-  px[0] = py[0] = pz[0] = 1.f;
-#pragma unroll
-  for (int e = 1; e <= ORDER; e++) {
-    px[e] = px[e - 1] * x;
-    py[e] = py[e - 1] * y;
-    pz[e] = pz[e - 1] * z;
-  }
-  float e4[4 * ((NCF + 3) / 4)];  // variable 4's entries
-#pragma unroll
-  for (int j = 0; j < (NCF + 3) / 4; j++) {
-    const float4 t = __ldg(r4 + NCF + j);
-    e4[4 * j] = t.x;
-    e4[4 * j + 1] = t.y;
-    e4[4 * j + 2] = t.z;
-    e4[4 * j + 3] = t.w;
-  }
-  const float4 c0 = __ldg(r4);
-  float2 u01 = make_float2(c0.x, c0.y), u23 = make_float2(c0.z, c0.w);
-  float2 gx01 = make_float2(0.f, 0.f), gx23 = gx01, gy01 = gx01, gy23 = gx01, gz01 = gx01, gz23 = gx01;
-  float u4 = e4[0], gx4 = 0.f, gy4 = 0.f, gz4 = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; k++) {
-    const int ex = basis_exp(k, 0), ey = basis_exp(k, 1), ez = basis_exp(k, 2);
-    const float mv = px[ex] * py[ey] * pz[ez];
-    const float4 cq = __ldg(r4 + k + 1);
-    const float2 c01 = make_float2(cq.x, cq.y), c23 = make_float2(cq.z, cq.w);
-    const float c4 = e4[k + 1];
-    u01 = __ffma2_rn(c01, make_float2(mv, mv), u01);
-    u23 = __ffma2_rn(c23, make_float2(mv, mv), u23);
-    u4 = fmaf(c4, mv, u4);
-    if (ex) {
-      const float m = ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez];
-      gx01 = __ffma2_rn(c01, make_float2(m, m), gx01);
-      gx23 = __ffma2_rn(c23, make_float2(m, m), gx23);
-      gx4 = fmaf(c4, m, gx4);
-    }
-    if (ey) {
-      const float m = ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez];
-      gy01 = __ffma2_rn(c01, make_float2(m, m), gy01);
-      gy23 = __ffma2_rn(c23, make_float2(m, m), gy23);
-      gy4 = fmaf(c4, m, gy4);
-    }
-    if (ez) {
-      const float m = ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0];
-      gz01 = __ffma2_rn(c01, make_float2(m, m), gz01);
-      gz23 = __ffma2_rn(c23, make_float2(m, m), gz23);
-      gz4 = fmaf(c4, m, gz4);
-    }
-  }
-  const float u[5] = {u01.x, u01.y, u23.x, u23.y, u4};
-  const float gx[5] = {gx01.x, gx01.y, gx23.x, gx23.y, gx4}, gy[5] = {gy01.x, gy01.y, gy23.x, gy23.y, gy4},
-              gz[5] = {gz01.x, gz01.y, gz23.x, gz23.y, gz4};
-#pragma unroll
-  for (int v = 0; v < 5; v++) {
-    U[v] = u[v];
-    if (ACC) {
-      g[v][0] += gx[v];
-      g[v][1] += gy[v];
-      g[v][2] += gz[v];
-    } else {
-      g[v][0] = gx[v];
-      g[v][1] = gy[v];
-      g[v][2] = gz[v];
-    }
-  }
-}
-
-struct FaceArgsHOMx {
-  const float* __restrict__ coef;  // [N][cs] rows as the reconstruction writes them
-  const float* __restrict__ fq;    // [F][nq][10]: x - x_L, x - x_R', n, |dS| of each Gauss point
-  const float* __restrict__ fpen;
-  const int32_t* __restrict__ fo;
-  const int32_t* __restrict__ fn;
-  float* __restrict__ G;  // [5][F] FP32 face totals
-  int N, F, cs;
-  FluxConstF c;
-};
-
-template <int ORDER, bool VISC>
-__global__ void __launch_bounds__(128) k_face_ho_mx(FaceArgsHOMx a) {
-  constexpr int NQ = ORDER * ORDER, FPW = 32 / NQ;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int grp = lane / NQ, q = lane - NQ * (lane / NQ);
-  const bool in_group = grp < FPW;
-  const int f = gw * FPW + (in_group ? grp : 0);
-  const bool live = in_group && f < a.F;
-  const int fc = live ? f : a.F - 1, qc = in_group ? q : 0;
-  const size_t F = a.F;
-  const float2* __restrict__ fq = reinterpret_cast<const float2*>(a.fq + ((size_t)fc * NQ + qc) * 10);
-  const float2 q0 = __ldg(fq), q1 = __ldg(fq + 1), q2 = __ldg(fq + 2), q3 = __ldg(fq + 3), q4 = __ldg(fq + 4);
-  const float n[3] = {q3.x, q3.y, q4.x};
-  const float area = q4.y;
-  const int o = a.fo[fc], nb = a.fn[fc];
-  float WL[5], WR[5], gs[5][3];
-  eval_side_ho_mx<ORDER, false>(a.coef + (size_t)o * a.cs, q0.x, q0.y, q1.x, WL, gs);
-  eval_side_ho_mx<ORDER, true>(a.coef + (size_t)nb * a.cs, q1.y, q2.x, q2.y, WR, gs);
-  float Fc[5];
-  hllc_flux_mx(WL, WR, n, a.c, Fc);
-  float flux[5];
-  if (VISC) {
-    // as in k_face_mx: twice the penalised face gradient, the flux of which is twice F_v
-    const float pen2 = 2.f * a.fpen[fc];
-    float Wf[5], gf2[5][3];
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float jump2 = pen2 * (WR[v] - WL[v]);
-      Wf[v] = 0.5f * (WL[v] + WR[v]);
-#pragma unroll
-      for (int j = 0; j < 3; j++) gf2[v][j] = fmaf(jump2, n[j], gs[v][j]);
-    }
-    float Fv2[5];
-    viscous_flux_mx(Wf, gf2, n, a.c, Fv2);
-#pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] = fmaf(-0.5f, Fv2[v], Fc[v]) * area;
-  } else {
-#pragma unroll
-    for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
-  }
-  // the group's sum on its first lane, a fixed tree over the point order
-  // (lanes past the group contribute nothing)
-#pragma unroll
-  for (int off = 8; off >= 1; off >>= 1) {
-    if (off >= NQ) continue;
-#pragma unroll
-    for (int v = 0; v < 5; v++) {
-      const float o = __shfl_down_sync(0xffffffffu, flux[v], off);
-      if (q + off < NQ) flux[v] += o;
-    }
-  }
-  if (live && q == 0) {
-#pragma unroll
-    for (int v = 0; v < 5; v++) a.G[(size_t)v * F + f] = flux[v];
-  }
 }
 
 }  // namespace ucns

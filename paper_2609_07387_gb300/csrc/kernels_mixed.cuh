@@ -18,6 +18,7 @@
 // (U* - U = r U + ...), which keeps every FP32 term O(1).
 #pragma once
 
+#include "basis.hpp"
 #include "bulk.cuh"
 #include "kernels.cuh"
 
@@ -118,28 +119,31 @@ struct FaceArgsMx {
 };
 
 // The face kernel's pipeline.  A persistent block has kFaceWarps warps that
-// evaluate (thread = one Gauss point, kFacePts points a batch) and
-// kFaceCopyWarps warps that copy, batch by batch in turn.  Faces are taken in
-// batches of kFacePts / nq; a copying warp brings each batch's Gauss points, penalty factors and row slots (bulk
-// copies) and the coefficient rows of its distinct cells (each once, a cell
-// shared by several of the batch's faces included; 16-byte asynchronous
-// copies spread over the lanes) into one of `stages` shared-memory stages, up
-// to stages - 1 batches ahead of the evaluating warps, which hand a stage
-// back through its "empty" barrier.
+// evaluate (thread = one Gauss point; a warp takes 32 / nq whole faces, so
+// 9-point faces leave 5 lanes idle) and kFaceCopyWarps warps that copy,
+// batch by batch in turn.  A copying warp brings each batch's Gauss points,
+// penalty factors and row slots (bulk copies) and the coefficient rows of its
+// distinct cells (each once, a cell shared by several of the batch's faces
+// included; 16-byte asynchronous copies spread over the lanes) into one of
+// `stages` shared-memory stages, up to stages - 1 batches ahead of the
+// evaluating warps, which hand a stage back through its "empty" barrier.
 constexpr int kFaceWarps = 16;
 constexpr int kFaceCopyWarps = 3;  // copying warp w takes the block's batches k = w mod 3
 constexpr int kFaceThreads = 32 * (kFaceWarps + kFaceCopyWarps);
-constexpr int kFacePts = 32 * kFaceWarps;
-constexpr int kFacePad = kFacePts;  // the per-face arrays hold whole batches at every order
+constexpr int kFacePad = 1536;     // the per-face arrays hold whole batches at every order (512, 128, 48, 32 faces)
 constexpr int kFaceMaxStages = 6;
+
+// faces per batch for nq Gauss points per face
+__host__ __device__ constexpr int face_batch_faces(int nq) { return kFaceWarps * (32 / nq); }
 
 template <int ORDER>
 struct FaceTileMx {
   static constexpr int NQ = ORDER * ORDER;
-  static constexpr int CS = ORDER == 1 ? 20 : 52;  // floats per coefficient row
-  static constexpr int FB = kFacePts / NQ;         // faces per batch
-  static constexpr int PTS = kFacePts * 10;        // the batch's Gauss points
-  static constexpr int NUR = 2 * FB / 32;          // slot registers per lane of a copying warp
+  static constexpr int FPW = 32 / NQ;                                                // faces per warp
+  static constexpr int CS = ORDER == 1 ? 20 : (ORDER == 2 ? 52 : (ORDER == 3 ? 100 : 176));  // floats per row
+  static constexpr int FB = face_batch_faces(NQ);                                    // faces per batch
+  static constexpr int PTS = FB * NQ * 10;                                           // the batch's Gauss points
+  static constexpr int NUR = (2 * FB + 31) / 32;  // slot registers per lane of a copying warp
   // a stage: Gauss points, penalties, slot words, then nu rows
   __host__ __device__ static constexpr int stage_floats(int nu) { return PTS + 2 * FB + nu * CS; }
   __host__ __device__ static constexpr size_t smem(int nu, int stages) {
@@ -595,6 +599,83 @@ __device__ __forceinline__ void viscous_flux_mx(const float W[5], const float g[
   Fv[4] = work + c.kap * c.gm1_over_R * qn;
 }
 
+// value and gradient at (x, y, z) of a P3/P4 cell polynomial from its row
+// (entries cidx(v, k, K + 1), in global or shared memory): variables 0-3 in
+// packed FP32x2 pairs from one 16-byte load per mode, variable 4 from four
+// modes per 16-byte load
+template <int ORDER, bool ACC>
+__device__ __forceinline__ void eval_side_ho_mx(const float* row, float x, float y, float z, float U[5],
+                                                float g[5][3]) {
+  constexpr int K = basis_count(ORDER), NCF = K + 1;
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+  float px[ORDER + 1], py[ORDER + 1], pz[ORDER + 1];
+  px[0] = py[0] = pz[0] = 1.f;
+#pragma unroll
+  for (int e = 1; e <= ORDER; e++) {
+    px[e] = px[e - 1] * x;
+    py[e] = py[e - 1] * y;
+    pz[e] = pz[e - 1] * z;
+  }
+  float e4[4 * ((NCF + 3) / 4)];  // variable 4's entries
+#pragma unroll
+  for (int jj = 0; jj < (NCF + 3) / 4; jj++) {
+    const float4 t = r4[NCF + jj];
+    e4[4 * jj] = t.x;
+    e4[4 * jj + 1] = t.y;
+    e4[4 * jj + 2] = t.z;
+    e4[4 * jj + 3] = t.w;
+  }
+  const float4 c0 = r4[0];
+  float2 u01 = make_float2(c0.x, c0.y), u23 = make_float2(c0.z, c0.w);
+  float2 gx01 = make_float2(0.f, 0.f), gx23 = gx01, gy01 = gx01, gy23 = gx01, gz01 = gx01, gz23 = gx01;
+  float u4 = e4[0], gx4 = 0.f, gy4 = 0.f, gz4 = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const int ex = basis_exp(k, 0), ey = basis_exp(k, 1), ez = basis_exp(k, 2);
+    const float mv = px[ex] * py[ey] * pz[ez];
+    const float4 cq = r4[k + 1];
+    const float2 c01 = make_float2(cq.x, cq.y), c23 = make_float2(cq.z, cq.w);
+    const float c4 = e4[k + 1];
+    u01 = __ffma2_rn(c01, make_float2(mv, mv), u01);
+    u23 = __ffma2_rn(c23, make_float2(mv, mv), u23);
+    u4 = fmaf(c4, mv, u4);
+    if (ex) {
+      const float m = ex * px[ex > 0 ? ex - 1 : 0] * py[ey] * pz[ez];
+      gx01 = __ffma2_rn(c01, make_float2(m, m), gx01);
+      gx23 = __ffma2_rn(c23, make_float2(m, m), gx23);
+      gx4 = fmaf(c4, m, gx4);
+    }
+    if (ey) {
+      const float m = ey * px[ex] * py[ey > 0 ? ey - 1 : 0] * pz[ez];
+      gy01 = __ffma2_rn(c01, make_float2(m, m), gy01);
+      gy23 = __ffma2_rn(c23, make_float2(m, m), gy23);
+      gy4 = fmaf(c4, m, gy4);
+    }
+    if (ez) {
+      const float m = ez * px[ex] * py[ey] * pz[ez > 0 ? ez - 1 : 0];
+      gz01 = __ffma2_rn(c01, make_float2(m, m), gz01);
+      gz23 = __ffma2_rn(c23, make_float2(m, m), gz23);
+      gz4 = fmaf(c4, m, gz4);
+    }
+  }
+  const float u[5] = {u01.x, u01.y, u23.x, u23.y, u4};
+  const float gx[5] = {gx01.x, gx01.y, gx23.x, gx23.y, gx4}, gy[5] = {gy01.x, gy01.y, gy23.x, gy23.y, gy4},
+              gz[5] = {gz01.x, gz01.y, gz23.x, gz23.y, gz4};
+#pragma unroll
+  for (int v = 0; v < 5; v++) {
+    U[v] = u[v];
+    if (ACC) {
+      g[v][0] += gx[v];
+      g[v][1] += gy[v];
+      g[v][2] += gz[v];
+    } else {
+      g[v][0] = gx[v];
+      g[v][1] = gy[v];
+      g[v][2] = gz[v];
+    }
+  }
+}
+
 template <int ORDER, bool VISC>
 __global__ void __launch_bounds__(kFaceThreads, 1) k_face_mx(FaceArgsMx a) {
   using T = FaceTileMx<ORDER>;
@@ -677,7 +758,12 @@ __global__ void __launch_bounds__(kFaceThreads, 1) k_face_mx(FaceArgsMx a) {
         if ((kk - w0) % kFaceCopyWarps == 0) bar_wait(&full[kk % S], (uint32_t)(kk / S) & 1u);
     return;
   }
-  const int j = t / NQ, q = t - NQ * (t / NQ);
+  // this thread's face j of the batch and point q: warp w takes faces
+  // w FPW .. w FPW + FPW - 1 (lanes past them compute a copy of the first and
+  // write nothing)
+  constexpr int FPW = T::FPW;
+  const int grp = lane / NQ, in_grp = grp < FPW;
+  const int j = warp * FPW + (in_grp ? grp : 0), q = in_grp ? lane - NQ * grp : 0;
   for (int k = 0; k < mine; k++) {
     const int s = k % S;
     const bool ok = __all_sync(0xffffffffu, bar_wait(&full[s], (uint32_t)(k / S) & 1u));
@@ -688,15 +774,20 @@ __global__ void __launch_bounds__(kFaceThreads, 1) k_face_mx(FaceArgsMx a) {
     const int f = ((int)blockIdx.x + k * (int)gridDim.x) * FB + j;
     const float* sr = st + (size_t)s * SF;
     // the point's 10 floats: five 8-byte loads
-    const float2* fq = reinterpret_cast<const float2*>(sr + t * 10);
+    const float2* fq = reinterpret_cast<const float2*>(sr + (j * NQ + q) * 10);
     const float2 q0 = fq[0], q1 = fq[1], q2 = fq[2], q3 = fq[3], q4 = fq[4];
     const float n[3] = {q3.x, q3.y, q4.x};
     const float area = q4.y;
     const int slots = reinterpret_cast<const int*>(sr + T::PTS + FB)[j];
     const float* rows = sr + T::PTS + 2 * FB;
     float WL[5], WR[5], gs[5][3];  // gs = grad U_L + grad U_R
-    eval_side_mx<ORDER, false>(rows + (slots & 0xffff) * CS, q0.x, q0.y, q1.x, WL, gs);
-    eval_side_mx<ORDER, true>(rows + (slots >> 16) * CS, q1.y, q2.x, q2.y, WR, gs);
+    if constexpr (ORDER <= 2) {
+      eval_side_mx<ORDER, false>(rows + (slots & 0xffff) * CS, q0.x, q0.y, q1.x, WL, gs);
+      eval_side_mx<ORDER, true>(rows + (slots >> 16) * CS, q1.y, q2.x, q2.y, WR, gs);
+    } else {
+      eval_side_ho_mx<ORDER, false>(rows + (slots & 0xffff) * CS, q0.x, q0.y, q1.x, WL, gs);
+      eval_side_ho_mx<ORDER, true>(rows + (slots >> 16) * CS, q1.y, q2.x, q2.y, WR, gs);
+    }
     const float pen2 = 2.f * sr[T::PTS + j];
     __syncwarp();
     if (lane == 0) bar_arrive(&empty[s]);  // this warp is done reading the stage
@@ -724,11 +815,21 @@ __global__ void __launch_bounds__(kFaceThreads, 1) k_face_mx(FaceArgsMx a) {
 #pragma unroll
       for (int v = 0; v < 5; v++) flux[v] = Fc[v] * area;
     }
+    if constexpr ((NQ & (NQ - 1)) == 0) {  // groups of 1, 4 or 16 lanes: a butterfly
 #pragma unroll
-    for (int off = 1; off < NQ; off <<= 1)
+      for (int off = 1; off < NQ; off <<= 1)
 #pragma unroll
-      for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
-    if (f < a.F && q == 0) {
+        for (int v = 0; v < 5; v++) flux[v] += __shfl_xor_sync(0xffffffffu, flux[v], off);
+    } else {  // 9 lanes: a fixed tree onto the group's first lane
+#pragma unroll
+      for (int off = 8; off >= 1; off >>= 1)
+#pragma unroll
+        for (int v = 0; v < 5; v++) {
+          const float o = __shfl_down_sync(0xffffffffu, flux[v], off);
+          if (q + off < NQ) flux[v] += o;
+        }
+    }
+    if (in_grp && f < a.F && q == 0) {
 #pragma unroll
       for (int v = 0; v < 5; v++) a.G[(size_t)v * a.F + f] = flux[v];
     }

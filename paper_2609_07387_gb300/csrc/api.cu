@@ -993,7 +993,7 @@ int ucns_stencil(const ucns_mesh* m, int64_t cell, int32_t which, int64_t* membe
 // distinct cells of its faces' owners and neighbours in order of first use,
 // per face the slots of its two rows (owner | neighbour << 16); arrays padded
 // to fpad faces.  nu = the largest count, rounded up to a multiple of 4.
-void face_batches(const std::vector<int32_t>& fo, const std::vector<int32_t>& fn, int64_t N, int fb, int64_t fpad,
+static void face_batches(const std::vector<int32_t>& fo, const std::vector<int32_t>& fn, int64_t N, int fb, int64_t fpad,
                   std::vector<int32_t>& fslot, std::vector<int32_t>& bcell, std::vector<int32_t>& bcount, int& nu) {
   const int64_t F = (int64_t)fo.size(), nbat = (F + fb - 1) / fb;
   std::vector<int64_t> stamp((size_t)N, -1);
@@ -1029,17 +1029,10 @@ void face_batches(const std::vector<int32_t>& fo, const std::vector<int32_t>& fn
     for (int32_t u = 0; u < bcount[b]; u++) bcell[(size_t)b * nu + u] = order[o++];
 }
 
-int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
-  int rc = check_params(m, p);
-  if (rc) return rc;
-  HostArrays h;
-  try {
-    rc = host_precompute(m, p, &h);
-    m->host.reset();
-  } catch (const std::bad_alloc&) {
-    rc = fail(UCNS_ERR_NOMEM, "out of host memory");
-  }
-  if (rc) return rc;
+// the device arrays of a precomputed mesh (host vectors built here may
+// throw std::bad_alloc; the caller turns that into an error code)
+static int device_upload(ucns_mesh* m, const ucns_params* p, const HostArrays& h) {
+  int rc = UCNS_OK;
   device_free(m);
   m->precomputed = false;
   m->P = *p;
@@ -1119,6 +1112,25 @@ int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
   UCNS_CUDA(cudaDeviceSynchronize());
   m->precomputed = true;
   return UCNS_OK;
+}
+
+int ucns_precompute(ucns_mesh* m, const ucns_params* p) {
+  int rc = check_params(m, p);
+  if (rc) return rc;
+  HostArrays h;
+  try {
+    rc = host_precompute(m, p, &h);
+    m->host.reset();
+  } catch (const std::bad_alloc&) {
+    rc = fail(UCNS_ERR_NOMEM, "out of host memory");
+  }
+  if (rc) return rc;
+  try {
+    return device_upload(m, p, h);
+  } catch (const std::bad_alloc&) {
+    device_free(m);
+    return fail(UCNS_ERR_NOMEM, "out of host memory while uploading the precompute");
+  }
 }
 
 int ucns_residual(ucns_mesh* m, const double* U, double* R, void* stream) {

@@ -148,8 +148,12 @@ int ucns_mesh_set_boundary(ucns_mesh* mesh, const int32_t* kinds, const double* 
  * FP64 on the host), uploaded to the current CUDA device once.  May be called
  * again with other parameters (re-uploads).  Meshes with boundary faces need
  * an inviscid flow (reynolds <= 0); boundary faces, prisms and pyramids are
- * built in the FP64 form at P1 and P2.  Errors: INVALID_ARG, STENCIL, CUDA,
- * NOMEM. */
+ * built in the FP64 form at P1 and P2.  Device memory is dominated by the
+ * pseudo-inverses: per cell about 2.7 KB (P2 FP64 CWENOZ), 9 / 33 KB (P3 / P4
+ * FP64) and 4.4 / 16.2 KB (P3 / P4 mixed, held in 64-cell tile records); the
+ * host needs the FP64 arrays and, briefly, the device layout's copy.  Errors:
+ * INVALID_ARG, STENCIL, CUDA, NOMEM (also when the host runs out of memory
+ * while building the device arrays; nothing stays allocated). */
 int ucns_precompute(ucns_mesh* mesh, const ucns_params* params);
 
 /* Host half of ucns_precompute only (no CUDA call): geometry, stencils and

@@ -1,7 +1,8 @@
 """Host logic of the indicator workflow on CPU (no GPU): the decision
 threshold keeps the requested recall of the troubled class, the confusion
-counts partition the samples, and the class weights balance the two classes
-(each contributes half of the loss weight)."""
+counts partition the samples, the class weights balance the two classes
+(each contributes half of the loss weight), and the fixed-error comparison's
+history error measure."""
 import numpy as np
 import pytest
 
@@ -54,3 +55,23 @@ def test_class_weights_balance_the_classes():
     w_pos, w_neg = gate.class_weights(y)
     p = float(y.mean().item())
     assert abs(w_pos * p - 0.5) < 1e-12 and abs(w_neg * (1 - p) - 0.5) < 1e-12
+
+
+def test_history_error_columns_and_the_dilatational_floor():
+    """Relative history errors per column (KE, eps_s, eps_d), the worst over
+    the history; eps_d is measured against max(|eps_d|, 1e-3 |eps_s|), so at a
+    vanishing eps_d (low Mach number) the error is relative to eps_s's scale."""
+    ref = np.array([[1.0, 2.0, 0.5], [0.9, 4.0, 1e-9], [0.8, 8.0, 0.25]])
+    h = ref.copy()
+    h[0, 0] *= 1 + 3e-5          # KE off by 3e-5 at the first record
+    h[2, 1] *= 1 - 2e-5          # eps_s off by 2e-5 at the last
+    h[1, 2] = 1e-9 + 4e-4 * 1e-3 * 4.0  # eps_d off by 4e-4 of the floor 1e-3 eps_s
+    h[2, 2] *= 1 + 1e-6
+    e = gate.history_error(h, ref)
+    assert np.allclose(e, [3e-5, 2e-5, 4e-4], rtol=1e-9, atol=0)
+    # where eps_d is above the floor it is an ordinary relative error
+    h2 = ref.copy()
+    h2[0, 2] *= 1 + 7e-5
+    assert np.isclose(gate.history_error(h2, ref)[2], 7e-5, rtol=1e-9)
+    # identical histories: no error
+    assert gate.history_error(ref, ref) == [0.0, 0.0, 0.0]

@@ -382,7 +382,8 @@ def algorithmic_ho(m, kind: str, w: int = 8) -> dict:
         g = sum(sum(1 for e in b if e) for b in basis)
         flops = F * nq * (2 * 5 * 2 * (K + g) + 2 * 4 * K + 358)
         alg = F * (nq * 6 * w + 3 * w + 4 + 2 * 4 + 5 * w) + N * (K + 1) * 5 * w
-        layout = F * (nq * 10 * w + w + 2 * 4 + 5 * w) + N * (K + 1) * 5 * w
+        row = (((K + 1) * 5 + 3) // 4 * 4) * 4 if w == 4 else (K + 1) * 5 * w  # mixed: 16-byte rows
+        layout = F * (nq * 10 * w + w + 2 * 4 + 5 * w) + N * row
     else:
         cen = 5 * (2 * K * m.Mc + m.Mc)
         dirf = 5 * 2 * (2 * m.nd * kd * m.Md + m.nd * m.Md) + 5 * 2 * (K * K + m.nd * kd * kd) + 5 * 60
